@@ -1,0 +1,144 @@
+"""Seeded synthetic edge streams (inputs only: no part of the update method lives here).
+
+The paper evaluates on sliding-window streams over Reddit, Pokec, a Graph500
+R-MAT graph and an Erdos-Renyi graph (Sec. 6.1, "Datasets" and "Stream
+Setup"): edges arrive in timestamp order, the first part of the stream is the
+initial graph, and every slide deletes the oldest edges of a fixed-size window
+and inserts the newest ones.  The real datasets are not available, so every
+stream here is synthetic with the shapes the paper states:
+
+* ``er_stream``      -- uniform random directed edges (the "Random" dataset);
+* ``rmat_stream``    -- R-MAT with Graph500 parameters a,b,c,d = .57,.19,.19,.05
+                        (the "Graph500" dataset), vertex ids permuted by a seeded
+                        permutation as the Graph500 generator does;
+* ``chung_lu_stream`` -- power-law expected degrees (stand-in for Pokec).
+
+Every stream is seeded (numpy PCG64), has no self-loops and no repeated edge:
+an edge appears at most once over the whole stream, so a slide never inserts an
+edge that is still inside the window.  Stream order is generation order, which
+plays the role of the paper's random timestamps.  Keys are uint64
+``(src << 32) | dst``.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+
+def make_keys(src: np.ndarray, dst: np.ndarray) -> np.ndarray:
+    return (src.astype(np.uint64) << np.uint64(32)) | dst.astype(np.uint64)
+
+
+def split_keys(keys: np.ndarray):
+    keys = np.asarray(keys, dtype=np.uint64)
+    return (keys >> np.uint64(32)).astype(np.int64), (keys & np.uint64(0xFFFFFFFF)).astype(np.int64)
+
+
+def _unique_in_order(keys: np.ndarray) -> np.ndarray:
+    """Drop repeated keys, keeping each key's first occurrence, in stream order."""
+    _, first = np.unique(keys, return_index=True)
+    first.sort()
+    return keys[first]
+
+
+def _grow(sampler, need: int, rng, chunk: int) -> np.ndarray:
+    """Draw chunks until ``need`` distinct edges exist; stream order is preserved."""
+    out = np.empty(0, np.uint64)
+    while out.size < need:
+        cand = sampler(rng, chunk)
+        out = _unique_in_order(np.concatenate([out, cand]))
+        chunk = max(chunk // 2, 1 << 16)
+    return out[:need]
+
+
+def er_stream(n_vertices: int, n_edges: int, seed: int = 0) -> np.ndarray:
+    """``n_edges`` distinct uniform random directed edges, no self-loops."""
+    def sampler(rng, n):
+        s = rng.integers(0, n_vertices, n, dtype=np.int64)
+        d = rng.integers(0, n_vertices, n, dtype=np.int64)
+        keep = s != d
+        return make_keys(s[keep], d[keep])
+    rng = np.random.Generator(np.random.PCG64(seed))
+    return _grow(sampler, n_edges, rng, int(n_edges * 1.1) + 16)
+
+
+RMAT_GRAPH500 = (0.57, 0.19, 0.19, 0.05)
+
+
+def rmat_stream(scale: int, n_edges: int, seed: int = 1, abcd=RMAT_GRAPH500,
+                permute: bool = True, samples: int | None = None) -> np.ndarray:
+    """R-MAT stream over 2^scale vertices.
+
+    Each sample descends ``scale`` levels of the adjacency matrix choosing the
+    quadrant (a, b, c, d) independently per level.  Vertex ids are relabelled by
+    one seeded permutation (shared by src and dst).  Self-loops and repeats are
+    dropped; sampling continues until ``n_edges`` distinct edges exist.
+    ``samples`` fixes the size of the first draw (e.g. 2^scale * 16).
+    """
+    a, b, c, _ = abcd
+    n = 1 << scale
+    rng = np.random.Generator(np.random.PCG64(seed))
+    perm = rng.permutation(n).astype(np.int64) if permute else np.arange(n, dtype=np.int64)
+
+    def sampler(rng, m):
+        src = np.zeros(m, np.int64)
+        dst = np.zeros(m, np.int64)
+        for _ in range(scale):
+            r = rng.random(m)
+            sb = r >= a + b
+            db = ((r >= a) & (r < a + b)) | (r >= a + b + c)
+            src = (src << 1) | sb
+            dst = (dst << 1) | db
+        keep = src != dst
+        return make_keys(perm[src[keep]], perm[dst[keep]])
+    first = samples if samples is not None else int(n_edges * 1.2) + 16
+    return _grow(sampler, n_edges, rng, first)
+
+
+def chung_lu_stream(n_vertices: int, n_edges: int, gamma: float = 2.1, seed: int = 7) -> np.ndarray:
+    """Directed Chung-Lu stream: both endpoints drawn independently with
+    probability proportional to w_i = (i+1)^(-1/(gamma-1))."""
+    w = (np.arange(n_vertices, dtype=np.float64) + 1.0) ** (-1.0 / (gamma - 1.0))
+    cdf = np.cumsum(w)
+    cdf /= cdf[-1]
+
+    def sampler(rng, m):
+        s = np.searchsorted(cdf, rng.random(m), side="right").clip(0, n_vertices - 1)
+        d = np.searchsorted(cdf, rng.random(m), side="right").clip(0, n_vertices - 1)
+        keep = s != d
+        return make_keys(s[keep], d[keep])
+    rng = np.random.Generator(np.random.PCG64(seed))
+    return _grow(sampler, n_edges, rng, int(n_edges * 1.3) + 16)
+
+
+class SlidingWindow:
+    """Fixed-size window over a stream (Sec. 6.1 "Stream Setup").
+
+    ``initial`` is the first ``window`` edges.  ``slide(k)`` returns
+    (inserts, deletes): the next ``k`` stream edges and the ``k`` oldest edges
+    of the window.
+    """
+
+    def __init__(self, stream: np.ndarray, window: int):
+        self.stream = np.asarray(stream, dtype=np.uint64)
+        self.window = int(window)
+        self.head = 0               # oldest edge still in the window
+        self.tail = self.window     # next edge to arrive
+
+    @property
+    def initial(self) -> np.ndarray:
+        return self.stream[: self.window]
+
+    def remaining(self) -> int:
+        return self.stream.size - self.tail
+
+    def slide(self, k: int):
+        if self.tail + k > self.stream.size:
+            raise IndexError("stream exhausted")
+        ins = self.stream[self.tail: self.tail + k]
+        dels = self.stream[self.head: self.head + k]
+        self.tail += k
+        self.head += k
+        return ins, dels
+
+    def live(self) -> np.ndarray:
+        return self.stream[self.head: self.tail]
