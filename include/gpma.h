@@ -1,0 +1,172 @@
+/*
+ * gpma.h -- C ABI of libgpma: a dynamic graph stored on one GB300 GPU as a GPMA+
+ * packed memory array (Sha, Li, He, Tan, "Accelerating Dynamic Graph Analytics on
+ * GPUs").
+ *
+ * Storage (Sec. 4.1 "Background of PMA", Sec. 4.2 Example 4): a sorted array of
+ * 64-bit keys (src << 32 | dst) with gaps (EMPTY = all ones), cut into leaf
+ * segments of L slots; a segment at height i spans L * 2^i slots.  Every vertex
+ * u owns a guard key (u << 32 | 0xFFFFFFFF) that sits right after its row, so
+ * the array doubles as CSR: row u is the valid, non-guard slots between the
+ * guard of u-1 and the guard of u.
+ *
+ * Conventions for every call:
+ *  - pointers named d_* are DEVICE pointers owned by the caller; they must stay
+ *    valid until the work enqueued on `stream` has finished;
+ *  - `stream` is a cudaStream_t passed as void* (NULL = the legacy default
+ *    stream); all work is stream-ordered on it;
+ *  - the library owns the array and its scratch memory (allocated through the
+ *    allocator given at create, else cudaMallocAsync on the call's stream);
+ *  - every call returns a status code; no exception, abort or exit crosses the
+ *    ABI.  GPMA_ETIMEOUT and GPMA_EDEVICE poison the handle: every later call
+ *    on it returns the same code.  A handle is not thread safe; distinct
+ *    handles are independent.
+ */
+#ifndef GPMA_H
+#define GPMA_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct gpma *gpma_t;
+
+#define GPMA_OK 0
+#define GPMA_EINVAL 1   /* bad argument or key; the batch was not applied */
+#define GPMA_ENOMEM 2   /* an allocation failed; the handle is unchanged */
+#define GPMA_ECAP 3     /* output buffer too small; *n_out holds the size needed */
+#define GPMA_ETIMEOUT 4 /* a bounded device-side wait gave up (handle poisoned) */
+#define GPMA_EDEVICE 5  /* a CUDA runtime error (handle poisoned) */
+
+#define GPMA_EMPTY 0xFFFFFFFFFFFFFFFFull
+#define GPMA_RAW_KEYS 1u   /* keys are opaque integers < 2^63: no guards, no analytics */
+#define GPMA_MAX_LEVELS 48
+
+/* Create-time parameters; a zero field takes the default.  Densities are whole
+ * percentages: tau_0 (leaf upper bound, default 92), tau_h (root upper bound, 80),
+ * rho_0 (8) and rho_h (40), the running example of Sec. 4.1 / Fig. 2.  The
+ * per-level bound is the largest count n with n < tau_i * L * 2^i, tau_i linear
+ * in the level between tau_0 and tau_h, clamped to twice the child bound. */
+typedef struct {
+  uint32_t leaf_size; /* L: power of two in [2, 1024]; default 64 */
+  uint32_t tau0_pct, tauh_pct, rho0_pct, rhoh_pct;
+  uint32_t flags;     /* GPMA_RAW_KEYS or 0 */
+} gpma_params;
+
+/* Optional device allocator.  alloc returns NULL on failure; both receive the
+ * cudaStream_t of the call as void*.  NULL allocator => cudaMallocAsync. */
+typedef struct {
+  void *(*alloc)(size_t bytes, void *stream, void *ctx);
+  void (*free)(void *ptr, void *stream, void *ctx);
+  void *ctx;
+} gpma_allocator;
+
+/* Per-batch statistics (filled only when a non-NULL pointer is passed, which
+ * makes the call wait for the batch). */
+typedef struct {
+  uint64_t n_inserted;     /* inserts that took effect */
+  uint64_t n_deleted;      /* deletes that took effect */
+  uint64_t n_ignored;      /* raw inputs with no effect: duplicates, cancelled pairs,
+                              inserts of stored keys, deletes of absent keys */
+  uint32_t levels_climbed; /* highest level at which a segment merged; old h + 1 on a resize */
+  uint32_t resized;        /* 1 if the capacity grew */
+  uint64_t alg_bytes;      /* algorithmic bytes of the batch (see the design notes) */
+  uint64_t touched_leaves; /* distinct leaves holding an update after cancellation */
+  uint64_t covered_leaves; /* leaves rewritten by merges (0 on a resize) */
+  uint64_t merges[GPMA_MAX_LEVELS]; /* segments merged at each level, Sec. 5.2 level order */
+} gpma_stats;
+
+/* Create an array for vertices [0, n_vertices) (n_vertices in [1, 2^31]; ignored
+ * with GPMA_RAW_KEYS) and load one guard per vertex through the update path
+ * (bulk load = update, Sec. 5.2).  params may be NULL.  On success *out owns the
+ * handle; the call waits for the stream. */
+int gpma_create(uint32_t n_vertices, const gpma_params *params, const gpma_allocator *alloc,
+                void *stream, gpma_t *out);
+
+/* Free the handle and all library memory (waits for the handle's last stream). */
+int gpma_destroy(gpma_t h);
+
+/* Apply one batch of edge insertions and deletions (Algorithm "GPMA+
+ * Segment-Oriented Insertion", Sec. 5.2, with lazy deletion, Sec. 6.1).
+ * d_ins[n_ins], d_del[n_del]: device arrays of keys (src << 32 | dst), in any
+ * order, duplicates allowed.  Semantics: each list is made unique; a key in both
+ * lists is dropped from both; inserts of stored keys and deletes of absent keys
+ * are ignored; deletes empty their slot in place; inserts go to their leaf (the
+ * last leaf whose smallest key is <= the key, before the batch) and every
+ * segment holding pending inserts merges and re-spreads evenly at the lowest
+ * level whose bound admits it; above the root the capacity doubles until all
+ * keys fit.  Every key must have src, dst < n_vertices (raw mode: key < 2^63),
+ * else GPMA_EINVAL and nothing changes.  n_ins + n_del < 2^30.
+ * With stats == NULL the call returns after enqueueing (except for a rare
+ * stream wait when the capacity might have to grow); a device-detected
+ * GPMA_EINVAL is then reported by the next gpma_status().  With stats != NULL
+ * the call waits and returns the batch's status. */
+int gpma_update_batch(gpma_t h, const uint64_t *d_ins, uint64_t n_ins, const uint64_t *d_del,
+                      uint64_t n_del, void *stream, gpma_stats *stats);
+
+/* Wait for `stream` and return (then clear) the first device-side error of the
+ * batches enqueued without stats. */
+int gpma_status(gpma_t h, void *stream);
+
+/* Breadth-first search from src over out-edges (Algorithm "BFS", Sec. 4.2, with
+ * the gap test of Algorithm "GPU-based BFS Neighbour Gathering").  d_depth[V]
+ * receives the hop count, -1 where unreachable.  Waits for the stream. */
+int gpma_bfs(gpma_t h, uint32_t src, int32_t *d_depth, void *stream);
+
+/* Weakly connected components (the Connected Component application of Sec. 6.1
+ * on the directed graph read as undirected).  d_label[V] receives, for every
+ * vertex, the smallest vertex id of its component.  Stream-ordered. */
+int gpma_cc(gpma_t h, uint32_t *d_label, void *stream);
+
+/* PageRank by power iteration (Sec. 6.1): x0 = 1/V and `iters` steps of
+ * x'_v = (1-d)/V + d * (sum_{u->v} x_u / outdeg(u) + (sum of x over vertices
+ * without out-edges) / V).  d_rank[V] receives FP32 ranks (sums accumulated in
+ * FP64).  Stream-ordered. */
+int gpma_pagerank(gpma_t h, uint32_t iters, float damping, float *d_rank, void *stream);
+
+/* Copy the stored edges (no guards) in ascending key order into d_out[cap];
+ * *n_out = number of edges.  GPMA_ECAP (nothing written past cap) if cap is too
+ * small.  Waits for the stream. */
+int gpma_export_sorted(gpma_t h, uint64_t *d_out, uint64_t cap, uint64_t *n_out, void *stream);
+
+/* CSR view (Sec. 4.2, Fig. 5): d_rowptr[V+1] row offsets, d_col[cap] column ids
+ * (dst).  *n_out = number of edges; GPMA_ECAP if cap is too small.  Waits. */
+int gpma_export_csr(gpma_t h, uint64_t *d_rowptr, uint32_t *d_col, uint64_t cap,
+                    uint64_t *n_out, void *stream);
+
+/* Copy the raw array (EMPTY slots and guards included) into d_slots[cap];
+ * *capacity_out = number of slots.  GPMA_ECAP if cap is too small. */
+int gpma_export_layout(gpma_t h, uint64_t *d_slots, uint64_t cap, uint64_t *capacity_out,
+                       void *stream);
+
+/* Replace the array with d_slots[capacity] (capacity = L * 2^k; valid keys
+ * strictly increasing; in graph mode one guard per vertex).  Used to restore a
+ * snapshot and by tests.  GPMA_EINVAL if the capacity is not L * 2^k or the
+ * layout fails the device checker (the handle is then unchanged). Waits. */
+int gpma_import_layout(gpma_t h, const uint64_t *d_slots, uint64_t capacity, void *stream);
+
+/* d_row_end[V] = slot index of the guard of each vertex.  Stream-ordered. */
+int gpma_row_end(gpma_t h, uint32_t *d_row_end, void *stream);
+
+/* Number of stored edges (guards excluded; raw mode: keys).  Waits. */
+int gpma_num_edges(gpma_t h, uint64_t *out, void *stream);
+
+/* Current number of slots (L * 2^h). */
+int gpma_capacity(gpma_t h, uint64_t *out);
+
+/* Device-side consistency check of the array and its indexes.  *code = 0 when
+ * all hold, else a bit set: 1 keys not strictly increasing, 2 a leaf count or
+ * first-key index is stale, 4 a leaf above its bound, 8 a guard index is stale,
+ * 16 a count-tree node is stale, 32 the total count is stale.  Waits. */
+int gpma_check(gpma_t h, uint32_t *code, void *stream);
+
+/* Static text for a status code. */
+const char *gpma_strerror(int status);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GPMA_H */

@@ -1,0 +1,309 @@
+"""GPMA+ dynamic graph store on one GB300 GPU -- thin Python binding of libgpma.
+
+Every function below has the name of the C entry point it calls (include/gpma.h)
+and only marshals arguments: device tensors (torch, CUDA) are passed by pointer,
+the current torch stream is passed as the cudaStream_t, and status codes become
+``GpmaError``.  All work runs in the library's kernels.  There is no fallback:
+if ``libgpma.so`` has not been built, ``lib()`` raises.
+
+Keys are 64-bit ``(src << 32) | dst``; torch tensors of dtype int64 or uint64
+are accepted (int64 is read as the same bits).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+from . import build as _build_mod
+
+GPMA_OK, GPMA_EINVAL, GPMA_ENOMEM, GPMA_ECAP, GPMA_ETIMEOUT, GPMA_EDEVICE = range(6)
+GPMA_RAW_KEYS = 1
+GPMA_MAX_LEVELS = 48
+EMPTY = 0xFFFFFFFFFFFFFFFF
+
+_lib = None
+
+
+class GpmaError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        self.code = code
+        msg = lib().gpma_strerror(code).decode() if _lib is not None else str(code)
+        super().__init__(f"{where}: {msg} (status {code})")
+
+
+class gpma_params(C.Structure):
+    _fields_ = [("leaf_size", C.c_uint32), ("tau0_pct", C.c_uint32), ("tauh_pct", C.c_uint32),
+                ("rho0_pct", C.c_uint32), ("rhoh_pct", C.c_uint32), ("flags", C.c_uint32)]
+
+
+class gpma_stats(C.Structure):
+    _fields_ = [
+        ("n_inserted", C.c_uint64), ("n_deleted", C.c_uint64), ("n_ignored", C.c_uint64),
+        ("levels_climbed", C.c_uint32), ("resized", C.c_uint32), ("alg_bytes", C.c_uint64),
+        ("touched_leaves", C.c_uint64), ("covered_leaves", C.c_uint64),
+        ("merges", C.c_uint64 * GPMA_MAX_LEVELS),
+    ]
+
+    def as_dict(self) -> dict:
+        d = {f: getattr(self, f) for f, _ in self._fields_ if f != "merges"}
+        d["merges"] = list(self.merges)
+        return d
+
+
+def build(force: bool = False, verbose: bool = False) -> str:
+    return _build_mod.build(force=force, verbose=verbose)
+
+
+def lib_path() -> str:
+    return _build_mod.LIB
+
+
+def lib():
+    """Load libgpma.so (built in-tree).  Raises when it is missing."""
+    global _lib
+    if _lib is None:
+        path = _build_mod.LIB
+        if not os.path.exists(path):
+            raise RuntimeError(f"libgpma.so is not built ({path}); run paper_1709_05061_gb300.build()")
+        l = C.CDLL(path)
+        vp, u32, u64, i = C.c_void_p, C.c_uint32, C.c_uint64, C.c_int
+        P = C.POINTER
+        sig = {
+            "gpma_create": ([u32, P(gpma_params), vp, vp, P(vp)], i),
+            "gpma_destroy": ([vp], i),
+            "gpma_update_batch": ([vp, vp, u64, vp, u64, vp, P(gpma_stats)], i),
+            "gpma_status": ([vp, vp], i),
+            "gpma_bfs": ([vp, u32, vp, vp], i),
+            "gpma_cc": ([vp, vp, vp], i),
+            "gpma_pagerank": ([vp, u32, C.c_float, vp, vp], i),
+            "gpma_export_sorted": ([vp, vp, u64, P(u64), vp], i),
+            "gpma_export_csr": ([vp, vp, vp, u64, P(u64), vp], i),
+            "gpma_export_layout": ([vp, vp, u64, P(u64), vp], i),
+            "gpma_import_layout": ([vp, vp, u64, vp], i),
+            "gpma_row_end": ([vp, vp, vp], i),
+            "gpma_num_edges": ([vp, P(u64), vp], i),
+            "gpma_capacity": ([vp, P(u64)], i),
+            "gpma_check": ([vp, P(u32), vp], i),
+            "gpma_strerror": ([i], C.c_char_p),
+        }
+        for name, (args, res) in sig.items():
+            f = getattr(l, name)
+            f.argtypes = args
+            f.restype = res
+        _lib = l
+    return _lib
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _stream(stream):
+    torch = _torch()
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return C.c_void_p(stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+
+
+def _ptr(t):
+    return C.c_void_p(t.data_ptr()) if t is not None and t.numel() > 0 else C.c_void_p(0)
+
+
+def _keys(t):
+    torch = _torch()
+    if t is None:
+        return torch.empty(0, dtype=torch.int64, device="cuda")
+    if not t.is_cuda or t.dtype not in (torch.int64, torch.uint64) or not t.is_contiguous():
+        raise ValueError("keys must be a contiguous CUDA int64/uint64 tensor")
+    return t
+
+
+def _check(rc: int, where: str):
+    if rc != GPMA_OK:
+        raise GpmaError(rc, where)
+
+
+# ---- the C entry points, one to one --------------------------------------------------------
+def gpma_create(n_vertices: int, leaf_size: int = 64, tau0: int = 92, tauh: int = 80, rho0: int = 8,
+                rhoh: int = 40, raw_keys: bool = False, stream=None) -> int:
+    p = gpma_params(leaf_size, tau0, tauh, rho0, rhoh, GPMA_RAW_KEYS if raw_keys else 0)
+    h = C.c_void_p()
+    _check(lib().gpma_create(n_vertices, C.byref(p), None, _stream(stream), C.byref(h)), "gpma_create")
+    return h.value
+
+
+def gpma_destroy(h: int):
+    _check(lib().gpma_destroy(C.c_void_p(h)), "gpma_destroy")
+
+
+def gpma_update_batch(h: int, ins, dels, stream=None, stats: bool = False):
+    ins, dels = _keys(ins), _keys(dels)
+    st = gpma_stats() if stats else None
+    rc = lib().gpma_update_batch(C.c_void_p(h), _ptr(ins), ins.numel(), _ptr(dels), dels.numel(),
+                                 _stream(stream), C.byref(st) if st is not None else None)
+    _check(rc, "gpma_update_batch")
+    return st.as_dict() if st is not None else None
+
+
+def gpma_status(h: int, stream=None):
+    _check(lib().gpma_status(C.c_void_p(h), _stream(stream)), "gpma_status")
+
+
+def gpma_bfs(h: int, src: int, out, stream=None):
+    _check(lib().gpma_bfs(C.c_void_p(h), src, _ptr(out), _stream(stream)), "gpma_bfs")
+    return out
+
+
+def gpma_cc(h: int, out, stream=None):
+    _check(lib().gpma_cc(C.c_void_p(h), _ptr(out), _stream(stream)), "gpma_cc")
+    return out
+
+
+def gpma_pagerank(h: int, iters: int, damping: float, out, stream=None):
+    _check(lib().gpma_pagerank(C.c_void_p(h), iters, damping, _ptr(out), _stream(stream)), "gpma_pagerank")
+    return out
+
+
+def gpma_export_sorted(h: int, out, stream=None) -> int:
+    n = C.c_uint64()
+    rc = lib().gpma_export_sorted(C.c_void_p(h), _ptr(out), out.numel() if out is not None else 0, C.byref(n),
+                                  _stream(stream))
+    if rc not in (GPMA_OK, GPMA_ECAP):
+        _check(rc, "gpma_export_sorted")
+    return n.value if rc == GPMA_OK else -n.value - 1
+
+
+def gpma_export_csr(h: int, rowptr, col, stream=None) -> int:
+    n = C.c_uint64()
+    rc = lib().gpma_export_csr(C.c_void_p(h), _ptr(rowptr), _ptr(col), col.numel() if col is not None else 0,
+                               C.byref(n), _stream(stream))
+    if rc not in (GPMA_OK, GPMA_ECAP):
+        _check(rc, "gpma_export_csr")
+    return n.value if rc == GPMA_OK else -n.value - 1
+
+
+def gpma_export_layout(h: int, out, stream=None) -> int:
+    n = C.c_uint64()
+    rc = lib().gpma_export_layout(C.c_void_p(h), _ptr(out), out.numel() if out is not None else 0, C.byref(n),
+                                  _stream(stream))
+    if rc not in (GPMA_OK, GPMA_ECAP):
+        _check(rc, "gpma_export_layout")
+    return n.value if rc == GPMA_OK else -n.value - 1
+
+
+def gpma_import_layout(h: int, slots, stream=None):
+    _check(lib().gpma_import_layout(C.c_void_p(h), _ptr(slots), slots.numel(), _stream(stream)),
+           "gpma_import_layout")
+
+
+def gpma_row_end(h: int, out, stream=None):
+    _check(lib().gpma_row_end(C.c_void_p(h), _ptr(out), _stream(stream)), "gpma_row_end")
+    return out
+
+
+def gpma_num_edges(h: int, stream=None) -> int:
+    n = C.c_uint64()
+    _check(lib().gpma_num_edges(C.c_void_p(h), C.byref(n), _stream(stream)), "gpma_num_edges")
+    return n.value
+
+
+def gpma_capacity(h: int) -> int:
+    n = C.c_uint64()
+    _check(lib().gpma_capacity(C.c_void_p(h), C.byref(n)), "gpma_capacity")
+    return n.value
+
+
+def gpma_check(h: int, stream=None) -> int:
+    c = C.c_uint32()
+    _check(lib().gpma_check(C.c_void_p(h), C.byref(c), _stream(stream)), "gpma_check")
+    return c.value
+
+
+def gpma_strerror(code: int) -> str:
+    return lib().gpma_strerror(code).decode()
+
+
+# ---- convenience object over the same calls -------------------------------------------------
+class Graph:
+    """A GPMA+ array on the current CUDA device (owns one libgpma handle)."""
+
+    def __init__(self, n_vertices: int, leaf_size: int = 64, raw_keys: bool = False, stream=None, **dens):
+        self.n_vertices = 0 if raw_keys else int(n_vertices)
+        self.raw = raw_keys
+        self.h = gpma_create(n_vertices, leaf_size=leaf_size, raw_keys=raw_keys, stream=stream, **dens)
+
+    def close(self):
+        if getattr(self, "h", None):
+            gpma_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def update(self, ins=None, dels=None, stats: bool = False, stream=None):
+        return gpma_update_batch(self.h, ins, dels, stream=stream, stats=stats)
+
+    def status(self, stream=None):
+        gpma_status(self.h, stream)
+
+    def bfs(self, src: int, stream=None):
+        torch = _torch()
+        out = torch.empty(self.n_vertices, dtype=torch.int32, device="cuda")
+        return gpma_bfs(self.h, src, out, stream)
+
+    def cc(self, stream=None):
+        torch = _torch()
+        out = torch.empty(self.n_vertices, dtype=torch.int32, device="cuda")
+        return gpma_cc(self.h, out, stream)
+
+    def pagerank(self, iters: int = 20, damping: float = 0.85, stream=None):
+        torch = _torch()
+        out = torch.empty(self.n_vertices, dtype=torch.float32, device="cuda")
+        return gpma_pagerank(self.h, iters, damping, out, stream)
+
+    def export_sorted(self, stream=None):
+        torch = _torch()
+        n = self.num_edges(stream)
+        out = torch.empty(max(n, 1), dtype=torch.int64, device="cuda")
+        got = gpma_export_sorted(self.h, out, stream)
+        if got < 0:
+            raise GpmaError(GPMA_ECAP, "export_sorted")
+        return out[:got]
+
+    def export_csr(self, stream=None):
+        torch = _torch()
+        n = self.num_edges(stream)
+        rowptr = torch.empty(self.n_vertices + 1, dtype=torch.int64, device="cuda")
+        col = torch.empty(max(n, 1), dtype=torch.int32, device="cuda")
+        got = gpma_export_csr(self.h, rowptr, col, stream)
+        if got < 0:
+            raise GpmaError(GPMA_ECAP, "export_csr")
+        return rowptr, col[:got]
+
+    def layout(self, stream=None):
+        torch = _torch()
+        out = torch.empty(self.capacity, dtype=torch.int64, device="cuda")
+        gpma_export_layout(self.h, out, stream)
+        return out
+
+    def import_layout(self, slots, stream=None):
+        gpma_import_layout(self.h, _keys(slots), stream)
+
+    def row_end(self, stream=None):
+        torch = _torch()
+        out = torch.empty(self.n_vertices, dtype=torch.int32, device="cuda")
+        return gpma_row_end(self.h, out, stream)
+
+    def num_edges(self, stream=None) -> int:
+        return gpma_num_edges(self.h, stream)
+
+    @property
+    def capacity(self) -> int:
+        return gpma_capacity(self.h)
+
+    def check(self, stream=None) -> int:
+        return gpma_check(self.h, stream)

@@ -1,0 +1,700 @@
+// gpma_api.cu -- the C ABI of include/gpma.h: handle, memory, and the order in
+// which one batch's kernels are enqueued.
+#include <cstdio>
+#include <cstring>
+#include <new>
+
+#include "gpma.h"
+#include "gpma_launch.h"
+
+using namespace gpk;
+
+namespace {
+
+// Threshold reading (Sec. 4.1 and the Fig. 2 table): tau_i and rho_i interpolate
+// linearly in the level between leaf and root in whole hundredths; max_i is the
+// largest count below tau_i * L * 2^i, clamped to twice the level below.
+void level_bounds(uint32_t L, uint32_t h, uint32_t t0, uint32_t th, uint64_t *mx) {
+  for (uint32_t i = 0; i <= h; i++) {
+    const uint64_t seg = (uint64_t)L << i;
+    uint64_t num, den;
+    if (h == 0) {
+      num = (uint64_t)t0 * seg;
+      den = 100;
+    } else {
+      num = ((uint64_t)th * h + (uint64_t)(t0 - th) * (h - i)) * seg;
+      den = 100ull * h;
+    }
+    uint64_t b = (num - 1) / den;
+    if (i > 0 && b > 2 * mx[i - 1]) b = 2 * mx[i - 1];
+    mx[i] = b;
+  }
+}
+
+uint32_t bits_for(uint64_t x) {
+  uint32_t b = 0;
+  while (x) {
+    ++b;
+    x >>= 1;
+  }
+  return b;
+}
+
+}  // namespace
+
+struct gpma {
+  uint32_t V, L, logL, raw;
+  uint32_t tau0, tauh, rho0, rhoh;
+  gpma_allocator alloc;
+  bool has_alloc;
+  Geo geo;
+  Ctl *ctl;
+  Ctl *h_ctl;
+  // per-batch work arrays
+  Work w;
+  uint64_t *bufA, *bufB;
+  uint32_t *hist;
+  uint64_t status_cap;
+  uint32_t cap;  // key capacity of the work arrays
+  // segment merge scratch
+  uint64_t *scratch;
+  uint64_t scratch_cap;
+  uint32_t *vbuf;
+  uint64_t vbuf_leaves;
+  uint64_t *partials;
+  uint64_t partials_cap;
+  // analytics
+  uint32_t *deg;
+  double *y;
+  float *contrib;
+  double *dsum;
+  uint32_t dsum_cap;
+  uint32_t *q0, *q1, *counter, *h_counter;
+  uint32_t *check_buf;
+  uint64_t *guards;
+  uint64_t count_ub;
+  int poisoned;
+  int host_sticky;
+};
+
+namespace {
+
+void *dmalloc(gpma *h, size_t bytes, cudaStream_t s) {
+  if (bytes == 0) bytes = 16;
+  void *p = nullptr;
+  if (h->has_alloc) {
+    p = h->alloc.alloc(bytes, (void *)s, h->alloc.ctx);
+  } else if (cudaMallocAsync(&p, bytes, s) != cudaSuccess) {
+    cudaGetLastError();
+    p = nullptr;
+  }
+  return p;
+}
+
+void dfree(gpma *h, void *p, cudaStream_t s) {
+  if (!p) return;
+  if (h->has_alloc) h->alloc.free(p, (void *)s, h->alloc.ctx);
+  else cudaFreeAsync(p, s);
+}
+
+template <typename T>
+bool dalloc(gpma *h, T **p, size_t count, cudaStream_t s) {
+  *p = (T *)dmalloc(h, sizeof(T) * count, s);
+  return *p != nullptr;
+}
+
+int poison(gpma *h, int code) {
+  if (!h->poisoned) h->poisoned = code;
+  return code;
+}
+
+int cuda_ok(gpma *h) {
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    fprintf(stderr, "libgpma: CUDA error %s\n", cudaGetErrorString(e));
+    return poison(h, GPMA_EDEVICE);
+  }
+  return GPMA_OK;
+}
+
+// geometry of an array of height hh (device pointers not set)
+void make_geo(gpma *h, uint32_t hh, Geo *g) {
+  memset(g, 0, sizeof(Geo));
+  g->L = h->L;
+  g->logL = h->logL;
+  g->h = hh;
+  g->V = h->V;
+  g->raw = h->raw;
+  g->nleaves = 1ull << hh;
+  g->C = (uint64_t)h->L << hh;
+  uint64_t off = 0;
+  for (uint32_t i = 1; i <= hh; i++) {
+    g->tree_off[i] = off;
+    off += g->nleaves >> i;
+  }
+  level_bounds(h->L, hh, h->tau0, h->tauh, g->maxc);
+}
+
+bool alloc_arrays(gpma *h, Geo *g, cudaStream_t s) {
+  const uint64_t tn = g->nleaves > 1 ? g->nleaves - 1 : 1;
+  g->slots = nullptr;
+  g->cnt = nullptr;
+  g->F = nullptr;
+  g->tree = nullptr;
+  g->mark = nullptr;
+  bool ok = dalloc(h, &g->slots, g->C, s) && dalloc(h, &g->cnt, g->nleaves, s) && dalloc(h, &g->F, g->nleaves, s) &&
+            dalloc(h, &g->tree, tn, s) && dalloc(h, &g->mark, tn, s);
+  if (ok) ok = cudaMemsetAsync(g->mark, 0, sizeof(uint32_t) * tn, s) == cudaSuccess;
+  return ok;
+}
+
+void free_arrays(gpma *h, Geo *g, cudaStream_t s) {
+  dfree(h, g->slots, s);
+  dfree(h, g->cnt, s);
+  dfree(h, g->F, s);
+  dfree(h, g->tree, s);
+  dfree(h, g->mark, s);
+  g->slots = nullptr;
+  g->cnt = nullptr;
+  g->F = nullptr;
+  g->tree = nullptr;
+  g->mark = nullptr;
+}
+
+void free_work(gpma *h, cudaStream_t s) {
+  Work &w = h->w;
+  void *ptrs[] = {h->bufA,   h->bufB,     w.ukey,  w.utag,     w.uleaf,   w.run_start, w.eflag,
+                  w.rleaf,   w.rdelta,    w.rinfo, w.rdel,     w.pkey,    w.pleaf,     w.erun,
+                  w.elvl,    w.etop,      w.seg_node, w.seg_top, w.seg_pstart, w.seg_lpre, w.status};
+  for (void *p : ptrs) dfree(h, p, s);
+  memset(&h->w, 0, sizeof(Work));
+  h->bufA = h->bufB = nullptr;
+  h->cap = 0;
+  h->status_cap = 0;
+}
+
+// work arrays for batches of up to n keys (grown geometrically)
+int ensure_work(gpma *h, uint64_t n, cudaStream_t s) {
+  if (n <= h->cap && h->w.status) return GPMA_OK;
+  uint64_t cap = h->cap ? h->cap : 4096;
+  while (cap < n) cap *= 2;
+  free_work(h, s);
+  Work &w = h->w;
+  const uint64_t c1 = cap + 1;
+  const uint64_t st = (uint64_t)sort_tiles(cap) * 256 + comp_tiles(cap) * 2 + 64;
+  bool ok = dalloc(h, &h->bufA, cap, s) && dalloc(h, &h->bufB, cap, s) && dalloc(h, &w.ukey, cap, s) &&
+            dalloc(h, &w.utag, cap, s) && dalloc(h, &w.uleaf, cap, s) && dalloc(h, &w.run_start, c1, s) &&
+            dalloc(h, &w.eflag, cap, s) && dalloc(h, &w.rleaf, cap, s) && dalloc(h, &w.rdelta, cap, s) &&
+            dalloc(h, &w.rinfo, cap, s) && dalloc(h, &w.rdel, cap, s) && dalloc(h, &w.pkey, cap, s) &&
+            dalloc(h, &w.pleaf, cap, s) && dalloc(h, &w.erun, c1, s) && dalloc(h, &w.elvl, cap, s) &&
+            dalloc(h, &w.etop, cap, s) && dalloc(h, &w.seg_node, c1, s) && dalloc(h, &w.seg_top, c1, s) &&
+            dalloc(h, &w.seg_pstart, c1, s) && dalloc(h, &w.seg_lpre, c1, s) && dalloc(h, &w.status, st, s);
+  if (!ok) {
+    free_work(h, s);
+    return GPMA_ENOMEM;
+  }
+  cudaMemsetAsync(w.status, 0, sizeof(uint64_t) * st, s);
+  h->cap = (uint32_t)cap;
+  h->status_cap = st;
+  w.cap = (uint32_t)cap;
+  return GPMA_OK;
+}
+
+// look-back status words for a scan over n elements (exports over the whole array)
+int ensure_status(gpma *h, uint64_t n, cudaStream_t s) {
+  const uint64_t need = (uint64_t)comp_tiles(n) * 2 + 64;
+  if (need <= h->status_cap) return GPMA_OK;
+  dfree(h, h->w.status, s);
+  if (!dalloc(h, &h->w.status, need, s)) {
+    h->status_cap = 0;
+    return GPMA_ENOMEM;
+  }
+  cudaMemsetAsync(h->w.status, 0, sizeof(uint64_t) * need, s);
+  h->status_cap = need;
+  return GPMA_OK;
+}
+
+// scratch of the segment merge: gathered keys (up to C) and per-leaf offsets
+int ensure_merge_scratch(gpma *h, cudaStream_t s) {
+  const Geo &g = h->geo;
+  if (h->scratch_cap < g.C) {
+    dfree(h, h->scratch, s);
+    if (!dalloc(h, &h->scratch, g.C, s)) {
+      h->scratch_cap = 0;
+      return GPMA_ENOMEM;
+    }
+    h->scratch_cap = g.C;
+  }
+  if (h->vbuf_leaves < g.nleaves) {
+    dfree(h, h->vbuf, s);
+    dfree(h, h->partials, s);
+    const uint64_t bytes = (g.nleaves + 1) * 4 + 16 + (g.nleaves + 1) * 8;
+    h->vbuf = (uint32_t *)dmalloc(h, bytes, s);
+    h->partials_cap = scan_partials(g.nleaves + 1) + 1;
+    h->partials = (uint64_t *)dmalloc(h, h->partials_cap * 8, s);
+    if (!h->vbuf || !h->partials) {
+      h->vbuf_leaves = 0;
+      return GPMA_ENOMEM;
+    }
+    h->vbuf_leaves = g.nleaves;
+  }
+  return GPMA_OK;
+}
+
+__global__ void k_finish(Ctl *ctl) { ctl->sticky |= ctl->err; }
+
+__global__ void k_make_guards(uint64_t *g, uint32_t V) {
+  for (uint32_t u = blockIdx.x * blockDim.x + threadIdx.x; u < V; u += gridDim.x * blockDim.x)
+    g[u] = ((uint64_t)u << 32) | 0xFFFFFFFFull;
+}
+
+int err_to_status(uint32_t err) {
+  if (err & kErrTimeout) return GPMA_ETIMEOUT;
+  if (err & kErrInternal) return GPMA_EDEVICE;
+  if (err & kErrKey) return GPMA_EINVAL;
+  return GPMA_OK;
+}
+
+int read_ctl(gpma *h, cudaStream_t s) {
+  cudaMemcpyAsync(h->h_ctl, h->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s);
+  if (cudaStreamSynchronize(s) != cudaSuccess) return poison(h, GPMA_EDEVICE);
+  return GPMA_OK;
+}
+
+// root resize (reading R7): every valid key and every pending insert spread over
+// the smallest taller array whose root bound holds them
+int do_resize(gpma *h, uint64_t total, cudaStream_t s) {
+  Geo &old = h->geo;
+  uint32_t h2 = old.h + 1;
+  uint64_t mx[kMaxLv];
+  for (;; h2++) {
+    if (h2 >= kMaxLv - 1 || ((uint64_t)h->L << h2) > (1ull << 32) || (1ull << h2) >= (1ull << 30))
+      return poison(h, GPMA_ENOMEM);
+    level_bounds(h->L, h2, h->tau0, h->tauh, mx);
+    if (total <= mx[h2]) break;
+  }
+  int rc = ensure_merge_scratch(h, s);
+  if (rc) return poison(h, rc);
+  Geo g2;
+  make_geo(h, h2, &g2);
+  g2.row_end = old.row_end;
+  if (!alloc_arrays(h, &g2, s)) {
+    free_arrays(h, &g2, s);
+    return poison(h, GPMA_ENOMEM);
+  }
+  launch_segment_merge(old, g2, h->ctl, h->w, h->scratch_cap, old.nleaves, h->scratch, h->vbuf, h->partials,
+                       true, s);
+  free_arrays(h, &old, s);
+  h->geo = g2;
+  return cuda_ok(h);
+}
+
+int update(gpma *h, const uint64_t *ins, uint64_t n_ins, const uint64_t *del, uint64_t n_del, cudaStream_t s,
+           gpma_stats *stats, bool allow_guards) {
+  if (h->poisoned) return h->poisoned;
+  if (stats) memset(stats, 0, sizeof(*stats));
+  const uint64_t n = n_ins + n_del;
+  if (n >= (1ull << 30) || (n_ins && !ins) || (n_del && !del)) return GPMA_EINVAL;
+  if (n == 0) return GPMA_OK;
+  int rc = ensure_work(h, n, s);
+  if (rc) return rc;
+  if ((rc = ensure_merge_scratch(h, s))) return rc;
+  const uint32_t h_old = h->geo.h;
+  const uint64_t C_old = h->geo.C;
+
+  PrepArgs pa;
+  memset(&pa, 0, sizeof(pa));
+  pa.n_ins = (uint32_t)n_ins;
+  pa.n_del = (uint32_t)n_del;
+  pa.V = h->V;
+  pa.raw = h->raw;
+  pa.allow_guards = allow_guards ? 1 : 0;
+  uint32_t bits;
+  if (h->raw) {
+    bits = 64;
+  } else {
+    uint32_t sb = bits_for(h->V - 1);
+    if (sb < 1) sb = 1;
+    pa.db = bits_for(h->V);
+    bits = sb + pa.db + 1;
+  }
+  pa.npass = (bits + 7) / 8;
+  pa.dbits = (bits + pa.npass - 1) / pa.npass;
+
+  FrontArgs f;
+  f.prep = pa;
+  f.ins = ins;
+  f.del = del;
+  f.bufA = h->bufA;
+  f.bufB = h->bufB;
+  f.hist = h->hist;
+  f.status = h->w.status;
+  f.ctl = h->ctl;
+  f.geo = &h->geo;
+  f.ukey = h->w.ukey;
+  f.utag = h->w.utag;
+  f.uleaf = h->w.uleaf;
+  f.run_start = h->w.run_start;
+  const uint32_t n32 = (uint32_t)n;
+  launch_front(f, s);
+  launch_leaf_pass(h->geo, h->ctl, h->w, n32, s);
+  launch_propagate(h->geo, h->ctl, h->w, n32, s);
+  launch_pending(h->geo, h->ctl, h->w, n32, s);
+  // the root can only refuse inserts when the count might exceed its bound
+  const bool may_fail = h->count_ub + n_ins > h->geo.maxc[h->geo.h];
+  launch_esc_level(h->geo, h->ctl, h->w, n32, may_fail, s);
+  if ((rc = cuda_ok(h))) return rc;
+
+  bool resized = false;
+  if (may_fail) {
+    if ((rc = read_ctl(h, s))) return rc;
+    if (h->h_ctl->err) {
+      k_finish<<<1, 1, 0, s>>>(h->ctl);
+      int st = err_to_status(h->h_ctl->err);
+      if (st != GPMA_EINVAL) poison(h, st);
+      return st;
+    }
+    h->count_ub = h->h_ctl->total;
+    if (h->h_ctl->nfail) {
+      launch_unmark(h->geo, h->ctl, h->w, n32, s);
+      if ((rc = do_resize(h, h->h_ctl->total, s))) return rc;
+      resized = true;
+    }
+  } else {
+    h->count_ub += n_ins;
+  }
+  if (!resized) {
+    launch_esc_top(h->geo, h->ctl, h->w, n32, s);
+    launch_segments(h->geo, h->ctl, h->w, n32, s);
+    launch_segment_merge(h->geo, h->geo, h->ctl, h->w, h->scratch_cap, h->geo.nleaves, h->scratch, h->vbuf,
+                         h->partials, false, s);
+    if (stats) launch_stats(h->geo, h->ctl, h->w, n32, s);
+  }
+  k_finish<<<1, 1, 0, s>>>(h->ctl);
+  if ((rc = cuda_ok(h))) return rc;
+  if (!stats) return GPMA_OK;
+
+  if ((rc = read_ctl(h, s))) return rc;
+  const Ctl &c = *h->h_ctl;
+  int st = err_to_status(c.err);
+  if (st) {
+    if (st != GPMA_EINVAL) poison(h, st);
+    return st;
+  }
+  h->count_ub = c.total;
+  const uint64_t L = h->L;
+  stats->n_inserted = c.n_inserted;
+  stats->n_deleted = c.n_deleted;
+  stats->n_ignored = n - c.n_inserted - c.n_deleted;
+  stats->touched_leaves = c.nruns;
+  stats->resized = resized ? 1 : 0;
+  for (int i = 0; i < GPMA_MAX_LEVELS && i < kMaxLv; i++) stats->merges[i] = c.merges[i];
+  stats->merges[0] = c.n_merged0;
+  uint32_t climbed = c.levels_climbed;
+  if (resized) climbed = h_old + 1;
+  stats->levels_climbed = climbed;
+  if (resized) {
+    stats->covered_leaves = 0;
+    stats->alg_bytes = 8 * n + 8 * L * c.nruns + 8 * C_old + 8 * h->geo.C;
+  } else {
+    const uint64_t cov = (uint64_t)c.nleafw + c.st_l0_only;
+    stats->covered_leaves = cov;
+    stats->alg_bytes = 8 * n + 8 * L * c.nruns + 8 * L * cov + 8 * L * (cov - c.st_cov_touched) + 8 * c.st_empties;
+  }
+  return GPMA_OK;
+}
+
+int ensure_analytics(gpma *h, uint32_t iters, cudaStream_t s) {
+  if (!h->deg) {
+    if (!dalloc(h, &h->deg, h->V, s) || !dalloc(h, &h->y, h->V, s) || !dalloc(h, &h->contrib, h->V, s) ||
+        !dalloc(h, &h->q0, h->V, s) || !dalloc(h, &h->q1, h->V, s) || !dalloc(h, &h->counter, 4, s))
+      return GPMA_ENOMEM;
+  }
+  if (iters + 1 > h->dsum_cap) {
+    dfree(h, h->dsum, s);
+    h->dsum_cap = iters + 1 < 64 ? 64 : iters + 1;
+    if (!dalloc(h, &h->dsum, h->dsum_cap, s)) {
+      h->dsum_cap = 0;
+      return GPMA_ENOMEM;
+    }
+  }
+  return GPMA_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *gpma_strerror(int status) {
+  switch (status) {
+    case GPMA_OK: return "ok";
+    case GPMA_EINVAL: return "invalid argument or key (nothing applied)";
+    case GPMA_ENOMEM: return "out of device memory";
+    case GPMA_ECAP: return "output buffer too small";
+    case GPMA_ETIMEOUT: return "a bounded device-side wait gave up (handle poisoned)";
+    case GPMA_EDEVICE: return "CUDA runtime error (handle poisoned)";
+    default: return "unknown status";
+  }
+}
+
+int gpma_create(uint32_t n_vertices, const gpma_params *params, const gpma_allocator *alloc, void *stream,
+                gpma_t *out) {
+  if (!out) return GPMA_EINVAL;
+  *out = nullptr;
+  gpma_params p;
+  memset(&p, 0, sizeof(p));
+  if (params) p = *params;
+  if (!p.leaf_size) p.leaf_size = 64;
+  if (!p.tau0_pct) p.tau0_pct = 92;
+  if (!p.tauh_pct) p.tauh_pct = 80;
+  if (!p.rho0_pct) p.rho0_pct = 8;
+  if (!p.rhoh_pct) p.rhoh_pct = 40;
+  const uint32_t L = p.leaf_size;
+  if (L < 2 || L > 1024 || (L & (L - 1))) return GPMA_EINVAL;
+  if (!(p.tauh_pct <= p.tau0_pct && p.tau0_pct <= 100 && p.rho0_pct <= p.rhoh_pct && p.rhoh_pct < p.tauh_pct))
+    return GPMA_EINVAL;
+  const bool raw = (p.flags & GPMA_RAW_KEYS) != 0;
+  if (!raw && (n_vertices == 0 || n_vertices > (1u << 31))) return GPMA_EINVAL;
+  if (alloc && (!alloc->alloc || !alloc->free)) return GPMA_EINVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+
+  gpma *h = new (std::nothrow) gpma;
+  if (!h) return GPMA_ENOMEM;
+  memset(h, 0, sizeof(gpma));
+  h->V = raw ? 0 : n_vertices;
+  h->L = L;
+  h->logL = bits_for(L) - 1;
+  h->raw = raw ? 1 : 0;
+  h->tau0 = p.tau0_pct;
+  h->tauh = p.tauh_pct;
+  h->rho0 = p.rho0_pct;
+  h->rhoh = p.rhoh_pct;
+  if (alloc) {
+    h->alloc = *alloc;
+    h->has_alloc = true;
+  }
+  make_geo(h, 0, &h->geo);
+  bool ok = alloc_arrays(h, &h->geo, s) && dalloc(h, &h->ctl, 1, s) && dalloc(h, &h->hist, 8 * 256, s) &&
+            dalloc(h, &h->check_buf, 4, s);
+  if (ok && !raw) ok = dalloc(h, &h->geo.row_end, h->V, s);
+  if (ok) ok = cudaMallocHost(&h->h_ctl, sizeof(Ctl)) == cudaSuccess && cudaMallocHost(&h->h_counter, 16) == cudaSuccess;
+  if (!ok) {
+    cudaGetLastError();
+    gpma_destroy(h);
+    return GPMA_ENOMEM;
+  }
+  cudaMemsetAsync(h->geo.slots, 0xFF, sizeof(uint64_t) * h->geo.C, s);
+  cudaMemsetAsync(h->geo.F, 0xFF, sizeof(uint64_t) * h->geo.nleaves, s);
+  cudaMemsetAsync(h->geo.cnt, 0, sizeof(uint32_t) * h->geo.nleaves, s);
+  cudaMemsetAsync(h->ctl, 0, sizeof(Ctl), s);
+  int rc = GPMA_OK;
+  if (!raw) {
+    if (!dalloc(h, &h->guards, h->V, s)) rc = GPMA_ENOMEM;
+    if (!rc) {
+      k_make_guards<<<(h->V + 255) / 256 < 4096 ? (h->V + 255) / 256 : 4096, 256, 0, s>>>(h->guards, h->V);
+      gpma_stats st;
+      rc = update(h, h->guards, h->V, nullptr, 0, s, &st, true);
+      dfree(h, h->guards, s);
+      h->guards = nullptr;
+    }
+  }
+  if (!rc && cudaStreamSynchronize(s) != cudaSuccess) rc = GPMA_EDEVICE;
+  if (rc) {
+    gpma_destroy(h);
+    return rc;
+  }
+  *out = h;
+  return GPMA_OK;
+}
+
+int gpma_destroy(gpma_t h) {
+  if (!h) return GPMA_EINVAL;
+  cudaStream_t s = 0;
+  cudaDeviceSynchronize();
+  free_arrays(h, &h->geo, s);
+  dfree(h, h->geo.row_end, s);
+  free_work(h, s);
+  void *ptrs[] = {h->ctl, h->hist, h->scratch, h->vbuf, h->partials, h->deg, h->y, h->contrib,
+                  h->dsum, h->q0,  h->q1,      h->counter, h->check_buf, h->guards};
+  for (void *p : ptrs) dfree(h, p, s);
+  cudaStreamSynchronize(s);
+  if (h->h_ctl) cudaFreeHost(h->h_ctl);
+  if (h->h_counter) cudaFreeHost(h->h_counter);
+  cudaGetLastError();
+  delete h;
+  return GPMA_OK;
+}
+
+int gpma_update_batch(gpma_t h, const uint64_t *d_ins, uint64_t n_ins, const uint64_t *d_del, uint64_t n_del,
+                      void *stream, gpma_stats *stats) {
+  if (!h) return GPMA_EINVAL;
+  return update(h, d_ins, n_ins, d_del, n_del, (cudaStream_t)stream, stats, false);
+}
+
+int gpma_status(gpma_t h, void *stream) {
+  if (!h) return GPMA_EINVAL;
+  if (h->poisoned) return h->poisoned;
+  cudaStream_t s = (cudaStream_t)stream;
+  int rc = read_ctl(h, s);
+  if (rc) return rc;
+  uint32_t sticky = h->h_ctl->sticky;
+  cudaMemsetAsync(&h->ctl->sticky, 0, sizeof(uint32_t), s);
+  if (cudaStreamSynchronize(s) != cudaSuccess) return poison(h, GPMA_EDEVICE);
+  int st = err_to_status(sticky);
+  if (st != GPMA_OK && st != GPMA_EINVAL) poison(h, st);
+  return st;
+}
+
+int gpma_bfs(gpma_t h, uint32_t src, int32_t *d_depth, void *stream) {
+  if (!h || !d_depth || h->raw || src >= h->V) return GPMA_EINVAL;
+  if (h->poisoned) return h->poisoned;
+  cudaStream_t s = (cudaStream_t)stream;
+  if (ensure_analytics(h, 1, s)) return GPMA_ENOMEM;
+  if (run_bfs(h->geo, src, d_depth, h->q0, h->q1, h->counter, h->h_counter, s) < 0) return poison(h, GPMA_EDEVICE);
+  return cuda_ok(h);
+}
+
+int gpma_cc(gpma_t h, uint32_t *d_label, void *stream) {
+  if (!h || !d_label || h->raw) return GPMA_EINVAL;
+  if (h->poisoned) return h->poisoned;
+  launch_cc(h->geo, d_label, (cudaStream_t)stream);
+  return cuda_ok(h);
+}
+
+int gpma_pagerank(gpma_t h, uint32_t iters, float damping, float *d_rank, void *stream) {
+  if (!h || !d_rank || h->raw || !(damping >= 0.0f && damping <= 1.0f)) return GPMA_EINVAL;
+  if (h->poisoned) return h->poisoned;
+  cudaStream_t s = (cudaStream_t)stream;
+  if (ensure_analytics(h, iters, s)) return GPMA_ENOMEM;
+  launch_pagerank(h->geo, iters, damping, d_rank, h->deg, h->y, h->contrib, h->dsum, s);
+  return cuda_ok(h);
+}
+
+int gpma_export_sorted(gpma_t h, uint64_t *d_out, uint64_t cap, uint64_t *n_out, void *stream) {
+  if (!h || !n_out || (cap && !d_out)) return GPMA_EINVAL;
+  if (h->poisoned) return h->poisoned;
+  cudaStream_t s = (cudaStream_t)stream;
+  if (ensure_status(h, h->geo.C, s)) return GPMA_ENOMEM;
+  launch_export(h->geo, h->ctl, d_out, nullptr, cap, h->w.status, s);
+  int rc = read_ctl(h, s);
+  if (rc) return rc;
+  *n_out = h->h_ctl->gen_count;
+  return *n_out > cap ? GPMA_ECAP : cuda_ok(h);
+}
+
+int gpma_export_csr(gpma_t h, uint64_t *d_rowptr, uint32_t *d_col, uint64_t cap, uint64_t *n_out, void *stream) {
+  if (!h || !n_out || !d_rowptr || (cap && !d_col) || h->raw) return GPMA_EINVAL;
+  if (h->poisoned) return h->poisoned;
+  cudaStream_t s = (cudaStream_t)stream;
+  if (ensure_analytics(h, 1, s) || ensure_status(h, h->geo.C, s)) return GPMA_ENOMEM;
+  uint64_t *partials = (uint64_t *)dmalloc(h, scan_partials(h->V + 1) * 8 + 8, s);
+  if (!partials) return GPMA_ENOMEM;
+  launch_degrees(h->geo, h->deg, s);
+  launch_rowptr(h->deg, d_rowptr, h->V, partials, s);
+  launch_export(h->geo, h->ctl, nullptr, d_col, cap, h->w.status, s);
+  dfree(h, partials, s);
+  int rc = read_ctl(h, s);
+  if (rc) return rc;
+  *n_out = h->h_ctl->gen_count;
+  return *n_out > cap ? GPMA_ECAP : cuda_ok(h);
+}
+
+int gpma_export_layout(gpma_t h, uint64_t *d_slots, uint64_t cap, uint64_t *capacity_out, void *stream) {
+  if (!h || !capacity_out) return GPMA_EINVAL;
+  if (h->poisoned) return h->poisoned;
+  *capacity_out = h->geo.C;
+  if (cap < h->geo.C) return GPMA_ECAP;
+  if (!d_slots) return GPMA_EINVAL;
+  cudaMemcpyAsync(d_slots, h->geo.slots, sizeof(uint64_t) * h->geo.C, cudaMemcpyDeviceToDevice,
+                  (cudaStream_t)stream);
+  return cuda_ok(h);
+}
+
+int gpma_import_layout(gpma_t h, const uint64_t *d_slots, uint64_t capacity, void *stream) {
+  if (!h || !d_slots) return GPMA_EINVAL;
+  if (h->poisoned) return h->poisoned;
+  uint32_t hh = 0;
+  while (((uint64_t)h->L << hh) < capacity && hh < kMaxLv - 2) hh++;
+  if (((uint64_t)h->L << hh) != capacity || capacity > (1ull << 32)) return GPMA_EINVAL;
+  cudaStream_t s = (cudaStream_t)stream;
+  Geo g2;
+  make_geo(h, hh, &g2);
+  g2.row_end = h->geo.row_end;
+  if (!alloc_arrays(h, &g2, s)) {
+    free_arrays(h, &g2, s);
+    return GPMA_ENOMEM;
+  }
+  // keep the old guard index in case the import is rejected
+  uint32_t *old_re = nullptr;
+  if (!h->raw) {
+    if (!dalloc(h, &old_re, h->V, s)) {
+      free_arrays(h, &g2, s);
+      return GPMA_ENOMEM;
+    }
+    cudaMemcpyAsync(old_re, h->geo.row_end, sizeof(uint32_t) * h->V, cudaMemcpyDeviceToDevice, s);
+    cudaMemsetAsync(h->geo.row_end, 0xFF, sizeof(uint32_t) * h->V, s);
+  }
+  const uint64_t old_total_ub = h->count_ub;
+  Ctl saved;
+  if (read_ctl(h, s)) return h->poisoned;
+  saved = *h->h_ctl;
+  cudaMemcpyAsync(g2.slots, d_slots, sizeof(uint64_t) * capacity, cudaMemcpyDeviceToDevice, s);
+  launch_rebuild_indexes(g2, h->ctl, s);
+  launch_check(g2, h->ctl, h->check_buf, s);
+  uint32_t code[4] = {0, 0, 0, 0};
+  cudaMemcpyAsync(code, h->check_buf, 16, cudaMemcpyDeviceToHost, s);
+  if (read_ctl(h, s)) return h->poisoned;
+  if (code[0]) {
+    free_arrays(h, &g2, s);
+    if (old_re) {
+      cudaMemcpyAsync(h->geo.row_end, old_re, sizeof(uint32_t) * h->V, cudaMemcpyDeviceToDevice, s);
+      dfree(h, old_re, s);
+    }
+    cudaMemcpyAsync(&h->ctl->total, &saved.total, sizeof(uint64_t), cudaMemcpyHostToDevice, s);
+    cudaStreamSynchronize(s);
+    h->count_ub = old_total_ub;
+    return GPMA_EINVAL;
+  }
+  if (old_re) dfree(h, old_re, s);
+  free_arrays(h, &h->geo, s);
+  h->geo = g2;
+  h->count_ub = h->h_ctl->total;
+  return cuda_ok(h);
+}
+
+int gpma_row_end(gpma_t h, uint32_t *d_row_end, void *stream) {
+  if (!h || !d_row_end || h->raw) return GPMA_EINVAL;
+  if (h->poisoned) return h->poisoned;
+  cudaMemcpyAsync(d_row_end, h->geo.row_end, sizeof(uint32_t) * h->V, cudaMemcpyDeviceToDevice,
+                  (cudaStream_t)stream);
+  return cuda_ok(h);
+}
+
+int gpma_num_edges(gpma_t h, uint64_t *out, void *stream) {
+  if (!h || !out) return GPMA_EINVAL;
+  if (h->poisoned) return h->poisoned;
+  int rc = read_ctl(h, (cudaStream_t)stream);
+  if (rc) return rc;
+  *out = h->h_ctl->total - (h->raw ? 0 : h->V);
+  return GPMA_OK;
+}
+
+int gpma_capacity(gpma_t h, uint64_t *out) {
+  if (!h || !out) return GPMA_EINVAL;
+  *out = h->geo.C;
+  return GPMA_OK;
+}
+
+int gpma_check(gpma_t h, uint32_t *code, void *stream) {
+  if (!h || !code) return GPMA_EINVAL;
+  if (h->poisoned) return h->poisoned;
+  cudaStream_t s = (cudaStream_t)stream;
+  launch_check(h->geo, h->ctl, h->check_buf, s);
+  uint32_t buf[4];
+  cudaMemcpyAsync(buf, h->check_buf, 16, cudaMemcpyDeviceToHost, s);
+  if (cudaStreamSynchronize(s) != cudaSuccess) return poison(h, GPMA_EDEVICE);
+  *code = buf[0];
+  return cuda_ok(h);
+}
+
+}  // extern "C"

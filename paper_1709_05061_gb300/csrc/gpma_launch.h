@@ -1,0 +1,101 @@
+// gpma_launch.h -- host-side launch interface between the libgpma translation units.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "gpma_dev.cuh"
+
+namespace gpk {
+
+// ticket / look-back epoch slots of one batch (Ctl::ticket, Ctl::epoch + slot)
+constexpr uint32_t kSlotKeep = 8, kSlotRuns = 9, kSlotPend = 10, kSlotERuns = 11, kSlotSegs = 12,
+                   kSlotMisc = 13, kSlotsPerBatch = 16;
+
+struct PrepArgs {
+  uint32_t n_ins, n_del;
+  uint32_t V, db, raw, allow_guards;
+  uint32_t npass, dbits;
+};
+
+struct FrontArgs {
+  PrepArgs prep;
+  const uint64_t *ins, *del;
+  uint64_t *bufA, *bufB;  // sort ping-pong
+  uint32_t *hist;         // npass * 256
+  uint64_t *status;       // look-back status words
+  Ctl *ctl;
+  const Geo *geo;
+  uint64_t *ukey;
+  uint8_t *utag;
+  uint32_t *uleaf;
+  uint32_t *run_start;
+};
+
+// per-batch work arrays of the update kernels
+struct Work {
+  uint64_t *ukey;
+  uint8_t *utag;
+  uint32_t *uleaf;
+  uint32_t *run_start;
+  uint8_t *eflag;     // per key: 0 no effect, 1 applied, 2 pending insert
+  uint32_t *rleaf;    // per run
+  int32_t *rdelta;
+  uint8_t *rinfo;     // 1 merged at level 0, 2 escalated
+  uint32_t *rdel;
+  uint64_t *pkey;     // pending inserts (sorted) and their leaves
+  uint32_t *pleaf;
+  uint32_t *erun;     // heads of pending runs (+ end)
+  uint8_t *elvl;      // merge level of each pending run
+  uint8_t *etop;      // top merged ancestor of each pending run
+  uint32_t *seg_node; // maximal merged segments: node, level, first pending, leaf prefix
+  uint8_t *seg_top;
+  uint32_t *seg_pstart;
+  uint32_t *seg_lpre;
+  uint64_t *status;
+  uint32_t cap;       // capacity of the per-key arrays
+};
+
+uint32_t sort_tiles(uint64_t n);
+uint32_t comp_tiles(uint64_t n);
+void launch_front(const FrontArgs &f, cudaStream_t s);
+
+// k_update.cu
+void launch_leaf_pass(const Geo &g, Ctl *ctl, const Work &w, uint32_t n, cudaStream_t s);
+void launch_propagate(const Geo &g, Ctl *ctl, const Work &w, uint32_t n, cudaStream_t s);
+void launch_pending(const Geo &g, Ctl *ctl, const Work &w, uint32_t n, cudaStream_t s);
+// merge level of every pending run; with may_fail a run no level admits is counted in
+// Ctl::nfail instead of being an error
+void launch_esc_level(const Geo &g, Ctl *ctl, const Work &w, uint32_t n, bool may_fail, cudaStream_t s);
+void launch_esc_top(const Geo &g, Ctl *ctl, const Work &w, uint32_t n, cudaStream_t s);
+void launch_unmark(const Geo &g, Ctl *ctl, const Work &w, uint32_t n, cudaStream_t s);
+void launch_segments(const Geo &g, Ctl *ctl, const Work &w, uint32_t n, cudaStream_t s);
+void launch_stats(const Geo &g, Ctl *ctl, const Work &w, uint32_t n, cudaStream_t s);
+// merge of maximal segments (escalation) or of the whole array into a new one (resize):
+// gathers valid keys of `src` over the segments' leaves into `scratch` (leaf offsets in
+// `voff`, nleafw + 1 entries), then writes `dst`.
+void launch_segment_merge(const Geo &src, const Geo &dst, Ctl *ctl, const Work &w, uint64_t scratch_cap,
+                          uint64_t nleafw_bound, uint64_t *scratch, uint32_t *voff, uint64_t *partials,
+                          bool whole, cudaStream_t s);
+
+// k_misc.cu
+void launch_rebuild_indexes(const Geo &g, Ctl *ctl, cudaStream_t s);  // cnt, F, tree, row_end, total
+void launch_check(const Geo &g, Ctl *ctl, uint32_t *code, cudaStream_t s);
+// valid non-guard keys (or their dst ids) in slot order; count in ctl->gen_count
+void launch_export(const Geo &g, Ctl *ctl, uint64_t *out_keys, uint32_t *out_cols, uint64_t cap, uint64_t *status,
+                   cudaStream_t s);
+void launch_degrees(const Geo &g, uint32_t *deg, cudaStream_t s);
+void launch_rowptr(const uint32_t *deg, uint64_t *rowptr, uint32_t V, uint64_t *partials, cudaStream_t s);
+// exclusive scan of u32 values into u64 (out[n] = total); partials >= scan_partials(n)
+uint64_t scan_partials(uint64_t n);
+// n_dev (optional): device-side element count, at most n_bound
+void launch_scan_u32_u64(const uint32_t *in, uint64_t *out, uint64_t n_bound, uint64_t *partials, cudaStream_t s,
+                         const uint32_t *n_dev = nullptr);
+
+// k_analytics.cu
+void launch_pagerank(const Geo &g, uint32_t iters, float damping, float *rank, uint32_t *deg, double *y,
+                     float *contrib, double *dsum, cudaStream_t s);
+int run_bfs(const Geo &g, uint32_t src, int32_t *depth, uint32_t *q0, uint32_t *q1, uint32_t *counter,
+            uint32_t *h_counter, cudaStream_t s);
+void launch_cc(const Geo &g, uint32_t *label, cudaStream_t s);
+
+}  // namespace gpk

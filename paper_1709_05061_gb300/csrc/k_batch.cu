@@ -1,0 +1,250 @@
+// k_batch.cu -- front end of one update batch (Algorithm "GPMA+ Segment-Oriented
+// Insertion", Sec. 5.2, lines Sort(U) and BinarySearchLeafSegments(U)):
+//   k_init_batch  reset the per-call control block and radix histograms
+//   k_prep        validate keys, compress (src, dst, insert/delete tag) into one
+//                 sortable word, build the radix histograms of every pass
+//   k_sort_pass   one stable LSD radix pass (single pass per digit with look-back)
+//   k_keep        unique + insert/delete cancellation on the sorted words, then the
+//                 leaf search of every surviving key (single-pass compaction)
+//   k_runs        heads of the runs of equal leaf (single-pass compaction)
+#include "gpma_dev.cuh"
+#include "gpma_launch.h"
+#include "scan_dev.cuh"
+
+namespace gpk {
+
+constexpr int kSortThreads = 256;
+constexpr int kSortItems = 16;  // keys per thread per pass
+constexpr int kSortTile = kSortThreads * kSortItems;
+
+// ---- key compression -----------------------------------------------------------------
+// Graph mode: word = ((src << db) | d) << 1 | tag with d = dst, or d = V for a guard
+// (so a guard sorts after every edge of its row); db = bits(V), sb = bits(V-1).
+// Raw mode: word = key << 1 | tag.  Order of words = order of (key, tag).
+__device__ __forceinline__ uint64_t compress(uint64_t key, uint32_t tag, const PrepArgs &a) {
+  if (a.raw) return (key << 1) | tag;
+  uint64_t src = key >> 32, dst = key & 0xFFFFFFFFull;
+  uint64_t d = (dst == 0xFFFFFFFFull) ? (uint64_t)a.V : dst;
+  return (((src << a.db) | d) << 1) | tag;
+}
+
+__device__ __forceinline__ uint64_t expand(uint64_t w, const PrepArgs &a) {
+  if (a.raw) return w >> 1;
+  uint64_t d = (w >> 1) & ((1ull << a.db) - 1ull);
+  uint64_t src = w >> (a.db + 1);
+  uint64_t dst = (d == (uint64_t)a.V) ? 0xFFFFFFFFull : d;
+  return (src << 32) | dst;
+}
+
+__global__ void k_init_batch(Ctl *ctl, uint32_t *hist, uint32_t nhist, uint32_t n) {
+  for (uint32_t i = threadIdx.x; i < nhist; i += blockDim.x) hist[i] = 0;
+  if (threadIdx.x == 0) {
+    ctl->err = 0;
+    ctl->n = n;
+    ctl->epoch += kSlotsPerBatch;
+    ctl->nesc = 0;
+    ctl->nfail = 0;
+    ctl->m = ctl->nruns = ctl->npend = ctl->neruns = ctl->nsegs = ctl->nleafw = 0;
+    for (int i = 0; i < 16; i++) ctl->ticket[i] = 0;
+    ctl->n_inserted = ctl->n_deleted = 0;
+    ctl->st_cov_touched = ctl->st_l0_only = ctl->st_empties = 0;
+    ctl->levels_climbed = 0;
+    ctl->n_merged0 = 0;
+    for (int i = 0; i < kMaxLv; i++) ctl->merges[i] = 0;
+  }
+}
+
+__global__ void __launch_bounds__(256) k_prep(PrepArgs a, const uint64_t *__restrict__ ins,
+                                              const uint64_t *__restrict__ del, uint64_t *__restrict__ out,
+                                              uint32_t *__restrict__ hist, Ctl *ctl) {
+  __shared__ uint32_t sh[8 * 256];
+  for (uint32_t i = threadIdx.x; i < a.npass * 256u; i += blockDim.x) sh[i] = 0;
+  __syncthreads();
+  const uint32_t n = a.n_ins + a.n_del;
+  const uint32_t mask = (1u << a.dbits) - 1u;
+  bool bad = false;
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    uint32_t tag = i >= a.n_ins;
+    uint64_t key = tag ? del[i - a.n_ins] : ins[i];
+    bool ok;
+    if (a.raw) {
+      ok = (key >> 63) == 0;
+    } else {
+      uint64_t src = key >> 32, dst = key & 0xFFFFFFFFull;
+      ok = src < a.V && (dst < a.V || (a.allow_guards && !tag && dst == 0xFFFFFFFFull));
+    }
+    bad |= !ok;
+    uint64_t w = ok ? compress(key, tag, a) : 0ull;
+    out[i] = w;
+    for (uint32_t p = 0; p < a.npass; p++)
+      atomicAdd(&sh[p * 256 + (uint32_t)((w >> (p * a.dbits)) & mask)], 1u);
+  }
+  if (__any_sync(0xFFFFFFFFu, bad) && lane_id() == 0) atomicOr(&ctl->err, kErrKey);
+  __syncthreads();
+  for (uint32_t i = threadIdx.x; i < a.npass * 256u; i += blockDim.x)
+    if (sh[i]) atomicAdd(&hist[i], sh[i]);
+}
+
+// One stable LSD pass.  A tile is 16 rounds x 256 keys; warp w owns the
+// contiguous sub-tile [w*512, w*512+512) so ranks inside a warp need no block
+// barrier; tiles are ordered by ticket and chained by a per-digit look-back.
+__global__ void __launch_bounds__(kSortThreads) k_sort_pass(const uint64_t *__restrict__ src,
+                                                            uint64_t *__restrict__ dst, const uint32_t *hist,
+                                                            uint64_t *status, Ctl *ctl, uint32_t pass,
+                                                            uint32_t shift, uint32_t dbits) {
+  __shared__ uint32_t wcnt[kSortThreads / 32][256];
+  __shared__ uint32_t gbase[256];
+  __shared__ uint32_t s_tile;
+  const uint32_t n = ctl->n;
+  const uint32_t w = threadIdx.x >> 5, lane = lane_id();
+  const uint32_t radix = 1u << dbits, mask = radix - 1u;
+  for (uint32_t d = threadIdx.x; d < 256; d += kSortThreads)
+    for (int q = 0; q < kSortThreads / 32; q++) wcnt[q][d] = 0;
+  if (threadIdx.x == 0) s_tile = atomicAdd(&ctl->ticket[pass], 1u);
+  __syncthreads();
+  const uint32_t tile = s_tile;
+  const uint64_t base = (uint64_t)tile * kSortTile + w * (kSortItems * 32);
+  uint64_t key[kSortItems];
+  uint32_t rank[kSortItems];
+  uint32_t dig[kSortItems];
+#pragma unroll
+  for (int r = 0; r < kSortItems; r++) {
+    uint64_t idx = base + r * 32 + lane;
+    bool valid = idx < n;
+    key[r] = valid ? src[idx] : 0ull;
+    dig[r] = valid ? (uint32_t)((key[r] >> shift) & mask) : 0xFFFFu;
+  }
+#pragma unroll
+  for (int r = 0; r < kSortItems; r++) {
+    uint32_t peers = __match_any_sync(0xFFFFFFFFu, dig[r]);
+    uint32_t before = 0;
+    if (dig[r] != 0xFFFFu) before = wcnt[w][dig[r]];
+    rank[r] = before + __popc(peers & lanemask_lt());
+    __syncwarp();
+    if (dig[r] != 0xFFFFu && lane == (uint32_t)(__ffs(peers) - 1)) wcnt[w][dig[r]] = before + __popc(peers);
+    __syncwarp();
+  }
+  __syncthreads();
+  // per digit: exclusive prefix over warps, tile total, look-back, global base
+  for (uint32_t d = threadIdx.x; d < radix; d += kSortThreads) {
+    uint32_t run = 0;
+    for (int q = 0; q < kSortThreads / 32; q++) {
+      uint32_t c = wcnt[q][d];
+      wcnt[q][d] = run;
+      run += c;
+    }
+    uint32_t excl = lookback(status, 256, d, tile, run, ctl->epoch + pass, &ctl->err);
+    gbase[d] = excl;
+  }
+  // exclusive scan of the global histogram of this pass
+  __shared__ uint32_t hs[256];
+  for (uint32_t d = threadIdx.x; d < 256; d += kSortThreads) hs[d] = d < radix ? hist[pass * 256 + d] : 0u;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    uint32_t carry = 0;
+    for (int c = 0; c < 256; c += 32) {
+      uint32_t v = hs[c + lane];
+      uint32_t inc = warp_incl_scan(v);
+      hs[c + lane] = carry + inc - v;
+      carry += __shfl_sync(0xFFFFFFFFu, inc, 31);
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int r = 0; r < kSortItems; r++) {
+    if (dig[r] == 0xFFFFu) continue;
+    uint32_t d = dig[r];
+    uint32_t pos = hs[d] + gbase[d] + wcnt[w][d] + rank[r];
+    if (pos < n) dst[pos] = key[r];  // always true unless a look-back gave up
+  }
+}
+
+// unique + cancellation (reading R2), then the leaf of every survivor (reading R4)
+__global__ void __launch_bounds__(kScanThreads) k_keep(PrepArgs a, const uint64_t *__restrict__ sorted,
+                                                        const uint64_t *__restrict__ F, uint64_t nleaves,
+                                                        uint64_t *__restrict__ ukey, uint8_t *__restrict__ utag,
+                                                        uint32_t *__restrict__ uleaf, uint64_t *status, Ctl *ctl) {
+  __shared__ ScanSmem sm;
+  const uint32_t tile = take_ticket(ctl, kSlotKeep, sm), n = ctl->n;
+  uint32_t flag[kScanItems];
+  uint64_t w[kScanItems];
+#pragma unroll
+  for (int r = 0; r < kScanItems; r++) {
+    uint64_t e = scan_elem(tile, r);
+    flag[r] = 0;
+    w[r] = 0;
+    if (e < n) {
+      w[r] = sorted[e];
+      uint64_t k = w[r] >> 1;
+      if (w[r] & 1ull)  // delete: kept iff no word with the same key precedes it
+        flag[r] = e == 0 || (sorted[e - 1] >> 1) != k;
+      else              // insert: kept iff no word with the same key follows it
+        flag[r] = e + 1 == n || (sorted[e + 1] >> 1) != k;
+    }
+  }
+  uint32_t off[kScanItems];
+  uint32_t total = tile_scan(flag, off, tile, status, 1, 0, ctl->epoch + kSlotKeep, &ctl->err, sm);
+#pragma unroll
+  for (int r = 0; r < kScanItems; r++) {
+    if (!flag[r] || off[r] >= n) continue;
+    uint64_t key = expand(w[r], a);
+    ukey[off[r]] = key;
+    utag[off[r]] = (uint8_t)(w[r] & 1ull);
+    uleaf[off[r]] = leaf_search(F, nleaves, key);
+  }
+  if ((uint64_t)(tile + 1) * kScanTile >= n && threadIdx.x == 0) ctl->m = total;
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_runs(const uint32_t *__restrict__ uleaf,
+                                                        uint32_t *__restrict__ run_start, uint64_t *status,
+                                                        Ctl *ctl) {
+  __shared__ ScanSmem sm;
+  const uint32_t tile = take_ticket(ctl, kSlotRuns, sm), m = ctl->m;
+  if ((uint64_t)tile * kScanTile >= m && tile > 0) return;  // past the end (tile 0 always runs)
+  uint32_t flag[kScanItems];
+#pragma unroll
+  for (int r = 0; r < kScanItems; r++) {
+    uint64_t e = scan_elem(tile, r);
+    flag[r] = e < m && (e == 0 || uleaf[e] != uleaf[e - 1]);
+  }
+  uint32_t off[kScanItems];
+  uint32_t total = tile_scan(flag, off, tile, status, 1, 0, ctl->epoch + kSlotRuns, &ctl->err, sm);
+#pragma unroll
+  for (int r = 0; r < kScanItems; r++)
+    if (flag[r] && off[r] < m) run_start[off[r]] = (uint32_t)scan_elem(tile, r);
+  if ((uint64_t)(tile + 1) * kScanTile >= m && threadIdx.x == 0) {
+    ctl->nruns = total;
+    run_start[total] = m;
+  }
+}
+
+// ---- host launchers ----------------------------------------------------------------------
+static uint32_t grid_for(uint64_t n, uint32_t per_block, uint32_t cap) {
+  uint64_t g = (n + per_block - 1) / per_block;
+  if (g < 1) g = 1;
+  if (g > cap) g = cap;
+  return (uint32_t)g;
+}
+
+uint32_t sort_tiles(uint64_t n) { return (uint32_t)((n + kSortTile - 1) / kSortTile); }
+uint32_t comp_tiles(uint64_t n) { return (uint32_t)((n + kScanTile - 1) / kScanTile); }
+
+void launch_front(const FrontArgs &f, cudaStream_t s) {
+  const PrepArgs &a = f.prep;
+  const uint64_t n = (uint64_t)a.n_ins + a.n_del;
+  k_init_batch<<<1, 256, 0, s>>>(f.ctl, f.hist, a.npass * 256u, (uint32_t)n);
+  k_prep<<<grid_for(n, 256, 4 * 152), 256, 0, s>>>(a, f.ins, f.del, f.bufA, f.hist, f.ctl);
+  uint64_t *src = f.bufA, *dst = f.bufB;
+  const uint32_t st = sort_tiles(n);
+  for (uint32_t p = 0; p < a.npass; p++) {
+    k_sort_pass<<<st, kSortThreads, 0, s>>>(src, dst, f.hist, f.status, f.ctl, p, p * a.dbits, a.dbits);
+    uint64_t *t = src; src = dst; dst = t;
+  }
+  // look-back epochs: pass p uses epoch + p, then the fixed slots of gpma_launch.h
+  const uint32_t ct = comp_tiles(n);
+  k_keep<<<ct, kScanThreads, 0, s>>>(a, src, f.geo->F, f.geo->nleaves, f.ukey, f.utag, f.uleaf, f.status,
+                                     f.ctl);
+  k_runs<<<ct, kScanThreads, 0, s>>>(f.uleaf, f.run_start, f.status, f.ctl);
+}
+
+}  // namespace gpk

@@ -1,0 +1,649 @@
+// k_update.cu -- the level loop of Algorithm "GPMA+ Segment-Oriented Insertion"
+// (Sec. 5.2) with lazy deletion (Sec. 6.1), organised for one GB300.
+//
+// Fact used throughout: for a segment s of level i the test of TryInsert+ compares
+// n_s + |U_s| with max_i, where n_s counts the valid keys of s after the deletes and
+// after the merges of lower levels, and U_s are the inserts of s still pending.
+// Every insert of s is either merged below (and counted in n_s) or pending (and
+// counted in U_s), so n_s + |U_s| = (valid keys of s after the deletes) + (all
+// surviving inserts of s): the test does not depend on the order of the merges.
+// The level at which an insert merges is therefore the lowest level whose
+// segment passes that test, computable from a count tree, and the final layout
+// is fixed by the outermost merged segments alone (a merge re-spreads its whole
+// segment, erasing any merge inside it).  So:
+//   k_leaf_pass    one warp per touched leaf: presence filter, lazy deletes, and the
+//                  level-0 TryInsert+ (merge + even re-dispatch inside the leaf)
+//   k_propagate    add every leaf's count change to its ancestors in the count tree
+//   k_pending / k_eruns / k_esc_level / k_esc_top / k_segs
+//                  inserts that did not fit their leaf: find their merge level,
+//                  the outermost merged segments and their pending inserts
+//   segment merge  gather valid keys of those segments, merge with the pending
+//                  inserts (merge path), re-dispatch evenly, rewrite the counts
+#include "gpma_dev.cuh"
+#include "gpma_launch.h"
+#include "scan_dev.cuh"
+
+namespace gpk {
+
+// per-warp shared memory of the leaf kernels: three key buffers of L, a u16
+// index array of L+1 and a byte mask of L
+__host__ __device__ inline uint32_t leaf_smem_bytes(uint32_t L) {
+  return 24u * L + ((2u * (L + 1u) + 15u) & ~15u) + ((L + 15u) & ~15u);
+}
+
+struct WarpBufs {
+  uint64_t *a, *b, *out;
+  uint16_t *pos;
+  uint8_t *mark;
+};
+
+__device__ __forceinline__ WarpBufs warp_bufs(unsigned char *smem, uint32_t per_warp, uint32_t L) {
+  unsigned char *base = smem + (threadIdx.x >> 5) * per_warp;
+  WarpBufs b;
+  b.a = (uint64_t *)base;
+  b.b = b.a + L;
+  b.out = b.b + L;
+  b.pos = (uint16_t *)(b.out + L);
+  b.mark = base + 24u * L + ((2u * (L + 1u) + 15u) & ~15u);
+  return b;
+}
+
+// ---- level 0: one warp per touched leaf ------------------------------------------------------
+__global__ void k_leaf_pass(Geo g, Ctl *ctl, Work w, uint32_t per_warp) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  if (ctl->err) return;
+  const uint32_t L = g.L, lane = lane_id();
+  const uint32_t wpb = blockDim.x >> 5;
+  WarpBufs B = warp_bufs(smem, per_warp, L);
+  uint64_t *vkeys = B.a, *ins = B.b, *out = B.out;
+  uint16_t *vpos = B.pos;
+  uint8_t *dmark = B.mark;
+  const uint32_t nruns = ctl->nruns;
+  const uint64_t max0 = g.maxc[0];
+  uint64_t acc_ins = 0, acc_del = 0;
+  uint32_t acc_m0 = 0, acc_esc = 0;
+  for (uint32_t r = blockIdx.x * wpb + (threadIdx.x >> 5); r < nruns; r += gridDim.x * wpb) {
+    const uint32_t rs = w.run_start[r], re = w.run_start[r + 1];
+    const uint32_t j = w.uleaf[rs];
+    uint64_t *leaf = g.slots + (uint64_t)j * L;
+    // the leaf's valid keys, compacted, with their slot offsets
+    uint32_t nv = 0;
+    for (uint32_t b = 0; b < L; b += 32) {
+      uint32_t o = b + lane;
+      uint64_t k = o < L ? leaf[o] : kEmpty;
+      bool v = k != kEmpty;
+      uint32_t bal = __ballot_sync(0xFFFFFFFFu, v);
+      if (v) {
+        uint32_t idx = nv + __popc(bal & lanemask_lt());
+        vkeys[idx] = k;
+        vpos[idx] = (uint16_t)o;
+        dmark[idx] = 0;
+      }
+      nv += __popc(bal);
+    }
+    __syncwarp();
+    // presence filter (reading R3) and lazy deletes (R5); surviving inserts in order
+    uint32_t nins = 0, ndel = 0;
+    for (uint32_t c = rs; c < re; c += 32) {
+      const uint32_t e = c + lane;
+      const bool act = e < re;
+      uint64_t key = act ? w.ukey[e] : 0ull;
+      uint32_t tag = act ? w.utag[e] : 0u;
+      uint32_t idx = act ? lower_bound_dev(vkeys, nv, key) : 0u;
+      bool found = act && idx < nv && vkeys[idx] == key;
+      bool dl = act && tag && found;
+      bool sv = act && !tag && !found;
+      if (dl) dmark[idx] = 1;
+      uint32_t bs = __ballot_sync(0xFFFFFFFFu, sv);
+      if (sv) {
+        uint32_t p = nins + __popc(bs & lanemask_lt());
+        if (p < L) ins[p] = key;
+      }
+      nins += __popc(bs);
+      ndel += __popc(__ballot_sync(0xFFFFFFFFu, dl));
+      if (act) w.eflag[e] = dl ? 1 : (sv ? 2 : 0);
+    }
+    __syncwarp();
+    const uint32_t cnt_del = nv - ndel;
+    const bool fits = nins > 0 && (uint64_t)cnt_del + nins <= max0;
+    if (fits) {
+      // TryInsert+ at level 0: merge the kept keys with the inserts, left-packed
+      uint32_t run = 0;
+      for (uint32_t b = 0; b < nv; b += 32) {
+        uint32_t a = b + lane;
+        bool kp = a < nv && !dmark[a];
+        uint32_t bal = __ballot_sync(0xFFFFFFFFu, kp);
+        if (a < nv) vpos[a] = (uint16_t)(run + __popc(bal & lanemask_lt()));  // kept keys before a
+        run += __popc(bal);
+      }
+      if (lane == 0) vpos[nv] = (uint16_t)run;
+      __syncwarp();
+      for (uint32_t a = lane; a < nv; a += 32)
+        if (!dmark[a]) out[vpos[a] + lower_bound_dev(ins, nins, vkeys[a])] = vkeys[a];
+      for (uint32_t b = lane; b < nins; b += 32) out[b + vpos[lower_bound_dev(vkeys, nv, ins[b])]] = ins[b];
+      __syncwarp();
+      const uint32_t n = cnt_del + nins;
+      for (uint32_t o = lane; o < L; o += 32) {
+        uint64_t k = o < n ? out[o] : kEmpty;
+        leaf[o] = k;
+        if (!g.raw && o < n && is_guard(k)) g.row_end[k >> 32] = (uint32_t)((uint64_t)j * L + o);
+      }
+      if (lane == 0) {
+        g.F[j] = out[0];
+        g.cnt[j] = n;
+      }
+      for (uint32_t c = rs + lane; c < re; c += 32)
+        if (w.eflag[c] == 2) w.eflag[c] = 1;
+    } else {
+      for (uint32_t a = lane; a < nv; a += 32)
+        if (dmark[a]) leaf[vpos[a]] = kEmpty;
+      uint32_t first = nv;
+      for (uint32_t b = 0; b < nv; b += 32) {
+        uint32_t a = b + lane;
+        uint32_t bal = __ballot_sync(0xFFFFFFFFu, a < nv && !dmark[a]);
+        if (bal) {
+          first = b + __ffs(bal) - 1;
+          break;
+        }
+      }
+      if (lane == 0) {
+        g.F[j] = first < nv ? vkeys[first] : kEmpty;
+        g.cnt[j] = cnt_del;
+      }
+    }
+    if (lane == 0) {
+      w.rleaf[r] = j;
+      w.rdelta[r] = (int32_t)nins - (int32_t)ndel;
+      w.rinfo[r] = fits ? 1 : (nins ? 2 : 0);
+      w.rdel[r] = ndel;
+    }
+    acc_ins += nins;
+    acc_del += ndel;
+    acc_m0 += fits;
+    acc_esc += (!fits && nins);
+    __syncwarp();
+  }
+  if (lane == 0) {
+    if (acc_ins) atomicAdd((unsigned long long *)&ctl->n_inserted, (unsigned long long)acc_ins);
+    if (acc_del) atomicAdd((unsigned long long *)&ctl->n_deleted, (unsigned long long)acc_del);
+    if (acc_m0) atomicAdd(&ctl->n_merged0, acc_m0);
+    if (acc_esc) atomicAdd(&ctl->nesc, acc_esc);
+  }
+}
+
+// ---- count tree: add each touched leaf's change to its ancestors ----------------------------
+// A block takes 1024 consecutive runs (sorted by leaf); per level it adds one
+// aggregated value per distinct ancestor, so the root sees one atomic per block.
+__global__ void __launch_bounds__(1024) k_propagate(Geo g, Ctl *ctl, const uint32_t *__restrict__ rleaf,
+                                                    const int32_t *__restrict__ rdelta) {
+  __shared__ int32_t P[1024];
+  __shared__ uint32_t lf[1024];
+  __shared__ int32_t wsum[32];
+  if (ctl->err) return;
+  const uint32_t nruns = ctl->nruns, lane = lane_id(), wid = threadIdx.x >> 5;
+  for (uint64_t c0 = (uint64_t)blockIdx.x * 1024; c0 < nruns; c0 += (uint64_t)gridDim.x * 1024) {
+    const uint64_t r = c0 + threadIdx.x;
+    const bool act = r < nruns;
+    const int32_t d = act ? rdelta[r] : 0;
+    const uint32_t leaf = act ? rleaf[r] : 0xFFFFFFFFu;
+    int32_t inc = warp_incl_scan(d);
+    if (lane == 31) wsum[wid] = inc;
+    __syncthreads();
+    if (wid == 0) {
+      int32_t v = wsum[lane];
+      wsum[lane] = warp_incl_scan(v) - v;
+    }
+    __syncthreads();
+    inc += wsum[wid];
+    P[threadIdx.x] = inc;
+    lf[threadIdx.x] = leaf;
+    __syncthreads();
+    if (threadIdx.x == 1023 && P[1023] != 0)
+      atomicAdd((unsigned long long *)&ctl->total, (unsigned long long)(long long)P[1023]);
+    const uint32_t cnt = (uint32_t)min((uint64_t)1024, nruns - c0);
+    if (act) {
+      for (uint32_t i = 1; i <= g.h; i++) {
+        const uint32_t node = leaf >> i;
+        if (threadIdx.x > 0 && (lf[threadIdx.x - 1] >> i) == node) continue;
+        uint32_t lo = threadIdx.x + 1, hi = cnt;  // end of this ancestor's runs in the block
+        while (lo < hi) {
+          uint32_t mid = (lo + hi) >> 1;
+          if ((lf[mid] >> i) > node) hi = mid; else lo = mid + 1;
+        }
+        int32_t s = P[lo - 1] - (threadIdx.x ? P[threadIdx.x - 1] : 0);
+        if (s) atomicAdd(&g.tree[g.tree_off[i] + node], (uint32_t)s);
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// ---- escalation: inserts that did not fit their leaf -----------------------------------------
+__global__ void __launch_bounds__(kScanThreads) k_pending(Ctl *ctl, Work w) {
+  __shared__ ScanSmem sm;
+  if (ctl->err || ctl->nesc == 0) return;
+  const uint32_t tile = take_ticket(ctl, kSlotPend, sm), m = ctl->m;
+  if ((uint64_t)tile * kScanTile >= m && tile > 0) return;
+  uint32_t flag[kScanItems];
+#pragma unroll
+  for (int r = 0; r < kScanItems; r++) {
+    uint64_t e = scan_elem(tile, r);
+    flag[r] = e < m && w.eflag[e] == 2;
+  }
+  uint32_t off[kScanItems];
+  uint32_t total = tile_scan(flag, off, tile, w.status, 1, 0, ctl->epoch + kSlotPend, &ctl->err, sm);
+#pragma unroll
+  for (int r = 0; r < kScanItems; r++) {
+    if (!flag[r] || off[r] >= m) continue;
+    uint64_t e = scan_elem(tile, r);
+    w.pkey[off[r]] = w.ukey[e];
+    w.pleaf[off[r]] = w.uleaf[e];
+  }
+  if ((uint64_t)(tile + 1) * kScanTile >= m && threadIdx.x == 0) ctl->npend = total;
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_eruns(Ctl *ctl, Work w) {
+  __shared__ ScanSmem sm;
+  if (ctl->err || ctl->npend == 0) return;
+  const uint32_t tile = take_ticket(ctl, kSlotERuns, sm), np = ctl->npend;
+  if ((uint64_t)tile * kScanTile >= np && tile > 0) return;
+  uint32_t flag[kScanItems];
+#pragma unroll
+  for (int r = 0; r < kScanItems; r++) {
+    uint64_t p = scan_elem(tile, r);
+    flag[r] = p < np && (p == 0 || w.pleaf[p] != w.pleaf[p - 1]);
+  }
+  uint32_t off[kScanItems];
+  uint32_t total = tile_scan(flag, off, tile, w.status, 1, 0, ctl->epoch + kSlotERuns, &ctl->err, sm);
+#pragma unroll
+  for (int r = 0; r < kScanItems; r++)
+    if (flag[r] && off[r] < np) w.erun[off[r]] = (uint32_t)scan_elem(tile, r);
+  if ((uint64_t)(tile + 1) * kScanTile >= np && threadIdx.x == 0) {
+    ctl->neruns = total;
+    w.erun[total] = np;
+  }
+}
+
+// merge level of every pending run: the lowest level whose segment passes the test.
+// With may_fail set, a run that no level admits is counted in nfail (root resize).
+__global__ void k_esc_level(Geo g, Ctl *ctl, Work w, int resize) {  // resize = may_fail
+  if (ctl->err) return;
+  const uint32_t ner = ctl->neruns;
+  for (uint32_t r = blockIdx.x * blockDim.x + threadIdx.x; r < ner; r += gridDim.x * blockDim.x) {
+    const uint32_t j = w.pleaf[w.erun[r]];
+    uint32_t lvl = kNoLevel;
+    for (uint32_t i = 1; i <= g.h; i++) {
+      if (g.tree[g.tree_off[i] + (j >> i)] <= g.maxc[i]) {
+        lvl = i;
+        break;
+      }
+    }
+    w.elvl[r] = (uint8_t)lvl;
+    if (lvl != kNoLevel) {
+      uint32_t old = atomicExch(&g.mark[g.tree_off[lvl] + (j >> lvl)], 1u);
+      if (!old) atomicAdd((unsigned long long *)&ctl->merges[lvl], 1ull);
+      atomicMax(&ctl->levels_climbed, lvl);
+    } else if (resize) {
+      atomicAdd(&ctl->nfail, 1u);
+    } else {
+      atomicOr(&ctl->err, kErrInternal);
+    }
+  }
+}
+
+// outermost merged segment above every pending run
+__global__ void k_esc_top(Geo g, Ctl *ctl, Work w) {
+  if (ctl->err) return;
+  const uint32_t ner = ctl->neruns;
+  for (uint32_t r = blockIdx.x * blockDim.x + threadIdx.x; r < ner; r += gridDim.x * blockDim.x) {
+    const uint32_t lvl = w.elvl[r];
+    const uint32_t j = w.pleaf[w.erun[r]];
+    uint32_t top = lvl;
+    for (uint32_t i = lvl + 1; i <= g.h; i++)
+      if (g.mark[g.tree_off[i] + (j >> i)]) top = i;
+    w.etop[r] = (uint8_t)top;
+  }
+}
+
+__global__ void k_unmark(Geo g, Ctl *ctl, Work w) {
+  const uint32_t ner = ctl->neruns;
+  for (uint32_t r = blockIdx.x * blockDim.x + threadIdx.x; r < ner; r += gridDim.x * blockDim.x) {
+    const uint32_t lvl = w.elvl[r];
+    if (lvl == kNoLevel) continue;
+    g.mark[g.tree_off[lvl] + (w.pleaf[w.erun[r]] >> lvl)] = 0;
+  }
+}
+
+// runs sharing an outermost segment are consecutive: one entry per segment, with
+// its first pending insert and the prefix of covered leaves; clears the marks
+__global__ void __launch_bounds__(kScanThreads) k_segs(Geo g, Ctl *ctl, Work w) {
+  __shared__ ScanSmem sm;
+  if (ctl->err || ctl->neruns == 0) return;
+  const uint32_t tile = take_ticket(ctl, kSlotSegs, sm), ner = ctl->neruns;
+  if ((uint64_t)tile * kScanTile >= ner && tile > 0) return;
+  uint32_t flag[kScanItems], lv[kScanItems];
+  uint32_t top[kScanItems], node[kScanItems];
+#pragma unroll
+  for (int r = 0; r < kScanItems; r++) {
+    uint64_t q = scan_elem(tile, r);
+    flag[r] = 0;
+    lv[r] = 0;
+    top[r] = 0;
+    node[r] = 0;
+    if (q < ner) {
+      top[r] = w.etop[q];
+      node[r] = w.pleaf[w.erun[q]] >> top[r];
+      if (q == 0) {
+        flag[r] = 1;
+      } else {
+        uint32_t pt = w.etop[q - 1];
+        uint32_t pn = w.pleaf[w.erun[q - 1]] >> pt;
+        flag[r] = (pt != top[r]) || (pn != node[r]);
+      }
+      lv[r] = flag[r] ? (1u << top[r]) : 0u;
+    }
+  }
+  uint32_t off[kScanItems], loff[kScanItems];
+  uint32_t total = tile_scan(flag, off, tile, w.status, 2, 0, ctl->epoch + kSlotSegs, &ctl->err, sm);
+  uint32_t ltotal = tile_scan(lv, loff, tile, w.status, 2, 1, ctl->epoch + kSlotSegs, &ctl->err, sm);
+#pragma unroll
+  for (int r = 0; r < kScanItems; r++) {
+    uint64_t q = scan_elem(tile, r);
+    if (q >= ner) continue;
+    const uint32_t lvl = w.elvl[q];
+    g.mark[g.tree_off[lvl] + (w.pleaf[w.erun[q]] >> lvl)] = 0;
+    if (!flag[r] || off[r] >= ner) continue;
+    w.seg_top[off[r]] = (uint8_t)top[r];
+    w.seg_node[off[r]] = node[r];
+    w.seg_pstart[off[r]] = w.erun[q];
+    w.seg_lpre[off[r]] = loff[r];
+  }
+  if ((uint64_t)(tile + 1) * kScanTile >= ner && threadIdx.x == 0) {
+    ctl->nsegs = total;
+    ctl->nleafw = ltotal;
+    w.seg_pstart[total] = ctl->npend;
+    w.seg_lpre[total] = ltotal;
+  }
+}
+
+// ---- merge of segments: gather, merge path, even re-dispatch ---------------------------------
+struct SegArgs {
+  int whole;            // 1: the whole source array into a new array (root resize)
+  uint32_t whole_top;   // height of the new array
+  uint64_t src_nleaves; // leaves of the source array (whole mode)
+};
+
+__device__ __forceinline__ uint32_t seg_of(const uint32_t *lpre, uint32_t nsegs, uint32_t wl) {
+  uint32_t lo = 0, hi = nsegs;  // last k with lpre[k] <= wl
+  while (hi - lo > 1) {
+    uint32_t mid = (lo + hi) >> 1;
+    if (lpre[mid] <= wl) lo = mid; else hi = mid;
+  }
+  return lo;
+}
+
+__global__ void k_seg_vcnt(Geo src, Ctl *ctl, Work w, uint32_t *vcnt) {
+  if (ctl->err) return;
+  const uint32_t nsegs = ctl->nsegs, nlw = ctl->nleafw;
+  for (uint32_t x = blockIdx.x * blockDim.x + threadIdx.x; x < nlw; x += gridDim.x * blockDim.x) {
+    uint32_t k = seg_of(w.seg_lpre, nsegs, x);
+    uint32_t top = w.seg_top[k];
+    uint64_t leaf = ((uint64_t)w.seg_node[k] << top) + (x - w.seg_lpre[k]);
+    vcnt[x] = src.cnt[leaf];
+  }
+}
+
+// one warp per source leaf: its valid keys go to scratch[voff[x] ...] in order
+__global__ void k_seg_gather(Geo src, Ctl *ctl, Work w, SegArgs sa, const uint64_t *voff, uint64_t *scratch,
+                             uint64_t scratch_cap) {
+  if (ctl->err) return;
+  const uint32_t lane = lane_id(), L = src.L;
+  const uint64_t nlw = sa.whole ? sa.src_nleaves : ctl->nleafw;
+  const uint32_t nsegs = ctl->nsegs;
+  const uint64_t nw = (uint64_t)gridDim.x * (blockDim.x >> 5);
+  for (uint64_t x = (uint64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); x < nlw; x += nw) {
+    uint64_t leaf = x;
+    if (!sa.whole) {
+      uint32_t k = seg_of(w.seg_lpre, nsegs, (uint32_t)x);
+      leaf = ((uint64_t)w.seg_node[k] << w.seg_top[k]) + (x - w.seg_lpre[k]);
+    }
+    const uint64_t *p = src.slots + leaf * L;
+    uint64_t o = voff[x];
+    for (uint32_t b = 0; b < L; b += 32) {
+      uint64_t k = (b + lane < L) ? p[b + lane] : kEmpty;
+      bool v = k != kEmpty;
+      uint32_t bal = __ballot_sync(0xFFFFFFFFu, v);
+      const uint64_t at = o + __popc(bal & lanemask_lt());
+      if (v && at < scratch_cap) scratch[at] = k;
+      o += __popc(bal);
+    }
+  }
+}
+
+// number of A elements among the first r of merge(A, B) (keys distinct)
+__device__ __forceinline__ uint64_t co_rank(const uint64_t *A, uint64_t na, const uint64_t *B, uint64_t nb,
+                                            uint64_t r) {
+  uint64_t lo = r > nb ? r - nb : 0, hi = r < na ? r : na;
+  while (lo < hi) {
+    uint64_t i = (lo + hi) >> 1;
+    if (A[i] < B[r - i - 1]) lo = i + 1; else hi = i;
+  }
+  return lo;
+}
+
+struct SegGeom {
+  uint64_t dleaf;     // destination leaf
+  uint64_t t, top;    // leaf index inside the segment, segment height
+  uint64_t abase, na; // valid keys of the segment in scratch
+  uint64_t bbase, nb; // pending inserts of the segment
+};
+
+__device__ __forceinline__ SegGeom seg_geom(const Work &w, SegArgs sa, const uint64_t *voff, Ctl *ctl,
+                                            uint64_t x) {
+  SegGeom s;
+  if (sa.whole) {
+    s.dleaf = x;
+    s.t = x;
+    s.top = sa.whole_top;
+    s.abase = 0;
+    s.na = voff[sa.src_nleaves];
+    s.bbase = 0;
+    s.nb = ctl->npend;
+  } else {
+    uint32_t k = seg_of(w.seg_lpre, ctl->nsegs, (uint32_t)x);
+    s.top = w.seg_top[k];
+    s.t = x - w.seg_lpre[k];
+    s.dleaf = ((uint64_t)w.seg_node[k] << s.top) + s.t;
+    s.abase = voff[w.seg_lpre[k]];
+    s.na = voff[w.seg_lpre[k + 1]] - s.abase;
+    s.bbase = w.seg_pstart[k];
+    s.nb = w.seg_pstart[k + 1] - s.bbase;
+  }
+  return s;
+}
+
+// one warp per destination leaf: its share [n t / m, n (t+1) / m) of the merged keys
+__global__ void k_seg_write(Geo dst, Ctl *ctl, Work w, SegArgs sa, const uint64_t *voff,
+                            const uint64_t *scratch, uint32_t per_warp) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  if (ctl->err) return;
+  const uint32_t lane = lane_id(), L = dst.L;
+  WarpBufs Bf = warp_bufs(smem, per_warp, L);
+  uint64_t *sa_ = Bf.a, *sb_ = Bf.b, *out = Bf.out;
+  const uint64_t nlw = sa.whole ? dst.nleaves : ctl->nleafw;
+  const uint64_t nw = (uint64_t)gridDim.x * (blockDim.x >> 5);
+  for (uint64_t x = (uint64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); x < nlw; x += nw) {
+    const SegGeom s = seg_geom(w, sa, voff, ctl, x);
+    const uint64_t n = s.na + s.nb;
+    const uint64_t a = (n * s.t) >> s.top, b = (n * (s.t + 1)) >> s.top;
+    if (b - a > L) {  // cannot happen when the counts are consistent
+      if (lane == 0) atomicOr(&ctl->err, kErrInternal);
+      break;
+    }
+    const uint64_t *A = scratch + s.abase, *Bk = w.pkey + s.bbase;
+    uint64_t i0 = 0, i1 = 0;
+    if (lane == 0) {
+      i0 = co_rank(A, s.na, Bk, s.nb, a);
+      i1 = co_rank(A, s.na, Bk, s.nb, b);
+    }
+    i0 = __shfl_sync(0xFFFFFFFFu, i0, 0);
+    i1 = __shfl_sync(0xFFFFFFFFu, i1, 0);
+    const uint32_t na = (uint32_t)(i1 - i0), nb = (uint32_t)((b - a) - na);
+    const uint64_t j0 = a - i0;
+    for (uint32_t q = lane; q < na; q += 32) sa_[q] = A[i0 + q];
+    for (uint32_t q = lane; q < nb; q += 32) sb_[q] = Bk[j0 + q];
+    __syncwarp();
+    for (uint32_t q = lane; q < na; q += 32) out[q + lower_bound_dev(sb_, nb, sa_[q])] = sa_[q];
+    for (uint32_t q = lane; q < nb; q += 32) out[q + lower_bound_dev(sa_, na, sb_[q])] = sb_[q];
+    __syncwarp();
+    const uint32_t cntl = na + nb;
+    uint64_t *leaf = dst.slots + s.dleaf * L;
+    for (uint32_t o = lane; o < L; o += 32) {
+      uint64_t k = o < cntl ? out[o] : kEmpty;
+      leaf[o] = k;
+      if (!dst.raw && o < cntl && is_guard(k)) dst.row_end[k >> 32] = (uint32_t)(s.dleaf * L + o);
+    }
+    if (lane == 0) {
+      dst.cnt[s.dleaf] = cntl;
+      dst.F[s.dleaf] = cntl ? out[0] : kEmpty;
+    }
+    __syncwarp();
+  }
+}
+
+// counts of the tree nodes inside each rewritten segment (their share of n)
+__global__ void k_seg_tree(Geo dst, Ctl *ctl, Work w, SegArgs sa, const uint64_t *voff) {
+  if (ctl->err) return;
+  const uint64_t nlw = sa.whole ? dst.nleaves : ctl->nleafw;
+  for (uint64_t x = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; x < nlw; x += (uint64_t)gridDim.x * blockDim.x) {
+    const SegGeom s = seg_geom(w, sa, voff, ctl, x);
+    const uint64_t n = s.na + s.nb;
+    const uint64_t qmax = sa.whole ? s.top : s.top - 1;
+    for (uint64_t q = 1; q <= qmax; q++) {
+      if (s.t & ((1ull << q) - 1ull)) break;
+      uint64_t c = ((n * (s.t + (1ull << q))) >> s.top) - ((n * s.t) >> s.top);
+      dst.tree[dst.tree_off[q] + (s.dleaf >> q)] = (uint32_t)c;
+    }
+  }
+}
+
+// ---- statistics (only when the caller asks for them) -------------------------------------------
+__global__ void k_stats(Ctl *ctl, Work w) {
+  const uint32_t nruns = ctl->nruns, nsegs = ctl->nsegs;
+  uint64_t cov = 0, emp = 0, l0 = 0;
+  for (uint32_t r = blockIdx.x * blockDim.x + threadIdx.x; r < nruns; r += gridDim.x * blockDim.x) {
+    const uint32_t leaf = w.rleaf[r], info = w.rinfo[r];
+    bool in = false;
+    if (nsegs) {
+      uint32_t lo = 0, hi = nsegs;  // last segment starting at or before leaf
+      while (hi - lo > 1) {
+        uint32_t mid = (lo + hi) >> 1;
+        if (((uint64_t)w.seg_node[mid] << w.seg_top[mid]) <= leaf) lo = mid; else hi = mid;
+      }
+      uint64_t st = (uint64_t)w.seg_node[lo] << w.seg_top[lo];
+      in = leaf >= st && leaf < st + (1ull << w.seg_top[lo]);
+    }
+    const bool covered = info == 1 || in;
+    cov += covered;
+    emp += covered ? 0 : w.rdel[r];
+    l0 += (info == 1 && !in);
+  }
+  cov = warp_sum(cov);
+  emp = warp_sum(emp);
+  l0 = warp_sum(l0);
+  if (lane_id() == 0) {
+    if (cov) atomicAdd((unsigned long long *)&ctl->st_cov_touched, (unsigned long long)cov);
+    if (emp) atomicAdd((unsigned long long *)&ctl->st_empties, (unsigned long long)emp);
+    if (l0) atomicAdd((unsigned long long *)&ctl->st_l0_only, (unsigned long long)l0);
+  }
+}
+
+// ---- host launchers ------------------------------------------------------------------------------
+static uint32_t blocks_for(uint64_t items, uint32_t per_block, uint32_t cap) {
+  uint64_t b = (items + per_block - 1) / per_block;
+  if (b < 1) b = 1;
+  if (b > cap) b = cap;
+  return (uint32_t)b;
+}
+
+static uint32_t warps_per_block(uint32_t L) {
+  uint32_t pw = leaf_smem_bytes(L);
+  uint32_t wpb = (96u * 1024u) / pw;
+  if (wpb > 8) wpb = 8;
+  if (wpb < 1) wpb = 1;
+  return wpb;
+}
+
+static void allow_big_smem() {
+  static bool done = false;
+  if (done) return;
+  cudaFuncSetAttribute(k_leaf_pass, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  cudaFuncSetAttribute(k_seg_write, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  done = true;
+}
+
+void launch_leaf_pass(const Geo &g, Ctl *ctl, const Work &w, uint32_t n, cudaStream_t s) {
+  allow_big_smem();
+  const uint32_t pw = leaf_smem_bytes(g.L), wpb = warps_per_block(g.L);
+  k_leaf_pass<<<blocks_for(n, wpb, 152 * 16), wpb * 32, wpb * pw, s>>>(g, ctl, w, pw);
+}
+
+void launch_propagate(const Geo &g, Ctl *ctl, const Work &w, uint32_t n, cudaStream_t s) {
+  k_propagate<<<blocks_for(n, 1024, 152 * 2), 1024, 0, s>>>(g, ctl, w.rleaf, w.rdelta);
+}
+
+void launch_pending(const Geo &g, Ctl *ctl, const Work &w, uint32_t n, cudaStream_t s) {
+  (void)g;
+  const uint32_t ct = comp_tiles(n);
+  k_pending<<<ct, kScanThreads, 0, s>>>(ctl, w);
+  k_eruns<<<ct, kScanThreads, 0, s>>>(ctl, w);
+}
+
+void launch_esc_level(const Geo &g, Ctl *ctl, const Work &w, uint32_t n, bool may_fail, cudaStream_t s) {
+  k_esc_level<<<blocks_for(n, 256, 152 * 8), 256, 0, s>>>(g, ctl, w, may_fail ? 1 : 0);
+}
+
+void launch_esc_top(const Geo &g, Ctl *ctl, const Work &w, uint32_t n, cudaStream_t s) {
+  k_esc_top<<<blocks_for(n, 256, 152 * 8), 256, 0, s>>>(g, ctl, w);
+}
+
+void launch_unmark(const Geo &g, Ctl *ctl, const Work &w, uint32_t n, cudaStream_t s) {
+  k_unmark<<<blocks_for(n, 256, 152 * 8), 256, 0, s>>>(g, ctl, w);
+}
+
+void launch_segments(const Geo &g, Ctl *ctl, const Work &w, uint32_t n, cudaStream_t s) {
+  k_segs<<<comp_tiles(n), kScanThreads, 0, s>>>(g, ctl, w);
+}
+
+void launch_stats(const Geo &g, Ctl *ctl, const Work &w, uint32_t n, cudaStream_t s) {
+  (void)g;
+  k_stats<<<blocks_for(n, 256, 152 * 8), 256, 0, s>>>(ctl, w);
+}
+
+void launch_segment_merge(const Geo &src, const Geo &dst, Ctl *ctl, const Work &w, uint64_t scratch_cap,
+                          uint64_t nleafw_bound, uint64_t *scratch, uint32_t *voff_u32tmp, uint64_t *partials,
+                          bool whole, cudaStream_t s) {
+  allow_big_smem();
+  SegArgs sa;
+  sa.whole = whole ? 1 : 0;
+  sa.whole_top = dst.h;
+  sa.src_nleaves = src.nleaves;
+  // voff (u64, nleafw + 1 entries) lives right after the u32 counts in the same buffer
+  uint32_t *vcnt = voff_u32tmp;
+  uint64_t *voff = (uint64_t *)(((uintptr_t)(vcnt + nleafw_bound + 1) + 15) & ~(uintptr_t)15);
+  const uint32_t *cnt_in = vcnt;
+  if (whole) {
+    cnt_in = src.cnt;
+  } else {
+    k_seg_vcnt<<<blocks_for(nleafw_bound, 256, 152 * 8), 256, 0, s>>>(src, ctl, w, vcnt);
+  }
+  launch_scan_u32_u64(cnt_in, voff, whole ? src.nleaves : nleafw_bound, partials, s,
+                      whole ? nullptr : &ctl->nleafw);
+  k_seg_gather<<<blocks_for(nleafw_bound, 8, 152 * 16), 256, 0, s>>>(src, ctl, w, sa, voff, scratch, scratch_cap);
+  const uint32_t pw = leaf_smem_bytes(dst.L), wpb = warps_per_block(dst.L);
+  const uint64_t dst_bound = whole ? dst.nleaves : nleafw_bound;
+  k_seg_write<<<blocks_for(dst_bound, wpb, 152 * 16), wpb * 32, wpb * pw, s>>>(dst, ctl, w, sa, voff, scratch, pw);
+  k_seg_tree<<<blocks_for(dst_bound, 256, 152 * 8), 256, 0, s>>>(dst, ctl, w, sa, voff);
+}
+
+}  // namespace gpk

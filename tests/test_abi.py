@@ -1,0 +1,56 @@
+"""The C-ABI library loads on a machine without a GPU and exports every entry
+point that include/gpma.h declares (no compute calls here)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+import paper_1709_05061_gb300 as gp
+
+HEADER = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include", "gpma.h")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    gp.build()
+    return gp.lib()
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(gpma_[a-z_]+)\s*\(", text)))
+
+
+def test_header_declares_the_survey_calls():
+    names = declared_functions()
+    for n in ["gpma_create", "gpma_destroy", "gpma_update_batch", "gpma_bfs", "gpma_cc", "gpma_pagerank",
+              "gpma_export_sorted", "gpma_export_csr", "gpma_export_layout", "gpma_import_layout",
+              "gpma_num_edges", "gpma_capacity", "gpma_strerror", "gpma_status", "gpma_check", "gpma_row_end"]:
+        assert n in names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    for name in declared_functions():
+        assert hasattr(lib, name), name
+        assert ctypes.cast(getattr(lib, name), ctypes.c_void_p).value
+
+
+def test_strerror_without_gpu(lib):
+    for code in range(6):
+        assert gp.gpma_strerror(code)
+    assert "unknown" in gp.gpma_strerror(99)
+
+
+def test_argument_errors_without_gpu(lib):
+    # rejected on the host before any CUDA call
+    assert lib.gpma_destroy(None) == gp.GPMA_EINVAL
+    assert lib.gpma_capacity(None, None) == gp.GPMA_EINVAL
+    out = ctypes.c_void_p()
+    p = gp.gpma_params(3, 0, 0, 0, 0, 0)  # leaf size not a power of two
+    assert lib.gpma_create(10, ctypes.byref(p), None, None, ctypes.byref(out)) == gp.GPMA_EINVAL
+    p = gp.gpma_params(64, 50, 80, 0, 0, 0)  # tau_0 below tau_h
+    assert lib.gpma_create(10, ctypes.byref(p), None, None, ctypes.byref(out)) == gp.GPMA_EINVAL
+    p = gp.gpma_params(64, 0, 0, 0, 0, 0)
+    assert lib.gpma_create(0, ctypes.byref(p), None, None, ctypes.byref(out)) == gp.GPMA_EINVAL

@@ -1,0 +1,253 @@
+"""GPU parity: the CUDA library against the CPU oracle, element by element,
+through the C ABI (via the thin binding).  Layout, exported edges, CSR, guard
+index, stats: bit-exact.  BFS depths and CC labels: exact.  PageRank (FP32):
+max relative error <= 1e-5 against the FP64 oracle."""
+import numpy as np
+import pytest
+
+import oracle
+from helpers import EMPTY, apply_set_semantics, ints, parse_leaves, read_golden
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+import paper_1709_05061_gb300 as gp  # noqa: E402
+from paper_1709_05061_gb300 import workloads as W  # noqa: E402
+
+PR_TOL = 1e-5
+STAT_KEYS = ("n_inserted", "n_deleted", "n_ignored", "levels_climbed", "resized", "alg_bytes",
+             "touched_leaves", "covered_leaves", "merges")
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(np.asarray(a, dtype=np.uint64)).view(np.int64)).cuda()
+
+
+def host(t):
+    return t.cpu().numpy().view(np.uint64)
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    gp.build()
+    gp.lib()
+
+
+def compare_layout(g, o):
+    lg, lo = host(g.layout()), o.layout()
+    assert lg.size == lo.size, (lg.size, lo.size)
+    bad = np.nonzero(lg != lo)[0]
+    assert bad.size == 0, f"layout differs at {bad.size} slots, first {bad[:8]}: gpu {lg[bad[:4]]} oracle {lo[bad[:4]]}"
+    assert g.check() == 0, f"device checker code {g.check()}"
+
+
+def compare_graph(g, o, srcs=(0,), pr_iters=20):
+    compare_layout(g, o)
+    assert np.array_equal(g.row_end().cpu().numpy().view(np.uint32), o.row_end())
+    assert np.array_equal(host(g.export_sorted()), o.export_sorted())
+    rp, col = g.export_csr()
+    orp, ocol = o.export_csr()
+    assert np.array_equal(rp.cpu().numpy().view(np.uint64), orp)
+    assert np.array_equal(col.cpu().numpy().view(np.uint32), ocol)
+    for s in srcs:
+        assert np.array_equal(g.bfs(s).cpu().numpy(), o.bfs(s))
+    assert np.array_equal(g.cc().cpu().numpy().view(np.uint32), o.cc())
+    pr = g.pagerank(pr_iters, 0.85).cpu().numpy().astype(np.float64)
+    ref = o.pagerank(pr_iters, 0.85)
+    rel = np.max(np.abs(pr - ref) / ref)
+    assert rel <= PR_TOL, rel
+
+
+def both_update(g, o, ins, dels):
+    st = g.update(dev(ins) if ins is not None else None, dev(dels) if dels is not None else None, stats=True)
+    rc, so = o.update(ins if ins is not None else [], dels if dels is not None else [])
+    assert rc == 0
+    for k in STAT_KEYS:
+        assert st[k] == so[k], (k, st[k], so[k])
+    return st
+
+
+# ---- the tiny configuration: ER 1,024 vertices, 8,192 edges, 16 slides of 256 --------------
+def test_er_1024_sliding_window():
+    V, E0, B = 1024, 8192, 256
+    stream = W.er_stream(V, E0 + 16 * B, seed=0)
+    win = W.SlidingWindow(stream, E0)
+    g = gp.Graph(V, leaf_size=64)
+    o = oracle.OraclePMA(V, L=64)
+    compare_graph(g, o)
+    both_update(g, o, win.initial, None)
+    compare_graph(g, o)
+    assert g.capacity == 16384
+    for b in range(16):
+        ins, dels = win.slide(B)
+        both_update(g, o, ins, dels)
+        compare_graph(g, o, srcs=(0, int(b * 61 % V)))
+        assert g.num_edges() == E0
+
+
+# ---- the paper's worked examples on the GPU ---------------------------------------------------
+@pytest.mark.parametrize("ex", ["ex3", "ex1"])
+def test_worked_examples_gpu(ex):
+    gd = read_golden("example_w.txt")
+    L = int(gd["L"])
+    init = parse_leaves(gd["initial"], L)
+    g = gp.Graph(0, leaf_size=L, raw_keys=True)
+    g.import_layout(dev(init))
+    assert np.array_equal(host(g.layout()), init)
+    st = g.update(dev(ints(gd[f"{ex}_insert"])), None, stats=True)
+    assert np.array_equal(host(g.layout()), parse_leaves(gd[f"{ex}_final"], L))
+    assert st["merges"][:4] == ints(gd[f"{ex}_merges_per_level"])
+    assert g.check() == 0
+
+
+# ---- randomized batches of every composition, several leaf sizes ------------------------------
+def random_batch(rng, V, live, n):
+    live_l = list(live)
+    ins = [(int(a) << 32) | int(b) for a, b in rng.integers(0, V, (n, 2))]
+    if live_l:
+        ins += [live_l[i] for i in rng.integers(0, len(live_l), n // 4)]
+    ins += ins[: n // 8]
+    dels = [live_l[i] for i in rng.integers(0, len(live_l), n)] if live_l else []
+    dels += [(int(a) << 32) | int(b) for a, b in rng.integers(0, V, (n // 4, 2))]
+    dels += ins[: n // 8]
+    return (rng.permutation(np.array(ins, np.uint64)) if ins else np.zeros(0, np.uint64),
+            rng.permutation(np.array(dels, np.uint64)) if dels else np.zeros(0, np.uint64))
+
+
+@pytest.mark.parametrize("V,L,seed", [(40, 4, 0), (200, 8, 1), (300, 32, 2), (1000, 64, 3), (3000, 128, 4),
+                                      (2000, 256, 5), (5000, 1024, 6), (700, 2, 7)])
+def test_random_batches(V, L, seed):
+    rng = np.random.default_rng(seed)
+    g = gp.Graph(V, leaf_size=L)
+    o = oracle.OraclePMA(V, L=L)
+    compare_layout(g, o)
+    live = set()
+    for it in range(24):
+        n = int(rng.integers(0, 3 * V if it % 5 else 10 * V))
+        ins, dels = random_batch(rng, V, live, n)
+        both_update(g, o, ins, dels)
+        live = apply_set_semantics(live, ins, dels)
+        compare_layout(g, o)
+    compare_graph(g, o, srcs=(0, V - 1))
+
+
+def test_raw_keys_random_layouts():
+    rng = np.random.default_rng(9)
+    for L in (4, 16, 64):
+        g = gp.Graph(0, leaf_size=L, raw_keys=True)
+        o = oracle.OraclePMA(0, L=L, raw_keys=True)
+        live = set()
+        for it in range(20):
+            k = rng.integers(0, 1 << 62, 400, dtype=np.int64).astype(np.uint64) % np.uint64(5000)
+            ins = k[:300]
+            dels = np.array(list(live)[: 100] if live else [], np.uint64)
+            both_update(g, o, ins, dels)
+            live = apply_set_semantics(live, ins, dels)
+            compare_layout(g, o)
+
+
+# ---- edge cases -------------------------------------------------------------------------------
+def test_edge_cases():
+    V, L = 500, 64
+    g = gp.Graph(V, leaf_size=L)
+    o = oracle.OraclePMA(V, L=L)
+    rng = np.random.default_rng(1)
+    base = W.er_stream(V, 4000, seed=3)
+    both_update(g, o, base, None)
+    compare_graph(g, o, srcs=(0, V - 1))
+    # empty batch
+    st = g.update(None, None, stats=True)
+    assert st["n_inserted"] == 0 and st["n_ignored"] == 0
+    # only deletes, with duplicates and absent keys
+    d = np.concatenate([base[:300], base[:50], W.make_keys(np.arange(10), np.arange(10) + 1)])
+    both_update(g, o, None, d)
+    compare_layout(g, o)
+    # insert and delete of the same keys cancel; re-inserting stored keys is ignored
+    both_update(g, o, base[300:400], base[300:400])
+    both_update(g, o, base[400:500], None)
+    compare_layout(g, o)
+    # keys at vertex 0 and V-1, self-loops
+    ek = W.make_keys(np.array([0, 0, V - 1, V - 1, 7]), np.array([V - 1, 0, 0, V - 1, 7]))
+    both_update(g, o, ek, None)
+    compare_graph(g, o, srcs=(0, V - 1, 7))
+    # one hot vertex: many inserts into one row (escalates far above its leaf)
+    hot = W.make_keys(np.full(V, 3), np.arange(V))
+    both_update(g, o, hot, None)
+    compare_graph(g, o, srcs=(3,))
+    # sorted and reverse-sorted batches
+    s2 = np.sort(W.er_stream(V, 3000, seed=11))
+    both_update(g, o, s2[:1500], None)
+    both_update(g, o, s2[1500:][::-1].copy(), s2[:700][::-1].copy())
+    compare_graph(g, o, srcs=(0, 100))
+    # a batch that forces the capacity to grow
+    cap0 = g.capacity
+    big = W.er_stream(V, 60000, seed=12)
+    st = both_update(g, o, big, None)
+    assert st["resized"] == 1 and g.capacity > cap0
+    compare_graph(g, o, srcs=(0,))
+    # delete everything but the guards
+    live = o.export_sorted()
+    both_update(g, o, None, rng.permutation(live))
+    compare_graph(g, o, srcs=(0,))
+    assert g.num_edges() == 0
+
+
+def test_invalid_keys_change_nothing():
+    V = 100
+    g = gp.Graph(V, leaf_size=8)
+    g.update(dev(W.er_stream(V, 500, seed=4)), None, stats=True)
+    before = host(g.layout())
+    for bad in ([V << 32 | 1], [1 << 32 | V], [(1 << 32) | 0xFFFFFFFF]):
+        with pytest.raises(gp.GpmaError) as e:
+            g.update(dev([(2 << 32) | 3] + bad), None, stats=True)
+        assert e.value.code == gp.GPMA_EINVAL
+        assert np.array_equal(host(g.layout()), before)
+    with pytest.raises(gp.GpmaError):
+        g.update(None, dev([(5 << 32) | 0xFFFFFFFF]), stats=True)
+    # without stats the error surfaces at the next status call and nothing is applied
+    g.update(dev([(2 << 32) | 3, V << 32]), None)
+    with pytest.raises(gp.GpmaError):
+        g.status()
+    g.status()  # cleared
+    assert np.array_equal(host(g.layout()), before)
+    assert g.check() == 0
+
+
+def test_async_batches_then_status():
+    V = 2048
+    stream = W.rmat_stream(11, 20000 + 20 * 500, seed=5)
+    win = W.SlidingWindow(stream, 20000)
+    g = gp.Graph(V, leaf_size=64)
+    o = oracle.OraclePMA(V, L=64)
+    g.update(dev(win.initial), None)
+    o.update(win.initial)
+    for _ in range(20):
+        ins, dels = win.slide(500)
+        g.update(dev(ins), dev(dels))
+        o.update(ins, dels)
+    g.status()
+    compare_graph(g, o, srcs=(int(W.split_keys(stream[:1])[0][0]),))
+
+
+def test_export_capacity_errors():
+    g = gp.Graph(50, leaf_size=8)
+    g.update(dev(W.er_stream(50, 300, seed=1)), None, stats=True)
+    small = torch.empty(10, dtype=torch.int64, device="cuda")
+    assert gp.gpma_export_sorted(g.h, small) == -301
+    assert gp.gpma_export_layout(g.h, small) < 0
+
+
+def test_import_rejects_bad_layouts():
+    g = gp.Graph(0, leaf_size=4, raw_keys=True)
+    good = parse_leaves(read_golden("example_w.txt")["initial"], 4)
+    g.import_layout(dev(good))
+    bad = good.copy()
+    bad[0], bad[4] = bad[4], bad[0]  # order broken
+    with pytest.raises(gp.GpmaError):
+        g.import_layout(dev(bad))
+    assert np.array_equal(host(g.layout()), good)
+    with pytest.raises(gp.GpmaError):
+        g.import_layout(dev(good[:12]))  # not L * 2^k
