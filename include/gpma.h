@@ -163,6 +163,36 @@ int gpma_capacity(gpma_t h, uint64_t *out);
  * 16 a count-tree node is stale, 32 the total count is stale.  Waits. */
 int gpma_check(gpma_t h, uint32_t *code, void *stream);
 
+/* ---- measurement ------------------------------------------------------------
+ * Optional per-phase timing.  While enabled, every call records a pair of CUDA
+ * events on its own stream around each phase below (one pair per PageRank push
+ * pass), so the times are device times of the work actually enqueued. */
+#define GPMA_PROF_SORT 0       /* validation, radix sort, unique/cancel, leaf search, runs */
+#define GPMA_PROF_LEAF 1       /* leaf pass (presence, deletes, level-0 merges) + count tree */
+#define GPMA_PROF_ESCALATE 2   /* pending inserts, merge levels, outer segment merges */
+#define GPMA_PROF_RESIZE 3     /* root resize */
+#define GPMA_PROF_PR_SCATTER 4 /* one PageRank push pass over the slots */
+#define GPMA_PROF_PAGERANK 5   /* one whole gpma_pagerank call */
+#define GPMA_PROF_BFS 6        /* one whole gpma_bfs call */
+#define GPMA_PROF_CC 7         /* one whole gpma_cc call */
+#define GPMA_PROF_N 8
+
+typedef struct {
+  double ms[GPMA_PROF_N];         /* summed device time */
+  uint64_t count[GPMA_PROF_N];    /* timed occurrences */
+  uint64_t launches[GPMA_PROF_N]; /* kernel launches inside those occurrences */
+} gpma_profile;
+
+/* Turn per-phase event recording on (on != 0) or off. */
+int gpma_profile_enable(gpma_t h, int on);
+
+/* Wait for the recorded events and sum them into *out; reset != 0 clears the
+ * accumulated record afterwards. */
+int gpma_profile_read(gpma_t h, gpma_profile *out, int reset);
+
+/* Number of kernels this library has launched in this process (all handles). */
+uint64_t gpma_launch_count(void);
+
 /* Static text for a status code. */
 const char *gpma_strerror(int status);
 

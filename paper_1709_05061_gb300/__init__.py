@@ -50,6 +50,17 @@ class gpma_stats(C.Structure):
         return d
 
 
+GPMA_PROF_NAMES = ("sort", "leaf", "escalate", "resize", "pr_scatter", "pagerank", "bfs", "cc")
+
+
+class gpma_profile(C.Structure):
+    _fields_ = [("ms", C.c_double * 8), ("count", C.c_uint64 * 8), ("launches", C.c_uint64 * 8)]
+
+    def as_dict(self) -> dict:
+        return {n: {"ms": self.ms[i], "count": self.count[i], "launches": self.launches[i]}
+                for i, n in enumerate(GPMA_PROF_NAMES)}
+
+
 def build(force: bool = False, verbose: bool = False) -> str:
     return _build_mod.build(force=force, verbose=verbose)
 
@@ -85,6 +96,9 @@ def lib():
             "gpma_capacity": ([vp, P(u64)], i),
             "gpma_check": ([vp, P(u32), vp], i),
             "gpma_strerror": ([i], C.c_char_p),
+            "gpma_profile_enable": ([vp, i], i),
+            "gpma_profile_read": ([vp, P(gpma_profile), i], i),
+            "gpma_launch_count": ([], u64),
         }
         for name, (args, res) in sig.items():
             f = getattr(l, name)
@@ -222,6 +236,20 @@ def gpma_check(h: int, stream=None) -> int:
 
 def gpma_strerror(code: int) -> str:
     return lib().gpma_strerror(code).decode()
+
+
+def gpma_profile_enable(h: int, on: bool = True):
+    _check(lib().gpma_profile_enable(C.c_void_p(h), 1 if on else 0), "gpma_profile_enable")
+
+
+def gpma_profile_read(h: int, reset: bool = True) -> dict:
+    p = gpma_profile()
+    _check(lib().gpma_profile_read(C.c_void_p(h), C.byref(p), 1 if reset else 0), "gpma_profile_read")
+    return p.as_dict()
+
+
+def gpma_launch_count() -> int:
+    return int(lib().gpma_launch_count())
 
 
 # ---- convenience object over the same calls -------------------------------------------------

@@ -1,13 +1,24 @@
 // gpma_api.cu -- the C ABI of include/gpma.h: handle, memory, and the order in
 // which one batch's kernels are enqueued.
+#include <atomic>
 #include <cstdio>
 #include <cstring>
 #include <new>
+#include <vector>
 
 #include "gpma.h"
 #include "gpma_launch.h"
 
 using namespace gpk;
+
+namespace {
+std::atomic<uint64_t> g_launches{0};
+}  // namespace
+
+namespace gpk {
+void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+uint64_t launch_count() { return g_launches.load(std::memory_order_relaxed); }
+}  // namespace gpk
 
 namespace {
 
@@ -42,6 +53,64 @@ uint32_t bits_for(uint64_t x) {
 
 }  // namespace
 
+// event pairs recorded around phases while profiling is on
+struct Prof {
+  bool on = false;
+  struct Pair {
+    cudaEvent_t a, b;
+    int phase;
+    uint64_t launches;
+  };
+  std::vector<Pair> pairs;
+  std::vector<cudaEvent_t> pool;
+  double ms[GPMA_PROF_N] = {};
+  uint64_t count[GPMA_PROF_N] = {};
+  uint64_t launches[GPMA_PROF_N] = {};
+  cudaEvent_t get() {
+    if (!pool.empty()) {
+      cudaEvent_t e = pool.back();
+      pool.pop_back();
+      return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+  }
+  ~Prof() {
+    for (auto &p : pairs) {
+      cudaEventDestroy(p.a);
+      cudaEventDestroy(p.b);
+    }
+    for (auto e : pool) cudaEventDestroy(e);
+  }
+};
+
+// brackets one phase of one call with events on the call's stream
+struct Phase {
+  Prof *p;
+  int phase;
+  cudaStream_t s;
+  cudaEvent_t a = nullptr;
+  uint64_t l0 = 0;
+  bool open = false;
+  Phase(Prof *p_, int ph, cudaStream_t s_) : p(p_), phase(ph), s(s_) {
+    if (p && p->on) {
+      a = p->get();
+      cudaEventRecord(a, s);
+      l0 = gpk::launch_count();
+      open = true;
+    }
+  }
+  void end() {
+    if (!open) return;
+    cudaEvent_t b = p->get();
+    cudaEventRecord(b, s);
+    p->pairs.push_back({a, b, phase, gpk::launch_count() - l0});
+    open = false;
+  }
+  ~Phase() { end(); }
+};
+
 struct gpma {
   uint32_t V, L, logL, raw;
   uint32_t tau0, tauh, rho0, rhoh;
@@ -75,6 +144,7 @@ struct gpma {
   uint64_t count_ub;
   int poisoned;
   int host_sticky;
+  Prof *prof;
 };
 
 namespace {
@@ -336,9 +406,16 @@ int update(gpma *h, const uint64_t *ins, uint64_t n_ins, const uint64_t *del, ui
   f.uleaf = h->w.uleaf;
   f.run_start = h->w.run_start;
   const uint32_t n32 = (uint32_t)n;
-  launch_front(f, s);
-  launch_leaf_pass(h->geo, h->ctl, h->w, n32, s);
-  launch_propagate(h->geo, h->ctl, h->w, n32, s);
+  {
+    Phase ph(h->prof, GPMA_PROF_SORT, s);
+    launch_front(f, s);
+  }
+  {
+    Phase ph(h->prof, GPMA_PROF_LEAF, s);
+    launch_leaf_pass(h->geo, h->ctl, h->w, n32, s);
+    launch_propagate(h->geo, h->ctl, h->w, n32, s);
+  }
+  Phase esc(h->prof, GPMA_PROF_ESCALATE, s);
   launch_pending(h->geo, h->ctl, h->w, n32, s);
   // the root can only refuse inserts when the count might exceed its bound
   const bool may_fail = h->count_ub + n_ins > h->geo.maxc[h->geo.h];
@@ -349,6 +426,7 @@ int update(gpma *h, const uint64_t *ins, uint64_t n_ins, const uint64_t *del, ui
   if (may_fail) {
     if ((rc = read_ctl(h, s))) return rc;
     if (h->h_ctl->err) {
+      note_launch();
       k_finish<<<1, 1, 0, s>>>(h->ctl);
       int st = err_to_status(h->h_ctl->err);
       if (st != GPMA_EINVAL) poison(h, st);
@@ -356,6 +434,8 @@ int update(gpma *h, const uint64_t *ins, uint64_t n_ins, const uint64_t *del, ui
     }
     h->count_ub = h->h_ctl->total;
     if (h->h_ctl->nfail) {
+      esc.end();
+      Phase ph(h->prof, GPMA_PROF_RESIZE, s);
       launch_unmark(h->geo, h->ctl, h->w, n32, s);
       if ((rc = do_resize(h, h->h_ctl->total, s))) return rc;
       resized = true;
@@ -370,6 +450,7 @@ int update(gpma *h, const uint64_t *ins, uint64_t n_ins, const uint64_t *del, ui
                          h->partials, false, s);
     if (stats) launch_stats(h->geo, h->ctl, h->w, n32, s);
   }
+  note_launch();
   k_finish<<<1, 1, 0, s>>>(h->ctl);
   if ((rc = cuda_ok(h))) return rc;
   if (!stats) return GPMA_OK;
@@ -461,6 +542,11 @@ int gpma_create(uint32_t n_vertices, const gpma_params *params, const gpma_alloc
   gpma *h = new (std::nothrow) gpma;
   if (!h) return GPMA_ENOMEM;
   memset(h, 0, sizeof(gpma));
+  h->prof = new (std::nothrow) Prof;
+  if (!h->prof) {
+    delete h;
+    return GPMA_ENOMEM;
+  }
   h->V = raw ? 0 : n_vertices;
   h->L = L;
   h->logL = bits_for(L) - 1;
@@ -491,6 +577,8 @@ int gpma_create(uint32_t n_vertices, const gpma_params *params, const gpma_alloc
   if (!raw) {
     if (!dalloc(h, &h->guards, h->V, s)) rc = GPMA_ENOMEM;
     if (!rc) {
+      note_launch();
+      note_launch();
       k_make_guards<<<(h->V + 255) / 256 < 4096 ? (h->V + 255) / 256 : 4096, 256, 0, s>>>(h->guards, h->V);
       gpma_stats st;
       rc = update(h, h->guards, h->V, nullptr, 0, s, &st, true);
@@ -520,6 +608,7 @@ int gpma_destroy(gpma_t h) {
   cudaStreamSynchronize(s);
   if (h->h_ctl) cudaFreeHost(h->h_ctl);
   if (h->h_counter) cudaFreeHost(h->h_counter);
+  delete h->prof;
   cudaGetLastError();
   delete h;
   return GPMA_OK;
@@ -550,6 +639,7 @@ int gpma_bfs(gpma_t h, uint32_t src, int32_t *d_depth, void *stream) {
   if (h->poisoned) return h->poisoned;
   cudaStream_t s = (cudaStream_t)stream;
   if (ensure_analytics(h, 1, s)) return GPMA_ENOMEM;
+  Phase ph(h->prof, GPMA_PROF_BFS, s);
   if (run_bfs(h->geo, src, d_depth, h->q0, h->q1, h->counter, h->h_counter, s) < 0) return poison(h, GPMA_EDEVICE);
   return cuda_ok(h);
 }
@@ -557,6 +647,7 @@ int gpma_bfs(gpma_t h, uint32_t src, int32_t *d_depth, void *stream) {
 int gpma_cc(gpma_t h, uint32_t *d_label, void *stream) {
   if (!h || !d_label || h->raw) return GPMA_EINVAL;
   if (h->poisoned) return h->poisoned;
+  Phase ph(h->prof, GPMA_PROF_CC, (cudaStream_t)stream);
   launch_cc(h->geo, d_label, (cudaStream_t)stream);
   return cuda_ok(h);
 }
@@ -566,7 +657,16 @@ int gpma_pagerank(gpma_t h, uint32_t iters, float damping, float *d_rank, void *
   if (h->poisoned) return h->poisoned;
   cudaStream_t s = (cudaStream_t)stream;
   if (ensure_analytics(h, iters, s)) return GPMA_ENOMEM;
-  launch_pagerank(h->geo, iters, damping, d_rank, h->deg, h->y, h->contrib, h->dsum, s);
+  Phase all(h->prof, GPMA_PROF_PAGERANK, s);
+  launch_pr_setup(h->geo, iters, d_rank, h->deg, h->y, h->contrib, h->dsum, s);
+  for (uint32_t it = 0; it < iters; it++) {
+    {
+      Phase ph(h->prof, GPMA_PROF_PR_SCATTER, s);
+      launch_pr_scatter(h->geo, h->contrib, h->y, s);
+    }
+    launch_pr_apply(h->geo, damping, d_rank, h->deg, h->y, h->contrib, h->dsum + it, h->dsum + it + 1, s);
+  }
+  all.end();
   return cuda_ok(h);
 }
 
@@ -696,5 +796,42 @@ int gpma_check(gpma_t h, uint32_t *code, void *stream) {
   *code = buf[0];
   return cuda_ok(h);
 }
+
+int gpma_profile_enable(gpma_t h, int on) {
+  if (!h) return GPMA_EINVAL;
+  h->prof->on = on != 0;
+  return GPMA_OK;
+}
+
+int gpma_profile_read(gpma_t h, gpma_profile *out, int reset) {
+  if (!h || !out) return GPMA_EINVAL;
+  Prof &p = *h->prof;
+  for (auto &pr : p.pairs) {
+    if (cudaEventSynchronize(pr.b) != cudaSuccess) return poison(h, GPMA_EDEVICE);
+    float ms = 0.0f;
+    cudaEventElapsedTime(&ms, pr.a, pr.b);
+    p.ms[pr.phase] += ms;
+    p.count[pr.phase] += 1;
+    p.launches[pr.phase] += pr.launches;
+    p.pool.push_back(pr.a);
+    p.pool.push_back(pr.b);
+  }
+  p.pairs.clear();
+  for (int i = 0; i < GPMA_PROF_N; i++) {
+    out->ms[i] = p.ms[i];
+    out->count[i] = p.count[i];
+    out->launches[i] = p.launches[i];
+  }
+  if (reset) {
+    for (int i = 0; i < GPMA_PROF_N; i++) {
+      p.ms[i] = 0;
+      p.count[i] = 0;
+      p.launches[i] = 0;
+    }
+  }
+  return cuda_ok(h);
+}
+
+uint64_t gpma_launch_count(void) { return gpk::launch_count(); }
 
 }  // extern "C"

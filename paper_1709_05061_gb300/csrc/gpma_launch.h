@@ -7,6 +7,10 @@
 
 namespace gpk {
 
+// process-wide count of kernel launches issued by the library
+void note_launch();
+uint64_t launch_count();
+
 // ticket / look-back epoch slots of one batch (Ctl::ticket, Ctl::epoch + slot)
 constexpr uint32_t kSlotKeep = 8, kSlotRuns = 9, kSlotPend = 10, kSlotERuns = 11, kSlotSegs = 12,
                    kSlotMisc = 13, kSlotsPerBatch = 16;
@@ -92,8 +96,12 @@ void launch_scan_u32_u64(const uint32_t *in, uint64_t *out, uint64_t n_bound, ui
                          const uint32_t *n_dev = nullptr);
 
 // k_analytics.cu
-void launch_pagerank(const Geo &g, uint32_t iters, float damping, float *rank, uint32_t *deg, double *y,
-                     float *contrib, double *dsum, cudaStream_t s);
+// PageRank: degrees + x0 (setup), then per iteration one push pass and one apply
+void launch_pr_setup(const Geo &g, uint32_t iters, float *rank, uint32_t *deg, double *y, float *contrib,
+                     double *dsum, cudaStream_t s);
+void launch_pr_scatter(const Geo &g, const float *contrib, double *y, cudaStream_t s);
+void launch_pr_apply(const Geo &g, float damping, float *rank, const uint32_t *deg, double *y, float *contrib,
+                     const double *dsum_in, double *dsum_out, cudaStream_t s);
 int run_bfs(const Geo &g, uint32_t src, int32_t *depth, uint32_t *q0, uint32_t *q1, uint32_t *counter,
             uint32_t *h_counter, cudaStream_t s);
 void launch_cc(const Geo &g, uint32_t *label, cudaStream_t s);

@@ -86,17 +86,23 @@ __global__ void k_pr_apply(uint32_t V, float damping, const uint32_t *__restrict
   block_add_double(dang, dsum_out);
 }
 
-void launch_pagerank(const Geo &g, uint32_t iters, float damping, float *rank, uint32_t *deg, double *y,
-                     float *contrib, double *dsum, cudaStream_t s) {
+void launch_pr_setup(const Geo &g, uint32_t iters, float *rank, uint32_t *deg, double *y, float *contrib,
+                     double *dsum, cudaStream_t s) {
   launch_degrees(g, deg, s);
   cudaMemsetAsync(dsum, 0, sizeof(double) * (iters + 1), s);
-  const uint32_t vb = nb(g.V, 256, 152 * 8);
-  k_pr_init<<<vb, 256, 0, s>>>(g.V, deg, rank, contrib, y, dsum);
-  const uint32_t sb = nb(g.C >> 1, 256, 152 * 16);
-  for (uint32_t it = 0; it < iters; it++) {
-    k_pr_scatter<<<sb, 256, 0, s>>>(g, contrib, y);
-    k_pr_apply<<<vb, 256, 0, s>>>(g.V, damping, deg, y, rank, contrib, dsum + it, dsum + it + 1);
-  }
+  note_launch();
+  k_pr_init<<<nb(g.V, 256, 152 * 8), 256, 0, s>>>(g.V, deg, rank, contrib, y, dsum);
+}
+
+void launch_pr_scatter(const Geo &g, const float *contrib, double *y, cudaStream_t s) {
+  note_launch();
+  k_pr_scatter<<<nb(g.C >> 1, 256, 152 * 16), 256, 0, s>>>(g, contrib, y);
+}
+
+void launch_pr_apply(const Geo &g, float damping, float *rank, const uint32_t *deg, double *y, float *contrib,
+                     const double *dsum_in, double *dsum_out, cudaStream_t s) {
+  note_launch();
+  k_pr_apply<<<nb(g.V, 256, 152 * 8), 256, 0, s>>>(g.V, damping, deg, y, rank, contrib, dsum_in, dsum_out);
 }
 
 // ---- BFS ----------------------------------------------------------------------------------------
@@ -142,6 +148,7 @@ __global__ void __launch_bounds__(256) k_bfs_expand(Geo g, int32_t *__restrict__
 int run_bfs(const Geo &g, uint32_t src, int32_t *depth, uint32_t *q0, uint32_t *q1, uint32_t *counter,
             uint32_t *h_counter, cudaStream_t s) {
   cudaMemsetAsync(depth, 0xFF, sizeof(int32_t) * g.V, s);
+  note_launch();
   k_bfs_init<<<1, 1, 0, s>>>(depth, src, q0, counter);
   uint32_t nfront = 1;
   int32_t level = 0;
@@ -149,6 +156,7 @@ int run_bfs(const Geo &g, uint32_t src, int32_t *depth, uint32_t *q0, uint32_t *
   uint32_t *cin = counter, *cout = counter + 1;
   while (nfront) {
     cudaMemsetAsync(cout, 0, sizeof(uint32_t), s);
+    note_launch();
     k_bfs_expand<<<nb(nfront, 8, 152 * 16), 256, 0, s>>>(g, depth, qin, cin, qout, cout, level);
     cudaMemcpyAsync(h_counter, cout, sizeof(uint32_t), cudaMemcpyDeviceToHost, s);
     if (cudaStreamSynchronize(s) != cudaSuccess) return -1;
@@ -207,8 +215,11 @@ __global__ void k_cc_compress(uint32_t *label, uint32_t V) {
 
 void launch_cc(const Geo &g, uint32_t *label, cudaStream_t s) {
   const uint32_t vb = nb(g.V, 256, 152 * 8);
+  note_launch();
   k_cc_init<<<vb, 256, 0, s>>>(label, g.V);
+  note_launch();
   k_cc_hook<<<nb(g.C, 256, 152 * 16), 256, 0, s>>>(g, label);
+  note_launch();
   k_cc_compress<<<vb, 256, 0, s>>>(label, g.V);
 }
 

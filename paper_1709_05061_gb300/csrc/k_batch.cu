@@ -232,18 +232,23 @@ uint32_t comp_tiles(uint64_t n) { return (uint32_t)((n + kScanTile - 1) / kScanT
 void launch_front(const FrontArgs &f, cudaStream_t s) {
   const PrepArgs &a = f.prep;
   const uint64_t n = (uint64_t)a.n_ins + a.n_del;
+  note_launch();
   k_init_batch<<<1, 256, 0, s>>>(f.ctl, f.hist, a.npass * 256u, (uint32_t)n);
+  note_launch();
   k_prep<<<grid_for(n, 256, 4 * 152), 256, 0, s>>>(a, f.ins, f.del, f.bufA, f.hist, f.ctl);
   uint64_t *src = f.bufA, *dst = f.bufB;
   const uint32_t st = sort_tiles(n);
   for (uint32_t p = 0; p < a.npass; p++) {
+    note_launch();
     k_sort_pass<<<st, kSortThreads, 0, s>>>(src, dst, f.hist, f.status, f.ctl, p, p * a.dbits, a.dbits);
     uint64_t *t = src; src = dst; dst = t;
   }
   // look-back epochs: pass p uses epoch + p, then the fixed slots of gpma_launch.h
   const uint32_t ct = comp_tiles(n);
+  note_launch();
   k_keep<<<ct, kScanThreads, 0, s>>>(a, src, f.geo->F, f.geo->nleaves, f.ukey, f.utag, f.uleaf, f.status,
                                      f.ctl);
+  note_launch();
   k_runs<<<ct, kScanThreads, 0, s>>>(f.uleaf, f.run_start, f.status, f.ctl);
 }
 

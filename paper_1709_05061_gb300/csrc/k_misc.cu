@@ -110,8 +110,11 @@ void launch_scan_u32_u64(const uint32_t *in, uint64_t *out, uint64_t n_bound, ui
                          const uint32_t *n_dev) {
   const uint32_t nb = (uint32_t)((n_bound + kTile - 1) / kTile);
   const uint32_t g = nb ? nb : 1;
+  note_launch();
   k_scan_reduce<<<g, 256, 0, s>>>(in, n_bound, n_dev, partials);
+  note_launch();
   k_scan_partials<<<1, 1024, 0, s>>>(partials, n_bound, n_dev, out);
+  note_launch();
   k_scan_down<<<g, 256, 0, s>>>(in, out, n_bound, n_dev, partials);
 }
 
@@ -159,10 +162,14 @@ __global__ void k_tree_level(Geo g, uint32_t i) {
 __global__ void k_zero_total(Ctl *ctl) { ctl->total = 0; }
 
 void launch_rebuild_indexes(const Geo &g, Ctl *ctl, cudaStream_t s) {
+  note_launch();
   k_zero_total<<<1, 1, 0, s>>>(ctl);
+  note_launch();
   k_leaf_index<<<nblocks(g.nleaves, 8, 152 * 16), 256, 0, s>>>(g, ctl);
-  for (uint32_t i = 1; i <= g.h; i++)
+  for (uint32_t i = 1; i <= g.h; i++) {
+    note_launch();
     k_tree_level<<<nblocks(g.nleaves >> i, 256, 152 * 8), 256, 0, s>>>(g, i);
+  }
 }
 
 // ---- consistency checker -----------------------------------------------------------------------
@@ -241,9 +248,15 @@ void launch_check(const Geo &g, Ctl *ctl, uint32_t *code, cudaStream_t s) {
   // code[0] = bits, code[1..2] = scratch sum (u64)
   cudaMemsetAsync(code, 0, 16, s);
   unsigned long long *sum = (unsigned long long *)(code + 2);
+  note_launch();
   k_check_leaves<<<nblocks(g.nleaves, 8, 152 * 16), 256, 0, s>>>(g, code, sum);
+  note_launch();
   k_check_tree<<<nblocks(g.nleaves / 2, 256, 152 * 8), 256, 0, s>>>(g, code);
-  if (!g.raw) k_check_guards<<<nblocks(g.V, 256, 152 * 8), 256, 0, s>>>(g, code);
+  if (!g.raw) {
+    note_launch();
+    k_check_guards<<<nblocks(g.V, 256, 152 * 8), 256, 0, s>>>(g, code);
+  }
+  note_launch();
   k_check_total<<<1, 1, 0, s>>>(ctl, code, sum);
 }
 
@@ -280,7 +293,9 @@ __global__ void k_export_prep(Ctl *ctl) {
 
 void launch_export(const Geo &g, Ctl *ctl, uint64_t *out_keys, uint32_t *out_cols, uint64_t cap, uint64_t *status,
                    cudaStream_t s) {
+  note_launch();
   k_export_prep<<<1, 1, 0, s>>>(ctl);
+  note_launch();
   k_export<<<comp_tiles(g.C), kScanThreads, 0, s>>>(g, ctl, out_keys, out_cols, cap, status);
 }
 
@@ -298,6 +313,7 @@ __global__ void k_degrees(Geo g, uint32_t *deg) {
 
 void launch_degrees(const Geo &g, uint32_t *deg, cudaStream_t s) {
   cudaMemsetAsync(deg, 0, sizeof(uint32_t) * g.V, s);
+  note_launch();
   k_degrees<<<nblocks(g.C, 256, 152 * 16), 256, 0, s>>>(g, deg);
 }
 

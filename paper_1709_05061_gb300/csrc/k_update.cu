@@ -585,38 +585,47 @@ static void allow_big_smem() {
 void launch_leaf_pass(const Geo &g, Ctl *ctl, const Work &w, uint32_t n, cudaStream_t s) {
   allow_big_smem();
   const uint32_t pw = leaf_smem_bytes(g.L), wpb = warps_per_block(g.L);
+  note_launch();
   k_leaf_pass<<<blocks_for(n, wpb, 152 * 16), wpb * 32, wpb * pw, s>>>(g, ctl, w, pw);
 }
 
 void launch_propagate(const Geo &g, Ctl *ctl, const Work &w, uint32_t n, cudaStream_t s) {
+  note_launch();
   k_propagate<<<blocks_for(n, 1024, 152 * 2), 1024, 0, s>>>(g, ctl, w.rleaf, w.rdelta);
 }
 
 void launch_pending(const Geo &g, Ctl *ctl, const Work &w, uint32_t n, cudaStream_t s) {
   (void)g;
   const uint32_t ct = comp_tiles(n);
+  note_launch();
   k_pending<<<ct, kScanThreads, 0, s>>>(ctl, w);
+  note_launch();
   k_eruns<<<ct, kScanThreads, 0, s>>>(ctl, w);
 }
 
 void launch_esc_level(const Geo &g, Ctl *ctl, const Work &w, uint32_t n, bool may_fail, cudaStream_t s) {
+  note_launch();
   k_esc_level<<<blocks_for(n, 256, 152 * 8), 256, 0, s>>>(g, ctl, w, may_fail ? 1 : 0);
 }
 
 void launch_esc_top(const Geo &g, Ctl *ctl, const Work &w, uint32_t n, cudaStream_t s) {
+  note_launch();
   k_esc_top<<<blocks_for(n, 256, 152 * 8), 256, 0, s>>>(g, ctl, w);
 }
 
 void launch_unmark(const Geo &g, Ctl *ctl, const Work &w, uint32_t n, cudaStream_t s) {
+  note_launch();
   k_unmark<<<blocks_for(n, 256, 152 * 8), 256, 0, s>>>(g, ctl, w);
 }
 
 void launch_segments(const Geo &g, Ctl *ctl, const Work &w, uint32_t n, cudaStream_t s) {
+  note_launch();
   k_segs<<<comp_tiles(n), kScanThreads, 0, s>>>(g, ctl, w);
 }
 
 void launch_stats(const Geo &g, Ctl *ctl, const Work &w, uint32_t n, cudaStream_t s) {
   (void)g;
+  note_launch();
   k_stats<<<blocks_for(n, 256, 152 * 8), 256, 0, s>>>(ctl, w);
 }
 
@@ -635,14 +644,18 @@ void launch_segment_merge(const Geo &src, const Geo &dst, Ctl *ctl, const Work &
   if (whole) {
     cnt_in = src.cnt;
   } else {
+    note_launch();
     k_seg_vcnt<<<blocks_for(nleafw_bound, 256, 152 * 8), 256, 0, s>>>(src, ctl, w, vcnt);
   }
   launch_scan_u32_u64(cnt_in, voff, whole ? src.nleaves : nleafw_bound, partials, s,
                       whole ? nullptr : &ctl->nleafw);
+  note_launch();
   k_seg_gather<<<blocks_for(nleafw_bound, 8, 152 * 16), 256, 0, s>>>(src, ctl, w, sa, voff, scratch, scratch_cap);
   const uint32_t pw = leaf_smem_bytes(dst.L), wpb = warps_per_block(dst.L);
   const uint64_t dst_bound = whole ? dst.nleaves : nleafw_bound;
+  note_launch();
   k_seg_write<<<blocks_for(dst_bound, wpb, 152 * 16), wpb * 32, wpb * pw, s>>>(dst, ctl, w, sa, voff, scratch, pw);
+  note_launch();
   k_seg_tree<<<blocks_for(dst_bound, 256, 152 * 8), 256, 0, s>>>(dst, ctl, w, sa, voff);
 }
 

@@ -41,12 +41,16 @@ def _unique_in_order(keys: np.ndarray) -> np.ndarray:
 
 
 def _grow(sampler, need: int, rng, chunk: int) -> np.ndarray:
-    """Draw chunks until ``need`` distinct edges exist; stream order is preserved."""
+    """Draw chunks until ``need`` distinct edges exist; stream order is preserved.
+    Each top-up draw is sized from the distinct-edge yield of the previous one."""
     out = np.empty(0, np.uint64)
     while out.size < need:
         cand = sampler(rng, chunk)
+        before = out.size
         out = _unique_in_order(np.concatenate([out, cand]))
-        chunk = max(chunk // 2, 1 << 16)
+        gained = out.size - before
+        rate = max(gained / max(chunk, 1), 1e-3)
+        chunk = int(min(max((need - out.size) / rate * 1.1, 1 << 16), 1 << 27))
     return out[:need]
 
 

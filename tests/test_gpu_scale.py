@@ -1,0 +1,63 @@
+"""Parity at full size: the R-MAT scale-20 sliding window that bench.py times
+(2^20 vertices, 16,000,000-edge window, leaf size 64), bulk load plus batches of
+10^2, 10^4 and 10^6 updates, through the same library calls as the benchmark.
+The oracle computes the whole array, so the layout is compared slot for slot
+(33.5M slots); BFS, CC and PageRank are compared in full."""
+import numpy as np
+import pytest
+
+import oracle
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+import paper_1709_05061_gb300 as gp  # noqa: E402
+from paper_1709_05061_gb300 import workloads as W  # noqa: E402
+
+STATS = ("n_inserted", "n_deleted", "n_ignored", "levels_climbed", "resized", "alg_bytes", "touched_leaves",
+         "covered_leaves", "merges")
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a).view(np.int64)).cuda()
+
+
+def test_rmat20_window_full_size():
+    gp.build()
+    scale, window = 20, 16_000_000
+    batches = (100, 10_000, 1_000_000)
+    stream = W.rmat_stream(scale, window + sum(b // 2 for b in batches), seed=1, samples=1 << 24)
+    win = W.SlidingWindow(stream, window)
+    V = 1 << scale
+    g = gp.Graph(V, leaf_size=64)
+    o = oracle.OraclePMA(V, L=64)
+
+    def step(ins, dels):
+        st = g.update(dev(ins), dev(dels) if dels is not None else None, stats=True)
+        rc, so = o.update(ins, dels if dels is not None else [])
+        assert rc == 0
+        for k in STATS:
+            assert st[k] == so[k], (k, st[k], so[k])
+        lg = g.layout().cpu().numpy().view(np.uint64)
+        lo = o.layout()
+        assert lg.size == lo.size
+        bad = np.count_nonzero(lg != lo)
+        assert bad == 0, f"{bad} slots differ"
+        assert g.check() == 0
+
+    step(win.initial, None)
+    assert g.capacity == 1 << 25
+    for b in batches:
+        ins, dels = win.slide(b // 2)
+        step(ins, dels)
+    src = int(stream[0] >> np.uint64(32))
+    assert np.array_equal(g.bfs(src).cpu().numpy(), o.bfs(src))
+    assert np.array_equal(g.cc().cpu().numpy().view(np.uint32), o.cc())
+    pr = g.pagerank(20, 0.85).cpu().numpy().astype(np.float64)
+    ref = o.pagerank(20, 0.85)
+    rel = np.max(np.abs(pr - ref) / ref)
+    assert rel <= 1e-5, rel
+    assert np.array_equal(g.row_end().cpu().numpy().view(np.uint32), o.row_end())
