@@ -139,6 +139,8 @@ struct gpma {
   double *dsum;
   uint32_t dsum_cap;
   uint32_t *q0, *q1, *counter, *h_counter;
+  double *pr_partials;
+  unsigned *pr_counter;
   uint32_t *check_buf;
   uint64_t *guards;
   uint64_t count_ub;
@@ -488,7 +490,8 @@ int update(gpma *h, const uint64_t *ins, uint64_t n_ins, const uint64_t *del, ui
 int ensure_analytics(gpma *h, uint32_t iters, cudaStream_t s) {
   if (!h->deg) {
     if (!dalloc(h, &h->deg, h->V, s) || !dalloc(h, &h->y, h->V, s) || !dalloc(h, &h->contrib, h->V, s) ||
-        !dalloc(h, &h->q0, h->V, s) || !dalloc(h, &h->q1, h->V, s) || !dalloc(h, &h->counter, 4, s))
+        !dalloc(h, &h->q0, h->V, s) || !dalloc(h, &h->q1, h->V, s) || !dalloc(h, &h->counter, 4, s) ||
+        !dalloc(h, &h->pr_partials, 152 * 8, s) || !dalloc(h, &h->pr_counter, 4, s))
       return GPMA_ENOMEM;
   }
   if (iters + 1 > h->dsum_cap) {
@@ -603,7 +606,8 @@ int gpma_destroy(gpma_t h) {
   dfree(h, h->geo.row_end, s);
   free_work(h, s);
   void *ptrs[] = {h->ctl, h->hist, h->scratch, h->vbuf, h->partials, h->deg, h->y, h->contrib,
-                  h->dsum, h->q0,  h->q1,      h->counter, h->check_buf, h->guards};
+                  h->dsum, h->q0,  h->q1,      h->counter, h->check_buf, h->guards, h->pr_partials,
+                  h->pr_counter};
   for (void *p : ptrs) dfree(h, p, s);
   cudaStreamSynchronize(s);
   if (h->h_ctl) cudaFreeHost(h->h_ctl);
@@ -658,13 +662,14 @@ int gpma_pagerank(gpma_t h, uint32_t iters, float damping, float *d_rank, void *
   cudaStream_t s = (cudaStream_t)stream;
   if (ensure_analytics(h, iters, s)) return GPMA_ENOMEM;
   Phase all(h->prof, GPMA_PROF_PAGERANK, s);
-  launch_pr_setup(h->geo, iters, d_rank, h->deg, h->y, h->contrib, h->dsum, s);
+  launch_pr_setup(h->geo, iters, d_rank, h->deg, h->y, h->contrib, h->dsum, h->pr_partials, h->pr_counter, s);
   for (uint32_t it = 0; it < iters; it++) {
     {
       Phase ph(h->prof, GPMA_PROF_PR_SCATTER, s);
       launch_pr_scatter(h->geo, h->contrib, h->y, s);
     }
-    launch_pr_apply(h->geo, damping, d_rank, h->deg, h->y, h->contrib, h->dsum + it, h->dsum + it + 1, s);
+    launch_pr_apply(h->geo, damping, d_rank, h->deg, h->y, h->contrib, h->dsum + it, h->dsum + it + 1,
+                    h->pr_partials, h->pr_counter, s);
   }
   all.end();
   return cuda_ok(h);

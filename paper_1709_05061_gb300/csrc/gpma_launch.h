@@ -97,11 +97,13 @@ void launch_scan_u32_u64(const uint32_t *in, uint64_t *out, uint64_t n_bound, ui
 
 // k_analytics.cu
 // PageRank: degrees + x0 (setup), then per iteration one push pass and one apply
+// partials: >= 152 * 4 doubles; counter: one unsigned (zeroed by setup, re-zeroed by each sum)
 void launch_pr_setup(const Geo &g, uint32_t iters, float *rank, uint32_t *deg, double *y, float *contrib,
-                     double *dsum, cudaStream_t s);
+                     double *dsum, double *partials, unsigned *counter, cudaStream_t s);
 void launch_pr_scatter(const Geo &g, const float *contrib, double *y, cudaStream_t s);
 void launch_pr_apply(const Geo &g, float damping, float *rank, const uint32_t *deg, double *y, float *contrib,
-                     const double *dsum_in, double *dsum_out, cudaStream_t s);
+                     const double *dsum_in, double *dsum_out, double *partials, unsigned *counter,
+                     cudaStream_t s);
 int run_bfs(const Geo &g, uint32_t src, int32_t *depth, uint32_t *q0, uint32_t *q1, uint32_t *counter,
             uint32_t *h_counter, cudaStream_t s);
 void launch_cc(const Geo &g, uint32_t *label, cudaStream_t s);
