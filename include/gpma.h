@@ -132,6 +132,19 @@ int gpma_pagerank(gpma_t h, uint32_t iters, float damping, float *d_rank, void *
  * small.  Waits for the stream. */
 int gpma_export_sorted(gpma_t h, uint64_t *d_out, uint64_t cap, uint64_t *n_out, void *stream);
 
+/* Same result as gpma_export_sorted, but the call allocates no device memory:
+ * the paper has no counterpart.  It is meant for callers that must not allocate
+ * while they query the graph, for instance a serving loop that has handed all
+ * free device memory to its own pool, or latency-bound code that cannot accept
+ * the synchronisation an allocation may bring.  The scratch words of its
+ * single-pass compaction live in one fixed array inside the library (1 MiB per
+ * GPU, kept until the process exits), so the array may hold at most 2^27 slots
+ * (GPMA_EINVAL otherwise).  The first call on each device looks up that array's
+ * device address; make that first call before any stream capture.  All calls
+ * share the array: calls that overlap on the GPU (other streams, other handles)
+ * race and must not be issued.  Waits for the stream. */
+int gpma_export_sorted_noalloc(gpma_t h, uint64_t *d_out, uint64_t cap, uint64_t *n_out, void *stream);
+
 /* CSR view (Sec. 4.2, Fig. 5): d_rowptr[V+1] row offsets, d_col[cap] column ids
  * (dst).  *n_out = number of edges; GPMA_ECAP if cap is too small.  Waits. */
 int gpma_export_csr(gpma_t h, uint64_t *d_rowptr, uint32_t *d_col, uint64_t cap,

@@ -88,6 +88,7 @@ def lib():
             "gpma_cc": ([vp, vp, vp], i),
             "gpma_pagerank": ([vp, u32, C.c_float, vp, vp], i),
             "gpma_export_sorted": ([vp, vp, u64, P(u64), vp], i),
+            "gpma_export_sorted_noalloc": ([vp, vp, u64, P(u64), vp], i),
             "gpma_export_csr": ([vp, vp, vp, u64, P(u64), vp], i),
             "gpma_export_layout": ([vp, vp, u64, P(u64), vp], i),
             "gpma_import_layout": ([vp, vp, u64, vp], i),
@@ -185,6 +186,15 @@ def gpma_export_sorted(h: int, out, stream=None) -> int:
                                   _stream(stream))
     if rc not in (GPMA_OK, GPMA_ECAP):
         _check(rc, "gpma_export_sorted")
+    return n.value if rc == GPMA_OK else -n.value - 1
+
+
+def gpma_export_sorted_noalloc(h: int, out, stream=None) -> int:
+    n = C.c_uint64()
+    rc = lib().gpma_export_sorted_noalloc(C.c_void_p(h), _ptr(out), out.numel() if out is not None else 0,
+                                          C.byref(n), _stream(stream))
+    if rc not in (GPMA_OK, GPMA_ECAP):
+        _check(rc, "gpma_export_sorted_noalloc")
     return n.value if rc == GPMA_OK else -n.value - 1
 
 

@@ -507,6 +507,18 @@ int ensure_analytics(gpma *h, uint32_t iters, cudaStream_t s) {
 
 }  // namespace
 
+namespace gpk {
+// Read-only view of a handle for entry points defined in other files.
+HandleView handle_view(gpma_t h) {
+  HandleView v;
+  v.geo = &h->geo;
+  v.ctl = h->ctl;
+  v.h_ctl = h->h_ctl;
+  v.poisoned = h->poisoned;
+  return v;
+}
+}  // namespace gpk
+
 extern "C" {
 
 const char *gpma_strerror(int status) {

@@ -108,4 +108,17 @@ int run_bfs(const Geo &g, uint32_t src, int32_t *depth, uint32_t *q0, uint32_t *
             uint32_t *h_counter, cudaStream_t s);
 void launch_cc(const Geo &g, uint32_t *label, cudaStream_t s);
 
+// read-only view of a handle (defined beside the handle in gpma_api.cu)
+struct HandleView {
+  const Geo *geo;
+  Ctl *ctl;
+  Ctl *h_ctl;
+  int poisoned;
+};
+
+}  // namespace gpk
+
+struct gpma;
+namespace gpk {
+HandleView handle_view(struct gpma *h);
 }  // namespace gpk
