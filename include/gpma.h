@@ -188,7 +188,9 @@ int gpma_check(gpma_t h, uint32_t *code, void *stream);
 #define GPMA_PROF_PAGERANK 5   /* one whole gpma_pagerank call */
 #define GPMA_PROF_BFS 6        /* one whole gpma_bfs call */
 #define GPMA_PROF_CC 7         /* one whole gpma_cc call */
-#define GPMA_PROF_N 8
+#define GPMA_PROF_UPDATE 8     /* one whole gpma_update_batch call (replayed batches run as one
+                                  CUDA graph: then only this phase is recorded) */
+#define GPMA_PROF_N 9
 
 typedef struct {
   double ms[GPMA_PROF_N];         /* summed device time */

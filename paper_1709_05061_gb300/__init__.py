@@ -50,11 +50,11 @@ class gpma_stats(C.Structure):
         return d
 
 
-GPMA_PROF_NAMES = ("sort", "leaf", "escalate", "resize", "pr_scatter", "pagerank", "bfs", "cc")
+GPMA_PROF_NAMES = ("sort", "leaf", "escalate", "resize", "pr_scatter", "pagerank", "bfs", "cc", "update")
 
 
 class gpma_profile(C.Structure):
-    _fields_ = [("ms", C.c_double * 8), ("count", C.c_uint64 * 8), ("launches", C.c_uint64 * 8)]
+    _fields_ = [("ms", C.c_double * 9), ("count", C.c_uint64 * 9), ("launches", C.c_uint64 * 9)]
 
     def as_dict(self) -> dict:
         return {n: {"ms": self.ms[i], "count": self.count[i], "launches": self.launches[i]}

@@ -18,6 +18,7 @@ std::atomic<uint64_t> g_launches{0};
 namespace gpk {
 void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 uint64_t launch_count() { return g_launches.load(std::memory_order_relaxed); }
+void unnote_launches(uint64_t k) { g_launches.fetch_sub(k, std::memory_order_relaxed); }
 }  // namespace gpk
 
 namespace {
@@ -111,6 +112,47 @@ struct Phase {
   ~Phase() { end(); }
 };
 
+// Instantiated CUDA graphs of the post-prep part of a batch, one per batch-size
+// bucket (and stats flag).  A graph bakes in device pointers, so every
+// (re)allocation of an array it touches bumps the handle's alloc epoch and
+// retires the graphs captured before.
+struct GraphCache {
+  struct Entry {
+    cudaGraphExec_t exec = nullptr;
+    uint64_t bucket = 0, epoch = 0, used = 0;
+    bool stats = false;
+    uint64_t kernels = 0;
+  };
+  static constexpr int kEntries = 8;
+  Entry e[kEntries];
+  cudaStream_t cap = nullptr;
+  uint64_t tick = 0;
+  bool enabled = true;
+  Entry *find(uint64_t bucket, uint64_t epoch, bool stats) {
+    for (auto &x : e)
+      if (x.exec && x.bucket == bucket && x.epoch == epoch && x.stats == stats) {
+        x.used = ++tick;
+        return &x;
+      }
+    return nullptr;
+  }
+  Entry *victim() {
+    Entry *v = &e[0];
+    for (auto &x : e) {
+      if (!x.exec) return &x;
+      if (x.used < v->used) v = &x;
+    }
+    cudaGraphExecDestroy(v->exec);
+    v->exec = nullptr;
+    return v;
+  }
+  ~GraphCache() {
+    for (auto &x : e)
+      if (x.exec) cudaGraphExecDestroy(x.exec);
+    if (cap) cudaStreamDestroy(cap);
+  }
+};
+
 struct gpma {
   uint32_t V, L, logL, raw;
   uint32_t tau0, tauh, rho0, rhoh;
@@ -138,7 +180,7 @@ struct gpma {
   float *contrib;
   double *dsum;
   uint32_t dsum_cap;
-  uint32_t *q0, *q1, *counter, *h_counter;
+  uint32_t *q0, *q1, *q2, *counter, *h_counter;
   double *pr_partials;
   unsigned *pr_counter;
   uint32_t *check_buf;
@@ -147,6 +189,8 @@ struct gpma {
   int poisoned;
   int host_sticky;
   Prof *prof;
+  GraphCache *graphs;
+  uint64_t alloc_epoch;
 };
 
 namespace {
@@ -266,6 +310,7 @@ int ensure_work(gpma *h, uint64_t n, cudaStream_t s) {
     return GPMA_ENOMEM;
   }
   cudaMemsetAsync(w.status, 0, sizeof(uint64_t) * st, s);
+  h->alloc_epoch++;
   h->cap = (uint32_t)cap;
   h->status_cap = st;
   w.cap = (uint32_t)cap;
@@ -282,6 +327,7 @@ int ensure_status(gpma *h, uint64_t n, cudaStream_t s) {
     return GPMA_ENOMEM;
   }
   cudaMemsetAsync(h->w.status, 0, sizeof(uint64_t) * need, s);
+  h->alloc_epoch++;
   h->status_cap = need;
   return GPMA_OK;
 }
@@ -296,6 +342,7 @@ int ensure_merge_scratch(gpma *h, cudaStream_t s) {
       return GPMA_ENOMEM;
     }
     h->scratch_cap = g.C;
+    h->alloc_epoch++;
   }
   if (h->vbuf_leaves < g.nleaves) {
     dfree(h, h->vbuf, s);
@@ -309,6 +356,7 @@ int ensure_merge_scratch(gpma *h, cudaStream_t s) {
       return GPMA_ENOMEM;
     }
     h->vbuf_leaves = g.nleaves;
+    h->alloc_epoch++;
   }
   return GPMA_OK;
 }
@@ -358,6 +406,7 @@ int do_resize(gpma *h, uint64_t total, cudaStream_t s) {
                        true, s);
   free_arrays(h, &old, s);
   h->geo = g2;
+  h->alloc_epoch++;
   return cuda_ok(h);
 }
 
@@ -407,53 +456,102 @@ int update(gpma *h, const uint64_t *ins, uint64_t n_ins, const uint64_t *del, ui
   f.utag = h->w.utag;
   f.uleaf = h->w.uleaf;
   f.run_start = h->w.run_start;
+  f.run_leaf = h->w.rleaf;
   const uint32_t n32 = (uint32_t)n;
-  {
-    Phase ph(h->prof, GPMA_PROF_SORT, s);
-    launch_front(f, s);
-  }
-  {
-    Phase ph(h->prof, GPMA_PROF_LEAF, s);
-    launch_leaf_pass(h->geo, h->ctl, h->w, n32, s);
-    launch_propagate(h->geo, h->ctl, h->w, n32, s);
-  }
-  Phase esc(h->prof, GPMA_PROF_ESCALATE, s);
-  launch_pending(h->geo, h->ctl, h->w, n32, s);
+  Phase whole(h->prof, GPMA_PROF_UPDATE, s);
+  launch_prep(f, s);
   // the root can only refuse inserts when the count might exceed its bound
   const bool may_fail = h->count_ub + n_ins > h->geo.maxc[h->geo.h];
-  launch_esc_level(h->geo, h->ctl, h->w, n32, may_fail, s);
-  if ((rc = cuda_ok(h))) return rc;
-
   bool resized = false;
-  if (may_fail) {
-    if ((rc = read_ctl(h, s))) return rc;
-    if (h->h_ctl->err) {
+  if (!may_fail && h->graphs->enabled) {
+    // replay: sort .. segment merge as one graph, grids sized for the bucket
+    uint64_t bucket = 2048;
+    while (bucket < n) bucket <<= 1;
+    const uint32_t nb = (uint32_t)bucket;
+    GraphCache::Entry *ge = h->graphs->find(bucket, h->alloc_epoch, stats != nullptr);
+    if (!ge) {
+      GraphCache &gc = *h->graphs;
+      if (!gc.cap && cudaStreamCreateWithFlags(&gc.cap, cudaStreamNonBlocking) != cudaSuccess) return poison(h, GPMA_EDEVICE);
+      const uint64_t l0 = launch_count();
+      cudaGraph_t graph = nullptr;
+      if (cudaStreamBeginCapture(gc.cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return poison(h, GPMA_EDEVICE);
+      launch_sort(f, nb, gc.cap);
+      launch_leaf_pass(h->geo, h->ctl, h->w, nb, gc.cap);
+      launch_propagate(h->geo, h->ctl, h->w, nb, gc.cap);
+      launch_pending(h->geo, h->ctl, h->w, nb, gc.cap);
+      launch_esc_level(h->geo, h->ctl, h->w, nb, false, gc.cap);
+      launch_esc_top(h->geo, h->ctl, h->w, nb, gc.cap);
+      launch_segments(h->geo, h->ctl, h->w, nb, gc.cap);
+      launch_segment_merge(h->geo, h->geo, h->ctl, h->w, h->scratch_cap, h->geo.nleaves, h->scratch, h->vbuf,
+                           h->partials, false, gc.cap);
+      if (stats) launch_stats(h->geo, h->ctl, h->w, nb, gc.cap);
       note_launch();
-      k_finish<<<1, 1, 0, s>>>(h->ctl);
-      int st = err_to_status(h->h_ctl->err);
-      if (st != GPMA_EINVAL) poison(h, st);
-      return st;
+      k_finish<<<1, 1, 0, gc.cap>>>(h->ctl);
+      const uint64_t kernels = launch_count() - l0;
+      unnote_launches(kernels);
+      if (cudaStreamEndCapture(gc.cap, &graph) != cudaSuccess) return poison(h, GPMA_EDEVICE);
+      ge = gc.victim();
+      cudaError_t ie = cudaGraphInstantiate(&ge->exec, graph, 0);
+      cudaGraphDestroy(graph);
+      if (ie != cudaSuccess) {
+        ge->exec = nullptr;
+        return poison(h, GPMA_EDEVICE);
+      }
+      ge->bucket = bucket;
+      ge->epoch = h->alloc_epoch;
+      ge->stats = stats != nullptr;
+      ge->kernels = kernels;
+      ge->used = ++gc.tick;
     }
-    h->count_ub = h->h_ctl->total;
-    if (h->h_ctl->nfail) {
-      esc.end();
-      Phase ph(h->prof, GPMA_PROF_RESIZE, s);
-      launch_unmark(h->geo, h->ctl, h->w, n32, s);
-      if ((rc = do_resize(h, h->h_ctl->total, s))) return rc;
-      resized = true;
-    }
-  } else {
+    if (cudaGraphLaunch(ge->exec, s) != cudaSuccess) return poison(h, GPMA_EDEVICE);
+    for (uint64_t k = 0; k < ge->kernels; k++) note_launch();
     h->count_ub += n_ins;
+  } else {
+    {
+      Phase ph(h->prof, GPMA_PROF_SORT, s);
+      launch_sort(f, n, s);
+    }
+    {
+      Phase ph(h->prof, GPMA_PROF_LEAF, s);
+      launch_leaf_pass(h->geo, h->ctl, h->w, n32, s);
+      launch_propagate(h->geo, h->ctl, h->w, n32, s);
+    }
+    Phase esc(h->prof, GPMA_PROF_ESCALATE, s);
+    launch_pending(h->geo, h->ctl, h->w, n32, s);
+    launch_esc_level(h->geo, h->ctl, h->w, n32, may_fail, s);
+    if ((rc = cuda_ok(h))) return rc;
+    if (may_fail) {
+      if ((rc = read_ctl(h, s))) return rc;
+      if (h->h_ctl->err) {
+        note_launch();
+        k_finish<<<1, 1, 0, s>>>(h->ctl);
+        int st = err_to_status(h->h_ctl->err);
+        if (st != GPMA_EINVAL) poison(h, st);
+        return st;
+      }
+      h->count_ub = h->h_ctl->total;
+      if (h->h_ctl->nfail) {
+        esc.end();
+        Phase ph(h->prof, GPMA_PROF_RESIZE, s);
+        launch_unmark(h->geo, h->ctl, h->w, n32, s);
+        if ((rc = do_resize(h, h->h_ctl->total, s))) return rc;
+        resized = true;
+      }
+    } else {
+      h->count_ub += n_ins;
+    }
+    if (!resized) {
+      launch_esc_top(h->geo, h->ctl, h->w, n32, s);
+      launch_segments(h->geo, h->ctl, h->w, n32, s);
+      launch_segment_merge(h->geo, h->geo, h->ctl, h->w, h->scratch_cap, h->geo.nleaves, h->scratch, h->vbuf,
+                           h->partials, false, s);
+      esc.end();
+      if (stats) launch_stats(h->geo, h->ctl, h->w, n32, s);
+    }
+    note_launch();
+    k_finish<<<1, 1, 0, s>>>(h->ctl);
   }
-  if (!resized) {
-    launch_esc_top(h->geo, h->ctl, h->w, n32, s);
-    launch_segments(h->geo, h->ctl, h->w, n32, s);
-    launch_segment_merge(h->geo, h->geo, h->ctl, h->w, h->scratch_cap, h->geo.nleaves, h->scratch, h->vbuf,
-                         h->partials, false, s);
-    if (stats) launch_stats(h->geo, h->ctl, h->w, n32, s);
-  }
-  note_launch();
-  k_finish<<<1, 1, 0, s>>>(h->ctl);
+  whole.end();
   if ((rc = cuda_ok(h))) return rc;
   if (!stats) return GPMA_OK;
 
@@ -490,7 +588,7 @@ int update(gpma *h, const uint64_t *ins, uint64_t n_ins, const uint64_t *del, ui
 int ensure_analytics(gpma *h, uint32_t iters, cudaStream_t s) {
   if (!h->deg) {
     if (!dalloc(h, &h->deg, h->V, s) || !dalloc(h, &h->y, h->V, s) || !dalloc(h, &h->contrib, h->V, s) ||
-        !dalloc(h, &h->q0, h->V, s) || !dalloc(h, &h->q1, h->V, s) || !dalloc(h, &h->counter, 4, s) ||
+        !dalloc(h, &h->q0, h->V, s) || !dalloc(h, &h->q1, h->V, s) || !dalloc(h, &h->q2, h->V, s) || !dalloc(h, &h->counter, 16, s) ||
         !dalloc(h, &h->pr_partials, 152 * 8, s) || !dalloc(h, &h->pr_counter, 4, s))
       return GPMA_ENOMEM;
   }
@@ -558,10 +656,14 @@ int gpma_create(uint32_t n_vertices, const gpma_params *params, const gpma_alloc
   if (!h) return GPMA_ENOMEM;
   memset(h, 0, sizeof(gpma));
   h->prof = new (std::nothrow) Prof;
-  if (!h->prof) {
+  h->graphs = new (std::nothrow) GraphCache;
+  if (!h->prof || !h->graphs) {
+    delete h->prof;
+    delete h->graphs;
     delete h;
     return GPMA_ENOMEM;
   }
+  allow_big_smem();
   h->V = raw ? 0 : n_vertices;
   h->L = L;
   h->logL = bits_for(L) - 1;
@@ -618,13 +720,14 @@ int gpma_destroy(gpma_t h) {
   dfree(h, h->geo.row_end, s);
   free_work(h, s);
   void *ptrs[] = {h->ctl, h->hist, h->scratch, h->vbuf, h->partials, h->deg, h->y, h->contrib,
-                  h->dsum, h->q0,  h->q1,      h->counter, h->check_buf, h->guards, h->pr_partials,
+                  h->dsum, h->q0,  h->q1,  h->q2,    h->counter, h->check_buf, h->guards, h->pr_partials,
                   h->pr_counter};
   for (void *p : ptrs) dfree(h, p, s);
   cudaStreamSynchronize(s);
   if (h->h_ctl) cudaFreeHost(h->h_ctl);
   if (h->h_counter) cudaFreeHost(h->h_counter);
   delete h->prof;
+  delete h->graphs;
   cudaGetLastError();
   delete h;
   return GPMA_OK;
@@ -656,7 +759,9 @@ int gpma_bfs(gpma_t h, uint32_t src, int32_t *d_depth, void *stream) {
   cudaStream_t s = (cudaStream_t)stream;
   if (ensure_analytics(h, 1, s)) return GPMA_ENOMEM;
   Phase ph(h->prof, GPMA_PROF_BFS, s);
-  if (run_bfs(h->geo, src, d_depth, h->q0, h->q1, h->counter, h->h_counter, s) < 0) return poison(h, GPMA_EDEVICE);
+  const int rb = run_bfs(h->geo, src, d_depth, h->q0, h->q1, h->q2, h->counter, h->h_counter, s);
+  if (rb == -2) return poison(h, GPMA_ETIMEOUT);
+  if (rb < 0) return poison(h, GPMA_EDEVICE);
   return cuda_ok(h);
 }
 
@@ -775,6 +880,7 @@ int gpma_import_layout(gpma_t h, const uint64_t *d_slots, uint64_t capacity, voi
   if (old_re) dfree(h, old_re, s);
   free_arrays(h, &h->geo, s);
   h->geo = g2;
+  h->alloc_epoch++;
   h->count_ub = h->h_ctl->total;
   return cuda_ok(h);
 }

@@ -52,6 +52,7 @@ struct Ctl {
   uint32_t nleafw;    // leaves covered by the maximal merged segments
   uint32_t nesc;      // runs whose inserts did not fit at level 0
   uint32_t nfail;     // pending runs that no level up to the root admits (root resize)
+  uint32_t nlong;     // runs left by the 64-slot fast leaf pass to the general one
   uint32_t epoch;     // bumped per single-pass scan, tags look-back status words
   uint32_t ticket[16];
   uint64_t total;     // logical number of stored keys (guards included)

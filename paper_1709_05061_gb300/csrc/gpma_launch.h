@@ -10,6 +10,8 @@ namespace gpk {
 // process-wide count of kernel launches issued by the library
 void note_launch();
 uint64_t launch_count();
+void unnote_launches(uint64_t k);  // launches recorded while capturing a graph
+void allow_big_smem();
 
 // ticket / look-back epoch slots of one batch (Ctl::ticket, Ctl::epoch + slot)
 constexpr uint32_t kSlotKeep = 8, kSlotRuns = 9, kSlotPend = 10, kSlotERuns = 11, kSlotSegs = 12,
@@ -33,6 +35,7 @@ struct FrontArgs {
   uint8_t *utag;
   uint32_t *uleaf;
   uint32_t *run_start;
+  uint32_t *run_leaf;
 };
 
 // per-batch work arrays of the update kernels
@@ -42,7 +45,7 @@ struct Work {
   uint32_t *uleaf;
   uint32_t *run_start;
   uint8_t *eflag;     // per key: 0 no effect, 1 applied, 2 pending insert
-  uint32_t *rleaf;    // per run
+  uint32_t *rleaf;    // per run: its leaf (written with the run heads)
   int32_t *rdelta;
   uint8_t *rinfo;     // 1 merged at level 0, 2 escalated
   uint32_t *rdel;
@@ -61,7 +64,10 @@ struct Work {
 
 uint32_t sort_tiles(uint64_t n);
 uint32_t comp_tiles(uint64_t n);
-void launch_front(const FrontArgs &f, cudaStream_t s);
+// k_init_batch + k_prep (take the batch's own pointers and sizes)
+void launch_prep(const FrontArgs &f, cudaStream_t s);
+// radix passes, unique/cancel + leaf search, run heads; grids for nb >= batch keys
+void launch_sort(const FrontArgs &f, uint64_t nb, cudaStream_t s);
 
 // k_update.cu
 void launch_leaf_pass(const Geo &g, Ctl *ctl, const Work &w, uint32_t n, cudaStream_t s);
@@ -104,8 +110,10 @@ void launch_pr_scatter(const Geo &g, const float *contrib, double *y, cudaStream
 void launch_pr_apply(const Geo &g, float damping, float *rank, const uint32_t *deg, double *y, float *contrib,
                      const double *dsum_in, double *dsum_out, double *partials, unsigned *counter,
                      cudaStream_t s);
-int run_bfs(const Geo &g, uint32_t src, int32_t *depth, uint32_t *q0, uint32_t *q1, uint32_t *counter,
-            uint32_t *h_counter, cudaStream_t s);
+// BFS in one cooperative launch; counter >= 16 u32, h_counter pinned; waits for the
+// stream; returns 0, -1 on a CUDA error, -2 when a bounded barrier wait gave up
+int run_bfs(const Geo &g, uint32_t src, int32_t *depth, uint32_t *q0, uint32_t *q1, uint32_t *q2,
+            uint32_t *counter, uint32_t *h_counter, cudaStream_t s);
 void launch_cc(const Geo &g, uint32_t *label, cudaStream_t s);
 
 // read-only view of a handle (defined beside the handle in gpma_api.cu)

@@ -44,6 +44,7 @@ __global__ void k_init_batch(Ctl *ctl, uint32_t *hist, uint32_t nhist, uint32_t 
     ctl->epoch += kSlotsPerBatch;
     ctl->nesc = 0;
     ctl->nfail = 0;
+    ctl->nlong = 0;
     ctl->m = ctl->nruns = ctl->npend = ctl->neruns = ctl->nsegs = ctl->nleafw = 0;
     for (int i = 0; i < 16; i++) ctl->ticket[i] = 0;
     ctl->n_inserted = ctl->n_deleted = 0;
@@ -196,7 +197,8 @@ __global__ void __launch_bounds__(kScanThreads) k_keep(PrepArgs a, const uint64_
 }
 
 __global__ void __launch_bounds__(kScanThreads) k_runs(const uint32_t *__restrict__ uleaf,
-                                                        uint32_t *__restrict__ run_start, uint64_t *status,
+                                                        uint32_t *__restrict__ run_start,
+                                                        uint32_t *__restrict__ run_leaf, uint64_t *status,
                                                         Ctl *ctl) {
   __shared__ ScanSmem sm;
   const uint32_t tile = take_ticket(ctl, kSlotRuns, sm), m = ctl->m;
@@ -211,7 +213,11 @@ __global__ void __launch_bounds__(kScanThreads) k_runs(const uint32_t *__restric
   uint32_t total = tile_scan(flag, off, tile, status, 1, 0, ctl->epoch + kSlotRuns, &ctl->err, sm);
 #pragma unroll
   for (int r = 0; r < kScanItems; r++)
-    if (flag[r] && off[r] < m) run_start[off[r]] = (uint32_t)scan_elem(tile, r);
+    if (flag[r] && off[r] < m) {
+      const uint32_t e = (uint32_t)scan_elem(tile, r);
+      run_start[off[r]] = e;
+      run_leaf[off[r]] = uleaf[e];
+    }
   if ((uint64_t)(tile + 1) * kScanTile >= m && threadIdx.x == 0) {
     ctl->nruns = total;
     run_start[total] = m;
@@ -229,27 +235,32 @@ static uint32_t grid_for(uint64_t n, uint32_t per_block, uint32_t cap) {
 uint32_t sort_tiles(uint64_t n) { return (uint32_t)((n + kSortTile - 1) / kSortTile); }
 uint32_t comp_tiles(uint64_t n) { return (uint32_t)((n + kScanTile - 1) / kScanTile); }
 
-void launch_front(const FrontArgs &f, cudaStream_t s) {
+void launch_prep(const FrontArgs &f, cudaStream_t s) {
   const PrepArgs &a = f.prep;
   const uint64_t n = (uint64_t)a.n_ins + a.n_del;
   note_launch();
   k_init_batch<<<1, 256, 0, s>>>(f.ctl, f.hist, a.npass * 256u, (uint32_t)n);
   note_launch();
   k_prep<<<grid_for(n, 256, 4 * 152), 256, 0, s>>>(a, f.ins, f.del, f.bufA, f.hist, f.ctl);
+}
+
+// grids sized for `nb` keys (>= the batch); the kernels read the batch size from ctl
+void launch_sort(const FrontArgs &f, uint64_t nb, cudaStream_t s) {
+  const PrepArgs &a = f.prep;
   uint64_t *src = f.bufA, *dst = f.bufB;
-  const uint32_t st = sort_tiles(n);
+  const uint32_t st = sort_tiles(nb);
   for (uint32_t p = 0; p < a.npass; p++) {
     note_launch();
     k_sort_pass<<<st, kSortThreads, 0, s>>>(src, dst, f.hist, f.status, f.ctl, p, p * a.dbits, a.dbits);
     uint64_t *t = src; src = dst; dst = t;
   }
   // look-back epochs: pass p uses epoch + p, then the fixed slots of gpma_launch.h
-  const uint32_t ct = comp_tiles(n);
+  const uint32_t ct = comp_tiles(nb);
   note_launch();
   k_keep<<<ct, kScanThreads, 0, s>>>(a, src, f.geo->F, f.geo->nleaves, f.ukey, f.utag, f.uleaf, f.status,
                                      f.ctl);
   note_launch();
-  k_runs<<<ct, kScanThreads, 0, s>>>(f.uleaf, f.run_start, f.status, f.ctl);
+  k_runs<<<ct, kScanThreads, 0, s>>>(f.uleaf, f.run_start, f.run_leaf, f.status, f.ctl);
 }
 
 }  // namespace gpk

@@ -49,9 +49,10 @@ __device__ __forceinline__ WarpBufs warp_bufs(unsigned char *smem, uint32_t per_
 }
 
 // ---- level 0: one warp per touched leaf ------------------------------------------------------
-__global__ void k_leaf_pass(Geo g, Ctl *ctl, Work w, uint32_t per_warp) {
+__global__ void k_leaf_pass(Geo g, Ctl *ctl, Work w, uint32_t per_warp, int rest_only) {
   extern __shared__ __align__(16) unsigned char smem[];
   if (ctl->err) return;
+  if (rest_only && ctl->nlong == 0) return;
   const uint32_t L = g.L, lane = lane_id();
   const uint32_t wpb = blockDim.x >> 5;
   WarpBufs B = warp_bufs(smem, per_warp, L);
@@ -64,7 +65,8 @@ __global__ void k_leaf_pass(Geo g, Ctl *ctl, Work w, uint32_t per_warp) {
   uint32_t acc_m0 = 0, acc_esc = 0;
   for (uint32_t r = blockIdx.x * wpb + (threadIdx.x >> 5); r < nruns; r += gridDim.x * wpb) {
     const uint32_t rs = w.run_start[r], re = w.run_start[r + 1];
-    const uint32_t j = w.uleaf[rs];
+    if (rest_only && re - rs <= 32) continue;  // done by the 64-slot fast path
+    const uint32_t j = w.rleaf[r];
     uint64_t *leaf = g.slots + (uint64_t)j * L;
     // the leaf's valid keys, compacted, with their slot offsets
     uint32_t nv = 0;
@@ -152,7 +154,6 @@ __global__ void k_leaf_pass(Geo g, Ctl *ctl, Work w, uint32_t per_warp) {
       }
     }
     if (lane == 0) {
-      w.rleaf[r] = j;
       w.rdelta[r] = (int32_t)nins - (int32_t)ndel;
       w.rinfo[r] = fits ? 1 : (nins ? 2 : 0);
       w.rdel[r] = ndel;
@@ -168,6 +169,131 @@ __global__ void k_leaf_pass(Geo g, Ctl *ctl, Work w, uint32_t per_warp) {
     if (acc_del) atomicAdd((unsigned long long *)&ctl->n_deleted, (unsigned long long)acc_del);
     if (acc_m0) atomicAdd(&ctl->n_merged0, acc_m0);
     if (acc_esc) atomicAdd(&ctl->nesc, acc_esc);
+  }
+}
+
+// ---- level 0, fast path for 64-slot leaves and runs of at most 32 updates ---------------------
+// Lane l holds slots 2l and 2l+1 of the leaf in registers (one 16-byte load),
+// lane i < len holds update i of the run; presence, deletes and ranks are warp
+// ballots.  The next run's leaf is loaded before the current one is processed.
+__global__ void __launch_bounds__(256) k_leaf64(Geo g, Ctl *ctl, Work w) {
+  __shared__ uint64_t sout[8][64];
+  if (ctl->err) return;
+  const uint32_t lane = lane_id(), wib = threadIdx.x >> 5;
+  const uint32_t nruns = ctl->nruns;
+  const uint64_t max0 = g.maxc[0];
+  const uint32_t nw = gridDim.x * 8;
+  ulonglong2 *s2 = reinterpret_cast<ulonglong2 *>(g.slots);
+  uint64_t acc_ins = 0, acc_del = 0;
+  uint32_t acc_m0 = 0, acc_esc = 0, acc_long = 0;
+  uint32_t r = blockIdx.x * 8 + wib;
+  uint32_t jn = 0, rsn = 0, ren = 0;
+  ulonglong2 kn = make_ulonglong2(kEmpty, kEmpty);
+  if (r < nruns) {
+    jn = w.rleaf[r];
+    rsn = w.run_start[r];
+    ren = w.run_start[r + 1];
+    kn = __ldcg(s2 + (uint64_t)jn * 32 + lane);
+  }
+  for (; r < nruns; r += nw) {
+    const uint32_t j = jn, rs = rsn, re = ren;
+    const uint64_t k0 = kn.x, k1 = kn.y;
+    const uint32_t rn = r + nw;
+    if (rn < nruns) {  // prefetch the next run's leaf (a different leaf: runs are distinct)
+      jn = w.rleaf[rn];
+      rsn = w.run_start[rn];
+      ren = w.run_start[rn + 1];
+      kn = __ldcg(s2 + (uint64_t)jn * 32 + lane);
+    }
+    const uint32_t len = re - rs;
+    if (len > 32) {
+      acc_long++;
+      continue;
+    }
+    const bool act = lane < len;
+    const uint64_t key = act ? w.ukey[rs + lane] : 0ull;
+    const uint32_t tag = act ? (uint32_t)w.utag[rs + lane] : 0u;
+    const bool v0 = k0 != kEmpty, v1 = k1 != kEmpty;
+    bool d0 = false, d1 = false, found = false;
+    for (uint32_t i = 0; i < len; i++) {
+      const uint64_t ki = __shfl_sync(0xFFFFFFFFu, key, i);
+      const uint32_t ti = __shfl_sync(0xFFFFFFFFu, tag, i);
+      const bool m0 = k0 == ki, m1 = k1 == ki;
+      const bool any = __ballot_sync(0xFFFFFFFFu, m0 || m1) != 0;
+      if (ti) {
+        d0 |= m0;
+        d1 |= m1;
+      }
+      if (lane == i) found = any;
+    }
+    const bool sv = act && !tag && !found;  // surviving insert (sorted in lane order)
+    const uint32_t svbal = __ballot_sync(0xFFFFFFFFu, sv);
+    const uint32_t nins = __popc(svbal);
+    const uint32_t ndel = __popc(__ballot_sync(0xFFFFFFFFu, d0)) + __popc(__ballot_sync(0xFFFFFFFFu, d1));
+    const bool kp0 = v0 && !d0, kp1 = v1 && !d1;
+    const uint32_t nkept = __popc(__ballot_sync(0xFFFFFFFFu, kp0)) + __popc(__ballot_sync(0xFFFFFFFFu, kp1));
+    const bool fits = nins > 0 && (uint64_t)nkept + nins <= max0;
+    if (fits) {
+      // TryInsert+ at level 0: rank-merge kept keys with the surviving inserts
+      const uint32_t c = (uint32_t)kp0 + (uint32_t)kp1;
+      const uint32_t before = warp_incl_scan(c) - c;
+      uint32_t lt0 = 0, lt1 = 0, my_pos = 0;
+      for (uint32_t bits = svbal; bits; bits &= bits - 1) {
+        const uint32_t b = __ffs(bits) - 1;
+        const uint64_t ik = __shfl_sync(0xFFFFFFFFu, key, b);
+        lt0 += ik < k0;
+        lt1 += ik < k1;
+        const uint32_t below = __popc(__ballot_sync(0xFFFFFFFFu, kp0 && k0 < ik)) +
+                               __popc(__ballot_sync(0xFFFFFFFFu, kp1 && k1 < ik));
+        if (lane == b) my_pos = __popc(svbal & lanemask_lt()) + below;
+      }
+      if (kp0) sout[wib][before + lt0] = k0;
+      if (kp1) sout[wib][before + kp0 + lt1] = k1;
+      if (sv) sout[wib][my_pos] = key;
+      __syncwarp();
+      const uint32_t n = nkept + nins;
+      const uint32_t o = 2 * lane;
+      const uint64_t a = o < n ? sout[wib][o] : kEmpty, b = o + 1 < n ? sout[wib][o + 1] : kEmpty;
+      s2[(uint64_t)j * 32 + lane] = make_ulonglong2(a, b);
+      if (!g.raw) {
+        if (o < n && is_guard(a)) g.row_end[a >> 32] = j * 64u + o;
+        if (o + 1 < n && is_guard(b)) g.row_end[b >> 32] = j * 64u + o + 1;
+      }
+      if (lane == 0) {
+        g.F[j] = sout[wib][0];
+        g.cnt[j] = n;
+      }
+      __syncwarp();
+    } else {
+      if (d0 || d1) s2[(uint64_t)j * 32 + lane] = make_ulonglong2(d0 ? kEmpty : k0, d1 ? kEmpty : k1);
+      const uint32_t fb = __ballot_sync(0xFFFFFFFFu, kp0 || kp1);
+      const uint32_t fl = fb ? __ffs(fb) - 1 : 0;
+      const uint64_t fk = __shfl_sync(0xFFFFFFFFu, kp0 ? k0 : k1, fl);
+      if (lane == 0) {
+        g.F[j] = fb ? fk : kEmpty;
+        g.cnt[j] = nkept;
+      }
+    }
+    if (act) {
+      const bool dl = tag && found;
+      w.eflag[rs + lane] = dl ? 1 : (sv ? (fits ? 1 : 2) : 0);
+    }
+    if (lane == 0) {
+      w.rdelta[r] = (int32_t)nins - (int32_t)ndel;
+      w.rinfo[r] = fits ? 1 : (nins ? 2 : 0);
+      w.rdel[r] = ndel;
+    }
+    acc_ins += nins;
+    acc_del += ndel;
+    acc_m0 += fits;
+    acc_esc += (!fits && nins);
+  }
+  if (lane == 0) {
+    if (acc_ins) atomicAdd((unsigned long long *)&ctl->n_inserted, (unsigned long long)acc_ins);
+    if (acc_del) atomicAdd((unsigned long long *)&ctl->n_deleted, (unsigned long long)acc_del);
+    if (acc_m0) atomicAdd(&ctl->n_merged0, acc_m0);
+    if (acc_esc) atomicAdd(&ctl->nesc, acc_esc);
+    if (acc_long) atomicAdd(&ctl->nlong, acc_long);
   }
 }
 
@@ -574,7 +700,7 @@ static uint32_t warps_per_block(uint32_t L) {
   return wpb;
 }
 
-static void allow_big_smem() {
+void allow_big_smem() {
   static bool done = false;
   if (done) return;
   cudaFuncSetAttribute(k_leaf_pass, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
@@ -585,8 +711,13 @@ static void allow_big_smem() {
 void launch_leaf_pass(const Geo &g, Ctl *ctl, const Work &w, uint32_t n, cudaStream_t s) {
   allow_big_smem();
   const uint32_t pw = leaf_smem_bytes(g.L), wpb = warps_per_block(g.L);
+  const int fast = g.L == 64;
+  if (fast) {
+    note_launch();
+    k_leaf64<<<blocks_for(n, 8, 152 * 8), 256, 0, s>>>(g, ctl, w);
+  }
   note_launch();
-  k_leaf_pass<<<blocks_for(n, wpb, 152 * 16), wpb * 32, wpb * pw, s>>>(g, ctl, w, pw);
+  k_leaf_pass<<<blocks_for(n, wpb, 152 * 16), wpb * 32, wpb * pw, s>>>(g, ctl, w, pw, fast);
 }
 
 void launch_propagate(const Geo &g, Ctl *ctl, const Work &w, uint32_t n, cudaStream_t s) {
