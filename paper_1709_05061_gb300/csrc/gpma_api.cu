@@ -175,13 +175,12 @@ struct gpma {
   uint64_t *partials;
   uint64_t partials_cap;
   // analytics
-  uint32_t *deg;
-  double *y;
-  float *contrib;
-  double *dsum;
+  uint64_t *y;    // PageRank sums, fixed point
+  uint64_t *cfx;  // PageRank contributions x/outdeg, fixed point
+  uint64_t *dsum;
   uint32_t dsum_cap;
   uint32_t *q0, *q1, *q2, *counter, *h_counter;
-  double *pr_partials;
+  uint64_t *pr_partials;
   unsigned *pr_counter;
   uint32_t *check_buf;
   uint64_t *guards;
@@ -398,6 +397,7 @@ int do_resize(gpma *h, uint64_t total, cudaStream_t s) {
   Geo g2;
   make_geo(h, h2, &g2);
   g2.row_end = old.row_end;
+  g2.deg = old.deg;
   if (!alloc_arrays(h, &g2, s)) {
     free_arrays(h, &g2, s);
     return poison(h, GPMA_ENOMEM);
@@ -586,10 +586,10 @@ int update(gpma *h, const uint64_t *ins, uint64_t n_ins, const uint64_t *del, ui
 }
 
 int ensure_analytics(gpma *h, uint32_t iters, cudaStream_t s) {
-  if (!h->deg) {
-    if (!dalloc(h, &h->deg, h->V, s) || !dalloc(h, &h->y, h->V, s) || !dalloc(h, &h->contrib, h->V, s) ||
-        !dalloc(h, &h->q0, h->V, s) || !dalloc(h, &h->q1, h->V, s) || !dalloc(h, &h->q2, h->V, s) || !dalloc(h, &h->counter, 16, s) ||
-        !dalloc(h, &h->pr_partials, 152 * 8, s) || !dalloc(h, &h->pr_counter, 4, s))
+  if (!h->y) {
+    if (!dalloc(h, &h->y, h->V, s) || !dalloc(h, &h->cfx, h->V, s) ||
+        !dalloc(h, &h->q0, h->V, s) || !dalloc(h, &h->q1, h->V, s) || !dalloc(h, &h->q2, 2ull * h->V, s) || !dalloc(h, &h->counter, 16, s) ||
+        !dalloc(h, &h->pr_partials, 152 * 16, s) || !dalloc(h, &h->pr_counter, 4, s))
       return GPMA_ENOMEM;
   }
   if (iters + 1 > h->dsum_cap) {
@@ -679,7 +679,8 @@ int gpma_create(uint32_t n_vertices, const gpma_params *params, const gpma_alloc
   make_geo(h, 0, &h->geo);
   bool ok = alloc_arrays(h, &h->geo, s) && dalloc(h, &h->ctl, 1, s) && dalloc(h, &h->hist, 8 * 256, s) &&
             dalloc(h, &h->check_buf, 4, s);
-  if (ok && !raw) ok = dalloc(h, &h->geo.row_end, h->V, s);
+  if (ok && !raw) ok = dalloc(h, &h->geo.row_end, h->V, s) && dalloc(h, &h->geo.deg, h->V, s);
+  if (ok && !raw) ok = cudaMemsetAsync(h->geo.deg, 0, sizeof(uint32_t) * h->V, s) == cudaSuccess;
   if (ok) ok = cudaMallocHost(&h->h_ctl, sizeof(Ctl)) == cudaSuccess && cudaMallocHost(&h->h_counter, 16) == cudaSuccess;
   if (!ok) {
     cudaGetLastError();
@@ -718,8 +719,9 @@ int gpma_destroy(gpma_t h) {
   cudaDeviceSynchronize();
   free_arrays(h, &h->geo, s);
   dfree(h, h->geo.row_end, s);
+  dfree(h, h->geo.deg, s);
   free_work(h, s);
-  void *ptrs[] = {h->ctl, h->hist, h->scratch, h->vbuf, h->partials, h->deg, h->y, h->contrib,
+  void *ptrs[] = {h->ctl, h->hist, h->scratch, h->vbuf, h->partials, h->cfx, h->y,
                   h->dsum, h->q0,  h->q1,  h->q2,    h->counter, h->check_buf, h->guards, h->pr_partials,
                   h->pr_counter};
   for (void *p : ptrs) dfree(h, p, s);
@@ -779,14 +781,14 @@ int gpma_pagerank(gpma_t h, uint32_t iters, float damping, float *d_rank, void *
   cudaStream_t s = (cudaStream_t)stream;
   if (ensure_analytics(h, iters, s)) return GPMA_ENOMEM;
   Phase all(h->prof, GPMA_PROF_PAGERANK, s);
-  launch_pr_setup(h->geo, iters, d_rank, h->deg, h->y, h->contrib, h->dsum, h->pr_partials, h->pr_counter, s);
+  launch_pr_setup(h->geo, iters, d_rank, h->y, h->cfx, h->dsum, h->pr_partials, h->pr_counter, s);
   for (uint32_t it = 0; it < iters; it++) {
     {
       Phase ph(h->prof, GPMA_PROF_PR_SCATTER, s);
-      launch_pr_scatter(h->geo, h->contrib, h->y, s);
+      launch_pr_scatter(h->geo, h->cfx, h->y, s);
     }
-    launch_pr_apply(h->geo, damping, d_rank, h->deg, h->y, h->contrib, h->dsum + it, h->dsum + it + 1,
-                    h->pr_partials, h->pr_counter, s);
+    launch_pr_apply(h->geo, damping, d_rank, h->y, h->cfx, h->dsum + it, h->dsum + it + 1, h->pr_partials,
+                    h->pr_counter, s);
   }
   all.end();
   return cuda_ok(h);
@@ -811,8 +813,7 @@ int gpma_export_csr(gpma_t h, uint64_t *d_rowptr, uint32_t *d_col, uint64_t cap,
   if (ensure_analytics(h, 1, s) || ensure_status(h, h->geo.C, s)) return GPMA_ENOMEM;
   uint64_t *partials = (uint64_t *)dmalloc(h, scan_partials(h->V + 1) * 8 + 8, s);
   if (!partials) return GPMA_ENOMEM;
-  launch_degrees(h->geo, h->deg, s);
-  launch_rowptr(h->deg, d_rowptr, h->V, partials, s);
+  launch_rowptr(h->geo.deg, d_rowptr, h->V, partials, s);
   launch_export(h->geo, h->ctl, nullptr, d_col, cap, h->w.status, s);
   dfree(h, partials, s);
   int rc = read_ctl(h, s);
@@ -842,18 +843,20 @@ int gpma_import_layout(gpma_t h, const uint64_t *d_slots, uint64_t capacity, voi
   Geo g2;
   make_geo(h, hh, &g2);
   g2.row_end = h->geo.row_end;
+  g2.deg = h->geo.deg;
   if (!alloc_arrays(h, &g2, s)) {
     free_arrays(h, &g2, s);
     return GPMA_ENOMEM;
   }
-  // keep the old guard index in case the import is rejected
+  // keep the old guard index and degrees in case the import is rejected
   uint32_t *old_re = nullptr;
   if (!h->raw) {
-    if (!dalloc(h, &old_re, h->V, s)) {
+    if (!dalloc(h, &old_re, 2ull * h->V, s)) {
       free_arrays(h, &g2, s);
       return GPMA_ENOMEM;
     }
     cudaMemcpyAsync(old_re, h->geo.row_end, sizeof(uint32_t) * h->V, cudaMemcpyDeviceToDevice, s);
+    cudaMemcpyAsync(old_re + h->V, h->geo.deg, sizeof(uint32_t) * h->V, cudaMemcpyDeviceToDevice, s);
     cudaMemsetAsync(h->geo.row_end, 0xFF, sizeof(uint32_t) * h->V, s);
   }
   const uint64_t old_total_ub = h->count_ub;
@@ -870,6 +873,7 @@ int gpma_import_layout(gpma_t h, const uint64_t *d_slots, uint64_t capacity, voi
     free_arrays(h, &g2, s);
     if (old_re) {
       cudaMemcpyAsync(h->geo.row_end, old_re, sizeof(uint32_t) * h->V, cudaMemcpyDeviceToDevice, s);
+      cudaMemcpyAsync(h->geo.deg, old_re + h->V, sizeof(uint32_t) * h->V, cudaMemcpyDeviceToDevice, s);
       dfree(h, old_re, s);
     }
     cudaMemcpyAsync(&h->ctl->total, &saved.total, sizeof(uint64_t), cudaMemcpyHostToDevice, s);

@@ -9,6 +9,7 @@
 //                   (logical counts: valid keys + inserts still pending in this batch)
 //   mark[]          u32 per segment of levels 1..h, set while a batch decides merges
 //   row_end[V]      u32 slot of the guard of every vertex (CSR row offsets, Sec. 4.2)
+//   deg[V]          u32 out-degree of every vertex, kept by the update kernels
 #pragma once
 #include <cstdint>
 #include <cuda_runtime.h>
@@ -31,6 +32,7 @@ struct Geo {
   uint32_t *tree;
   uint32_t *mark;
   uint32_t *row_end;
+  uint32_t *deg;  // out-degree of every vertex (stored edges, guards excluded)
   uint64_t C, nleaves;
   uint32_t L, logL, h, V, raw;
   uint32_t pad;
@@ -69,6 +71,15 @@ __device__ __forceinline__ bool is_guard(uint64_t k) {
 }
 
 __device__ __forceinline__ uint32_t lane_id() { return threadIdx.x & 31u; }
+
+// add +1 / -1 to the out-degree of the source of every marked lane's key; lanes
+// of one source (rows are contiguous) combine into one atomic
+__device__ __forceinline__ void degree_delta(uint32_t *deg, bool active, uint64_t key, int d) {
+  const uint32_t src = active ? (uint32_t)(key >> 32) : 0xFFFFFFFFu;
+  const uint32_t peers = __match_any_sync(0xFFFFFFFFu, src);
+  if (active && (threadIdx.x & 31u) == (uint32_t)(__ffs(peers) - 1))
+    atomicAdd(&deg[src], (uint32_t)(d * __popc(peers)));
+}
 __device__ __forceinline__ uint32_t lanemask_lt() { return (1u << lane_id()) - 1u; }
 
 template <typename T>

@@ -102,13 +102,14 @@ void launch_scan_u32_u64(const uint32_t *in, uint64_t *out, uint64_t n_bound, ui
                          const uint32_t *n_dev = nullptr);
 
 // k_analytics.cu
-// PageRank: degrees + x0 (setup), then per iteration one push pass and one apply
-// partials: >= 152 * 4 doubles; counter: one unsigned (zeroed by setup, re-zeroed by each sum)
-void launch_pr_setup(const Geo &g, uint32_t iters, float *rank, uint32_t *deg, double *y, float *contrib,
-                     double *dsum, double *partials, unsigned *counter, cudaStream_t s);
-void launch_pr_scatter(const Geo &g, const float *contrib, double *y, cudaStream_t s);
-void launch_pr_apply(const Geo &g, float damping, float *rank, const uint32_t *deg, double *y, float *contrib,
-                     const double *dsum_in, double *dsum_out, double *partials, unsigned *counter,
+// PageRank: x0 (setup), then per iteration one push pass and one apply.  y, cfx:
+// u64[V] fixed point (2^60); dsum: u64[iters + 1]; partials >= 152 * 16; counter
+// one unsigned (zeroed by setup, re-zeroed by each sum)
+void launch_pr_setup(const Geo &g, uint32_t iters, float *rank, uint64_t *y, uint64_t *cfx, uint64_t *dsum,
+                     uint64_t *partials, unsigned *counter, cudaStream_t s);
+void launch_pr_scatter(const Geo &g, const uint64_t *cfx, uint64_t *y, cudaStream_t s);
+void launch_pr_apply(const Geo &g, float damping, float *rank, uint64_t *y, uint64_t *cfx,
+                     const uint64_t *dsum_in, uint64_t *dsum_out, uint64_t *partials, unsigned *counter,
                      cudaStream_t s);
 // BFS in one cooperative launch; counter >= 16 u32, h_counter pinned; waits for the
 // stream; returns 0, -1 on a CUDA error, -2 when a bounded barrier wait gave up

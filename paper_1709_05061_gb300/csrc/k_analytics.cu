@@ -1,12 +1,13 @@
 // k_analytics.cu -- graph analytics that read the gapped array in place
 // (Sec. 4.2: every access tests IsEntryExist, i.e. skips EMPTY slots; guards
 // delimit the rows).
-//   PageRank  power iteration with a push SpMV over the slots (Sec. 6.1)
+//   PageRank  power iteration with a push SpMV over the slots (Sec. 6.1), exact
+//             fixed-point sums
 //   BFS       level-synchronous in one persistent cooperative kernel: a warp gathers
 //             a frontier vertex's row for small frontiers, one pass over the array
 //             for large ones
-//   CC        lock-free union-find over the edges; a root is always the smallest
-//             id of its tree, so the final label is the component's minimum id
+//   CC        lock-free union-find (sampled first pass, then every edge); a root is
+//             always the smallest id of its tree, so labels are component minima
 #include "gpma_dev.cuh"
 #include "gpma_launch.h"
 
@@ -20,16 +21,42 @@ static uint32_t nb(uint64_t items, uint32_t per_block, uint32_t cap) {
 }
 
 // ---- PageRank -----------------------------------------------------------------------------------
-// Sum of one double per thread over the grid: per-block partials, and the last
-// block to finish adds them in block order (fixed order, one atomic per block).
-__device__ __forceinline__ void grid_sum_double(double v, double *partials, unsigned *counter, double *out) {
-  __shared__ double ws[32];
+// Sums are exact: every contribution x_u / outdeg(u) is formed in FP32 and
+// rounded once to a 64-bit fixed-point number with 60 fractional bits (all ranks
+// and sums are <= 1), and the scatter adds integers, so the result does not
+// depend on the order in which the reductions land.  Ranks are FP32 and the
+// per-vertex arithmetic stays in FP32 and integer units.
+
+// Conversions between FP32 and the 2^60 fixed point use integer operations only
+// (GB300's FP64 pipe is narrow and 64-bit int <-> float conversions run there).
+// fx(v) = round(v * 2^60) for v in [0, 1]: mantissa shifted by its exponent.
+__device__ __forceinline__ uint64_t to_fx(float v) {
+  const uint32_t b = __float_as_uint(v);
+  const int32_t ex = (int32_t)((b >> 23) & 0xFFu);
+  if (ex == 0) return 0ull;  // zero (no subnormal contribution matters at 2^-60)
+  const uint64_t m = (uint64_t)((b & 0x7FFFFFu) | 0x800000u);
+  const int32_t sh = ex - 127 - 23 + 60;  // value = m * 2^(ex - 150); times 2^60
+  if (sh >= 0) return m << sh;
+  if (sh <= -64) return 0ull;
+  return (m + (1ull << (-sh - 1))) >> (-sh);  // round half up
+}
+
+// y * 2^-60 as FP32 from the two 32-bit halves: hi * 2^-28 + lo * 2^-60
+__device__ __forceinline__ float fx_to_float(uint64_t y) {
+  return __uint2float_rn((uint32_t)(y >> 32)) * 3.7252902984619140625e-09f +
+         __uint2float_rn((uint32_t)y) * 8.6736173798840354720e-19f;
+}
+
+// Sum of one u64 per thread over the grid: per-block partials, and the last
+// block to finish adds them (integers: exact, any order).
+__device__ __forceinline__ void grid_sum_u64(uint64_t v, uint64_t *partials, unsigned *counter, uint64_t *out) {
+  __shared__ uint64_t ws[32];
   __shared__ bool last;
   v = warp_sum(v);
   if (lane_id() == 0) ws[threadIdx.x >> 5] = v;
   __syncthreads();
   if (threadIdx.x == 0) {
-    double b = 0.0;
+    uint64_t b = 0;
     for (uint32_t q = 0; q < (blockDim.x >> 5); q++) b += ws[q];
     partials[blockIdx.x] = b;
     __threadfence();
@@ -37,14 +64,14 @@ __device__ __forceinline__ void grid_sum_double(double v, double *partials, unsi
   }
   __syncthreads();
   if (last) {
-    double t = 0.0;
-    const volatile double *vp = partials;
+    uint64_t t = 0;
+    const volatile uint64_t *vp = partials;
     for (uint32_t q = threadIdx.x; q < gridDim.x; q += blockDim.x) t += vp[q];
     t = warp_sum(t);
     if (lane_id() == 0) ws[threadIdx.x >> 5] = t;
     __syncthreads();
     if (threadIdx.x == 0) {
-      double tot = 0.0;
+      uint64_t tot = 0;
       for (uint32_t q = 0; q < (blockDim.x >> 5); q++) tot += ws[q];
       *out = tot;
       *counter = 0;
@@ -53,30 +80,31 @@ __device__ __forceinline__ void grid_sum_double(double v, double *partials, unsi
 }
 
 __global__ void k_pr_init(uint32_t V, const uint32_t *__restrict__ deg, float *__restrict__ x,
-                          float *__restrict__ contrib, double *__restrict__ y, double *dsum0, double *partials,
+                          uint64_t *__restrict__ cfx, uint64_t *__restrict__ y, uint64_t *dsum0, uint64_t *partials,
                           unsigned *counter) {
-  const float x0 = (float)(1.0 / (double)V);
-  double dang = 0.0;
+  const float x0 = __fdiv_rn(1.0f, (float)V);
+  uint64_t dang = 0;
   const uint32_t stride = gridDim.x * blockDim.x;
   for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < V; v += stride) {
     const uint32_t d = deg[v];
     x[v] = x0;
-    y[v] = 0.0;
-    contrib[v] = d ? x0 / (float)d : 0.0f;
-    if (!d) dang += (double)x0;
+    y[v] = 0;
+    cfx[v] = d ? to_fx(__fdiv_rn(x0, (float)d)) : 0ull;
+    if (!d) dang += to_fx(x0);
   }
-  grid_sum_double(dang, partials, counter, dsum0);
+  grid_sum_u64(dang, partials, counter, dsum0);
 }
 
-// y[v] += x[u] / outdeg(u) for every stored edge u -> v.  Each thread owns two
+// y[v] += fx(x_u / outdeg(u)) for every stored edge u -> v.  Each thread owns two
 // 16-byte slot pairs per step and loads the next step's pairs before it works on
-// the current ones, so the HBM stream overlaps the gathers and the reductions.
-__device__ __forceinline__ void pr_push(uint64_t k, const float *__restrict__ contrib, double *__restrict__ y) {
-  if (k != kEmpty && !is_guard(k)) atomicAdd(&y[k & 0xFFFFFFFFull], (double)__ldg(contrib + (k >> 32)));
+// the current ones.
+__device__ __forceinline__ void pr_push(uint64_t k, const uint64_t *__restrict__ cfx, uint64_t *__restrict__ y) {
+  if (k != kEmpty && !is_guard(k))
+    atomicAdd((unsigned long long *)&y[k & 0xFFFFFFFFull], (unsigned long long)__ldg(cfx + (k >> 32)));
 }
 
-__global__ void __launch_bounds__(256) k_pr_scatter(Geo g, const float *__restrict__ contrib,
-                                                    double *__restrict__ y) {
+__global__ void __launch_bounds__(256) k_pr_scatter(Geo g, const uint64_t *__restrict__ cfx,
+                                                    uint64_t *__restrict__ y) {
   const uint64_t npairs = g.C >> 1;
   const ulonglong2 *s2 = reinterpret_cast<const ulonglong2 *>(g.slots);
   const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
@@ -88,56 +116,55 @@ __global__ void __launch_bounds__(256) k_pr_scatter(Geo g, const float *__restri
     const uint64_t q = p + 2 * stride;
     const ulonglong2 na = q < npairs ? __ldcs(s2 + q) : none;
     const ulonglong2 nb = q + stride < npairs ? __ldcs(s2 + q + stride) : none;
-    pr_push(a.x, contrib, y);
-    pr_push(a.y, contrib, y);
-    pr_push(b.x, contrib, y);
-    pr_push(b.y, contrib, y);
+    pr_push(a.x, cfx, y);
+    pr_push(a.y, cfx, y);
+    pr_push(b.x, cfx, y);
+    pr_push(b.y, cfx, y);
     a = na;
     b = nb;
     p = q;
   }
 }
 
-__global__ void k_pr_apply(uint32_t V, float damping, const uint32_t *__restrict__ deg, double *__restrict__ y,
-                           float *__restrict__ x, float *__restrict__ contrib, const double *dsum_in,
-                           double *dsum_out, double *partials, unsigned *counter) {
-  const double base = (1.0 - (double)damping) / (double)V;
-  const double dn = *dsum_in / (double)V;
-  double dang = 0.0;
+__global__ void k_pr_apply(uint32_t V, float damping, const uint32_t *__restrict__ deg, uint64_t *__restrict__ y,
+                           float *__restrict__ x, uint64_t *__restrict__ cfx, const uint64_t *dsum_in,
+                           uint64_t *dsum_out, uint64_t *partials, unsigned *counter) {
+  // x' = (1 - d)/V + d * (y + dangling / V), all in FP32 (the sums themselves are exact)
+  const float base = __fdiv_rn(1.0f - damping, (float)V);
+  const float dn = __fdiv_rn(fx_to_float(*dsum_in), (float)V);
+  uint64_t dang = 0;
   const uint32_t stride = gridDim.x * blockDim.x;
   for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < V; v += stride) {
-    const double nx = base + (double)damping * (y[v] + dn);
-    const float xf = (float)nx;
     const uint32_t d = deg[v];
+    const float xf = __fmaf_rn(damping, fx_to_float(y[v]) + dn, base);
     x[v] = xf;
-    y[v] = 0.0;
-    contrib[v] = d ? xf / (float)d : 0.0f;
-    if (!d) dang += (double)xf;
+    y[v] = 0;
+    cfx[v] = d ? to_fx(__fdiv_rn(xf, (float)d)) : 0ull;
+    if (!d) dang += to_fx(xf);
   }
-  grid_sum_double(dang, partials, counter, dsum_out);
+  grid_sum_u64(dang, partials, counter, dsum_out);
 }
 
-constexpr uint32_t kVecBlocks = 152 * 4;  // grid of the per-vertex kernels (and partials per sum)
+constexpr uint32_t kVecBlocks = 152 * 8;  // grid of the per-vertex kernels (and partials per sum)
 
-void launch_pr_setup(const Geo &g, uint32_t iters, float *rank, uint32_t *deg, double *y, float *contrib,
-                     double *dsum, double *partials, unsigned *counter, cudaStream_t s) {
-  launch_degrees(g, deg, s);
-  cudaMemsetAsync(dsum, 0, sizeof(double) * (iters + 1), s);
+void launch_pr_setup(const Geo &g, uint32_t iters, float *rank, uint64_t *y, uint64_t *cfx, uint64_t *dsum,
+                     uint64_t *partials, unsigned *counter, cudaStream_t s) {
+  cudaMemsetAsync(dsum, 0, sizeof(uint64_t) * (iters + 1), s);
   cudaMemsetAsync(counter, 0, sizeof(unsigned), s);
   note_launch();
-  k_pr_init<<<nb(g.V, 256, kVecBlocks), 256, 0, s>>>(g.V, deg, rank, contrib, y, dsum, partials, counter);
+  k_pr_init<<<nb(g.V, 256, kVecBlocks), 256, 0, s>>>(g.V, g.deg, rank, cfx, y, dsum, partials, counter);
 }
 
-void launch_pr_scatter(const Geo &g, const float *contrib, double *y, cudaStream_t s) {
+void launch_pr_scatter(const Geo &g, const uint64_t *cfx, uint64_t *y, cudaStream_t s) {
   note_launch();
-  k_pr_scatter<<<nb(g.C >> 2, 256, 152 * 8), 256, 0, s>>>(g, contrib, y);
+  k_pr_scatter<<<nb(g.C >> 2, 256, 152 * 8), 256, 0, s>>>(g, cfx, y);
 }
 
-void launch_pr_apply(const Geo &g, float damping, float *rank, const uint32_t *deg, double *y, float *contrib,
-                     const double *dsum_in, double *dsum_out, double *partials, unsigned *counter,
+void launch_pr_apply(const Geo &g, float damping, float *rank, uint64_t *y, uint64_t *cfx,
+                     const uint64_t *dsum_in, uint64_t *dsum_out, uint64_t *partials, unsigned *counter,
                      cudaStream_t s) {
   note_launch();
-  k_pr_apply<<<nb(g.V, 256, kVecBlocks), 256, 0, s>>>(g.V, damping, deg, y, rank, contrib, dsum_in, dsum_out,
+  k_pr_apply<<<nb(g.V, 256, kVecBlocks), 256, 0, s>>>(g.V, damping, g.deg, y, rank, cfx, dsum_in, dsum_out,
                                                          partials, counter);
 }
 
@@ -206,7 +233,8 @@ __device__ __forceinline__ void bfs_gather(const Geo &g, int32_t *depth, uint64_
 constexpr uint64_t kBigRow = 1024, kRowChunk = 256;
 
 // cnt[0..2]: frontier sizes (rotating), cnt[3]: queue rebuild, cnt[4]: levels,
-// cnt[5]: long rows of the level (listed in `big`)
+// cnt[6..7]: one u64 = (long rows listed << 32) | chunks of those rows; `big` holds
+// (row, first chunk) pairs
 __global__ void __launch_bounds__(256) k_bfs_persist(Geo g, int32_t *depth, uint32_t *qa, uint32_t *qb,
                                                      uint32_t *big, uint32_t *cnt, unsigned *bar, uint32_t *err,
                                                      uint32_t scan_from) {
@@ -256,26 +284,37 @@ __global__ void __launch_bounds__(256) k_bfs_persist(Geo g, int32_t *depth, uint
         }
         if (!grid_barrier(bar, err)) return;
       }
-      // top-down: a warp per short row; long rows are listed and split below
+      // top-down: a warp per short row; long rows are listed with the running
+      // total of their 256-slot chunks (one packed 64-bit atomic keeps the list
+      // order and the chunk bases consistent), then all warps share the chunks
+      unsigned long long *bigctr = reinterpret_cast<unsigned long long *>(cnt + 6);
       for (uint32_t i = warp; i < nfront; i += nwarps) {
         const uint32_t u = __ldcg(qin + i);
         const uint64_t beg = u ? (uint64_t)__ldg(g.row_end + u - 1) + 1 : 0, end = __ldg(g.row_end + u);
         if (end - beg > kBigRow) {
-          if (lane == 0) big[atomicAdd(cnt + 5, 1u)] = u;
+          if (lane == 0) {
+            const uint32_t nch = (uint32_t)((end - beg + kRowChunk - 1) / kRowChunk);
+            const unsigned long long old = atomicAdd(bigctr, (1ull << 32) | nch);
+            big[2 * (old >> 32)] = u;
+            big[2 * (old >> 32) + 1] = (uint32_t)old;  // first chunk of this row
+          }
           continue;
         }
         bfs_gather(g, depth, beg, end, qout, cnext, level);
       }
       if (!grid_barrier(bar, err)) return;
-      const uint32_t nbig = *(volatile uint32_t *)(cnt + 5);
-      for (uint32_t b = 0; b < nbig; b++) {
-        const uint32_t u = __ldcg(big + b);
-        const uint64_t beg = u ? (uint64_t)__ldg(g.row_end + u - 1) + 1 : 0, end = __ldg(g.row_end + u);
-        const uint64_t chunks = (end - beg + kRowChunk - 1) / kRowChunk;
-        for (uint64_t c = warp; c < chunks; c += nwarps) {
-          const uint64_t a = beg + c * kRowChunk;
-          bfs_gather(g, depth, a, a + kRowChunk < end ? a + kRowChunk : end, qout, cnext, level);
+      const unsigned long long bc = *(volatile unsigned long long *)bigctr;
+      const uint32_t nbig = (uint32_t)(bc >> 32), nchunks = (uint32_t)bc;
+      for (uint32_t c = warp; c < nchunks; c += nwarps) {
+        uint32_t lo = 0, hi = nbig;  // last listed row whose first chunk is <= c
+        while (hi - lo > 1) {
+          const uint32_t mid = (lo + hi) >> 1;
+          if (__ldcg(big + 2 * mid + 1) <= c) lo = mid; else hi = mid;
         }
+        const uint32_t u = __ldcg(big + 2 * lo);
+        const uint64_t beg = u ? (uint64_t)__ldg(g.row_end + u - 1) + 1 : 0, end = __ldg(g.row_end + u);
+        const uint64_t a = beg + (uint64_t)(c - __ldcg(big + 2 * lo + 1)) * kRowChunk;
+        bfs_gather(g, depth, a, a + kRowChunk < end ? a + kRowChunk : end, qout, cnext, level);
       }
     }
     if (!grid_barrier(bar, err)) return;
@@ -288,7 +327,8 @@ __global__ void __launch_bounds__(256) k_bfs_persist(Geo g, int32_t *depth, uint
     }
     if (tid == 0) {
       cnt[3] = 0;
-      cnt[5] = 0;
+      cnt[6] = 0;  // long-row list (packed with cnt[7])
+      cnt[7] = 0;
     }
     ++level;
     // every block has read nfront and the queue pointers before anyone reuses them
@@ -306,6 +346,8 @@ __global__ void k_bfs_setup(int32_t *depth, uint32_t src, uint32_t *q0, uint32_t
   cnt[3] = 0;
   cnt[4] = 0;
   cnt[5] = 0;
+  cnt[6] = 0;
+  cnt[7] = 0;
   bar[0] = 0;
   bar[1] = 0;
 }
@@ -321,7 +363,7 @@ int run_bfs(const Geo &g, uint32_t src, int32_t *depth, uint32_t *q0, uint32_t *
     grid = sms * (per_sm > 4 ? 4 : per_sm);
     if (grid < 1) grid = 1;
   }
-  // counter layout: cnt[0..4], barrier words, error word
+  // counter layout: cnt[0..7], barrier words, error word
   uint32_t *cnt = counter;
   unsigned *bar = counter + 8;
   uint32_t *err = counter + 12;
@@ -342,13 +384,15 @@ int run_bfs(const Geo &g, uint32_t src, int32_t *depth, uint32_t *q0, uint32_t *
 }
 
 // ---- connected components -------------------------------------------------------------------------
+// Parents only ever point to smaller ids, so a root is the smallest id of its
+// tree and any (even stale) chain of parent reads strictly decreases: finds use
+// plain loads, the CAS that hooks a root checks freshness.
 __device__ __forceinline__ uint32_t cc_find(uint32_t *parent, uint32_t v) {
-  volatile uint32_t *p = parent;
-  uint32_t par = p[v];
+  uint32_t par = parent[v];
   if (par != v) {
     uint32_t prev = v, next;
-    while (par > (next = p[par])) {  // parents are never larger than their children
-      p[prev] = next;                // path halving towards the root
+    while (par > (next = parent[par])) {
+      parent[prev] = next;  // path halving towards the root
       prev = par;
       par = next;
     }
@@ -356,28 +400,47 @@ __device__ __forceinline__ uint32_t cc_find(uint32_t *parent, uint32_t v) {
   return par;
 }
 
+__device__ __forceinline__ void cc_link(uint32_t *label, uint32_t a, uint32_t b) {
+  for (;;) {
+    a = cc_find(label, a);
+    b = cc_find(label, b);
+    if (a == b) return;
+    if (a < b) {
+      uint32_t t = a; a = b; b = t;
+    }
+    // hook the larger root under the smaller one
+    const uint32_t old = atomicCAS(&label[a], a, b);
+    if (old == a) return;
+    a = old;
+  }
+}
+
 __global__ void k_cc_init(uint32_t *label, uint32_t V) {
   for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < V; v += gridDim.x * blockDim.x) label[v] = v;
+}
+
+// first pass: the first two stored out-edges of every row, which already joins
+// most vertices into large, shallow trees before the pass over all edges
+__global__ void k_cc_sample(Geo g, uint32_t *label) {
+  for (uint32_t u = blockIdx.x * blockDim.x + threadIdx.x; u < g.V; u += gridDim.x * blockDim.x) {
+    const uint64_t beg = u ? (uint64_t)g.row_end[u - 1] + 1 : 0, end = g.row_end[u];
+    uint32_t taken = 0;
+    for (uint64_t e = beg; e < end && taken < 2; e++) {
+      const uint64_t k = g.slots[e];
+      if (k == kEmpty) continue;
+      ++taken;
+      const uint32_t v = (uint32_t)(k & 0xFFFFFFFFull);
+      if (v != u) cc_link(label, u, v);
+    }
+  }
 }
 
 __global__ void __launch_bounds__(256) k_cc_hook(Geo g, uint32_t *label) {
   for (uint64_t e = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; e < g.C; e += (uint64_t)gridDim.x * blockDim.x) {
     const uint64_t k = g.slots[e];
     if (k == kEmpty || is_guard(k)) continue;
-    uint32_t a = (uint32_t)(k >> 32), b = (uint32_t)(k & 0xFFFFFFFFull);
-    if (a == b) continue;
-    for (;;) {
-      a = cc_find(label, a);
-      b = cc_find(label, b);
-      if (a == b) break;
-      if (a < b) {
-        uint32_t t = a; a = b; b = t;
-      }
-      // hook the larger root under the smaller one
-      const uint32_t old = atomicCAS(&label[a], a, b);
-      if (old == a) break;
-      a = old;
-    }
+    const uint32_t a = (uint32_t)(k >> 32), b = (uint32_t)(k & 0xFFFFFFFFull);
+    if (a != b) cc_link(label, a, b);
   }
 }
 
@@ -390,6 +453,10 @@ void launch_cc(const Geo &g, uint32_t *label, cudaStream_t s) {
   const uint32_t vb = nb(g.V, 256, 152 * 8);
   note_launch();
   k_cc_init<<<vb, 256, 0, s>>>(label, g.V);
+  note_launch();
+  k_cc_sample<<<vb, 256, 0, s>>>(g, label);
+  note_launch();
+  k_cc_compress<<<vb, 256, 0, s>>>(label, g.V);
   note_launch();
   k_cc_hook<<<nb(g.C, 256, 152 * 16), 256, 0, s>>>(g, label);
   note_launch();

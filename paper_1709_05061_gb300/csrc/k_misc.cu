@@ -162,6 +162,7 @@ __global__ void k_tree_level(Geo g, uint32_t i) {
 __global__ void k_zero_total(Ctl *ctl) { ctl->total = 0; }
 
 void launch_rebuild_indexes(const Geo &g, Ctl *ctl, cudaStream_t s) {
+  if (!g.raw) launch_degrees(g, g.deg, s);
   note_launch();
   k_zero_total<<<1, 1, 0, s>>>(ctl);
   note_launch();
@@ -230,6 +231,26 @@ __global__ void k_check_tree(Geo g, uint32_t *code) {
   if (bad) atomicOr(code, bad);
 }
 
+// every vertex's kept out-degree equals the stored edges of its row
+__global__ void k_check_degrees(Geo g, uint32_t *code) {
+  const uint32_t lane = lane_id();
+  uint32_t bad = 0;
+  const uint32_t nw = gridDim.x * (blockDim.x >> 5);
+  for (uint32_t u = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); u < g.V; u += nw) {
+    const uint32_t r = g.row_end[u];
+    const uint64_t beg = u ? (uint64_t)g.row_end[u - 1] + 1 : 0, end = r;
+    if (end > g.C || beg > end) {
+      bad |= 64;
+      continue;
+    }
+    uint32_t c = 0;
+    for (uint64_t e = beg + lane; e < end; e += 32) c += g.slots[e] != kEmpty;
+    c = warp_sum(c);
+    if (c != g.deg[u]) bad |= 64;
+  }
+  if (bad && lane == 0) atomicOr(code, bad);
+}
+
 // every vertex has its guard exactly where row_end says
 __global__ void k_check_guards(Geo g, uint32_t *code) {
   uint32_t bad = 0;
@@ -255,6 +276,8 @@ void launch_check(const Geo &g, Ctl *ctl, uint32_t *code, cudaStream_t s) {
   if (!g.raw) {
     note_launch();
     k_check_guards<<<nblocks(g.V, 256, 152 * 8), 256, 0, s>>>(g, code);
+    note_launch();
+    k_check_degrees<<<nblocks(g.V, 8, 152 * 16), 256, 0, s>>>(g, code);
   }
   note_launch();
   k_check_total<<<1, 1, 0, s>>>(ctl, code, sum);

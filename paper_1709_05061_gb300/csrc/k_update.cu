@@ -104,6 +104,10 @@ __global__ void k_leaf_pass(Geo g, Ctl *ctl, Work w, uint32_t per_warp, int rest
       nins += __popc(bs);
       ndel += __popc(__ballot_sync(0xFFFFFFFFu, dl));
       if (act) w.eflag[e] = dl ? 1 : (sv ? 2 : 0);
+      if (!g.raw) {
+        degree_delta(g.deg, sv && !is_guard(key), key, 1);
+        degree_delta(g.deg, dl, key, -1);
+      }
     }
     __syncwarp();
     const uint32_t cnt_del = nv - ndel;
@@ -274,9 +278,11 @@ __global__ void __launch_bounds__(256) k_leaf64(Geo g, Ctl *ctl, Work w) {
         g.cnt[j] = nkept;
       }
     }
-    if (act) {
-      const bool dl = tag && found;
-      w.eflag[rs + lane] = dl ? 1 : (sv ? (fits ? 1 : 2) : 0);
+    const bool dl = act && tag && found;
+    if (act) w.eflag[rs + lane] = dl ? 1 : (sv ? (fits ? 1 : 2) : 0);
+    if (!g.raw) {
+      degree_delta(g.deg, sv && !is_guard(key), key, 1);
+      degree_delta(g.deg, dl, key, -1);
     }
     if (lane == 0) {
       w.rdelta[r] = (int32_t)nins - (int32_t)ndel;
