@@ -173,7 +173,7 @@ int gpma_capacity(gpma_t h, uint64_t *out);
 /* Device-side consistency check of the array and its indexes.  *code = 0 when
  * all hold, else a bit set: 1 keys not strictly increasing, 2 a leaf count or
  * first-key index is stale, 4 a leaf above its bound, 8 a guard index is stale,
- * 16 a count-tree node is stale, 32 the total count is stale, 64 an out-degree is
+ * 16 a merge mark was left set, 32 the total count is stale, 64 an out-degree is
  * stale.  Waits. */
 int gpma_check(gpma_t h, uint32_t *code, void *stream);
 

@@ -125,7 +125,7 @@ struct GraphCache {
   };
   static constexpr int kEntries = 8;
   Entry e[kEntries];
-  cudaStream_t cap = nullptr;
+  cudaStream_t cap = nullptr, cap2 = nullptr;
   uint64_t tick = 0;
   bool enabled = true;
   Entry *find(uint64_t bucket, uint64_t epoch, bool stats) {
@@ -150,6 +150,7 @@ struct GraphCache {
     for (auto &x : e)
       if (x.exec) cudaGraphExecDestroy(x.exec);
     if (cap) cudaStreamDestroy(cap);
+    if (cap2) cudaStreamDestroy(cap2);
   }
 };
 
@@ -410,6 +411,96 @@ int do_resize(gpma *h, uint64_t total, cudaStream_t s) {
   return cuda_ok(h);
 }
 
+__global__ void k_gate(const Ctl *ctl, cudaGraphConditionalHandle cond) {
+  cudaGraphSetConditional(cond, (ctl->err == 0 && ctl->nesc > 0) ? 1u : 0u);
+}
+
+// Capture the part of a batch after k_prep as one graph, grids sized for `nb`
+// keys.  The escalation (pending inserts, count tree, merge levels, outermost
+// segments, segment merge) sits in the body of an IF node that runs only when
+// some leaf could not take its inserts, which a sliding window rarely produces.
+bool capture_update(gpma *h, FrontArgs &f, uint32_t nb, bool stats, GraphCache::Entry **out) {
+  GraphCache &gc = *h->graphs;
+  if (!gc.cap && cudaStreamCreateWithFlags(&gc.cap, cudaStreamNonBlocking) != cudaSuccess) return false;
+  if (!gc.cap2 && cudaStreamCreateWithFlags(&gc.cap2, cudaStreamNonBlocking) != cudaSuccess) return false;
+  cudaGraph_t graph = nullptr;
+  if (cudaGraphCreate(&graph, 0) != cudaSuccess) return false;
+  cudaGraphConditionalHandle cond;
+  bool ok = cudaGraphConditionalHandleCreate(&cond, graph, 0, cudaGraphCondAssignDefault) == cudaSuccess;
+  const uint64_t l0 = launch_count();
+  ok = ok && cudaStreamBeginCaptureToGraph(gc.cap, graph, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal) ==
+                 cudaSuccess;
+  if (!ok) {
+    cudaGraphDestroy(graph);
+    return false;
+  }
+  launch_sort(f, nb, gc.cap);
+  launch_leaf_pass(h->geo, h->ctl, h->w, nb, gc.cap);
+  note_launch();
+  k_gate<<<1, 1, 0, gc.cap>>>(h->ctl, cond);
+  cudaStreamCaptureStatus cs;
+  cudaGraph_t cg = nullptr;
+  const cudaGraphNode_t *deps = nullptr;
+  size_t ndeps = 0;
+  ok = cudaStreamGetCaptureInfo(gc.cap, &cs, nullptr, &cg, &deps, nullptr, &ndeps) == cudaSuccess;
+  cudaGraphNode_t cnode = nullptr;
+  cudaGraph_t body = nullptr;
+  if (ok) {
+    // zero-initialised storage: the parameter union has no default constructor
+    alignas(cudaGraphNodeParams) unsigned char raw[sizeof(cudaGraphNodeParams)] = {};
+    cudaGraphNodeParams *p = reinterpret_cast<cudaGraphNodeParams *>(raw);
+    p->type = cudaGraphNodeTypeConditional;
+    p->conditional.handle = cond;
+    p->conditional.type = cudaGraphCondTypeIf;
+    p->conditional.size = 1;
+    ok = cudaGraphAddNode(&cnode, cg, deps, nullptr, ndeps, p) == cudaSuccess;
+    if (ok) body = p->conditional.phGraph_out[0];
+  }
+  ok = ok && cudaStreamUpdateCaptureDependencies(gc.cap, &cnode, nullptr, 1, cudaStreamSetCaptureDependencies) ==
+                 cudaSuccess;
+  if (ok && cudaStreamBeginCaptureToGraph(gc.cap2, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal) ==
+                cudaSuccess) {
+    launch_pending(h->geo, h->ctl, h->w, nb, gc.cap2);
+    launch_tree_rebuild(h->geo, h->ctl, h->w, nb, gc.cap2);
+    launch_esc_level(h->geo, h->ctl, h->w, nb, false, gc.cap2);
+    launch_esc_top(h->geo, h->ctl, h->w, nb, gc.cap2);
+    launch_segments(h->geo, h->ctl, h->w, nb, gc.cap2);
+    launch_segment_merge(h->geo, h->geo, h->ctl, h->w, h->scratch_cap, h->geo.nleaves, h->scratch, h->vbuf,
+                         h->partials, false, gc.cap2);
+    cudaGraph_t body_out = nullptr;
+    ok = cudaStreamEndCapture(gc.cap2, &body_out) == cudaSuccess;
+  } else {
+    ok = false;
+  }
+  if (stats) launch_stats(h->geo, h->ctl, h->w, nb, gc.cap);
+  note_launch();
+  k_finish<<<1, 1, 0, gc.cap>>>(h->ctl);
+  cudaGraph_t done = nullptr;
+  const bool ended = cudaStreamEndCapture(gc.cap, &done) == cudaSuccess;
+  const uint64_t kernels = launch_count() - l0;
+  unnote_launches(kernels);
+  if (!ok || !ended) {
+    cudaGetLastError();
+    cudaGraphDestroy(graph);
+    return false;
+  }
+  GraphCache::Entry *ge = gc.victim();
+  const cudaError_t ie = cudaGraphInstantiate(&ge->exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (ie != cudaSuccess) {
+    cudaGetLastError();
+    ge->exec = nullptr;
+    return false;
+  }
+  ge->bucket = 0;
+  ge->epoch = h->alloc_epoch;
+  ge->stats = stats;
+  ge->kernels = kernels;  // an upper bound: the IF body runs only when needed
+  ge->used = ++gc.tick;
+  *out = ge;
+  return true;
+}
+
 int update(gpma *h, const uint64_t *ins, uint64_t n_ins, const uint64_t *del, uint64_t n_del, cudaStream_t s,
            gpma_stats *stats, bool allow_guards) {
   if (h->poisoned) return h->poisoned;
@@ -470,38 +561,8 @@ int update(gpma *h, const uint64_t *ins, uint64_t n_ins, const uint64_t *del, ui
     const uint32_t nb = (uint32_t)bucket;
     GraphCache::Entry *ge = h->graphs->find(bucket, h->alloc_epoch, stats != nullptr);
     if (!ge) {
-      GraphCache &gc = *h->graphs;
-      if (!gc.cap && cudaStreamCreateWithFlags(&gc.cap, cudaStreamNonBlocking) != cudaSuccess) return poison(h, GPMA_EDEVICE);
-      const uint64_t l0 = launch_count();
-      cudaGraph_t graph = nullptr;
-      if (cudaStreamBeginCapture(gc.cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return poison(h, GPMA_EDEVICE);
-      launch_sort(f, nb, gc.cap);
-      launch_leaf_pass(h->geo, h->ctl, h->w, nb, gc.cap);
-      launch_propagate(h->geo, h->ctl, h->w, nb, gc.cap);
-      launch_pending(h->geo, h->ctl, h->w, nb, gc.cap);
-      launch_esc_level(h->geo, h->ctl, h->w, nb, false, gc.cap);
-      launch_esc_top(h->geo, h->ctl, h->w, nb, gc.cap);
-      launch_segments(h->geo, h->ctl, h->w, nb, gc.cap);
-      launch_segment_merge(h->geo, h->geo, h->ctl, h->w, h->scratch_cap, h->geo.nleaves, h->scratch, h->vbuf,
-                           h->partials, false, gc.cap);
-      if (stats) launch_stats(h->geo, h->ctl, h->w, nb, gc.cap);
-      note_launch();
-      k_finish<<<1, 1, 0, gc.cap>>>(h->ctl);
-      const uint64_t kernels = launch_count() - l0;
-      unnote_launches(kernels);
-      if (cudaStreamEndCapture(gc.cap, &graph) != cudaSuccess) return poison(h, GPMA_EDEVICE);
-      ge = gc.victim();
-      cudaError_t ie = cudaGraphInstantiate(&ge->exec, graph, 0);
-      cudaGraphDestroy(graph);
-      if (ie != cudaSuccess) {
-        ge->exec = nullptr;
-        return poison(h, GPMA_EDEVICE);
-      }
+      if (!capture_update(h, f, nb, stats != nullptr, &ge)) return poison(h, GPMA_EDEVICE);
       ge->bucket = bucket;
-      ge->epoch = h->alloc_epoch;
-      ge->stats = stats != nullptr;
-      ge->kernels = kernels;
-      ge->used = ++gc.tick;
     }
     if (cudaGraphLaunch(ge->exec, s) != cudaSuccess) return poison(h, GPMA_EDEVICE);
     for (uint64_t k = 0; k < ge->kernels; k++) note_launch();
@@ -514,10 +575,10 @@ int update(gpma *h, const uint64_t *ins, uint64_t n_ins, const uint64_t *del, ui
     {
       Phase ph(h->prof, GPMA_PROF_LEAF, s);
       launch_leaf_pass(h->geo, h->ctl, h->w, n32, s);
-      launch_propagate(h->geo, h->ctl, h->w, n32, s);
     }
     Phase esc(h->prof, GPMA_PROF_ESCALATE, s);
     launch_pending(h->geo, h->ctl, h->w, n32, s);
+    launch_tree_rebuild(h->geo, h->ctl, h->w, n32, s);
     launch_esc_level(h->geo, h->ctl, h->w, n32, may_fail, s);
     if ((rc = cuda_ok(h))) return rc;
     if (may_fail) {

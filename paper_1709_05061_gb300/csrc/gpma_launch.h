@@ -71,7 +71,9 @@ void launch_sort(const FrontArgs &f, uint64_t nb, cudaStream_t s);
 
 // k_update.cu
 void launch_leaf_pass(const Geo &g, Ctl *ctl, const Work &w, uint32_t n, cudaStream_t s);
-void launch_propagate(const Geo &g, Ctl *ctl, const Work &w, uint32_t n, cudaStream_t s);
+// levels 1..h of the count tree from the leaf counts and this batch's pending
+// inserts (run after launch_pending; does nothing when no insert is pending)
+void launch_tree_rebuild(const Geo &g, Ctl *ctl, const Work &w, uint32_t n, cudaStream_t s);
 void launch_pending(const Geo &g, Ctl *ctl, const Work &w, uint32_t n, cudaStream_t s);
 // merge level of every pending run; with may_fail a run no level admits is counted in
 // Ctl::nfail instead of being an error

@@ -217,17 +217,13 @@ __global__ void k_check_leaves(Geo g, uint32_t *code, unsigned long long *sum) {
   if (lane_id() == 0 && acc) atomicAdd(sum, (unsigned long long)acc);
 }
 
+// the merge marks are all clear between batches (the count tree itself is
+// rebuilt whenever a batch needs it)
 __global__ void k_check_tree(Geo g, uint32_t *code) {
   uint32_t bad = 0;
-  for (uint32_t i = 1; i <= g.h; i++) {
-    const uint64_t nodes = g.nleaves >> i;
-    for (uint64_t s = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; s < nodes; s += (uint64_t)gridDim.x * blockDim.x) {
-      uint32_t a = i == 1 ? g.cnt[2 * s] : g.tree[g.tree_off[i - 1] + 2 * s];
-      uint32_t b = i == 1 ? g.cnt[2 * s + 1] : g.tree[g.tree_off[i - 1] + 2 * s + 1];
-      if (g.tree[g.tree_off[i] + s] != a + b) bad |= 16;
-      if (g.mark[g.tree_off[i] + s] != 0) bad |= 16;
-    }
-  }
+  const uint64_t total = g.nleaves > 1 ? g.nleaves - 1 : 0;
+  for (uint64_t s = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; s < total; s += (uint64_t)gridDim.x * blockDim.x)
+    if (g.mark[s] != 0) bad |= 16;
   if (bad) atomicOr(code, bad);
 }
 

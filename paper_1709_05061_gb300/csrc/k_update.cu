@@ -13,10 +13,10 @@
 // segment, erasing any merge inside it).  So:
 //   k_leaf_pass    one warp per touched leaf: presence filter, lazy deletes, and the
 //                  level-0 TryInsert+ (merge + even re-dispatch inside the leaf)
-//   k_propagate    add every leaf's count change to its ancestors in the count tree
-//   k_pending / k_eruns / k_esc_level / k_esc_top / k_segs
-//                  inserts that did not fit their leaf: find their merge level,
-//                  the outermost merged segments and their pending inserts
+//   k_pending / k_eruns / k_tree_* / k_esc_level / k_esc_top / k_segs
+//                  inserts that did not fit their leaf (only then): rebuild the
+//                  count tree, find their merge level, the outermost merged
+//                  segments and their pending inserts
 //   segment merge  gather valid keys of those segments, merge with the pending
 //                  inserts (merge path), re-dispatch evenly, rewrite the counts
 #include "gpma_dev.cuh"
@@ -171,6 +171,8 @@ __global__ void k_leaf_pass(Geo g, Ctl *ctl, Work w, uint32_t per_warp, int rest
   if (lane == 0) {
     if (acc_ins) atomicAdd((unsigned long long *)&ctl->n_inserted, (unsigned long long)acc_ins);
     if (acc_del) atomicAdd((unsigned long long *)&ctl->n_deleted, (unsigned long long)acc_del);
+    if (acc_ins != acc_del)  // logical key count (pending inserts included), two's complement
+      atomicAdd((unsigned long long *)&ctl->total, (unsigned long long)(acc_ins - acc_del));
     if (acc_m0) atomicAdd(&ctl->n_merged0, acc_m0);
     if (acc_esc) atomicAdd(&ctl->nesc, acc_esc);
   }
@@ -297,56 +299,65 @@ __global__ void __launch_bounds__(256) k_leaf64(Geo g, Ctl *ctl, Work w) {
   if (lane == 0) {
     if (acc_ins) atomicAdd((unsigned long long *)&ctl->n_inserted, (unsigned long long)acc_ins);
     if (acc_del) atomicAdd((unsigned long long *)&ctl->n_deleted, (unsigned long long)acc_del);
+    if (acc_ins != acc_del)  // logical key count (pending inserts included), two's complement
+      atomicAdd((unsigned long long *)&ctl->total, (unsigned long long)(acc_ins - acc_del));
     if (acc_m0) atomicAdd(&ctl->n_merged0, acc_m0);
     if (acc_esc) atomicAdd(&ctl->nesc, acc_esc);
     if (acc_long) atomicAdd(&ctl->nlong, acc_long);
   }
 }
 
-// ---- count tree: add each touched leaf's change to its ancestors ----------------------------
-// A block takes 1024 consecutive runs (sorted by leaf); per level it adds one
-// aggregated value per distinct ancestor, so the root sees one atomic per block.
-__global__ void __launch_bounds__(1024) k_propagate(Geo g, Ctl *ctl, const uint32_t *__restrict__ rleaf,
-                                                    const int32_t *__restrict__ rdelta) {
-  __shared__ int32_t P[1024];
-  __shared__ uint32_t lf[1024];
-  __shared__ int32_t wsum[32];
+// ---- count tree, rebuilt only when some inserts did not fit their leaf ----------------------
+// Levels 1..h of the tree hold logical counts for the merge-level test: valid
+// keys of every segment plus the inserts still pending in this batch.  Stage A:
+// one block per 4096 leaves builds the levels inside its range in shared memory;
+// stage B: one block builds the levels above from the block sums; then every
+// pending run adds its inserts to its ancestors.
+constexpr uint32_t kTreeSpan = 4096;
+
+__global__ void __launch_bounds__(1024) k_tree_a(Geo g, Ctl *ctl) {
+  __shared__ uint32_t sv[kTreeSpan];
+  if (ctl->err || ctl->nesc == 0) return;
+  const uint64_t span = g.nleaves < kTreeSpan ? g.nleaves : kTreeSpan;
+  const uint64_t base = (uint64_t)blockIdx.x * span;
+  for (uint32_t t = threadIdx.x; t < span; t += blockDim.x) sv[t] = g.cnt[base + t];
+  __syncthreads();
+  uint32_t i = 1;
+  for (uint64_t nodes = span >> 1; nodes >= 1 && i <= g.h; nodes >>= 1, ++i) {
+    uint32_t v[4];
+    uint32_t k = 0;
+    for (uint32_t t = threadIdx.x; t < nodes; t += blockDim.x) v[k++] = sv[2 * t] + sv[2 * t + 1];
+    __syncthreads();
+    k = 0;
+    for (uint32_t t = threadIdx.x; t < nodes; t += blockDim.x) {
+      sv[t] = v[k];
+      g.tree[g.tree_off[i] + (base >> i) + t] = v[k];
+      ++k;
+    }
+    __syncthreads();
+  }
+}
+
+// levels above the blocks' span, one level at a time through global memory
+__global__ void __launch_bounds__(1024) k_tree_b(Geo g, Ctl *ctl) {
+  if (ctl->err || ctl->nesc == 0) return;
+  uint32_t first = 0;  // first level above a block's span
+  while ((1ull << first) < kTreeSpan && first < g.h) ++first;
+  for (uint32_t i = first + 1; i <= g.h; i++) {
+    const uint64_t nodes = g.nleaves >> i;
+    for (uint64_t t = threadIdx.x; t < nodes; t += blockDim.x)
+      g.tree[g.tree_off[i] + t] = g.tree[g.tree_off[i - 1] + 2 * t] + g.tree[g.tree_off[i - 1] + 2 * t + 1];
+    __syncthreads();
+  }
+}
+
+__global__ void k_tree_pend(Geo g, Ctl *ctl, Work w) {
   if (ctl->err) return;
-  const uint32_t nruns = ctl->nruns, lane = lane_id(), wid = threadIdx.x >> 5;
-  for (uint64_t c0 = (uint64_t)blockIdx.x * 1024; c0 < nruns; c0 += (uint64_t)gridDim.x * 1024) {
-    const uint64_t r = c0 + threadIdx.x;
-    const bool act = r < nruns;
-    const int32_t d = act ? rdelta[r] : 0;
-    const uint32_t leaf = act ? rleaf[r] : 0xFFFFFFFFu;
-    int32_t inc = warp_incl_scan(d);
-    if (lane == 31) wsum[wid] = inc;
-    __syncthreads();
-    if (wid == 0) {
-      int32_t v = wsum[lane];
-      wsum[lane] = warp_incl_scan(v) - v;
-    }
-    __syncthreads();
-    inc += wsum[wid];
-    P[threadIdx.x] = inc;
-    lf[threadIdx.x] = leaf;
-    __syncthreads();
-    if (threadIdx.x == 1023 && P[1023] != 0)
-      atomicAdd((unsigned long long *)&ctl->total, (unsigned long long)(long long)P[1023]);
-    const uint32_t cnt = (uint32_t)min((uint64_t)1024, nruns - c0);
-    if (act) {
-      for (uint32_t i = 1; i <= g.h; i++) {
-        const uint32_t node = leaf >> i;
-        if (threadIdx.x > 0 && (lf[threadIdx.x - 1] >> i) == node) continue;
-        uint32_t lo = threadIdx.x + 1, hi = cnt;  // end of this ancestor's runs in the block
-        while (lo < hi) {
-          uint32_t mid = (lo + hi) >> 1;
-          if ((lf[mid] >> i) > node) hi = mid; else lo = mid + 1;
-        }
-        int32_t s = P[lo - 1] - (threadIdx.x ? P[threadIdx.x - 1] : 0);
-        if (s) atomicAdd(&g.tree[g.tree_off[i] + node], (uint32_t)s);
-      }
-    }
-    __syncthreads();
+  const uint32_t ner = ctl->neruns;
+  for (uint32_t r = blockIdx.x * blockDim.x + threadIdx.x; r < ner; r += gridDim.x * blockDim.x) {
+    const uint32_t j = w.pleaf[w.erun[r]];
+    const uint32_t c = w.erun[r + 1] - w.erun[r];
+    for (uint32_t i = 1; i <= g.h; i++) atomicAdd(&g.tree[g.tree_off[i] + (j >> i)], c);
   }
 }
 
@@ -643,22 +654,6 @@ __global__ void k_seg_write(Geo dst, Ctl *ctl, Work w, SegArgs sa, const uint64_
   }
 }
 
-// counts of the tree nodes inside each rewritten segment (their share of n)
-__global__ void k_seg_tree(Geo dst, Ctl *ctl, Work w, SegArgs sa, const uint64_t *voff) {
-  if (ctl->err) return;
-  const uint64_t nlw = sa.whole ? dst.nleaves : ctl->nleafw;
-  for (uint64_t x = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; x < nlw; x += (uint64_t)gridDim.x * blockDim.x) {
-    const SegGeom s = seg_geom(w, sa, voff, ctl, x);
-    const uint64_t n = s.na + s.nb;
-    const uint64_t qmax = sa.whole ? s.top : s.top - 1;
-    for (uint64_t q = 1; q <= qmax; q++) {
-      if (s.t & ((1ull << q) - 1ull)) break;
-      uint64_t c = ((n * (s.t + (1ull << q))) >> s.top) - ((n * s.t) >> s.top);
-      dst.tree[dst.tree_off[q] + (s.dleaf >> q)] = (uint32_t)c;
-    }
-  }
-}
-
 // ---- statistics (only when the caller asks for them) -------------------------------------------
 __global__ void k_stats(Ctl *ctl, Work w) {
   const uint32_t nruns = ctl->nruns, nsegs = ctl->nsegs;
@@ -726,9 +721,17 @@ void launch_leaf_pass(const Geo &g, Ctl *ctl, const Work &w, uint32_t n, cudaStr
   k_leaf_pass<<<blocks_for(n, wpb, 152 * 16), wpb * 32, wpb * pw, s>>>(g, ctl, w, pw, fast);
 }
 
-void launch_propagate(const Geo &g, Ctl *ctl, const Work &w, uint32_t n, cudaStream_t s) {
+void launch_tree_rebuild(const Geo &g, Ctl *ctl, const Work &w, uint32_t n, cudaStream_t s) {
+  if (g.h == 0) return;
+  const uint64_t span = g.nleaves < kTreeSpan ? g.nleaves : kTreeSpan;
   note_launch();
-  k_propagate<<<blocks_for(n, 1024, 152 * 2), 1024, 0, s>>>(g, ctl, w.rleaf, w.rdelta);
+  k_tree_a<<<(uint32_t)(g.nleaves / span), 1024, 0, s>>>(g, ctl);
+  if ((1ull << g.h) > kTreeSpan) {
+    note_launch();
+    k_tree_b<<<1, 1024, 0, s>>>(g, ctl);
+  }
+  note_launch();
+  k_tree_pend<<<blocks_for(n, 256, 152 * 8), 256, 0, s>>>(g, ctl, w);
 }
 
 void launch_pending(const Geo &g, Ctl *ctl, const Work &w, uint32_t n, cudaStream_t s) {
@@ -792,8 +795,6 @@ void launch_segment_merge(const Geo &src, const Geo &dst, Ctl *ctl, const Work &
   const uint64_t dst_bound = whole ? dst.nleaves : nleafw_bound;
   note_launch();
   k_seg_write<<<blocks_for(dst_bound, wpb, 152 * 16), wpb * 32, wpb * pw, s>>>(dst, ctl, w, sa, voff, scratch, pw);
-  note_launch();
-  k_seg_tree<<<blocks_for(dst_bound, 256, 152 * 8), 256, 0, s>>>(dst, ctl, w, sa, voff);
 }
 
 }  // namespace gpk
