@@ -43,6 +43,9 @@ typedef struct gpma *gpma_t;
 
 #define GPMA_EMPTY 0xFFFFFFFFFFFFFFFFull
 #define GPMA_RAW_KEYS 1u   /* keys are opaque integers < 2^63: no guards, no analytics */
+#define GPMA_PLAIN_SEARCH 2u /* find leaves by binary search only (default: a learned two-stage
+                                linear model over the leaf pivots narrows the search; both
+                                give the same leaf, hence the same array) */
 #define GPMA_MAX_LEVELS 48
 
 /* Create-time parameters; a zero field takes the default.  Densities are whole
@@ -53,7 +56,7 @@ typedef struct gpma *gpma_t;
 typedef struct {
   uint32_t leaf_size; /* L: power of two in [2, 1024]; default 64 */
   uint32_t tau0_pct, tauh_pct, rho0_pct, rhoh_pct;
-  uint32_t flags;     /* GPMA_RAW_KEYS or 0 */
+  uint32_t flags;     /* GPMA_RAW_KEYS | GPMA_PLAIN_SEARCH, or 0 */
 } gpma_params;
 
 /* Optional device allocator.  alloc returns NULL on failure; both receive the

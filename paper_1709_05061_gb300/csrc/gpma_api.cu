@@ -191,6 +191,11 @@ struct gpma {
   Prof *prof;
   GraphCache *graphs;
   uint64_t alloc_epoch;
+  // learned leaf search (nullptr with GPMA_PLAIN_SEARCH)
+  ModelHead *mhead;
+  Piece *mpieces;
+  uint32_t *mtmp;
+  uint32_t since_train;
 };
 
 namespace {
@@ -381,6 +386,12 @@ int read_ctl(gpma *h, cudaStream_t s) {
   return GPMA_OK;
 }
 
+void train_model(gpma *h, cudaStream_t s) {
+  if (!h->mhead) return;
+  launch_train_model(h->geo, h->mhead, h->mpieces, h->mtmp, s);
+  h->since_train = 0;
+}
+
 // root resize (reading R7): every valid key and every pending insert spread over
 // the smallest taller array whose root bound holds them
 int do_resize(gpma *h, uint64_t total, cudaStream_t s) {
@@ -408,6 +419,7 @@ int do_resize(gpma *h, uint64_t total, cudaStream_t s) {
   free_arrays(h, &old, s);
   h->geo = g2;
   h->alloc_epoch++;
+  train_model(h, s);
   return cuda_ok(h);
 }
 
@@ -467,6 +479,7 @@ bool capture_update(gpma *h, FrontArgs &f, uint32_t nb, bool stats, GraphCache::
     launch_segments(h->geo, h->ctl, h->w, nb, gc.cap2);
     launch_segment_merge(h->geo, h->geo, h->ctl, h->w, h->scratch_cap, h->geo.nleaves, h->scratch, h->vbuf,
                          h->partials, false, gc.cap2);
+    if (h->mhead) launch_train_model(h->geo, h->mhead, h->mpieces, h->mtmp, gc.cap2);
     cudaGraph_t body_out = nullptr;
     ok = cudaStreamEndCapture(gc.cap2, &body_out) == cudaSuccess;
   } else {
@@ -521,20 +534,22 @@ int update(gpma *h, const uint64_t *ins, uint64_t n_ins, const uint64_t *del, ui
   pa.V = h->V;
   pa.raw = h->raw;
   pa.allow_guards = allow_guards ? 1 : 0;
-  uint32_t bits;
+  uint32_t bits;  // sorted bits of the compressed key (the tag is not sorted on)
   if (h->raw) {
-    bits = 64;
+    bits = 63;
   } else {
     uint32_t sb = bits_for(h->V - 1);
     if (sb < 1) sb = 1;
-    pa.db = bits_for(h->V);
-    bits = sb + pa.db + 1;
+    pa.db = allow_guards ? bits_for(h->V) : (bits_for(h->V - 1) ? bits_for(h->V - 1) : 1);
+    bits = sb + pa.db;
   }
   pa.npass = (bits + 7) / 8;
   pa.dbits = (bits + pa.npass - 1) / pa.npass;
 
   FrontArgs f;
   f.prep = pa;
+  f.mhead = h->mhead;
+  f.mpieces = h->mpieces;
   f.ins = ins;
   f.del = del;
   f.bufA = h->bufA;
@@ -550,6 +565,9 @@ int update(gpma *h, const uint64_t *ins, uint64_t n_ins, const uint64_t *del, ui
   f.run_leaf = h->w.rleaf;
   const uint32_t n32 = (uint32_t)n;
   Phase whole(h->prof, GPMA_PROF_UPDATE, s);
+  // level-0 merges move pivots only inside their leaves and the search widens
+  // its window when the model has drifted; retrain now and then all the same
+  if (h->mhead && ++h->since_train >= 64) train_model(h, s);
   launch_prep(f, s);
   // the root can only refuse inserts when the count might exceed its bound
   const bool may_fail = h->count_ub + n_ins > h->geo.maxc[h->geo.h];
@@ -559,10 +577,13 @@ int update(gpma *h, const uint64_t *ins, uint64_t n_ins, const uint64_t *del, ui
     uint64_t bucket = 2048;
     while (bucket < n) bucket <<= 1;
     const uint32_t nb = (uint32_t)bucket;
-    GraphCache::Entry *ge = h->graphs->find(bucket, h->alloc_epoch, stats != nullptr);
+    // the key layout of a guard batch differs: never share its graph
+    GraphCache::Entry *ge = h->graphs->find(bucket, h->alloc_epoch + (allow_guards ? (1ull << 62) : 0),
+                                           stats != nullptr);
     if (!ge) {
       if (!capture_update(h, f, nb, stats != nullptr, &ge)) return poison(h, GPMA_EDEVICE);
       ge->bucket = bucket;
+      ge->epoch = h->alloc_epoch + (allow_guards ? (1ull << 62) : 0);
     }
     if (cudaGraphLaunch(ge->exec, s) != cudaSuccess) return poison(h, GPMA_EDEVICE);
     for (uint64_t k = 0; k < ge->kernels; k++) note_launch();
@@ -608,6 +629,7 @@ int update(gpma *h, const uint64_t *ins, uint64_t n_ins, const uint64_t *del, ui
                            h->partials, false, s);
       esc.end();
       if (stats) launch_stats(h->geo, h->ctl, h->w, n32, s);
+      train_model(h, s);
     }
     note_launch();
     k_finish<<<1, 1, 0, s>>>(h->ctl);
@@ -740,6 +762,10 @@ int gpma_create(uint32_t n_vertices, const gpma_params *params, const gpma_alloc
   make_geo(h, 0, &h->geo);
   bool ok = alloc_arrays(h, &h->geo, s) && dalloc(h, &h->ctl, 1, s) && dalloc(h, &h->hist, 8 * 256, s) &&
             dalloc(h, &h->check_buf, 4, s);
+  if (ok && !(p.flags & GPMA_PLAIN_SEARCH)) {
+    ok = dalloc(h, &h->mhead, 1, s) && dalloc(h, &h->mpieces, kPieces, s) && dalloc(h, &h->mtmp, 2 * kPieces, s);
+    if (ok) ok = cudaMemsetAsync(h->mhead, 0, sizeof(ModelHead), s) == cudaSuccess;
+  }
   if (ok && !raw) ok = dalloc(h, &h->geo.row_end, h->V, s) && dalloc(h, &h->geo.deg, h->V, s);
   if (ok && !raw) ok = cudaMemsetAsync(h->geo.deg, 0, sizeof(uint32_t) * h->V, s) == cudaSuccess;
   if (ok) ok = cudaMallocHost(&h->h_ctl, sizeof(Ctl)) == cudaSuccess && cudaMallocHost(&h->h_counter, 16) == cudaSuccess;
@@ -782,7 +808,7 @@ int gpma_destroy(gpma_t h) {
   dfree(h, h->geo.row_end, s);
   dfree(h, h->geo.deg, s);
   free_work(h, s);
-  void *ptrs[] = {h->ctl, h->hist, h->scratch, h->vbuf, h->partials, h->cfx, h->y,
+  void *ptrs[] = {h->mhead, h->mpieces, h->mtmp, h->ctl, h->hist, h->scratch, h->vbuf, h->partials, h->cfx, h->y,
                   h->dsum, h->q0,  h->q1,  h->q2,    h->counter, h->check_buf, h->guards, h->pr_partials,
                   h->pr_counter};
   for (void *p : ptrs) dfree(h, p, s);
@@ -947,6 +973,7 @@ int gpma_import_layout(gpma_t h, const uint64_t *d_slots, uint64_t capacity, voi
   h->geo = g2;
   h->alloc_epoch++;
   h->count_ub = h->h_ctl->total;
+  train_model(h, s);
   return cuda_ok(h);
 }
 

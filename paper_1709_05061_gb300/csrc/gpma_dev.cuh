@@ -111,11 +111,13 @@ __device__ __forceinline__ uint32_t lower_bound_dev(const T *a, uint32_t n, T k)
 }
 
 // Leaf of key k on the current array: the last leaf whose smallest valid key is
-// <= k, leaf 0 if none.  Binary search over the pivots F with empty leaves
-// skipped forward (an empty leaf takes the pivot of the next non-empty one).
-__device__ __forceinline__ uint32_t leaf_search(const uint64_t *__restrict__ F, uint64_t nleaves,
-                                                uint64_t k) {
-  uint64_t lo = 0, hi = nleaves;  // find p = first leaf whose effective pivot is > k
+// <= k, leaf 0 if none.  With eff(j) = smallest valid key of the first non-empty
+// leaf at or after j (+inf past the end), eff is non-decreasing and the leaf is
+// p - 1 for p = the first j with eff(j) > k.  search_first_above finds p inside
+// [lo, hi] given eff(lo - 1) <= k (or lo = 0) and eff(hi) > k (or hi = nleaves);
+// empty leaves are skipped forward.
+__device__ __forceinline__ uint64_t search_first_above(const uint64_t *__restrict__ F, uint64_t lo, uint64_t hi,
+                                                       uint64_t k) {
   while (lo < hi) {
     uint64_t mid = (lo + hi) >> 1, j = mid;
     uint64_t f = kEmpty;
@@ -127,7 +129,86 @@ __device__ __forceinline__ uint32_t leaf_search(const uint64_t *__restrict__ F, 
     if (j >= hi || f > k) hi = mid;
     else lo = j + 1;
   }
-  return lo ? (uint32_t)(lo - 1) : 0u;
+  return lo;
+}
+
+__device__ __forceinline__ uint32_t leaf_search(const uint64_t *__restrict__ F, uint64_t nleaves, uint64_t k) {
+  const uint64_t p = search_first_above(F, 0, nleaves, k);
+  return p ? (uint32_t)(p - 1) : 0u;
+}
+
+// ---- learned leaf search (two-stage linear model over the pivots) -----------------------------
+// Root: piece = floor((k - kmin) * rscale), monotone in k.  Piece i: the leaves its
+// training pivots fell in span [first, last]; every key routed to it has its
+// leaf in [lo, hi] (lo = last leaf of the pieces before it); the piece predicts
+// first + (k - kb) * slope with training error err.  The search window is
+// checked against the current pivots and widened until it brackets the answer,
+// so the result equals leaf_search exactly whatever the model's staleness.
+constexpr uint32_t kPieces = 4096;
+
+struct Piece {
+  uint64_t kb;      // pivot of the piece's first training leaf
+  uint32_t lo, hi;  // answer bracket at training time
+  uint32_t first;   // first training leaf (kNoLeaf: no leaf routed here)
+  uint32_t err;     // max |prediction - leaf| over the training leaves
+  float slope;
+  uint32_t pad;
+};
+
+struct ModelHead {
+  uint64_t kmin;
+  float rscale;
+  uint32_t valid;
+  uint64_t kmax;
+};
+
+constexpr uint32_t kNoLeaf = 0xFFFFFFFFu;
+
+__device__ __forceinline__ uint32_t model_route(const ModelHead &m, uint64_t k) {
+  const float d = (float)(k > m.kmin ? k - m.kmin : 0ull) * m.rscale;
+  const uint32_t p = d >= (float)(kPieces - 1) ? kPieces - 1 : (uint32_t)d;
+  return p;
+}
+
+// eff(j) <= k ?
+__device__ __forceinline__ bool eff_at_most(const uint64_t *__restrict__ F, uint64_t nleaves, uint64_t j, uint64_t k) {
+  for (; j < nleaves; ++j) {
+    const uint64_t f = __ldg(F + j);
+    if (f != kEmpty) return f <= k;
+  }
+  return false;
+}
+
+__device__ __forceinline__ uint32_t learned_leaf_search(const ModelHead &m, const Piece *__restrict__ pieces,
+                                                        const uint64_t *__restrict__ F, uint64_t nleaves,
+                                                        uint64_t k) {
+  const Piece pc = pieces[model_route(m, k)];
+  // candidate window for p (= answer + 1)
+  int64_t pred = (int64_t)pc.lo;
+  if (pc.first != kNoLeaf) {
+    const float d = (float)(k > pc.kb ? k - pc.kb : 0ull) * pc.slope;
+    pred = (int64_t)pc.first + (int64_t)d;
+    if (pred < (int64_t)pc.lo) pred = pc.lo;
+    if (pred > (int64_t)pc.hi) pred = pc.hi;
+  }
+  int64_t a = pred - (int64_t)pc.err, b = pred + (int64_t)pc.err + 2;
+  if (a < 0) a = 0;
+  if (a > (int64_t)nleaves) a = (int64_t)nleaves;  // a model trained on another geometry
+  if (b > (int64_t)nleaves) b = (int64_t)nleaves;
+  if (b < a) b = a;
+  // widen until eff(a - 1) <= k (or a = 0) and eff(b) > k (or b = nleaves)
+  uint64_t step = pc.err + 2;
+  while (a > 0 && !eff_at_most(F, nleaves, (uint64_t)(a - 1), k)) {
+    a = a > (int64_t)step ? a - (int64_t)step : 0;
+    step <<= 1;
+  }
+  step = pc.err + 2;
+  while (b < (int64_t)nleaves && eff_at_most(F, nleaves, (uint64_t)b, k)) {
+    b = b + (int64_t)step < (int64_t)nleaves ? b + (int64_t)step : (int64_t)nleaves;
+    step <<= 1;
+  }
+  const uint64_t p = search_first_above(F, (uint64_t)a, (uint64_t)b, k);
+  return p ? (uint32_t)(p - 1) : 0u;
 }
 
 // ---- single-pass look-back (tiles take tickets in launch order) -------------------

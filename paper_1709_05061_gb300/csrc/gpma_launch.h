@@ -25,6 +25,8 @@ struct PrepArgs {
 
 struct FrontArgs {
   PrepArgs prep;
+  const ModelHead *mhead;  // learned leaf search (nullptr: plain binary search)
+  const Piece *mpieces;
   const uint64_t *ins, *del;
   uint64_t *bufA, *bufB;  // sort ping-pong
   uint32_t *hist;         // npass * 256
@@ -88,6 +90,9 @@ void launch_stats(const Geo &g, Ctl *ctl, const Work &w, uint32_t n, cudaStream_
 void launch_segment_merge(const Geo &src, const Geo &dst, Ctl *ctl, const Work &w, uint64_t scratch_cap,
                           uint64_t nleafw_bound, uint64_t *scratch, uint32_t *voff, uint64_t *partials,
                           bool whole, cudaStream_t s);
+
+// k_model.cu: train the learned leaf search on the current pivots (tmp >= 2 * kPieces)
+void launch_train_model(const Geo &g, ModelHead *head, Piece *pieces, uint32_t *tmp, cudaStream_t s);
 
 // k_misc.cu
 void launch_rebuild_indexes(const Geo &g, Ctl *ctl, cudaStream_t s);  // cnt, F, tree, row_end, total

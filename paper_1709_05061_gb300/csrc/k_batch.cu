@@ -5,7 +5,8 @@
 //                 sortable word, build the radix histograms of every pass
 //   k_sort_pass   one stable LSD radix pass (single pass per digit with look-back)
 //   k_keep        unique + insert/delete cancellation on the sorted words, then the
-//                 leaf search of every surviving key (single-pass compaction)
+//                 leaf search of every surviving key (learned model when trained,
+//                 else binary search; both give the same leaf)
 //   k_runs        heads of the runs of equal leaf (single-pass compaction)
 #include "gpma_dev.cuh"
 #include "gpma_launch.h"
@@ -14,24 +15,33 @@
 namespace gpk {
 
 constexpr int kSortThreads = 256;
-constexpr int kSortItems = 16;  // keys per thread per pass
-constexpr int kSortTile = kSortThreads * kSortItems;
+// keys per thread per pass: 8 for small batches (more tiles in flight, fewer
+// registers), 16 for large ones (half the tiles on the look-back chain)
+constexpr int kSortItemsSmall = 8, kSortItemsLarge = 16;
+constexpr uint64_t kSortLargeFrom = 1ull << 19;
+constexpr int kSortTile = kSortThreads * kSortItemsSmall;  // status words are sized for the small tile
 
 // ---- key compression -----------------------------------------------------------------
-// Graph mode: word = ((src << db) | d) << 1 | tag with d = dst, or d = V for a guard
-// (so a guard sorts after every edge of its row); db = bits(V), sb = bits(V-1).
-// Raw mode: word = key << 1 | tag.  Order of words = order of (key, tag).
+// Graph mode: word = (src << db) | d with d = dst, or d = V for a guard (so a
+// guard sorts after every edge of its row); db = bits(V) when guards may occur,
+// else bits(V-1).  Raw mode: word = key.  The insert/delete tag rides in bit 63,
+// outside the sorted digits: the sort is stable and inserts precede deletes in
+// its input, so words of equal key keep inserts first.
+constexpr uint64_t kTagBit = 1ull << 63;
+
 __device__ __forceinline__ uint64_t compress(uint64_t key, uint32_t tag, const PrepArgs &a) {
-  if (a.raw) return (key << 1) | tag;
+  const uint64_t t = tag ? kTagBit : 0ull;
+  if (a.raw) return key | t;
   uint64_t src = key >> 32, dst = key & 0xFFFFFFFFull;
   uint64_t d = (dst == 0xFFFFFFFFull) ? (uint64_t)a.V : dst;
-  return (((src << a.db) | d) << 1) | tag;
+  return ((src << a.db) | d) | t;
 }
 
 __device__ __forceinline__ uint64_t expand(uint64_t w, const PrepArgs &a) {
-  if (a.raw) return w >> 1;
-  uint64_t d = (w >> 1) & ((1ull << a.db) - 1ull);
-  uint64_t src = w >> (a.db + 1);
+  w &= ~kTagBit;
+  if (a.raw) return w;
+  uint64_t d = w & ((1ull << a.db) - 1ull);
+  uint64_t src = w >> a.db;
   uint64_t dst = (d == (uint64_t)a.V) ? 0xFFFFFFFFull : d;
   return (src << 32) | dst;
 }
@@ -77,8 +87,9 @@ __global__ void __launch_bounds__(256) k_prep(PrepArgs a, const uint64_t *__rest
     bad |= !ok;
     uint64_t w = ok ? compress(key, tag, a) : 0ull;
     out[i] = w;
+    const uint64_t kw = w & ~kTagBit;
     for (uint32_t p = 0; p < a.npass; p++)
-      atomicAdd(&sh[p * 256 + (uint32_t)((w >> (p * a.dbits)) & mask)], 1u);
+      atomicAdd(&sh[p * 256 + (uint32_t)((kw >> (p * a.dbits)) & mask)], 1u);
   }
   if (__any_sync(0xFFFFFFFFu, bad) && lane_id() == 0) atomicOr(&ctl->err, kErrKey);
   __syncthreads();
@@ -86,9 +97,10 @@ __global__ void __launch_bounds__(256) k_prep(PrepArgs a, const uint64_t *__rest
     if (sh[i]) atomicAdd(&hist[i], sh[i]);
 }
 
-// One stable LSD pass.  A tile is 16 rounds x 256 keys; warp w owns the
-// contiguous sub-tile [w*512, w*512+512) so ranks inside a warp need no block
-// barrier; tiles are ordered by ticket and chained by a per-digit look-back.
+// One stable LSD pass.  A tile is ITEMS rounds x 256 keys; warp w owns the
+// contiguous sub-tile [w*32*ITEMS, (w+1)*32*ITEMS) so ranks inside a warp need no
+// block barrier; tiles are ordered by ticket and chained by a per-digit look-back.
+template <int kSortItems>
 __global__ void __launch_bounds__(kSortThreads) k_sort_pass(const uint64_t *__restrict__ src,
                                                             uint64_t *__restrict__ dst, const uint32_t *hist,
                                                             uint64_t *status, Ctl *ctl, uint32_t pass,
@@ -104,7 +116,7 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_pass(const uint64_t *__re
   if (threadIdx.x == 0) s_tile = atomicAdd(&ctl->ticket[pass], 1u);
   __syncthreads();
   const uint32_t tile = s_tile;
-  const uint64_t base = (uint64_t)tile * kSortTile + w * (kSortItems * 32);
+  const uint64_t base = (uint64_t)tile * (kSortThreads * kSortItems) + w * (kSortItems * 32);
   uint64_t key[kSortItems];
   uint32_t rank[kSortItems];
   uint32_t dig[kSortItems];
@@ -113,7 +125,7 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_pass(const uint64_t *__re
     uint64_t idx = base + r * 32 + lane;
     bool valid = idx < n;
     key[r] = valid ? src[idx] : 0ull;
-    dig[r] = valid ? (uint32_t)((key[r] >> shift) & mask) : 0xFFFFu;
+    dig[r] = valid ? (uint32_t)(((key[r] & ~kTagBit) >> shift) & mask) : 0xFFFFu;
   }
 #pragma unroll
   for (int r = 0; r < kSortItems; r++) {
@@ -164,7 +176,8 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_pass(const uint64_t *__re
 __global__ void __launch_bounds__(kScanThreads) k_keep(PrepArgs a, const uint64_t *__restrict__ sorted,
                                                         const uint64_t *__restrict__ F, uint64_t nleaves,
                                                         uint64_t *__restrict__ ukey, uint8_t *__restrict__ utag,
-                                                        uint32_t *__restrict__ uleaf, uint64_t *status, Ctl *ctl) {
+                                                        uint32_t *__restrict__ uleaf, uint64_t *status, Ctl *ctl,
+                                                        const ModelHead *mhead, const Piece *__restrict__ mpieces) {
   __shared__ ScanSmem sm;
   const uint32_t tile = take_ticket(ctl, kSlotKeep, sm), n = ctl->n;
   uint32_t flag[kScanItems];
@@ -176,22 +189,26 @@ __global__ void __launch_bounds__(kScanThreads) k_keep(PrepArgs a, const uint64_
     w[r] = 0;
     if (e < n) {
       w[r] = sorted[e];
-      uint64_t k = w[r] >> 1;
-      if (w[r] & 1ull)  // delete: kept iff no word with the same key precedes it
-        flag[r] = e == 0 || (sorted[e - 1] >> 1) != k;
-      else              // insert: kept iff no word with the same key follows it
-        flag[r] = e + 1 == n || (sorted[e + 1] >> 1) != k;
+      const uint64_t k = w[r] & ~kTagBit;
+      if (w[r] & kTagBit)  // delete: kept iff no word with the same key precedes it
+        flag[r] = e == 0 || (sorted[e - 1] & ~kTagBit) != k;
+      else                 // insert: kept iff no word with the same key follows it
+        flag[r] = e + 1 == n || (sorted[e + 1] & ~kTagBit) != k;
     }
   }
   uint32_t off[kScanItems];
   uint32_t total = tile_scan(flag, off, tile, status, 1, 0, ctl->epoch + kSlotKeep, &ctl->err, sm);
+  ModelHead m;
+  m.valid = 0;
+  if (mhead) m = *mhead;
+  const bool learned = m.valid != 0;
 #pragma unroll
   for (int r = 0; r < kScanItems; r++) {
     if (!flag[r] || off[r] >= n) continue;
     uint64_t key = expand(w[r], a);
     ukey[off[r]] = key;
-    utag[off[r]] = (uint8_t)(w[r] & 1ull);
-    uleaf[off[r]] = leaf_search(F, nleaves, key);
+    utag[off[r]] = (uint8_t)(w[r] >> 63);
+    uleaf[off[r]] = learned ? learned_leaf_search(m, mpieces, F, nleaves, key) : leaf_search(F, nleaves, key);
   }
   if ((uint64_t)(tile + 1) * kScanTile >= n && threadIdx.x == 0) ctl->m = total;
 }
@@ -248,17 +265,24 @@ void launch_prep(const FrontArgs &f, cudaStream_t s) {
 void launch_sort(const FrontArgs &f, uint64_t nb, cudaStream_t s) {
   const PrepArgs &a = f.prep;
   uint64_t *src = f.bufA, *dst = f.bufB;
-  const uint32_t st = sort_tiles(nb);
+  const bool large = nb >= kSortLargeFrom;
+  const uint32_t st = large ? (uint32_t)((nb + kSortThreads * kSortItemsLarge - 1) / (kSortThreads * kSortItemsLarge))
+                            : sort_tiles(nb);
   for (uint32_t p = 0; p < a.npass; p++) {
     note_launch();
-    k_sort_pass<<<st, kSortThreads, 0, s>>>(src, dst, f.hist, f.status, f.ctl, p, p * a.dbits, a.dbits);
+    if (large)
+      k_sort_pass<kSortItemsLarge><<<st, kSortThreads, 0, s>>>(src, dst, f.hist, f.status, f.ctl, p, p * a.dbits,
+                                                               a.dbits);
+    else
+      k_sort_pass<kSortItemsSmall><<<st, kSortThreads, 0, s>>>(src, dst, f.hist, f.status, f.ctl, p, p * a.dbits,
+                                                               a.dbits);
     uint64_t *t = src; src = dst; dst = t;
   }
   // look-back epochs: pass p uses epoch + p, then the fixed slots of gpma_launch.h
   const uint32_t ct = comp_tiles(nb);
   note_launch();
   k_keep<<<ct, kScanThreads, 0, s>>>(a, src, f.geo->F, f.geo->nleaves, f.ukey, f.utag, f.uleaf, f.status,
-                                     f.ctl);
+                                     f.ctl, f.mhead, f.mpieces);
   note_launch();
   k_runs<<<ct, kScanThreads, 0, s>>>(f.uleaf, f.run_start, f.run_leaf, f.status, f.ctl);
 }

@@ -251,3 +251,34 @@ def test_import_rejects_bad_layouts():
     assert np.array_equal(host(g.layout()), good)
     with pytest.raises(gp.GpmaError):
         g.import_layout(dev(good[:12]))  # not L * 2^k
+
+
+# ---- learned leaf search: the same array as plain binary search ----------------------------------
+def test_learned_search_matches_plain():
+    rng = np.random.default_rng(17)
+    scale = 14
+    V = 1 << scale
+    stream = W.rmat_stream(scale, 400_000, seed=8)
+    learned = gp.Graph(V, leaf_size=64)
+    plain = gp.Graph(V, leaf_size=64, plain_search=True)
+    o = oracle.OraclePMA(V, L=64)
+    win = W.SlidingWindow(stream, 100_000)
+    for g in (learned, plain):
+        g.update(dev(win.initial), None, stats=True)
+    o.update(win.initial)
+    # growth (escalations, resizes) then sliding batches of mixed sizes
+    for step in range(40):
+        b = int(rng.choice([64, 1000, 5000, 20000]))
+        if step < 8:
+            ins, dels = win.stream[win.tail: win.tail + b], np.zeros(0, np.uint64)
+            win.tail += b
+        else:
+            ins, dels = win.slide(b // 2)
+        st1 = learned.update(dev(ins), dev(dels) if dels.size else None, stats=True)
+        st2 = plain.update(dev(ins), dev(dels) if dels.size else None, stats=True)
+        o.update(ins, dels)
+        assert st1 == st2
+        a, b2 = host(learned.layout()), host(plain.layout())
+        assert np.array_equal(a, b2), f"step {step}: learned and plain layouts differ"
+    assert np.array_equal(host(learned.layout()), o.layout())
+    assert learned.check() == 0
