@@ -52,6 +52,10 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--seed", type=int, default=1)
+    ap.add_argument("--learned-study", action="store_true",
+                    help="only compare the learned and the plain leaf search on the power-law workload")
+    ap.add_argument("--many-study", action="store_true",
+                    help="only time the batched many-graph update (64 uneven R-MAT graphs)")
     return ap.parse_args()
 
 
@@ -337,6 +341,131 @@ def run_gpu(a, stream, rank, world, dist):
     return out
 
 
+# ---- learned vs plain leaf search (power-law workload) -----------------------------------------------
+def learned_study(a):
+    """Chung-Lu graph (1.6M vertices, 30M edges, degree exponent 2.1, seed 7),
+    batches of 1e5 updates: 70% new edges inserted, 30% random live edges deleted.
+    The same batches go to a handle with the learned leaf search and one with
+    plain binary search; per-batch device time from the library's events, and the
+    two arrays compared slot for slot at the end."""
+    import torch
+    import paper_1709_05061_gb300 as gp
+    from paper_1709_05061_gb300 import workloads as W
+    gp.build()
+    torch.cuda.set_device(0)
+    V, E0, B = 1_600_000, 30_000_000, 100_000
+    n_ins, n_del = int(B * 0.7), B - int(B * 0.7)
+    warm, timed = 3, 10
+    stream = W.chung_lu_stream(V, E0 + (warm + timed) * n_ins, gamma=2.1, seed=7)
+    rng = np.random.default_rng(7)
+    live = stream[:E0].copy()
+
+    def dev(x):
+        return torch.from_numpy(np.ascontiguousarray(x).view(np.int64)).cuda()
+    graphs = {"learned": gp.Graph(V, leaf_size=LEAF), "plain": gp.Graph(V, leaf_size=LEAF, plain_search=True)}
+    for g in graphs.values():
+        g.update(dev(stream[:E0]), None, stats=True)
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.int32, device="cuda")
+    times = {k: [] for k in graphs}
+    for i in range(warm + timed):
+        ins = stream[E0 + i * n_ins: E0 + (i + 1) * n_ins]
+        pick = rng.choice(live.size, n_del, replace=False)
+        dels = live[pick]
+        keep = np.ones(live.size, bool)
+        keep[pick] = False
+        live = np.concatenate([live[keep], ins])
+        di, dd = dev(ins), dev(dels)
+        for name, g in graphs.items():
+            flush.zero_()
+            gp.gpma_profile_enable(g.h, True)
+            g.update(di, dd, stats=True)
+            p = gp.gpma_profile_read(g.h, reset=True)
+            gp.gpma_profile_enable(g.h, False)
+            if i >= warm:
+                times[name].append(p["update"]["ms"])
+    same = bool(torch.equal(graphs["learned"].layout(), graphs["plain"].layout()))
+    out = {"workload": f"chung-lu V={V} E={E0} gamma=2.1 seed=7, batch {B} (70% insert / 30% random delete)",
+           "plain_p50_ms": statistics.median(times["plain"]), "learned_p50_ms": statistics.median(times["learned"]),
+           "layouts_identical": same, "capacity_slots": graphs["plain"].capacity}
+    out["speedup"] = out["plain_p50_ms"] / out["learned_p50_ms"]
+    for g in graphs.values():
+        g.close()
+    return out
+
+
+def many_study(a):
+    """64 independent R-MAT graphs, window sizes log-uniform in [2^10, 2^22]
+    edges, per-step batches log-uniform in [64, 2^18] updates (half inserts, half
+    deletes).  Per step: all 64 batches through gpma_update_many (forked onto side
+    streams, each replaying its graph) against the same batches applied one
+    graph after another on one stream, at leaf size 64 and at the leaf size the
+    autotuner picks per graph.  Batches are resident on the device before timing;
+    device time with CUDA events on the calling stream; the batched and the
+    sequential arrays are compared slot for slot at the end."""
+    import torch
+    import paper_1709_05061_gb300 as gp
+    from paper_1709_05061_gb300 import tune
+    from paper_1709_05061_gb300 import workloads as W
+    gp.build()
+    torch.cuda.set_device(0)
+    warm, timed = 3, 10
+    wl = W.ManyGraphWorkload(64, 1 << 10, 1 << 22, 64, 1 << 18, steps=warm + timed, seed=11)
+    n = wl.n_graphs
+
+    def dev(x):
+        return torch.from_numpy(np.ascontiguousarray(x).view(np.int64)).cuda()
+    init = [dev(w.initial) for w in wl.windows]
+    batches = [[(dev(i), dev(d)) for i, d in wl.slide()] for _ in range(warm + timed)]
+    # autotune on the first step's batches, on copies of the initial graphs
+    t0 = time.perf_counter()
+    tuned, tables = [], []
+    for i in range(n):
+        L, tab = tune.autotune_leaf_size(wl.n_vertices(i), init[i], batches[0][i][0], batches[0][i][1], reps=3)
+        tuned.append(L)
+        tables.append(tab)
+    tune_s = time.perf_counter() - t0
+    s = torch.cuda.current_stream()
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.int32, device="cuda")
+    res = {}
+    layouts = {}
+    for label, sizes in (("L64", [64] * n), ("tuned", tuned)):
+        for mode in ("sequential", "batched"):
+            gs = [gp.Graph(wl.n_vertices(i), leaf_size=sizes[i]) for i in range(n)]
+            gp.Graph.update_many(gs, init, [None] * n)
+            ts = []
+            for k, b in enumerate(batches):
+                flush.zero_()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(s)
+                if mode == "batched":
+                    gp.Graph.update_many(gs, [x[0] for x in b], [x[1] for x in b])
+                else:
+                    for g, (bi, bd) in zip(gs, b):
+                        g.update(bi, bd)
+                e1.record(s)
+                e1.synchronize()
+                if k >= warm:
+                    ts.append(e0.elapsed_time(e1))
+            for g in gs:
+                g.status()
+            layouts[(label, mode)] = [g.layout().cpu() for g in gs]
+            for g in gs:
+                g.close()
+            ms = statistics.median(ts)
+            res[f"{label}_{mode}"] = {"p50_ms": ms, "p99_ms": float(np.percentile(ts, 99)),
+                                     "edge_updates_per_s": float(wl.batch.sum()) / (ms * 1e-3)}
+        same = all(torch.equal(x, y) for x, y in zip(layouts[(label, "sequential")], layouts[(label, "batched")]))
+        res[f"{label}_batched_equals_sequential"] = same
+    res["workload"] = (f"64 R-MAT graphs (.57/.19/.19/.05), windows log-uniform in [2^10, 2^22] edges "
+                       f"(total {int(wl.edges.sum())}), batches log-uniform in [64, 2^18] "
+                       f"(total {int(wl.batch.sum())} updates per step), seed 11")
+    res["tuned_leaf_sizes"] = {str(L): tuned.count(L) for L in sorted(set(tuned))}
+    res["autotune_seconds"] = tune_s
+    res["speedup_batched_vs_sequential_L64"] = res["L64_sequential"]["p50_ms"] / res["L64_batched"]["p50_ms"]
+    res["speedup_tuned_batched_vs_L64_sequential"] = res["L64_sequential"]["p50_ms"] / res["tuned_batched"]["p50_ms"]
+    return res
+
+
 # ---- the oracle (CPU) --------------------------------------------------------------------------------
 def run_oracle(a, stream, steps, max_seconds=None, skip=0):
     import oracle
@@ -375,6 +504,13 @@ def main():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     cfg = workload_config(a, world)
+
+    if a.learned_study:
+        print(json.dumps({"learned_study": learned_study(a)}), flush=True)
+        return 0
+    if a.many_study:
+        print(json.dumps({"many_study": many_study(a)}), flush=True)
+        return 0
 
     if a.impl == "reference":
         if rank != 0:

@@ -110,6 +110,18 @@ int gpma_destroy(gpma_t h);
 int gpma_update_batch(gpma_t h, const uint64_t *d_ins, uint64_t n_ins, const uint64_t *d_del,
                       uint64_t n_del, void *stream, gpma_stats *stats);
 
+/* Apply one batch to each of `count` distinct handles (the batched form of
+ * gpma_update_batch for many independent graphs).  d_ins[i][n_ins[i]] and
+ * d_del[i][n_del[i]] go to handles[i] with exactly the semantics of
+ * gpma_update_batch; each handle ends as if its batch had been applied alone.
+ * The batches are forked from `stream` onto side streams (each replaying its
+ * handle's CUDA graph) and joined back, so the GPU overlaps the graphs' kernels;
+ * work enqueued on `stream` afterwards sees every batch applied.  Returns the
+ * first host-detected error; device-detected GPMA_EINVAL is reported per handle by
+ * gpma_status().  The handles must not be in use on other streams meanwhile. */
+int gpma_update_many(gpma_t const *handles, const uint64_t *const *d_ins, const uint64_t *n_ins,
+                     const uint64_t *const *d_del, const uint64_t *n_del, uint32_t count, void *stream);
+
 /* Wait for `stream` and return (then clear) the first device-side error of the
  * batches enqueued without stats. */
 int gpma_status(gpma_t h, void *stream);

@@ -85,6 +85,7 @@ def lib():
             "gpma_destroy": ([vp], i),
             "gpma_update_batch": ([vp, vp, u64, vp, u64, vp, P(gpma_stats)], i),
             "gpma_status": ([vp, vp], i),
+            "gpma_update_many": ([P(vp), P(vp), P(u64), P(vp), P(u64), u32, vp], i),
             "gpma_bfs": ([vp, u32, vp, vp], i),
             "gpma_cc": ([vp, vp, vp], i),
             "gpma_pagerank": ([vp, u32, C.c_float, vp, vp], i),
@@ -161,6 +162,19 @@ def gpma_update_batch(h: int, ins, dels, stream=None, stats: bool = False):
                                  _stream(stream), C.byref(st) if st is not None else None)
     _check(rc, "gpma_update_batch")
     return st.as_dict() if st is not None else None
+
+
+def gpma_update_many(handles, ins_list, del_list, stream=None):
+    """One batch per handle, overlapped on the GPU (see include/gpma.h)."""
+    n = len(handles)
+    ins_list = [_keys(x) for x in ins_list]
+    del_list = [_keys(x) for x in del_list]
+    H = (C.c_void_p * n)(*handles)
+    PI = (C.c_void_p * n)(*[_ptr(x).value for x in ins_list])
+    PD = (C.c_void_p * n)(*[_ptr(x).value for x in del_list])
+    NI = (C.c_uint64 * n)(*[x.numel() for x in ins_list])
+    ND = (C.c_uint64 * n)(*[x.numel() for x in del_list])
+    _check(lib().gpma_update_many(H, PI, NI, PD, ND, n, _stream(stream)), "gpma_update_many")
 
 
 def gpma_status(h: int, stream=None):
@@ -288,6 +302,11 @@ class Graph:
 
     def update(self, ins=None, dels=None, stats: bool = False, stream=None):
         return gpma_update_batch(self.h, ins, dels, stream=stream, stats=stats)
+
+    @staticmethod
+    def update_many(graphs, ins_list, del_list, stream=None):
+        """Apply ins_list[i] / del_list[i] to graphs[i], all batches overlapped."""
+        gpma_update_many([g.h for g in graphs], ins_list, del_list, stream=stream)
 
     def status(self, stream=None):
         gpma_status(self.h, stream)

@@ -2,7 +2,9 @@
 // which one batch's kernels are enqueued.
 #include <atomic>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <vector>
 
@@ -196,6 +198,13 @@ struct gpma {
   Piece *mpieces;
   uint32_t *mtmp;
   uint32_t since_train;
+  // device-side root resize: the array of height h+1 a batch may grow into, and
+  // the control block such a batch sends back (read before the next call)
+  Geo spare;
+  bool has_spare;
+  Ctl *h_mirror;
+  cudaEvent_t ev_mirror;
+  bool mirror_pending;
 };
 
 namespace {
@@ -386,10 +395,10 @@ int read_ctl(gpma *h, cudaStream_t s) {
   return GPMA_OK;
 }
 
-void train_model(gpma *h, cudaStream_t s) {
+void train_model(gpma *h, cudaStream_t s, bool only_if_escalated = false) {
   if (!h->mhead) return;
-  launch_train_model(h->geo, h->mhead, h->mpieces, h->mtmp, s);
-  h->since_train = 0;
+  launch_train_model(h->geo, h->mhead, h->mpieces, h->mtmp, h->ctl, only_if_escalated, s);
+  if (!only_if_escalated) h->since_train = 0;
 }
 
 // root resize (reading R7): every valid key and every pending insert spread over
@@ -427,18 +436,64 @@ __global__ void k_gate(const Ctl *ctl, cudaGraphConditionalHandle cond) {
   cudaGraphSetConditional(cond, (ctl->err == 0 && ctl->nesc > 0) ? 1u : 0u);
 }
 
+// after the merge levels of a batch that may overflow the root: either some
+// pending run fits no level (grow into the spare array) or the usual merges run
+__global__ void k_gate_grow(Ctl *ctl, cudaGraphConditionalHandle grow, cudaGraphConditionalHandle merge) {
+  const bool esc = ctl->err == 0 && ctl->nesc > 0;
+  const bool g = esc && ctl->nfail > 0;
+  ctl->resized = g ? 1u : 0u;
+  cudaGraphSetConditional(grow, g ? 1u : 0u);
+  cudaGraphSetConditional(merge, (esc && !g) ? 1u : 0u);
+}
+
+// Append an IF node on `cond` to the graph being captured on `cap`, and capture
+// `body` (launches on the stream it is given) into the node's body graph.
+template <typename Body>
+bool capture_if(cudaStream_t cap, cudaStream_t cap2, cudaGraphConditionalHandle cond, Body body) {
+  cudaStreamCaptureStatus cs;
+  cudaGraph_t cg = nullptr;
+  const cudaGraphNode_t *deps = nullptr;
+  size_t ndeps = 0;
+  if (cudaStreamGetCaptureInfo(cap, &cs, nullptr, &cg, &deps, nullptr, &ndeps) != cudaSuccess) return false;
+  // zero-initialised storage: the parameter union has no default constructor
+  alignas(cudaGraphNodeParams) unsigned char raw[sizeof(cudaGraphNodeParams)] = {};
+  cudaGraphNodeParams *p = reinterpret_cast<cudaGraphNodeParams *>(raw);
+  p->type = cudaGraphNodeTypeConditional;
+  p->conditional.handle = cond;
+  p->conditional.type = cudaGraphCondTypeIf;
+  p->conditional.size = 1;
+  cudaGraphNode_t cnode = nullptr;
+  if (cudaGraphAddNode(&cnode, cg, deps, nullptr, ndeps, p) != cudaSuccess) return false;
+  cudaGraph_t bgraph = p->conditional.phGraph_out[0];
+  if (cudaStreamUpdateCaptureDependencies(cap, &cnode, nullptr, 1, cudaStreamSetCaptureDependencies) != cudaSuccess)
+    return false;
+  if (cudaStreamBeginCaptureToGraph(cap2, bgraph, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal) !=
+      cudaSuccess)
+    return false;
+  body(cap2);
+  cudaGraph_t out = nullptr;
+  return cudaStreamEndCapture(cap2, &out) == cudaSuccess;
+}
+
 // Capture the part of a batch after k_prep as one graph, grids sized for `nb`
 // keys.  The escalation (pending inserts, count tree, merge levels, outermost
 // segments, segment merge) sits in the body of an IF node that runs only when
 // some leaf could not take its inserts, which a sliding window rarely produces.
-bool capture_update(gpma *h, FrontArgs &f, uint32_t nb, bool stats, GraphCache::Entry **out) {
+// With `grow` (the batch might overflow the root, reading R7) the merge levels
+// also count the runs no level admits, and two more IF nodes follow: the root
+// resize into the preallocated spare array of height h+1, or the usual merges.
+bool capture_update(gpma *h, FrontArgs &f, uint32_t nb, bool stats, bool grow, GraphCache::Entry **out) {
   GraphCache &gc = *h->graphs;
   if (!gc.cap && cudaStreamCreateWithFlags(&gc.cap, cudaStreamNonBlocking) != cudaSuccess) return false;
   if (!gc.cap2 && cudaStreamCreateWithFlags(&gc.cap2, cudaStreamNonBlocking) != cudaSuccess) return false;
   cudaGraph_t graph = nullptr;
   if (cudaGraphCreate(&graph, 0) != cudaSuccess) return false;
-  cudaGraphConditionalHandle cond;
+  cudaGraphConditionalHandle cond, cgrow, cmerge;
   bool ok = cudaGraphConditionalHandleCreate(&cond, graph, 0, cudaGraphCondAssignDefault) == cudaSuccess;
+  if (grow) {
+    ok = ok && cudaGraphConditionalHandleCreate(&cgrow, graph, 0, cudaGraphCondAssignDefault) == cudaSuccess &&
+         cudaGraphConditionalHandleCreate(&cmerge, graph, 0, cudaGraphCondAssignDefault) == cudaSuccess;
+  }
   const uint64_t l0 = launch_count();
   ok = ok && cudaStreamBeginCaptureToGraph(gc.cap, graph, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal) ==
                  cudaSuccess;
@@ -446,46 +501,37 @@ bool capture_update(gpma *h, FrontArgs &f, uint32_t nb, bool stats, GraphCache::
     cudaGraphDestroy(graph);
     return false;
   }
+  const Geo &g = h->geo;
+  auto merges = [&](cudaStream_t t) {
+    launch_esc_top(g, h->ctl, h->w, nb, t);
+    launch_segments(g, h->ctl, h->w, nb, t);
+    launch_segment_merge(g, g, h->ctl, h->w, h->scratch_cap, g.nleaves, h->scratch, h->vbuf, h->partials, false,
+                         t);
+    if (h->mhead) launch_train_model(g, h->mhead, h->mpieces, h->mtmp, h->ctl, false, t);
+  };
   launch_sort(f, nb, gc.cap);
-  launch_leaf_pass(h->geo, h->ctl, h->w, nb, gc.cap);
+  launch_leaf_pass(g, h->ctl, h->w, nb, gc.cap);
   note_launch();
   k_gate<<<1, 1, 0, gc.cap>>>(h->ctl, cond);
-  cudaStreamCaptureStatus cs;
-  cudaGraph_t cg = nullptr;
-  const cudaGraphNode_t *deps = nullptr;
-  size_t ndeps = 0;
-  ok = cudaStreamGetCaptureInfo(gc.cap, &cs, nullptr, &cg, &deps, nullptr, &ndeps) == cudaSuccess;
-  cudaGraphNode_t cnode = nullptr;
-  cudaGraph_t body = nullptr;
-  if (ok) {
-    // zero-initialised storage: the parameter union has no default constructor
-    alignas(cudaGraphNodeParams) unsigned char raw[sizeof(cudaGraphNodeParams)] = {};
-    cudaGraphNodeParams *p = reinterpret_cast<cudaGraphNodeParams *>(raw);
-    p->type = cudaGraphNodeTypeConditional;
-    p->conditional.handle = cond;
-    p->conditional.type = cudaGraphCondTypeIf;
-    p->conditional.size = 1;
-    ok = cudaGraphAddNode(&cnode, cg, deps, nullptr, ndeps, p) == cudaSuccess;
-    if (ok) body = p->conditional.phGraph_out[0];
+  ok = capture_if(gc.cap, gc.cap2, cond, [&](cudaStream_t t) {
+    launch_pending(g, h->ctl, h->w, nb, t);
+    launch_tree_rebuild(g, h->ctl, h->w, nb, t);
+    launch_esc_level(g, h->ctl, h->w, nb, grow, t);
+    if (!grow) merges(t);
+  });
+  if (ok && grow) {
+    note_launch();
+    k_gate_grow<<<1, 1, 0, gc.cap>>>(h->ctl, cgrow, cmerge);
+    ok = capture_if(gc.cap, gc.cap2, cgrow, [&](cudaStream_t t) {
+      const Geo &g2 = h->spare;
+      launch_unmark(g, h->ctl, h->w, nb, t);
+      launch_segment_merge(g, g2, h->ctl, h->w, h->scratch_cap, g.nleaves, h->scratch, h->vbuf, h->partials,
+                           true, t);
+      if (h->mhead) launch_train_model(g2, h->mhead, h->mpieces, h->mtmp, h->ctl, false, t);
+    });
+    ok = ok && capture_if(gc.cap, gc.cap2, cmerge, merges);
   }
-  ok = ok && cudaStreamUpdateCaptureDependencies(gc.cap, &cnode, nullptr, 1, cudaStreamSetCaptureDependencies) ==
-                 cudaSuccess;
-  if (ok && cudaStreamBeginCaptureToGraph(gc.cap2, body, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal) ==
-                cudaSuccess) {
-    launch_pending(h->geo, h->ctl, h->w, nb, gc.cap2);
-    launch_tree_rebuild(h->geo, h->ctl, h->w, nb, gc.cap2);
-    launch_esc_level(h->geo, h->ctl, h->w, nb, false, gc.cap2);
-    launch_esc_top(h->geo, h->ctl, h->w, nb, gc.cap2);
-    launch_segments(h->geo, h->ctl, h->w, nb, gc.cap2);
-    launch_segment_merge(h->geo, h->geo, h->ctl, h->w, h->scratch_cap, h->geo.nleaves, h->scratch, h->vbuf,
-                         h->partials, false, gc.cap2);
-    if (h->mhead) launch_train_model(h->geo, h->mhead, h->mpieces, h->mtmp, gc.cap2);
-    cudaGraph_t body_out = nullptr;
-    ok = cudaStreamEndCapture(gc.cap2, &body_out) == cudaSuccess;
-  } else {
-    ok = false;
-  }
-  if (stats) launch_stats(h->geo, h->ctl, h->w, nb, gc.cap);
+  if (stats) launch_stats(g, h->ctl, h->w, nb, gc.cap);
   note_launch();
   k_finish<<<1, 1, 0, gc.cap>>>(h->ctl);
   cudaGraph_t done = nullptr;
@@ -508,10 +554,47 @@ bool capture_update(gpma *h, FrontArgs &f, uint32_t nb, bool stats, GraphCache::
   ge->bucket = 0;
   ge->epoch = h->alloc_epoch;
   ge->stats = stats;
-  ge->kernels = kernels;  // an upper bound: the IF body runs only when needed
+  ge->kernels = kernels;  // an upper bound: the IF bodies run only when needed
   ge->used = ++gc.tick;
   *out = ge;
   return true;
+}
+
+// The spare array of height h+1 that a batch captured with `grow` resizes into.
+int ensure_spare(gpma *h, cudaStream_t s) {
+  if (h->has_spare && h->spare.h == h->geo.h + 1) return GPMA_OK;
+  if (h->has_spare) free_arrays(h, &h->spare, s);
+  h->has_spare = false;
+  make_geo(h, h->geo.h + 1, &h->spare);
+  h->spare.row_end = h->geo.row_end;
+  h->spare.deg = h->geo.deg;
+  if (!alloc_arrays(h, &h->spare, s)) {
+    free_arrays(h, &h->spare, s);
+    return GPMA_ENOMEM;
+  }
+  h->has_spare = true;
+  h->alloc_epoch++;
+  return GPMA_OK;
+}
+
+// A batch that may have grown the array on the device left its control block
+// on its way to the host; before anything else uses the geometry, wait for it
+// and, if the array grew, switch to the spare.
+int settle(gpma *h, cudaStream_t s) {
+  if (!h->mirror_pending) return GPMA_OK;
+  h->mirror_pending = false;
+  if (cudaEventSynchronize(h->ev_mirror) != cudaSuccess) return poison(h, GPMA_EDEVICE);
+  const Ctl &c = *h->h_mirror;
+  if (c.resized) {
+    free_arrays(h, &h->geo, s);
+    h->geo = h->spare;
+    memset(&h->spare, 0, sizeof(Geo));
+    h->has_spare = false;
+    h->alloc_epoch++;
+    h->since_train = 0;
+  }
+  h->count_ub = c.total;
+  return cuda_ok(h);
 }
 
 int update(gpma *h, const uint64_t *ins, uint64_t n_ins, const uint64_t *del, uint64_t n_del, cudaStream_t s,
@@ -521,7 +604,9 @@ int update(gpma *h, const uint64_t *ins, uint64_t n_ins, const uint64_t *del, ui
   const uint64_t n = n_ins + n_del;
   if (n >= (1ull << 30) || (n_ins && !ins) || (n_del && !del)) return GPMA_EINVAL;
   if (n == 0) return GPMA_OK;
-  int rc = ensure_work(h, n, s);
+  int rc = settle(h, s);
+  if (rc) return rc;
+  rc = ensure_work(h, n, s);
   if (rc) return rc;
   if ((rc = ensure_merge_scratch(h, s))) return rc;
   const uint32_t h_old = h->geo.h;
@@ -571,23 +656,37 @@ int update(gpma *h, const uint64_t *ins, uint64_t n_ins, const uint64_t *del, ui
   launch_prep(f, s);
   // the root can only refuse inserts when the count might exceed its bound
   const bool may_fail = h->count_ub + n_ins > h->geo.maxc[h->geo.h];
+  // such a batch still replays a graph (no host wait) when one level of growth
+  // surely suffices: it resizes on the device into a preallocated spare array
+  bool grow = false;
+  if (may_fail && !stats && h->graphs->enabled && h->ev_mirror && h->geo.h + 2 < kMaxLv &&
+      ((uint64_t)h->L << (h->geo.h + 1)) <= (1ull << 32)) {
+    uint64_t mx[kMaxLv];
+    level_bounds(h->L, h->geo.h + 1, h->tau0, h->tauh, mx);
+    grow = h->count_ub + n_ins <= mx[h->geo.h + 1] && ensure_spare(h, s) == GPMA_OK;
+  }
   bool resized = false;
-  if (!may_fail && h->graphs->enabled) {
+  if ((!may_fail || grow) && h->graphs->enabled) {
     // replay: sort .. segment merge as one graph, grids sized for the bucket
     uint64_t bucket = 2048;
     while (bucket < n) bucket <<= 1;
     const uint32_t nb = (uint32_t)bucket;
     // the key layout of a guard batch differs: never share its graph
-    GraphCache::Entry *ge = h->graphs->find(bucket, h->alloc_epoch + (allow_guards ? (1ull << 62) : 0),
-                                           stats != nullptr);
+    const uint64_t key = h->alloc_epoch + (allow_guards ? (1ull << 62) : 0) + (grow ? (1ull << 61) : 0);
+    GraphCache::Entry *ge = h->graphs->find(bucket, key, stats != nullptr);
     if (!ge) {
-      if (!capture_update(h, f, nb, stats != nullptr, &ge)) return poison(h, GPMA_EDEVICE);
+      if (!capture_update(h, f, nb, stats != nullptr, grow, &ge)) return poison(h, GPMA_EDEVICE);
       ge->bucket = bucket;
-      ge->epoch = h->alloc_epoch + (allow_guards ? (1ull << 62) : 0);
+      ge->epoch = key;
     }
     if (cudaGraphLaunch(ge->exec, s) != cudaSuccess) return poison(h, GPMA_EDEVICE);
     for (uint64_t k = 0; k < ge->kernels; k++) note_launch();
     h->count_ub += n_ins;
+    if (grow) {
+      cudaMemcpyAsync(h->h_mirror, h->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, s);
+      if (cudaEventRecord(h->ev_mirror, s) != cudaSuccess) return poison(h, GPMA_EDEVICE);
+      h->mirror_pending = true;
+    }
   } else {
     {
       Phase ph(h->prof, GPMA_PROF_SORT, s);
@@ -629,7 +728,7 @@ int update(gpma *h, const uint64_t *ins, uint64_t n_ins, const uint64_t *del, ui
                            h->partials, false, s);
       esc.end();
       if (stats) launch_stats(h->geo, h->ctl, h->w, n32, s);
-      train_model(h, s);
+      train_model(h, s, true);
     }
     note_launch();
     k_finish<<<1, 1, 0, s>>>(h->ctl);
@@ -690,8 +789,9 @@ int ensure_analytics(gpma *h, uint32_t iters, cudaStream_t s) {
 
 namespace gpk {
 // Read-only view of a handle for entry points defined in other files.
-HandleView handle_view(gpma_t h) {
+HandleView handle_view(gpma_t h, cudaStream_t s) {
   HandleView v;
+  if (!h->poisoned) settle(h, s);
   v.geo = &h->geo;
   v.ctl = h->ctl;
   v.h_ctl = h->h_ctl;
@@ -747,6 +847,10 @@ int gpma_create(uint32_t n_vertices, const gpma_params *params, const gpma_alloc
     return GPMA_ENOMEM;
   }
   allow_big_smem();
+  // GPMA_NO_GRAPHS=1 launches every kernel of a batch directly (profilers then
+  // see each launch; the results are the same)
+  const char *ng = getenv("GPMA_NO_GRAPHS");
+  if (ng && ng[0] == '1') h->graphs->enabled = false;
   h->V = raw ? 0 : n_vertices;
   h->L = L;
   h->logL = bits_for(L) - 1;
@@ -769,6 +873,8 @@ int gpma_create(uint32_t n_vertices, const gpma_params *params, const gpma_alloc
   if (ok && !raw) ok = dalloc(h, &h->geo.row_end, h->V, s) && dalloc(h, &h->geo.deg, h->V, s);
   if (ok && !raw) ok = cudaMemsetAsync(h->geo.deg, 0, sizeof(uint32_t) * h->V, s) == cudaSuccess;
   if (ok) ok = cudaMallocHost(&h->h_ctl, sizeof(Ctl)) == cudaSuccess && cudaMallocHost(&h->h_counter, 16) == cudaSuccess;
+  if (ok) ok = cudaMallocHost(&h->h_mirror, sizeof(Ctl)) == cudaSuccess;
+  if (ok) ok = cudaEventCreateWithFlags(&h->ev_mirror, cudaEventDisableTiming) == cudaSuccess;
   if (!ok) {
     cudaGetLastError();
     gpma_destroy(h);
@@ -805,6 +911,7 @@ int gpma_destroy(gpma_t h) {
   cudaStream_t s = 0;
   cudaDeviceSynchronize();
   free_arrays(h, &h->geo, s);
+  if (h->has_spare) free_arrays(h, &h->spare, s);
   dfree(h, h->geo.row_end, s);
   dfree(h, h->geo.deg, s);
   free_work(h, s);
@@ -815,6 +922,8 @@ int gpma_destroy(gpma_t h) {
   cudaStreamSynchronize(s);
   if (h->h_ctl) cudaFreeHost(h->h_ctl);
   if (h->h_counter) cudaFreeHost(h->h_counter);
+  if (h->h_mirror) cudaFreeHost(h->h_mirror);
+  if (h->ev_mirror) cudaEventDestroy(h->ev_mirror);
   delete h->prof;
   delete h->graphs;
   cudaGetLastError();
@@ -831,6 +940,7 @@ int gpma_update_batch(gpma_t h, const uint64_t *d_ins, uint64_t n_ins, const uin
 int gpma_status(gpma_t h, void *stream) {
   if (!h) return GPMA_EINVAL;
   if (h->poisoned) return h->poisoned;
+  if (int rs = settle(h, (cudaStream_t)stream)) return rs;
   cudaStream_t s = (cudaStream_t)stream;
   int rc = read_ctl(h, s);
   if (rc) return rc;
@@ -845,6 +955,7 @@ int gpma_status(gpma_t h, void *stream) {
 int gpma_bfs(gpma_t h, uint32_t src, int32_t *d_depth, void *stream) {
   if (!h || !d_depth || h->raw || src >= h->V) return GPMA_EINVAL;
   if (h->poisoned) return h->poisoned;
+  if (int rs = settle(h, (cudaStream_t)stream)) return rs;
   cudaStream_t s = (cudaStream_t)stream;
   if (ensure_analytics(h, 1, s)) return GPMA_ENOMEM;
   Phase ph(h->prof, GPMA_PROF_BFS, s);
@@ -857,6 +968,7 @@ int gpma_bfs(gpma_t h, uint32_t src, int32_t *d_depth, void *stream) {
 int gpma_cc(gpma_t h, uint32_t *d_label, void *stream) {
   if (!h || !d_label || h->raw) return GPMA_EINVAL;
   if (h->poisoned) return h->poisoned;
+  if (int rs = settle(h, (cudaStream_t)stream)) return rs;
   Phase ph(h->prof, GPMA_PROF_CC, (cudaStream_t)stream);
   launch_cc(h->geo, d_label, (cudaStream_t)stream);
   return cuda_ok(h);
@@ -865,6 +977,7 @@ int gpma_cc(gpma_t h, uint32_t *d_label, void *stream) {
 int gpma_pagerank(gpma_t h, uint32_t iters, float damping, float *d_rank, void *stream) {
   if (!h || !d_rank || h->raw || !(damping >= 0.0f && damping <= 1.0f)) return GPMA_EINVAL;
   if (h->poisoned) return h->poisoned;
+  if (int rs = settle(h, (cudaStream_t)stream)) return rs;
   cudaStream_t s = (cudaStream_t)stream;
   if (ensure_analytics(h, iters, s)) return GPMA_ENOMEM;
   Phase all(h->prof, GPMA_PROF_PAGERANK, s);
@@ -884,6 +997,7 @@ int gpma_pagerank(gpma_t h, uint32_t iters, float damping, float *d_rank, void *
 int gpma_export_sorted(gpma_t h, uint64_t *d_out, uint64_t cap, uint64_t *n_out, void *stream) {
   if (!h || !n_out || (cap && !d_out)) return GPMA_EINVAL;
   if (h->poisoned) return h->poisoned;
+  if (int rs = settle(h, (cudaStream_t)stream)) return rs;
   cudaStream_t s = (cudaStream_t)stream;
   if (ensure_status(h, h->geo.C, s)) return GPMA_ENOMEM;
   launch_export(h->geo, h->ctl, d_out, nullptr, cap, h->w.status, s);
@@ -896,6 +1010,7 @@ int gpma_export_sorted(gpma_t h, uint64_t *d_out, uint64_t cap, uint64_t *n_out,
 int gpma_export_csr(gpma_t h, uint64_t *d_rowptr, uint32_t *d_col, uint64_t cap, uint64_t *n_out, void *stream) {
   if (!h || !n_out || !d_rowptr || (cap && !d_col) || h->raw) return GPMA_EINVAL;
   if (h->poisoned) return h->poisoned;
+  if (int rs = settle(h, (cudaStream_t)stream)) return rs;
   cudaStream_t s = (cudaStream_t)stream;
   if (ensure_analytics(h, 1, s) || ensure_status(h, h->geo.C, s)) return GPMA_ENOMEM;
   uint64_t *partials = (uint64_t *)dmalloc(h, scan_partials(h->V + 1) * 8 + 8, s);
@@ -912,6 +1027,7 @@ int gpma_export_csr(gpma_t h, uint64_t *d_rowptr, uint32_t *d_col, uint64_t cap,
 int gpma_export_layout(gpma_t h, uint64_t *d_slots, uint64_t cap, uint64_t *capacity_out, void *stream) {
   if (!h || !capacity_out) return GPMA_EINVAL;
   if (h->poisoned) return h->poisoned;
+  if (int rs = settle(h, (cudaStream_t)stream)) return rs;
   *capacity_out = h->geo.C;
   if (cap < h->geo.C) return GPMA_ECAP;
   if (!d_slots) return GPMA_EINVAL;
@@ -923,6 +1039,7 @@ int gpma_export_layout(gpma_t h, uint64_t *d_slots, uint64_t cap, uint64_t *capa
 int gpma_import_layout(gpma_t h, const uint64_t *d_slots, uint64_t capacity, void *stream) {
   if (!h || !d_slots) return GPMA_EINVAL;
   if (h->poisoned) return h->poisoned;
+  if (int rs = settle(h, (cudaStream_t)stream)) return rs;
   uint32_t hh = 0;
   while (((uint64_t)h->L << hh) < capacity && hh < kMaxLv - 2) hh++;
   if (((uint64_t)h->L << hh) != capacity || capacity > (1ull << 32)) return GPMA_EINVAL;
@@ -980,6 +1097,7 @@ int gpma_import_layout(gpma_t h, const uint64_t *d_slots, uint64_t capacity, voi
 int gpma_row_end(gpma_t h, uint32_t *d_row_end, void *stream) {
   if (!h || !d_row_end || h->raw) return GPMA_EINVAL;
   if (h->poisoned) return h->poisoned;
+  if (int rs = settle(h, (cudaStream_t)stream)) return rs;
   cudaMemcpyAsync(d_row_end, h->geo.row_end, sizeof(uint32_t) * h->V, cudaMemcpyDeviceToDevice,
                   (cudaStream_t)stream);
   return cuda_ok(h);
@@ -988,6 +1106,7 @@ int gpma_row_end(gpma_t h, uint32_t *d_row_end, void *stream) {
 int gpma_num_edges(gpma_t h, uint64_t *out, void *stream) {
   if (!h || !out) return GPMA_EINVAL;
   if (h->poisoned) return h->poisoned;
+  if (int rs = settle(h, (cudaStream_t)stream)) return rs;
   int rc = read_ctl(h, (cudaStream_t)stream);
   if (rc) return rc;
   *out = h->h_ctl->total - (h->raw ? 0 : h->V);
@@ -996,6 +1115,7 @@ int gpma_num_edges(gpma_t h, uint64_t *out, void *stream) {
 
 int gpma_capacity(gpma_t h, uint64_t *out) {
   if (!h || !out) return GPMA_EINVAL;
+  if (int rs = settle(h, nullptr)) return rs;
   *out = h->geo.C;
   return GPMA_OK;
 }
@@ -1003,6 +1123,7 @@ int gpma_capacity(gpma_t h, uint64_t *out) {
 int gpma_check(gpma_t h, uint32_t *code, void *stream) {
   if (!h || !code) return GPMA_EINVAL;
   if (h->poisoned) return h->poisoned;
+  if (int rs = settle(h, (cudaStream_t)stream)) return rs;
   cudaStream_t s = (cudaStream_t)stream;
   launch_check(h->geo, h->ctl, h->check_buf, s);
   uint32_t buf[4];
@@ -1010,6 +1131,44 @@ int gpma_check(gpma_t h, uint32_t *code, void *stream) {
   if (cudaStreamSynchronize(s) != cudaSuccess) return poison(h, GPMA_EDEVICE);
   *code = buf[0];
   return cuda_ok(h);
+}
+
+int gpma_update_many(gpma_t const *handles, const uint64_t *const *d_ins, const uint64_t *n_ins,
+                     const uint64_t *const *d_del, const uint64_t *n_del, uint32_t count, void *stream) {
+  if (!handles || (count && (!n_ins || !n_del))) return GPMA_EINVAL;
+  for (uint32_t i = 0; i < count; i++) {
+    if (!handles[i]) return GPMA_EINVAL;
+    for (uint32_t j = 0; j < i; j++)
+      if (handles[j] == handles[i]) return GPMA_EINVAL;  // one batch per handle
+  }
+  // process-wide pool of side streams and events for the fork / join
+  static std::mutex mu;
+  static std::vector<cudaStream_t> side;
+  static std::vector<cudaEvent_t> ev;
+  std::lock_guard<std::mutex> lock(mu);
+  while (side.size() < count) {
+    cudaStream_t t = nullptr;
+    if (cudaStreamCreateWithFlags(&t, cudaStreamNonBlocking) != cudaSuccess) return GPMA_EDEVICE;
+    side.push_back(t);
+  }
+  while (ev.size() < (size_t)count + 1) {
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) return GPMA_EDEVICE;
+    ev.push_back(e);
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  if (cudaEventRecord(ev[count], s) != cudaSuccess) return GPMA_EDEVICE;
+  int first_err = GPMA_OK;
+  for (uint32_t i = 0; i < count; i++) {
+    cudaStreamWaitEvent(side[i], ev[count], 0);
+    const int rc = update(handles[i], d_ins ? d_ins[i] : nullptr, n_ins[i], d_del ? d_del[i] : nullptr, n_del[i],
+                          side[i], nullptr, false);
+    if (rc && !first_err) first_err = rc;
+    cudaEventRecord(ev[i], side[i]);
+    cudaStreamWaitEvent(s, ev[i], 0);
+  }
+  if (cudaGetLastError() != cudaSuccess && !first_err) first_err = GPMA_EDEVICE;
+  return first_err;
 }
 
 int gpma_profile_enable(gpma_t h, int on) {

@@ -64,6 +64,8 @@ struct Ctl {
   uint32_t n_merged0;
   uint64_t merges[kMaxLv];
   uint64_t gen_count;  // general-purpose counter (exports)
+  uint32_t resized;    // this call grew the array on the device (into the spare)
+  uint32_t pad_;
 };
 
 __device__ __forceinline__ bool is_guard(uint64_t k) {

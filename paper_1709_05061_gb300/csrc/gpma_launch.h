@@ -91,8 +91,11 @@ void launch_segment_merge(const Geo &src, const Geo &dst, Ctl *ctl, const Work &
                           uint64_t nleafw_bound, uint64_t *scratch, uint32_t *voff, uint64_t *partials,
                           bool whole, cudaStream_t s);
 
-// k_model.cu: train the learned leaf search on the current pivots (tmp >= 2 * kPieces)
-void launch_train_model(const Geo &g, ModelHead *head, Piece *pieces, uint32_t *tmp, cudaStream_t s);
+// k_model.cu: train the learned leaf search on the current pivots (tmp >= 2 * kPieces);
+// with only_if_escalated the kernels do nothing unless this batch had inserts that
+// did not fit their leaf (level-0 merges move pivots only inside their leaves)
+void launch_train_model(const Geo &g, ModelHead *head, Piece *pieces, uint32_t *tmp, const Ctl *ctl,
+                        bool only_if_escalated, cudaStream_t s);
 
 // k_misc.cu
 void launch_rebuild_indexes(const Geo &g, Ctl *ctl, cudaStream_t s);  // cnt, F, tree, row_end, total
@@ -136,5 +139,5 @@ struct HandleView {
 
 struct gpma;
 namespace gpk {
-HandleView handle_view(struct gpma *h);
+HandleView handle_view(struct gpma *h, cudaStream_t s);  // waits for a pending device resize
 }  // namespace gpk

@@ -55,6 +55,7 @@ __global__ void k_init_batch(Ctl *ctl, uint32_t *hist, uint32_t nhist, uint32_t 
     ctl->nesc = 0;
     ctl->nfail = 0;
     ctl->nlong = 0;
+    ctl->resized = 0;
     ctl->m = ctl->nruns = ctl->npend = ctl->neruns = ctl->nsegs = ctl->nleafw = 0;
     for (int i = 0; i < 16; i++) ctl->ticket[i] = 0;
     ctl->n_inserted = ctl->n_deleted = 0;

@@ -23,7 +23,8 @@ uint32_t nblk(uint64_t items, uint32_t per_block, uint32_t cap) {
 }
 }  // namespace
 
-__global__ void k_lm_init(ModelHead *head, uint32_t *first, uint32_t *last) {
+__global__ void k_lm_init(ModelHead *head, uint32_t *first, uint32_t *last, const Ctl *ctl, int only_if_escalated) {
+  if (only_if_escalated && ctl->nesc == 0) return;
   const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t == 0) {
     head->kmin = kEmpty;
@@ -37,50 +38,61 @@ __global__ void k_lm_init(ModelHead *head, uint32_t *first, uint32_t *last) {
   }
 }
 
-__global__ void k_lm_minmax(Geo g, ModelHead *head) {
-  uint64_t mn = kEmpty, mx = 0;
-  for (uint64_t j = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; j < g.nleaves; j += (uint64_t)gridDim.x * blockDim.x) {
-    const uint64_t f = g.F[j];
-    if (f == kEmpty) continue;
-    mn = f < mn ? f : mn;
-    mx = f > mx ? f : mx;
-  }
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    const uint64_t a = __shfl_xor_sync(0xFFFFFFFFu, mn, o), b = __shfl_xor_sync(0xFFFFFFFFu, mx, o);
-    mn = a < mn ? a : mn;
-    mx = b > mx ? b : mx;
-  }
-  if (lane_id() == 0) {
-    if (mn != kEmpty) atomicMin((unsigned long long *)&head->kmin, (unsigned long long)mn);
-    if (mx) atomicMax((unsigned long long *)&head->kmax, (unsigned long long)mx);
+// the pivots of non-empty leaves increase with the leaf: the smallest is the
+// first non-empty leaf's, the largest the last one's (warp 0 scans from the
+// front, warp 1 from the back, 32 leaves at a time)
+__global__ void k_lm_minmax(Geo g, ModelHead *head, const Ctl *ctl, int only_if_escalated) {
+  if (only_if_escalated && ctl->nesc == 0) return;
+  const uint32_t lane = lane_id(), w = threadIdx.x >> 5;
+  if (w > 1) return;
+  for (uint64_t b = 0; b < g.nleaves; b += 32) {
+    const uint64_t j = w == 0 ? b + lane : g.nleaves - 1 - (b + lane);
+    const bool inb = b + lane < g.nleaves;
+    const uint64_t f = inb ? g.F[j] : kEmpty;
+    const uint32_t bal = __ballot_sync(0xFFFFFFFFu, f != kEmpty);
+    if (bal) {
+      const uint64_t pick = __shfl_sync(0xFFFFFFFFu, f, __ffs(bal) - 1);
+      if (lane == 0) {
+        if (w == 0) head->kmin = pick; else head->kmax = pick;
+      }
+      return;
+    }
   }
 }
 
-__global__ void k_lm_scale(ModelHead *head) {
+__global__ void k_lm_scale(ModelHead *head, const Ctl *ctl, int only_if_escalated) {
+  if (only_if_escalated && ctl->nesc == 0) return;
   if (head->kmin == kEmpty) return;  // no pivot: the model stays invalid
   const uint64_t span = head->kmax - head->kmin + 1;
   head->rscale = (float)kPieces / (float)span;
 }
 
-__global__ void k_lm_route(Geo g, const ModelHead *head, uint32_t *first, uint32_t *last) {
+// neighbouring leaves mostly share a piece: lanes of one piece combine first
+__global__ void k_lm_route(Geo g, const ModelHead *head, uint32_t *first, uint32_t *last, const Ctl *ctl,
+                           int only_if_escalated) {
+  if (only_if_escalated && ctl->nesc == 0) return;
   const ModelHead m = *head;
   if (m.kmin == kEmpty) return;
-  for (uint64_t j = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; j < g.nleaves; j += (uint64_t)gridDim.x * blockDim.x) {
-    const uint64_t f = g.F[j];
-    if (f == kEmpty) continue;
-    const uint32_t p = model_route(m, f);
-    atomicMin(&first[p], (uint32_t)j);
-    atomicMax(&last[p], (uint32_t)j);
+  const uint64_t n32 = (g.nleaves + 31) & ~31ull;
+  for (uint64_t j = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n32; j += (uint64_t)gridDim.x * blockDim.x) {
+    const uint64_t f = j < g.nleaves ? g.F[j] : kEmpty;
+    const uint32_t p = f != kEmpty ? model_route(m, f) : 0xFFFFFFFFu;
+    const uint32_t peers = __match_any_sync(0xFFFFFFFFu, p);
+    if (p == 0xFFFFFFFFu) continue;
+    const uint32_t lo = __ffs(peers) - 1, hi = 31 - __clz(peers);
+    if (lane_id() == lo) atomicMin(&first[p], (uint32_t)j);
+    if (lane_id() == hi) atomicMax(&last[p], (uint32_t)j);
   }
 }
 
 // one block: running maximum of the last training leaf over the pieces in order
 __global__ void __launch_bounds__(1024) k_lm_fit(Geo g, const ModelHead *head, const uint32_t *first,
-                                                 const uint32_t *last, Piece *pieces) {
+                                                 const uint32_t *last, Piece *pieces, const Ctl *ctl,
+                                                 int only_if_escalated) {
   __shared__ uint32_t wmax[32];
   constexpr uint32_t kPer = kPieces / 1024;
   const uint32_t t = threadIdx.x, lane = lane_id(), wid = t >> 5;
+  if (only_if_escalated && ctl->nesc == 0) return;
   if (head->kmin == kEmpty) return;
   // pieces [t*kPer, (t+1)*kPer) per thread: local running max, then a block scan of maxima
   uint32_t lmax = 0;
@@ -140,42 +152,57 @@ __global__ void __launch_bounds__(1024) k_lm_fit(Geo g, const ModelHead *head, c
   }
 }
 
-__global__ void k_lm_err(Geo g, const ModelHead *head, Piece *pieces) {
+__global__ void k_lm_err(Geo g, const ModelHead *head, Piece *pieces, const Ctl *ctl, int only_if_escalated) {
+  if (only_if_escalated && ctl->nesc == 0) return;
   const ModelHead m = *head;
   if (m.kmin == kEmpty) return;
-  for (uint64_t j = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; j < g.nleaves; j += (uint64_t)gridDim.x * blockDim.x) {
-    const uint64_t f = g.F[j];
-    if (f == kEmpty) continue;
-    const uint32_t p = model_route(m, f);
-    const Piece pc = pieces[p];
-    const float d = (float)(f > pc.kb ? f - pc.kb : 0ull) * pc.slope;
-    int64_t pred = (int64_t)pc.first + (int64_t)d;
-    if (pred < (int64_t)pc.lo) pred = pc.lo;
-    if (pred > (int64_t)pc.hi) pred = pc.hi;
-    const int64_t e = pred > (int64_t)j ? pred - (int64_t)j : (int64_t)j - pred;
-    atomicMax(&pieces[p].err, (uint32_t)e);
+  const uint64_t n32 = (g.nleaves + 31) & ~31ull;
+  for (uint64_t j = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n32; j += (uint64_t)gridDim.x * blockDim.x) {
+    const uint64_t f = j < g.nleaves ? g.F[j] : kEmpty;
+    uint32_t p = 0xFFFFFFFFu, e = 0;
+    if (f != kEmpty) {
+      p = model_route(m, f);
+      const Piece pc = pieces[p];
+      const float d = (float)(f > pc.kb ? f - pc.kb : 0ull) * pc.slope;
+      int64_t pred = (int64_t)pc.first + (int64_t)d;
+      if (pred < (int64_t)pc.lo) pred = pc.lo;
+      if (pred > (int64_t)pc.hi) pred = pc.hi;
+      e = (uint32_t)(pred > (int64_t)j ? pred - (int64_t)j : (int64_t)j - pred);
+    }
+    const uint32_t peers = __match_any_sync(0xFFFFFFFFu, p);
+    uint32_t mx = e;
+    for (uint32_t b = peers; b; b &= b - 1) {
+      const uint32_t o = __shfl_sync(peers, e, __ffs(b) - 1);
+      mx = o > mx ? o : mx;
+    }
+    if (p != 0xFFFFFFFFu && lane_id() == (uint32_t)(__ffs(peers) - 1) && mx) atomicMax(&pieces[p].err, mx);
   }
 }
 
-__global__ void k_lm_valid(ModelHead *head) { head->valid = head->kmin != kEmpty; }
+__global__ void k_lm_valid(ModelHead *head, const Ctl *ctl, int only_if_escalated) {
+  if (only_if_escalated && ctl->nesc == 0) return;
+  head->valid = head->kmin != kEmpty;
+}
 
-void launch_train_model(const Geo &g, ModelHead *head, Piece *pieces, uint32_t *tmp, cudaStream_t s) {
+void launch_train_model(const Geo &g, ModelHead *head, Piece *pieces, uint32_t *tmp, const Ctl *ctl,
+                        bool only_if_escalated, cudaStream_t s) {
   uint32_t *first = tmp, *last = tmp + kPieces;
+  const int c = only_if_escalated ? 1 : 0;
   note_launch();
-  k_lm_init<<<16, 256, 0, s>>>(head, first, last);
+  k_lm_init<<<16, 256, 0, s>>>(head, first, last, ctl, c);
+  note_launch();
+  k_lm_minmax<<<1, 64, 0, s>>>(g, head, ctl, c);
+  note_launch();
+  k_lm_scale<<<1, 1, 0, s>>>(head, ctl, c);
   const uint32_t b = nblk(g.nleaves, 256, 152 * 8);
   note_launch();
-  k_lm_minmax<<<b, 256, 0, s>>>(g, head);
+  k_lm_route<<<b, 256, 0, s>>>(g, head, first, last, ctl, c);
   note_launch();
-  k_lm_scale<<<1, 1, 0, s>>>(head);
+  k_lm_fit<<<1, 1024, 0, s>>>(g, head, first, last, pieces, ctl, c);
   note_launch();
-  k_lm_route<<<b, 256, 0, s>>>(g, head, first, last);
+  k_lm_err<<<b, 256, 0, s>>>(g, head, pieces, ctl, c);
   note_launch();
-  k_lm_fit<<<1, 1024, 0, s>>>(g, head, first, last, pieces);
-  note_launch();
-  k_lm_err<<<b, 256, 0, s>>>(g, head, pieces);
-  note_launch();
-  k_lm_valid<<<1, 1, 0, s>>>(head);
+  k_lm_valid<<<1, 1, 0, s>>>(head, ctl, c);
 }
 
 }  // namespace gpk

@@ -46,7 +46,7 @@ int status_address(uint64_t **out) {
 extern "C" int gpma_export_sorted_noalloc(gpma_t h, uint64_t *d_out, uint64_t cap, uint64_t *n_out,
                                           void *stream) {
   if (!h || !n_out || (cap && !d_out)) return GPMA_EINVAL;
-  const gpk::HandleView v = gpk::handle_view(h);
+  const gpk::HandleView v = gpk::handle_view(h, (cudaStream_t)stream);
   if (v.poisoned) return v.poisoned;
   if (v.geo->C > kMaxSlots) return GPMA_EINVAL;  // larger than the fixed scratch
   uint64_t *status = nullptr;

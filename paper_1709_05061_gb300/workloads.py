@@ -146,3 +146,44 @@ class SlidingWindow:
 
     def live(self) -> np.ndarray:
         return self.stream[self.head: self.tail]
+
+
+def log_uniform_ints(rng, lo: int, hi: int, n: int) -> np.ndarray:
+    """``n`` integers whose logarithm is uniform on [log lo, log hi]."""
+    return np.exp(rng.uniform(np.log(lo), np.log(hi), n)).astype(np.int64).clip(lo, hi)
+
+
+class ManyGraphWorkload:
+    """Independent R-MAT sliding-window streams for the batched many-graph update.
+
+    Graph i holds a window of ``edges[i]`` edges (log-uniform in [e_lo, e_hi])
+    over 2^scale[i] vertices, scale = ceil(log2(edges / 8)) clamped to [8, 22]
+    (an edge factor of 8, enough distinct pairs for the stream to go on).  Every
+    step gives graph i an uneven batch of ``batch[i]`` updates (log-uniform in
+    [b_lo, b_hi], at most the window), half inserts and half deletes.  Each
+    graph's stream has its own seed (seed + i), so the workload is seeded."""
+
+    def __init__(self, n_graphs: int, e_lo: int, e_hi: int, b_lo: int, b_hi: int, steps: int, seed: int = 11):
+        rng = np.random.Generator(np.random.PCG64(seed))
+        self.edges = log_uniform_ints(rng, e_lo, e_hi, n_graphs)
+        self.batch = np.minimum(log_uniform_ints(rng, b_lo, b_hi, n_graphs), self.edges) // 2 * 2
+        self.batch = np.maximum(self.batch, 2)
+        self.scale = np.clip(np.ceil(np.log2(self.edges / 8.0)).astype(np.int64), 8, 22)
+        self.steps = int(steps)
+        self.windows = []
+        for i in range(n_graphs):
+            half = int(self.batch[i]) // 2
+            need = int(self.edges[i]) + self.steps * half
+            st = rmat_stream(int(self.scale[i]), need, seed=seed + 1 + i)
+            self.windows.append(SlidingWindow(st, int(self.edges[i])))
+
+    @property
+    def n_graphs(self) -> int:
+        return len(self.windows)
+
+    def n_vertices(self, i: int) -> int:
+        return 1 << int(self.scale[i])
+
+    def slide(self):
+        """(inserts, deletes) of the next step, one pair per graph."""
+        return [w.slide(int(b) // 2) for w, b in zip(self.windows, self.batch)]

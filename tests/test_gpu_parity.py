@@ -282,3 +282,30 @@ def test_learned_search_matches_plain():
         assert np.array_equal(a, b2), f"step {step}: learned and plain layouts differ"
     assert np.array_equal(host(learned.layout()), o.layout())
     assert learned.check() == 0
+
+
+def test_growth_without_stats_matches_oracle():
+    """Insert-only batches of about a tenth of the array, no stats: batches that
+    may overflow the root replay the graph that grows the array on the device
+    (into the spare of height h+1); layout and capacity follow the oracle."""
+    V = 4096
+    stream = W.er_stream(V, 120_000, seed=21)
+    g = gp.Graph(V, leaf_size=32)
+    o = oracle.OraclePMA(V, L=32)
+    caps = set()
+    at = 0
+    while at < stream.size:
+        k = max(256, (V + at) // 10)
+        ins = stream[at: at + k]
+        at += k
+        g.update(dev(ins), None)
+        o.update(ins)
+        lg = host(g.layout())
+        lo = o.layout()
+        assert lg.size == lo.size == g.capacity
+        assert np.array_equal(lg, lo)
+        caps.add(g.capacity)
+    g.status()
+    assert len(caps) >= 4
+    assert g.check() == 0
+    assert g.num_edges() == stream.size
