@@ -29,6 +29,8 @@ import time
 import numpy as np
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
+# more hardware work queues: the batched many-graph update forks onto one stream per graph
+os.environ.setdefault("CUDA_DEVICE_MAX_CONNECTIONS", "32")
 sys.path.insert(0, ROOT)
 
 SCALE, WINDOW, LEAF = 20, 16_000_000, 64

@@ -509,7 +509,7 @@ bool capture_update(gpma *h, FrontArgs &f, uint32_t nb, bool stats, bool grow, G
                          t);
     if (h->mhead) launch_train_model(g, h->mhead, h->mpieces, h->mtmp, h->ctl, false, t);
   };
-  launch_sort(f, nb, gc.cap);
+  if (!small_front(nb)) launch_sort(f, nb, gc.cap);
   launch_leaf_pass(g, h->ctl, h->w, nb, gc.cap);
   note_launch();
   k_gate<<<1, 1, 0, gc.cap>>>(h->ctl, cond);
@@ -653,7 +653,8 @@ int update(gpma *h, const uint64_t *ins, uint64_t n_ins, const uint64_t *del, ui
   // level-0 merges move pivots only inside their leaves and the search widens
   // its window when the model has drifted; retrain now and then all the same
   if (h->mhead && ++h->since_train >= 64) train_model(h, s);
-  launch_prep(f, s);
+  if (small_front(n)) launch_small_front(f, s);
+  else launch_prep(f, s);
   // the root can only refuse inserts when the count might exceed its bound
   const bool may_fail = h->count_ub + n_ins > h->geo.maxc[h->geo.h];
   // such a batch still replays a graph (no host wait) when one level of growth
@@ -668,7 +669,7 @@ int update(gpma *h, const uint64_t *ins, uint64_t n_ins, const uint64_t *del, ui
   bool resized = false;
   if ((!may_fail || grow) && h->graphs->enabled) {
     // replay: sort .. segment merge as one graph, grids sized for the bucket
-    uint64_t bucket = 2048;
+    uint64_t bucket = kSmallBatch;  // one graph serves every batch of the fused front end
     while (bucket < n) bucket <<= 1;
     const uint32_t nb = (uint32_t)bucket;
     // the key layout of a guard batch differs: never share its graph
@@ -690,7 +691,7 @@ int update(gpma *h, const uint64_t *ins, uint64_t n_ins, const uint64_t *del, ui
   } else {
     {
       Phase ph(h->prof, GPMA_PROF_SORT, s);
-      launch_sort(f, n, s);
+      if (!small_front(n)) launch_sort(f, n, s);
     }
     {
       Phase ph(h->prof, GPMA_PROF_LEAF, s);

@@ -67,6 +67,10 @@ struct Work {
 uint32_t sort_tiles(uint64_t n);
 uint32_t comp_tiles(uint64_t n);
 // k_init_batch + k_prep (take the batch's own pointers and sizes)
+// batches of at most kSmallBatch keys: validation .. run heads in one block
+constexpr uint32_t kSmallBatch = 4096;
+bool small_front(uint64_t n);
+void launch_small_front(const FrontArgs &f, cudaStream_t s);
 void launch_prep(const FrontArgs &f, cudaStream_t s);
 // radix passes, unique/cancel + leaf search, run heads; grids for nb >= batch keys
 void launch_sort(const FrontArgs &f, uint64_t nb, cudaStream_t s);

@@ -8,6 +8,8 @@
 //                 leaf search of every surviving key (learned model when trained,
 //                 else binary search; both give the same leaf)
 //   k_runs        heads of the runs of equal leaf (single-pass compaction)
+//   k_small_front all of the above in one block for batches of at most
+//                 kSmallBatch keys (bitonic sort in shared memory)
 #include "gpma_dev.cuh"
 #include "gpma_launch.h"
 #include "scan_dev.cuh"
@@ -242,6 +244,186 @@ __global__ void __launch_bounds__(kScanThreads) k_runs(const uint32_t *__restric
   }
 }
 
+// ---- small batches: the whole front end in one block ---------------------------------------
+// Sort word = (compressed key without tag) << 1 | tag.  Inserts (tag 0) order
+// before deletes (tag 1) of the same key, and equal words are identical, so the
+// sorted sequence equals the stable radix sort's.  Each thread owns `ipt`
+// consecutive positions for the two compactions (survivors, run heads).
+__device__ __forceinline__ uint32_t block_excl_scan(uint32_t v, uint32_t *wsum, uint32_t *total) {
+  const uint32_t lane = lane_id(), wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const uint32_t inc = warp_incl_scan(v);
+  if (lane == 31) wsum[wid] = inc;
+  __syncthreads();
+  if (wid == 0) {
+    const uint32_t x = lane < nw ? wsum[lane] : 0u;
+    const uint32_t xi = warp_incl_scan(x);
+    wsum[lane] = xi - x;
+    if (lane == 31) wsum[32] = xi;
+  }
+  __syncthreads();
+  const uint32_t r = wsum[wid] + inc - v;
+  *total = wsum[32];
+  __syncthreads();  // wsum is reused by the next scan
+  return r;
+}
+
+// Leaf search with a sampled first stage: S evenly spaced pivots F[i * stride]
+// sit in shared memory, the non-empty ones compacted in order.  The last sampled
+// pivot <= k and the first one > k bracket the answer (eff(lo - 1) <= k and
+// eff(hi) > k), and search_first_above finishes inside that bracket, so the leaf
+// equals leaf_search's.
+__device__ __forceinline__ uint32_t sampled_leaf_search(const uint64_t *__restrict__ F, uint64_t nleaves,
+                                                        const uint64_t *cv, const uint32_t *cpos, uint32_t cnt,
+                                                        uint64_t k) {
+  uint32_t a = 0, b = cnt;  // first compacted sample with value > k
+  while (a < b) {
+    const uint32_t mid = (a + b) >> 1;
+    if (cv[mid] > k) b = mid; else a = mid + 1;
+  }
+  const uint64_t lo = a ? (uint64_t)cpos[a - 1] + 1 : 0;
+  const uint64_t hi = a < cnt ? (uint64_t)cpos[a] : nleaves;
+  const uint64_t p = search_first_above(F, lo, hi, k);
+  return p ? (uint32_t)(p - 1) : 0u;
+}
+
+__global__ void __launch_bounds__(1024) k_small_front(PrepArgs a, const uint64_t *__restrict__ ins,
+                                                      const uint64_t *__restrict__ del, Ctl *ctl,
+                                                      const uint64_t *__restrict__ F, uint64_t nleaves,
+                                                      uint64_t *__restrict__ ukey, uint8_t *__restrict__ utag,
+                                                      uint32_t *__restrict__ uleaf, uint32_t *__restrict__ run_start,
+                                                      uint32_t *__restrict__ run_leaf, const ModelHead *mhead,
+                                                      const Piece *__restrict__ mpieces, uint32_t P, uint32_t S) {
+  extern __shared__ uint64_t sk[];           // P sort words
+  uint64_t *sw = sk + P;                     // P survivor words
+  uint64_t *cv = sw + P;                     // S compacted sampled pivots
+  uint32_t *sleaf = (uint32_t *)(cv + S);    // P leaves of the survivors
+  uint32_t *cpos = sleaf + P;                // S leaf indices of the compacted samples
+  __shared__ uint32_t wsum[33];
+  const uint32_t n = a.n_ins + a.n_del, t = threadIdx.x, nt = blockDim.x;
+  const uint32_t ipt = (P + nt - 1) / nt, e0 = t * ipt;
+  const uint32_t spt = (S + nt - 1) / nt, s0 = t * spt;
+  const uint64_t stride = nleaves / S;
+  if (t == 0) {
+    ctl->err = 0;
+    ctl->n = n;
+    ctl->epoch += kSlotsPerBatch;
+    ctl->nesc = ctl->nfail = ctl->nlong = ctl->resized = 0;
+    ctl->m = ctl->nruns = ctl->npend = ctl->neruns = ctl->nsegs = ctl->nleafw = 0;
+    for (int i = 0; i < 16; i++) ctl->ticket[i] = 0;
+    ctl->n_inserted = ctl->n_deleted = 0;
+    ctl->st_cov_touched = ctl->st_l0_only = ctl->st_empties = 0;
+    ctl->levels_climbed = 0;
+    ctl->n_merged0 = 0;
+    for (int i = 0; i < kMaxLv; i++) ctl->merges[i] = 0;
+  }
+  bool bad = false;
+  for (uint32_t i = t; i < P; i += nt) {
+    uint64_t word = ~0ull;  // padding sorts last
+    if (i < n) {
+      const uint32_t tag = i >= a.n_ins;
+      const uint64_t key = tag ? del[i - a.n_ins] : ins[i];
+      bool ok;
+      if (a.raw) {
+        ok = (key >> 63) == 0;
+      } else {
+        const uint64_t src = key >> 32, dst = key & 0xFFFFFFFFull;
+        ok = src < a.V && (dst < a.V || (a.allow_guards && !tag && dst == 0xFFFFFFFFull));
+      }
+      bad |= !ok;
+      word = ok ? ((compress(key, 0, a) << 1) | tag) : 0ull;
+    }
+    sk[i] = word;
+  }
+  // sampled pivots (the stores land in cv; compacted in place below)
+  uint32_t nonempty = 0;
+  for (uint32_t q = 0; q < spt; q++) {
+    const uint32_t i = s0 + q;
+    if (i >= S) break;
+    const uint64_t f = __ldg(F + i * stride);
+    cv[i] = f;
+    nonempty += f != kEmpty;
+  }
+  if (__syncthreads_or(bad)) {
+    if (t == 0) atomicOr(&ctl->err, kErrKey);
+    return;  // nothing of the batch is applied
+  }
+  // bitonic sort, ascending
+  for (uint32_t k = 2; k <= P; k <<= 1) {
+    for (uint32_t j = k >> 1; j > 0; j >>= 1) {
+      for (uint32_t i = t; i < P / 2; i += nt) {
+        const uint32_t lo = ((i & ~(j - 1)) << 1) | (i & (j - 1)), hi = lo + j;
+        const uint64_t x = sk[lo], y = sk[hi];
+        if ((x > y) == ((lo & k) == 0)) {
+          sk[lo] = y;
+          sk[hi] = x;
+        }
+      }
+      __syncthreads();
+    }
+  }
+  // compact the non-empty samples in order (read own values before the scan's barrier)
+  uint64_t mine[8];
+  for (uint32_t q = 0; q < spt && q < 8; q++) mine[q] = s0 + q < S ? cv[s0 + q] : kEmpty;
+  uint32_t cnt;
+  uint32_t co = block_excl_scan(nonempty, wsum, &cnt);
+  for (uint32_t q = 0; q < spt && q < 8; q++) {
+    if (mine[q] == kEmpty) continue;
+    cv[co] = mine[q];
+    cpos[co] = (uint32_t)((s0 + q) * stride);
+    co++;
+  }
+  // unique + cancellation (reading R2) on positions [e0, e0 + ipt)
+  uint32_t keep = 0;
+  for (uint32_t q = 0; q < ipt; q++) {
+    const uint32_t e = e0 + q;
+    if (e >= n) break;
+    const uint64_t k = sk[e] >> 1;
+    const bool kept = (sk[e] & 1) ? (e == 0 || (sk[e - 1] >> 1) != k) : (e + 1 == n || (sk[e + 1] >> 1) != k);
+    keep |= (uint32_t)kept << q;
+  }
+  uint32_t m;
+  uint32_t off = block_excl_scan(__popc(keep), wsum, &m);
+  for (uint32_t q = 0; q < ipt; q++)
+    if ((keep >> q) & 1) sw[off++] = sk[e0 + q];
+  __syncthreads();
+  // the leaf of every survivor (reading R4), one survivor per thread at a time
+  ModelHead hd;
+  hd.valid = 0;
+  if (mhead) hd = *mhead;
+  const bool learned = hd.valid != 0;
+  for (uint32_t e = t; e < m; e += nt) {
+    const uint64_t w = sw[e];
+    const uint64_t key = expand(w >> 1, a);
+    const uint32_t leaf = learned ? learned_leaf_search(hd, mpieces, F, nleaves, key)
+                                  : sampled_leaf_search(F, nleaves, cv, cpos, cnt, key);
+    ukey[e] = key;
+    utag[e] = (uint8_t)(w & 1);
+    uleaf[e] = leaf;
+    sleaf[e] = leaf;
+  }
+  __syncthreads();
+  // run heads over the m survivors
+  uint32_t head = 0;
+  for (uint32_t q = 0; q < ipt; q++) {
+    const uint32_t e = e0 + q;
+    if (e >= m) break;
+    head |= (uint32_t)(e == 0 || sleaf[e] != sleaf[e - 1]) << q;
+  }
+  uint32_t nr;
+  uint32_t ro = block_excl_scan(__popc(head), wsum, &nr);
+  for (uint32_t q = 0; q < ipt; q++) {
+    if (!((head >> q) & 1)) continue;
+    run_start[ro] = e0 + q;
+    run_leaf[ro] = sleaf[e0 + q];
+    ro++;
+  }
+  if (t == 0) {
+    ctl->m = m;
+    ctl->nruns = nr;
+    run_start[nr] = m;
+  }
+}
+
 // ---- host launchers ----------------------------------------------------------------------
 static uint32_t grid_for(uint64_t n, uint32_t per_block, uint32_t cap) {
   uint64_t g = (n + per_block - 1) / per_block;
@@ -252,6 +434,28 @@ static uint32_t grid_for(uint64_t n, uint32_t per_block, uint32_t cap) {
 
 uint32_t sort_tiles(uint64_t n) { return (uint32_t)((n + kSortTile - 1) / kSortTile); }
 uint32_t comp_tiles(uint64_t n) { return (uint32_t)((n + kScanTile - 1) / kScanTile); }
+
+bool small_front(uint64_t n) { return n <= kSmallBatch; }
+
+void launch_small_front(const FrontArgs &f, cudaStream_t s) {
+  const PrepArgs &a = f.prep;
+  const uint32_t n = a.n_ins + a.n_del;
+  constexpr uint32_t kSamples = 2048;
+  static bool attr = false;
+  if (!attr) {
+    cudaFuncSetAttribute(k_small_front, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         kSmallBatch * 20 + kSamples * 12);
+    attr = true;
+  }
+  uint32_t P = 64;
+  while (P < n) P <<= 1;
+  const uint32_t nt = P >= 2048 ? 1024 : 256;  // at most 4 positions and 8 samples per thread
+  const uint64_t nl = f.geo->nleaves;
+  const uint32_t S = nl < kSamples ? (uint32_t)nl : kSamples;  // nleaves is a power of two
+  note_launch();
+  k_small_front<<<1, nt, P * 20 + S * 12, s>>>(a, f.ins, f.del, f.ctl, f.geo->F, nl, f.ukey, f.utag, f.uleaf,
+                                               f.run_start, f.run_leaf, f.mhead, f.mpieces, P, S);
+}
 
 void launch_prep(const FrontArgs &f, cudaStream_t s) {
   const PrepArgs &a = f.prep;
