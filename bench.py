@@ -56,6 +56,9 @@ def parse():
     ap.add_argument("--seed", type=int, default=1)
     ap.add_argument("--learned-study", action="store_true",
                     help="only compare the learned and the plain leaf search on the power-law workload")
+    ap.add_argument("--serve-study", action="store_true",
+                    help="only run the served stream (R-MAT scale 24, Poisson updates and queries)")
+    ap.add_argument("--serve-requests", type=int, default=1500)
     ap.add_argument("--many-study", action="store_true",
                     help="only time the batched many-graph update (64 uneven R-MAT graphs)")
     return ap.parse_args()
@@ -468,6 +471,58 @@ def many_study(a):
     return res
 
 
+def serve_study(a):
+    """Served stream on a resident R-MAT scale-24 graph (2^28 samples, seed 24,
+    generated on the device; about 2.6e8 distinct edges, the last 6e7 of the
+    stream held back as future inserts).  Requests: Poisson arrivals, updates of
+    log-uniform 1e2..1e5 keys (half new edges, half the window's oldest) mixed 4:1
+    with queries (BFS from a uniform random source, CC, PageRank-10), update keys
+    arriving in pinned host memory.  First a closed loop measures capacity
+    (requests/s with every request available at once), then open loops at 50%,
+    80% and 95% of it report p50/p99 latency (arrival to result on the host) and
+    sustained edge updates/s."""
+    import torch
+    import paper_1709_05061_gb300 as gp
+    from paper_1709_05061_gb300 import serve as S
+    from paper_1709_05061_gb300 import workloads as W
+    gp.build()
+    torch.cuda.set_device(0)
+    scale = 24
+    t0 = time.perf_counter()
+    st = W.rmat_stream_device(scale, 1 << 28, seed=24)
+    gen_s = time.perf_counter() - t0
+    reserve = 60_000_000
+    window = st.numel() - reserve
+    V = 1 << scale
+    g = gp.Graph(V, leaf_size=LEAF)
+    t0 = time.perf_counter()
+    g.update(st[:window])
+    g.status()
+    load_s = time.perf_counter() - t0
+    host_stream = st.cpu().numpy().view(np.uint64)
+    del st
+    torch.cuda.empty_cache()
+    win = W.SlidingWindow(host_stream, window)
+    srv = S.Server(g, max_batch_keys=1 << 20, result_slots=4, max_inflight=2, keep_results=False)
+    n = a.serve_requests
+    # warm-up (graph capture for every batch size bucket, first analytics calls)
+    srv.run(S.make_requests(60, V, win, rate=1.0, seed=100), realtime=False)
+    out = {"workload": f"R-MAT scale 24 (.57/.19/.19/.05, 2^28 samples, seed 24, device-generated), "
+                       f"{window} edges resident, capacity {g.capacity} slots; requests: Poisson, updates "
+                       f"log-uniform 1e2..1e5 (50/50) : queries (BFS / CC / PageRank-10) = 4 : 1",
+           "generate_s": gen_s, "bulk_load_s": load_s, "requests_per_run": n}
+    cap = srv.run(S.make_requests(n, V, win, rate=1.0, seed=101), realtime=False)
+    out["closed_loop"] = cap
+    for frac in (0.5, 0.8, 0.95):
+        rate = frac * cap["requests_per_s"]
+        r = srv.run(S.make_requests(n, V, win, rate=rate, seed=102 + int(frac * 100)), realtime=True)
+        r["offered_rate_per_s"] = rate
+        out[f"load_{int(frac * 100)}"] = r
+    out["check"] = g.check()
+    g.close()
+    return out
+
+
 # ---- the oracle (CPU) --------------------------------------------------------------------------------
 def run_oracle(a, stream, steps, max_seconds=None, skip=0):
     import oracle
@@ -512,6 +567,9 @@ def main():
         return 0
     if a.many_study:
         print(json.dumps({"many_study": many_study(a)}), flush=True)
+        return 0
+    if a.serve_study:
+        print(json.dumps({"serve_study": serve_study(a)}), flush=True)
         return 0
 
     if a.impl == "reference":

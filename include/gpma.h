@@ -103,8 +103,11 @@ int gpma_destroy(gpma_t h);
  * level whose bound admits it; above the root the capacity doubles until all
  * keys fit.  Every key must have src, dst < n_vertices (raw mode: key < 2^63),
  * else GPMA_EINVAL and nothing changes.  n_ins + n_del < 2^30.
- * With stats == NULL the call returns after enqueueing (except for a rare
- * stream wait when the capacity might have to grow); a device-detected
+ * With stats == NULL the call returns after enqueueing; a batch that might
+ * overflow the root grows the array on the device into a preallocated spare of
+ * twice the capacity, and the next call on the handle first waits for that batch
+ * to learn the geometry.  Only a batch that might need more than one doubling
+ * (a bulk load) waits inside the call.  A device-detected
  * GPMA_EINVAL is then reported by the next gpma_status().  With stats != NULL
  * the call waits and returns the batch's status. */
 int gpma_update_batch(gpma_t h, const uint64_t *d_ins, uint64_t n_ins, const uint64_t *d_del,
@@ -128,7 +131,9 @@ int gpma_status(gpma_t h, void *stream);
 
 /* Breadth-first search from src over out-edges (Algorithm "BFS", Sec. 4.2, with
  * the gap test of Algorithm "GPU-based BFS Neighbour Gathering").  d_depth[V]
- * receives the hop count, -1 where unreachable.  Waits for the stream. */
+ * receives the hop count, -1 where unreachable.  Asynchronous: one cooperative
+ * kernel whose grid barriers are bounded; a barrier that gave up is reported as
+ * GPMA_ETIMEOUT by the next gpma_status (the depths are then not valid). */
 int gpma_bfs(gpma_t h, uint32_t src, int32_t *d_depth, void *stream);
 
 /* Weakly connected components (the Connected Component application of Sec. 6.1

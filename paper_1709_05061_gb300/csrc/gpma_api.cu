@@ -960,9 +960,7 @@ int gpma_bfs(gpma_t h, uint32_t src, int32_t *d_depth, void *stream) {
   cudaStream_t s = (cudaStream_t)stream;
   if (ensure_analytics(h, 1, s)) return GPMA_ENOMEM;
   Phase ph(h->prof, GPMA_PROF_BFS, s);
-  const int rb = run_bfs(h->geo, src, d_depth, h->q0, h->q1, h->q2, h->counter, h->h_counter, s);
-  if (rb == -2) return poison(h, GPMA_ETIMEOUT);
-  if (rb < 0) return poison(h, GPMA_EDEVICE);
+  if (run_bfs(h->geo, src, d_depth, h->q0, h->q1, h->q2, h->counter, h->ctl, s) < 0) return poison(h, GPMA_EDEVICE);
   return cuda_ok(h);
 }
 

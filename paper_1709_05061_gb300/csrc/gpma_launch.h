@@ -128,7 +128,7 @@ void launch_pr_apply(const Geo &g, float damping, float *rank, uint64_t *y, uint
 // BFS in one cooperative launch; counter >= 16 u32, h_counter pinned; waits for the
 // stream; returns 0, -1 on a CUDA error, -2 when a bounded barrier wait gave up
 int run_bfs(const Geo &g, uint32_t src, int32_t *depth, uint32_t *q0, uint32_t *q1, uint32_t *q2,
-            uint32_t *counter, uint32_t *h_counter, cudaStream_t s);
+            uint32_t *counter, Ctl *ctl, cudaStream_t s);
 void launch_cc(const Geo &g, uint32_t *label, cudaStream_t s);
 
 // read-only view of a handle (defined beside the handle in gpma_api.cu)

@@ -352,8 +352,13 @@ __global__ void k_bfs_setup(int32_t *depth, uint32_t src, uint32_t *q0, uint32_t
   bar[1] = 0;
 }
 
+// a barrier wait that gave up becomes the handle's sticky timeout error
+__global__ void k_bfs_flag(const uint32_t *err, Ctl *ctl) {
+  if (*err) atomicOr(&ctl->sticky, kErrTimeout);
+}
+
 int run_bfs(const Geo &g, uint32_t src, int32_t *depth, uint32_t *q0, uint32_t *q1, uint32_t *q2,
-            uint32_t *counter, uint32_t *h_counter, cudaStream_t s) {
+            uint32_t *counter, Ctl *ctl, cudaStream_t s) {
   static int grid = 0;
   if (!grid) {
     int dev = 0, sms = 0, per_sm = 0;
@@ -378,9 +383,9 @@ int run_bfs(const Geo &g, uint32_t src, int32_t *depth, uint32_t *q0, uint32_t *
   note_launch();
   if (cudaLaunchCooperativeKernel((const void *)k_bfs_persist, dim3(grid), dim3(256), args, 0, s) != cudaSuccess)
     return -1;
-  cudaMemcpyAsync(h_counter, err, sizeof(uint32_t), cudaMemcpyDeviceToHost, s);
-  if (cudaStreamSynchronize(s) != cudaSuccess) return -1;
-  return *h_counter ? -2 : 0;  // -2: a bounded barrier wait gave up
+  note_launch();
+  k_bfs_flag<<<1, 1, 0, s>>>(err, ctl);
+  return 0;
 }
 
 // ---- connected components -------------------------------------------------------------------------

@@ -187,3 +187,35 @@ class ManyGraphWorkload:
     def slide(self):
         """(inserts, deletes) of the next step, one pair per graph."""
         return [w.slide(int(b) // 2) for w, b in zip(self.windows, self.batch)]
+
+
+def rmat_stream_device(scale: int, n_samples: int, seed: int = 24, abcd=RMAT_GRAPH500):
+    """R-MAT stream generated on the current CUDA device (torch's seeded Philox
+    generator) for sizes where the host generator is slow: the same definition as
+    ``rmat_stream`` (independent quadrant draws per level, one seeded vertex
+    permutation, self-loops and repeats dropped keeping first occurrences in draw
+    order), but a different random sequence.  Returns an int64 CUDA tensor of keys
+    in stream order."""
+    import torch
+    a, b, c, _ = abcd
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(seed)
+    n = 1 << scale
+    perm = torch.randperm(n, generator=gen, device="cuda")
+    src = torch.zeros(n_samples, dtype=torch.int64, device="cuda")
+    dst = torch.zeros(n_samples, dtype=torch.int64, device="cuda")
+    for _ in range(scale):
+        r = torch.rand(n_samples, generator=gen, device="cuda")
+        sb = r >= a + b
+        db = ((r >= a) & (r < a + b)) | (r >= a + b + c)
+        src = (src << 1) | sb
+        dst = (dst << 1) | db
+        del r, sb, db
+    keep = src != dst
+    keys = (perm[src[keep]] << 32) | perm[dst[keep]]
+    del src, dst, keep
+    uniq, inv = torch.unique(keys, sorted=True, return_inverse=True)
+    first = torch.full((uniq.numel(),), keys.numel(), dtype=torch.int64, device="cuda")
+    first.scatter_reduce_(0, inv, torch.arange(keys.numel(), device="cuda"), reduce="amin")
+    del keys, inv
+    return uniq[torch.argsort(first)]

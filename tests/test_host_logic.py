@@ -45,3 +45,60 @@ def test_pick_leaf_size():
         with pytest.raises(ValueError):
             tune.pick_leaf_size(bad)
     assert all(L & (L - 1) == 0 for L in tune.LEAF_CANDIDATES)
+
+
+def _req(rid, kind, t, n=0):
+    from paper_1709_05061_gb300 import serve as S
+    k = np.arange(n, dtype=np.uint64)
+    return S.Request(rid, kind, t, ins=k if kind == S.UPDATE else None, dels=k if kind == S.UPDATE else None)
+
+
+def test_admit_order_coalescing_and_budget():
+    from paper_1709_05061_gb300 import serve as S
+    q = [_req(0, S.UPDATE, 0.0, 10), _req(1, S.UPDATE, 0.1, 10), _req(2, S.UPDATE, 0.2, 50),
+         _req(3, S.BFS, 0.3), _req(4, S.UPDATE, 0.4, 5), _req(5, S.CC, 0.5)]
+    # nothing has arrived yet
+    assert S.admit(q, 0, -1.0, 100) == (None, 0)
+    # at t=0.15 the first two updates coalesce (40 keys), the third has not arrived
+    op, h = S.admit(q, 0, 0.15, 100)
+    assert op.kind == S.UPDATE and [r.rid for r in op.reqs] == [0, 1] and h == 2
+    # budget: 20 + 20 + 100 keys > 100 stops before request 2, which then goes alone
+    op, h = S.admit(q, 0, 1.0, 100)
+    assert [r.rid for r in op.reqs] == [0, 1] and h == 2
+    op, h = S.admit(q, h, 1.0, 100)
+    assert [r.rid for r in op.reqs] == [2] and h == 3
+    # a query is never coalesced and never overtaken by a later update
+    op, h = S.admit(q, h, 1.0, 100)
+    assert op.kind == S.BFS and [r.rid for r in op.reqs] == [3] and h == 4
+    op, h = S.admit(q, h, 1.0, 100)
+    assert [r.rid for r in op.reqs] == [4] and h == 5
+    op, h = S.admit(q, h, 1.0, 100)
+    assert op.kind == S.CC and h == 6
+    assert S.admit(q, h, 1.0, 100) == (None, 6)
+    # one request larger than the budget still goes; coalescing can be turned off
+    op, h = S.admit([_req(0, S.UPDATE, 0.0, 500)], 0, 1.0, 100)
+    assert len(op.reqs) == 1 and h == 1
+    op, h = S.admit(q, 0, 1.0, 100, coalesce=False)
+    assert [r.rid for r in op.reqs] == [0] and h == 1
+
+
+def test_make_requests_mix_and_arrivals():
+    from paper_1709_05061_gb300 import serve as S
+    stream = W.er_stream(500, 40_000, seed=3)
+    win = W.SlidingWindow(stream, 10_000)
+    reqs = S.make_requests(400, 500, win, rate=1000.0, seed=5, upd_lo=10, upd_hi=200)
+    kinds = [r.kind for r in reqs]
+    n_upd = kinds.count(S.UPDATE)
+    assert 0.72 < n_upd / len(reqs) < 0.88  # 4:1
+    assert all(kinds.count(k) > 10 for k in (S.BFS, S.CC, S.PAGERANK))
+    t = np.array([r.arrival for r in reqs])
+    assert t[0] == 0.0 and np.all(np.diff(t) >= 0)
+    assert 0.3 < t[-1] < 0.5  # 400 arrivals at 1000/s
+    live = set(win.initial.tolist())
+    for r in reqs:
+        if r.kind == S.UPDATE:
+            assert 5 <= r.ins.size <= 100 and r.ins.size == r.dels.size
+            assert set(r.dels.tolist()) <= live and not (set(r.ins.tolist()) & live)
+            live = (live - set(r.dels.tolist())) | set(r.ins.tolist())
+        else:
+            assert 0 <= r.src < 500
