@@ -91,6 +91,22 @@ def stream_needed(a, reference: bool):
     return n
 
 
+def max_over_ranks(x: float, dist, device) -> float:
+    """The largest ``x`` over all ranks (the job's time is its slowest rank's)."""
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([x], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(world: int, batch: int, steps: int, ms: float) -> float:
+    """Whole-job edge updates per second: every rank applies ``steps`` batches of
+    ``batch`` updates to its own replica; ``ms`` is the max over ranks."""
+    return world * batch * steps / (ms * 1e-3)
+
+
 def make_stream(a, rank, reference=False):
     from paper_1709_05061_gb300 import workloads as W
     return W.rmat_stream(a.scale, stream_needed(a, reference), seed=a.seed + 1000 * rank,
@@ -271,10 +287,7 @@ def run_gpu(a, stream, rank, world, dist):
     prof = gp.gpma_profile_read(g.h, reset=True)
     gp.gpma_status(g.h)
     ms = e0.elapsed_time(e1)
-    if dist:
-        t = torch.tensor([ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(ms, dist, dev)
     out["ms_total"] = ms
     out["launches"] = launches
     out["profile"] = prof
@@ -334,11 +347,8 @@ def run_gpu(a, stream, rank, world, dist):
         torch.cuda.synchronize()
         wall = (time.perf_counter() - t0) * 1e3
         ems = max(f0.elapsed_time(f1), wall)
-        if dist:
-            t = torch.tensor([ems], device=dev, dtype=torch.float64)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ems = float(t.item())
-        out["e2e"] = {"value": world * a.batch * a.steps / (ems * 1e-3), "unit": "edge updates/s",
+        ems = max_over_ranks(ems, dist, dev)
+        out["e2e"] = {"value": job_value(world, a.batch, a.steps, ems), "unit": "edge updates/s",
                       "h2d_bytes_per_step": 2 * half * 8, "d2h_bytes_per_step": 3 * 4 * V,
                       "ms_per_step": ems / a.steps}
         gp.gpma_status(g.h)
@@ -463,7 +473,7 @@ def many_study(a):
         res[f"{label}_batched_equals_sequential"] = same
     res["workload"] = (f"64 R-MAT graphs (.57/.19/.19/.05), windows log-uniform in [2^10, 2^22] edges "
                        f"(total {int(wl.edges.sum())}), batches log-uniform in [64, 2^18] "
-                       f"(total {int(wl.batch.sum())} updates per step), seed 11")
+                       f"(total {int(wl.batch.sum())} updates per step), size seed 11, graph seeds 1000+g")
     res["tuned_leaf_sizes"] = {str(L): tuned.count(L) for L in sorted(set(tuned))}
     res["autotune_seconds"] = tune_s
     res["speedup_batched_vs_sequential_L64"] = res["L64_sequential"]["p50_ms"] / res["L64_batched"]["p50_ms"]
@@ -599,7 +609,7 @@ def main():
     stream = make_stream(a, rank)
     out = run_gpu(a, stream, rank, world, dist)
     ms = out["ms_total"]
-    value = world * a.batch * a.steps / (ms * 1e-3)
+    value = job_value(world, a.batch, a.steps, ms)
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "edge updates/s", "n_gpus": world, "steps": a.steps,
                 "warmup": a.warmup, "ms_per_step": ms / a.steps, "higher_is_better": True, "scaling": "weak",

@@ -160,10 +160,11 @@ class ManyGraphWorkload:
     over 2^scale[i] vertices, scale = ceil(log2(edges / 8)) clamped to [8, 22]
     (an edge factor of 8, enough distinct pairs for the stream to go on).  Every
     step gives graph i an uneven batch of ``batch[i]`` updates (log-uniform in
-    [b_lo, b_hi], at most the window), half inserts and half deletes.  Each
-    graph's stream has its own seed (seed + i), so the workload is seeded."""
+    [b_lo, b_hi], at most the window), half inserts and half deletes.  ``seed``
+    draws the sizes; graph i's stream has seed graph_seed0 + i."""
 
-    def __init__(self, n_graphs: int, e_lo: int, e_hi: int, b_lo: int, b_hi: int, steps: int, seed: int = 11):
+    def __init__(self, n_graphs: int, e_lo: int, e_hi: int, b_lo: int, b_hi: int, steps: int, seed: int = 11,
+                 graph_seed0: int = 1000):
         rng = np.random.Generator(np.random.PCG64(seed))
         self.edges = log_uniform_ints(rng, e_lo, e_hi, n_graphs)
         self.batch = np.minimum(log_uniform_ints(rng, b_lo, b_hi, n_graphs), self.edges) // 2 * 2
@@ -174,7 +175,7 @@ class ManyGraphWorkload:
         for i in range(n_graphs):
             half = int(self.batch[i]) // 2
             need = int(self.edges[i]) + self.steps * half
-            st = rmat_stream(int(self.scale[i]), need, seed=seed + 1 + i)
+            st = rmat_stream(int(self.scale[i]), need, seed=graph_seed0 + i)
             self.windows.append(SlidingWindow(st, int(self.edges[i])))
 
     @property
