@@ -23,6 +23,7 @@ _lib = None
 
 EMPTY = np.uint64(0xFFFFFFFFFFFFFFFF)
 RAW_KEYS = 1
+DUAL_DELETE = 2
 MAX_LEVELS = 48
 
 
@@ -99,12 +100,14 @@ class OraclePMA:
     """One packed memory array holding a dynamic graph (or raw keys)."""
 
     def __init__(self, n_vertices: int, L: int = 64, tau0=92, tauh=80, rho0=8, rhoh=40,
-                 raw_keys: bool = False):
+                 raw_keys: bool = False, dual: bool = False):
         self.n_vertices = int(n_vertices)
         self.L = L
         self.raw = raw_keys
+        self.dual = dual
+        self.params = (tau0, tauh, rho0, rhoh)
         self._p = lib().or_create(self.n_vertices, L, tau0, tauh, rho0, rhoh,
-                                  RAW_KEYS if raw_keys else 0)
+                                  (RAW_KEYS if raw_keys else 0) | (DUAL_DELETE if dual else 0))
         if not self._p:
             raise ValueError("oracle: invalid parameters")
 

@@ -30,6 +30,17 @@
  *     everything fits under the new root bound ("double the space of the old
  *     root segment", read as repeated doubling), and all keys are spread over
  *     the new array.
+ *  D  dual deletion (OR_DUAL_DELETE; Sec. 4.1: deletions are the dual of
+ *     insertions, the density must stay inside (rho_i, tau_i)).  After the
+ *     deletes and inserts of a batch, a touched leaf whose count c lies in
+ *     [min_0, max_0] is rewritten left-packed at level 0 (the whole array being
+ *     one leaf waives min_0).  Every other touched leaf is a pending unit; at
+ *     level i a segment holding pending units merges iff
+ *     min_i <= n_s + |U_s| <= max_i, the root waiving min_h.  If the root
+ *     cannot take them (count > max_h) the array grows as in R7.  After the
+ *     batch, a root holding fewer than min_h keys is rebuilt at the smallest
+ *     height whose root bound holds them when that height is lower (halving,
+ *     possibly repeated).
  *  RD "re-dispatch evenly": a segment of m leaves receiving n sorted keys
  *     gives leaf t the ranks [floor(n t / m), floor(n (t+1) / m)), stored at
  *     the front of the leaf; the rest of the leaf is EMPTY.
@@ -259,6 +270,77 @@ int or_update(or_pma *p, const uint64_t *ins, uint64_t n_ins, const uint64_t *de
   return rc;
 }
 
+/* Reading D, levels 0..h: pending units are touched leaves out of bounds.  On
+   return *npend counts the inserts still pending and *nunits the leaves still
+   pending (both nonzero only if the root could not take them). */
+static int level_loop_dual(or_pma *p, const uint64_t *I, const uint64_t *leafI, uint64_t nI, uint8_t *pend,
+                           const uint8_t *touched, int8_t *cover, uint64_t *merges, uint32_t *climbed,
+                           uint64_t *npend, uint8_t **unit_out, uint64_t *nunits_out) {
+  const uint32_t L = p->L;
+  const uint64_t nleaves = p->C / L;
+  uint8_t *unit = (uint8_t *)calloc(nleaves, 1);
+  uint64_t *keys = (uint64_t *)malloc(sizeof(uint64_t) * (p->C + nI + 1));
+  uint64_t *ins = (uint64_t *)malloc(sizeof(uint64_t) * (nI + 1));
+  uint64_t *mrg = (uint64_t *)malloc(sizeof(uint64_t) * (p->C + nI + 1));
+  *unit_out = unit;
+  if (!unit || !keys || !ins || !mrg) { free(keys); free(ins); free(mrg); return OR_ENOMEM; }
+  uint64_t nunits = 0;
+  /* level 0: every touched leaf, with its inserts (contiguous in I, leaves ascending) */
+  uint64_t a = 0;
+  for (uint64_t j = 0; j < nleaves; j++) {
+    uint64_t b = a;
+    while (b < nI && leafI[b] == j) b++;
+    if (touched[j]) {
+      uint64_t nv = 0;
+      for (uint64_t o = 0; o < L; o++) if (p->slots[j * L + o] != OR_EMPTY) keys[nv++] = p->slots[j * L + o];
+      uint64_t c = nv + (b - a);
+      if (c <= p->maxc[0] && (c >= p->minc[0] || p->h == 0)) {
+        uint64_t n = merge2(keys, nv, I + a, b - a, mrg);
+        redistribute(p->slots + j * L, L, 1, mrg, n);
+        for (uint64_t x = a; x < b; x++) pend[x] = 0;
+        *npend -= b - a;
+        merges[0]++;
+        cover[j] = 0;
+      } else {
+        unit[j] = 1;
+        nunits++;
+      }
+    }
+    a = b;
+  }
+  /* levels 1..h: segments holding pending units */
+  for (uint32_t lvl = 1; lvl <= p->h && nunits > 0; lvl++) {
+    const uint64_t span = (uint64_t)1 << lvl;
+    for (uint64_t s = 0; s < nleaves >> lvl; s++) {
+      uint64_t j0 = s * span, u_units = 0;
+      for (uint64_t j = j0; j < j0 + span; j++) u_units += unit[j];
+      if (!u_units) continue;
+      uint64_t nv = 0, q = 0;
+      for (uint64_t x = j0 * L; x < (j0 + span) * L; x++) if (p->slots[x] != OR_EMPTY) keys[nv++] = p->slots[x];
+      for (uint64_t x = 0; x < nI; x++)
+        if (pend[x] && (leafI[x] >> lvl) == s) ins[q++] = I[x];
+      uint64_t t = nv + q;
+      if (t <= p->maxc[lvl] && (t >= p->minc[lvl] || lvl == p->h)) {
+        uint64_t n = merge2(keys, nv, ins, q, mrg);
+        redistribute(p->slots + j0 * L, L, span, mrg, n);
+        for (uint64_t x = 0; x < nI; x++)
+          if (pend[x] && (leafI[x] >> lvl) == s) pend[x] = 0;
+        *npend -= q;
+        for (uint64_t j = j0; j < j0 + span; j++) {
+          nunits -= unit[j];
+          unit[j] = 0;
+          cover[j] = (int8_t)lvl;
+        }
+        merges[lvl]++;
+        *climbed = lvl;
+      }
+    }
+  }
+  *nunits_out = nunits;
+  free(keys); free(ins); free(mrg);
+  return OR_OK;
+}
+
 /* R3..R7 on sorted, unique, disjoint I and D */
 static int apply_batch(or_pma *p, uint64_t *I, uint64_t nI, uint64_t *D, uint64_t nD,
                        uint64_t n_raw, or_stats *st) {
@@ -310,7 +392,14 @@ static int apply_batch(or_pma *p, uint64_t *I, uint64_t nI, uint64_t *D, uint64_
   uint64_t merges[OR_MAX_LEVELS];
   memset(merges, 0, sizeof(merges));
   int rc = OR_OK;
-  for (uint32_t lvl = 0; lvl <= p->h && npend > 0; lvl++) {
+  const int dual = (p->flags & OR_DUAL_DELETE) != 0;
+  uint64_t nunits = 0;
+  uint8_t *unit = NULL;
+  if (dual) {
+    rc = level_loop_dual(p, I, leafI, nI, pend, touched, cover, merges, &climbed, &npend, &unit, &nunits);
+    if (rc) goto done;
+  }
+  for (uint32_t lvl = 0; lvl <= p->h && npend > 0 && !dual; lvl++) {
     const uint64_t seg_slots = (uint64_t)L << lvl;
     uint64_t a = 0;
     while (a < nI) {
@@ -349,11 +438,11 @@ static int apply_batch(or_pma *p, uint64_t *I, uint64_t nI, uint64_t *D, uint64_
 
   /* R7: the root could not take the rest -- grow and spread everything */
   int resized = 0;
-  if (npend > 0) {
+  if (npend > 0 || nunits > 0) {
     uint64_t nv = 0;
     for (uint64_t x = 0; x < p->C; x++) nv += p->slots[x] != OR_EMPTY;
     uint64_t *all = (uint64_t *)malloc(sizeof(uint64_t) * (nv ? nv : 1));
-    uint64_t *rest = (uint64_t *)malloc(sizeof(uint64_t) * npend);
+    uint64_t *rest = (uint64_t *)malloc(sizeof(uint64_t) * (npend ? npend : 1));
     uint64_t *mer = (uint64_t *)malloc(sizeof(uint64_t) * (nv + npend));
     if (!all || !rest || !mer) { free(all); free(rest); free(mer); rc = OR_ENOMEM; goto done; }
     uint64_t k = 0;
@@ -381,6 +470,33 @@ static int apply_batch(or_pma *p, uint64_t *I, uint64_t nI, uint64_t *D, uint64_
     npend = 0;
     resized = 1;
     climbed = h_old + 1;
+  } else if (dual && p->h > 0) {
+    /* D: a root below min_h is rebuilt at the smallest height that holds it */
+    uint64_t nv = 0;
+    for (uint64_t x = 0; x < p->C; x++) nv += p->slots[x] != OR_EMPTY;
+    if (nv < p->minc[p->h]) {
+      uint32_t h2 = 0;
+      uint64_t mx[OR_MAX_LEVELS], mn[OR_MAX_LEVELS];
+      for (;; h2++) {
+        or_thresholds(L, h2, p->tau0, p->tauh, p->rho0, p->rhoh, mx, mn);
+        if (nv <= mx[h2]) break;
+      }
+      if (h2 < p->h) {
+        uint64_t *all = (uint64_t *)malloc(sizeof(uint64_t) * (nv ? nv : 1));
+        uint64_t C2 = (uint64_t)L << h2;
+        uint64_t *ns = (uint64_t *)malloc(sizeof(uint64_t) * C2);
+        if (!all || !ns) { free(all); free(ns); rc = OR_ENOMEM; goto done; }
+        uint64_t k = 0;
+        for (uint64_t x = 0; x < p->C; x++) if (p->slots[x] != OR_EMPTY) all[k++] = p->slots[x];
+        redistribute(ns, L, (uint64_t)1 << h2, all, nv);
+        free(all);
+        free(p->slots);
+        p->slots = ns;
+        p->C = C2;
+        set_height(p, h2);
+        resized = 2;
+      }
+    }
   }
 
   if (st) {
@@ -408,6 +524,7 @@ static int apply_batch(or_pma *p, uint64_t *I, uint64_t nI, uint64_t *D, uint64_
     for (uint32_t i = 0; i < OR_MAX_LEVELS; i++) st->merges[i] = merges[i];
   }
 done:
+  free(unit);
   free(buf); free(mrg); free(ub);
   free(leafI); free(leafD); free(touched); free(cover); free(pend); free(slotD);
   free_pivots(&pv);
@@ -545,6 +662,9 @@ int or_check_invariants(const or_pma *p) {
     uint64_t c = 0;
     for (uint64_t o = 0; o < p->L; o++) c += p->slots[j * p->L + o] != OR_EMPTY;
     if (c > p->maxc[0]) return 2;
+    if (p->flags & OR_DUAL_DELETE) /* no deletion leaves a hole: leaves stay left-packed */
+      for (uint64_t o = 0; o < p->L; o++)
+        if ((p->slots[j * p->L + o] != OR_EMPTY) != (o < c)) return 5;
   }
   if (!(p->flags & OR_RAW_KEYS)) {
     uint64_t guards = 0;

@@ -27,6 +27,7 @@ extern "C" {
 
 #define OR_EMPTY 0xFFFFFFFFFFFFFFFFull
 #define OR_RAW_KEYS 1u /* keys are opaque integers < 2^63: no guards, no analytics */
+#define OR_DUAL_DELETE 2u /* deletion as the dual of insertion (lower thresholds kept) */
 
 #define OR_OK 0
 #define OR_EINVAL 1
@@ -41,7 +42,7 @@ typedef struct {
   uint64_t n_deleted;       /* deletes that took effect */
   uint64_t n_ignored;       /* raw inputs that took no effect (dups, cancelled, present/absent) */
   uint32_t levels_climbed;  /* highest level at which a segment merged; h_old+1 on resize */
-  uint32_t resized;         /* 1 if the root was grown */
+  uint32_t resized;         /* 1 if the array was grown, 2 if it was shrunk (dual mode) */
   uint64_t alg_bytes;       /* algorithmic bytes of the batch (definition in gpma_oracle.c) */
   uint64_t touched_leaves;  /* distinct leaves holding an insert or delete after cancellation */
   uint64_t covered_leaves;  /* leaves rewritten by a merge (union of merged segments) */
@@ -74,7 +75,8 @@ int or_bfs(const or_pma *p, uint32_t src, int32_t *depth);
 int or_cc(const or_pma *p, uint32_t *label);
 int or_pagerank(const or_pma *p, uint32_t iters, double damping, double *rank);
 
-/* 0 if every checked property holds, else a code naming the first violated one. */
+/* 0 if every checked property holds, else a code naming the first violated one.
+   Dual mode adds: 5 a leaf with a hole (a valid key after an EMPTY slot). */
 int or_check_invariants(const or_pma *p);
 
 #ifdef __cplusplus

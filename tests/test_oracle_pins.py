@@ -280,3 +280,73 @@ def test_pagerank_cycle_uniform_and_eigenvector():
     pv = np.real(vecs[:, np.argmax(np.real(w))])
     pv /= pv.sum()
     assert np.allclose(o.pagerank(400), pv, rtol=1e-9)
+
+
+# ---- dual deletion (reading D): hand-computed cases, set semantics, bounds ------------
+@pytest.mark.parametrize("case", ["d1", "d2", "d3", "d4"])
+def test_dual_worked_examples(case):
+    g = read_golden("dual_w.txt")
+    L = int(g["L"])
+    o = oracle.OraclePMA(0, L=L, raw_keys=True, dual=True)
+    assert o.import_layout(parse_leaves(g["initial"], L)) == 0
+    rc, st = o.update(ints(g[f"{case}_insert"]), ints(g[f"{case}_delete"]))
+    assert rc == 0
+    assert o.capacity == int(g[f"{case}_capacity"])
+    assert np.array_equal(o.layout(), parse_leaves(g[f"{case}_final"], L))
+    assert st["merges"][:4] == ints(g[f"{case}_merges_per_level"])
+    assert st["resized"] == (2 if o.capacity < 32 else 0)
+    assert o.check_invariants() == 0
+
+
+def test_dual_lazy_differs_only_in_layout():
+    """The same deletes in lazy mode leave holes and keep the capacity (R5)."""
+    g = read_golden("dual_w.txt")
+    L = int(g["L"])
+    o = oracle.OraclePMA(0, L=L, raw_keys=True)
+    o.import_layout(parse_leaves(g["initial"], L))
+    o.update([], ints(g["d3_delete"]))
+    assert o.capacity == 32 and sorted(edges_of(o.layout()).tolist()) == [3, 5, 7]
+
+
+def _leaf_counts(lay, L):
+    return (lay.reshape(-1, L) != EMPTY).sum(axis=1)
+
+
+@pytest.mark.parametrize("V,L,seed", [(60, 4, 10), (300, 8, 11), (2000, 64, 12), (800, 16, 13)])
+def test_dual_bruteforce_stream_and_bounds(V, L, seed):
+    """Set semantics; no holes; leaves written by a batch hold at least the even-split
+    lower bound min_i / 2^i (some level i >= 1) once the root holds min_h; the capacity
+    shrinks to the smallest height whose root bound holds the keys."""
+    rng = np.random.default_rng(seed)
+    o = oracle.OraclePMA(V, L=L, dual=True)
+    live = set()
+    for it in range(40):
+        grow = it < 15 or it % 9 == 0
+        n = int(rng.integers(1, 3 * V))
+        ins, dels = _random_batch(rng, V, live, n)
+        if not grow:  # mostly deletes: shrink the graph
+            ins = ins[: ins.size // 8]
+            dels = np.concatenate([dels, np.array(list(live), np.uint64)[: len(live) // 2]])
+        before = o.layout()
+        rc, st = o.update(ins, dels)
+        assert rc == 0
+        new_live = apply_set_semantics(live, ins, dels)
+        lay = o.layout()
+        assert np.array_equal(edges_of(lay), np.array(sorted(new_live), np.uint64))
+        check_layout(lay, L, V)
+        assert o.check_invariants() == 0
+        h, total = o.height, len(new_live) + V
+        mx, mn = oracle.thresholds(L, h)
+        if h > 0 and total >= mn[h]:
+            lmin = min(int(mn[i]) // (1 << i) for i in range(1, h + 1))
+            cnt = _leaf_counts(lay, L)
+            changed = np.ones(cnt.size, bool) if lay.size != before.size else \
+                (lay.reshape(-1, L) != before.reshape(-1, L)).any(axis=1)
+            assert np.all(cnt[changed] >= lmin), (it, lmin, cnt[changed].min())
+        # the array is never taller than needed while the root is underfull
+        if h > 0 and total < mn[h]:
+            mx1, _ = oracle.thresholds(L, h - 1)
+            assert total > mx1[h - 1]
+        if st["resized"] == 2:
+            assert o.capacity < before.size
+        live = new_live
