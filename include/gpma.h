@@ -46,6 +46,11 @@ typedef struct gpma *gpma_t;
 #define GPMA_PLAIN_SEARCH 2u /* find leaves by binary search only (default: a learned two-stage
                                 linear model over the leaf pivots narrows the search; both
                                 give the same leaf, hence the same array) */
+#define GPMA_DUAL_DELETE 4u /* deletion as the dual of insertion (Sec. 4.1): a touched leaf or
+                                a merged segment must end within [min_i, max_i]; deletes leave
+                                no holes; an underfull root halves.  Default: lazy deletion
+                                (Sec. 6.1), slots become EMPTY in place */
+
 #define GPMA_MAX_LEVELS 48
 
 /* Create-time parameters; a zero field takes the default.  Densities are whole
@@ -56,7 +61,7 @@ typedef struct gpma *gpma_t;
 typedef struct {
   uint32_t leaf_size; /* L: power of two in [2, 1024]; default 64 */
   uint32_t tau0_pct, tauh_pct, rho0_pct, rhoh_pct;
-  uint32_t flags;     /* GPMA_RAW_KEYS | GPMA_PLAIN_SEARCH, or 0 */
+  uint32_t flags;     /* GPMA_RAW_KEYS | GPMA_PLAIN_SEARCH | GPMA_DUAL_DELETE, or 0 */
 } gpma_params;
 
 /* Optional device allocator.  alloc returns NULL on failure; both receive the
@@ -75,7 +80,7 @@ typedef struct {
   uint64_t n_ignored;      /* raw inputs with no effect: duplicates, cancelled pairs,
                               inserts of stored keys, deletes of absent keys */
   uint32_t levels_climbed; /* highest level at which a segment merged; old h + 1 on a resize */
-  uint32_t resized;        /* 1 if the capacity grew */
+  uint32_t resized;        /* 1 if the capacity grew, 2 if it shrank (GPMA_DUAL_DELETE) */
   uint64_t alg_bytes;      /* algorithmic bytes of the batch (see the design notes) */
   uint64_t touched_leaves; /* distinct leaves holding an update after cancellation */
   uint64_t covered_leaves; /* leaves rewritten by merges (0 on a resize) */
@@ -194,7 +199,7 @@ int gpma_capacity(gpma_t h, uint64_t *out);
  * all hold, else a bit set: 1 keys not strictly increasing, 2 a leaf count or
  * first-key index is stale, 4 a leaf above its bound, 8 a guard index is stale,
  * 16 a merge mark was left set, 32 the total count is stale, 64 an out-degree is
- * stale.  Waits. */
+ * stale, 128 a leaf has a hole (GPMA_DUAL_DELETE only).  Waits. */
 int gpma_check(gpma_t h, uint32_t *code, void *stream);
 
 /* ---- measurement ------------------------------------------------------------

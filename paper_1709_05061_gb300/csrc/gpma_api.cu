@@ -45,6 +45,25 @@ void level_bounds(uint32_t L, uint32_t h, uint32_t t0, uint32_t th, uint64_t *mx
   }
 }
 
+// min_i = floor(rho_i * c_i) + 1 clamped to 2 min_{i-1}, rho_i linear in the
+// level between rho_0 (leaf) and rho_h (root), in exact integer hundredths
+void level_min_bounds(uint32_t L, uint32_t h, uint32_t r0, uint32_t rh, uint64_t *mn) {
+  for (uint32_t i = 0; i <= h; i++) {
+    const uint64_t seg = (uint64_t)L << i;
+    uint64_t num, den;
+    if (h == 0) {
+      num = (uint64_t)r0 * seg;
+      den = 100;
+    } else {
+      num = ((uint64_t)rh * h - (uint64_t)(rh - r0) * (h - i)) * seg;
+      den = 100ull * h;
+    }
+    uint64_t b = num / den + 1;
+    if (i > 0 && b > 2 * mn[i - 1]) b = 2 * mn[i - 1];
+    mn[i] = b;
+  }
+}
+
 uint32_t bits_for(uint64_t x) {
   uint32_t b = 0;
   while (x) {
@@ -188,6 +207,8 @@ struct gpma {
   uint32_t *check_buf;
   uint64_t *guards;
   uint64_t count_ub;
+  uint64_t count_lb;  // a lower bound of the stored key count (dual mode: root underflow check)
+  uint32_t dual;      // GPMA_DUAL_DELETE
   int poisoned;
   int host_sticky;
   Prof *prof;
@@ -263,6 +284,8 @@ void make_geo(gpma *h, uint32_t hh, Geo *g) {
     off += g->nleaves >> i;
   }
   level_bounds(h->L, hh, h->tau0, h->tauh, g->maxc);
+  level_min_bounds(h->L, hh, h->rho0, h->rhoh, g->minc);
+  g->dual = h->dual;
 }
 
 bool alloc_arrays(gpma *h, Geo *g, cudaStream_t s) {
@@ -294,7 +317,7 @@ void free_arrays(gpma *h, Geo *g, cudaStream_t s) {
 void free_work(gpma *h, cudaStream_t s) {
   Work &w = h->w;
   void *ptrs[] = {h->bufA,   h->bufB,     w.ukey,  w.utag,     w.uleaf,   w.run_start, w.eflag,
-                  w.rleaf,   w.rdelta,    w.rinfo, w.rdel,     w.pkey,    w.pleaf,     w.erun,
+                  w.rleaf,   w.rdelta,    w.rinfo, w.rdel,     w.pkey,    w.pleaf,     w.erun, w.eleaf,
                   w.elvl,    w.etop,      w.seg_node, w.seg_top, w.seg_pstart, w.seg_lpre, w.status};
   for (void *p : ptrs) dfree(h, p, s);
   memset(&h->w, 0, sizeof(Work));
@@ -316,7 +339,7 @@ int ensure_work(gpma *h, uint64_t n, cudaStream_t s) {
             dalloc(h, &w.utag, cap, s) && dalloc(h, &w.uleaf, cap, s) && dalloc(h, &w.run_start, c1, s) &&
             dalloc(h, &w.eflag, cap, s) && dalloc(h, &w.rleaf, cap, s) && dalloc(h, &w.rdelta, cap, s) &&
             dalloc(h, &w.rinfo, cap, s) && dalloc(h, &w.rdel, cap, s) && dalloc(h, &w.pkey, cap, s) &&
-            dalloc(h, &w.pleaf, cap, s) && dalloc(h, &w.erun, c1, s) && dalloc(h, &w.elvl, cap, s) &&
+            dalloc(h, &w.pleaf, cap, s) && dalloc(h, &w.erun, c1, s) && dalloc(h, &w.eleaf, cap, s) && dalloc(h, &w.elvl, cap, s) &&
             dalloc(h, &w.etop, cap, s) && dalloc(h, &w.seg_node, c1, s) && dalloc(h, &w.seg_top, c1, s) &&
             dalloc(h, &w.seg_pstart, c1, s) && dalloc(h, &w.seg_lpre, c1, s) && dalloc(h, &w.status, st, s);
   if (!ok) {
@@ -401,18 +424,10 @@ void train_model(gpma *h, cudaStream_t s, bool only_if_escalated = false) {
   if (!only_if_escalated) h->since_train = 0;
 }
 
-// root resize (reading R7): every valid key and every pending insert spread over
-// the smallest taller array whose root bound holds them
-int do_resize(gpma *h, uint64_t total, cudaStream_t s) {
+// Rebuild the whole array at height h2: every valid key and every pending insert
+// of the batch spread evenly over the new array (segment merge in whole mode).
+int rebuild_at(gpma *h, uint32_t h2, cudaStream_t s) {
   Geo &old = h->geo;
-  uint32_t h2 = old.h + 1;
-  uint64_t mx[kMaxLv];
-  for (;; h2++) {
-    if (h2 >= kMaxLv - 1 || ((uint64_t)h->L << h2) > (1ull << 32) || (1ull << h2) >= (1ull << 30))
-      return poison(h, GPMA_ENOMEM);
-    level_bounds(h->L, h2, h->tau0, h->tauh, mx);
-    if (total <= mx[h2]) break;
-  }
   int rc = ensure_merge_scratch(h, s);
   if (rc) return poison(h, rc);
   Geo g2;
@@ -430,6 +445,37 @@ int do_resize(gpma *h, uint64_t total, cudaStream_t s) {
   h->alloc_epoch++;
   train_model(h, s);
   return cuda_ok(h);
+}
+
+// smallest height whose root bound holds `total` keys, searching from h0 upwards
+// (0 when none below the limits: the caller checks against the current height)
+uint32_t smallest_height(const gpma *h, uint64_t total, uint32_t h0) {
+  uint64_t mx[kMaxLv];
+  for (uint32_t h2 = h0;; h2++) {
+    if (h2 >= kMaxLv - 1 || ((uint64_t)h->L << h2) > (1ull << 32) || (1ull << h2) >= (1ull << 30)) return kMaxLv;
+    level_bounds(h->L, h2, h->tau0, h->tauh, mx);
+    if (total <= mx[h2]) return h2;
+  }
+}
+
+// root resize (reading R7): the smallest taller array whose root bound holds
+// every valid key and every pending insert
+int do_resize(gpma *h, uint64_t total, cudaStream_t s) {
+  const uint32_t h2 = smallest_height(h, total, h->geo.h + 1);
+  if (h2 >= kMaxLv) return poison(h, GPMA_ENOMEM);
+  return rebuild_at(h, h2, s);
+}
+
+// dual deletion: a root below min_h is rebuilt at the smallest height that holds
+// its keys, if that is lower (nothing is pending: the batch is complete)
+int maybe_shrink(gpma *h, uint64_t total, cudaStream_t s, bool *shrunk) {
+  *shrunk = false;
+  if (h->geo.h == 0 || total >= h->geo.minc[h->geo.h]) return GPMA_OK;
+  const uint32_t h2 = smallest_height(h, total, 0);
+  if (h2 >= h->geo.h) return GPMA_OK;
+  if (cudaMemsetAsync(&h->ctl->npend, 0, sizeof(uint32_t), s) != cudaSuccess) return poison(h, GPMA_EDEVICE);
+  *shrunk = true;
+  return rebuild_at(h, h2, s);
 }
 
 __global__ void k_gate(const Ctl *ctl, cudaGraphConditionalHandle cond) {
@@ -593,7 +639,7 @@ int settle(gpma *h, cudaStream_t s) {
     h->alloc_epoch++;
     h->since_train = 0;
   }
-  h->count_ub = c.total;
+  h->count_ub = h->count_lb = c.total;
   return cuda_ok(h);
 }
 
@@ -711,7 +757,7 @@ int update(gpma *h, const uint64_t *ins, uint64_t n_ins, const uint64_t *del, ui
         if (st != GPMA_EINVAL) poison(h, st);
         return st;
       }
-      h->count_ub = h->h_ctl->total;
+      h->count_ub = h->count_lb = h->h_ctl->total;
       if (h->h_ctl->nfail) {
         esc.end();
         Phase ph(h->prof, GPMA_PROF_RESIZE, s);
@@ -736,6 +782,19 @@ int update(gpma *h, const uint64_t *ins, uint64_t n_ins, const uint64_t *del, ui
   }
   whole.end();
   if ((rc = cuda_ok(h))) return rc;
+  bool shrunk = false;
+  if (h->dual && !resized) {
+    // deletes can only lower the count: look only when the root might be underfull
+    h->count_lb = h->count_lb > n_del ? h->count_lb - n_del : 0;
+    if (h->count_lb < h->geo.minc[h->geo.h]) {
+      if ((rc = settle(h, s)) || (rc = read_ctl(h, s))) return rc;
+      if (h->h_ctl->err == 0) {
+        h->count_ub = h->count_lb = h->h_ctl->total;
+        Phase ph(h->prof, GPMA_PROF_RESIZE, s);
+        if ((rc = maybe_shrink(h, h->h_ctl->total, s, &shrunk))) return rc;
+      }
+    }
+  }
   if (!stats) return GPMA_OK;
 
   if ((rc = read_ctl(h, s))) return rc;
@@ -745,19 +804,19 @@ int update(gpma *h, const uint64_t *ins, uint64_t n_ins, const uint64_t *del, ui
     if (st != GPMA_EINVAL) poison(h, st);
     return st;
   }
-  h->count_ub = c.total;
+  h->count_ub = h->count_lb = c.total;
   const uint64_t L = h->L;
   stats->n_inserted = c.n_inserted;
   stats->n_deleted = c.n_deleted;
   stats->n_ignored = n - c.n_inserted - c.n_deleted;
   stats->touched_leaves = c.nruns;
-  stats->resized = resized ? 1 : 0;
+  stats->resized = resized ? 1 : (shrunk ? 2 : 0);
   for (int i = 0; i < GPMA_MAX_LEVELS && i < kMaxLv; i++) stats->merges[i] = c.merges[i];
   stats->merges[0] = c.n_merged0;
   uint32_t climbed = c.levels_climbed;
   if (resized) climbed = h_old + 1;
   stats->levels_climbed = climbed;
-  if (resized) {
+  if (resized || shrunk) {
     stats->covered_leaves = 0;
     stats->alg_bytes = 8 * n + 8 * L * c.nruns + 8 * C_old + 8 * h->geo.C;
   } else {
@@ -856,6 +915,7 @@ int gpma_create(uint32_t n_vertices, const gpma_params *params, const gpma_alloc
   h->L = L;
   h->logL = bits_for(L) - 1;
   h->raw = raw ? 1 : 0;
+  h->dual = (p.flags & GPMA_DUAL_DELETE) ? 1 : 0;
   h->tau0 = p.tau0_pct;
   h->tauh = p.tauh_pct;
   h->rho0 = p.rho0_pct;
@@ -1082,13 +1142,14 @@ int gpma_import_layout(gpma_t h, const uint64_t *d_slots, uint64_t capacity, voi
     cudaMemcpyAsync(&h->ctl->total, &saved.total, sizeof(uint64_t), cudaMemcpyHostToDevice, s);
     cudaStreamSynchronize(s);
     h->count_ub = old_total_ub;
+    h->count_lb = saved.total;
     return GPMA_EINVAL;
   }
   if (old_re) dfree(h, old_re, s);
   free_arrays(h, &h->geo, s);
   h->geo = g2;
   h->alloc_epoch++;
-  h->count_ub = h->h_ctl->total;
+  h->count_ub = h->count_lb = h->h_ctl->total;
   train_model(h, s);
   return cuda_ok(h);
 }

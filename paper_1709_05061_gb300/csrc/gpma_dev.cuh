@@ -35,10 +35,25 @@ struct Geo {
   uint32_t *deg;  // out-degree of every vertex (stored edges, guards excluded)
   uint64_t C, nleaves;
   uint32_t L, logL, h, V, raw;
-  uint32_t pad;
+  uint32_t dual;              // deletion as the dual of insertion: lower bounds kept
   uint64_t tree_off[kMaxLv];  // offset of level i (1..h) inside tree/mark
   uint64_t maxc[kMaxLv];      // max_i: largest admissible count at level i
+  uint64_t minc[kMaxLv];      // min_i: smallest admissible count at level i (dual mode)
 };
+
+// Level-0 test of a touched leaf holding c keys after its deletes and inserts:
+// lazy mode merges a leaf with inserts iff c <= max_0; dual mode rewrites every
+// touched leaf with min_0 <= c <= max_0 (a single-leaf array waives min_0).
+__device__ __forceinline__ bool leaf_fits(const Geo &g, uint64_t c, uint32_t nins) {
+  if (!g.dual) return nins > 0 && c <= g.maxc[0];
+  return c <= g.maxc[0] && (c >= g.minc[0] || g.h == 0);
+}
+
+// Level test of an escalated segment of level i holding t keys (valid + pending):
+// t <= max_i, and in dual mode t >= min_i below the root.
+__device__ __forceinline__ bool level_admits(const Geo &g, uint32_t i, uint64_t t) {
+  return t <= g.maxc[i] && (!g.dual || i == g.h || t >= g.minc[i]);
+}
 
 // Device control block of one handle: counters written by kernels, read by
 // later kernels of the same batch and (at sync points) by the host.

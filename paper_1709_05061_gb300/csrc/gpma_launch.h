@@ -53,7 +53,8 @@ struct Work {
   uint32_t *rdel;
   uint64_t *pkey;     // pending inserts (sorted) and their leaves
   uint32_t *pleaf;
-  uint32_t *erun;     // heads of pending runs (+ end)
+  uint32_t *erun;     // per escalated run: its first pending insert (+ end)
+  uint32_t *eleaf;    // per escalated run: its leaf
   uint8_t *elvl;      // merge level of each pending run
   uint8_t *etop;      // top merged ancestor of each pending run
   uint32_t *seg_node; // maximal merged segments: node, level, first pending, leaf prefix

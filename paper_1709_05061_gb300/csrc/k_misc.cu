@@ -202,6 +202,10 @@ __global__ void k_check_leaves(Geo g, uint32_t *code, unsigned long long *sum) {
     }
     if (c != g.cnt[j] || first != g.F[j]) bad |= 2;
     if (c > g.maxc[0]) bad |= 4;
+    // dual mode: no deletion leaves a hole, every leaf is left-packed
+    if (g.dual)
+      for (uint32_t b = 0; b < L; b += 32)
+        if (b + lane < L && ((p[b + lane] != kEmpty) != (b + lane < c))) bad |= 128;
     // the last key of this leaf is below the first key of the next non-empty leaf
     if (have_last) {
       for (uint64_t q = j + 1; q < g.nleaves; q++) {

@@ -60,7 +60,6 @@ __global__ void k_leaf_pass(Geo g, Ctl *ctl, Work w, uint32_t per_warp, int rest
   uint16_t *vpos = B.pos;
   uint8_t *dmark = B.mark;
   const uint32_t nruns = ctl->nruns;
-  const uint64_t max0 = g.maxc[0];
   uint64_t acc_ins = 0, acc_del = 0;
   uint32_t acc_m0 = 0, acc_esc = 0;
   for (uint32_t r = blockIdx.x * wpb + (threadIdx.x >> 5); r < nruns; r += gridDim.x * wpb) {
@@ -111,7 +110,7 @@ __global__ void k_leaf_pass(Geo g, Ctl *ctl, Work w, uint32_t per_warp, int rest
     }
     __syncwarp();
     const uint32_t cnt_del = nv - ndel;
-    const bool fits = nins > 0 && (uint64_t)cnt_del + nins <= max0;
+    const bool fits = leaf_fits(g, (uint64_t)cnt_del + nins, nins);
     if (fits) {
       // TryInsert+ at level 0: merge the kept keys with the inserts, left-packed
       uint32_t run = 0;
@@ -135,7 +134,7 @@ __global__ void k_leaf_pass(Geo g, Ctl *ctl, Work w, uint32_t per_warp, int rest
         if (!g.raw && o < n && is_guard(k)) g.row_end[k >> 32] = (uint32_t)((uint64_t)j * L + o);
       }
       if (lane == 0) {
-        g.F[j] = out[0];
+        g.F[j] = n ? out[0] : kEmpty;  // n = 0 only for a single-leaf array in dual mode
         g.cnt[j] = n;
       }
       for (uint32_t c = rs + lane; c < re; c += 32)
@@ -159,13 +158,13 @@ __global__ void k_leaf_pass(Geo g, Ctl *ctl, Work w, uint32_t per_warp, int rest
     }
     if (lane == 0) {
       w.rdelta[r] = (int32_t)nins - (int32_t)ndel;
-      w.rinfo[r] = fits ? 1 : (nins ? 2 : 0);
+      w.rinfo[r] = fits ? 1 : ((nins || g.dual) ? 2 : 0);
       w.rdel[r] = ndel;
     }
     acc_ins += nins;
     acc_del += ndel;
     acc_m0 += fits;
-    acc_esc += (!fits && nins);
+    acc_esc += !fits && (nins || g.dual);
     __syncwarp();
   }
   if (lane == 0) {
@@ -187,7 +186,6 @@ __global__ void __launch_bounds__(256) k_leaf64(Geo g, Ctl *ctl, Work w) {
   if (ctl->err) return;
   const uint32_t lane = lane_id(), wib = threadIdx.x >> 5;
   const uint32_t nruns = ctl->nruns;
-  const uint64_t max0 = g.maxc[0];
   const uint32_t nw = gridDim.x * 8;
   ulonglong2 *s2 = reinterpret_cast<ulonglong2 *>(g.slots);
   uint64_t acc_ins = 0, acc_del = 0;
@@ -238,7 +236,7 @@ __global__ void __launch_bounds__(256) k_leaf64(Geo g, Ctl *ctl, Work w) {
     const uint32_t ndel = __popc(__ballot_sync(0xFFFFFFFFu, d0)) + __popc(__ballot_sync(0xFFFFFFFFu, d1));
     const bool kp0 = v0 && !d0, kp1 = v1 && !d1;
     const uint32_t nkept = __popc(__ballot_sync(0xFFFFFFFFu, kp0)) + __popc(__ballot_sync(0xFFFFFFFFu, kp1));
-    const bool fits = nins > 0 && (uint64_t)nkept + nins <= max0;
+    const bool fits = leaf_fits(g, (uint64_t)nkept + nins, nins);
     if (fits) {
       // TryInsert+ at level 0: rank-merge kept keys with the surviving inserts
       const uint32_t c = (uint32_t)kp0 + (uint32_t)kp1;
@@ -266,7 +264,7 @@ __global__ void __launch_bounds__(256) k_leaf64(Geo g, Ctl *ctl, Work w) {
         if (o + 1 < n && is_guard(b)) g.row_end[b >> 32] = j * 64u + o + 1;
       }
       if (lane == 0) {
-        g.F[j] = sout[wib][0];
+        g.F[j] = n ? sout[wib][0] : kEmpty;
         g.cnt[j] = n;
       }
       __syncwarp();
@@ -288,13 +286,13 @@ __global__ void __launch_bounds__(256) k_leaf64(Geo g, Ctl *ctl, Work w) {
     }
     if (lane == 0) {
       w.rdelta[r] = (int32_t)nins - (int32_t)ndel;
-      w.rinfo[r] = fits ? 1 : (nins ? 2 : 0);
+      w.rinfo[r] = fits ? 1 : ((nins || g.dual) ? 2 : 0);
       w.rdel[r] = ndel;
     }
     acc_ins += nins;
     acc_del += ndel;
     acc_m0 += fits;
-    acc_esc += (!fits && nins);
+    acc_esc += !fits && (nins || g.dual);
   }
   if (lane == 0) {
     if (acc_ins) atomicAdd((unsigned long long *)&ctl->n_inserted, (unsigned long long)acc_ins);
@@ -355,7 +353,7 @@ __global__ void k_tree_pend(Geo g, Ctl *ctl, Work w) {
   if (ctl->err) return;
   const uint32_t ner = ctl->neruns;
   for (uint32_t r = blockIdx.x * blockDim.x + threadIdx.x; r < ner; r += gridDim.x * blockDim.x) {
-    const uint32_t j = w.pleaf[w.erun[r]];
+    const uint32_t j = w.eleaf[r];
     const uint32_t c = w.erun[r + 1] - w.erun[r];
     for (uint32_t i = 1; i <= g.h; i++) atomicAdd(&g.tree[g.tree_off[i] + (j >> i)], c);
   }
@@ -385,25 +383,32 @@ __global__ void __launch_bounds__(kScanThreads) k_pending(Ctl *ctl, Work w) {
   if ((uint64_t)(tile + 1) * kScanTile >= m && threadIdx.x == 0) ctl->npend = total;
 }
 
+// escalated runs (leaves that did not settle at level 0), in leaf order, with the
+// first of their pending inserts (those are contiguous and in the same order)
 __global__ void __launch_bounds__(kScanThreads) k_eruns(Ctl *ctl, Work w) {
   __shared__ ScanSmem sm;
-  if (ctl->err || ctl->npend == 0) return;
-  const uint32_t tile = take_ticket(ctl, kSlotERuns, sm), np = ctl->npend;
-  if ((uint64_t)tile * kScanTile >= np && tile > 0) return;
-  uint32_t flag[kScanItems];
+  if (ctl->err || ctl->nesc == 0) return;
+  const uint32_t tile = take_ticket(ctl, kSlotERuns, sm), nr = ctl->nruns;
+  if ((uint64_t)tile * kScanTile >= nr && tile > 0) return;
+  uint32_t flag[kScanItems], pc[kScanItems];
 #pragma unroll
   for (int r = 0; r < kScanItems; r++) {
-    uint64_t p = scan_elem(tile, r);
-    flag[r] = p < np && (p == 0 || w.pleaf[p] != w.pleaf[p - 1]);
+    const uint64_t q = scan_elem(tile, r);
+    flag[r] = q < nr && w.rinfo[q] == 2;
+    pc[r] = flag[r] ? (uint32_t)(w.rdelta[q] + (int32_t)w.rdel[q]) : 0u;  // its surviving inserts
   }
-  uint32_t off[kScanItems];
-  uint32_t total = tile_scan(flag, off, tile, w.status, 1, 0, ctl->epoch + kSlotERuns, &ctl->err, sm);
+  uint32_t off[kScanItems], poff[kScanItems];
+  const uint32_t total = tile_scan(flag, off, tile, w.status, 2, 0, ctl->epoch + kSlotERuns, &ctl->err, sm);
+  const uint32_t ptotal = tile_scan(pc, poff, tile, w.status, 2, 1, ctl->epoch + kSlotERuns, &ctl->err, sm);
 #pragma unroll
   for (int r = 0; r < kScanItems; r++)
-    if (flag[r] && off[r] < np) w.erun[off[r]] = (uint32_t)scan_elem(tile, r);
-  if ((uint64_t)(tile + 1) * kScanTile >= np && threadIdx.x == 0) {
+    if (flag[r] && off[r] < nr) {
+      w.erun[off[r]] = poff[r];
+      w.eleaf[off[r]] = w.rleaf[scan_elem(tile, r)];
+    }
+  if ((uint64_t)(tile + 1) * kScanTile >= nr && threadIdx.x == 0) {
     ctl->neruns = total;
-    w.erun[total] = np;
+    w.erun[total] = ptotal;
   }
 }
 
@@ -413,10 +418,10 @@ __global__ void k_esc_level(Geo g, Ctl *ctl, Work w, int resize) {  // resize = 
   if (ctl->err) return;
   const uint32_t ner = ctl->neruns;
   for (uint32_t r = blockIdx.x * blockDim.x + threadIdx.x; r < ner; r += gridDim.x * blockDim.x) {
-    const uint32_t j = w.pleaf[w.erun[r]];
+    const uint32_t j = w.eleaf[r];
     uint32_t lvl = kNoLevel;
     for (uint32_t i = 1; i <= g.h; i++) {
-      if (g.tree[g.tree_off[i] + (j >> i)] <= g.maxc[i]) {
+      if (level_admits(g, i, g.tree[g.tree_off[i] + (j >> i)])) {
         lvl = i;
         break;
       }
@@ -440,7 +445,7 @@ __global__ void k_esc_top(Geo g, Ctl *ctl, Work w) {
   const uint32_t ner = ctl->neruns;
   for (uint32_t r = blockIdx.x * blockDim.x + threadIdx.x; r < ner; r += gridDim.x * blockDim.x) {
     const uint32_t lvl = w.elvl[r];
-    const uint32_t j = w.pleaf[w.erun[r]];
+    const uint32_t j = w.eleaf[r];
     uint32_t top = lvl;
     for (uint32_t i = lvl + 1; i <= g.h; i++)
       if (g.mark[g.tree_off[i] + (j >> i)]) top = i;
@@ -453,7 +458,7 @@ __global__ void k_unmark(Geo g, Ctl *ctl, Work w) {
   for (uint32_t r = blockIdx.x * blockDim.x + threadIdx.x; r < ner; r += gridDim.x * blockDim.x) {
     const uint32_t lvl = w.elvl[r];
     if (lvl == kNoLevel) continue;
-    g.mark[g.tree_off[lvl] + (w.pleaf[w.erun[r]] >> lvl)] = 0;
+    g.mark[g.tree_off[lvl] + (w.eleaf[r] >> lvl)] = 0;
   }
 }
 
@@ -475,12 +480,12 @@ __global__ void __launch_bounds__(kScanThreads) k_segs(Geo g, Ctl *ctl, Work w) 
     node[r] = 0;
     if (q < ner) {
       top[r] = w.etop[q];
-      node[r] = w.pleaf[w.erun[q]] >> top[r];
+      node[r] = w.eleaf[q] >> top[r];
       if (q == 0) {
         flag[r] = 1;
       } else {
         uint32_t pt = w.etop[q - 1];
-        uint32_t pn = w.pleaf[w.erun[q - 1]] >> pt;
+        uint32_t pn = w.eleaf[q - 1] >> pt;
         flag[r] = (pt != top[r]) || (pn != node[r]);
       }
       lv[r] = flag[r] ? (1u << top[r]) : 0u;
@@ -494,7 +499,7 @@ __global__ void __launch_bounds__(kScanThreads) k_segs(Geo g, Ctl *ctl, Work w) 
     uint64_t q = scan_elem(tile, r);
     if (q >= ner) continue;
     const uint32_t lvl = w.elvl[q];
-    g.mark[g.tree_off[lvl] + (w.pleaf[w.erun[q]] >> lvl)] = 0;
+    g.mark[g.tree_off[lvl] + (w.eleaf[q] >> lvl)] = 0;
     if (!flag[r] || off[r] >= ner) continue;
     w.seg_top[off[r]] = (uint8_t)top[r];
     w.seg_node[off[r]] = node[r];
