@@ -483,7 +483,7 @@ def many_study(a):
 
 def serve_study(a):
     """Served stream on a resident R-MAT scale-24 graph (2^28 samples, seed 24,
-    generated on the device; about 2.6e8 distinct edges, the last 6e7 of the
+    generated on the device; about 2.6e8 distinct edges, the last 7e7 of the
     stream held back as future inserts).  Requests: Poisson arrivals, updates of
     log-uniform 1e2..1e5 keys (half new edges, half the window's oldest) mixed 4:1
     with queries (BFS from a uniform random source, CC, PageRank-10), update keys
@@ -501,7 +501,7 @@ def serve_study(a):
     t0 = time.perf_counter()
     st = W.rmat_stream_device(scale, 1 << 28, seed=24)
     gen_s = time.perf_counter() - t0
-    reserve = 60_000_000
+    reserve = 70_000_000
     window = st.numel() - reserve
     V = 1 << scale
     g = gp.Graph(V, leaf_size=LEAF)
@@ -523,11 +523,40 @@ def serve_study(a):
            "generate_s": gen_s, "bulk_load_s": load_s, "requests_per_run": n}
     cap = srv.run(S.make_requests(n, V, win, rate=1.0, seed=101), realtime=False)
     out["closed_loop"] = cap
+    # the plain path on the same kind of stream: one request at a time, nothing
+    # coalesced or overlapped
+    plain = S.Server(g, max_batch_keys=1 << 20, result_slots=1, max_inflight=1, coalesce=False, keep_results=False)
+    out["plain_closed_loop"] = plain.run(S.make_requests(n, V, win, rate=1.0, seed=101), realtime=False)
+    out["served_vs_plain_requests_per_s"] = cap["requests_per_s"] / out["plain_closed_loop"]["requests_per_s"]
     for frac in (0.5, 0.8, 0.95):
         rate = frac * cap["requests_per_s"]
         r = srv.run(S.make_requests(n, V, win, rate=rate, seed=102 + int(frac * 100)), realtime=True)
         r["offered_rate_per_s"] = rate
         out[f"load_{int(frac * 100)}"] = r
+    # update-only sweep on the resident scale-24 array: device time per batch from
+    # the library's events (the 4.3 GB array is far larger than L2), algorithmic
+    # bytes from the batch's stats, fraction of the measured HBM peak
+    peak = measured_hbm_peak()[0]
+    sweep = []
+    for B in (100_000, 1_000_000):
+        ts, ab = [], []
+        for k in range(13):
+            ins, dels = win.slide(B // 2)
+            di = torch.from_numpy(np.ascontiguousarray(ins).view(np.int64)).cuda()
+            dd = torch.from_numpy(np.ascontiguousarray(dels).view(np.int64)).cuda()
+            gp.gpma_profile_enable(g.h, True)
+            st = g.update(di, dd, stats=True)
+            p = gp.gpma_profile_read(g.h, reset=True)
+            gp.gpma_profile_enable(g.h, False)
+            if k >= 3:
+                ts.append(p["update"]["ms"])
+                ab.append(st["alg_bytes"])
+        ms = statistics.median(ts)
+        gbs = statistics.median(ab) / (ms * 1e-3) / 1e9
+        sweep.append({"batch": B, "p50_ms": ms, "p99_ms": float(np.percentile(ts, 99)),
+                      "updates_per_s": B / (ms * 1e-3), "alg_bytes": int(statistics.median(ab)), "alg_GBps": gbs,
+                      "hbm_frac": gbs / peak})
+    out["update_sweep_scale24"] = sweep
     out["check"] = g.check()
     g.close()
     return out

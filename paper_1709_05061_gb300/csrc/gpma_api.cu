@@ -418,10 +418,10 @@ int read_ctl(gpma *h, cudaStream_t s) {
   return GPMA_OK;
 }
 
-void train_model(gpma *h, cudaStream_t s, bool only_if_escalated = false) {
+void train_model(gpma *h, cudaStream_t s, bool after_batch = false) {
   if (!h->mhead) return;
-  launch_train_model(h->geo, h->mhead, h->mpieces, h->mtmp, h->ctl, only_if_escalated, s);
-  if (!only_if_escalated) h->since_train = 0;
+  launch_train_model(h->geo, h->mhead, h->mpieces, h->mtmp, h->ctl, after_batch, s);
+  if (!after_batch) h->since_train = 0;
 }
 
 // Rebuild the whole array at height h2: every valid key and every pending insert
@@ -553,7 +553,7 @@ bool capture_update(gpma *h, FrontArgs &f, uint32_t nb, bool stats, bool grow, G
     launch_segments(g, h->ctl, h->w, nb, t);
     launch_segment_merge(g, g, h->ctl, h->w, h->scratch_cap, g.nleaves, h->scratch, h->vbuf, h->partials, false,
                          t);
-    if (h->mhead) launch_train_model(g, h->mhead, h->mpieces, h->mtmp, h->ctl, false, t);
+    if (h->mhead) launch_train_model(g, h->mhead, h->mpieces, h->mtmp, h->ctl, true, t);
   };
   if (!small_front(nb)) launch_sort(f, nb, gc.cap);
   launch_leaf_pass(g, h->ctl, h->w, nb, gc.cap);

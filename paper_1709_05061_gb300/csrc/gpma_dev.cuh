@@ -177,6 +177,9 @@ struct ModelHead {
   float rscale;
   uint32_t valid;
   uint64_t kmax;
+  uint64_t drift;  // leaves rewritten by merges above level 0 since the model was trained
+  uint32_t train;  // this call retrains (decided by k_lm_decide)
+  uint32_t pad;
 };
 
 constexpr uint32_t kNoLeaf = 0xFFFFFFFFu;
@@ -213,7 +216,15 @@ __device__ __forceinline__ uint32_t learned_leaf_search(const ModelHead &m, cons
   if (a > (int64_t)nleaves) a = (int64_t)nleaves;  // a model trained on another geometry
   if (b > (int64_t)nleaves) b = (int64_t)nleaves;
   if (b < a) b = a;
-  // widen until eff(a - 1) <= k (or a = 0) and eff(b) > k (or b = nleaves)
+  // widen until eff(a - 1) <= k (or a = 0) and eff(b) > k (or b = nleaves); the
+  // first probe of both ends goes out together (no empty leaf: one load each)
+  if (a > 0 && b < (int64_t)nleaves) {
+    const uint64_t fa = __ldg(F + (a - 1)), fb = __ldg(F + b);
+    if (fa != kEmpty && fb != kEmpty && fa <= k && fb > k) {
+      const uint64_t p = search_first_above(F, (uint64_t)a, (uint64_t)b, k);
+      return p ? (uint32_t)(p - 1) : 0u;
+    }
+  }
   uint64_t step = pc.err + 2;
   while (a > 0 && !eff_at_most(F, nleaves, (uint64_t)(a - 1), k)) {
     a = a > (int64_t)step ? a - (int64_t)step : 0;

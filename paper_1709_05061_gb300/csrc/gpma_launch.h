@@ -97,10 +97,10 @@ void launch_segment_merge(const Geo &src, const Geo &dst, Ctl *ctl, const Work &
                           bool whole, cudaStream_t s);
 
 // k_model.cu: train the learned leaf search on the current pivots (tmp >= 2 * kPieces);
-// with only_if_escalated the kernels do nothing unless this batch had inserts that
-// did not fit their leaf (level-0 merges move pivots only inside their leaves)
+// with after_batch the model is retrained only once merges above level 0 have
+// rewritten enough leaves since the last training (decided on the device)
 void launch_train_model(const Geo &g, ModelHead *head, Piece *pieces, uint32_t *tmp, const Ctl *ctl,
-                        bool only_if_escalated, cudaStream_t s);
+                        bool after_batch, cudaStream_t s);
 
 // k_misc.cu
 void launch_rebuild_indexes(const Geo &g, Ctl *ctl, cudaStream_t s);  // cnt, F, tree, row_end, total

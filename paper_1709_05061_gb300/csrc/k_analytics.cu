@@ -103,17 +103,17 @@ __device__ __forceinline__ void pr_push(uint64_t k, const uint64_t *__restrict__
     atomicAdd((unsigned long long *)&y[k & 0xFFFFFFFFull], (unsigned long long)__ldg(cfx + (k >> 32)));
 }
 
-__global__ void __launch_bounds__(256) k_pr_scatter(Geo g, const uint64_t *__restrict__ cfx,
-                                                    uint64_t *__restrict__ y) {
-  const uint64_t npairs = g.C >> 1;
-  const ulonglong2 *s2 = reinterpret_cast<const ulonglong2 *>(g.slots);
-  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+// 32-bit indices (C <= 2^32 slots) keep the pass at 32 registers: eight resident
+// blocks per SM, four 16-byte slot loads in flight per thread
+__global__ void __launch_bounds__(256, 8) k_pr_scatter(const ulonglong2 *__restrict__ s2, uint32_t npairs,
+                                                       const uint64_t *__restrict__ cfx, uint64_t *__restrict__ y) {
+  const uint32_t stride = gridDim.x * blockDim.x;
   const ulonglong2 none = make_ulonglong2(kEmpty, kEmpty);
-  uint64_t p = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  uint32_t p = blockIdx.x * blockDim.x + threadIdx.x;
   ulonglong2 a = p < npairs ? __ldcs(s2 + p) : none;
   ulonglong2 b = p + stride < npairs ? __ldcs(s2 + p + stride) : none;
   while (p < npairs) {
-    const uint64_t q = p + 2 * stride;
+    const uint32_t q = p + 2 * stride;
     const ulonglong2 na = q < npairs ? __ldcs(s2 + q) : none;
     const ulonglong2 nb = q + stride < npairs ? __ldcs(s2 + q + stride) : none;
     pr_push(a.x, cfx, y);
@@ -157,7 +157,8 @@ void launch_pr_setup(const Geo &g, uint32_t iters, float *rank, uint64_t *y, uin
 
 void launch_pr_scatter(const Geo &g, const uint64_t *cfx, uint64_t *y, cudaStream_t s) {
   note_launch();
-  k_pr_scatter<<<nb(g.C >> 2, 256, 152 * 8), 256, 0, s>>>(g, cfx, y);
+  k_pr_scatter<<<nb(g.C >> 2, 256, 152 * 8), 256, 0, s>>>(reinterpret_cast<const ulonglong2 *>(g.slots),
+                                                           (uint32_t)(g.C >> 1), cfx, y);
 }
 
 void launch_pr_apply(const Geo &g, float damping, float *rank, uint64_t *y, uint64_t *cfx,

@@ -4,9 +4,9 @@
 //   k_prep        validate keys, compress (src, dst, insert/delete tag) into one
 //                 sortable word, build the radix histograms of every pass
 //   k_sort_pass   one stable LSD radix pass (single pass per digit with look-back)
-//   k_keep        unique + insert/delete cancellation on the sorted words, then the
-//                 leaf search of every surviving key (learned model when trained,
-//                 else binary search; both give the same leaf)
+//   k_keep        unique + insert/delete cancellation on the sorted words
+//   k_search      leaf search of every surviving key, one per thread (learned
+//                 model when trained, else binary search; both give the same leaf)
 //   k_runs        heads of the runs of equal leaf (single-pass compaction)
 //   k_small_front all of the above in one block for batches of at most
 //                 kSmallBatch keys (bitonic sort in shared memory)
@@ -175,12 +175,10 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_pass(const uint64_t *__re
   }
 }
 
-// unique + cancellation (reading R2), then the leaf of every survivor (reading R4)
+// unique + cancellation (reading R2): survivors compacted in order
 __global__ void __launch_bounds__(kScanThreads) k_keep(PrepArgs a, const uint64_t *__restrict__ sorted,
-                                                        const uint64_t *__restrict__ F, uint64_t nleaves,
                                                         uint64_t *__restrict__ ukey, uint8_t *__restrict__ utag,
-                                                        uint32_t *__restrict__ uleaf, uint64_t *status, Ctl *ctl,
-                                                        const ModelHead *mhead, const Piece *__restrict__ mpieces) {
+                                                        uint64_t *status, Ctl *ctl) {
   __shared__ ScanSmem sm;
   const uint32_t tile = take_ticket(ctl, kSlotKeep, sm), n = ctl->n;
   uint32_t flag[kScanItems];
@@ -201,19 +199,29 @@ __global__ void __launch_bounds__(kScanThreads) k_keep(PrepArgs a, const uint64_
   }
   uint32_t off[kScanItems];
   uint32_t total = tile_scan(flag, off, tile, status, 1, 0, ctl->epoch + kSlotKeep, &ctl->err, sm);
-  ModelHead m;
-  m.valid = 0;
-  if (mhead) m = *mhead;
-  const bool learned = m.valid != 0;
 #pragma unroll
   for (int r = 0; r < kScanItems; r++) {
     if (!flag[r] || off[r] >= n) continue;
-    uint64_t key = expand(w[r], a);
-    ukey[off[r]] = key;
+    ukey[off[r]] = expand(w[r], a);
     utag[off[r]] = (uint8_t)(w[r] >> 63);
-    uleaf[off[r]] = learned ? learned_leaf_search(m, mpieces, F, nleaves, key) : leaf_search(F, nleaves, key);
   }
   if ((uint64_t)(tile + 1) * kScanTile >= n && threadIdx.x == 0) ctl->m = total;
+}
+
+// the leaf of every survivor (reading R4), one per thread so the searches' load
+// chains overlap: the learned model when trained, else binary search (same leaf)
+__global__ void __launch_bounds__(256) k_search(const uint64_t *__restrict__ ukey, uint32_t *__restrict__ uleaf,
+                                                const uint64_t *__restrict__ F, uint64_t nleaves, const Ctl *ctl,
+                                                const ModelHead *mhead, const Piece *__restrict__ mpieces) {
+  const uint32_t m = ctl->m;
+  ModelHead hd;
+  hd.valid = 0;
+  if (mhead) hd = *mhead;
+  const bool learned = hd.valid != 0;
+  for (uint32_t e = blockIdx.x * blockDim.x + threadIdx.x; e < m; e += gridDim.x * blockDim.x) {
+    const uint64_t key = ukey[e];
+    uleaf[e] = learned ? learned_leaf_search(hd, mpieces, F, nleaves, key) : leaf_search(F, nleaves, key);
+  }
 }
 
 __global__ void __launch_bounds__(kScanThreads) k_runs(const uint32_t *__restrict__ uleaf,
@@ -486,8 +494,10 @@ void launch_sort(const FrontArgs &f, uint64_t nb, cudaStream_t s) {
   // look-back epochs: pass p uses epoch + p, then the fixed slots of gpma_launch.h
   const uint32_t ct = comp_tiles(nb);
   note_launch();
-  k_keep<<<ct, kScanThreads, 0, s>>>(a, src, f.geo->F, f.geo->nleaves, f.ukey, f.utag, f.uleaf, f.status,
-                                     f.ctl, f.mhead, f.mpieces);
+  k_keep<<<ct, kScanThreads, 0, s>>>(a, src, f.ukey, f.utag, f.status, f.ctl);
+  note_launch();
+  k_search<<<grid_for(nb, 256, 152 * 16), 256, 0, s>>>(f.ukey, f.uleaf, f.geo->F, f.geo->nleaves, f.ctl, f.mhead,
+                                                       f.mpieces);
   note_launch();
   k_runs<<<ct, kScanThreads, 0, s>>>(f.uleaf, f.run_start, f.run_leaf, f.status, f.ctl);
 }

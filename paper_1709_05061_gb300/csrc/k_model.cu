@@ -23,8 +23,20 @@ uint32_t nblk(uint64_t items, uint32_t per_block, uint32_t cap) {
 }
 }  // namespace
 
-__global__ void k_lm_init(ModelHead *head, uint32_t *first, uint32_t *last, const Ctl *ctl, int only_if_escalated) {
-  if (only_if_escalated && ctl->nesc == 0) return;
+__global__ void k_lm_decide(Geo g, ModelHead *head, const Ctl *ctl, int after_batch) {
+  bool now = true;
+  if (after_batch) {
+    const uint64_t d = head->drift + (ctl->err == 0 ? ctl->nleafw : 0u);
+    now = head->valid == 0 || d * 32 >= g.nleaves;
+    head->drift = now ? 0 : d;
+  } else {
+    head->drift = 0;
+  }
+  head->train = now ? 1u : 0u;
+}
+
+__global__ void k_lm_init(ModelHead *head, uint32_t *first, uint32_t *last) {
+  if (!head->train) return;
   const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t == 0) {
     head->kmin = kEmpty;
@@ -41,8 +53,8 @@ __global__ void k_lm_init(ModelHead *head, uint32_t *first, uint32_t *last, cons
 // the pivots of non-empty leaves increase with the leaf: the smallest is the
 // first non-empty leaf's, the largest the last one's (warp 0 scans from the
 // front, warp 1 from the back, 32 leaves at a time)
-__global__ void k_lm_minmax(Geo g, ModelHead *head, const Ctl *ctl, int only_if_escalated) {
-  if (only_if_escalated && ctl->nesc == 0) return;
+__global__ void k_lm_minmax(Geo g, ModelHead *head) {
+  if (!head->train) return;
   const uint32_t lane = lane_id(), w = threadIdx.x >> 5;
   if (w > 1) return;
   for (uint64_t b = 0; b < g.nleaves; b += 32) {
@@ -60,17 +72,16 @@ __global__ void k_lm_minmax(Geo g, ModelHead *head, const Ctl *ctl, int only_if_
   }
 }
 
-__global__ void k_lm_scale(ModelHead *head, const Ctl *ctl, int only_if_escalated) {
-  if (only_if_escalated && ctl->nesc == 0) return;
+__global__ void k_lm_scale(ModelHead *head) {
+  if (!head->train) return;
   if (head->kmin == kEmpty) return;  // no pivot: the model stays invalid
   const uint64_t span = head->kmax - head->kmin + 1;
   head->rscale = (float)kPieces / (float)span;
 }
 
 // neighbouring leaves mostly share a piece: lanes of one piece combine first
-__global__ void k_lm_route(Geo g, const ModelHead *head, uint32_t *first, uint32_t *last, const Ctl *ctl,
-                           int only_if_escalated) {
-  if (only_if_escalated && ctl->nesc == 0) return;
+__global__ void k_lm_route(Geo g, const ModelHead *head, uint32_t *first, uint32_t *last) {
+  if (!head->train) return;
   const ModelHead m = *head;
   if (m.kmin == kEmpty) return;
   const uint64_t n32 = (g.nleaves + 31) & ~31ull;
@@ -87,12 +98,11 @@ __global__ void k_lm_route(Geo g, const ModelHead *head, uint32_t *first, uint32
 
 // one block: running maximum of the last training leaf over the pieces in order
 __global__ void __launch_bounds__(1024) k_lm_fit(Geo g, const ModelHead *head, const uint32_t *first,
-                                                 const uint32_t *last, Piece *pieces, const Ctl *ctl,
-                                                 int only_if_escalated) {
+                                                 const uint32_t *last, Piece *pieces) {
   __shared__ uint32_t wmax[32];
   constexpr uint32_t kPer = kPieces / 1024;
   const uint32_t t = threadIdx.x, lane = lane_id(), wid = t >> 5;
-  if (only_if_escalated && ctl->nesc == 0) return;
+  if (!head->train) return;
   if (head->kmin == kEmpty) return;
   // pieces [t*kPer, (t+1)*kPer) per thread: local running max, then a block scan of maxima
   uint32_t lmax = 0;
@@ -152,8 +162,8 @@ __global__ void __launch_bounds__(1024) k_lm_fit(Geo g, const ModelHead *head, c
   }
 }
 
-__global__ void k_lm_err(Geo g, const ModelHead *head, Piece *pieces, const Ctl *ctl, int only_if_escalated) {
-  if (only_if_escalated && ctl->nesc == 0) return;
+__global__ void k_lm_err(Geo g, const ModelHead *head, Piece *pieces) {
+  if (!head->train) return;
   const ModelHead m = *head;
   if (m.kmin == kEmpty) return;
   const uint64_t n32 = (g.nleaves + 31) & ~31ull;
@@ -179,30 +189,31 @@ __global__ void k_lm_err(Geo g, const ModelHead *head, Piece *pieces, const Ctl 
   }
 }
 
-__global__ void k_lm_valid(ModelHead *head, const Ctl *ctl, int only_if_escalated) {
-  if (only_if_escalated && ctl->nesc == 0) return;
+__global__ void k_lm_valid(ModelHead *head) {
+  if (!head->train) return;
   head->valid = head->kmin != kEmpty;
 }
 
 void launch_train_model(const Geo &g, ModelHead *head, Piece *pieces, uint32_t *tmp, const Ctl *ctl,
-                        bool only_if_escalated, cudaStream_t s) {
+                        bool after_batch, cudaStream_t s) {
   uint32_t *first = tmp, *last = tmp + kPieces;
-  const int c = only_if_escalated ? 1 : 0;
   note_launch();
-  k_lm_init<<<16, 256, 0, s>>>(head, first, last, ctl, c);
+  k_lm_decide<<<1, 1, 0, s>>>(g, head, ctl, after_batch ? 1 : 0);
   note_launch();
-  k_lm_minmax<<<1, 64, 0, s>>>(g, head, ctl, c);
+  k_lm_init<<<16, 256, 0, s>>>(head, first, last);
   note_launch();
-  k_lm_scale<<<1, 1, 0, s>>>(head, ctl, c);
+  k_lm_minmax<<<1, 64, 0, s>>>(g, head);
+  note_launch();
+  k_lm_scale<<<1, 1, 0, s>>>(head);
   const uint32_t b = nblk(g.nleaves, 256, 152 * 8);
   note_launch();
-  k_lm_route<<<b, 256, 0, s>>>(g, head, first, last, ctl, c);
+  k_lm_route<<<b, 256, 0, s>>>(g, head, first, last);
   note_launch();
-  k_lm_fit<<<1, 1024, 0, s>>>(g, head, first, last, pieces, ctl, c);
+  k_lm_fit<<<1, 1024, 0, s>>>(g, head, first, last, pieces);
   note_launch();
-  k_lm_err<<<b, 256, 0, s>>>(g, head, pieces, ctl, c);
+  k_lm_err<<<b, 256, 0, s>>>(g, head, pieces);
   note_launch();
-  k_lm_valid<<<1, 1, 0, s>>>(head, ctl, c);
+  k_lm_valid<<<1, 1, 0, s>>>(head);
 }
 
 }  // namespace gpk

@@ -309,3 +309,23 @@ def test_growth_without_stats_matches_oracle():
     assert len(caps) >= 4
     assert g.check() == 0
     assert g.num_edges() == stream.size
+
+
+def test_pagerank_mid_size():
+    """R-MAT scale 16, 10^6 edges (2^21 slots): ranks after 1 and 20 iterations,
+    BFS and CC against the oracle."""
+    V = 1 << 16
+    stream = W.rmat_stream(16, 1_000_000, seed=8)
+    g = gp.Graph(V, leaf_size=64)
+    o = oracle.OraclePMA(V, L=64)
+    g.update(dev(stream), None, stats=True)
+    o.update(stream)
+    assert g.capacity == 1 << 21
+    for it in (1, 20):
+        pr = g.pagerank(it, 0.85).cpu().numpy().astype(np.float64)
+        ref = o.pagerank(it, 0.85)
+        assert np.max(np.abs(pr - ref) / ref) <= PR_TOL
+    g.status()
+    src = int(stream[0] >> np.uint64(32))
+    assert np.array_equal(g.bfs(src).cpu().numpy(), o.bfs(src))
+    assert np.array_equal(g.cc().cpu().numpy().view(np.uint32), o.cc())
