@@ -217,7 +217,6 @@ struct gpma {
   // learned leaf search (nullptr with GPMA_PLAIN_SEARCH)
   ModelHead *mhead;
   Piece *mpieces;
-  uint32_t *mtmp;
   uint32_t since_train;
   // device-side root resize: the array of height h+1 a batch may grow into, and
   // the control block such a batch sends back (read before the next call)
@@ -420,7 +419,7 @@ int read_ctl(gpma *h, cudaStream_t s) {
 
 void train_model(gpma *h, cudaStream_t s, bool after_batch = false) {
   if (!h->mhead) return;
-  launch_train_model(h->geo, h->mhead, h->mpieces, h->mtmp, h->ctl, after_batch, s);
+  launch_train_model(h->geo, h->mhead, h->mpieces, h->ctl, after_batch, s);
   if (!after_batch) h->since_train = 0;
 }
 
@@ -553,7 +552,7 @@ bool capture_update(gpma *h, FrontArgs &f, uint32_t nb, bool stats, bool grow, G
     launch_segments(g, h->ctl, h->w, nb, t);
     launch_segment_merge(g, g, h->ctl, h->w, h->scratch_cap, g.nleaves, h->scratch, h->vbuf, h->partials, false,
                          t);
-    if (h->mhead) launch_train_model(g, h->mhead, h->mpieces, h->mtmp, h->ctl, true, t);
+    if (h->mhead) launch_train_model(g, h->mhead, h->mpieces, h->ctl, true, t);
   };
   if (!small_front(nb)) launch_sort(f, nb, gc.cap);
   launch_leaf_pass(g, h->ctl, h->w, nb, gc.cap);
@@ -573,7 +572,7 @@ bool capture_update(gpma *h, FrontArgs &f, uint32_t nb, bool stats, bool grow, G
       launch_unmark(g, h->ctl, h->w, nb, t);
       launch_segment_merge(g, g2, h->ctl, h->w, h->scratch_cap, g.nleaves, h->scratch, h->vbuf, h->partials,
                            true, t);
-      if (h->mhead) launch_train_model(g2, h->mhead, h->mpieces, h->mtmp, h->ctl, false, t);
+      if (h->mhead) launch_train_model(g2, h->mhead, h->mpieces, h->ctl, false, t);
     });
     ok = ok && capture_if(gc.cap, gc.cap2, cmerge, merges);
   }
@@ -928,7 +927,7 @@ int gpma_create(uint32_t n_vertices, const gpma_params *params, const gpma_alloc
   bool ok = alloc_arrays(h, &h->geo, s) && dalloc(h, &h->ctl, 1, s) && dalloc(h, &h->hist, 8 * 256, s) &&
             dalloc(h, &h->check_buf, 4, s);
   if (ok && !(p.flags & GPMA_PLAIN_SEARCH)) {
-    ok = dalloc(h, &h->mhead, 1, s) && dalloc(h, &h->mpieces, kPieces, s) && dalloc(h, &h->mtmp, 2 * kPieces, s);
+    ok = dalloc(h, &h->mhead, 1, s) && dalloc(h, &h->mpieces, kPieces, s);
     if (ok) ok = cudaMemsetAsync(h->mhead, 0, sizeof(ModelHead), s) == cudaSuccess;
   }
   if (ok && !raw) ok = dalloc(h, &h->geo.row_end, h->V, s) && dalloc(h, &h->geo.deg, h->V, s);
@@ -976,7 +975,7 @@ int gpma_destroy(gpma_t h) {
   dfree(h, h->geo.row_end, s);
   dfree(h, h->geo.deg, s);
   free_work(h, s);
-  void *ptrs[] = {h->mhead, h->mpieces, h->mtmp, h->ctl, h->hist, h->scratch, h->vbuf, h->partials, h->cfx, h->y,
+  void *ptrs[] = {h->mhead, h->mpieces, h->ctl, h->hist, h->scratch, h->vbuf, h->partials, h->cfx, h->y,
                   h->dsum, h->q0,  h->q1,  h->q2,    h->counter, h->check_buf, h->guards, h->pr_partials,
                   h->pr_counter};
   for (void *p : ptrs) dfree(h, p, s);

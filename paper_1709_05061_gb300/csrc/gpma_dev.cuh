@@ -99,6 +99,26 @@ __device__ __forceinline__ void degree_delta(uint32_t *deg, bool active, uint64_
 }
 __device__ __forceinline__ uint32_t lanemask_lt() { return (1u << lane_id()) - 1u; }
 
+// Out-degree change of one run held in lanes [0, len) in ascending key order
+// (lanes of one source are contiguous): d = +1 for an inserted edge, -1 for a
+// deleted one, 0 otherwise.  One atomic per source, from its first lane.
+__device__ __forceinline__ void run_degree_delta(uint32_t *deg, uint32_t len, uint64_t key, int d) {
+  const uint32_t lane = lane_id();
+  const bool act = lane < len;
+  const uint32_t pos = __ballot_sync(0xFFFFFFFFu, act && d > 0), neg = __ballot_sync(0xFFFFFFFFu, act && d < 0);
+  if (!(pos | neg)) return;  // the same on every lane
+  const uint32_t src = (uint32_t)(key >> 32);
+  const uint32_t prev = __shfl_up_sync(0xFFFFFFFFu, src, 1);
+  const uint32_t heads = __ballot_sync(0xFFFFFFFFu, act && (lane == 0 || prev != src));
+  if (act && ((heads >> lane) & 1u)) {
+    const uint32_t later = heads & ~((2u << lane) - 1u);  // lane 31: 2u << 31 == 0, so none
+    const uint32_t end = later ? (uint32_t)(__ffs(later) - 1) : len;
+    const uint32_t seg = (end >= 32 ? 0xFFFFFFFFu : ((1u << end) - 1u)) & ~((1u << lane) - 1u);
+    const int sum = __popc(pos & seg) - __popc(neg & seg);
+    if (sum) atomicAdd(&deg[src], (uint32_t)sum);
+  }
+}
+
 template <typename T>
 __device__ __forceinline__ T warp_incl_scan(T v) {
 #pragma unroll
@@ -154,40 +174,47 @@ __device__ __forceinline__ uint32_t leaf_search(const uint64_t *__restrict__ F, 
   return p ? (uint32_t)(p - 1) : 0u;
 }
 
-// ---- learned leaf search (two-stage linear model over the pivots) -----------------------------
-// Root: piece = floor((k - kmin) * rscale), monotone in k.  Piece i: the leaves its
-// training pivots fell in span [first, last]; every key routed to it has its
-// leaf in [lo, hi] (lo = last leaf of the pieces before it); the piece predicts
-// first + (k - kb) * slope with training error err.  The search window is
-// checked against the current pivots and widened until it brackets the answer,
-// so the result equals leaf_search exactly whatever the model's staleness.
+// ---- learned leaf search (two-stage model over the pivots) -------------------------------------
+// Pieces: the leaves are cut into kPieces equal ranges of 2^span leaves each (the
+// density bounds keep the keys per range near-equal, so these are quantile buckets
+// of the pivots).  Root: the piece of key k is the last piece whose boundary (its
+// first training pivot) is <= k, found by a search over the 4096 boundaries, which
+// stay in L1.  Piece: an FP32 linear model first + (k - kb) * slope over its own
+// leaves, clamped to the piece's answer bracket [lo, hi], with training error err.
+// The predicted window is checked against the current pivots and widened until it
+// brackets the answer, so the result equals leaf_search exactly, whatever the
+// model's staleness.
 constexpr uint32_t kPieces = 4096;
 
 struct Piece {
-  uint64_t kb;      // pivot of the piece's first training leaf
+  uint64_t kb;      // boundary: pivot of the piece's first non-empty leaf (empty piece:
+                    // the next non-empty piece's boundary, EMPTY at the end)
   uint32_t lo, hi;  // answer bracket at training time
-  uint32_t first;   // first training leaf (kNoLeaf: no leaf routed here)
+  uint32_t first;   // first non-empty training leaf (kNoLeaf: none)
   uint32_t err;     // max |prediction - leaf| over the training leaves
   float slope;
   uint32_t pad;
 };
 
 struct ModelHead {
-  uint64_t kmin;
-  float rscale;
+  uint32_t npieces;  // pieces in use (min(kPieces, leaves))
+  uint32_t span;     // log2 leaves per piece
   uint32_t valid;
-  uint64_t kmax;
-  uint64_t drift;  // leaves rewritten by merges above level 0 since the model was trained
-  uint32_t train;  // this call retrains (decided by k_lm_decide)
-  uint32_t pad;
+  uint32_t train;    // this call retrains (decided by k_lm_decide)
+  uint64_t drift;    // leaves rewritten by merges above level 0 since the model was trained
 };
 
 constexpr uint32_t kNoLeaf = 0xFFFFFFFFu;
 
-__device__ __forceinline__ uint32_t model_route(const ModelHead &m, uint64_t k) {
-  const float d = (float)(k > m.kmin ? k - m.kmin : 0ull) * m.rscale;
-  const uint32_t p = d >= (float)(kPieces - 1) ? kPieces - 1 : (uint32_t)d;
-  return p;
+// last piece whose boundary is <= k, or -1
+__device__ __forceinline__ int32_t model_route(const ModelHead &m, const Piece *__restrict__ pieces, uint64_t k) {
+  uint32_t a = 0, b = m.npieces;
+  while (a < b) {
+    const uint32_t mid = (a + b) >> 1;
+    if (__ldg(&pieces[mid].kb) <= k) a = mid + 1;
+    else b = mid;
+  }
+  return (int32_t)a - 1;
 }
 
 // eff(j) <= k ?
@@ -202,10 +229,11 @@ __device__ __forceinline__ bool eff_at_most(const uint64_t *__restrict__ F, uint
 __device__ __forceinline__ uint32_t learned_leaf_search(const ModelHead &m, const Piece *__restrict__ pieces,
                                                         const uint64_t *__restrict__ F, uint64_t nleaves,
                                                         uint64_t k) {
-  const Piece pc = pieces[model_route(m, k)];
+  const int32_t pi = model_route(m, pieces, k);
+  const Piece pc = pieces[pi < 0 ? 0 : pi];
   // candidate window for p (= answer + 1)
-  int64_t pred = (int64_t)pc.lo;
-  if (pc.first != kNoLeaf) {
+  int64_t pred = pi < 0 ? 0 : (int64_t)pc.lo;
+  if (pi >= 0 && pc.first != kNoLeaf) {
     const float d = (float)(k > pc.kb ? k - pc.kb : 0ull) * pc.slope;
     pred = (int64_t)pc.first + (int64_t)d;
     if (pred < (int64_t)pc.lo) pred = pc.lo;

@@ -99,8 +99,8 @@ void launch_segment_merge(const Geo &src, const Geo &dst, Ctl *ctl, const Work &
 // k_model.cu: train the learned leaf search on the current pivots (tmp >= 2 * kPieces);
 // with after_batch the model is retrained only once merges above level 0 have
 // rewritten enough leaves since the last training (decided on the device)
-void launch_train_model(const Geo &g, ModelHead *head, Piece *pieces, uint32_t *tmp, const Ctl *ctl,
-                        bool after_batch, cudaStream_t s);
+void launch_train_model(const Geo &g, ModelHead *head, Piece *pieces, const Ctl *ctl, bool after_batch,
+                        cudaStream_t s);
 
 // k_misc.cu
 void launch_rebuild_indexes(const Geo &g, Ctl *ctl, cudaStream_t s);  // cnt, F, tree, row_end, total

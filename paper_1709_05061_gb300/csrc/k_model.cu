@@ -1,27 +1,19 @@
-// k_model.cu -- training of the learned leaf search (a two-stage linear model
-// over the leaf pivots; the search itself is learned_leaf_search in
-// gpma_dev.cuh).  Everything runs on the device from the current pivots:
-//   k_lm_init    reset the head and the per-piece first/last training leaf
-//   k_lm_minmax  smallest and largest pivot (range of the root model)
-//   k_lm_scale   root slope: pieces per key unit
-//   k_lm_route   route every non-empty leaf's pivot to its piece
-//   k_lm_fit     per piece: base key, slope, answer bracket (running max of the
-//                last leaves of the pieces before it)
-//   k_lm_err     per piece: largest |prediction - leaf| over its training leaves
-//   k_lm_valid   publish the model
+// k_model.cu -- training of the learned leaf search (the model and the search
+// are in gpma_dev.cuh).  Everything runs on the device from the current pivots:
+//   k_lm_decide  retrain now?  Always after a resize or import and periodically;
+//                after a batch only once merges above level 0 have rewritten a
+//                thirty-second of the leaves since the last training (a level-0
+//                merge moves keys only inside their leaf, and the search stays
+//                exact whatever the staleness, only slower)
+//   k_lm_fit     one warp per piece (2^span consecutive leaves): its first and
+//                last non-empty leaf, boundary, slope, answer bracket and the
+//                largest prediction error over its leaves
+//   k_lm_valid   one block: empty pieces take the next boundary (so the
+//                boundaries never decrease), then the model is published
 #include "gpma_dev.cuh"
 #include "gpma_launch.h"
 
 namespace gpk {
-
-namespace {
-uint32_t nblk(uint64_t items, uint32_t per_block, uint32_t cap) {
-  uint64_t b = (items + per_block - 1) / per_block;
-  if (b < 1) b = 1;
-  if (b > cap) b = cap;
-  return (uint32_t)b;
-}
-}  // namespace
 
 __global__ void k_lm_decide(Geo g, ModelHead *head, const Ctl *ctl, int after_batch) {
   bool now = true;
@@ -32,188 +24,129 @@ __global__ void k_lm_decide(Geo g, ModelHead *head, const Ctl *ctl, int after_ba
   } else {
     head->drift = 0;
   }
+  uint32_t span = 0;
+  while ((g.nleaves >> span) > kPieces) span++;
   head->train = now ? 1u : 0u;
-}
-
-__global__ void k_lm_init(ModelHead *head, uint32_t *first, uint32_t *last) {
-  if (!head->train) return;
-  const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t == 0) {
-    head->kmin = kEmpty;
-    head->kmax = 0;
+  if (now) {
     head->valid = 0;
-    head->rscale = 0.0f;
-  }
-  for (uint32_t p = t; p < kPieces; p += gridDim.x * blockDim.x) {
-    first[p] = kNoLeaf;
-    last[p] = 0;
+    head->span = span;
+    head->npieces = (uint32_t)(g.nleaves >> span);
   }
 }
 
-// the pivots of non-empty leaves increase with the leaf: the smallest is the
-// first non-empty leaf's, the largest the last one's (warp 0 scans from the
-// front, warp 1 from the back, 32 leaves at a time)
-__global__ void k_lm_minmax(Geo g, ModelHead *head) {
+__global__ void __launch_bounds__(256) k_lm_fit(Geo g, const ModelHead *head, Piece *pieces) {
   if (!head->train) return;
-  const uint32_t lane = lane_id(), w = threadIdx.x >> 5;
-  if (w > 1) return;
-  for (uint64_t b = 0; b < g.nleaves; b += 32) {
-    const uint64_t j = w == 0 ? b + lane : g.nleaves - 1 - (b + lane);
-    const bool inb = b + lane < g.nleaves;
-    const uint64_t f = inb ? g.F[j] : kEmpty;
-    const uint32_t bal = __ballot_sync(0xFFFFFFFFu, f != kEmpty);
+  const uint32_t lane = lane_id(), span = head->span, np = head->npieces;
+  const uint64_t S = 1ull << span;
+  const uint32_t p = blockIdx.x * 8 + (threadIdx.x >> 5);
+  if (p >= np) return;
+  const uint64_t j0 = (uint64_t)p << span;
+  // first and last non-empty leaf of the piece
+  uint64_t first = kEmpty, last = kEmpty;
+  for (uint64_t b = 0; b < S; b += 32) {
+    const uint64_t j = j0 + b + lane;
+    const bool ne = b + lane < S && __ldg(g.F + j) != kEmpty;
+    const uint32_t bal = __ballot_sync(0xFFFFFFFFu, ne);
     if (bal) {
-      const uint64_t pick = __shfl_sync(0xFFFFFFFFu, f, __ffs(bal) - 1);
-      if (lane == 0) {
-        if (w == 0) head->kmin = pick; else head->kmax = pick;
-      }
-      return;
+      if (first == kEmpty) first = j0 + b + (__ffs(bal) - 1);
+      last = j0 + b + (31 - __clz(bal));
     }
   }
-}
-
-__global__ void k_lm_scale(ModelHead *head) {
-  if (!head->train) return;
-  if (head->kmin == kEmpty) return;  // no pivot: the model stays invalid
-  const uint64_t span = head->kmax - head->kmin + 1;
-  head->rscale = (float)kPieces / (float)span;
-}
-
-// neighbouring leaves mostly share a piece: lanes of one piece combine first
-__global__ void k_lm_route(Geo g, const ModelHead *head, uint32_t *first, uint32_t *last) {
-  if (!head->train) return;
-  const ModelHead m = *head;
-  if (m.kmin == kEmpty) return;
-  const uint64_t n32 = (g.nleaves + 31) & ~31ull;
-  for (uint64_t j = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n32; j += (uint64_t)gridDim.x * blockDim.x) {
-    const uint64_t f = j < g.nleaves ? g.F[j] : kEmpty;
-    const uint32_t p = f != kEmpty ? model_route(m, f) : 0xFFFFFFFFu;
-    const uint32_t peers = __match_any_sync(0xFFFFFFFFu, p);
-    if (p == 0xFFFFFFFFu) continue;
-    const uint32_t lo = __ffs(peers) - 1, hi = 31 - __clz(peers);
-    if (lane_id() == lo) atomicMin(&first[p], (uint32_t)j);
-    if (lane_id() == hi) atomicMax(&last[p], (uint32_t)j);
-  }
-}
-
-// one block: running maximum of the last training leaf over the pieces in order
-__global__ void __launch_bounds__(1024) k_lm_fit(Geo g, const ModelHead *head, const uint32_t *first,
-                                                 const uint32_t *last, Piece *pieces) {
-  __shared__ uint32_t wmax[32];
-  constexpr uint32_t kPer = kPieces / 1024;
-  const uint32_t t = threadIdx.x, lane = lane_id(), wid = t >> 5;
-  if (!head->train) return;
-  if (head->kmin == kEmpty) return;
-  // pieces [t*kPer, (t+1)*kPer) per thread: local running max, then a block scan of maxima
-  uint32_t lmax = 0;
-  bool any = false;
-  for (uint32_t q = 0; q < kPer; q++) {
-    const uint32_t p = t * kPer + q;
-    if (first[p] != kNoLeaf) {
-      lmax = last[p] > lmax ? last[p] : lmax;
-      any = true;
-    }
-  }
-  // exclusive running max over threads (a leaf index + 1, 0 = none)
-  uint32_t v = any ? lmax + 1 : 0, inc = v;
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const uint32_t u = __shfl_up_sync(0xFFFFFFFFu, inc, o);
-    if ((int)lane >= o && u > inc) inc = u;
-  }
-  if (lane == 31) wmax[wid] = inc;
-  __syncthreads();
-  if (wid == 0) {
-    uint32_t x = wmax[lane], xi = x;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const uint32_t u = __shfl_up_sync(0xFFFFFFFFu, xi, o);
-      if ((int)lane >= o && u > xi) xi = u;
-    }
-    wmax[lane] = xi;  // inclusive over warps
-  }
-  __syncthreads();
-  uint32_t before = __shfl_up_sync(0xFFFFFFFFu, inc, 1);
-  if (lane == 0) before = 0;
-  if (wid > 0 && wmax[wid - 1] > before) before = wmax[wid - 1];
-  // walk this thread's pieces in order
-  uint32_t run = before;  // last leaf + 1 of the pieces before, 0 = none
-  for (uint32_t q = 0; q < kPer; q++) {
-    const uint32_t p = t * kPer + q;
-    Piece pc;
-    pc.lo = run ? run - 1 : 0;
+  Piece pc;
+  pc.pad = 0;
+  if (first == kEmpty) {
+    pc.kb = kEmpty;  // filled in by k_lm_valid
+    pc.first = kNoLeaf;
+    pc.lo = pc.hi = (uint32_t)j0;
+    pc.slope = 0.0f;
     pc.err = 0;
-    pc.pad = 0;
-    if (first[p] != kNoLeaf) {
-      const uint32_t a = first[p], b = last[p];
-      pc.first = a;
-      pc.kb = g.F[a];
-      const uint64_t kspan = g.F[b] - g.F[a];
-      pc.slope = (b > a && kspan) ? (float)(b - a) / (float)kspan : 0.0f;
-      pc.hi = b > pc.lo ? b : pc.lo;
-      run = b + 1 > run ? b + 1 : run;
-    } else {
-      pc.first = kNoLeaf;
-      pc.kb = 0;
-      pc.slope = 0.0f;
-      pc.hi = pc.lo;
+  } else {
+    pc.kb = __ldg(g.F + first);
+    pc.first = (uint32_t)first;
+    pc.lo = (uint32_t)first;
+    pc.hi = (uint32_t)last;
+    const uint64_t kspan = __ldg(g.F + last) - pc.kb;
+    pc.slope = (last > first && kspan) ? (float)(last - first) / (float)kspan : 0.0f;
+    // largest |prediction - leaf| over the non-empty leaves
+    uint32_t e = 0;
+    for (uint64_t b = 0; b < S; b += 32) {
+      const uint64_t j = j0 + b + lane;
+      const uint64_t f = b + lane < S ? __ldg(g.F + j) : kEmpty;
+      if (f != kEmpty) {
+        const float d = (float)(f - pc.kb) * pc.slope;
+        int64_t pred = (int64_t)pc.first + (int64_t)d;
+        if (pred < (int64_t)pc.lo) pred = pc.lo;
+        if (pred > (int64_t)pc.hi) pred = pc.hi;
+        const uint32_t ej = (uint32_t)(pred > (int64_t)j ? pred - (int64_t)j : (int64_t)j - pred);
+        e = ej > e ? ej : e;
+      }
     }
-    pieces[p] = pc;
+    for (int o = 16; o > 0; o >>= 1) {
+      const uint32_t u = __shfl_xor_sync(0xFFFFFFFFu, e, o);
+      e = u > e ? u : e;
+    }
+    pc.err = e;
   }
+  if (lane == 0) pieces[p] = pc;
 }
 
-__global__ void k_lm_err(Geo g, const ModelHead *head, Piece *pieces) {
+// suffix minimum of the boundaries (an empty piece takes the next boundary), then publish
+__global__ void __launch_bounds__(1024) k_lm_valid(ModelHead *head, Piece *pieces) {
+  __shared__ uint64_t wmin[32];
+  __shared__ uint32_t any;
   if (!head->train) return;
-  const ModelHead m = *head;
-  if (m.kmin == kEmpty) return;
-  const uint64_t n32 = (g.nleaves + 31) & ~31ull;
-  for (uint64_t j = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n32; j += (uint64_t)gridDim.x * blockDim.x) {
-    const uint64_t f = j < g.nleaves ? g.F[j] : kEmpty;
-    uint32_t p = 0xFFFFFFFFu, e = 0;
-    if (f != kEmpty) {
-      p = model_route(m, f);
-      const Piece pc = pieces[p];
-      const float d = (float)(f > pc.kb ? f - pc.kb : 0ull) * pc.slope;
-      int64_t pred = (int64_t)pc.first + (int64_t)d;
-      if (pred < (int64_t)pc.lo) pred = pc.lo;
-      if (pred > (int64_t)pc.hi) pred = pc.hi;
-      e = (uint32_t)(pred > (int64_t)j ? pred - (int64_t)j : (int64_t)j - pred);
-    }
-    const uint32_t peers = __match_any_sync(0xFFFFFFFFu, p);
-    uint32_t mx = e;
-    for (uint32_t b = peers; b; b &= b - 1) {
-      const uint32_t o = __shfl_sync(peers, e, __ffs(b) - 1);
-      mx = o > mx ? o : mx;
-    }
-    if (p != 0xFFFFFFFFu && lane_id() == (uint32_t)(__ffs(peers) - 1) && mx) atomicMax(&pieces[p].err, mx);
+  const uint32_t np = head->npieces, t = threadIdx.x, lane = lane_id(), w = t >> 5;
+  constexpr uint32_t kPer = kPieces / 1024;
+  if (t == 0) any = 0;
+  // this thread's pieces [t*kPer, (t+1)*kPer), scanned from the right
+  uint64_t v[kPer], run = kEmpty;
+  bool mine = false;
+  for (int q = (int)kPer - 1; q >= 0; q--) {
+    const uint32_t p = t * kPer + q;
+    const uint64_t kb = p < np ? pieces[p].kb : kEmpty;
+    mine |= p < np && pieces[p].first != kNoLeaf;
+    run = kb < run ? kb : run;
+    v[q] = run;
   }
+  // minimum over this thread and the threads after it: in the warp, then over warps
+  uint64_t inc = run;
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint64_t u = __shfl_down_sync(0xFFFFFFFFu, inc, o);
+    if (lane + o < 32 && u < inc) inc = u;
+  }
+  if (lane == 0) wmin[w] = inc;
+  __syncthreads();
+  if (w == 0) {
+    uint64_t x = wmin[lane];
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint64_t u = __shfl_down_sync(0xFFFFFFFFu, x, o);
+      if (lane + o < 32 && u < x) x = u;
+    }
+    wmin[lane] = x;  // minimum over warps lane..31
+  }
+  if (mine) atomicOr(&any, 1u);
+  __syncthreads();
+  uint64_t right = __shfl_down_sync(0xFFFFFFFFu, inc, 1);  // threads after this one in the warp
+  if (lane == 31) right = kEmpty;
+  if (w + 1 < 32 && wmin[w + 1] < right) right = wmin[w + 1];
+  for (uint32_t q = 0; q < kPer; q++) {
+    const uint32_t p = t * kPer + q;
+    if (p >= np) break;
+    const uint64_t fill = v[q] < right ? v[q] : right;
+    if (pieces[p].first == kNoLeaf) pieces[p].kb = fill;
+  }
+  if (t == 0) head->valid = any;
 }
 
-__global__ void k_lm_valid(ModelHead *head) {
-  if (!head->train) return;
-  head->valid = head->kmin != kEmpty;
-}
-
-void launch_train_model(const Geo &g, ModelHead *head, Piece *pieces, uint32_t *tmp, const Ctl *ctl,
-                        bool after_batch, cudaStream_t s) {
-  uint32_t *first = tmp, *last = tmp + kPieces;
+void launch_train_model(const Geo &g, ModelHead *head, Piece *pieces, const Ctl *ctl, bool after_batch,
+                        cudaStream_t s) {
   note_launch();
   k_lm_decide<<<1, 1, 0, s>>>(g, head, ctl, after_batch ? 1 : 0);
+  const uint64_t np = g.nleaves < kPieces ? g.nleaves : kPieces;
   note_launch();
-  k_lm_init<<<16, 256, 0, s>>>(head, first, last);
+  k_lm_fit<<<(uint32_t)((np + 7) / 8), 256, 0, s>>>(g, head, pieces);
   note_launch();
-  k_lm_minmax<<<1, 64, 0, s>>>(g, head);
-  note_launch();
-  k_lm_scale<<<1, 1, 0, s>>>(head);
-  const uint32_t b = nblk(g.nleaves, 256, 152 * 8);
-  note_launch();
-  k_lm_route<<<b, 256, 0, s>>>(g, head, first, last);
-  note_launch();
-  k_lm_fit<<<1, 1024, 0, s>>>(g, head, first, last, pieces);
-  note_launch();
-  k_lm_err<<<b, 256, 0, s>>>(g, head, pieces);
-  note_launch();
-  k_lm_valid<<<1, 1, 0, s>>>(head);
+  k_lm_valid<<<1, 1024, 0, s>>>(head, pieces);
 }
 
 }  // namespace gpk

@@ -280,10 +280,7 @@ __global__ void __launch_bounds__(256) k_leaf64(Geo g, Ctl *ctl, Work w) {
     }
     const bool dl = act && tag && found;
     if (act) w.eflag[rs + lane] = dl ? 1 : (sv ? (fits ? 1 : 2) : 0);
-    if (!g.raw) {
-      degree_delta(g.deg, sv && !is_guard(key), key, 1);
-      degree_delta(g.deg, dl, key, -1);
-    }
+    if (!g.raw) run_degree_delta(g.deg, len, key, (sv && !is_guard(key)) ? 1 : (dl ? -1 : 0));
     if (lane == 0) {
       w.rdelta[r] = (int32_t)nins - (int32_t)ndel;
       w.rinfo[r] = fits ? 1 : ((nins || g.dual) ? 2 : 0);
