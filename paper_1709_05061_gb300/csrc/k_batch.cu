@@ -132,7 +132,18 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_pass(const uint64_t *__re
   }
 #pragma unroll
   for (int r = 0; r < kSortItems; r++) {
-    uint32_t peers = __match_any_sync(0xFFFFFFFFu, dig[r]);
+    // lanes holding the same digit, from one ballot per digit bit (cheaper than match.any)
+    uint32_t peers = 0xFFFFFFFFu;
+    for (uint32_t b = 0; b < dbits; b++) {
+      const bool bit = (dig[r] >> b) & 1u;
+      const uint32_t bal = __ballot_sync(0xFFFFFFFFu, bit);
+      peers &= bit ? bal : ~bal;
+    }
+    {
+      const bool inv = dig[r] == 0xFFFFu;
+      const uint32_t bal = __ballot_sync(0xFFFFFFFFu, inv);
+      peers &= inv ? bal : ~bal;
+    }
     uint32_t before = 0;
     if (dig[r] != 0xFFFFu) before = wcnt[w][dig[r]];
     rank[r] = before + __popc(peers & lanemask_lt());
