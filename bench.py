@@ -37,6 +37,10 @@ SCALE, WINDOW, LEAF = 20, 16_000_000, 64
 SWEEP = (100, 1000, 10_000, 100_000, 1_000_000)
 SWEEP_WARM, SWEEP_TIMED = 3, 10
 PR_ITERS, DAMPING = 20, 0.85
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one k_pr_scatter launch on
+# the default workload (R-MAT scale 20, 16M-edge window, 2^25 slots), from one ncu capture
+# of the kernel as it stands: 285,246,720 read + 3,048,448 written
+PR_SCATTER_TRAFFIC = 288_295_168
 METRIC = "edge updates/sec vs batch size (+HBM GB/s frac); p50/p99 update+query latency"
 L2_BYTES = 129 * 1024 * 1024
 
@@ -297,13 +301,14 @@ def run_gpu(a, stream, rank, world, dist):
     # dominant kernel by device time inside the timed region
     pr = prof["pr_scatter"]
     per_launch_ms = pr["ms"] / max(pr["count"], 1)
-    alg_pr = 8 * C + 20 * Vn  # stream every slot; read contrib, read+write the FP64 sum once per vertex
+    alg_pr = 8 * C + 20 * Vn  # stream every slot; read contrib, read+write the fixed-point sum once per vertex
     out["roofline"] = {
         "kernel": "k_pr_scatter (PageRank push pass over the gapped array)",
         "bound": "hbm", "achieved": alg_pr / (per_launch_ms * 1e-3) / 1e9, "peak": peak,
         "peak_kind": peak_kind, "unit": "GB/s",
         "frac": alg_pr / (per_launch_ms * 1e-3) / 1e9 / peak,
-        "traffic": None, "alg_bytes_per_launch": alg_pr, "launch_ms": per_launch_ms,
+        "traffic": PR_SCATTER_TRAFFIC if (a.scale, a.window) == (SCALE, WINDOW) else None,
+        "alg_bytes_per_launch": alg_pr, "launch_ms": per_launch_ms,
         "share_of_step": pr["ms"] / ms if ms else None,
     }
 
