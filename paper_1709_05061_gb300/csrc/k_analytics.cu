@@ -256,16 +256,25 @@ __global__ void __launch_bounds__(256) k_bfs_persist(Geo g, int32_t *depth, uint
     const bool scan = nfront >= scan_from;
     if (scan) {
       // one pass over the array: edges u -> v with depth[u] == level claim v
+      // four 16-byte loads in flight per thread, then the sources' depths together
       uint32_t found = 0;
-      for (uint64_t p = tid; p < npairs; p += nthreads) {
-        const ulonglong2 kk = __ldcs(s2 + p);
-        const uint64_t ks[2] = {kk.x, kk.y};
+      for (uint64_t p = tid; p < npairs; p += 4 * nthreads) {
+        uint64_t ks[8];
 #pragma unroll
-        for (int q = 0; q < 2; q++) {
-          const uint64_t k = ks[q];
-          if (k == kEmpty || is_guard(k)) continue;
-          if (__ldcg(depth + (k >> 32)) != level) continue;
-          const uint32_t v = (uint32_t)(k & 0xFFFFFFFFull);
+        for (int q = 0; q < 4; q++) {
+          const uint64_t pq = p + (uint64_t)q * nthreads;
+          const ulonglong2 kk = pq < npairs ? __ldcs(s2 + pq) : make_ulonglong2(kEmpty, kEmpty);
+          ks[2 * q] = kk.x;
+          ks[2 * q + 1] = kk.y;
+        }
+        int32_t du[8];
+#pragma unroll
+        for (int q = 0; q < 8; q++)
+          du[q] = (ks[q] != kEmpty && !is_guard(ks[q])) ? __ldcg(depth + (ks[q] >> 32)) : -2;
+#pragma unroll
+        for (int q = 0; q < 8; q++) {
+          if (du[q] != level) continue;
+          const uint32_t v = (uint32_t)(ks[q] & 0xFFFFFFFFull);
           if (__ldcg(depth + v) < 0 && atomicCAS(&depth[v], -1, level + 1) == -1) ++found;
         }
       }
