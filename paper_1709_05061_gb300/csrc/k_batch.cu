@@ -110,6 +110,8 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_pass(const uint64_t *__re
                                                             uint32_t shift, uint32_t dbits) {
   __shared__ uint32_t wcnt[kSortThreads / 32][256];
   __shared__ uint32_t gbase[256];
+  __shared__ uint32_t ltile[256];  // digit totals of the tile, then their exclusive prefix
+  __shared__ uint64_t skey[kSortThreads * kSortItems];
   __shared__ uint32_t s_tile;
   const uint32_t n = ctl->n;
   const uint32_t w = threadIdx.x >> 5, lane = lane_id();
@@ -160,29 +162,39 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_pass(const uint64_t *__re
       wcnt[q][d] = run;
       run += c;
     }
+    ltile[d] = run;
     uint32_t excl = lookback(status, 256, d, tile, run, ctl->epoch + pass, &ctl->err);
     gbase[d] = excl;
   }
+  for (uint32_t d = radix + threadIdx.x; d < 256; d += kSortThreads) ltile[d] = 0;
   // exclusive scan of the global histogram of this pass
   __shared__ uint32_t hs[256];
   for (uint32_t d = threadIdx.x; d < 256; d += kSortThreads) hs[d] = d < radix ? hist[pass * 256 + d] : 0u;
   __syncthreads();
-  if (threadIdx.x < 32) {
+  if (threadIdx.x < 64) {  // warp 0: global digit offsets; warp 1: digit offsets inside the tile
+    uint32_t *arr = threadIdx.x < 32 ? hs : ltile;
     uint32_t carry = 0;
     for (int c = 0; c < 256; c += 32) {
-      uint32_t v = hs[c + lane];
+      uint32_t v = arr[c + lane];
       uint32_t inc = warp_incl_scan(v);
-      hs[c + lane] = carry + inc - v;
+      arr[c + lane] = carry + inc - v;
       carry += __shfl_sync(0xFFFFFFFFu, inc, 31);
     }
   }
   __syncthreads();
+  // the tile sorted by digit in shared memory, then written out in digit runs
+  // (consecutive keys of one digit go to consecutive addresses)
 #pragma unroll
-  for (int r = 0; r < kSortItems; r++) {
-    if (dig[r] == 0xFFFFu) continue;
-    uint32_t d = dig[r];
-    uint32_t pos = hs[d] + gbase[d] + wcnt[w][d] + rank[r];
-    if (pos < n) dst[pos] = key[r];  // always true unless a look-back gave up
+  for (int r = 0; r < kSortItems; r++)
+    if (dig[r] != 0xFFFFu) skey[ltile[dig[r]] + wcnt[w][dig[r]] + rank[r]] = key[r];
+  __syncthreads();
+  const uint64_t t0 = (uint64_t)tile * (kSortThreads * kSortItems);
+  const uint32_t cnt = t0 >= n ? 0u : (n - t0 < kSortThreads * kSortItems ? (uint32_t)(n - t0) : kSortThreads * kSortItems);
+  for (uint32_t i = threadIdx.x; i < cnt; i += kSortThreads) {
+    const uint64_t k = skey[i];
+    const uint32_t d = (uint32_t)(((k & ~kTagBit) >> shift) & mask);
+    const uint32_t pos = hs[d] + gbase[d] + (i - ltile[d]);
+    if (pos < n) dst[pos] = k;  // always true unless a look-back gave up
   }
 }
 
