@@ -80,7 +80,7 @@ struct Ctl {
   uint64_t merges[kMaxLv];
   uint64_t gen_count;  // general-purpose counter (exports)
   uint32_t resized;    // this call grew the array on the device (into the spare)
-  uint32_t pad_;
+  uint32_t nvlong;     // runs longer than kLongRun, left to the chunked level-0 path
 };
 
 __device__ __forceinline__ bool is_guard(uint64_t k) {

@@ -68,6 +68,9 @@ struct Work {
 uint32_t sort_tiles(uint64_t n);
 uint32_t comp_tiles(uint64_t n);
 // k_init_batch + k_prep (take the batch's own pointers and sizes)
+// runs longer than this (bulk loads) take the chunked level-0 path: many warps
+// share one run's presence filter and deletes, one warp per run finishes it
+constexpr uint32_t kLongRun = 1024;
 // batches of at most kSmallBatch keys: validation .. run heads in one block
 constexpr uint32_t kSmallBatch = 4096;
 bool small_front(uint64_t n);

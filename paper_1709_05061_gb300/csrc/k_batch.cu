@@ -57,6 +57,7 @@ __global__ void k_init_batch(Ctl *ctl, uint32_t *hist, uint32_t nhist, uint32_t 
     ctl->nesc = 0;
     ctl->nfail = 0;
     ctl->nlong = 0;
+    ctl->nvlong = 0;
     ctl->resized = 0;
     ctl->m = ctl->nruns = ctl->npend = ctl->neruns = ctl->nsegs = ctl->nleafw = 0;
     for (int i = 0; i < 16; i++) ctl->ticket[i] = 0;
@@ -338,7 +339,7 @@ __global__ void __launch_bounds__(1024) k_small_front(PrepArgs a, const uint64_t
     ctl->err = 0;
     ctl->n = n;
     ctl->epoch += kSlotsPerBatch;
-    ctl->nesc = ctl->nfail = ctl->nlong = ctl->resized = 0;
+    ctl->nesc = ctl->nfail = ctl->nlong = ctl->nvlong = ctl->resized = 0;
     ctl->m = ctl->nruns = ctl->npend = ctl->neruns = ctl->nsegs = ctl->nleafw = 0;
     for (int i = 0; i < 16; i++) ctl->ticket[i] = 0;
     ctl->n_inserted = ctl->n_deleted = 0;

@@ -65,6 +65,14 @@ __global__ void k_leaf_pass(Geo g, Ctl *ctl, Work w, uint32_t per_warp, int rest
   for (uint32_t r = blockIdx.x * wpb + (threadIdx.x >> 5); r < nruns; r += gridDim.x * wpb) {
     const uint32_t rs = w.run_start[r], re = w.run_start[r + 1];
     if (rest_only && re - rs <= 32) continue;  // done by the 64-slot fast path
+    if (re - rs > kLongRun) {  // done by the chunked path: reset its accumulators
+      if (lane == 0) {
+        w.rdelta[r] = 0;
+        w.rdel[r] = 0;
+        atomicAdd(&ctl->nvlong, 1u);
+      }
+      continue;
+    }
     const uint32_t j = w.rleaf[r];
     uint64_t *leaf = g.slots + (uint64_t)j * L;
     // the leaf's valid keys, compacted, with their slot offsets
@@ -171,6 +179,148 @@ __global__ void k_leaf_pass(Geo g, Ctl *ctl, Work w, uint32_t per_warp, int rest
     if (acc_ins) atomicAdd((unsigned long long *)&ctl->n_inserted, (unsigned long long)acc_ins);
     if (acc_del) atomicAdd((unsigned long long *)&ctl->n_deleted, (unsigned long long)acc_del);
     if (acc_ins != acc_del)  // logical key count (pending inserts included), two's complement
+      atomicAdd((unsigned long long *)&ctl->total, (unsigned long long)(acc_ins - acc_del));
+    if (acc_m0) atomicAdd(&ctl->n_merged0, acc_m0);
+    if (acc_esc) atomicAdd(&ctl->nesc, acc_esc);
+  }
+}
+
+// ---- level 0 for runs longer than kLongRun (bulk loads) -----------------------------------------
+// Phase A, a warp per 32 consecutive keys: the presence filter against the
+// leaf's valid keys, deletes made EMPTY in place (distinct slots), surviving
+// inserts marked pending and counted per run; the first L surviving inserts of
+// a run are recorded (a run can only settle at level 0 with fewer than L).
+// Phase B, a warp per long run: with the run's counts, the level-0 test, and the
+// merge of the recorded inserts when it passes.
+__device__ __forceinline__ uint32_t run_of(const uint32_t *run_start, uint32_t nruns, uint32_t e) {
+  uint32_t lo = 0, hi = nruns;  // last run starting at or before e
+  while (hi - lo > 1) {
+    const uint32_t mid = (lo + hi) >> 1;
+    if (run_start[mid] <= e) lo = mid; else hi = mid;
+  }
+  return lo;
+}
+
+// the leaf's valid keys compacted into vkeys (with their slot offsets); returns how many
+__device__ __forceinline__ uint32_t load_leaf(const uint64_t *leaf, uint32_t L, uint64_t *vkeys, uint16_t *vpos) {
+  const uint32_t lane = lane_id();
+  uint32_t nv = 0;
+  for (uint32_t b = 0; b < L; b += 32) {
+    const uint32_t o = b + lane;
+    const uint64_t k = o < L ? leaf[o] : kEmpty;
+    const bool v = k != kEmpty;
+    const uint32_t bal = __ballot_sync(0xFFFFFFFFu, v);
+    if (v) {
+      vkeys[nv + __popc(bal & lanemask_lt())] = k;
+      if (vpos) vpos[nv + __popc(bal & lanemask_lt())] = (uint16_t)o;
+    }
+    nv += __popc(bal);
+  }
+  __syncwarp();
+  return nv;
+}
+
+__global__ void k_long_a(Geo g, Ctl *ctl, Work w, uint32_t per_warp) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  if (ctl->err || ctl->nvlong == 0) return;
+  const uint32_t L = g.L, lane = lane_id(), wpb = blockDim.x >> 5;
+  WarpBufs B = warp_bufs(smem, per_warp, L);
+  const uint32_t m = ctl->m, nruns = ctl->nruns;
+  for (uint32_t c = (blockIdx.x * wpb + (threadIdx.x >> 5)) * 32; c < m; c += gridDim.x * wpb * 32) {
+    // the keys [c, c+32) span at most two runs: the run of the first key, then the next
+    const uint32_t r0 = run_of(w.run_start, nruns, c);
+    for (uint32_t r = r0; r < nruns && w.run_start[r] < c + 32 && w.run_start[r] < m; r++) {
+      const uint32_t rs = w.run_start[r], re = w.run_start[r + 1];
+      if (re - rs <= kLongRun) continue;
+      const uint32_t j = w.rleaf[r];
+      uint64_t *leaf = g.slots + (uint64_t)j * L;
+      const uint32_t nv = load_leaf(leaf, L, B.a, B.pos);
+      const uint32_t e = c + lane;
+      const bool act = e >= rs && e < re && e < m;
+      const uint64_t key = act ? w.ukey[e] : 0ull;
+      const uint32_t tag = act ? (uint32_t)w.utag[e] : 0u;
+      const uint32_t idx = act ? lower_bound_dev(B.a, nv, key) : 0u;
+      const bool found = act && idx < nv && B.a[idx] == key;
+      const bool dl = act && tag && found, sv = act && !tag && !found;
+      if (dl) leaf[B.pos[idx]] = kEmpty;
+      if (act) w.eflag[e] = dl ? 1 : (sv ? 2 : 0);
+      const uint32_t svb = __ballot_sync(0xFFFFFFFFu, sv), dlb = __ballot_sync(0xFFFFFFFFu, dl);
+      uint32_t base = 0;
+      if (lane == 0 && svb) base = (uint32_t)atomicAdd(&w.rdelta[r], (int32_t)__popc(svb));
+      if (lane == 0 && dlb) atomicAdd(&w.rdel[r], __popc(dlb));
+      base = __shfl_sync(0xFFFFFFFFu, base, 0);
+      const uint32_t slot = base + __popc(svb & lanemask_lt());
+      if (sv && slot < L) {  // record (a level-0 merge takes fewer than L; the run has more than L keys)
+        w.pkey[rs + slot] = key;
+        w.pleaf[rs + slot] = e;
+      }
+      if (!g.raw) {
+        degree_delta(g.deg, sv && !is_guard(key), key, 1);
+        degree_delta(g.deg, dl, key, -1);
+      }
+      __syncwarp();
+    }
+  }
+}
+
+__global__ void k_long_b(Geo g, Ctl *ctl, Work w, uint32_t per_warp) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  if (ctl->err || ctl->nvlong == 0) return;
+  const uint32_t L = g.L, lane = lane_id(), wpb = blockDim.x >> 5;
+  WarpBufs B = warp_bufs(smem, per_warp, L);
+  uint64_t *vkeys = B.a, *ins = B.b, *out = B.out;
+  const uint32_t nruns = ctl->nruns;
+  uint64_t acc_ins = 0, acc_del = 0;
+  uint32_t acc_m0 = 0, acc_esc = 0;
+  for (uint32_t r = blockIdx.x * wpb + (threadIdx.x >> 5); r < nruns; r += gridDim.x * wpb) {
+    const uint32_t rs = w.run_start[r], re = w.run_start[r + 1];
+    if (re - rs <= kLongRun) continue;
+    const uint32_t j = w.rleaf[r];
+    uint64_t *leaf = g.slots + (uint64_t)j * L;
+    const uint32_t nins = (uint32_t)w.rdelta[r], ndel = w.rdel[r];
+    const uint32_t nv = load_leaf(leaf, L, vkeys, nullptr);  // deletes already EMPTY
+    const bool fits = nins < L && leaf_fits(g, (uint64_t)nv + nins, nins);
+    if (fits) {
+      // the recorded inserts, sorted by rank (distinct keys), merged with the kept keys
+      for (uint32_t t = lane; t < nins; t += 32) {
+        const uint64_t k = w.pkey[rs + t];
+        uint32_t rk = 0;
+        for (uint32_t u = 0; u < nins; u++) rk += w.pkey[rs + u] < k;
+        ins[rk] = k;
+        w.eflag[w.pleaf[rs + t]] = 1;
+      }
+      __syncwarp();
+      for (uint32_t a = lane; a < nv; a += 32) out[a + lower_bound_dev(ins, nins, vkeys[a])] = vkeys[a];
+      for (uint32_t b = lane; b < nins; b += 32) out[b + lower_bound_dev(vkeys, nv, ins[b])] = ins[b];
+      __syncwarp();
+      const uint32_t n = nv + nins;
+      for (uint32_t o = lane; o < L; o += 32) {
+        const uint64_t k = o < n ? out[o] : kEmpty;
+        leaf[o] = k;
+        if (!g.raw && o < n && is_guard(k)) g.row_end[k >> 32] = (uint32_t)((uint64_t)j * L + o);
+      }
+      if (lane == 0) {
+        g.F[j] = n ? out[0] : kEmpty;
+        g.cnt[j] = n;
+      }
+    } else if (lane == 0) {
+      g.F[j] = nv ? vkeys[0] : kEmpty;
+      g.cnt[j] = nv;
+    }
+    if (lane == 0) {
+      w.rdelta[r] = (int32_t)nins - (int32_t)ndel;
+      w.rinfo[r] = fits ? 1 : ((nins || g.dual) ? 2 : 0);
+      acc_ins += nins;
+      acc_del += ndel;
+      acc_m0 += fits;
+      acc_esc += !fits && (nins || g.dual);
+    }
+    __syncwarp();
+  }
+  if (lane == 0) {
+    if (acc_ins) atomicAdd((unsigned long long *)&ctl->n_inserted, (unsigned long long)acc_ins);
+    if (acc_del) atomicAdd((unsigned long long *)&ctl->n_deleted, (unsigned long long)acc_del);
+    if (acc_ins != acc_del)
       atomicAdd((unsigned long long *)&ctl->total, (unsigned long long)(acc_ins - acc_del));
     if (acc_m0) atomicAdd(&ctl->n_merged0, acc_m0);
     if (acc_esc) atomicAdd(&ctl->nesc, acc_esc);
@@ -708,6 +858,8 @@ void allow_big_smem() {
   if (done) return;
   cudaFuncSetAttribute(k_leaf_pass, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
   cudaFuncSetAttribute(k_seg_write, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  cudaFuncSetAttribute(k_long_a, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  cudaFuncSetAttribute(k_long_b, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
   done = true;
 }
 
@@ -721,6 +873,12 @@ void launch_leaf_pass(const Geo &g, Ctl *ctl, const Work &w, uint32_t n, cudaStr
   }
   note_launch();
   k_leaf_pass<<<blocks_for(n, wpb, 152 * 16), wpb * 32, wpb * pw, s>>>(g, ctl, w, pw, fast);
+  if (n > kLongRun) {  // only a batch this large can hold a run this long
+    note_launch();
+    k_long_a<<<blocks_for((n + 31) / 32, wpb, 152 * 16), wpb * 32, wpb * pw, s>>>(g, ctl, w, pw);
+    note_launch();
+    k_long_b<<<blocks_for(n / kLongRun + 1, wpb, 152 * 16), wpb * 32, wpb * pw, s>>>(g, ctl, w, pw);
+  }
 }
 
 void launch_tree_rebuild(const Geo &g, Ctl *ctl, const Work &w, uint32_t n, cudaStream_t s) {
