@@ -1046,7 +1046,7 @@ int gpma_pagerank(gpma_t h, uint32_t iters, float damping, float *d_rank, void *
       launch_pr_scatter(h->geo, h->cfx, h->y, s);
     }
     launch_pr_apply(h->geo, damping, d_rank, h->y, h->cfx, h->dsum + it, h->dsum + it + 1, h->pr_partials,
-                    h->pr_counter, s);
+                    h->pr_counter, it + 1 == iters, s);
   }
   all.end();
   return cuda_ok(h);

@@ -127,7 +127,7 @@ void launch_pr_setup(const Geo &g, uint32_t iters, float *rank, uint64_t *y, uin
                      uint64_t *partials, unsigned *counter, cudaStream_t s);
 void launch_pr_scatter(const Geo &g, const uint64_t *cfx, uint64_t *y, cudaStream_t s);
 void launch_pr_apply(const Geo &g, float damping, float *rank, uint64_t *y, uint64_t *cfx,
-                     const uint64_t *dsum_in, uint64_t *dsum_out, uint64_t *partials, unsigned *counter,
+                     const uint64_t *dsum_in, uint64_t *dsum_out, uint64_t *partials, unsigned *counter, bool last,
                      cudaStream_t s);
 // BFS in one cooperative launch; counter >= 16 u32, h_counter pinned; waits for the
 // stream; returns 0, -1 on a CUDA error, -2 when a bounded barrier wait gave up

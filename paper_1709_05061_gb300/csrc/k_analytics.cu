@@ -128,7 +128,7 @@ __global__ void __launch_bounds__(256, 8) k_pr_scatter(const ulonglong2 *__restr
 
 __global__ void k_pr_apply(uint32_t V, float damping, const uint32_t *__restrict__ deg, uint64_t *__restrict__ y,
                            float *__restrict__ x, uint64_t *__restrict__ cfx, const uint64_t *dsum_in,
-                           uint64_t *dsum_out, uint64_t *partials, unsigned *counter) {
+                           uint64_t *dsum_out, uint64_t *partials, unsigned *counter, int write_x) {
   // x' = (1 - d)/V + d * (y + dangling / V), all in FP32 (the sums themselves are exact)
   const float base = __fdiv_rn(1.0f - damping, (float)V);
   const float dn = __fdiv_rn(fx_to_float(*dsum_in), (float)V);
@@ -137,7 +137,7 @@ __global__ void k_pr_apply(uint32_t V, float damping, const uint32_t *__restrict
   for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < V; v += stride) {
     const uint32_t d = deg[v];
     const float xf = __fmaf_rn(damping, fx_to_float(y[v]) + dn, base);
-    x[v] = xf;
+    if (write_x) x[v] = xf;  // the ranks are read only after the last iteration
     y[v] = 0;
     cfx[v] = d ? to_fx(__fdiv_rn(xf, (float)d)) : 0ull;
     if (!d) dang += to_fx(xf);
@@ -163,10 +163,10 @@ void launch_pr_scatter(const Geo &g, const uint64_t *cfx, uint64_t *y, cudaStrea
 
 void launch_pr_apply(const Geo &g, float damping, float *rank, uint64_t *y, uint64_t *cfx,
                      const uint64_t *dsum_in, uint64_t *dsum_out, uint64_t *partials, unsigned *counter,
-                     cudaStream_t s) {
+                     bool last, cudaStream_t s) {
   note_launch();
   k_pr_apply<<<nb(g.V, 256, kVecBlocks), 256, 0, s>>>(g.V, damping, g.deg, y, rank, cfx, dsum_in, dsum_out,
-                                                         partials, counter);
+                                                         partials, counter, last ? 1 : 0);
 }
 
 // ---- BFS ----------------------------------------------------------------------------------------
