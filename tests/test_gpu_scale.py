@@ -61,3 +61,35 @@ def test_rmat20_window_full_size():
     rel = np.max(np.abs(pr - ref) / ref)
     assert rel <= 1e-5, rel
     assert np.array_equal(g.row_end().cpu().numpy().view(np.uint32), o.row_end())
+
+
+def test_chung_lu_learned_full_size():
+    """The learned-search workload at full size: Chung-Lu, 1.6M vertices, 30M edges
+    (degree exponent 2.1, seed 7), batches of 1e5 (70% new edges, 30% random live
+    edges).  The learned and the plain search give the oracle's array slot for slot."""
+    V, E0, B = 1_600_000, 30_000_000, 100_000
+    n_ins, n_del = 70_000, 30_000
+    stream = W.chung_lu_stream(V, E0 + 4 * n_ins, gamma=2.1, seed=7)
+    rng = np.random.default_rng(7)
+    live = stream[:E0].copy()
+    learned, plain = gp.Graph(V, leaf_size=64), gp.Graph(V, leaf_size=64, plain_search=True)
+    o = oracle.OraclePMA(V, L=64)
+    for g in (learned, plain):
+        g.update(dev(stream[:E0]), None)
+    o.update(stream[:E0])
+    for i in range(4):
+        ins = stream[E0 + i * n_ins: E0 + (i + 1) * n_ins]
+        pick = rng.choice(live.size, n_del, replace=False)
+        dels = live[pick]
+        keep = np.ones(live.size, bool)
+        keep[pick] = False
+        live = np.concatenate([live[keep], ins])
+        for g in (learned, plain):
+            g.update(dev(ins), dev(dels))
+        o.update(ins, dels)
+    lo = o.layout()
+    for g in (learned, plain):
+        g.status()
+        lg = g.layout().cpu().numpy().view(np.uint64)
+        assert lg.size == lo.size and np.count_nonzero(lg != lo) == 0
+        assert g.check() == 0

@@ -74,3 +74,42 @@ def test_served_queries_equal_alone(realtime, rate, coalesce):
             o.update(r.ins, r.dels)
     assert np.array_equal(served, np.sort(o.export_sorted()))
     assert g.check() == 0
+
+
+def test_served_full_size_properties():
+    """The served configuration at full size (R-MAT scale 24, 2^28 device-drawn
+    samples): every query answered in the mix equals the same query on a second
+    handle fed the same updates one request at a time, and the final queries (after
+    the last update) satisfy what holds at any size -- BFS depths grow by at most
+    one along every sampled edge, CC labels agree along sampled edges and never
+    exceed the vertex id, PageRank sums to one."""
+    scale = 24
+    st = W.rmat_stream_device(scale, 1 << 28, seed=24)
+    window = st.numel() - 5_000_000
+    V = 1 << scale
+    host_stream = st.cpu().numpy().view(np.uint64)
+    win = W.SlidingWindow(host_stream, window)
+    reqs = S.make_requests(24, V, win, rate=1.0, seed=12, upd_lo=100, upd_hi=100_000, pr_iters=10)
+    t_end = reqs[-1].arrival
+    final = [S.Request(len(reqs) + i, kind, t_end + 1.0 + i, src=int(host_stream[0] >> np.uint64(32)), iters=10)
+             for i, kind in enumerate((S.BFS, S.CC, S.PAGERANK))]
+    reqs += final
+    g = gp.Graph(V, leaf_size=64)
+    g.update(st[:window])
+    del st
+    srv = S.Server(g, max_batch_keys=1 << 20, result_slots=2, max_inflight=2)
+    srv.run(reqs, realtime=False)
+    alone = replay_alone(V, host_stream[:window], reqs)
+    edges = g.export_sorted().cpu().numpy().view(np.uint64)
+    sample = edges[np.random.default_rng(3).integers(0, edges.size, 200_000)]
+    su = (sample >> np.uint64(32)).astype(np.int64)
+    sv = (sample & np.uint64(0xFFFFFFFF)).astype(np.int64)
+    bfs, cc, pr = (r.result for r in final)
+    d = bfs.astype(np.int64)
+    ok = d[su] >= 0
+    assert d[final[0].src] == 0
+    assert np.all(d[sv][ok] >= 0) and np.all(d[sv][ok] <= d[su][ok] + 1)
+    lab = cc.view(np.uint32).astype(np.int64)
+    assert np.all(lab[su] == lab[sv]) and np.all(lab <= np.arange(V))
+    assert abs(float(pr.view(np.float32).astype(np.float64).sum()) - 1.0) < 1e-3
+    assert g.check() == 0 and alone.check() == 0
