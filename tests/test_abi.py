@@ -23,7 +23,7 @@ def declared_functions():
     return sorted(set(re.findall(r"\b(gpma_[a-z_]+)\s*\(", text)))
 
 
-def test_header_declares_the_survey_calls():
+def test_header_declares_the_boundary_calls():
     names = declared_functions()
     for n in ["gpma_create", "gpma_destroy", "gpma_update_batch", "gpma_bfs", "gpma_cc", "gpma_pagerank",
               "gpma_export_sorted", "gpma_export_csr", "gpma_export_layout", "gpma_import_layout",
