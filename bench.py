@@ -518,14 +518,16 @@ def serve_study(a):
     del st
     torch.cuda.empty_cache()
     win = W.SlidingWindow(host_stream, window)
-    srv = S.Server(g, max_batch_keys=1 << 20, result_slots=4, max_inflight=2, keep_results=False)
+    budget = 2 << 30  # device memory for staging and results, split by Server.with_budget
+    srv = S.Server.with_budget(g, budget, max_inflight=2, keep_results=False)
     n = a.serve_requests
     # warm-up (graph capture for every batch size bucket, first analytics calls)
     srv.run(S.make_requests(60, V, win, rate=1.0, seed=100), realtime=False)
     out = {"workload": f"R-MAT scale 24 (.57/.19/.19/.05, 2^28 samples, seed 24, device-generated), "
                        f"{window} edges resident, capacity {g.capacity} slots; requests: Poisson, updates "
                        f"log-uniform 1e2..1e5 (50/50) : queries (BFS / CC / PageRank-10) = 4 : 1",
-           "generate_s": gen_s, "bulk_load_s": load_s, "requests_per_run": n}
+           "generate_s": gen_s, "bulk_load_s": load_s, "requests_per_run": n, "hbm_budget_bytes": budget,
+           "max_batch_keys": srv.max_batch_keys, "result_slots": len(srv.d_res)}
     cap = srv.run(S.make_requests(n, V, win, rate=1.0, seed=101), realtime=False)
     out["closed_loop"] = cap
     # the plain path on the same kind of stream: one request at a time, nothing

@@ -13,7 +13,8 @@ queries).  The server admits them in arrival order:
   stream alone;
 * the HBM budget bounds what is in flight: update staging buffers hold at most
   ``max_batch_keys`` keys and query results use a fixed pool of
-  ``result_slots`` device buffers (a query waits for a free slot).
+  ``result_slots`` device buffers (a query waits for a free slot);
+  ``Server.with_budget`` derives both from a byte budget.
 
 Two CUDA streams overlap transfers with compute: host-to-device copies of
 update keys and device-to-host copies of query results run on the copy stream,
@@ -135,6 +136,22 @@ class Server:
         self.inflight = []                      # (event, op) in completion order
         self.n_updates = 0
         self.n_batches = 0
+
+    @staticmethod
+    def budget_split(hbm_budget_bytes: int, n_vertices: int, max_slots: int = 8, max_keys: int = 1 << 22):
+        """(max_batch_keys, result_slots) that fit ``hbm_budget_bytes`` of device memory:
+        half of it for the two update staging buffers (8 bytes per key each), half for
+        query result buffers (4 bytes per vertex each); at least one of each."""
+        half = max(int(hbm_budget_bytes) // 2, 1)
+        keys = max(min(half // 16, max_keys), 1024)
+        slots = max(min(half // max(4 * n_vertices, 1), max_slots), 1)
+        return keys, slots
+
+    @classmethod
+    def with_budget(cls, graph, hbm_budget_bytes: int, **kw):
+        """A server whose staging and result buffers fit the given device-memory budget."""
+        keys, slots = cls.budget_split(hbm_budget_bytes, graph.n_vertices)
+        return cls(graph, max_batch_keys=keys, result_slots=slots, **kw)
 
     # ---- completion bookkeeping --------------------------------------------------------------
     def _poll(self, t0, block=False):

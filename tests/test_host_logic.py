@@ -102,3 +102,15 @@ def test_make_requests_mix_and_arrivals():
             live = (live - set(r.dels.tolist())) | set(r.ins.tolist())
         else:
             assert 0 <= r.src < 500
+
+
+def test_serve_budget_split():
+    from paper_1709_05061_gb300 import serve as S
+    # 1 GiB: 512 MiB for keys (two buffers of 8-byte keys, capped) and 512 MiB of 64 MiB results (capped at 8)
+    keys, slots = S.Server.budget_split(1 << 30, 1 << 24)
+    assert keys == 1 << 22 and slots == 8
+    keys, slots = S.Server.budget_split(100 << 20, 1 << 24)  # 50 MiB each side
+    assert keys == (50 << 20) // 16 and slots == 1
+    assert 2 * 8 * keys + 4 * (1 << 24) * slots <= (100 << 20) + 4 * (1 << 24)  # at least one slot always
+    keys, slots = S.Server.budget_split(0, 10)
+    assert keys == 1024 and slots == 1
