@@ -81,7 +81,10 @@ typedef struct {
                               inserts of stored keys, deletes of absent keys */
   uint32_t levels_climbed; /* highest level at which a segment merged; old h + 1 on a resize */
   uint32_t resized;        /* 1 if the capacity grew, 2 if it shrank (GPMA_DUAL_DELETE) */
-  uint64_t alg_bytes;      /* algorithmic bytes of the batch (see the design notes) */
+  uint64_t alg_bytes;      /* algorithmic bytes of the batch: 8 per raw key, 8L per touched leaf
+                              (read), 8L per covered leaf (write), 8L per covered leaf not
+                              touched (read), 8 per EMPTY written outside covered leaves; on a
+                              resize 8 per raw key + 8L per touched leaf + 8 (C_old + C_new) */
   uint64_t touched_leaves; /* distinct leaves holding an update after cancellation */
   uint64_t covered_leaves; /* leaves rewritten by merges (0 on a resize) */
   uint64_t merges[GPMA_MAX_LEVELS]; /* segments merged at each level, Sec. 5.2 level order */
@@ -98,7 +101,8 @@ int gpma_create(uint32_t n_vertices, const gpma_params *params, const gpma_alloc
 int gpma_destroy(gpma_t h);
 
 /* Apply one batch of edge insertions and deletions (Algorithm "GPMA+
- * Segment-Oriented Insertion", Sec. 5.2, with lazy deletion, Sec. 6.1).
+ * Segment-Oriented Insertion", Sec. 5.2, with lazy deletion, Sec. 6.1, or with
+ * the lower bounds kept when the handle was created with GPMA_DUAL_DELETE).
  * d_ins[n_ins], d_del[n_del]: device arrays of keys (src << 32 | dst), in any
  * order, duplicates allowed.  Semantics: each list is made unique; a key in both
  * lists is dropped from both; inserts of stored keys and deletes of absent keys
