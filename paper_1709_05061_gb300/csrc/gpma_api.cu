@@ -829,7 +829,7 @@ int update(gpma *h, const uint64_t *ins, uint64_t n_ins, const uint64_t *del, ui
 int ensure_analytics(gpma *h, uint32_t iters, cudaStream_t s) {
   if (!h->y) {
     if (!dalloc(h, &h->y, h->V, s) || !dalloc(h, &h->cfx, h->V, s) ||
-        !dalloc(h, &h->q0, h->V, s) || !dalloc(h, &h->q1, h->V, s) || !dalloc(h, &h->q2, 2ull * h->V, s) || !dalloc(h, &h->counter, 16, s) ||
+        !dalloc(h, &h->q0, h->V, s) || !dalloc(h, &h->q1, h->V, s) || !dalloc(h, &h->q2, 2ull * h->V, s) || !dalloc(h, &h->counter, 32, s) ||
         !dalloc(h, &h->pr_partials, 152 * 16, s) || !dalloc(h, &h->pr_counter, 4, s))
       return GPMA_ENOMEM;
   }

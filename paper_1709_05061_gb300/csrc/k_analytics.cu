@@ -179,7 +179,8 @@ void launch_pr_apply(const Geo &g, float damping, float *rank, uint64_t *y, uint
 // All levels run inside one cooperative launch (every block resident), separated
 // by a grid barrier whose waits are bounded: a barrier that gives up sets
 // kErrTimeout and every block leaves.  Counters: cnt[0..2] rotate per level
-// (frontier sizes), cnt[3] is the queue-rebuild counter, cnt[4] the level count.
+// (frontier sizes), cnt[3..4] are the queue-rebuild counters of even and odd
+// levels, cnt[5] the level count.
 __device__ __forceinline__ bool grid_barrier(unsigned *bar, uint32_t *err) {
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -233,8 +234,11 @@ __device__ __forceinline__ void bfs_gather(const Geo &g, int32_t *depth, uint64_
 
 constexpr uint64_t kBigRow = 1024, kRowChunk = 256;
 
-// cnt[0..2]: frontier sizes (rotating), cnt[3]: queue rebuild, cnt[4]: levels,
-// cnt[6..7]: one u64 = (long rows listed << 32) | chunks of those rows; `big` holds
+// cnt[0..2]: frontier sizes (rotating), cnt[3..4]: queue rebuild (by level parity),
+// cnt[5]: levels, cnt[6..7] / cnt[8..9]: one u64 per level parity = (long rows
+// listed << 32) | chunks of those rows.  A level zeroes the next level's counters
+// when it starts (their last users finished before this level's first barrier),
+// so a level needs no barrier after its last one.  `big` holds
 // (row, first chunk) pairs
 __global__ void __launch_bounds__(256) k_bfs_persist(Geo g, int32_t *depth, uint32_t *qa, uint32_t *qb,
                                                      uint32_t *big, uint32_t *cnt, unsigned *bar, uint32_t *err,
@@ -252,7 +256,13 @@ __global__ void __launch_bounds__(256) k_bfs_persist(Geo g, int32_t *depth, uint
   bool have_queue = true;
   while (nfront) {
     uint32_t *cnext = cnt + (level + 1) % 3;
-    if (tid == 0) cnt[(level + 2) % 3] = 0;
+    const uint32_t par = (uint32_t)level & 1u;
+    if (tid == 0) {
+      cnt[(level + 2) % 3] = 0;
+      cnt[3 + (par ^ 1u)] = 0;      // next level's queue-rebuild counter
+      cnt[6 + 2 * (par ^ 1u)] = 0;  // next level's long-row list
+      cnt[7 + 2 * (par ^ 1u)] = 0;
+    }
     const bool scan = nfront >= scan_from;
     if (scan) {
       // one pass over the array: edges u -> v with depth[u] == level claim v
@@ -288,7 +298,7 @@ __global__ void __launch_bounds__(256) k_bfs_persist(Geo g, int32_t *depth, uint
           const uint32_t bal = __ballot_sync(0xFFFFFFFFu, hit);
           if (!bal) continue;
           uint32_t base = 0;
-          if (lane == (uint32_t)(__ffs(bal) - 1)) base = atomicAdd(cnt + 3, (uint32_t)__popc(bal));
+          if (lane == (uint32_t)(__ffs(bal) - 1)) base = atomicAdd(cnt + 3 + par, (uint32_t)__popc(bal));
           base = __shfl_sync(0xFFFFFFFFu, base, __ffs(bal) - 1);
           if (hit) qin[base + __popc(bal & lanemask_lt())] = v;
         }
@@ -297,7 +307,7 @@ __global__ void __launch_bounds__(256) k_bfs_persist(Geo g, int32_t *depth, uint
       // top-down: a warp per short row; long rows are listed with the running
       // total of their 256-slot chunks (one packed 64-bit atomic keeps the list
       // order and the chunk bases consistent), then all warps share the chunks
-      unsigned long long *bigctr = reinterpret_cast<unsigned long long *>(cnt + 6);
+      unsigned long long *bigctr = reinterpret_cast<unsigned long long *>(cnt + 6 + 2 * par);
       for (uint32_t i = warp; i < nfront; i += nwarps) {
         const uint32_t u = __ldcg(qin + i);
         const uint64_t beg = u ? (uint64_t)__ldg(g.row_end + u - 1) + 1 : 0, end = __ldg(g.row_end + u);
@@ -335,29 +345,16 @@ __global__ void __launch_bounds__(256) k_bfs_persist(Geo g, int32_t *depth, uint
       qin = qout;
       qout = t;
     }
-    if (tid == 0) {
-      cnt[3] = 0;
-      cnt[6] = 0;  // long-row list (packed with cnt[7])
-      cnt[7] = 0;
-    }
     ++level;
-    // every block has read nfront and the queue pointers before anyone reuses them
-    if (!grid_barrier(bar, err)) return;
   }
-  if (tid == 0) cnt[4] = (uint32_t)level;
+  if (tid == 0) cnt[5] = (uint32_t)level;
 }
 
 __global__ void k_bfs_setup(int32_t *depth, uint32_t src, uint32_t *q0, uint32_t *cnt, unsigned *bar) {
   depth[src] = 0;
   q0[0] = src;
-  cnt[0] = 0;  // the level-0 frontier (src) is implicit; level L appends to cnt[(L + 1) % 3]
-  cnt[1] = 0;
-  cnt[2] = 0;
-  cnt[3] = 0;
-  cnt[4] = 0;
-  cnt[5] = 0;
-  cnt[6] = 0;
-  cnt[7] = 0;
+  // the level-0 frontier (src) is implicit; level L appends to cnt[(L + 1) % 3]
+  for (int i = 0; i < 16; i++) cnt[i] = 0;
   bar[0] = 0;
   bar[1] = 0;
 }
@@ -378,10 +375,10 @@ int run_bfs(const Geo &g, uint32_t src, int32_t *depth, uint32_t *q0, uint32_t *
     grid = sms * (per_sm > 4 ? 4 : per_sm);
     if (grid < 1) grid = 1;
   }
-  // counter layout: cnt[0..7], barrier words, error word
+  // counter layout: cnt[0..15], barrier words, error word
   uint32_t *cnt = counter;
-  unsigned *bar = counter + 8;
-  uint32_t *err = counter + 12;
+  unsigned *bar = counter + 16;
+  uint32_t *err = counter + 20;
   cudaMemsetAsync(depth, 0xFF, sizeof(int32_t) * g.V, s);
   cudaMemsetAsync(err, 0, sizeof(uint32_t), s);
   note_launch();
