@@ -693,6 +693,7 @@ int update(gpma *h, const uint64_t *ins, uint64_t n_ins, const uint64_t *del, ui
   f.uleaf = h->w.uleaf;
   f.run_start = h->w.run_start;
   f.run_leaf = h->w.rleaf;
+  f.lfull = h->w.pleaf;  // free until the escalation compacts pending inserts
   const uint32_t n32 = (uint32_t)n;
   Phase whole(h->prof, GPMA_PROF_UPDATE, s);
   // level-0 merges move pivots only inside their leaves and the search widens

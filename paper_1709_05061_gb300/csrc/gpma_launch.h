@@ -38,6 +38,7 @@ struct FrontArgs {
   uint32_t *uleaf;
   uint32_t *run_start;
   uint32_t *run_leaf;
+  uint32_t *lfull;        // leaf of every sorted word (kNoLeaf if dropped), before compaction
 };
 
 // per-batch work arrays of the update kernels

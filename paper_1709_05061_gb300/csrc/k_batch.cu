@@ -4,10 +4,11 @@
 //   k_prep        validate keys, compress (src, dst, insert/delete tag) into one
 //                 sortable word, build the radix histograms of every pass
 //   k_sort_pass   one stable LSD radix pass (single pass per digit with look-back)
-//   k_keep        unique + insert/delete cancellation on the sorted words
-//   k_search      leaf search of every surviving key, one per thread (learned
-//                 model when trained, else binary search; both give the same leaf)
-//   k_runs        heads of the runs of equal leaf (single-pass compaction)
+//   k_search_all  unique + insert/delete cancellation on the sorted words and the
+//                 leaf search of every survivor, one word per thread (learned model
+//                 when trained, else binary search; both give the same leaf)
+//   k_compact     survivors and the heads of their runs of equal leaf, one
+//                 single-pass compaction with two counts
 //   k_small_front all of the above in one block for batches of at most
 //                 kSmallBatch keys (bitonic sort in shared memory)
 #include "gpma_dev.cuh"
@@ -199,83 +200,6 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_pass(const uint64_t *__re
   }
 }
 
-// unique + cancellation (reading R2): survivors compacted in order
-__global__ void __launch_bounds__(kScanThreads) k_keep(PrepArgs a, const uint64_t *__restrict__ sorted,
-                                                        uint64_t *__restrict__ ukey, uint8_t *__restrict__ utag,
-                                                        uint64_t *status, Ctl *ctl) {
-  __shared__ ScanSmem sm;
-  const uint32_t tile = take_ticket(ctl, kSlotKeep, sm), n = ctl->n;
-  uint32_t flag[kScanItems];
-  uint64_t w[kScanItems];
-#pragma unroll
-  for (int r = 0; r < kScanItems; r++) {
-    uint64_t e = scan_elem(tile, r);
-    flag[r] = 0;
-    w[r] = 0;
-    if (e < n) {
-      w[r] = sorted[e];
-      const uint64_t k = w[r] & ~kTagBit;
-      if (w[r] & kTagBit)  // delete: kept iff no word with the same key precedes it
-        flag[r] = e == 0 || (sorted[e - 1] & ~kTagBit) != k;
-      else                 // insert: kept iff no word with the same key follows it
-        flag[r] = e + 1 == n || (sorted[e + 1] & ~kTagBit) != k;
-    }
-  }
-  uint32_t off[kScanItems];
-  uint32_t total = tile_scan(flag, off, tile, status, 1, 0, ctl->epoch + kSlotKeep, &ctl->err, sm);
-#pragma unroll
-  for (int r = 0; r < kScanItems; r++) {
-    if (!flag[r] || off[r] >= n) continue;
-    ukey[off[r]] = expand(w[r], a);
-    utag[off[r]] = (uint8_t)(w[r] >> 63);
-  }
-  if ((uint64_t)(tile + 1) * kScanTile >= n && threadIdx.x == 0) ctl->m = total;
-}
-
-// the leaf of every survivor (reading R4), one per thread so the searches' load
-// chains overlap: the learned model when trained, else binary search (same leaf)
-__global__ void __launch_bounds__(256) k_search(const uint64_t *__restrict__ ukey, uint32_t *__restrict__ uleaf,
-                                                const uint64_t *__restrict__ F, uint64_t nleaves, const Ctl *ctl,
-                                                const ModelHead *mhead, const Piece *__restrict__ mpieces) {
-  const uint32_t m = ctl->m;
-  ModelHead hd;
-  hd.valid = 0;
-  if (mhead) hd = *mhead;
-  const bool learned = hd.valid != 0;
-  for (uint32_t e = blockIdx.x * blockDim.x + threadIdx.x; e < m; e += gridDim.x * blockDim.x) {
-    const uint64_t key = ukey[e];
-    uleaf[e] = learned ? learned_leaf_search(hd, mpieces, F, nleaves, key) : leaf_search(F, nleaves, key);
-  }
-}
-
-__global__ void __launch_bounds__(kScanThreads) k_runs(const uint32_t *__restrict__ uleaf,
-                                                        uint32_t *__restrict__ run_start,
-                                                        uint32_t *__restrict__ run_leaf, uint64_t *status,
-                                                        Ctl *ctl) {
-  __shared__ ScanSmem sm;
-  const uint32_t tile = take_ticket(ctl, kSlotRuns, sm), m = ctl->m;
-  if ((uint64_t)tile * kScanTile >= m && tile > 0) return;  // past the end (tile 0 always runs)
-  uint32_t flag[kScanItems];
-#pragma unroll
-  for (int r = 0; r < kScanItems; r++) {
-    uint64_t e = scan_elem(tile, r);
-    flag[r] = e < m && (e == 0 || uleaf[e] != uleaf[e - 1]);
-  }
-  uint32_t off[kScanItems];
-  uint32_t total = tile_scan(flag, off, tile, status, 1, 0, ctl->epoch + kSlotRuns, &ctl->err, sm);
-#pragma unroll
-  for (int r = 0; r < kScanItems; r++)
-    if (flag[r] && off[r] < m) {
-      const uint32_t e = (uint32_t)scan_elem(tile, r);
-      run_start[off[r]] = e;
-      run_leaf[off[r]] = uleaf[e];
-    }
-  if ((uint64_t)(tile + 1) * kScanTile >= m && threadIdx.x == 0) {
-    ctl->nruns = total;
-    run_start[total] = m;
-  }
-}
-
 // ---- small batches: the whole front end in one block ---------------------------------------
 // Sort word = (compressed key without tag) << 1 | tag.  Inserts (tag 0) order
 // before deletes (tag 1) of the same key, and equal words are identical, so the
@@ -456,6 +380,75 @@ __global__ void __launch_bounds__(1024) k_small_front(PrepArgs a, const uint64_t
   }
 }
 
+// ---- unique/cancel, leaf search and run heads in two kernels ---------------------------------
+// k_search_all: one sorted word per thread: the survivor test of reading R2 and,
+// for survivors, the leaf (reading R4); lfull[e] = kNoLeaf for dropped words.
+// k_compact: one single-pass compaction with two counts (survivors, runs): a run
+// starts at a survivor whose leaf differs from the previous survivor's.
+__global__ void __launch_bounds__(256) k_search_all(PrepArgs a, const uint64_t *__restrict__ sorted,
+                                                    uint32_t *__restrict__ lfull, const uint64_t *__restrict__ F,
+                                                    uint64_t nleaves, const Ctl *ctl, const ModelHead *mhead,
+                                                    const Piece *__restrict__ mpieces) {
+  const uint32_t n = ctl->n;
+  ModelHead hd;
+  hd.valid = 0;
+  if (mhead) hd = *mhead;
+  const bool learned = hd.valid != 0;
+  for (uint32_t e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) {
+    const uint64_t w = sorted[e], k = w & ~kTagBit;
+    const bool kept = (w & kTagBit) ? (e == 0 || (sorted[e - 1] & ~kTagBit) != k)
+                                    : (e + 1 == n || (sorted[e + 1] & ~kTagBit) != k);
+    uint32_t leaf = kNoLeaf;
+    if (kept) {
+      const uint64_t key = expand(w, a);
+      leaf = learned ? learned_leaf_search(hd, mpieces, F, nleaves, key) : leaf_search(F, nleaves, key);
+    }
+    lfull[e] = leaf;
+  }
+}
+
+__global__ void __launch_bounds__(kScanThreads) k_compact(PrepArgs a, const uint64_t *__restrict__ sorted,
+                                                          const uint32_t *__restrict__ lfull,
+                                                          uint64_t *__restrict__ ukey, uint8_t *__restrict__ utag,
+                                                          uint32_t *__restrict__ uleaf, uint32_t *__restrict__ run_start,
+                                                          uint32_t *__restrict__ run_leaf, uint64_t *status, Ctl *ctl) {
+  __shared__ ScanSmem sm;
+  const uint32_t tile = take_ticket(ctl, kSlotKeep, sm), n = ctl->n;
+  uint32_t keep[kScanItems], head[kScanItems], lf[kScanItems];
+#pragma unroll
+  for (int r = 0; r < kScanItems; r++) {
+    const uint64_t e = scan_elem(tile, r);
+    lf[r] = e < n ? lfull[e] : kNoLeaf;
+    keep[r] = lf[r] != kNoLeaf;
+    head[r] = 0;
+    if (keep[r]) {
+      int64_t j = (int64_t)e - 1;  // previous survivor (dropped words are rare)
+      while (j >= 0 && lfull[j] == kNoLeaf) --j;
+      head[r] = j < 0 || lfull[j] != lf[r];
+    }
+  }
+  uint32_t koff[kScanItems], hoff[kScanItems];
+  const uint32_t m = tile_scan(keep, koff, tile, status, 2, 0, ctl->epoch + kSlotKeep, &ctl->err, sm);
+  const uint32_t nr = tile_scan(head, hoff, tile, status, 2, 1, ctl->epoch + kSlotKeep, &ctl->err, sm);
+#pragma unroll
+  for (int r = 0; r < kScanItems; r++) {
+    if (!keep[r] || koff[r] >= n) continue;
+    const uint64_t w = sorted[scan_elem(tile, r)];
+    ukey[koff[r]] = expand(w, a);
+    utag[koff[r]] = (uint8_t)(w >> 63);
+    uleaf[koff[r]] = lf[r];
+    if (head[r]) {
+      run_start[hoff[r]] = koff[r];
+      run_leaf[hoff[r]] = lf[r];
+    }
+  }
+  if ((uint64_t)(tile + 1) * kScanTile >= n && threadIdx.x == 0) {
+    ctl->m = m;
+    ctl->nruns = nr;
+    run_start[nr] = m;
+  }
+}
+
 // ---- host launchers ----------------------------------------------------------------------
 static uint32_t grid_for(uint64_t n, uint32_t per_block, uint32_t cap) {
   uint64_t g = (n + per_block - 1) / per_block;
@@ -518,12 +511,11 @@ void launch_sort(const FrontArgs &f, uint64_t nb, cudaStream_t s) {
   // look-back epochs: pass p uses epoch + p, then the fixed slots of gpma_launch.h
   const uint32_t ct = comp_tiles(nb);
   note_launch();
-  k_keep<<<ct, kScanThreads, 0, s>>>(a, src, f.ukey, f.utag, f.status, f.ctl);
+  k_search_all<<<grid_for(nb, 256, 152 * 16), 256, 0, s>>>(a, src, f.lfull, f.geo->F, f.geo->nleaves, f.ctl, f.mhead,
+                                                           f.mpieces);
   note_launch();
-  k_search<<<grid_for(nb, 256, 152 * 16), 256, 0, s>>>(f.ukey, f.uleaf, f.geo->F, f.geo->nleaves, f.ctl, f.mhead,
-                                                       f.mpieces);
-  note_launch();
-  k_runs<<<ct, kScanThreads, 0, s>>>(f.uleaf, f.run_start, f.run_leaf, f.status, f.ctl);
+  k_compact<<<ct, kScanThreads, 0, s>>>(a, src, f.lfull, f.ukey, f.utag, f.uleaf, f.run_start, f.run_leaf, f.status,
+                                        f.ctl);
 }
 
 }  // namespace gpk
