@@ -114,14 +114,26 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_pass(const uint64_t *__re
   __shared__ uint32_t gbase[256];
   __shared__ uint32_t ltile[256];  // digit totals of the tile, then their exclusive prefix
   __shared__ uint64_t skey[kSortThreads * kSortItems];
+  __shared__ uint32_t hs[256];  // this pass's global digit counts, then their exclusive prefix
   __shared__ uint32_t s_tile;
   const uint32_t n = ctl->n;
   const uint32_t w = threadIdx.x >> 5, lane = lane_id();
   const uint32_t radix = 1u << dbits, mask = radix - 1u;
-  for (uint32_t d = threadIdx.x; d < 256; d += kSortThreads)
+  for (uint32_t d = threadIdx.x; d < 256; d += kSortThreads) {
     for (int q = 0; q < kSortThreads / 32; q++) wcnt[q][d] = 0;
+    hs[d] = d < radix ? hist[pass * 256 + d] : 0u;
+  }
   if (threadIdx.x == 0) s_tile = atomicAdd(&ctl->ticket[pass], 1u);
   __syncthreads();
+  if (w == 0) {  // the global offsets, while the other warps rank their keys
+    uint32_t carry = 0;
+    for (int c = 0; c < 256; c += 32) {
+      const uint32_t v = hs[c + lane];
+      const uint32_t inc = warp_incl_scan(v);
+      hs[c + lane] = carry + inc - v;
+      carry += __shfl_sync(0xFFFFFFFFu, inc, 31);
+    }
+  }
   const uint32_t tile = s_tile;
   const uint64_t base = (uint64_t)tile * (kSortThreads * kSortItems) + w * (kSortItems * 32);
   uint64_t key[kSortItems];
@@ -170,16 +182,13 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_pass(const uint64_t *__re
   }
   for (uint32_t d = radix + threadIdx.x; d < 256; d += kSortThreads) ltile[d] = 0;
   // exclusive scan of the global histogram of this pass
-  __shared__ uint32_t hs[256];
-  for (uint32_t d = threadIdx.x; d < 256; d += kSortThreads) hs[d] = d < radix ? hist[pass * 256 + d] : 0u;
   __syncthreads();
-  if (threadIdx.x < 64) {  // warp 0: global digit offsets; warp 1: digit offsets inside the tile
-    uint32_t *arr = threadIdx.x < 32 ? hs : ltile;
+  if (threadIdx.x < 32) {  // digit offsets inside the tile
     uint32_t carry = 0;
     for (int c = 0; c < 256; c += 32) {
-      uint32_t v = arr[c + lane];
-      uint32_t inc = warp_incl_scan(v);
-      arr[c + lane] = carry + inc - v;
+      const uint32_t v = ltile[c + lane];
+      const uint32_t inc = warp_incl_scan(v);
+      ltile[c + lane] = carry + inc - v;
       carry += __shfl_sync(0xFFFFFFFFu, inc, 31);
     }
   }
