@@ -37,10 +37,13 @@ SCALE, WINDOW, LEAF = 20, 16_000_000, 64
 SWEEP = (100, 1000, 10_000, 100_000, 1_000_000)
 SWEEP_WARM, SWEEP_TIMED = 3, 10
 PR_ITERS, DAMPING = 20, 0.85
-# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one k_pr_scatter launch on
-# the default workload (R-MAT scale 20, 16M-edge window, 2^25 slots), from one ncu capture
-# of the kernel as it stands: 285,246,720 read + 3,048,448 written
-PR_SCATTER_TRAFFIC = 288_295_168
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch of the PageRank sum
+# pass on the default workload (R-MAT scale 20, 16M-edge window, 2^25 slots), from one ncu
+# capture of each kernel as it stands; None where no capture of the current kernel exists
+PR_PASS_TRAFFIC = {"k_pr_scatter": 288_295_168, "k_pb_acc": None}
+# bucketed pass geometry (heads per bucket, target blocks, most parts per bucket), as the
+# library plans it for graphs of at most 2^24 vertices
+PB_BUCKET, PB_TARGET_BLOCKS, PB_MAX_PARTS, PB_MAX_V = 4096, 1024, 8, 1 << 24
 METRIC = "edge updates/sec vs batch size (+HBM GB/s frac); p50/p99 update+query latency"
 L2_BYTES = 129 * 1024 * 1024
 
@@ -58,6 +61,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--seed", type=int, default=1)
+    ap.add_argument("--push-pagerank", action="store_true",
+                    help="PageRank by the push pass (one L2 reduction per edge) instead of the bucketed pass")
     ap.add_argument("--learned-study", action="store_true",
                     help="only compare the learned and the plain leaf search on the power-law workload")
     ap.add_argument("--serve-study", action="store_true",
@@ -199,7 +204,7 @@ def run_gpu(a, stream, rank, world, dist):
     def to_dev(x):
         return torch.from_numpy(np.ascontiguousarray(x).view(np.int64)).to(dev)
 
-    g = gp.Graph(V, leaf_size=LEAF)
+    g = gp.Graph(V, leaf_size=LEAF, push_pagerank=a.push_pagerank)
     st = g.update(to_dev(win.initial), None, stats=True)
     torch.cuda.synchronize()
     src = bfs_source(stream)
@@ -297,20 +302,31 @@ def run_gpu(a, stream, rank, world, dist):
     out["profile"] = prof
     out["clocks"] = clk.summary()
     out["capacity"] = g.capacity
+    out["n_edges"] = g.num_edges()
     C, Vn = g.capacity, V
     # dominant kernel by device time inside the timed region
     pr = prof["pr_scatter"]
     per_launch_ms = pr["ms"] / max(pr["count"], 1)
-    alg_pr = 8 * C + 20 * Vn  # stream every slot; read contrib, read+write the fixed-point sum once per vertex
+    if a.push_pagerank or Vn > PB_MAX_V:
+        kname, what = "k_pr_scatter", "PageRank push pass over the gapped array"
+        alg_pr = 8 * C + 20 * Vn  # stream every slot; read contrib, read+write the fixed-point sum once per vertex
+    else:
+        kname, what = "k_pb_acc", "PageRank sum pass over the head-bucketed edge copy"
+        nb = -(-Vn // PB_BUCKET)
+        parts = min(max(-(-PB_TARGET_BLOCKS // nb), 1), PB_MAX_PARTS)
+        # read every edge of the copy once, every FP32 contribution once, write every partial sum
+        alg_pr = 8 * out["n_edges"] + 4 * Vn + 8 * parts * nb * PB_BUCKET
     out["roofline"] = {
-        "kernel": "k_pr_scatter (PageRank push pass over the gapped array)",
+        "kernel": f"{kname} ({what})",
         "bound": "hbm", "achieved": alg_pr / (per_launch_ms * 1e-3) / 1e9, "peak": peak,
         "peak_kind": peak_kind, "unit": "GB/s",
         "frac": alg_pr / (per_launch_ms * 1e-3) / 1e9 / peak,
-        "traffic": PR_SCATTER_TRAFFIC if (a.scale, a.window) == (SCALE, WINDOW) else None,
+        "traffic": PR_PASS_TRAFFIC[kname] if (a.scale, a.window) == (SCALE, WINDOW) else None,
         "alg_bytes_per_launch": alg_pr, "launch_ms": per_launch_ms,
         "share_of_step": pr["ms"] / ms if ms else None,
     }
+    if prof["pr_bucket"]["count"]:
+        out["roofline"]["bucketing_ms_per_call"] = prof["pr_bucket"]["ms"] / prof["pr_bucket"]["count"]
 
     # -- e2e: host (pinned) inputs copied in and results copied out every step ---------------------
     if not a.no_e2e:

@@ -50,6 +50,11 @@ typedef struct gpma *gpma_t;
                                 a merged segment must end within [min_i, max_i]; deletes leave
                                 no holes; an underfull root halves.  Default: lazy deletion
                                 (Sec. 6.1), slots become EMPTY in place */
+#define GPMA_PUSH_PAGERANK 8u /* PageRank sums by one push pass over the slots per iteration
+                                (a reduction per edge into the L2).  Default, for graphs
+                                of at most 2^24 vertices: the edges are bucketed by head
+                                once per call and each iteration sums every bucket in
+                                shared memory.  Both give the same ranks, bit for bit */
 
 #define GPMA_MAX_LEVELS 48
 
@@ -61,7 +66,8 @@ typedef struct gpma *gpma_t;
 typedef struct {
   uint32_t leaf_size; /* L: power of two in [2, 1024]; default 64 */
   uint32_t tau0_pct, tauh_pct, rho0_pct, rhoh_pct;
-  uint32_t flags;     /* GPMA_RAW_KEYS | GPMA_PLAIN_SEARCH | GPMA_DUAL_DELETE, or 0 */
+  uint32_t flags;     /* GPMA_RAW_KEYS | GPMA_PLAIN_SEARCH | GPMA_DUAL_DELETE |
+                         GPMA_PUSH_PAGERANK, or 0 */
 } gpma_params;
 
 /* Optional device allocator.  alloc returns NULL on failure; both receive the
@@ -152,8 +158,12 @@ int gpma_cc(gpma_t h, uint32_t *d_label, void *stream);
 
 /* PageRank by power iteration (Sec. 6.1): x0 = 1/V and `iters` steps of
  * x'_v = (1-d)/V + d * (sum_{u->v} x_u / outdeg(u) + (sum of x over vertices
- * without out-edges) / V).  d_rank[V] receives FP32 ranks (sums accumulated in
- * FP64).  Stream-ordered. */
+ * without out-edges) / V).  d_rank[V] receives FP32 ranks.  Each quotient
+ * x_u / outdeg(u) is formed in FP32 and rounded once to fixed point with 60
+ * fractional bits; the sums over edges are exact integer sums, so the ranks do not
+ * depend on the order of the edges or of the reductions.  The first call
+ * allocates the pass's buffers (with the bucketed pass: an edge copy as large as
+ * the slot array).  Stream-ordered. */
 int gpma_pagerank(gpma_t h, uint32_t iters, float damping, float *d_rank, void *stream);
 
 /* Copy the stored edges (no guards) in ascending key order into d_out[cap];
@@ -214,13 +224,14 @@ int gpma_check(gpma_t h, uint32_t *code, void *stream);
 #define GPMA_PROF_LEAF 1       /* leaf pass (presence, deletes, level-0 merges) + count tree */
 #define GPMA_PROF_ESCALATE 2   /* pending inserts, merge levels, outer segment merges */
 #define GPMA_PROF_RESIZE 3     /* root resize */
-#define GPMA_PROF_PR_SCATTER 4 /* one PageRank push pass over the slots */
+#define GPMA_PROF_PR_SCATTER 4 /* one PageRank sum pass (bucketed, or push over the slots) */
 #define GPMA_PROF_PAGERANK 5   /* one whole gpma_pagerank call */
 #define GPMA_PROF_BFS 6        /* one whole gpma_bfs call */
 #define GPMA_PROF_CC 7         /* one whole gpma_cc call */
 #define GPMA_PROF_UPDATE 8     /* one whole gpma_update_batch call (replayed batches run as one
                                   CUDA graph: then only this phase is recorded) */
-#define GPMA_PROF_N 9
+#define GPMA_PROF_PR_BUCKET 9  /* bucketing the edges by head, once per gpma_pagerank call */
+#define GPMA_PROF_N 10
 
 typedef struct {
   double ms[GPMA_PROF_N];         /* summed device time */

@@ -20,6 +20,7 @@ GPMA_OK, GPMA_EINVAL, GPMA_ENOMEM, GPMA_ECAP, GPMA_ETIMEOUT, GPMA_EDEVICE = rang
 GPMA_RAW_KEYS = 1
 GPMA_PLAIN_SEARCH = 2
 GPMA_DUAL_DELETE = 4
+GPMA_PUSH_PAGERANK = 8
 GPMA_MAX_LEVELS = 48
 EMPTY = 0xFFFFFFFFFFFFFFFF
 
@@ -52,11 +53,14 @@ class gpma_stats(C.Structure):
         return d
 
 
-GPMA_PROF_NAMES = ("sort", "leaf", "escalate", "resize", "pr_scatter", "pagerank", "bfs", "cc", "update")
+GPMA_PROF_NAMES = ("sort", "leaf", "escalate", "resize", "pr_scatter", "pagerank", "bfs", "cc", "update",
+                   "pr_bucket")
+GPMA_PROF_N = len(GPMA_PROF_NAMES)
 
 
 class gpma_profile(C.Structure):
-    _fields_ = [("ms", C.c_double * 9), ("count", C.c_uint64 * 9), ("launches", C.c_uint64 * 9)]
+    _fields_ = [("ms", C.c_double * GPMA_PROF_N), ("count", C.c_uint64 * GPMA_PROF_N),
+                ("launches", C.c_uint64 * GPMA_PROF_N)]
 
     def as_dict(self) -> dict:
         return {n: {"ms": self.ms[i], "count": self.count[i], "launches": self.launches[i]}
@@ -145,9 +149,9 @@ def _check(rc: int, where: str):
 # ---- the C entry points, one to one --------------------------------------------------------
 def gpma_create(n_vertices: int, leaf_size: int = 64, tau0: int = 92, tauh: int = 80, rho0: int = 8,
                 rhoh: int = 40, raw_keys: bool = False, plain_search: bool = False, dual: bool = False,
-                stream=None) -> int:
+                push_pagerank: bool = False, stream=None) -> int:
     flags = ((GPMA_RAW_KEYS if raw_keys else 0) | (GPMA_PLAIN_SEARCH if plain_search else 0) |
-             (GPMA_DUAL_DELETE if dual else 0))
+             (GPMA_DUAL_DELETE if dual else 0) | (GPMA_PUSH_PAGERANK if push_pagerank else 0))
     p = gpma_params(leaf_size, tau0, tauh, rho0, rhoh, flags)
     h = C.c_void_p()
     _check(lib().gpma_create(n_vertices, C.byref(p), None, _stream(stream), C.byref(h)), "gpma_create")
@@ -286,11 +290,11 @@ class Graph:
     """A GPMA+ array on the current CUDA device (owns one libgpma handle)."""
 
     def __init__(self, n_vertices: int, leaf_size: int = 64, raw_keys: bool = False, plain_search: bool = False,
-                 dual: bool = False, stream=None, **dens):
+                 dual: bool = False, push_pagerank: bool = False, stream=None, **dens):
         self.n_vertices = 0 if raw_keys else int(n_vertices)
         self.raw = raw_keys
         self.h = gpma_create(n_vertices, leaf_size=leaf_size, raw_keys=raw_keys, plain_search=plain_search,
-                             dual=dual, stream=stream, **dens)
+                             dual=dual, push_pagerank=push_pagerank, stream=stream, **dens)
 
     def close(self):
         if getattr(self, "h", None):

@@ -204,6 +204,12 @@ struct gpma {
   uint32_t *q0, *q1, *q2, *counter, *h_counter;
   uint64_t *pr_partials;
   unsigned *pr_counter;
+  // bucketed PageRank: per-chunk bucket counts and their scan, the edges by head
+  // bucket (as many slots as the array, grown with it) and the partial sums
+  bool push_pr;  // GPMA_PUSH_PAGERANK
+  uint32_t *pb_cnt;
+  uint64_t *pb_off, *pb_scan, *pb_keys, *pb_part;
+  uint64_t pb_keys_cap;
   uint32_t *check_buf;
   uint64_t *guards;
   uint64_t count_ub;
@@ -845,6 +851,37 @@ int ensure_analytics(gpma *h, uint32_t iters, cudaStream_t s) {
   return GPMA_OK;
 }
 
+// Buffers of the bucketed PageRank pass; false (nothing changed that matters)
+// when the heads do not fit its bucket table or memory is short: the caller then
+// takes the push pass.
+bool ensure_pb(gpma *h, const PbPlan &p, cudaStream_t s) {
+  if (h->push_pr || h->V > kPbMaxBuckets * kPbBucket) return false;
+  if (!h->pb_cnt) {
+    const uint64_t n = (uint64_t)p.nb * kPbMaxChunks;
+    if (!dalloc(h, &h->pb_cnt, n, s) || !dalloc(h, &h->pb_off, n + 1, s) ||
+        !dalloc(h, &h->pb_scan, scan_partials(n), s) ||
+        !dalloc(h, &h->pb_part, (uint64_t)p.nparts * p.nb * kPbBucket, s)) {
+      dfree(h, h->pb_cnt, s);
+      dfree(h, h->pb_off, s);
+      dfree(h, h->pb_scan, s);
+      dfree(h, h->pb_part, s);
+      h->pb_cnt = nullptr;
+      h->pb_off = h->pb_scan = h->pb_part = nullptr;
+      return false;
+    }
+  }
+  if (h->pb_keys_cap < h->geo.C) {
+    dfree(h, h->pb_keys, s);
+    h->pb_keys_cap = 0;
+    if (!dalloc(h, &h->pb_keys, h->geo.C, s)) {
+      h->pb_keys = nullptr;
+      return false;
+    }
+    h->pb_keys_cap = h->geo.C;
+  }
+  return true;
+}
+
 }  // namespace
 
 namespace gpk {
@@ -916,6 +953,7 @@ int gpma_create(uint32_t n_vertices, const gpma_params *params, const gpma_alloc
   h->logL = bits_for(L) - 1;
   h->raw = raw ? 1 : 0;
   h->dual = (p.flags & GPMA_DUAL_DELETE) ? 1 : 0;
+  h->push_pr = (p.flags & GPMA_PUSH_PAGERANK) != 0;
   h->tau0 = p.tau0_pct;
   h->tauh = p.tauh_pct;
   h->rho0 = p.rho0_pct;
@@ -978,7 +1016,7 @@ int gpma_destroy(gpma_t h) {
   free_work(h, s);
   void *ptrs[] = {h->mhead, h->mpieces, h->ctl, h->hist, h->scratch, h->vbuf, h->partials, h->cfx, h->y,
                   h->dsum, h->q0,  h->q1,  h->q2,    h->counter, h->check_buf, h->guards, h->pr_partials,
-                  h->pr_counter};
+                  h->pr_counter, h->pb_cnt, h->pb_off, h->pb_scan, h->pb_keys, h->pb_part};
   for (void *p : ptrs) dfree(h, p, s);
   cudaStreamSynchronize(s);
   if (h->h_ctl) cudaFreeHost(h->h_ctl);
@@ -1040,14 +1078,26 @@ int gpma_pagerank(gpma_t h, uint32_t iters, float damping, float *d_rank, void *
   cudaStream_t s = (cudaStream_t)stream;
   if (ensure_analytics(h, iters, s)) return GPMA_ENOMEM;
   Phase all(h->prof, GPMA_PROF_PAGERANK, s);
-  launch_pr_setup(h->geo, iters, d_rank, h->y, h->cfx, h->dsum, h->pr_partials, h->pr_counter, s);
+  const PbPlan plan = pb_plan(h->geo);
+  const bool bucketed = iters > 0 && ensure_pb(h, plan, s);
+  float *cf = bucketed ? reinterpret_cast<float *>(h->cfx) : nullptr;
+  if (bucketed) {
+    Phase ph(h->prof, GPMA_PROF_PR_BUCKET, s);
+    launch_pb_build(h->geo, plan, h->pb_cnt, h->pb_off, h->pb_scan, h->pb_keys, s);
+  }
+  launch_pr_setup(h->geo, iters, d_rank, h->y, h->cfx, cf, h->dsum, h->pr_partials, h->pr_counter, s);
   for (uint32_t it = 0; it < iters; it++) {
     {
       Phase ph(h->prof, GPMA_PROF_PR_SCATTER, s);
-      launch_pr_scatter(h->geo, h->cfx, h->y, s);
+      if (bucketed) launch_pb_acc(plan, h->pb_keys, h->pb_off, cf, h->pb_part, s);
+      else launch_pr_scatter(h->geo, h->cfx, h->y, s);
     }
-    launch_pr_apply(h->geo, damping, d_rank, h->y, h->cfx, h->dsum + it, h->dsum + it + 1, h->pr_partials,
-                    h->pr_counter, it + 1 == iters, s);
+    if (bucketed)
+      launch_pr_apply(h->geo, damping, d_rank, h->pb_part, plan.nparts, (uint64_t)plan.nb * kPbBucket, nullptr, cf,
+                      h->dsum + it, h->dsum + it + 1, h->pr_partials, h->pr_counter, it + 1 == iters, s);
+    else
+      launch_pr_apply(h->geo, damping, d_rank, h->y, 1, h->V, h->cfx, nullptr, h->dsum + it, h->dsum + it + 1,
+                      h->pr_partials, h->pr_counter, it + 1 == iters, s);
   }
   all.end();
   return cuda_ok(h);

@@ -1,8 +1,9 @@
 // k_analytics.cu -- graph analytics that read the gapped array in place
 // (Sec. 4.2: every access tests IsEntryExist, i.e. skips EMPTY slots; guards
 // delimit the rows).
-//   PageRank  power iteration with a push SpMV over the slots (Sec. 6.1), exact
-//             fixed-point sums
+//   PageRank  power iteration (Sec. 6.1) with exact fixed-point sums: by default
+//             the edges are bucketed by head once per call and every iteration sums
+//             each bucket in shared memory; or a push SpMV over the slots
 //   BFS       level-synchronous in one persistent cooperative kernel: a warp gathers
 //             a frontier vertex's row for small frontiers, one pass over the array
 //             for large ones
@@ -79,17 +80,24 @@ __device__ __forceinline__ void grid_sum_u64(uint64_t v, uint64_t *partials, uns
   }
 }
 
+// Contributions x_u / outdeg(u) are kept as fixed point (push pass: cfx) or as
+// the FP32 quotient (bucketed pass: cf, converted per edge), the same value either way.
 __global__ void k_pr_init(uint32_t V, const uint32_t *__restrict__ deg, float *__restrict__ x,
-                          uint64_t *__restrict__ cfx, uint64_t *__restrict__ y, uint64_t *dsum0, uint64_t *partials,
-                          unsigned *counter) {
+                          uint64_t *__restrict__ cfx, float *__restrict__ cf, uint64_t *__restrict__ y,
+                          uint64_t *dsum0, uint64_t *partials, unsigned *counter) {
   const float x0 = __fdiv_rn(1.0f, (float)V);
   uint64_t dang = 0;
   const uint32_t stride = gridDim.x * blockDim.x;
   for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < V; v += stride) {
     const uint32_t d = deg[v];
     x[v] = x0;
-    y[v] = 0;
-    cfx[v] = d ? to_fx(__fdiv_rn(x0, (float)d)) : 0ull;
+    const float q = d ? __fdiv_rn(x0, (float)d) : 0.0f;
+    if (cf) {
+      cf[v] = q;
+    } else {
+      y[v] = 0;
+      cfx[v] = to_fx(q);
+    }
     if (!d) dang += to_fx(x0);
   }
   grid_sum_u64(dang, partials, counter, dsum0);
@@ -126,9 +134,12 @@ __global__ void __launch_bounds__(256, 8) k_pr_scatter(const ulonglong2 *__restr
   }
 }
 
-__global__ void k_pr_apply(uint32_t V, float damping, const uint32_t *__restrict__ deg, uint64_t *__restrict__ y,
-                           float *__restrict__ x, uint64_t *__restrict__ cfx, const uint64_t *dsum_in,
-                           uint64_t *dsum_out, uint64_t *partials, unsigned *counter, int write_x) {
+// y[v] is the sum of nparts partial sums part[s * pstride + v] (the bucketed
+// pass; one part, zeroed after reading, for the push pass)
+__global__ void k_pr_apply(uint32_t V, float damping, const uint32_t *__restrict__ deg, uint64_t *__restrict__ part,
+                           uint32_t nparts, uint64_t pstride, float *__restrict__ x, uint64_t *__restrict__ cfx,
+                           float *__restrict__ cf, const uint64_t *dsum_in, uint64_t *dsum_out, uint64_t *partials,
+                           unsigned *counter, int write_x) {
   // x' = (1 - d)/V + d * (y + dangling / V), all in FP32 (the sums themselves are exact)
   const float base = __fdiv_rn(1.0f - damping, (float)V);
   const float dn = __fdiv_rn(fx_to_float(*dsum_in), (float)V);
@@ -136,23 +147,115 @@ __global__ void k_pr_apply(uint32_t V, float damping, const uint32_t *__restrict
   const uint32_t stride = gridDim.x * blockDim.x;
   for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < V; v += stride) {
     const uint32_t d = deg[v];
-    const float xf = __fmaf_rn(damping, fx_to_float(y[v]) + dn, base);
+    uint64_t yv = 0;
+    for (uint32_t q = 0; q < nparts; q++) yv += part[q * pstride + v];
+    const float xf = __fmaf_rn(damping, fx_to_float(yv) + dn, base);
     if (write_x) x[v] = xf;  // the ranks are read only after the last iteration
-    y[v] = 0;
-    cfx[v] = d ? to_fx(__fdiv_rn(xf, (float)d)) : 0ull;
+    const float c = d ? __fdiv_rn(xf, (float)d) : 0.0f;
+    if (cf) {
+      cf[v] = c;
+    } else {
+      part[v] = 0;
+      cfx[v] = to_fx(c);
+    }
     if (!d) dang += to_fx(xf);
   }
   grid_sum_u64(dang, partials, counter, dsum_out);
 }
 
+// ---- bucketed PageRank pass ----------------------------------------------------------------------
+// Once per call the stored edges are copied into buckets by head (v >> 12, a
+// stable-by-chunk counting sort: per-chunk bucket counts, a scan, a placement
+// pass).  Every iteration then gives each (bucket, part) pair one block that sums
+// the contributions of its share of the bucket into a 4096-entry table in shared
+// memory and writes the table out as one partial sum; the apply step adds the
+// parts.  The random reductions of the push pass become shared-memory atomics;
+// the copy keeps the chunks in slot order, so within a bucket the tails (and
+// the contribution loads) move forward through the array.  Each 64-bit sum is kept as two 32-bit words: the
+// low word's atomic returns the old value, and a carry out of it is added to the
+// high word with the high half, so the sum is exact modulo 2^64 whatever the
+// order, as in the push pass.
+__global__ void __launch_bounds__(256) k_pb_count(const ulonglong2 *__restrict__ s2, uint64_t npairs, uint64_t chunk,
+                                                  uint32_t nb, uint32_t *__restrict__ cnt) {
+  __shared__ uint32_t hist[kPbMaxBuckets];
+  for (uint32_t b = threadIdx.x; b < nb; b += blockDim.x) hist[b] = 0;
+  __syncthreads();
+  const uint64_t p0 = (uint64_t)blockIdx.x * chunk, p1 = p0 + chunk < npairs ? p0 + chunk : npairs;
+  for (uint64_t p = p0 + threadIdx.x; p < p1; p += blockDim.x) {
+    const ulonglong2 k = __ldcs(s2 + p);
+    if (k.x != kEmpty && !is_guard(k.x)) atomicAdd(&hist[(uint32_t)k.x >> kPbShift], 1u);
+    if (k.y != kEmpty && !is_guard(k.y)) atomicAdd(&hist[(uint32_t)k.y >> kPbShift], 1u);
+  }
+  __syncthreads();
+  for (uint32_t b = threadIdx.x; b < nb; b += blockDim.x) cnt[(uint64_t)b * gridDim.x + blockIdx.x] = hist[b];
+}
+
+__global__ void __launch_bounds__(256) k_pb_place(const ulonglong2 *__restrict__ s2, uint64_t npairs, uint64_t chunk,
+                                                  uint32_t nb, const uint64_t *__restrict__ off,
+                                                  uint64_t *__restrict__ keys) {
+  __shared__ uint32_t cur[kPbMaxBuckets];
+  __shared__ uint64_t base[kPbMaxBuckets];
+  for (uint32_t b = threadIdx.x; b < nb; b += blockDim.x) {
+    cur[b] = 0;
+    base[b] = off[(uint64_t)b * gridDim.x + blockIdx.x];
+  }
+  __syncthreads();
+  const uint64_t p0 = (uint64_t)blockIdx.x * chunk, p1 = p0 + chunk < npairs ? p0 + chunk : npairs;
+  for (uint64_t p = p0 + threadIdx.x; p < p1; p += blockDim.x) {
+    const ulonglong2 k = __ldcs(s2 + p);
+    if (k.x != kEmpty && !is_guard(k.x)) {
+      const uint32_t b = (uint32_t)k.x >> kPbShift;
+      keys[base[b] + atomicAdd(&cur[b], 1u)] = k.x;
+    }
+    if (k.y != kEmpty && !is_guard(k.y)) {
+      const uint32_t b = (uint32_t)k.y >> kPbShift;
+      keys[base[b] + atomicAdd(&cur[b], 1u)] = k.y;
+    }
+  }
+}
+
+// block (bucket b, part q) of nparts: edges [off[b*G] + len*q/nparts, off[b*G] + len*(q+1)/nparts)
+__global__ void __launch_bounds__(kPbThreads) k_pb_acc(const uint64_t *__restrict__ keys, const uint64_t *__restrict__ off,
+                                                       uint32_t G, uint32_t nb, uint32_t nparts,
+                                                       const float *__restrict__ cf, uint64_t *__restrict__ part) {
+  __shared__ uint32_t lo[kPbBucket], hi[kPbBucket];
+  const uint32_t b = blockIdx.x / nparts, q = blockIdx.x % nparts;
+  for (uint32_t i = threadIdx.x; i < kPbBucket; i += kPbThreads) lo[i] = hi[i] = 0;
+  __syncthreads();
+  const uint64_t e0 = off[(uint64_t)b * G], len = off[(uint64_t)(b + 1) * G] - e0;
+  const uint64_t a = e0 + len * q / nparts, z = e0 + len * (q + 1) / nparts;
+  for (uint64_t i0 = a; i0 < z; i0 += 4 * kPbThreads) {
+    uint64_t k[4];
+    float c[4];
+#pragma unroll
+    for (int u = 0; u < 4; u++) {
+      const uint64_t i = i0 + u * kPbThreads + threadIdx.x;
+      k[u] = i < z ? __ldcs(keys + i) : kEmpty;
+    }
+#pragma unroll
+    for (int u = 0; u < 4; u++) c[u] = k[u] != kEmpty ? __ldg(cf + (k[u] >> 32)) : 0.0f;
+#pragma unroll
+    for (int u = 0; u < 4; u++) {
+      if (k[u] == kEmpty) continue;
+      const uint64_t fx = to_fx(c[u]);
+      const uint32_t dl = (uint32_t)k[u] & (kPbBucket - 1), cl = (uint32_t)fx;
+      const uint32_t old = atomicAdd(&lo[dl], cl);
+      atomicAdd(&hi[dl], (uint32_t)(fx >> 32) + ((uint32_t)(old + cl) < old ? 1u : 0u));
+    }
+  }
+  __syncthreads();
+  uint64_t *o = part + ((uint64_t)q * nb + b) * kPbBucket;
+  for (uint32_t i = threadIdx.x; i < kPbBucket; i += kPbThreads) o[i] = ((uint64_t)hi[i] << 32) | lo[i];
+}
+
 constexpr uint32_t kVecBlocks = 152 * 8;  // grid of the per-vertex kernels (and partials per sum)
 
-void launch_pr_setup(const Geo &g, uint32_t iters, float *rank, uint64_t *y, uint64_t *cfx, uint64_t *dsum,
-                     uint64_t *partials, unsigned *counter, cudaStream_t s) {
+void launch_pr_setup(const Geo &g, uint32_t iters, float *rank, uint64_t *y, uint64_t *cfx, float *cf,
+                     uint64_t *dsum, uint64_t *partials, unsigned *counter, cudaStream_t s) {
   cudaMemsetAsync(dsum, 0, sizeof(uint64_t) * (iters + 1), s);
   cudaMemsetAsync(counter, 0, sizeof(unsigned), s);
   note_launch();
-  k_pr_init<<<nb(g.V, 256, kVecBlocks), 256, 0, s>>>(g.V, g.deg, rank, cfx, y, dsum, partials, counter);
+  k_pr_init<<<nb(g.V, 256, kVecBlocks), 256, 0, s>>>(g.V, g.deg, rank, cfx, cf, y, dsum, partials, counter);
 }
 
 void launch_pr_scatter(const Geo &g, const uint64_t *cfx, uint64_t *y, cudaStream_t s) {
@@ -161,12 +264,42 @@ void launch_pr_scatter(const Geo &g, const uint64_t *cfx, uint64_t *y, cudaStrea
                                                            (uint32_t)(g.C >> 1), cfx, y);
 }
 
-void launch_pr_apply(const Geo &g, float damping, float *rank, uint64_t *y, uint64_t *cfx,
-                     const uint64_t *dsum_in, uint64_t *dsum_out, uint64_t *partials, unsigned *counter,
-                     bool last, cudaStream_t s) {
+void launch_pr_apply(const Geo &g, float damping, float *rank, uint64_t *part, uint32_t nparts, uint64_t pstride,
+                     uint64_t *cfx, float *cf, const uint64_t *dsum_in, uint64_t *dsum_out, uint64_t *partials,
+                     unsigned *counter, bool last, cudaStream_t s) {
   note_launch();
-  k_pr_apply<<<nb(g.V, 256, kVecBlocks), 256, 0, s>>>(g.V, damping, g.deg, y, rank, cfx, dsum_in, dsum_out,
-                                                         partials, counter, last ? 1 : 0);
+  k_pr_apply<<<nb(g.V, 256, kVecBlocks), 256, 0, s>>>(g.V, damping, g.deg, part, nparts, pstride, rank, cfx, cf,
+                                                         dsum_in, dsum_out, partials, counter, last ? 1 : 0);
+}
+
+PbPlan pb_plan(const Geo &g) {
+  PbPlan p;
+  p.nb = (uint32_t)((g.V + kPbBucket - 1) / kPbBucket);
+  const uint64_t npairs = g.C >> 1;
+  uint64_t G = (npairs + 2047) / 2048;
+  if (G < 1) G = 1;
+  if (G > kPbMaxChunks) G = kPbMaxChunks;
+  p.G = (uint32_t)G;
+  p.chunk = (npairs + G - 1) / G;
+  uint32_t S = (kPbTargetBlocks + p.nb - 1) / p.nb;
+  p.nparts = S < 1 ? 1 : (S > kPbMaxParts ? kPbMaxParts : S);
+  return p;
+}
+
+void launch_pb_build(const Geo &g, const PbPlan &p, uint32_t *cnt, uint64_t *off, uint64_t *scan_tmp, uint64_t *keys,
+                     cudaStream_t s) {
+  const ulonglong2 *s2 = reinterpret_cast<const ulonglong2 *>(g.slots);
+  note_launch();
+  k_pb_count<<<p.G, 256, 0, s>>>(s2, g.C >> 1, p.chunk, p.nb, cnt);
+  launch_scan_u32_u64(cnt, off, (uint64_t)p.nb * p.G, scan_tmp, s);
+  note_launch();
+  k_pb_place<<<p.G, 256, 0, s>>>(s2, g.C >> 1, p.chunk, p.nb, off, keys);
+}
+
+void launch_pb_acc(const PbPlan &p, const uint64_t *keys, const uint64_t *off, const float *cf, uint64_t *part,
+                   cudaStream_t s) {
+  note_launch();
+  k_pb_acc<<<p.nb * p.nparts, kPbThreads, 0, s>>>(keys, off, p.G, p.nb, p.nparts, cf, part);
 }
 
 // ---- BFS ----------------------------------------------------------------------------------------

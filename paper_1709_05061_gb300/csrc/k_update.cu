@@ -368,38 +368,39 @@ __global__ void __launch_bounds__(256) k_leaf64(Geo g, Ctl *ctl, Work w) {
     const uint64_t key = act ? w.ukey[rs + lane] : 0ull;
     const uint32_t tag = act ? (uint32_t)w.utag[rs + lane] : 0u;
     const bool v0 = k0 != kEmpty, v1 = k1 != kEmpty;
-    bool d0 = false, d1 = false, found = false;
+    const uint32_t tbal = __ballot_sync(0xFFFFFFFFu, tag != 0);  // deletes of the run
+    bool d0 = false, d1 = false;
+    uint32_t fbal = 0;  // run keys present in the leaf
     for (uint32_t i = 0; i < len; i++) {
       const uint64_t ki = __shfl_sync(0xFFFFFFFFu, key, i);
-      const uint32_t ti = __shfl_sync(0xFFFFFFFFu, tag, i);
       const bool m0 = k0 == ki, m1 = k1 == ki;
-      const bool any = __ballot_sync(0xFFFFFFFFu, m0 || m1) != 0;
-      if (ti) {
+      if (__ballot_sync(0xFFFFFFFFu, m0 || m1)) fbal |= 1u << i;
+      if ((tbal >> i) & 1u) {
         d0 |= m0;
         d1 |= m1;
       }
-      if (lane == i) found = any;
     }
+    const bool found = (fbal >> lane) & 1u;
     const bool sv = act && !tag && !found;  // surviving insert (sorted in lane order)
     const uint32_t svbal = __ballot_sync(0xFFFFFFFFu, sv);
     const uint32_t nins = __popc(svbal);
-    const uint32_t ndel = __popc(__ballot_sync(0xFFFFFFFFu, d0)) + __popc(__ballot_sync(0xFFFFFFFFu, d1));
+    const uint32_t ndel = __reduce_add_sync(0xFFFFFFFFu, (uint32_t)d0 + (uint32_t)d1);
     const bool kp0 = v0 && !d0, kp1 = v1 && !d1;
-    const uint32_t nkept = __popc(__ballot_sync(0xFFFFFFFFu, kp0)) + __popc(__ballot_sync(0xFFFFFFFFu, kp1));
+    const uint32_t kb0 = __ballot_sync(0xFFFFFFFFu, kp0), kb1 = __ballot_sync(0xFFFFFFFFu, kp1);
+    const uint32_t nkept = __popc(kb0) + __popc(kb1);
     const bool fits = leaf_fits(g, (uint64_t)nkept + nins, nins);
     if (fits) {
       // TryInsert+ at level 0: rank-merge kept keys with the surviving inserts
-      const uint32_t c = (uint32_t)kp0 + (uint32_t)kp1;
-      const uint32_t before = warp_incl_scan(c) - c;
+      const uint32_t lt_mask = lanemask_lt();
+      const uint32_t before = __popc(kb0 & lt_mask) + __popc(kb1 & lt_mask);
       uint32_t lt0 = 0, lt1 = 0, my_pos = 0;
       for (uint32_t bits = svbal; bits; bits &= bits - 1) {
         const uint32_t b = __ffs(bits) - 1;
         const uint64_t ik = __shfl_sync(0xFFFFFFFFu, key, b);
         lt0 += ik < k0;
         lt1 += ik < k1;
-        const uint32_t below = __popc(__ballot_sync(0xFFFFFFFFu, kp0 && k0 < ik)) +
-                               __popc(__ballot_sync(0xFFFFFFFFu, kp1 && k1 < ik));
-        if (lane == b) my_pos = __popc(svbal & lanemask_lt()) + below;
+        const uint32_t below = __reduce_add_sync(0xFFFFFFFFu, (uint32_t)(kp0 && k0 < ik) + (uint32_t)(kp1 && k1 < ik));
+        if (lane == b) my_pos = __popc(svbal & lt_mask) + below;
       }
       if (kp0) sout[wib][before + lt0] = k0;
       if (kp1) sout[wib][before + kp0 + lt1] = k1;

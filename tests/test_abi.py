@@ -54,3 +54,20 @@ def test_argument_errors_without_gpu(lib):
     assert lib.gpma_create(10, ctypes.byref(p), None, None, ctypes.byref(out)) == gp.GPMA_EINVAL
     p = gp.gpma_params(64, 0, 0, 0, 0, 0)
     assert lib.gpma_create(0, ctypes.byref(p), None, None, ctypes.byref(out)) == gp.GPMA_EINVAL
+
+
+def header_defines():
+    text = open(HEADER).read()
+    return {m.group(1): m.group(2) for m in re.finditer(r"#define\s+(GPMA_[A-Z0-9_]+)\s+(\S+)", text)}
+
+
+def test_binding_constants_match_the_header():
+    """The binding's flag values and profile layout follow include/gpma.h (a
+    mismatch in the profile struct would let the library write past it)."""
+    d = header_defines()
+    assert int(d["GPMA_PROF_N"]) == gp.GPMA_PROF_N == len(gp.GPMA_PROF_NAMES)
+    assert ctypes.sizeof(gp.gpma_profile) == 3 * 8 * int(d["GPMA_PROF_N"])
+    for i, n in enumerate(gp.GPMA_PROF_NAMES):
+        assert int(d["GPMA_PROF_" + n.upper()]) == i, n
+    for name in ("GPMA_RAW_KEYS", "GPMA_PLAIN_SEARCH", "GPMA_DUAL_DELETE", "GPMA_PUSH_PAGERANK"):
+        assert int(d[name].rstrip("u")) == getattr(gp, name), name
