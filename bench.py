@@ -40,10 +40,9 @@ PR_ITERS, DAMPING = 20, 0.85
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch of the PageRank sum
 # pass on the default workload (R-MAT scale 20, 16M-edge window, 2^25 slots), from one ncu
 # capture of each kernel as it stands; None where no capture of the current kernel exists
-PR_PASS_TRAFFIC = {"k_pr_scatter": 288_295_168, "k_pb_acc": None}
-# bucketed pass geometry (heads per bucket, target blocks, most parts per bucket), as the
-# library plans it for graphs of at most 2^24 vertices
-PB_BUCKET, PB_TARGET_BLOCKS, PB_MAX_PARTS, PB_MAX_V = 4096, 1024, 8, 1 << 24
+PR_PASS_TRAFFIC = {"k_pr_scatter": 288_295_168, "k_pb_iter": None}
+# the library buckets the edges for PageRank on graphs of at most 2^24 vertices
+PB_MAX_V = 1 << 24
 METRIC = "edge updates/sec vs batch size (+HBM GB/s frac); p50/p99 update+query latency"
 L2_BYTES = 129 * 1024 * 1024
 
@@ -311,11 +310,10 @@ def run_gpu(a, stream, rank, world, dist):
         kname, what = "k_pr_scatter", "PageRank push pass over the gapped array"
         alg_pr = 8 * C + 20 * Vn  # stream every slot; read contrib, read+write the fixed-point sum once per vertex
     else:
-        kname, what = "k_pb_acc", "PageRank sum pass over the head-bucketed edge copy"
-        nb = -(-Vn // PB_BUCKET)
-        parts = min(max(-(-PB_TARGET_BLOCKS // nb), 1), PB_MAX_PARTS)
-        # read every edge of the copy once, every FP32 contribution once, write every partial sum
-        alg_pr = 8 * out["n_edges"] + 4 * Vn + 8 * parts * nb * PB_BUCKET
+        kname, what = "k_pb_iter", "PageRank iteration over the head-bucketed edge copy, update fused"
+        # read every edge of the copy once; per vertex read its contribution and out-degree
+        # once and write the next contribution
+        alg_pr = 8 * out["n_edges"] + 12 * Vn
     out["roofline"] = {
         "kernel": f"{kname} ({what})",
         "bound": "hbm", "achieved": alg_pr / (per_launch_ms * 1e-3) / 1e9, "peak": peak,

@@ -205,10 +205,10 @@ struct gpma {
   uint64_t *pr_partials;
   unsigned *pr_counter;
   // bucketed PageRank: per-chunk bucket counts and their scan, the edges by head
-  // bucket (as many slots as the array, grown with it) and the partial sums
+  // bucket (as many slots as the array, grown with it), per-block dangling sums
   bool push_pr;  // GPMA_PUSH_PAGERANK
   uint32_t *pb_cnt;
-  uint64_t *pb_off, *pb_scan, *pb_keys, *pb_part;
+  uint64_t *pb_off, *pb_scan, *pb_keys, *pb_dang;
   uint64_t pb_keys_cap;
   uint32_t *check_buf;
   uint64_t *guards;
@@ -855,18 +855,18 @@ int ensure_analytics(gpma *h, uint32_t iters, cudaStream_t s) {
 // when the heads do not fit its bucket table or memory is short: the caller then
 // takes the push pass.
 bool ensure_pb(gpma *h, const PbPlan &p, cudaStream_t s) {
-  if (h->push_pr || h->V > kPbMaxBuckets * kPbBucket) return false;
+  if (h->push_pr || p.nb > kPbMaxBuckets) return false;
   if (!h->pb_cnt) {
     const uint64_t n = (uint64_t)p.nb * kPbMaxChunks;
     if (!dalloc(h, &h->pb_cnt, n, s) || !dalloc(h, &h->pb_off, n + 1, s) ||
         !dalloc(h, &h->pb_scan, scan_partials(n), s) ||
-        !dalloc(h, &h->pb_part, (uint64_t)p.nparts * p.nb * kPbBucket, s)) {
+        !dalloc(h, &h->pb_dang, (uint64_t)p.nparts * p.nb, s)) {
       dfree(h, h->pb_cnt, s);
       dfree(h, h->pb_off, s);
       dfree(h, h->pb_scan, s);
-      dfree(h, h->pb_part, s);
+      dfree(h, h->pb_dang, s);
       h->pb_cnt = nullptr;
-      h->pb_off = h->pb_scan = h->pb_part = nullptr;
+      h->pb_off = h->pb_scan = h->pb_dang = nullptr;
       return false;
     }
   }
@@ -1016,7 +1016,7 @@ int gpma_destroy(gpma_t h) {
   free_work(h, s);
   void *ptrs[] = {h->mhead, h->mpieces, h->ctl, h->hist, h->scratch, h->vbuf, h->partials, h->cfx, h->y,
                   h->dsum, h->q0,  h->q1,  h->q2,    h->counter, h->check_buf, h->guards, h->pr_partials,
-                  h->pr_counter, h->pb_cnt, h->pb_off, h->pb_scan, h->pb_keys, h->pb_part};
+                  h->pr_counter, h->pb_cnt, h->pb_off, h->pb_scan, h->pb_keys, h->pb_dang};
   for (void *p : ptrs) dfree(h, p, s);
   cudaStreamSynchronize(s);
   if (h->h_ctl) cudaFreeHost(h->h_ctl);
@@ -1080,24 +1080,25 @@ int gpma_pagerank(gpma_t h, uint32_t iters, float damping, float *d_rank, void *
   Phase all(h->prof, GPMA_PROF_PAGERANK, s);
   const PbPlan plan = pb_plan(h->geo);
   const bool bucketed = iters > 0 && ensure_pb(h, plan, s);
-  float *cf = bucketed ? reinterpret_cast<float *>(h->cfx) : nullptr;
+  // bucketed: the two halves of cfx hold the FP32 contributions of alternate iterations
+  float *cf[2] = {reinterpret_cast<float *>(h->cfx), reinterpret_cast<float *>(h->cfx) + h->V};
   if (bucketed) {
     Phase ph(h->prof, GPMA_PROF_PR_BUCKET, s);
     launch_pb_build(h->geo, plan, h->pb_cnt, h->pb_off, h->pb_scan, h->pb_keys, s);
   }
-  launch_pr_setup(h->geo, iters, d_rank, h->y, h->cfx, cf, h->dsum, h->pr_partials, h->pr_counter, s);
+  launch_pr_setup(h->geo, iters, d_rank, h->y, h->cfx, bucketed ? cf[0] : nullptr, h->dsum, h->pr_partials,
+                  h->pr_counter, s);
   for (uint32_t it = 0; it < iters; it++) {
-    {
-      Phase ph(h->prof, GPMA_PROF_PR_SCATTER, s);
-      if (bucketed) launch_pb_acc(plan, h->pb_keys, h->pb_off, cf, h->pb_part, s);
-      else launch_pr_scatter(h->geo, h->cfx, h->y, s);
+    Phase ph(h->prof, GPMA_PROF_PR_SCATTER, s);
+    if (bucketed) {
+      launch_pb_iter(h->geo, plan, h->pb_keys, h->pb_off, damping, cf[it & 1], cf[(it + 1) & 1], d_rank,
+                     it + 1 == iters, h->dsum + it, h->dsum + it + 1, h->pb_dang, h->pr_counter, s);
+    } else {
+      launch_pr_scatter(h->geo, h->cfx, h->y, s);
+      ph.end();
+      launch_pr_apply(h->geo, damping, d_rank, h->y, h->cfx, h->dsum + it, h->dsum + it + 1, h->pr_partials,
+                      h->pr_counter, it + 1 == iters, s);
     }
-    if (bucketed)
-      launch_pr_apply(h->geo, damping, d_rank, h->pb_part, plan.nparts, (uint64_t)plan.nb * kPbBucket, nullptr, cf,
-                      h->dsum + it, h->dsum + it + 1, h->pr_partials, h->pr_counter, it + 1 == iters, s);
-    else
-      launch_pr_apply(h->geo, damping, d_rank, h->y, 1, h->V, h->cfx, nullptr, h->dsum + it, h->dsum + it + 1,
-                      h->pr_partials, h->pr_counter, it + 1 == iters, s);
   }
   all.end();
   return cuda_ok(h);

@@ -136,6 +136,26 @@ __device__ __forceinline__ T warp_sum(T v) {
   return v;
 }
 
+// Exclusive scan of one u32 per thread over the block; wsum: 33 words of shared
+// memory; *total = the block's sum.  Every thread of the block must call it.
+__device__ __forceinline__ uint32_t block_excl_scan(uint32_t v, uint32_t *wsum, uint32_t *total) {
+  const uint32_t lane = lane_id(), wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const uint32_t inc = warp_incl_scan(v);
+  if (lane == 31) wsum[wid] = inc;
+  __syncthreads();
+  if (wid == 0) {
+    const uint32_t x = lane < nw ? wsum[lane] : 0u;
+    const uint32_t xi = warp_incl_scan(x);
+    wsum[lane] = xi - x;
+    if (lane == 31) wsum[32] = xi;
+  }
+  __syncthreads();
+  const uint32_t r = wsum[wid] + inc - v;
+  *total = wsum[32];
+  __syncthreads();  // wsum is reused by the next scan
+  return r;
+}
+
 // first index in a[0..n) with a[i] >= k (a sorted ascending)
 template <typename T>
 __device__ __forceinline__ uint32_t lower_bound_dev(const T *a, uint32_t n, T k) {

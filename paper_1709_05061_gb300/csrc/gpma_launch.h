@@ -122,32 +122,34 @@ void launch_scan_u32_u64(const uint32_t *in, uint64_t *out, uint64_t n_bound, ui
 
 // k_analytics.cu
 // PageRank: x0 (setup), then per iteration one sum pass and one apply.  y, cfx:
-// u64[V] fixed point (2^60); cf: FP32 contributions (bucketed pass, else nullptr);
-// dsum: u64[iters + 1]; partials >= 152 * 16; counter one unsigned (zeroed by
-// setup, re-zeroed by each sum)
+// u64[V] fixed point (2^60); cf: FP32 contributions of the first iteration
+// (bucketed pass, else nullptr); dsum: u64[iters + 1]; partials >= 152 * 16;
+// counter one unsigned (zeroed by setup, re-zeroed by each sum)
 void launch_pr_setup(const Geo &g, uint32_t iters, float *rank, uint64_t *y, uint64_t *cfx, float *cf,
                      uint64_t *dsum, uint64_t *partials, unsigned *counter, cudaStream_t s);
 void launch_pr_scatter(const Geo &g, const uint64_t *cfx, uint64_t *y, cudaStream_t s);
-// part: nparts partial sums of V entries, pstride apart (push pass: y, 1, V)
-void launch_pr_apply(const Geo &g, float damping, float *rank, uint64_t *part, uint32_t nparts, uint64_t pstride,
-                     uint64_t *cfx, float *cf, const uint64_t *dsum_in, uint64_t *dsum_out, uint64_t *partials,
-                     unsigned *counter, bool last, cudaStream_t s);
-// Bucketed pass: buckets of kPbBucket heads, G chunks of the slot array, nparts
-// blocks per bucket.  cnt: u32[nb * G]; off: u64[nb * G + 1] (scan output, off[nb*G]
-// = edges); scan_tmp >= scan_partials(nb * G); keys: u64[edges] (<= C); part:
-// u64[nparts * nb * kPbBucket]
-constexpr uint32_t kPbShift = 12, kPbBucket = 1u << kPbShift, kPbThreads = 512;
-constexpr uint32_t kPbMaxBuckets = 4096;  // heads < 2^24
+void launch_pr_apply(const Geo &g, float damping, float *rank, uint64_t *y, uint64_t *cfx,
+                     const uint64_t *dsum_in, uint64_t *dsum_out, uint64_t *partials, unsigned *counter, bool last,
+                     cudaStream_t s);
+// Bucketed pass: buckets of kPbBucket heads, G chunks of the slot array, a
+// cluster of nparts blocks per bucket.  cnt: u32[nb * G]; off: u64[nb * G + 1]
+// (scan output, off[nb*G] = edges); scan_tmp >= scan_partials(nb * G); keys:
+// u64[edges] (<= C).  One iteration reads cf_in and writes cf_out (FP32 x/outdeg,
+// V each), the ranks when last, and dsum_out; partials >= nb * nparts.
+constexpr uint32_t kPbShift = 12, kPbMaxShift = 14, kPbThreads = 512;
+constexpr uint32_t kPbMaxBuckets = 4096;  // heads < kPbMaxBuckets << shift
 constexpr uint32_t kPbMaxChunks = 152 * 8, kPbTargetBlocks = 1024, kPbMaxParts = 8;
+constexpr uint32_t kPbTile = 8192, kPbPlaceThreads = 512;  // placement: slots per tile, threads
 struct PbPlan {
-  uint32_t nb, G, nparts;
+  uint32_t shift, nb, G, nparts;  // 2^shift heads per bucket
   uint64_t chunk;  // slot pairs per chunk
 };
 PbPlan pb_plan(const Geo &g);
 void launch_pb_build(const Geo &g, const PbPlan &p, uint32_t *cnt, uint64_t *off, uint64_t *scan_tmp, uint64_t *keys,
                      cudaStream_t s);
-void launch_pb_acc(const PbPlan &p, const uint64_t *keys, const uint64_t *off, const float *cf, uint64_t *part,
-                   cudaStream_t s);
+void launch_pb_iter(const Geo &g, const PbPlan &p, const uint64_t *keys, const uint64_t *off, float damping,
+                    const float *cf_in, float *cf_out, float *rank, bool last, const uint64_t *dsum_in,
+                    uint64_t *dsum_out, uint64_t *partials, unsigned *counter, cudaStream_t s);
 // BFS in one cooperative launch; counter >= 16 u32, h_counter pinned; waits for the
 // stream; returns 0, -1 on a CUDA error, -2 when a bounded barrier wait gave up
 int run_bfs(const Geo &g, uint32_t src, int32_t *depth, uint32_t *q0, uint32_t *q1, uint32_t *q2,

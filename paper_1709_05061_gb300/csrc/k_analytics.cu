@@ -134,12 +134,9 @@ __global__ void __launch_bounds__(256, 8) k_pr_scatter(const ulonglong2 *__restr
   }
 }
 
-// y[v] is the sum of nparts partial sums part[s * pstride + v] (the bucketed
-// pass; one part, zeroed after reading, for the push pass)
-__global__ void k_pr_apply(uint32_t V, float damping, const uint32_t *__restrict__ deg, uint64_t *__restrict__ part,
-                           uint32_t nparts, uint64_t pstride, float *__restrict__ x, uint64_t *__restrict__ cfx,
-                           float *__restrict__ cf, const uint64_t *dsum_in, uint64_t *dsum_out, uint64_t *partials,
-                           unsigned *counter, int write_x) {
+__global__ void k_pr_apply(uint32_t V, float damping, const uint32_t *__restrict__ deg, uint64_t *__restrict__ y,
+                           float *__restrict__ x, uint64_t *__restrict__ cfx, const uint64_t *dsum_in,
+                           uint64_t *dsum_out, uint64_t *partials, unsigned *counter, int write_x) {
   // x' = (1 - d)/V + d * (y + dangling / V), all in FP32 (the sums themselves are exact)
   const float base = __fdiv_rn(1.0f - damping, (float)V);
   const float dn = __fdiv_rn(fx_to_float(*dsum_in), (float)V);
@@ -147,17 +144,10 @@ __global__ void k_pr_apply(uint32_t V, float damping, const uint32_t *__restrict
   const uint32_t stride = gridDim.x * blockDim.x;
   for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < V; v += stride) {
     const uint32_t d = deg[v];
-    uint64_t yv = 0;
-    for (uint32_t q = 0; q < nparts; q++) yv += part[q * pstride + v];
-    const float xf = __fmaf_rn(damping, fx_to_float(yv) + dn, base);
+    const float xf = __fmaf_rn(damping, fx_to_float(y[v]) + dn, base);
     if (write_x) x[v] = xf;  // the ranks are read only after the last iteration
-    const float c = d ? __fdiv_rn(xf, (float)d) : 0.0f;
-    if (cf) {
-      cf[v] = c;
-    } else {
-      part[v] = 0;
-      cfx[v] = to_fx(c);
-    }
+    y[v] = 0;
+    cfx[v] = d ? to_fx(__fdiv_rn(xf, (float)d)) : 0ull;
     if (!d) dang += to_fx(xf);
   }
   grid_sum_u64(dang, partials, counter, dsum_out);
@@ -165,62 +155,136 @@ __global__ void k_pr_apply(uint32_t V, float damping, const uint32_t *__restrict
 
 // ---- bucketed PageRank pass ----------------------------------------------------------------------
 // Once per call the stored edges are copied into buckets by head (v >> 12, a
-// stable-by-chunk counting sort: per-chunk bucket counts, a scan, a placement
-// pass).  Every iteration then gives each (bucket, part) pair one block that sums
-// the contributions of its share of the bucket into a 4096-entry table in shared
-// memory and writes the table out as one partial sum; the apply step adds the
-// parts.  The random reductions of the push pass become shared-memory atomics;
+// counting sort by chunk: per-chunk bucket counts, a scan, a placement pass).
+// Every iteration then gives each bucket a cluster of blocks; each block sums the
+// contributions of its share of the bucket into a 4096-entry table in shared
+// memory, and the cluster adds its tables through distributed shared memory and
+// applies the update.  The random reductions of the push pass become
+// shared-memory atomics;
 // the copy keeps the chunks in slot order, so within a bucket the tails (and
 // the contribution loads) move forward through the array.  Each 64-bit sum is kept as two 32-bit words: the
 // low word's atomic returns the old value, and a carry out of it is added to the
 // high word with the high half, so the sum is exact modulo 2^64 whatever the
 // order, as in the push pass.
 __global__ void __launch_bounds__(256) k_pb_count(const ulonglong2 *__restrict__ s2, uint64_t npairs, uint64_t chunk,
-                                                  uint32_t nb, uint32_t *__restrict__ cnt) {
+                                                  uint32_t nb, uint32_t shift, uint32_t *__restrict__ cnt) {
   __shared__ uint32_t hist[kPbMaxBuckets];
   for (uint32_t b = threadIdx.x; b < nb; b += blockDim.x) hist[b] = 0;
   __syncthreads();
   const uint64_t p0 = (uint64_t)blockIdx.x * chunk, p1 = p0 + chunk < npairs ? p0 + chunk : npairs;
   for (uint64_t p = p0 + threadIdx.x; p < p1; p += blockDim.x) {
     const ulonglong2 k = __ldcs(s2 + p);
-    if (k.x != kEmpty && !is_guard(k.x)) atomicAdd(&hist[(uint32_t)k.x >> kPbShift], 1u);
-    if (k.y != kEmpty && !is_guard(k.y)) atomicAdd(&hist[(uint32_t)k.y >> kPbShift], 1u);
+    if (k.x != kEmpty && !is_guard(k.x)) atomicAdd(&hist[(uint32_t)k.x >> shift], 1u);
+    if (k.y != kEmpty && !is_guard(k.y)) atomicAdd(&hist[(uint32_t)k.y >> shift], 1u);
   }
   __syncthreads();
   for (uint32_t b = threadIdx.x; b < nb; b += blockDim.x) cnt[(uint64_t)b * gridDim.x + blockIdx.x] = hist[b];
 }
 
-__global__ void __launch_bounds__(256) k_pb_place(const ulonglong2 *__restrict__ s2, uint64_t npairs, uint64_t chunk,
-                                                  uint32_t nb, const uint64_t *__restrict__ off,
-                                                  uint64_t *__restrict__ keys) {
-  __shared__ uint32_t cur[kPbMaxBuckets];
-  __shared__ uint64_t base[kPbMaxBuckets];
-  for (uint32_t b = threadIdx.x; b < nb; b += blockDim.x) {
-    cur[b] = 0;
-    base[b] = off[(uint64_t)b * gridDim.x + blockIdx.x];
-  }
-  __syncthreads();
+// Placement, one tile of kPbTile slots at a time: the tile's edges are ranked
+// within their bucket (shared-memory counters), the counts scanned, the edges
+// staged in bucket order in shared memory, and then written out so that the
+// edges of one bucket go to consecutive addresses.
+__global__ void __launch_bounds__(kPbPlaceThreads) k_pb_place(const ulonglong2 *__restrict__ s2, uint64_t npairs,
+                                                              uint64_t chunk, uint32_t nb, uint32_t shift,
+                                                              const uint64_t *__restrict__ off,
+                                                              uint64_t *__restrict__ keys) {
+  extern __shared__ uint64_t pb_smem[];
+  uint64_t *stage = pb_smem;                                         // kPbTile keys
+  uint32_t *toff = reinterpret_cast<uint32_t *>(stage + kPbTile);    // nb + 1: counts, then offsets
+  uint32_t *cur = toff + nb + 1;                                     // nb: placed so far in this chunk
+  __shared__ uint32_t wsum[33];
+  constexpr uint32_t kPer = kPbTile / 2 / kPbPlaceThreads;           // slot pairs per thread per tile
+  const uint32_t t = threadIdx.x;
+  const uint32_t per = (nb + 1 + kPbPlaceThreads - 1) / kPbPlaceThreads;  // scan entries per thread
+  for (uint32_t b = t; b < nb; b += kPbPlaceThreads) cur[b] = 0;
   const uint64_t p0 = (uint64_t)blockIdx.x * chunk, p1 = p0 + chunk < npairs ? p0 + chunk : npairs;
-  for (uint64_t p = p0 + threadIdx.x; p < p1; p += blockDim.x) {
-    const ulonglong2 k = __ldcs(s2 + p);
-    if (k.x != kEmpty && !is_guard(k.x)) {
-      const uint32_t b = (uint32_t)k.x >> kPbShift;
-      keys[base[b] + atomicAdd(&cur[b], 1u)] = k.x;
+  for (uint64_t tp = p0; tp < p1; tp += kPbTile / 2) {
+    for (uint32_t b = t; b <= nb; b += kPbPlaceThreads) toff[b] = 0;
+    __syncthreads();
+    uint64_t k[2 * kPer];
+    uint32_t r[2 * kPer];
+#pragma unroll
+    for (uint32_t u = 0; u < kPer; u++) {
+      const uint64_t p = tp + u * kPbPlaceThreads + t;
+      const ulonglong2 v = p < p1 ? __ldcs(s2 + p) : make_ulonglong2(kEmpty, kEmpty);
+      k[2 * u] = (v.x != kEmpty && !is_guard(v.x)) ? v.x : kEmpty;
+      k[2 * u + 1] = (v.y != kEmpty && !is_guard(v.y)) ? v.y : kEmpty;
     }
-    if (k.y != kEmpty && !is_guard(k.y)) {
-      const uint32_t b = (uint32_t)k.y >> kPbShift;
-      keys[base[b] + atomicAdd(&cur[b], 1u)] = k.y;
+#pragma unroll
+    for (uint32_t j = 0; j < 2 * kPer; j++)
+      if (k[j] != kEmpty) r[j] = atomicAdd(&toff[(uint32_t)k[j] >> shift], 1u);
+    __syncthreads();
+    // exclusive scan of the nb counts (toff[nb] = 0 before, the tile's total after)
+    uint32_t loc = 0;
+    for (uint32_t e = 0; e < per; e++) {
+      const uint32_t b = t * per + e;
+      if (b <= nb) loc += toff[b];
     }
+    uint32_t total;
+    uint32_t run = block_excl_scan(loc, wsum, &total);
+    for (uint32_t e = 0; e < per; e++) {
+      const uint32_t b = t * per + e;
+      if (b <= nb) {
+        const uint32_t c = toff[b];
+        toff[b] = run;
+        run += c;
+      }
+    }
+    __syncthreads();
+#pragma unroll
+    for (uint32_t j = 0; j < 2 * kPer; j++)
+      if (k[j] != kEmpty) stage[toff[(uint32_t)k[j] >> shift] + r[j]] = k[j];
+    __syncthreads();
+    const uint32_t n = toff[nb];
+    for (uint32_t i = t; i < n; i += kPbPlaceThreads) {
+      const uint64_t key = stage[i];
+      const uint32_t b = (uint32_t)key >> shift;
+      keys[__ldg(off + (uint64_t)b * gridDim.x + blockIdx.x) + cur[b] + (i - toff[b])] = key;
+    }
+    __syncthreads();
+    for (uint32_t b = t; b < nb; b += kPbPlaceThreads) cur[b] += toff[b + 1] - toff[b];
+    __syncthreads();
   }
 }
 
-// block (bucket b, part q) of nparts: edges [off[b*G] + len*q/nparts, off[b*G] + len*(q+1)/nparts)
-__global__ void __launch_bounds__(kPbThreads) k_pb_acc(const uint64_t *__restrict__ keys, const uint64_t *__restrict__ off,
-                                                       uint32_t G, uint32_t nb, uint32_t nparts,
-                                                       const float *__restrict__ cf, uint64_t *__restrict__ part) {
-  __shared__ uint32_t lo[kPbBucket], hi[kPbBucket];
-  const uint32_t b = blockIdx.x / nparts, q = blockIdx.x % nparts;
-  for (uint32_t i = threadIdx.x; i < kPbBucket; i += kPbThreads) lo[i] = hi[i] = 0;
+// Cluster primitives (sm_90+): a barrier over the blocks of a cluster that also
+// orders their shared-memory writes, and 32-bit loads from another block's shared
+// memory (distributed shared memory).
+__device__ __forceinline__ void cluster_barrier() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+__device__ __forceinline__ uint32_t cluster_smem_addr(const void *p, uint32_t rank) {
+  uint32_t r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;"
+               : "=r"(r)
+               : "r"((uint32_t)__cvta_generic_to_shared(p)), "r"(rank));
+  return r;
+}
+__device__ __forceinline__ uint32_t ld_cluster_u32(uint32_t addr) {
+  uint32_t v;
+  asm volatile("ld.shared::cluster.u32 %0, [%1];" : "=r"(v) : "r"(addr) : "memory");
+  return v;
+}
+
+// One PageRank iteration over the bucketed copy.  A cluster of nparts blocks owns
+// bucket b; block q sums its share of the bucket's edges into its own table, then
+// (after a cluster barrier) adds the nparts tables over its share of the bucket's
+// heads through distributed shared memory and applies the update there:
+// x'_v = (1-d)/V + d * (y_v + dangling/V), the next contribution x'_v/outdeg(v)
+// into cf_out, and the dangling mass of the next iteration by a grid sum.
+__global__ void __launch_bounds__(kPbThreads) k_pb_iter(const uint64_t *__restrict__ keys,
+                                                        const uint64_t *__restrict__ off, uint32_t G, uint32_t shift,
+                                                        uint32_t nparts,
+                                                        uint32_t V, float damping, const uint32_t *__restrict__ deg,
+                                                        const float *__restrict__ cf_in, float *__restrict__ cf_out,
+                                                        float *__restrict__ x, int write_x, const uint64_t *dsum_in,
+                                                        uint64_t *dsum_out, uint64_t *partials, unsigned *counter) {
+  extern __shared__ uint32_t pb_tab[];  // low words, then high words, 2^shift each
+  const uint32_t bs = 1u << shift;
+  uint32_t *lo = pb_tab, *hi = pb_tab + bs;
+  const uint32_t b = blockIdx.x / nparts, q = blockIdx.x % nparts;  // q is the rank in the cluster
+  for (uint32_t i = threadIdx.x; i < bs; i += kPbThreads) lo[i] = hi[i] = 0;
   __syncthreads();
   const uint64_t e0 = off[(uint64_t)b * G], len = off[(uint64_t)(b + 1) * G] - e0;
   const uint64_t a = e0 + len * q / nparts, z = e0 + len * (q + 1) / nparts;
@@ -233,19 +297,36 @@ __global__ void __launch_bounds__(kPbThreads) k_pb_acc(const uint64_t *__restric
       k[u] = i < z ? __ldcs(keys + i) : kEmpty;
     }
 #pragma unroll
-    for (int u = 0; u < 4; u++) c[u] = k[u] != kEmpty ? __ldg(cf + (k[u] >> 32)) : 0.0f;
+    for (int u = 0; u < 4; u++) c[u] = k[u] != kEmpty ? __ldg(cf_in + (k[u] >> 32)) : 0.0f;
 #pragma unroll
     for (int u = 0; u < 4; u++) {
       if (k[u] == kEmpty) continue;
       const uint64_t fx = to_fx(c[u]);
-      const uint32_t dl = (uint32_t)k[u] & (kPbBucket - 1), cl = (uint32_t)fx;
+      const uint32_t dl = (uint32_t)k[u] & (bs - 1), cl = (uint32_t)fx;
       const uint32_t old = atomicAdd(&lo[dl], cl);
       atomicAdd(&hi[dl], (uint32_t)(fx >> 32) + ((uint32_t)(old + cl) < old ? 1u : 0u));
     }
   }
-  __syncthreads();
-  uint64_t *o = part + ((uint64_t)q * nb + b) * kPbBucket;
-  for (uint32_t i = threadIdx.x; i < kPbBucket; i += kPbThreads) o[i] = ((uint64_t)hi[i] << 32) | lo[i];
+  cluster_barrier();
+  const float base = __fdiv_rn(1.0f - damping, (float)V);
+  const float dn = __fdiv_rn(fx_to_float(*dsum_in), (float)V);
+  uint64_t dang = 0;
+  const uint32_t h0 = q * bs / nparts, h1 = (q + 1) * bs / nparts;
+  for (uint32_t e = h0 + threadIdx.x; e < h1; e += kPbThreads) {
+    uint64_t y = 0;
+    for (uint32_t r = 0; r < nparts; r++)
+      y += ((uint64_t)ld_cluster_u32(cluster_smem_addr(hi + e, r)) << 32) | ld_cluster_u32(cluster_smem_addr(lo + e, r));
+    const uint32_t v = b * bs + e;
+    if (v < V) {
+      const uint32_t d = deg[v];
+      const float xf = __fmaf_rn(damping, fx_to_float(y) + dn, base);
+      if (write_x) x[v] = xf;
+      cf_out[v] = d ? __fdiv_rn(xf, (float)d) : 0.0f;
+      if (!d) dang += to_fx(xf);
+    }
+  }
+  cluster_barrier();  // no block leaves while another still reads its tables
+  grid_sum_u64(dang, partials, counter, dsum_out);
 }
 
 constexpr uint32_t kVecBlocks = 152 * 8;  // grid of the per-vertex kernels (and partials per sum)
@@ -264,25 +345,28 @@ void launch_pr_scatter(const Geo &g, const uint64_t *cfx, uint64_t *y, cudaStrea
                                                            (uint32_t)(g.C >> 1), cfx, y);
 }
 
-void launch_pr_apply(const Geo &g, float damping, float *rank, uint64_t *part, uint32_t nparts, uint64_t pstride,
-                     uint64_t *cfx, float *cf, const uint64_t *dsum_in, uint64_t *dsum_out, uint64_t *partials,
-                     unsigned *counter, bool last, cudaStream_t s) {
+void launch_pr_apply(const Geo &g, float damping, float *rank, uint64_t *y, uint64_t *cfx,
+                     const uint64_t *dsum_in, uint64_t *dsum_out, uint64_t *partials, unsigned *counter,
+                     bool last, cudaStream_t s) {
   note_launch();
-  k_pr_apply<<<nb(g.V, 256, kVecBlocks), 256, 0, s>>>(g.V, damping, g.deg, part, nparts, pstride, rank, cfx, cf,
-                                                         dsum_in, dsum_out, partials, counter, last ? 1 : 0);
+  k_pr_apply<<<nb(g.V, 256, kVecBlocks), 256, 0, s>>>(g.V, damping, g.deg, y, rank, cfx, dsum_in, dsum_out,
+                                                         partials, counter, last ? 1 : 0);
 }
 
 PbPlan pb_plan(const Geo &g) {
   PbPlan p;
-  p.nb = (uint32_t)((g.V + kPbBucket - 1) / kPbBucket);
+  p.shift = kPbShift;  // 4096 heads: wider buckets (2^13, 2^14) measured slower at scales 20 and 24
+  p.nb = (uint32_t)((g.V + (1u << p.shift) - 1) >> p.shift);
   const uint64_t npairs = g.C >> 1;
   uint64_t G = (npairs + 2047) / 2048;
   if (G < 1) G = 1;
   if (G > kPbMaxChunks) G = kPbMaxChunks;
   p.G = (uint32_t)G;
   p.chunk = (npairs + G - 1) / G;
-  uint32_t S = (kPbTargetBlocks + p.nb - 1) / p.nb;
-  p.nparts = S < 1 ? 1 : (S > kPbMaxParts ? kPbMaxParts : S);
+  // blocks per bucket: a power of two (the cluster size), at most kPbMaxParts
+  const uint32_t want = (kPbTargetBlocks + p.nb - 1) / p.nb;
+  p.nparts = 1;
+  while (p.nparts * 2 <= want && p.nparts * 2 <= kPbMaxParts) p.nparts *= 2;
   return p;
 }
 
@@ -290,16 +374,42 @@ void launch_pb_build(const Geo &g, const PbPlan &p, uint32_t *cnt, uint64_t *off
                      cudaStream_t s) {
   const ulonglong2 *s2 = reinterpret_cast<const ulonglong2 *>(g.slots);
   note_launch();
-  k_pb_count<<<p.G, 256, 0, s>>>(s2, g.C >> 1, p.chunk, p.nb, cnt);
+  k_pb_count<<<p.G, 256, 0, s>>>(s2, g.C >> 1, p.chunk, p.nb, p.shift, cnt);
   launch_scan_u32_u64(cnt, off, (uint64_t)p.nb * p.G, scan_tmp, s);
+  const size_t smem = sizeof(uint64_t) * kPbTile + sizeof(uint32_t) * (2 * p.nb + 1);
+  static bool big = false;
+  if (!big) {
+    cudaFuncSetAttribute(k_pb_place, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)(sizeof(uint64_t) * kPbTile + sizeof(uint32_t) * (2 * kPbMaxBuckets + 1)));
+    big = true;
+  }
   note_launch();
-  k_pb_place<<<p.G, 256, 0, s>>>(s2, g.C >> 1, p.chunk, p.nb, off, keys);
+  k_pb_place<<<p.G, kPbPlaceThreads, smem, s>>>(s2, g.C >> 1, p.chunk, p.nb, p.shift, off, keys);
 }
 
-void launch_pb_acc(const PbPlan &p, const uint64_t *keys, const uint64_t *off, const float *cf, uint64_t *part,
-                   cudaStream_t s) {
+void launch_pb_iter(const Geo &g, const PbPlan &p, const uint64_t *keys, const uint64_t *off, float damping,
+                    const float *cf_in, float *cf_out, float *rank, bool last, const uint64_t *dsum_in,
+                    uint64_t *dsum_out, uint64_t *partials, unsigned *counter, cudaStream_t s) {
+  static bool big = false;
+  if (!big) {
+    cudaFuncSetAttribute(k_pb_iter, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(8u << kPbMaxShift));
+    big = true;
+  }
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(p.nb * p.nparts);
+  cfg.blockDim = dim3(kPbThreads);
+  cfg.dynamicSmemBytes = 8u << p.shift;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = p.nparts;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
   note_launch();
-  k_pb_acc<<<p.nb * p.nparts, kPbThreads, 0, s>>>(keys, off, p.G, p.nb, p.nparts, cf, part);
+  cudaLaunchKernelEx(&cfg, k_pb_iter, keys, off, p.G, p.shift, p.nparts, g.V, damping, (const uint32_t *)g.deg, cf_in, cf_out,
+                     rank, last ? 1 : 0, dsum_in, dsum_out, partials, counter);
 }
 
 // ---- BFS ----------------------------------------------------------------------------------------

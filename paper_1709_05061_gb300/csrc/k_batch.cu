@@ -214,23 +214,6 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_pass(const uint64_t *__re
 // before deletes (tag 1) of the same key, and equal words are identical, so the
 // sorted sequence equals the stable radix sort's.  Each thread owns `ipt`
 // consecutive positions for the two compactions (survivors, run heads).
-__device__ __forceinline__ uint32_t block_excl_scan(uint32_t v, uint32_t *wsum, uint32_t *total) {
-  const uint32_t lane = lane_id(), wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-  const uint32_t inc = warp_incl_scan(v);
-  if (lane == 31) wsum[wid] = inc;
-  __syncthreads();
-  if (wid == 0) {
-    const uint32_t x = lane < nw ? wsum[lane] : 0u;
-    const uint32_t xi = warp_incl_scan(x);
-    wsum[lane] = xi - x;
-    if (lane == 31) wsum[32] = xi;
-  }
-  __syncthreads();
-  const uint32_t r = wsum[wid] + inc - v;
-  *total = wsum[32];
-  __syncthreads();  // wsum is reused by the next scan
-  return r;
-}
 
 // Leaf search with a sampled first stage: S evenly spaced pivots F[i * stride]
 // sit in shared memory, the non-empty ones compacted in order.  The last sampled

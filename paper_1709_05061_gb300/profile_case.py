@@ -1,6 +1,7 @@
 """Small, self-contained runs of one hot kernel family for profilers.
 
-    python -m paper_1709_05061_gb300.profile_case --case pr      # PageRank push passes
+    python -m paper_1709_05061_gb300.profile_case --case pr      # PageRank: bucketing + 20 sum passes
+    python -m paper_1709_05061_gb300.profile_case --case pr --push  # PageRank by the push pass
     python -m paper_1709_05061_gb300.profile_case --case update  # one batch of --batch updates
     python -m paper_1709_05061_gb300.profile_case --case bfs
     python -m paper_1709_05061_gb300.profile_case --case cc
@@ -24,6 +25,7 @@ def main():
     ap.add_argument("--window", type=int, default=16_000_000)
     ap.add_argument("--batch", type=int, default=1_000_000)
     ap.add_argument("--repeat", type=int, default=1)
+    ap.add_argument("--push", action="store_true", help="PageRank by the push pass over the slots")
     a = ap.parse_args()
     import torch
 
@@ -37,7 +39,7 @@ def main():
 
     def dev(x):
         return torch.from_numpy(np.ascontiguousarray(x).view(np.int64)).cuda()
-    g = gp.Graph(1 << a.scale, leaf_size=64)
+    g = gp.Graph(1 << a.scale, leaf_size=64, push_pagerank=a.push)
     g.update(dev(win.initial), None)
     ins, dels = win.slide(half)
     g.update(dev(ins), dev(dels))  # first batch of this size: graph capture, work arrays
