@@ -334,35 +334,66 @@ def run_gpu(a, stream, rank, world, dist):
             ins, dels = win.slide(half)
             h_ins.append(torch.from_numpy(np.ascontiguousarray(ins).view(np.int64)).pin_memory())
             h_del.append(torch.from_numpy(np.ascontiguousarray(dels).view(np.int64)).pin_memory())
-        d_ins = torch.empty(half, dtype=torch.int64, device=dev)
-        d_del = torch.empty(half, dtype=torch.int64, device=dev)
-        o_rank = torch.empty(V, dtype=torch.float32).pin_memory()
-        o_depth = torch.empty(V, dtype=torch.int32).pin_memory()
-        o_label = torch.empty(V, dtype=torch.int32).pin_memory()
+        # Two sets of device inputs and host outputs: while step i computes on the default
+        # stream, a copy stream brings in step i+1's inputs; step i's results go back while
+        # step i+1 computes, and the host waits for them before it moves on.
+        d_ins = [torch.empty(half, dtype=torch.int64, device=dev) for _ in range(2)]
+        d_del = [torch.empty(half, dtype=torch.int64, device=dev) for _ in range(2)]
+        d_rank = [rank_t, torch.empty_like(rank_t)]
+        d_depth = [depth, torch.empty_like(depth)]
+        d_label = [label, torch.empty_like(label)]
+        o_rank = [torch.empty(V, dtype=torch.float32).pin_memory() for _ in range(2)]
+        o_depth = [torch.empty(V, dtype=torch.int32).pin_memory() for _ in range(2)]
+        o_label = [torch.empty(V, dtype=torch.int32).pin_memory() for _ in range(2)]
+        cs, xs = torch.cuda.current_stream(), torch.cuda.Stream()
+        ev_in = [torch.cuda.Event() for _ in range(2)]
+        ev_done = [torch.cuda.Event() for _ in range(2)]
+        ev_out = [torch.cuda.Event() for _ in range(2)]
 
-        def e2e_step(i):
-            d_ins.copy_(h_ins[i], non_blocking=True)
-            d_del.copy_(h_del[i], non_blocking=True)
-            step_io = gp.gpma_update_batch(g.h, d_ins, d_del)
-            del step_io
-            gp.gpma_pagerank(g.h, PR_ITERS, DAMPING, rank_t)
-            gp.gpma_bfs(g.h, src, depth)
-            gp.gpma_cc(g.h, label)
-            o_rank.copy_(rank_t, non_blocking=True)
-            o_depth.copy_(depth, non_blocking=True)
-            o_label.copy_(label, non_blocking=True)
-            torch.cuda.current_stream().synchronize()
+        def fetch(i):  # inputs of step i into set i % 2, once step i - 2 is done with it
+            b = i % 2
+            with torch.cuda.stream(xs):
+                if i >= 2:
+                    xs.wait_event(ev_done[b])
+                d_ins[b].copy_(h_ins[i], non_blocking=True)
+                d_del[b].copy_(h_del[i], non_blocking=True)
+                ev_in[b].record(xs)
 
-        for i in range(a.warmup):
-            e2e_step(i)
+        def run(i, last):
+            b = i % 2
+            cs.wait_event(ev_in[b])
+            if i >= 2:
+                cs.wait_event(ev_out[b])  # step i-2's results have left set b
+            gp.gpma_update_batch(g.h, d_ins[b], d_del[b])
+            gp.gpma_pagerank(g.h, PR_ITERS, DAMPING, d_rank[b])
+            gp.gpma_bfs(g.h, src, d_depth[b])
+            gp.gpma_cc(g.h, d_label[b])
+            ev_done[b].record(cs)
+            if not last:
+                fetch(i + 1)
+            with torch.cuda.stream(xs):
+                xs.wait_event(ev_done[b])
+                o_rank[b].copy_(d_rank[b], non_blocking=True)
+                o_depth[b].copy_(d_depth[b], non_blocking=True)
+                o_label[b].copy_(d_label[b], non_blocking=True)
+                ev_out[b].record(xs)
+
+        def steps(first, n):
+            fetch(first)
+            for i in range(first, first + n):
+                run(i, i == first + n - 1)
+                if i > first:
+                    ev_out[(i - 1) % 2].synchronize()  # the host has step i-1's results
+            ev_out[(first + n - 1) % 2].synchronize()
+
+        steps(0, a.warmup)
         torch.cuda.synchronize()
         if dist:
             dist.barrier()
         t0 = time.perf_counter()
         f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         f0.record()
-        for i in range(a.warmup, a.warmup + a.steps):
-            e2e_step(i)
+        steps(a.warmup, a.steps)
         f1.record()
         torch.cuda.synchronize()
         wall = (time.perf_counter() - t0) * 1e3

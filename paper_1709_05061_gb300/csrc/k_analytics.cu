@@ -674,18 +674,21 @@ __global__ void k_cc_init(uint32_t *label, uint32_t V) {
   for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < V; v += gridDim.x * blockDim.x) label[v] = v;
 }
 
-// first pass: the first stored out-edge of every row, which already joins most
-// vertices into large, shallow trees before the pass over all edges (taking the
-// first two edges, or no first pass, measured slower at R-MAT scales 20 and 24)
+// first pass: the first two stored out-edges of every row, which already joins
+// most vertices into large, shallow trees before the pass over all edges.  One edge
+// per row was measured faster on a freshly loaded graph but slower in a sliding
+// window (0.46 against 0.29 ms per call at R-MAT scale 20): its longer parent chains
+// cost the compression more than the first pass saves.
 __global__ void k_cc_sample(Geo g, uint32_t *label) {
   for (uint32_t u = blockIdx.x * blockDim.x + threadIdx.x; u < g.V; u += gridDim.x * blockDim.x) {
     const uint64_t beg = u ? (uint64_t)g.row_end[u - 1] + 1 : 0, end = g.row_end[u];
-    for (uint64_t e = beg; e < end; e++) {
+    uint32_t taken = 0;
+    for (uint64_t e = beg; e < end && taken < 2; e++) {
       const uint64_t k = g.slots[e];
       if (k == kEmpty) continue;
+      ++taken;
       const uint32_t v = (uint32_t)(k & 0xFFFFFFFFull);
       if (v != u) cc_link(label, u, v);
-      break;
     }
   }
 }
