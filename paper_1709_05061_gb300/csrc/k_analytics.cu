@@ -698,7 +698,8 @@ __global__ void __launch_bounds__(256) k_cc_hook(Geo g, uint32_t *label) {
     const uint64_t k = g.slots[e];
     if (k == kEmpty || is_guard(k)) continue;
     const uint32_t a = (uint32_t)(k >> 32), b = (uint32_t)(k & 0xFFFFFFFFull);
-    if (a != b) cc_link(label, a, b);
+    // equal labels: already one tree (after the compression most edges end here)
+    if (a != b && label[a] != label[b]) cc_link(label, a, b);
   }
 }
 
