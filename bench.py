@@ -51,7 +51,7 @@ L2_BYTES = 129 * 1024 * 1024
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--steps", type=int, default=30)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gpma", choices=["gpma", "reference"])
     ap.add_argument("--batch", type=int, default=1_000_000)
@@ -144,16 +144,22 @@ class ClockSampler:
                                       stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
+            t_end = time.perf_counter() + 5.0  # the sampler is running before the timed region starts
+            while not self.lines and time.perf_counter() < t_end:
+                time.sleep(0.005)
         except Exception:
             self.p = None
+        self.t0 = time.perf_counter()
         return self
 
     def _read(self):
         for line in self.p.stdout:
-            self.lines.append(line.strip())
+            self.lines.append((time.perf_counter(), line.strip()))
 
     def __exit__(self, *exc):
+        self.t1 = time.perf_counter()
         if self.p:
+            time.sleep(0.025)  # one more sample after the region
             self.p.terminate()
             try:
                 self.p.wait(timeout=5)
@@ -163,7 +169,10 @@ class ClockSampler:
     def summary(self):
         sm, mx, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for ln in self.lines:
+        # samples taken inside the region, and the first one after it
+        inside = [ln for t, ln in self.lines if self.t0 <= t <= self.t1]
+        after = [ln for t, ln in self.lines if t > self.t1][:1]
+        for ln in inside + after:
             f = [x.strip() for x in ln.split(",")]
             if len(f) < 9:
                 continue

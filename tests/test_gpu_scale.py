@@ -93,3 +93,23 @@ def test_chung_lu_learned_full_size():
         lg = g.layout().cpu().numpy().view(np.uint64)
         assert lg.size == lo.size and np.count_nonzero(lg != lo) == 0
         assert g.check() == 0
+
+
+@pytest.mark.parametrize("V", [1 << 24, (1 << 24) + 1])
+def test_pagerank_largest_bucketed_graph(V):
+    """2^24 vertices is the largest graph the bucketed PageRank pass takes (4096
+    buckets of 4096 heads: the bucket tables of the count and placement kernels at
+    their largest); one vertex more and the library takes the push pass.  Both give
+    the ranks of a handle forced onto the push pass, bit for bit, on an R-MAT
+    scale-24 stream of 2^22 samples held on the device."""
+    gp.build()
+    st = W.rmat_stream_device(24, 1 << 22, seed=5)
+    a, b = gp.Graph(V, leaf_size=64), gp.Graph(V, leaf_size=64, push_pagerank=True)
+    for g in (a, b):
+        g.update(st)
+    ra = a.pagerank(5, 0.85).cpu().numpy()
+    rb = b.pagerank(5, 0.85).cpu().numpy()
+    assert np.array_equal(ra.view(np.uint32), rb.view(np.uint32))
+    assert abs(float(ra.astype(np.float64).sum()) - 1.0) < 1e-3
+    a.status()
+    b.status()

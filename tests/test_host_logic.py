@@ -1,6 +1,8 @@
 """Host-side logic that needs no GPU: the synthetic workloads' promises (seeded,
 no repeats, windows slide over live edges), the leaf-size picker, and the
 binding's argument checks that fire before any device call."""
+import os
+
 import numpy as np
 import pytest
 
@@ -114,3 +116,24 @@ def test_serve_budget_split():
     assert 2 * 8 * keys + 4 * (1 << 24) * slots <= (100 << 20) + 4 * (1 << 24)  # at least one slot always
     keys, slots = S.Server.budget_split(0, 10)
     assert keys == 1024 and slots == 1
+
+
+def test_clock_summary_keeps_samples_of_the_timed_region():
+    """bench.py's clock record: only samples taken between the start and the end of
+    the timed region, plus the first one after it, count; a throttle reason seen
+    outside that window is not reported."""
+    import sys
+    sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+    import bench
+    c = bench.ClockSampler(0)
+    row = "0, {sm}, 2070, 900.0, 0x0, Not Active, Not Active, {thermal}, Not Active"
+    c.lines = [(0.5, row.format(sm=1200, thermal="Active")),   # before the region
+               (1.1, row.format(sm=2070, thermal="Not Active")),
+               (1.2, row.format(sm=2060, thermal="Not Active")),
+               (2.1, row.format(sm=2070, thermal="Not Active")),  # first one after
+               (2.2, row.format(sm=900, thermal="Active"))]
+    c.t0, c.t1 = 1.0, 2.0
+    s = c.summary()
+    assert s["samples"] == 3 and s["sm_mhz"] == 2070 and s["reasons"] == []
+    c.lines = []
+    assert c.summary()["reasons"] == ["unsampled"]
