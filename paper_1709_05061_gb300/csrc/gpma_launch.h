@@ -136,12 +136,12 @@ void launch_pr_apply(const Geo &g, float damping, float *rank, uint64_t *y, uint
 // (scan output, off[nb*G] = edges); scan_tmp >= scan_partials(nb * G); keys:
 // u64[edges] (<= C).  One iteration reads cf_in and writes cf_out (FP32 x/outdeg,
 // V each), the ranks when last, and dsum_out; partials >= nb * nparts.
-constexpr uint32_t kPbShift = 12, kPbMaxShift = 14, kPbThreads = 512;
+constexpr uint32_t kPbShift = 12, kPbMaxShift = 14;
 constexpr uint32_t kPbMaxBuckets = 4096;  // heads < kPbMaxBuckets << shift
-constexpr uint32_t kPbMaxChunks = 152 * 8, kPbTargetBlocks = 1024, kPbMaxParts = 8;
+constexpr uint32_t kPbMaxChunks = 152 * 8, kPbTargetBlocks = 512, kPbMaxParts = 8;
 constexpr uint32_t kPbTile = 8192, kPbPlaceThreads = 512;  // placement: slots per tile, threads
 struct PbPlan {
-  uint32_t shift, nb, G, nparts;  // 2^shift heads per bucket
+  uint32_t shift, nb, G, nparts, threads;  // 2^shift heads per bucket; threads per iteration block
   uint64_t chunk;  // slot pairs per chunk
 };
 PbPlan pb_plan(const Geo &g);

@@ -273,7 +273,8 @@ __device__ __forceinline__ uint32_t ld_cluster_u32(uint32_t addr) {
 // heads through distributed shared memory and applies the update there:
 // x'_v = (1-d)/V + d * (y_v + dangling/V), the next contribution x'_v/outdeg(v)
 // into cf_out, and the dangling mass of the next iteration by a grid sum.
-__global__ void __launch_bounds__(kPbThreads) k_pb_iter(const uint64_t *__restrict__ keys,
+template <uint32_t TPB>
+__global__ void __launch_bounds__(TPB) k_pb_iter(const uint64_t *__restrict__ keys,
                                                         const uint64_t *__restrict__ off, uint32_t G, uint32_t shift,
                                                         uint32_t nparts,
                                                         uint32_t V, float damping, const uint32_t *__restrict__ deg,
@@ -284,16 +285,16 @@ __global__ void __launch_bounds__(kPbThreads) k_pb_iter(const uint64_t *__restri
   const uint32_t bs = 1u << shift;
   uint32_t *lo = pb_tab, *hi = pb_tab + bs;
   const uint32_t b = blockIdx.x / nparts, q = blockIdx.x % nparts;  // q is the rank in the cluster
-  for (uint32_t i = threadIdx.x; i < bs; i += kPbThreads) lo[i] = hi[i] = 0;
+  for (uint32_t i = threadIdx.x; i < bs; i += TPB) lo[i] = hi[i] = 0;
   __syncthreads();
   const uint64_t e0 = off[(uint64_t)b * G], len = off[(uint64_t)(b + 1) * G] - e0;
   const uint64_t a = e0 + len * q / nparts, z = e0 + len * (q + 1) / nparts;
-  for (uint64_t i0 = a; i0 < z; i0 += 4 * kPbThreads) {
+  for (uint64_t i0 = a; i0 < z; i0 += 4 * TPB) {
     uint64_t k[4];
     float c[4];
 #pragma unroll
     for (int u = 0; u < 4; u++) {
-      const uint64_t i = i0 + u * kPbThreads + threadIdx.x;
+      const uint64_t i = i0 + u * TPB + threadIdx.x;
       k[u] = i < z ? __ldcs(keys + i) : kEmpty;
     }
 #pragma unroll
@@ -312,7 +313,7 @@ __global__ void __launch_bounds__(kPbThreads) k_pb_iter(const uint64_t *__restri
   const float dn = __fdiv_rn(fx_to_float(*dsum_in), (float)V);
   uint64_t dang = 0;
   const uint32_t h0 = q * bs / nparts, h1 = (q + 1) * bs / nparts;
-  for (uint32_t e = h0 + threadIdx.x; e < h1; e += kPbThreads) {
+  for (uint32_t e = h0 + threadIdx.x; e < h1; e += TPB) {
     uint64_t y = 0;
     for (uint32_t r = 0; r < nparts; r++)
       y += ((uint64_t)ld_cluster_u32(cluster_smem_addr(hi + e, r)) << 32) | ld_cluster_u32(cluster_smem_addr(lo + e, r));
@@ -367,6 +368,11 @@ PbPlan pb_plan(const Geo &g) {
   const uint32_t want = (kPbTargetBlocks + p.nb - 1) / p.nb;
   p.nparts = 1;
   while (p.nparts * 2 <= want && p.nparts * 2 <= kPbMaxParts) p.nparts *= 2;
+  // a bucket per block (many buckets): 1024 threads; a cluster per bucket: 512
+  // (measured: PageRank-20 at R-MAT scale 20, 2 blocks per bucket, 1.47 ms with 512
+  // threads against 1.68 with 1024 and 2.40 with 256; at scale 24, one block per
+  // bucket, 29.1 ms with 1024 against 31.0 with 512)
+  p.threads = p.nparts == 1 ? 1024 : 512;
   return p;
 }
 
@@ -392,12 +398,13 @@ void launch_pb_iter(const Geo &g, const PbPlan &p, const uint64_t *keys, const u
                     uint64_t *dsum_out, uint64_t *partials, unsigned *counter, cudaStream_t s) {
   static bool big = false;
   if (!big) {
-    cudaFuncSetAttribute(k_pb_iter, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(8u << kPbMaxShift));
+    cudaFuncSetAttribute(k_pb_iter<512>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(8u << kPbMaxShift));
+    cudaFuncSetAttribute(k_pb_iter<1024>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(8u << kPbMaxShift));
     big = true;
   }
   cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3(p.nb * p.nparts);
-  cfg.blockDim = dim3(kPbThreads);
+  cfg.blockDim = dim3(p.threads);
   cfg.dynamicSmemBytes = 8u << p.shift;
   cfg.stream = s;
   cudaLaunchAttribute at[1];
@@ -408,7 +415,8 @@ void launch_pb_iter(const Geo &g, const PbPlan &p, const uint64_t *keys, const u
   cfg.attrs = at;
   cfg.numAttrs = 1;
   note_launch();
-  cudaLaunchKernelEx(&cfg, k_pb_iter, keys, off, p.G, p.shift, p.nparts, g.V, damping, (const uint32_t *)g.deg, cf_in, cf_out,
+  auto kern = p.threads == 1024 ? k_pb_iter<1024> : k_pb_iter<512>;
+  cudaLaunchKernelEx(&cfg, kern, keys, off, p.G, p.shift, p.nparts, g.V, damping, (const uint32_t *)g.deg, cf_in, cf_out,
                      rank, last ? 1 : 0, dsum_in, dsum_out, partials, counter);
 }
 
