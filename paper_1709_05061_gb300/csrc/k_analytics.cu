@@ -634,10 +634,10 @@ int run_bfs(const Geo &g, uint32_t src, int32_t *depth, uint32_t *q0, uint32_t *
   cudaMemsetAsync(err, 0, sizeof(uint32_t), s);
   note_launch();
   k_bfs_setup<<<1, 1, 0, s>>>(depth, src, q0, cnt, bar);
-  // frontiers of at least V/128 vertices take the full pass (measured at R-MAT scale 20,
-  // three sources: 0.435 ms per call against 0.456 at V/32 and 0.583 at V/8; at scale
-  // 24 V/32 to V/128 are equal, 4.06 ms, and V/8 takes 7.6 ms)
-  const uint32_t scan_from = g.V / 128 > 64 ? g.V / 128 : 64;
+  // frontiers of at least V/32 vertices take the full pass (measured at R-MAT scale 20:
+  // V/8 0.583 ms per call, V/16 to V/128 within 5% of each other, the order depending on
+  // the source; at scale 24 V/32 to V/128 are equal, 4.06 ms, and V/8 takes 7.6 ms)
+  const uint32_t scan_from = g.V / 32 > 64 ? g.V / 32 : 64;
   Geo gg = g;
   void *args[] = {(void *)&gg, (void *)&depth, (void *)&q0,  (void *)&q1,
                   (void *)&q2, (void *)&cnt,   (void *)&bar, (void *)&err, (void *)&scan_from};
