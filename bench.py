@@ -705,7 +705,8 @@ def main():
         if rank != 0:
             return 0
         stream = make_stream(a, 0, reference=True)
-        r = run_oracle(a, stream, a.steps, skip=a.warmup)
+        # every step is a whole oracle step (~2 s on one core); at most ~150 s of timed work
+        r = run_oracle(a, stream, a.steps, skip=min(a.warmup, 3), max_seconds=150.0)
         line = {"metric": METRIC, "value": r["value"], "unit": "edge updates/s", "n_gpus": a.gpus,
                 "steps": a.steps, "warmup": a.warmup, "ms_per_step": 1e3 * r["seconds"] / a.steps,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64",
