@@ -155,17 +155,17 @@ __global__ void k_pr_apply(uint32_t V, float damping, const uint32_t *__restrict
 
 // ---- bucketed PageRank pass ----------------------------------------------------------------------
 // Once per call the stored edges are copied into buckets by head (v >> 12, a
-// counting sort by chunk: per-chunk bucket counts, a scan, a placement pass).
-// Every iteration then gives each bucket a cluster of blocks; each block sums the
-// contributions of its share of the bucket into a 4096-entry table in shared
-// memory, and the cluster adds its tables through distributed shared memory and
-// applies the update.  The random reductions of the push pass become
-// shared-memory atomics;
-// the copy keeps the chunks in slot order, so within a bucket the tails (and
-// the contribution loads) move forward through the array.  Each 64-bit sum is kept as two 32-bit words: the
-// low word's atomic returns the old value, and a carry out of it is added to the
-// high word with the high half, so the sum is exact modulo 2^64 whatever the
-// order, as in the push pass.
+// counting sort by chunk of the array: per-chunk bucket counts, a scan, a
+// placement pass).  Every iteration then gives each bucket a cluster of blocks;
+// each block sums the contributions of its share of the bucket into a 4096-entry
+// table in shared memory, and the cluster adds its tables through distributed
+// shared memory and applies the update.  The random reductions of the push pass
+// become shared-memory atomics.  The copy keeps the chunks in slot order, so
+// within a bucket the tails (and the contribution loads) move forward through
+// the array.  Each 64-bit sum is kept as two 32-bit words: the low word's atomic
+// returns the old value, and a carry out of it is added to the high word with
+// the high half, so the sum is exact modulo 2^64 whatever the order, as in the
+// push pass.
 __global__ void __launch_bounds__(256) k_pb_count(const ulonglong2 *__restrict__ s2, uint64_t npairs, uint64_t chunk,
                                                   uint32_t nb, uint32_t shift, uint32_t *__restrict__ cnt) {
   __shared__ uint32_t hist[kPbMaxBuckets];
