@@ -140,6 +140,7 @@ constexpr uint32_t kPbShift = 12, kPbMaxShift = 14;
 constexpr uint32_t kPbMaxBuckets = 4096;  // heads < kPbMaxBuckets << shift
 constexpr uint32_t kPbMaxChunks = 152 * 8, kPbTargetBlocks = 512, kPbMaxParts = 8;
 constexpr uint32_t kPbTile = 8192, kPbPlaceThreads = 512;  // placement: slots per tile, threads
+constexpr uint32_t kPbStageMax = 512;  // more buckets than this: placement without staging
 struct PbPlan {
   uint32_t shift, nb, G, nparts, threads;  // 2^shift heads per bucket; threads per iteration block
   uint64_t chunk;  // slot pairs per chunk

@@ -248,6 +248,34 @@ __global__ void __launch_bounds__(kPbPlaceThreads) k_pb_place(const ulonglong2 *
   }
 }
 
+// Placement without staging, for many buckets (a tile then holds about one edge
+// per bucket, so staging would not group the writes): each edge goes straight to
+// its bucket's next free position of this chunk.
+__global__ void __launch_bounds__(256) k_pb_place_direct(const ulonglong2 *__restrict__ s2, uint64_t npairs,
+                                                         uint64_t chunk, uint32_t nb, uint32_t shift,
+                                                         const uint64_t *__restrict__ off,
+                                                         uint64_t *__restrict__ keys) {
+  __shared__ uint32_t cur[kPbMaxBuckets];
+  __shared__ uint64_t base[kPbMaxBuckets];
+  for (uint32_t b = threadIdx.x; b < nb; b += blockDim.x) {
+    cur[b] = 0;
+    base[b] = off[(uint64_t)b * gridDim.x + blockIdx.x];
+  }
+  __syncthreads();
+  const uint64_t p0 = (uint64_t)blockIdx.x * chunk, p1 = p0 + chunk < npairs ? p0 + chunk : npairs;
+  for (uint64_t p = p0 + threadIdx.x; p < p1; p += blockDim.x) {
+    const ulonglong2 k = __ldcs(s2 + p);
+    if (k.x != kEmpty && !is_guard(k.x)) {
+      const uint32_t b = (uint32_t)k.x >> shift;
+      keys[base[b] + atomicAdd(&cur[b], 1u)] = k.x;
+    }
+    if (k.y != kEmpty && !is_guard(k.y)) {
+      const uint32_t b = (uint32_t)k.y >> shift;
+      keys[base[b] + atomicAdd(&cur[b], 1u)] = k.y;
+    }
+  }
+}
+
 // Cluster primitives (sm_90+): a barrier over the blocks of a cluster that also
 // orders their shared-memory writes, and 32-bit loads from another block's shared
 // memory (distributed shared memory).
@@ -382,6 +410,11 @@ void launch_pb_build(const Geo &g, const PbPlan &p, uint32_t *cnt, uint64_t *off
   note_launch();
   k_pb_count<<<p.G, 256, 0, s>>>(s2, g.C >> 1, p.chunk, p.nb, p.shift, cnt);
   launch_scan_u32_u64(cnt, off, (uint64_t)p.nb * p.G, scan_tmp, s);
+  if (p.nb > kPbStageMax) {
+    note_launch();
+    k_pb_place_direct<<<p.G, 256, 0, s>>>(s2, g.C >> 1, p.chunk, p.nb, p.shift, off, keys);
+    return;
+  }
   const size_t smem = sizeof(uint64_t) * kPbTile + sizeof(uint32_t) * (2 * p.nb + 1);
   static bool big = false;
   if (!big) {
