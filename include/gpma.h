@@ -21,6 +21,12 @@
  *    ABI.  GPMA_ETIMEOUT and GPMA_EDEVICE poison the handle: every later call
  *    on it returns the same code.  A handle is not thread safe; distinct
  *    handles are independent.
+ *  - calls on one handle issued from one thread on DIFFERENT streams: the
+ *    caller orders them with events, except that gpma_bfs, gpma_cc and
+ *    gpma_pagerank only read the array and keep separate buffers, so one of
+ *    each may run concurrently on separate streams once the first call of each
+ *    kind has completed (first calls allocate).  Updates, exports and two calls
+ *    of the same kind must not overlap.
  */
 #ifndef GPMA_H
 #define GPMA_H
