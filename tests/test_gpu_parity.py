@@ -351,7 +351,7 @@ def test_pagerank_bucketed_equals_push(V, n_edges, seed):
     for g in (gb, gpush):
         g.update(dev(stream), None)
     o.update(stream)
-    for it in (1, 3, 20):
+    for it in (0, 1, 3, 20):
         a = gb.pagerank(it, 0.85).cpu().numpy()
         b = gpush.pagerank(it, 0.85).cpu().numpy()
         assert np.array_equal(a.view(np.uint32), b.view(np.uint32)), it
