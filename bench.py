@@ -353,6 +353,17 @@ def run_gpu(a, stream, rank, world, dist):
     }
     if prof["pr_bucket"]["count"]:
         out["roofline"]["bucketing_ms_per_call"] = prof["pr_bucket"]["ms"] / prof["pr_bucket"]["count"]
+    # the queries in edge terms: stored edges times PageRank iterations per second of the
+    # PageRank call, and stored edges per second of one BFS / CC call (device time of the
+    # calls inside the timed region, where BFS and CC overlap PageRank)
+    per_call = {k: prof[k]["ms"] / max(prof[k]["count"], 1) for k in ("pagerank", "bfs", "cc")}
+    out["analytics"] = {
+        "pagerank_ms": per_call["pagerank"], "bfs_ms": per_call["bfs"], "cc_ms": per_call["cc"],
+        "pagerank_edge_iters_per_s": out["n_edges"] * PR_ITERS / (per_call["pagerank"] * 1e-3)
+        if per_call["pagerank"] else None,
+        "bfs_edges_per_s": out["n_edges"] / (per_call["bfs"] * 1e-3) if per_call["bfs"] else None,
+        "cc_edges_per_s": out["n_edges"] / (per_call["cc"] * 1e-3) if per_call["cc"] else None,
+    }
     # Inside the step BFS and CC share the GPU with PageRank, which stretches its launches;
     # the same kernel timed once more after the timed region with the GPU to itself:
     torch.cuda.synchronize()
@@ -736,7 +747,7 @@ def main():
                 "vs_baseline": None, "dtype": "u64", "data": "synthetic", "config": cfg,
                 "gpu_launches": out["launches"], "roofline": out["roofline"], "clocks": out["clocks"],
                 "phases_ms_per_step": {k: v["ms"] / a.steps for k, v in out["profile"].items()},
-                "capacity_slots": out["capacity"]}
+                "capacity_slots": out["capacity"], "analytics": out["analytics"]}
         if "e2e" in out:
             line["e2e"] = out["e2e"]
         if "sweep" in out:
