@@ -287,7 +287,13 @@ def gpma_launch_count() -> int:
 
 # ---- convenience object over the same calls -------------------------------------------------
 class Graph:
-    """A GPMA+ array on the current CUDA device (owns one libgpma handle)."""
+    """A GPMA+ array on the current CUDA device (owns one libgpma handle).
+
+    Flags (include/gpma.h): ``raw_keys`` (opaque keys, no guards or queries),
+    ``plain_search`` (binary leaf search only), ``dual`` (deletion as the dual of
+    insertion), ``push_pagerank`` (PageRank by the push pass instead of the bucketed
+    pass; same ranks).  Extra keywords ``tau0``, ``tauh``, ``rho0``, ``rhoh`` set the
+    density bounds in whole percent."""
 
     def __init__(self, n_vertices: int, leaf_size: int = 64, raw_keys: bool = False, plain_search: bool = False,
                  dual: bool = False, push_pagerank: bool = False, stream=None, **dens):
