@@ -37,6 +37,9 @@ SCALE, WINDOW, LEAF = 20, 16_000_000, 64
 SWEEP = (100, 1000, 10_000, 100_000, 1_000_000)
 SWEEP_WARM, SWEEP_TIMED = 3, 10
 PR_ITERS, DAMPING = 20, 0.85
+# steps run again after the timed region with per-phase events on (phase times,
+# the dominant kernel's per-launch time); the timed region itself records none
+PROFILED_STEPS = 10
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch of the PageRank sum
 # pass on the default workload (R-MAT scale 20, 16M-edge window, 2^25 slots), from one ncu
 # capture of each kernel as it stands: push pass 285,246,720 read + 3,048,448 written;
@@ -70,6 +73,10 @@ def parse():
     ap.add_argument("--serve-requests", type=int, default=1500)
     ap.add_argument("--many-study", action="store_true",
                     help="only time the batched many-graph update (64 uneven R-MAT graphs)")
+    ap.add_argument("--profile-case", choices=["pr", "update", "bfs", "cc"],
+                    help="load the window, run one call of this kind --repeat times and exit (a small, "
+                         "self-contained run for ncu; GPMA_NO_GRAPHS=1 launches an update's kernels directly)")
+    ap.add_argument("--repeat", type=int, default=1)
     return ap.parse_args()
 
 
@@ -93,6 +100,7 @@ def stream_needed(a, reference: bool):
     n = a.window + half * (a.warmup + a.steps)
     if reference:
         return n
+    n += half * PROFILED_STEPS
     if not a.no_e2e:
         n += half * (a.warmup + a.steps)
     if not a.no_sweep:
@@ -266,7 +274,7 @@ def run_gpu(a, stream, rank, world, dist):
     # the sweep slid only rank 0's window; every rank now continues from its own state
 
     ins_all, del_all = [], []
-    for _ in range(a.warmup + a.steps):
+    for _ in range(a.warmup + a.steps + PROFILED_STEPS):
         ins, dels = win.slide(half)
         ins_all.append(to_dev(ins))
         del_all.append(to_dev(dels))
@@ -305,8 +313,6 @@ def run_gpu(a, stream, rank, world, dist):
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
-    gp.gpma_profile_read(g.h, reset=True)
-    gp.gpma_profile_enable(g.h, True)
     l0 = gp.gpma_launch_count()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     with ClockSampler(torch.cuda.current_device()) as clk:
@@ -319,9 +325,21 @@ def run_gpu(a, stream, rank, world, dist):
         dist.barrier()
     torch.cuda.synchronize()
     launches = gp.gpma_launch_count() - l0
+    gp.gpma_status(g.h)
+    # the same steps again with an event pair around every phase and PageRank launch
+    # (the timed region above records none): phase times and per-launch kernel times
+    gp.gpma_profile_read(g.h, reset=True)
+    gp.gpma_profile_enable(g.h, True)
+    p0 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    p0[0].record()
+    for i in range(a.warmup + a.steps, a.warmup + a.steps + PROFILED_STEPS):
+        step(i)
+    p0[1].record()
+    torch.cuda.synchronize()
     gp.gpma_profile_enable(g.h, False)
     prof = gp.gpma_profile_read(g.h, reset=True)
     gp.gpma_status(g.h)
+    out["profiled_ms_per_step"] = p0[0].elapsed_time(p0[1]) / PROFILED_STEPS
     ms = e0.elapsed_time(e1)
     ms = max_over_ranks(ms, dist, dev)
     out["ms_total"] = ms
@@ -349,7 +367,9 @@ def run_gpu(a, stream, rank, world, dist):
         "frac": alg_pr / (per_launch_ms * 1e-3) / 1e9 / peak,
         "traffic": PR_PASS_TRAFFIC[kname] if (a.scale, a.window) == (SCALE, WINDOW) else None,
         "alg_bytes_per_launch": alg_pr, "launch_ms": per_launch_ms,
-        "share_of_step": pr["ms"] / ms if ms else None,
+        "share_of_step": pr["ms"] / (out["profiled_ms_per_step"] * PROFILED_STEPS),
+        "timing": f"per-launch CUDA events on the launching stream over {PROFILED_STEPS} steps run right "
+                  f"after the timed region (the timed region itself records no events)",
     }
     if prof["pr_bucket"]["count"]:
         out["roofline"]["bucketing_ms_per_call"] = prof["pr_bucket"]["ms"] / prof["pr_bucket"]["count"]
@@ -663,6 +683,46 @@ def serve_study(a):
     return out
 
 
+# ---- small runs for ncu --------------------------------------------------------------------------------
+def profile_case(a):
+    """Load the window (R-MAT scale --scale, --window edges: 268 MB at the defaults,
+    larger than the L2, a few GB on the device in all), apply one batch of --batch
+    updates (graph capture, work arrays), then run one call of the case --repeat
+    times, so that ncu can capture a handful of launches with few before them."""
+    import torch
+    import paper_1709_05061_gb300 as gp
+    from paper_1709_05061_gb300 import workloads as W
+    gp.build()
+    torch.cuda.set_device(0)
+    half = a.batch // 2
+    stream = W.rmat_stream(a.scale, a.window + half * (a.repeat + 1), seed=a.seed, samples=(1 << a.scale) * 16)
+    win = W.SlidingWindow(stream, a.window)
+
+    def dev(x):
+        return torch.from_numpy(np.ascontiguousarray(x).view(np.int64)).cuda()
+    g = gp.Graph(1 << a.scale, leaf_size=LEAF, push_pagerank=a.push_pagerank)
+    g.update(dev(win.initial), None)
+    ins, dels = win.slide(half)
+    g.update(dev(ins), dev(dels))
+    g.status()
+    torch.cuda.synchronize()
+    for _ in range(a.repeat):
+        if a.profile_case == "pr":
+            g.pagerank(PR_ITERS, DAMPING)
+        elif a.profile_case == "update":
+            ins, dels = win.slide(half)
+            g.update(dev(ins), dev(dels))
+        elif a.profile_case == "bfs":
+            g.bfs(bfs_source(stream))
+        else:
+            g.cc()
+    g.status()
+    torch.cuda.synchronize()
+    out = {"profile_case": a.profile_case, "capacity": g.capacity, "check": g.check()}
+    g.close()
+    return out
+
+
 # ---- the oracle (CPU) --------------------------------------------------------------------------------
 def run_oracle(a, stream, steps, max_seconds=None, skip=0):
     import oracle
@@ -702,6 +762,9 @@ def main():
     local = int(os.environ.get("LOCAL_RANK", "0"))
     cfg = workload_config(a, world)
 
+    if a.profile_case:
+        print(json.dumps(profile_case(a)), flush=True)
+        return 0
     if a.learned_study:
         print(json.dumps({"learned_study": learned_study(a)}), flush=True)
         return 0
@@ -746,7 +809,8 @@ def main():
                 "warmup": a.warmup, "ms_per_step": ms / a.steps, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "u64", "data": "synthetic", "config": cfg,
                 "gpu_launches": out["launches"], "roofline": out["roofline"], "clocks": out["clocks"],
-                "phases_ms_per_step": {k: v["ms"] / a.steps for k, v in out["profile"].items()},
+                "phases_ms_per_step": {k: v["ms"] / PROFILED_STEPS for k, v in out["profile"].items()},
+                "profiled_ms_per_step": out["profiled_ms_per_step"],
                 "capacity_slots": out["capacity"], "analytics": out["analytics"]}
         if "e2e" in out:
             line["e2e"] = out["e2e"]

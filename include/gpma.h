@@ -42,7 +42,9 @@ typedef struct gpma *gpma_t;
 
 #define GPMA_OK 0
 #define GPMA_EINVAL 1   /* bad argument or key; the batch was not applied */
-#define GPMA_ENOMEM 2   /* an allocation failed; the handle is unchanged */
+#define GPMA_ENOMEM 2   /* an allocation failed; the handle is unchanged, except when the
+                           new array of a root resize was refused (the batch had begun
+                           to apply): the handle is then poisoned */
 #define GPMA_ECAP 3     /* output buffer too small; *n_out holds the size needed */
 #define GPMA_ETIMEOUT 4 /* a bounded device-side wait gave up (handle poisoned) */
 #define GPMA_EDEVICE 5  /* a CUDA runtime error (handle poisoned) */
@@ -66,7 +68,7 @@ typedef struct gpma *gpma_t;
 
 /* Create-time parameters; a zero field takes the default.  Densities are whole
  * percentages: tau_0 (leaf upper bound, default 92), tau_h (root upper bound, 80),
- * rho_0 (8) and rho_h (40), the running example of Sec. 4.1 / Fig. 2.  The
+ * rho_0 (8) and rho_h (40), the running example of Sec. 4.1 / Fig. 3.  The
  * per-level bound is the largest count n with n < tau_i * L * 2^i, tau_i linear
  * in the level between tau_0 and tau_h, clamped to twice the child bound. */
 typedef struct {
@@ -172,9 +174,12 @@ int gpma_cc(gpma_t h, uint32_t *d_label, void *stream);
  * the slot array).  Stream-ordered. */
 int gpma_pagerank(gpma_t h, uint32_t iters, float damping, float *d_rank, void *stream);
 
-/* Copy the stored edges (no guards) in ascending key order into d_out[cap];
- * *n_out = number of edges.  GPMA_ECAP (nothing written past cap) if cap is too
- * small.  Waits for the stream. */
+/* Copy the stored edges (no guards) in ascending key order into d_out[cap]:
+ * the edge set a query of the stream model sees (Sec. 3, "Graph Streams" and the
+ * query buffer of Fig. 1), read off the gapped array in slot order.  *n_out =
+ * number of edges.  GPMA_ECAP (nothing written past cap) if cap is too small;
+ * GPMA_ETIMEOUT (handle poisoned) if a look-back wait of the compaction gave up.
+ * Waits for the stream. */
 int gpma_export_sorted(gpma_t h, uint64_t *d_out, uint64_t cap, uint64_t *n_out, void *stream);
 
 /* Same result as gpma_export_sorted, but the call allocates no device memory:
@@ -182,12 +187,14 @@ int gpma_export_sorted(gpma_t h, uint64_t *d_out, uint64_t cap, uint64_t *n_out,
  * while they query the graph, for instance a serving loop that has handed all
  * free device memory to its own pool, or latency-bound code that cannot accept
  * the synchronisation an allocation may bring.  The scratch words of its
- * single-pass compaction live in one fixed array inside the library (1 MiB per
- * GPU, kept until the process exits), so the array may hold at most 2^27 slots
+ * single-pass compaction live in one fixed array inside the library (about
+ * 512 KiB per GPU, kept until the process exits), so the array may hold at most 2^27 slots
  * (GPMA_EINVAL otherwise).  The first call on each device looks up that array's
  * device address; make that first call before any stream capture.  All calls
  * share the array: calls that overlap on the GPU (other streams, other handles)
- * race and must not be issued.  Waits for the stream. */
+ * race and must not be issued.  A look-back wait that gave up returns
+ * GPMA_ETIMEOUT and a CUDA error GPMA_EDEVICE; both poison the handle.  Waits
+ * for the stream. */
 int gpma_export_sorted_noalloc(gpma_t h, uint64_t *d_out, uint64_t cap, uint64_t *n_out, void *stream);
 
 /* CSR view (Sec. 4.2, Fig. 5): d_rowptr[V+1] row offsets, d_col[cap] column ids
@@ -195,13 +202,17 @@ int gpma_export_sorted_noalloc(gpma_t h, uint64_t *d_out, uint64_t cap, uint64_t
 int gpma_export_csr(gpma_t h, uint64_t *d_rowptr, uint32_t *d_col, uint64_t cap,
                     uint64_t *n_out, void *stream);
 
-/* Copy the raw array (EMPTY slots and guards included) into d_slots[cap];
- * *capacity_out = number of slots.  GPMA_ECAP if cap is too small. */
+/* Copy the raw array (EMPTY slots and guards included) into d_slots[cap]: the
+ * packed memory array itself, leaf segments of L slots with their gaps (Sec. 4.1,
+ * Fig. 3; guards as in Sec. 4.2, Fig. 5).  *capacity_out = number of slots.
+ * GPMA_ECAP if cap is too small. */
 int gpma_export_layout(gpma_t h, uint64_t *d_slots, uint64_t cap, uint64_t *capacity_out,
                        void *stream);
 
 /* Replace the array with d_slots[capacity] (capacity = L * 2^k; valid keys
- * strictly increasing; in graph mode one guard per vertex).  Used to restore a
+ * strictly increasing; in graph mode one guard per vertex): a layout of the
+ * packed memory array of Sec. 4.1 as gpma_export_layout writes it, every leaf
+ * within its bound and the CSR guards of Sec. 4.2 in place.  Used to restore a
  * snapshot and by tests.  GPMA_EINVAL if the capacity is not L * 2^k or the
  * layout fails the device checker (the handle is then unchanged). Waits. */
 int gpma_import_layout(gpma_t h, const uint64_t *d_slots, uint64_t capacity, void *stream);
@@ -209,10 +220,13 @@ int gpma_import_layout(gpma_t h, const uint64_t *d_slots, uint64_t capacity, voi
 /* d_row_end[V] = slot index of the guard of each vertex.  Stream-ordered. */
 int gpma_row_end(gpma_t h, uint32_t *d_row_end, void *stream);
 
-/* Number of stored edges (guards excluded; raw mode: keys).  Waits. */
+/* Number of stored edges (guards excluded; raw mode: keys): |E| of the graph
+ * the stream has built so far (Sec. 3).  Waits. */
 int gpma_num_edges(gpma_t h, uint64_t *out, void *stream);
 
-/* Current number of slots (L * 2^h). */
+/* Current number of slots, L * 2^h: the capacity of the root segment, which
+ * doubles when the root exceeds its upper density bound (Sec. 4.1, and the root
+ * case of Algorithm "GPMA+ Segment-Oriented Insertion", Sec. 5.2). */
 int gpma_capacity(gpma_t h, uint64_t *out);
 
 /* Device-side consistency check of the array and its indexes.  *code = 0 when
@@ -221,6 +235,16 @@ int gpma_capacity(gpma_t h, uint64_t *out);
  * 16 a merge mark was left set, 32 the total count is stale, 64 an out-degree is
  * stale, 128 a leaf has a hole (GPMA_DUAL_DELETE only).  Waits. */
 int gpma_check(gpma_t h, uint32_t *code, void *stream);
+
+/* Bound every device-side wait of this handle (look-back of the single-pass
+ * sorts, scans and exports; grid barriers of gpma_bfs) to `polls` polls of the
+ * awaited word; 0 restores the built-in limits (about a second).  A wait that
+ * runs out makes its kernel return; the call (or the next gpma_status, for calls
+ * that return before the work ends) reports GPMA_ETIMEOUT and poisons the handle.
+ * The paper has no counterpart: this is failure detection for callers that would
+ * rather give up than wait.  Stream-ordered: calls enqueued later on `stream`
+ * use the new limit. */
+int gpma_set_wait_limit(gpma_t h, uint32_t polls, void *stream);
 
 /* ---- measurement ------------------------------------------------------------
  * Optional per-phase timing.  While enabled, every call records a pair of CUDA

@@ -8,11 +8,11 @@
  *
  * Readings taken where the paper is silent, ambiguous or garbled (each one is
  * also used by the CUDA library, which implements it independently):
- *  T  thresholds (Sec. 4.1, Fig. 2 table): tau_i and rho_i interpolate
+ *  T  thresholds (Sec. 4.1, Fig. 3 table): tau_i and rho_i interpolate
  *     linearly between the leaf (height 0) and the root (height h) in exact
  *     integer hundredths; max_i is the largest count n with n < tau_i * c_i,
  *     clamped to 2 * max_{i-1}; min_i = floor(rho_i * c_i) + 1 clamped to
- *     2 * min_{i-1}.  With L=4, h=3 this reproduces the Fig. 2 table row for
+ *     2 * min_{i-1}.  With L=4, h=3 this reproduces the Fig. 3 table row for
  *     row.  h = 0 uses tau_0 / rho_0.
  *  R1 inputs: src, dst < n_vertices (RAW mode: key < 2^63); a bad key rejects
  *     the whole batch and nothing changes.

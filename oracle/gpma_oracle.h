@@ -8,7 +8,7 @@
  * the two share no source, header, table or helper.
  *
  * Every routine follows the paper step by step in its own order:
- *   - thresholds: Sec. 4.1 "Background of PMA" and the Fig. 2 table;
+ *   - thresholds: Sec. 4.1 "Background of PMA" and the Fig. 3 table;
  *   - batch update: Algorithm "GPMA+ Segment-Oriented Insertion" (Sec. 5.2),
  *     with lazy deletion (Sec. 6.1, "Maintaining Dynamic Graph");
  *   - CSR with guard entries: Sec. 4.2, Example 4 / Fig. 5;

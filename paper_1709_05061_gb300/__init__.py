@@ -53,6 +53,55 @@ class gpma_stats(C.Structure):
         return d
 
 
+_ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p, C.c_void_p)
+_FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p, C.c_void_p)
+
+
+class gpma_allocator(C.Structure):
+    _fields_ = [("alloc", _ALLOC_FN), ("free", _FREE_FN), ("ctx", C.c_void_p)]
+
+
+class Allocator:
+    """Device memory of a handle from two Python callables (the ``gpma_allocator``
+    of include/gpma.h): ``alloc(nbytes, stream) -> int`` returns a device pointer,
+    0 on failure; ``free(ptr, stream)`` releases one.  ``stream`` is the call's
+    cudaStream_t as an int (0 = the legacy default stream).  Keep the object alive
+    as long as the handle (``Graph`` does)."""
+
+    def __init__(self, alloc, free):
+        def _a(nbytes, stream, ctx):
+            try:
+                return int(alloc(int(nbytes), int(stream or 0)) or 0) or None
+            except Exception:  # an exception must not cross the C ABI: report a failed allocation
+                return None
+
+        def _f(ptr, stream, ctx):
+            try:
+                free(int(ptr or 0), int(stream or 0))
+            except Exception:
+                pass
+
+        self._cb = (_ALLOC_FN(_a), _FREE_FN(_f))
+        self.struct = gpma_allocator(self._cb[0], self._cb[1], None)
+
+
+def torch_allocator() -> Allocator:
+    """An Allocator over torch's caching allocator (library memory then shows up
+    in torch's memory statistics and is reused from its pool)."""
+    torch = _torch()
+
+    def alloc(nbytes, stream):
+        try:
+            return torch.cuda.caching_allocator_alloc(nbytes, stream=stream)
+        except RuntimeError:  # torch's out-of-memory error
+            return 0
+
+    def free(ptr, stream):
+        torch.cuda.caching_allocator_delete(ptr)
+
+    return Allocator(alloc, free)
+
+
 GPMA_PROF_NAMES = ("sort", "leaf", "escalate", "resize", "pr_scatter", "pagerank", "bfs", "cc", "update",
                    "pr_bucket")
 GPMA_PROF_N = len(GPMA_PROF_NAMES)
@@ -86,7 +135,7 @@ def lib():
         vp, u32, u64, i = C.c_void_p, C.c_uint32, C.c_uint64, C.c_int
         P = C.POINTER
         sig = {
-            "gpma_create": ([u32, P(gpma_params), vp, vp, P(vp)], i),
+            "gpma_create": ([u32, P(gpma_params), P(gpma_allocator), vp, P(vp)], i),
             "gpma_destroy": ([vp], i),
             "gpma_update_batch": ([vp, vp, u64, vp, u64, vp, P(gpma_stats)], i),
             "gpma_status": ([vp, vp], i),
@@ -107,6 +156,7 @@ def lib():
             "gpma_profile_enable": ([vp, i], i),
             "gpma_profile_read": ([vp, P(gpma_profile), i], i),
             "gpma_launch_count": ([], u64),
+            "gpma_set_wait_limit": ([vp, u32, vp], i),
         }
         for name, (args, res) in sig.items():
             f = getattr(l, name)
@@ -149,12 +199,13 @@ def _check(rc: int, where: str):
 # ---- the C entry points, one to one --------------------------------------------------------
 def gpma_create(n_vertices: int, leaf_size: int = 64, tau0: int = 92, tauh: int = 80, rho0: int = 8,
                 rhoh: int = 40, raw_keys: bool = False, plain_search: bool = False, dual: bool = False,
-                push_pagerank: bool = False, stream=None) -> int:
+                push_pagerank: bool = False, stream=None, allocator: "Allocator | None" = None) -> int:
     flags = ((GPMA_RAW_KEYS if raw_keys else 0) | (GPMA_PLAIN_SEARCH if plain_search else 0) |
              (GPMA_DUAL_DELETE if dual else 0) | (GPMA_PUSH_PAGERANK if push_pagerank else 0))
     p = gpma_params(leaf_size, tau0, tauh, rho0, rhoh, flags)
     h = C.c_void_p()
-    _check(lib().gpma_create(n_vertices, C.byref(p), None, _stream(stream), C.byref(h)), "gpma_create")
+    a = C.byref(allocator.struct) if allocator is not None else None
+    _check(lib().gpma_create(n_vertices, C.byref(p), a, _stream(stream), C.byref(h)), "gpma_create")
     return h.value
 
 
@@ -267,6 +318,10 @@ def gpma_check(h: int, stream=None) -> int:
     return c.value
 
 
+def gpma_set_wait_limit(h: int, polls: int, stream=None):
+    _check(lib().gpma_set_wait_limit(C.c_void_p(h), polls, _stream(stream)), "gpma_set_wait_limit")
+
+
 def gpma_strerror(code: int) -> str:
     return lib().gpma_strerror(code).decode()
 
@@ -293,14 +348,19 @@ class Graph:
     ``plain_search`` (binary leaf search only), ``dual`` (deletion as the dual of
     insertion), ``push_pagerank`` (PageRank by the push pass instead of the bucketed
     pass; same ranks).  Extra keywords ``tau0``, ``tauh``, ``rho0``, ``rhoh`` set the
-    density bounds in whole percent."""
+    density bounds in whole percent.  ``allocator`` (an ``Allocator``, e.g.
+    ``torch_allocator()``) supplies the library's device memory; default
+    cudaMallocAsync."""
 
     def __init__(self, n_vertices: int, leaf_size: int = 64, raw_keys: bool = False, plain_search: bool = False,
-                 dual: bool = False, push_pagerank: bool = False, stream=None, **dens):
+                 dual: bool = False, push_pagerank: bool = False, stream=None, allocator: Allocator | None = None,
+                 **dens):
         self.n_vertices = 0 if raw_keys else int(n_vertices)
         self.raw = raw_keys
+        self.allocator = allocator  # the callbacks must outlive the handle
+        self.h = None
         self.h = gpma_create(n_vertices, leaf_size=leaf_size, raw_keys=raw_keys, plain_search=plain_search,
-                             dual=dual, push_pagerank=push_pagerank, stream=stream, **dens)
+                             dual=dual, push_pagerank=push_pagerank, stream=stream, allocator=allocator, **dens)
 
     def close(self):
         if getattr(self, "h", None):

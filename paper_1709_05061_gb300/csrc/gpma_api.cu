@@ -25,7 +25,7 @@ void unnote_launches(uint64_t k) { g_launches.fetch_sub(k, std::memory_order_rel
 
 namespace {
 
-// Threshold reading (Sec. 4.1 and the Fig. 2 table): tau_i and rho_i interpolate
+// Threshold reading (Sec. 4.1 and the Fig. 3 table): tau_i and rho_i interpolate
 // linearly in the level between leaf and root in whole hundredths; max_i is the
 // largest count below tau_i * L * 2^i, clamped to twice the level below.
 void level_bounds(uint32_t L, uint32_t h, uint32_t t0, uint32_t th, uint64_t *mx) {
@@ -404,6 +404,8 @@ int ensure_merge_scratch(gpma *h, cudaStream_t s) {
 }
 
 __global__ void k_finish(Ctl *ctl) { ctl->sticky |= ctl->err; }
+
+__global__ void k_set_wait_limit(Ctl *ctl, uint32_t polls) { ctl->spin_limit = polls; }
 
 __global__ void k_make_guards(uint64_t *g, uint32_t V) {
   for (uint32_t u = blockIdx.x * blockDim.x + threadIdx.x; u < V; u += gridDim.x * blockDim.x)
@@ -895,6 +897,11 @@ HandleView handle_view(gpma_t h, cudaStream_t s) {
   v.poisoned = h->poisoned;
   return v;
 }
+int poison_handle(gpma_t h, int code) { return poison(h, code); }
+int export_status(gpma_t h, uint32_t err) {
+  const int st = err_to_status(err);
+  return st ? poison(h, st) : GPMA_OK;
+}
 }  // namespace gpk
 
 extern "C" {
@@ -1113,6 +1120,7 @@ int gpma_export_sorted(gpma_t h, uint64_t *d_out, uint64_t cap, uint64_t *n_out,
   launch_export(h->geo, h->ctl, d_out, nullptr, cap, h->w.status, s);
   int rc = read_ctl(h, s);
   if (rc) return rc;
+  if ((rc = export_status(h, h->h_ctl->err))) return rc;
   *n_out = h->h_ctl->gen_count;
   return *n_out > cap ? GPMA_ECAP : cuda_ok(h);
 }
@@ -1130,6 +1138,7 @@ int gpma_export_csr(gpma_t h, uint64_t *d_rowptr, uint32_t *d_col, uint64_t cap,
   dfree(h, partials, s);
   int rc = read_ctl(h, s);
   if (rc) return rc;
+  if ((rc = export_status(h, h->h_ctl->err))) return rc;
   *n_out = h->h_ctl->gen_count;
   return *n_out > cap ? GPMA_ECAP : cuda_ok(h);
 }
@@ -1280,6 +1289,15 @@ int gpma_update_many(gpma_t const *handles, const uint64_t *const *d_ins, const 
   }
   if (cudaGetLastError() != cudaSuccess && !first_err) first_err = GPMA_EDEVICE;
   return first_err;
+}
+
+int gpma_set_wait_limit(gpma_t h, uint32_t polls, void *stream) {
+  if (!h) return GPMA_EINVAL;
+  if (h->poisoned) return h->poisoned;
+  if (int rs = settle(h, (cudaStream_t)stream)) return rs;
+  note_launch();
+  k_set_wait_limit<<<1, 1, 0, (cudaStream_t)stream>>>(h->ctl, polls);
+  return cuda_ok(h);
 }
 
 int gpma_profile_enable(gpma_t h, int on) {

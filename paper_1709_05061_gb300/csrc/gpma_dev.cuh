@@ -81,6 +81,7 @@ struct Ctl {
   uint64_t gen_count;  // general-purpose counter (exports)
   uint32_t resized;    // this call grew the array on the device (into the spare)
   uint32_t nvlong;     // runs longer than kLongRun, left to the chunked level-0 path
+  uint32_t spin_limit; // polls a bounded wait may make before it gives up (0: the built-in limits)
 };
 
 __device__ __forceinline__ bool is_guard(uint64_t k) {
@@ -293,7 +294,14 @@ __device__ __forceinline__ uint32_t learned_leaf_search(const ModelHead &m, cons
 // gets kErrTimeout and the value read so far is used (the batch is then discarded).
 constexpr uint64_t kFlagAgg = 1ull << 30;
 constexpr uint64_t kFlagPre = 2ull << 30;
-constexpr uint32_t kSpinLimit = 1u << 22;
+constexpr uint32_t kSpinLimit = 1u << 22;         // look-back waits
+constexpr uint32_t kBarrierSpinLimit = 1u << 24;  // grid barriers
+
+// the handle's wait limit, or `dflt` when none was set
+__device__ __forceinline__ uint32_t spin_limit(const Ctl *ctl, uint32_t dflt) {
+  const uint32_t v = ctl->spin_limit;
+  return v ? v : dflt;
+}
 
 __device__ __forceinline__ uint64_t pack_status(uint32_t epoch, uint64_t flag, uint32_t v) {
   return ((uint64_t)epoch << 32) | flag | (uint64_t)(v & 0x3FFFFFFFu);
@@ -310,9 +318,10 @@ __device__ __forceinline__ uint64_t ld_status(const uint64_t *p) {
 
 // Exclusive prefix of `agg` over earlier tiles in column `col` of a status
 // matrix laid out status[tile * stride + col].  Called by one thread per column.
+// A wait that exceeds the handle's limit sets kErrTimeout in ctl->err.
 __device__ __forceinline__ uint32_t lookback(uint64_t *status, uint32_t stride, uint32_t col,
                                              uint32_t tile, uint32_t agg, uint32_t epoch,
-                                             uint32_t *err) {
+                                             Ctl *ctl) {
   if (tile == 0) {
     st_status(status + col, pack_status(epoch, kFlagPre, agg));
     return 0;
@@ -321,11 +330,12 @@ __device__ __forceinline__ uint32_t lookback(uint64_t *status, uint32_t stride, 
   uint32_t excl = 0;
   int64_t t = (int64_t)tile - 1;
   uint32_t spins = 0;
+  const uint32_t limit = spin_limit(ctl, kSpinLimit);
   while (t >= 0) {
     uint64_t s = ld_status(status + (uint64_t)t * stride + col);
     if ((uint32_t)(s >> 32) != epoch || (s & (3ull << 30)) == 0) {
-      if (++spins > kSpinLimit) {
-        atomicOr(err, kErrTimeout);
+      if (++spins > limit) {
+        atomicOr(&ctl->err, kErrTimeout);
         break;
       }
       __nanosleep(20);

@@ -170,4 +170,8 @@ struct HandleView {
 struct gpma;
 namespace gpk {
 HandleView handle_view(struct gpma *h, cudaStream_t s);  // waits for a pending device resize
+int poison_handle(struct gpma *h, int code);             // every later call returns `code`
+// status of an export from the control block read back after it: a look-back
+// wait that gave up poisons the handle with GPMA_ETIMEOUT
+int export_status(struct gpma *h, uint32_t err);
 }  // namespace gpk

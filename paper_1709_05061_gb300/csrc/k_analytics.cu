@@ -465,7 +465,7 @@ void launch_pb_iter(const Geo &g, const PbPlan &p, const uint64_t *keys, const u
 // kErrTimeout and every block leaves.  Counters: cnt[0..2] rotate per level
 // (frontier sizes), cnt[3..4] are the queue-rebuild counters of even and odd
 // levels, cnt[5] the level count.
-__device__ __forceinline__ bool grid_barrier(unsigned *bar, uint32_t *err) {
+__device__ __forceinline__ bool grid_barrier(unsigned *bar, uint32_t *err, uint32_t limit) {
   __syncthreads();
   if (threadIdx.x == 0) {
     volatile unsigned *gen = bar + 1;
@@ -478,7 +478,7 @@ __device__ __forceinline__ bool grid_barrier(unsigned *bar, uint32_t *err) {
     } else {
       uint32_t spins = 0;
       while (*gen == g0) {
-        if (++spins > (1u << 24)) {
+        if (++spins > limit) {
           atomicOr(err, kErrTimeout);
           break;
         }
@@ -526,8 +526,9 @@ constexpr uint64_t kBigRow = 1024, kRowChunk = 256;
 // (row, first chunk) pairs
 __global__ void __launch_bounds__(256) k_bfs_persist(Geo g, int32_t *depth, uint32_t *qa, uint32_t *qb,
                                                      uint32_t *big, uint32_t *cnt, unsigned *bar, uint32_t *err,
-                                                     uint32_t scan_from) {
+                                                     uint32_t scan_from, const Ctl *ctl) {
   const uint32_t lane = lane_id();
+  const uint32_t limit = spin_limit(ctl, kBarrierSpinLimit);
   const uint32_t warp = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   const uint32_t nwarps = gridDim.x * (blockDim.x >> 5);
   const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -586,7 +587,7 @@ __global__ void __launch_bounds__(256) k_bfs_persist(Geo g, int32_t *depth, uint
           base = __shfl_sync(0xFFFFFFFFu, base, __ffs(bal) - 1);
           if (hit) qin[base + __popc(bal & lanemask_lt())] = v;
         }
-        if (!grid_barrier(bar, err)) return;
+        if (!grid_barrier(bar, err, limit)) return;
       }
       // top-down: a warp per short row; long rows are listed with the running
       // total of their 256-slot chunks (one packed 64-bit atomic keeps the list
@@ -606,7 +607,7 @@ __global__ void __launch_bounds__(256) k_bfs_persist(Geo g, int32_t *depth, uint
         }
         bfs_gather(g, depth, beg, end, qout, cnext, level);
       }
-      if (!grid_barrier(bar, err)) return;
+      if (!grid_barrier(bar, err, limit)) return;
       const unsigned long long bc = *(volatile unsigned long long *)bigctr;
       const uint32_t nbig = (uint32_t)(bc >> 32), nchunks = (uint32_t)bc;
       for (uint32_t c = warp; c < nchunks; c += nwarps) {
@@ -621,7 +622,7 @@ __global__ void __launch_bounds__(256) k_bfs_persist(Geo g, int32_t *depth, uint
         bfs_gather(g, depth, a, a + kRowChunk < end ? a + kRowChunk : end, qout, cnext, level);
       }
     }
-    if (!grid_barrier(bar, err)) return;
+    if (!grid_barrier(bar, err, limit)) return;
     nfront = *(volatile uint32_t *)cnext;
     have_queue = !scan;
     if (!scan) {
@@ -673,7 +674,7 @@ int run_bfs(const Geo &g, uint32_t src, int32_t *depth, uint32_t *q0, uint32_t *
   const uint32_t scan_from = g.V / 32 > 64 ? g.V / 32 : 64;
   Geo gg = g;
   void *args[] = {(void *)&gg, (void *)&depth, (void *)&q0,  (void *)&q1,
-                  (void *)&q2, (void *)&cnt,   (void *)&bar, (void *)&err, (void *)&scan_from};
+                  (void *)&q2, (void *)&cnt,   (void *)&bar, (void *)&err, (void *)&scan_from, (void *)&ctl};
   note_launch();
   if (cudaLaunchCooperativeKernel((const void *)k_bfs_persist, dim3(grid), dim3(256), args, 0, s) != cudaSuccess)
     return -1;

@@ -177,7 +177,7 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_pass(const uint64_t *__re
       run += c;
     }
     ltile[d] = run;
-    uint32_t excl = lookback(status, 256, d, tile, run, ctl->epoch + pass, &ctl->err);
+    uint32_t excl = lookback(status, 256, d, tile, run, ctl->epoch + pass, ctl);
     gbase[d] = excl;
   }
   for (uint32_t d = radix + threadIdx.x; d < 256; d += kSortThreads) ltile[d] = 0;
@@ -420,8 +420,8 @@ __global__ void __launch_bounds__(kScanThreads) k_compact(PrepArgs a, const uint
     }
   }
   uint32_t koff[kScanItems], hoff[kScanItems];
-  const uint32_t m = tile_scan(keep, koff, tile, status, 2, 0, ctl->epoch + kSlotKeep, &ctl->err, sm);
-  const uint32_t nr = tile_scan(head, hoff, tile, status, 2, 1, ctl->epoch + kSlotKeep, &ctl->err, sm);
+  const uint32_t m = tile_scan(keep, koff, tile, status, 2, 0, ctl->epoch + kSlotKeep, ctl, sm);
+  const uint32_t nr = tile_scan(head, hoff, tile, status, 2, 1, ctl->epoch + kSlotKeep, ctl, sm);
 #pragma unroll
   for (int r = 0; r < kScanItems; r++) {
     if (!keep[r] || koff[r] >= n) continue;

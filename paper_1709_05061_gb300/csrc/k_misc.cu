@@ -298,7 +298,7 @@ __global__ void __launch_bounds__(kScanThreads) k_export(Geo g, Ctl *ctl, uint64
     flag[r] = k[r] != kEmpty && (g.raw || !is_guard(k[r]));
   }
   uint32_t off[kScanItems];
-  uint32_t total = tile_scan(flag, off, tile, status, 1, 0, ctl->epoch + kSlotMisc, &ctl->err, sm);
+  uint32_t total = tile_scan(flag, off, tile, status, 1, 0, ctl->epoch + kSlotMisc, ctl, sm);
 #pragma unroll
   for (int r = 0; r < kScanItems; r++) {
     if (!flag[r] || off[r] >= cap) continue;
@@ -308,7 +308,9 @@ __global__ void __launch_bounds__(kScanThreads) k_export(Geo g, Ctl *ctl, uint64
   if ((uint64_t)(tile + 1) * kScanTile >= g.C && threadIdx.x == 0) ctl->gen_count = total;
 }
 
+// starts an export: its own error word (a batch's error is already in sticky)
 __global__ void k_export_prep(Ctl *ctl) {
+  ctl->err = 0;
   ctl->epoch += kSlotsPerBatch;
   ctl->ticket[kSlotMisc] = 0;
   ctl->gen_count = 0;

@@ -520,7 +520,7 @@ __global__ void __launch_bounds__(kScanThreads) k_pending(Ctl *ctl, Work w) {
     flag[r] = e < m && w.eflag[e] == 2;
   }
   uint32_t off[kScanItems];
-  uint32_t total = tile_scan(flag, off, tile, w.status, 1, 0, ctl->epoch + kSlotPend, &ctl->err, sm);
+  uint32_t total = tile_scan(flag, off, tile, w.status, 1, 0, ctl->epoch + kSlotPend, ctl, sm);
 #pragma unroll
   for (int r = 0; r < kScanItems; r++) {
     if (!flag[r] || off[r] >= m) continue;
@@ -546,8 +546,8 @@ __global__ void __launch_bounds__(kScanThreads) k_eruns(Ctl *ctl, Work w) {
     pc[r] = flag[r] ? (uint32_t)(w.rdelta[q] + (int32_t)w.rdel[q]) : 0u;  // its surviving inserts
   }
   uint32_t off[kScanItems], poff[kScanItems];
-  const uint32_t total = tile_scan(flag, off, tile, w.status, 2, 0, ctl->epoch + kSlotERuns, &ctl->err, sm);
-  const uint32_t ptotal = tile_scan(pc, poff, tile, w.status, 2, 1, ctl->epoch + kSlotERuns, &ctl->err, sm);
+  const uint32_t total = tile_scan(flag, off, tile, w.status, 2, 0, ctl->epoch + kSlotERuns, ctl, sm);
+  const uint32_t ptotal = tile_scan(pc, poff, tile, w.status, 2, 1, ctl->epoch + kSlotERuns, ctl, sm);
 #pragma unroll
   for (int r = 0; r < kScanItems; r++)
     if (flag[r] && off[r] < nr) {
@@ -640,8 +640,8 @@ __global__ void __launch_bounds__(kScanThreads) k_segs(Geo g, Ctl *ctl, Work w) 
     }
   }
   uint32_t off[kScanItems], loff[kScanItems];
-  uint32_t total = tile_scan(flag, off, tile, w.status, 2, 0, ctl->epoch + kSlotSegs, &ctl->err, sm);
-  uint32_t ltotal = tile_scan(lv, loff, tile, w.status, 2, 1, ctl->epoch + kSlotSegs, &ctl->err, sm);
+  uint32_t total = tile_scan(flag, off, tile, w.status, 2, 0, ctl->epoch + kSlotSegs, ctl, sm);
+  uint32_t ltotal = tile_scan(lv, loff, tile, w.status, 2, 1, ctl->epoch + kSlotSegs, ctl, sm);
 #pragma unroll
   for (int r = 0; r < kScanItems; r++) {
     uint64_t q = scan_elem(tile, r);

@@ -9,11 +9,12 @@
 
 namespace {
 
-// Look-back status words of the single-pass compaction: two per tile of 2,048
-// slots.  Sized for arrays of up to 2^27 slots (1 MiB, held by every GPU that
-// loads the library until the process exits).
+// Look-back status words of the single-pass compaction: one per tile of 2,048
+// slots (the export scans one column), plus a margin.  Sized for arrays of up
+// to 2^27 slots (about 512 KiB, held by every GPU that loads the library until
+// the process exits).
 constexpr uint64_t kMaxSlots = 1ull << 27;
-constexpr uint64_t kStatusWords = 2 * (kMaxSlots / 2048) + 64;
+constexpr uint64_t kStatusWords = kMaxSlots / 2048 + 64;
 static __device__ __align__(256) uint64_t g_export_status[kStatusWords];
 
 constexpr int kMaxDevices = 64;
@@ -51,22 +52,23 @@ extern "C" int gpma_export_sorted_noalloc(gpma_t h, uint64_t *d_out, uint64_t ca
   if (v.geo->C > kMaxSlots) return GPMA_EINVAL;  // larger than the fixed scratch
   uint64_t *status = nullptr;
   int rc = status_address(&status);
-  if (rc) return rc;
+  if (rc) return gpk::poison_handle(h, rc);
   cudaStream_t s = (cudaStream_t)stream;
   // the array keeps the previous call's words (maybe another handle's): clear
   // the part this call uses so no stale word can pass for this call's
-  const uint64_t words = 2ull * gpk::comp_tiles(v.geo->C) + 64;
+  const uint64_t words = (uint64_t)gpk::comp_tiles(v.geo->C) + 64;
   if (cudaMemsetAsync(status, 0, words * sizeof(uint64_t), s) != cudaSuccess) {
     cudaGetLastError();
-    return GPMA_EDEVICE;
+    return gpk::poison_handle(h, GPMA_EDEVICE);
   }
   gpk::launch_export(*v.geo, v.ctl, d_out, nullptr, cap, status, s);
   if (cudaMemcpyAsync(v.h_ctl, v.ctl, sizeof(gpk::Ctl), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
-      cudaStreamSynchronize(s) != cudaSuccess) {
+      cudaStreamSynchronize(s) != cudaSuccess || cudaGetLastError() != cudaSuccess) {
     cudaGetLastError();
-    return GPMA_EDEVICE;
+    return gpk::poison_handle(h, GPMA_EDEVICE);
   }
+  // a look-back wait that gave up leaves the count and keys wrong
+  if ((rc = gpk::export_status(h, v.h_ctl->err))) return rc;
   *n_out = v.h_ctl->gen_count;
-  if (cudaGetLastError() != cudaSuccess) return GPMA_EDEVICE;
   return *n_out > cap ? GPMA_ECAP : GPMA_OK;
 }

@@ -28,7 +28,7 @@ __device__ __forceinline__ uint32_t take_ticket(Ctl *ctl, uint32_t slot, ScanSme
 // tile total must stay below 2^30.  Returns the running total after this tile.
 __device__ __forceinline__ uint32_t tile_scan(const uint32_t (&v)[kScanItems], uint32_t (&off)[kScanItems],
                                               uint32_t tile, uint64_t *status, uint32_t stride, uint32_t col,
-                                              uint32_t epoch, uint32_t *err, ScanSmem &sm) {
+                                              uint32_t epoch, Ctl *ctl, ScanSmem &sm) {
   const uint32_t w = threadIdx.x >> 5, lane = lane_id();
   uint32_t inc[kScanItems];
 #pragma unroll
@@ -46,7 +46,7 @@ __device__ __forceinline__ uint32_t tile_scan(const uint32_t (&v)[kScanItems], u
     sm.cnt[i0 / 8][i0 % 8] = s - a - b;
     sm.cnt[i1 / 8][i1 % 8] = s - b;
     if (lane == 0) {
-      sm.excl = lookback(status, stride, col, tile, tot, epoch, err);
+      sm.excl = lookback(status, stride, col, tile, tot, epoch, ctl);
       sm.tot = tot;
     }
   }

@@ -71,3 +71,19 @@ def test_binding_constants_match_the_header():
         assert int(d["GPMA_PROF_" + n.upper()]) == i, n
     for name in ("GPMA_RAW_KEYS", "GPMA_PLAIN_SEARCH", "GPMA_DUAL_DELETE", "GPMA_PUSH_PAGERANK"):
         assert int(d[name].rstrip("u")) == getattr(gp, name), name
+
+
+def test_allocator_failure_without_gpu(lib):
+    """A caller-supplied allocator that refuses the first request: gpma_create
+    returns GPMA_ENOMEM, hands out no handle and frees nothing it did not get."""
+    asked, freed = [], []
+    A = gp.Allocator(lambda n, s: asked.append(n) or 0, lambda p, s: freed.append(p))
+    out = ctypes.c_void_p()
+    p = gp.gpma_params(64, 0, 0, 0, 0, 0)
+    rc = lib.gpma_create(1000, ctypes.byref(p), ctypes.byref(A.struct), None, ctypes.byref(out))
+    assert rc == gp.GPMA_ENOMEM
+    assert not out.value
+    assert asked and not freed
+    # an allocator without both functions is rejected before any allocation
+    bad = gp.gpma_allocator()
+    assert lib.gpma_create(1000, ctypes.byref(p), ctypes.byref(bad), None, ctypes.byref(out)) == gp.GPMA_EINVAL

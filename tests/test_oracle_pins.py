@@ -10,18 +10,18 @@ from helpers import (EMPTY, apply_set_semantics, check_layout, edges_of, floats,
                      parse_leaves, read_golden)
 
 
-# ---- Fig. 2 threshold table -------------------------------------------------------
-def test_fig2_threshold_table():
-    g = read_golden("fig2_thresholds.txt")
+# ---- Fig. 3 threshold table -------------------------------------------------------
+def test_fig3_threshold_table():
+    g = read_golden("fig3_thresholds.txt")
     L, h = int(g["L"]), int(g["h"])
     mx, mn = oracle.thresholds(L, h)
     assert list(mx) == ints(g["max_entries"])
     assert list(mn) == ints(g["min_entries"])
 
 
-def test_fig2_densities_follow_linear_reading():
+def test_fig3_densities_follow_linear_reading():
     """The printed tau/rho rows are the linear interpolation between leaf and root."""
-    g = read_golden("fig2_thresholds.txt")
+    g = read_golden("fig3_thresholds.txt")
     h = int(g["h"])
     tau, rho = ints(g["tau_pct"]), ints(g["rho_pct"])
     for i in range(h + 1):
@@ -350,3 +350,78 @@ def test_dual_bruteforce_stream_and_bounds(V, L, seed):
         if st["resized"] == 2:
             assert o.capacity < before.size
         live = new_live
+
+
+# ---- negative pins of the invariant checker -----------------------------------------
+def _broken(o, mutate, **kw):
+    """A copy of o's layout with one property broken, imported into a fresh oracle
+    of the same parameters (import does no checking of its own)."""
+    lay = o.layout().copy()
+    mutate(lay)
+    b = oracle.OraclePMA(o.n_vertices, L=o.L, dual=o.dual, **kw)
+    assert b.import_layout(lay) == 0
+    return b
+
+
+@pytest.mark.parametrize("dual", [False, True])
+def test_check_invariants_flags_each_broken_property(dual):
+    """The checker returns 0 on a valid layout and the code of the property that a
+    hand-made layout breaks: 1 keys not strictly increasing, 2 a leaf above max_0,
+    5 a hole inside a leaf (dual deletion only; lazy deletion leaves holes by
+    design).  Raw keys 100, 200, ... leave room for keys in between."""
+    L = 8
+    E = np.uint64(EMPTY)
+    o = oracle.OraclePMA(0, L=L, raw_keys=True, dual=dual)
+    assert o.update(np.arange(1, 61, dtype=np.uint64) * np.uint64(100))[0] == 0
+    assert o.check_invariants() == 0
+    lay = o.layout()
+    valid = np.nonzero(lay != E)[0]
+    max0 = int(oracle.thresholds(L, o.height)[0][0])
+    assert max0 == 7
+
+    def swap_two_keys(a):
+        i, j = valid[3], valid[4]
+        a[i], a[j] = a[j], a[i]
+    assert _broken(o, swap_two_keys, raw_keys=True).check_invariants() == 1
+
+    def duplicate_key(a):
+        a[valid[4]] = a[valid[3]]
+    assert _broken(o, duplicate_key, raw_keys=True).check_invariants() == 1
+
+    def overfill_leaf(a):
+        # leaf 1 gets max_0 + 1 keys, all between the keys of leaves 0 and 2
+        lo = max(int(x) for x in a[:L] if x != E)
+        a[L:2 * L] = np.arange(lo + 1, lo + 1 + L, dtype=np.uint64)
+    assert _broken(o, overfill_leaf, raw_keys=True).check_invariants() == 2
+
+    def hole(a):  # the first slot of a leaf holding two keys or more becomes EMPTY
+        per = (a.reshape(-1, L) != E).sum(axis=1)
+        j = int(np.nonzero(per >= 2)[0][0])
+        a[j * L] = E
+    assert _broken(o, hole, raw_keys=True).check_invariants() == (5 if dual else 0)
+    # code 3 (capacity not L * 2^h) cannot be imported: the import refuses it
+    assert oracle.OraclePMA(0, L=L, raw_keys=True, dual=dual).import_layout(lay[:3 * L]) != 0
+
+
+def test_check_invariants_flags_bad_vertices_and_guards():
+    """Graph mode adds code 4: a vertex id >= V, or not exactly one guard per vertex."""
+    V, L = 16, 8
+    E = np.uint64(EMPTY)
+    o = oracle.OraclePMA(V, L=L)
+    edges = [(u << 32) | ((u + 1) % V) for u in range(V)] + [(u << 32) | ((u + 5) % V) for u in range(V)]
+    assert o.update(np.array(edges, np.uint64))[0] == 0
+    assert o.check_invariants() == 0
+    lay = o.layout()
+    guard_slots = [i for i in np.nonzero(lay != E)[0] if (int(lay[i]) & 0xFFFFFFFF) == 0xFFFFFFFF]
+    assert len(guard_slots) == V
+
+    def dst_out_of_range(a):  # the last edge of row V-1 gets dst = V (still below the guard)
+        i = guard_slots[-1] - 1
+        while a[i] == E:
+            i -= 1
+        a[i] = np.uint64(((V - 1) << 32) | V)
+    assert _broken(o, dst_out_of_range).check_invariants() == 4
+
+    def drop_a_guard(a):
+        a[guard_slots[V // 2]] = E
+    assert _broken(o, drop_a_guard).check_invariants() == 4
