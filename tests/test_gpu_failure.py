@@ -73,7 +73,7 @@ def test_bfs_barrier_wait_runs_out_and_poisons():
 
 @pytest.mark.parametrize("noalloc", [False, True])
 def test_export_wait_runs_out_and_is_reported(noalloc):
-    """With a two-poll limit, some of the 16,384 look-back tiles of the export find
+    """With a two-poll limit, some of the ~2,000 look-back tiles of the export find
     their predecessor unpublished and give up.  An export is either complete and
     right, or reports GPMA_ETIMEOUT and poisons the handle; at least one of a few
     tries must run out."""
