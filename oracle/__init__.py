@@ -80,6 +80,10 @@ def lib():
         l.or_cc.argtypes = [vp, vp]; l.or_cc.restype = C.c_int
         l.or_pagerank.argtypes = [vp, u32, C.c_double, vp]; l.or_pagerank.restype = C.c_int
         l.or_check_invariants.argtypes = [vp]; l.or_check_invariants.restype = C.c_int
+        l.or_bfs_edges.argtypes = [u32, vp, u64, u32, vp]; l.or_bfs_edges.restype = C.c_int
+        l.or_cc_edges.argtypes = [u32, vp, u64, vp]; l.or_cc_edges.restype = C.c_int
+        l.or_pagerank_edges.argtypes = [u32, vp, u64, u32, C.c_double, vp]
+        l.or_pagerank_edges.restype = C.c_int
         _lib = l
     return _lib
 
@@ -94,6 +98,40 @@ def thresholds(L: int, h: int, tau0=92, tauh=80, rho0=8, rhoh=40):
     mn = np.zeros(h + 1, np.uint64)
     lib().or_thresholds(L, h, tau0, tauh, rho0, rhoh, _ptr(mx), _ptr(mn))
     return mx, mn
+
+
+def _edges(keys) -> np.ndarray:
+    return np.ascontiguousarray(np.asarray(keys, dtype=np.uint64))
+
+
+def bfs_edges(n_vertices: int, keys, src: int) -> np.ndarray:
+    """BFS depths over a plain edge list (src << 32 | dst, any order)."""
+    k = _edges(keys)
+    out = np.empty(n_vertices, np.int32)
+    rc = lib().or_bfs_edges(n_vertices, _ptr(k), k.size, src, _ptr(out))
+    if rc:
+        raise ValueError(f"oracle bfs_edges rc={rc}")
+    return out
+
+
+def cc_edges(n_vertices: int, keys) -> np.ndarray:
+    """Weakly connected component labels (smallest vertex id) of a plain edge list."""
+    k = _edges(keys)
+    out = np.empty(n_vertices, np.uint32)
+    rc = lib().or_cc_edges(n_vertices, _ptr(k), k.size, _ptr(out))
+    if rc:
+        raise ValueError(f"oracle cc_edges rc={rc}")
+    return out
+
+
+def pagerank_edges(n_vertices: int, keys, iters: int = 20, damping: float = 0.85) -> np.ndarray:
+    """FP64 PageRank (the oracle's definition) over a plain edge list."""
+    k = _edges(keys)
+    out = np.empty(n_vertices, np.float64)
+    rc = lib().or_pagerank_edges(n_vertices, _ptr(k), k.size, iters, damping, _ptr(out))
+    if rc:
+        raise ValueError(f"oracle pagerank_edges rc={rc}")
+    return out
 
 
 class OraclePMA:

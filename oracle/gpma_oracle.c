@@ -564,23 +564,40 @@ void or_row_end(const or_pma *p, uint32_t *row_end) {
 }
 
 /* ---- analytics (Sec. 4.2 and Sec. 6.1 "Applications") ------------------------ */
-static int build_csr(const or_pma *p, uint64_t **rowptr, uint32_t **col, uint64_t *ne) {
-  *rowptr = (uint64_t *)malloc(sizeof(uint64_t) * ((uint64_t)p->V + 1));
-  uint64_t e = or_export_sorted(p, NULL);
-  *col = (uint32_t *)malloc(sizeof(uint32_t) * (e ? e : 1));
-  if (!*rowptr || !*col) return OR_ENOMEM;
-  *ne = or_export_csr(p, *rowptr, *col);
-  return OR_OK;
+/* BFS (Algorithm "BFS"): hop depth from src along out-edges, -1 if unreachable */
+/* The three analytics below read a plain array of keys: the slot array of a PMA
+   (EMPTY slots and guards are skipped) or a list of edges (src << 32 | dst) in any
+   order.  Every src and dst must be below V. */
+static int keys_in_range(uint32_t V, const uint64_t *keys, uint64_t n) {
+  for (uint64_t i = 0; i < n; i++) {
+    uint64_t k = keys[i];
+    if (k == OR_EMPTY || is_guard(k)) continue;
+    if ((k >> 32) >= V || (k & 0xFFFFFFFFull) >= V) return 0;
+  }
+  return 1;
 }
 
-/* BFS (Algorithm "BFS"): hop depth from src along out-edges, -1 if unreachable */
-int or_bfs(const or_pma *p, uint32_t src, int32_t *depth) {
-  if ((p->flags & OR_RAW_KEYS) || src >= p->V) return OR_EINVAL;
-  uint64_t *rp; uint32_t *col; uint64_t ne;
-  if (build_csr(p, &rp, &col, &ne)) return OR_ENOMEM;
-  uint32_t *queue = (uint32_t *)malloc(sizeof(uint32_t) * p->V);
-  if (!queue) { free(rp); free(col); return OR_ENOMEM; }
-  for (uint32_t v = 0; v < p->V; v++) depth[v] = -1;
+/* breadth-first search from src over out-edges (Algorithm "BFS", Sec. 4.2):
+   out-neighbour lists by a counting pass, then a FIFO queue; -1 = unreachable */
+static int bfs_keys(uint32_t V, const uint64_t *keys, uint64_t n, uint32_t src, int32_t *depth) {
+  if (src >= V || !keys_in_range(V, keys, n)) return OR_EINVAL;
+  uint64_t *rp = (uint64_t *)calloc((uint64_t)V + 1, sizeof(uint64_t));
+  uint64_t *cur = (uint64_t *)malloc(sizeof(uint64_t) * ((uint64_t)V + 1));
+  uint32_t *queue = (uint32_t *)malloc(sizeof(uint32_t) * ((uint64_t)V + 1));
+  if (!rp || !cur || !queue) { free(rp); free(cur); free(queue); return OR_ENOMEM; }
+  for (uint64_t i = 0; i < n; i++) {
+    uint64_t k = keys[i];
+    if (k != OR_EMPTY && !is_guard(k)) rp[(k >> 32) + 1]++;
+  }
+  for (uint64_t u = 0; u < V; u++) rp[u + 1] += rp[u];
+  uint32_t *col = (uint32_t *)malloc(sizeof(uint32_t) * (rp[V] ? rp[V] : 1));
+  if (!col) { free(rp); free(cur); free(queue); return OR_ENOMEM; }
+  for (uint64_t u = 0; u < V; u++) cur[u] = rp[u];
+  for (uint64_t i = 0; i < n; i++) {
+    uint64_t k = keys[i];
+    if (k != OR_EMPTY && !is_guard(k)) col[cur[k >> 32]++] = (uint32_t)(k & 0xFFFFFFFFull);
+  }
+  for (uint32_t v = 0; v < V; v++) depth[v] = -1;
   uint64_t head = 0, tail = 0;
   depth[src] = 0;
   queue[tail++] = src;
@@ -591,8 +608,17 @@ int or_bfs(const or_pma *p, uint32_t src, int32_t *depth) {
       if (depth[v] < 0) { depth[v] = depth[u] + 1; queue[tail++] = v; }
     }
   }
-  free(queue); free(rp); free(col);
+  free(queue); free(rp); free(cur); free(col);
   return OR_OK;
+}
+
+int or_bfs(const or_pma *p, uint32_t src, int32_t *depth) {
+  if (p->flags & OR_RAW_KEYS) return OR_EINVAL;
+  return bfs_keys(p->V, p->slots, p->C, src, depth);
+}
+
+int or_bfs_edges(uint32_t V, const uint64_t *keys, uint64_t n, uint32_t src, int32_t *depth) {
+  return bfs_keys(V, keys, n, src, depth);
 }
 
 /* weakly connected components; every vertex is labelled with the smallest
@@ -602,38 +628,48 @@ static uint32_t uf_find(uint32_t *parent, uint32_t x) {
   return x;
 }
 
-int or_cc(const or_pma *p, uint32_t *label) {
-  if (p->flags & OR_RAW_KEYS) return OR_EINVAL;
-  for (uint32_t v = 0; v < p->V; v++) label[v] = v;
-  for (uint64_t s = 0; s < p->C; s++) {
-    uint64_t k = p->slots[s];
+static int cc_keys(uint32_t V, const uint64_t *keys, uint64_t n, uint32_t *label) {
+  if (!keys_in_range(V, keys, n)) return OR_EINVAL;
+  for (uint32_t v = 0; v < V; v++) label[v] = v;
+  for (uint64_t i = 0; i < n; i++) {
+    uint64_t k = keys[i];
     if (k == OR_EMPTY || is_guard(k)) continue;
     uint32_t a = uf_find(label, (uint32_t)(k >> 32)), b = uf_find(label, (uint32_t)(k & 0xFFFFFFFFu));
     if (a < b) label[b] = a; else if (b < a) label[a] = b;
   }
-  for (uint32_t v = 0; v < p->V; v++) label[v] = uf_find(label, v);
+  for (uint32_t v = 0; v < V; v++) label[v] = uf_find(label, v);
   return OR_OK;
+}
+
+int or_cc(const or_pma *p, uint32_t *label) {
+  if (p->flags & OR_RAW_KEYS) return OR_EINVAL;
+  return cc_keys(p->V, p->slots, p->C, label);
+}
+
+int or_cc_edges(uint32_t V, const uint64_t *keys, uint64_t n, uint32_t *label) {
+  return cc_keys(V, keys, n, label);
 }
 
 /* PageRank by power iteration (Sec. 6.1): x0 = 1/N,
    x'_v = (1-d)/N + d * ( sum_{u->v} x_u / outdeg(u) + sum_{outdeg(w)=0} x_w / N ),
    a fixed number of iterations, in double precision. */
-int or_pagerank(const or_pma *p, uint32_t iters, double damping, double *rank) {
-  if (p->flags & OR_RAW_KEYS) return OR_EINVAL;
-  uint64_t N = p->V;
-  double *y = (double *)malloc(sizeof(double) * N);
-  uint64_t *deg = (uint64_t *)calloc(N, sizeof(uint64_t));
+static int pagerank_keys(uint32_t V, const uint64_t *keys, uint64_t n, uint32_t iters, double damping,
+                         double *rank) {
+  if (!keys_in_range(V, keys, n)) return OR_EINVAL;
+  uint64_t N = V;
+  double *y = (double *)malloc(sizeof(double) * (N ? N : 1));
+  uint64_t *deg = (uint64_t *)calloc(N ? N : 1, sizeof(uint64_t));
   if (!y || !deg) { free(y); free(deg); return OR_ENOMEM; }
-  for (uint64_t s = 0; s < p->C; s++) {
-    uint64_t k = p->slots[s];
+  for (uint64_t i = 0; i < n; i++) {
+    uint64_t k = keys[i];
     if (k != OR_EMPTY && !is_guard(k)) deg[k >> 32]++;
   }
   for (uint64_t v = 0; v < N; v++) rank[v] = 1.0 / (double)N;
   for (uint32_t it = 0; it < iters; it++) {
     double dangling = 0.0;
     for (uint64_t v = 0; v < N; v++) { y[v] = 0.0; if (deg[v] == 0) dangling += rank[v]; }
-    for (uint64_t s = 0; s < p->C; s++) {
-      uint64_t k = p->slots[s];
+    for (uint64_t i = 0; i < n; i++) {
+      uint64_t k = keys[i];
       if (k == OR_EMPTY || is_guard(k)) continue;
       uint64_t u = k >> 32, v = k & 0xFFFFFFFFull;
       y[v] += rank[u] / (double)deg[u];
@@ -643,6 +679,16 @@ int or_pagerank(const or_pma *p, uint32_t iters, double damping, double *rank) {
   }
   free(y); free(deg);
   return OR_OK;
+}
+
+int or_pagerank(const or_pma *p, uint32_t iters, double damping, double *rank) {
+  if (p->flags & OR_RAW_KEYS) return OR_EINVAL;
+  return pagerank_keys(p->V, p->slots, p->C, iters, damping, rank);
+}
+
+int or_pagerank_edges(uint32_t V, const uint64_t *keys, uint64_t n, uint32_t iters, double damping,
+                      double *rank) {
+  return pagerank_keys(V, keys, n, iters, damping, rank);
 }
 
 /* ---- invariants ----------------------------------------------------------------

@@ -74,6 +74,12 @@ void or_row_end(const or_pma *p, uint32_t *row_end);
 int or_bfs(const or_pma *p, uint32_t src, int32_t *depth);
 int or_cc(const or_pma *p, uint32_t *label);
 int or_pagerank(const or_pma *p, uint32_t iters, double damping, double *rank);
+/* the same three analytics over a plain list of edges (src << 32 | dst, any order,
+   every id below V): for graphs too large to load into the oracle's PMA */
+int or_bfs_edges(uint32_t V, const uint64_t *keys, uint64_t n, uint32_t src, int32_t *depth);
+int or_cc_edges(uint32_t V, const uint64_t *keys, uint64_t n, uint32_t *label);
+int or_pagerank_edges(uint32_t V, const uint64_t *keys, uint64_t n, uint32_t iters, double damping,
+                      double *rank);
 
 /* 0 if every checked property holds, else a code naming the first violated one.
    Dual mode adds: 5 a leaf with a hole (a valid key after an EMPTY slot). */

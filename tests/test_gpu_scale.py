@@ -113,3 +113,39 @@ def test_pagerank_largest_bucketed_graph(V):
     assert abs(float(ra.astype(np.float64).sum()) - 1.0) < 1e-3
     a.status()
     b.status()
+
+
+@pytest.mark.parametrize("scale", [21, 22])
+def test_large_graph_analytics_match_oracle(scale):
+    """Graphs past 2^20 vertices take other branches of the analytics: at 2^21
+    vertices (512 head buckets) the bucketed PageRank runs one 1024-thread block per
+    bucket; past 2^21 (1024 buckets at scale 22) the placement writes every edge
+    straight to its bucket.  R-MAT with 2^(scale+1) distinct edges: layout slot for
+    slot, BFS from two sources and CC exactly, PageRank-20 (bucketed and push
+    passes) within 1e-5 of the oracle's FP64 ranks, and the two passes bit for bit
+    equal."""
+    gp.build()
+    V = 1 << scale
+    stream = W.rmat_stream(scale, 1 << (scale + 1), seed=50 + scale)
+    o = oracle.OraclePMA(V, L=64)
+    assert o.update(stream)[0] == 0
+    gb, gpush = gp.Graph(V, leaf_size=64), gp.Graph(V, leaf_size=64, push_pagerank=True)
+    for g in (gb, gpush):
+        g.update(dev(stream), None, stats=True)
+    lg = gb.layout().cpu().numpy().view(np.uint64)
+    lo = o.layout()
+    assert lg.size == lo.size and np.count_nonzero(lg != lo) == 0
+    assert gb.check() == 0
+    srcs = (int(stream[0] >> np.uint64(32)), int(stream[len(stream) // 2] >> np.uint64(32)))
+    for s in srcs:
+        assert np.array_equal(gb.bfs(s).cpu().numpy(), o.bfs(s)), s
+    assert np.array_equal(gb.cc().cpu().numpy().view(np.uint32), o.cc())
+    ref = o.pagerank(20, 0.85)
+    rb = gb.pagerank(20, 0.85).cpu().numpy()
+    rp = gpush.pagerank(20, 0.85).cpu().numpy()
+    assert np.array_equal(rb.view(np.uint32), rp.view(np.uint32))
+    rel = np.max(np.abs(rb.astype(np.float64) - ref) / ref)
+    assert rel <= 1e-5, rel
+    for g in (gb, gpush):
+        g.status()
+        g.close()

@@ -252,6 +252,25 @@ def test_analytics_vs_networkx():
         pr = nx.pagerank(G, alpha=0.85, tol=1e-15, max_iter=10000)
         assert np.allclose(x, [pr[v] for v in range(V)], rtol=1e-9, atol=0)
         assert abs(o.pagerank(iters=7).sum() - 1.0) < 1e-12
+        # the edge-list forms (for graphs too large for the oracle's PMA), fed the
+        # edges in a shuffled order, against networkx directly
+        el = rng.permutation(np.array([(u << 32) | v for u, v in ed], np.uint64))
+        for s in (0, V // 2):
+            d = nx.single_source_shortest_path_length(G, s)
+            assert list(oracle.bfs_edges(V, el, s)) == [d.get(v, -1) for v in range(V)]
+        lab_e = oracle.cc_edges(V, el)
+        for comp in nx.weakly_connected_components(G):
+            assert all(lab_e[v] == min(comp) for v in comp)
+        assert np.allclose(oracle.pagerank_edges(V, el, 300), [pr[v] for v in range(V)], rtol=1e-9, atol=0)
+
+
+def test_edge_list_analytics_reject_out_of_range_ids():
+    with pytest.raises(ValueError):
+        oracle.bfs_edges(4, np.array([(1 << 32) | 4], np.uint64), 0)
+    with pytest.raises(ValueError):
+        oracle.cc_edges(4, np.array([(4 << 32) | 1], np.uint64))
+    with pytest.raises(ValueError):
+        oracle.pagerank_edges(4, np.array([(0 << 32) | 9], np.uint64), 3)
 
 
 def test_pagerank_two_vertex_hand_computed():
