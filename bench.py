@@ -63,6 +63,9 @@ def parse():
     ap.add_argument("--no-sweep", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-studies", action="store_true",
+                    help="skip the scale-24 update sweep and served stream, the learned-search and the "
+                         "many-graph studies that the default run adds to the line")
     ap.add_argument("--seed", type=int, default=1)
     ap.add_argument("--push-pagerank", action="store_true",
                     help="PageRank by the push pass (one L2 reduction per edge) instead of the bucketed pass")
@@ -198,12 +201,36 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def alg_bytes_table(st: dict, n_raw: int, C_old: int, C_new: int) -> int:
+    """Algorithmic bytes of one batch by the measurement plan's formula: 16 B per
+    raw update key (read once, written once while staging), a 512-byte read of
+    every leaf holding a delete, an 8-byte EMPTY store per delete, a read and a
+    write of every slot of the merged segments, and on a resize a read of the
+    old array and a write of the new one."""
+    a = 16 * n_raw + 8 * LEAF * st["delete_leaves"] + 8 * st["n_deleted"] + 16 * LEAF * st["covered_leaves"]
+    if st["resized"]:
+        a += 8 * C_old + 8 * C_new
+    return a
+
+
 def measured_hbm_peak():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
             return float(json.load(f)["hbm_gbs"]), "measured"
     except Exception:
         return 6800.0, "fallback"
+
+
+def sweep_entry(b, times, algb, algt, peak):
+    """p50/p99 of the per-batch device times, and the HBM fraction by the library's
+    algorithmic bytes (alg_*) and by the measurement plan's formula (table_*)."""
+    med = statistics.median(times)
+    gbs = statistics.median([x / (t * 1e-3) / 1e9 for x, t in zip(algb, times)])
+    gbt = statistics.median([x / (t * 1e-3) / 1e9 for x, t in zip(algt, times)])
+    return {"batch": b, "updates_per_s": b / (med * 1e-3), "p50_ms": med,
+            "p99_ms": float(np.percentile(times, 99)),
+            "alg_bytes": int(statistics.median(algb)), "alg_GBps": gbs, "hbm_frac": gbs / peak,
+            "table_alg_bytes": int(statistics.median(algt)), "table_GBps": gbt, "table_hbm_frac": gbt / peak}
 
 
 # ---- the GPU arm -----------------------------------------------------------------------------------
@@ -234,11 +261,12 @@ def run_gpu(a, stream, rank, world, dist):
         live = to_dev(np.sort(win.live()))
         sweep = []
         for b in SWEEP:
-            times, algb, rb_times = [], [], []
+            times, algb, algt, rb_times = [], [], [], []
             for it in range(SWEEP_WARM + SWEEP_TIMED):
                 ins, dels = win.slide(b // 2)
                 di, dd = to_dev(ins), to_dev(dels)
                 flush.zero_()
+                c_old = g.capacity
                 gp.gpma_profile_enable(g.h, True)
                 s = g.update(di, dd, stats=True)
                 p = gp.gpma_profile_read(g.h, reset=True)
@@ -259,16 +287,11 @@ def run_gpu(a, stream, rank, world, dist):
                 if it >= SWEEP_WARM:
                     times.append(ms)
                     algb.append(s["alg_bytes"])
+                    algt.append(alg_bytes_table(s, b, c_old, g.capacity))
                     rb_times.append(e0.elapsed_time(e1))
-            med = statistics.median(times)
-            gbs = statistics.median([x / (t * 1e-3) / 1e9 for x, t in zip(algb, times)])
-            sweep.append({
-                "batch": b, "updates_per_s": b / (med * 1e-3),
-                "p50_ms": med, "p99_ms": float(np.percentile(times, 99)),
-                "alg_GBps": gbs, "hbm_frac": gbs / peak,
-                "rebuild_p50_ms": statistics.median(rb_times),
-                "speedup_vs_rebuild": statistics.median(rb_times) / med,
-            })
+            sweep.append(sweep_entry(b, times, algb, algt, peak))
+            sweep[-1]["rebuild_p50_ms"] = statistics.median(rb_times)
+            sweep[-1]["speedup_vs_rebuild"] = statistics.median(rb_times) / sweep[-1]["p50_ms"]
         out["sweep"] = sweep
         del live
     # the sweep slid only rank 0's window; every rank now continues from its own state
@@ -501,6 +524,7 @@ def learned_study(a):
         g.update(dev(stream[:E0]), None, stats=True)
     flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.int32, device="cuda")
     times = {k: [] for k in graphs}
+    clk = ClockSampler(torch.cuda.current_device()).__enter__()
     for i in range(warm + timed):
         ins = stream[E0 + i * n_ins: E0 + (i + 1) * n_ins]
         pick = rng.choice(live.size, n_del, replace=False)
@@ -517,8 +541,10 @@ def learned_study(a):
             gp.gpma_profile_enable(g.h, False)
             if i >= warm:
                 times[name].append(p["update"]["ms"])
+    clk.__exit__(None, None, None)
     same = bool(torch.equal(graphs["learned"].layout(), graphs["plain"].layout()))
     out = {"workload": f"chung-lu V={V} E={E0} gamma=2.1 seed=7, batch {B} (70% insert / 30% random delete)",
+           "clocks": clk.summary(),
            "plain_p50_ms": statistics.median(times["plain"]), "learned_p50_ms": statistics.median(times["learned"]),
            "layouts_identical": same, "capacity_slots": graphs["plain"].capacity}
     out["speedup"] = out["plain_p50_ms"] / out["learned_p50_ms"]
@@ -562,6 +588,7 @@ def many_study(a):
     flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.int32, device="cuda")
     res = {}
     layouts = {}
+    clk = ClockSampler(torch.cuda.current_device()).__enter__()
     for label, sizes in (("L64", [64] * n), ("tuned", tuned)):
         for mode in ("sequential", "batched"):
             gs = [gp.Graph(wl.n_vertices(i), leaf_size=sizes[i]) for i in range(n)]
@@ -590,6 +617,8 @@ def many_study(a):
                                      "edge_updates_per_s": float(wl.batch.sum()) / (ms * 1e-3)}
         same = all(torch.equal(x, y) for x, y in zip(layouts[(label, "sequential")], layouts[(label, "batched")]))
         res[f"{label}_batched_equals_sequential"] = same
+    clk.__exit__(None, None, None)
+    res["clocks"] = clk.summary()
     res["workload"] = (f"64 R-MAT graphs (.57/.19/.19/.05), windows log-uniform in [2^10, 2^22] edges "
                        f"(total {int(wl.edges.sum())}), batches log-uniform in [64, 2^18] "
                        f"(total {int(wl.batch.sum())} updates per step), size seed 11, graph seeds 1000+g")
@@ -632,6 +661,29 @@ def serve_study(a):
     del st
     torch.cuda.empty_cache()
     win = W.SlidingWindow(host_stream, window)
+    # update-only sweep on the freshly loaded scale-24 array: device time per batch
+    # from the library's events (the 4.3 GB array is far larger than L2), algorithmic
+    # bytes from the batch's stats (both definitions), fraction of the measured peak
+    peak = measured_hbm_peak()[0]
+    sweep = []
+    clk = ClockSampler(torch.cuda.current_device()).__enter__()
+    for B in (100_000, 1_000_000):
+        ts, ab, at = [], [], []
+        for k in range(SWEEP_WARM + SWEEP_TIMED):
+            ins, dels = win.slide(B // 2)
+            di = torch.from_numpy(np.ascontiguousarray(ins).view(np.int64)).cuda()
+            dd = torch.from_numpy(np.ascontiguousarray(dels).view(np.int64)).cuda()
+            c_old = g.capacity
+            gp.gpma_profile_enable(g.h, True)
+            st = g.update(di, dd, stats=True)
+            p = gp.gpma_profile_read(g.h, reset=True)
+            gp.gpma_profile_enable(g.h, False)
+            if k >= SWEEP_WARM:
+                ts.append(p["update"]["ms"])
+                ab.append(st["alg_bytes"])
+                at.append(alg_bytes_table(st, B, c_old, g.capacity))
+        sweep.append(sweep_entry(B, ts, ab, at, peak))
+    clk.__exit__(None, None, None)
     budget = 2 << 30  # device memory for staging and results, split by Server.with_budget
     srv = S.Server.with_budget(g, budget, max_inflight=2, keep_results=False)
     n = a.serve_requests
@@ -642,6 +694,9 @@ def serve_study(a):
                        f"log-uniform 1e2..1e5 (50/50) : queries (BFS / CC / PageRank-10) = 4 : 1",
            "generate_s": gen_s, "bulk_load_s": load_s, "requests_per_run": n, "hbm_budget_bytes": budget,
            "max_batch_keys": srv.max_batch_keys, "result_slots": len(srv.d_res)}
+    out["update_sweep_scale24"] = sweep
+    out["update_sweep_clocks"] = clk.summary()
+    clk = ClockSampler(torch.cuda.current_device()).__enter__()
     cap = srv.run(S.make_requests(n, V, win, rate=1.0, seed=101), realtime=False)
     out["closed_loop"] = cap
     # the plain path on the same kind of stream: one request at a time, nothing
@@ -654,30 +709,8 @@ def serve_study(a):
         r = srv.run(S.make_requests(n, V, win, rate=rate, seed=102 + int(frac * 100)), realtime=True)
         r["offered_rate_per_s"] = rate
         out[f"load_{int(frac * 100)}"] = r
-    # update-only sweep on the resident scale-24 array: device time per batch from
-    # the library's events (the 4.3 GB array is far larger than L2), algorithmic
-    # bytes from the batch's stats, fraction of the measured HBM peak
-    peak = measured_hbm_peak()[0]
-    sweep = []
-    for B in (100_000, 1_000_000):
-        ts, ab = [], []
-        for k in range(13):
-            ins, dels = win.slide(B // 2)
-            di = torch.from_numpy(np.ascontiguousarray(ins).view(np.int64)).cuda()
-            dd = torch.from_numpy(np.ascontiguousarray(dels).view(np.int64)).cuda()
-            gp.gpma_profile_enable(g.h, True)
-            st = g.update(di, dd, stats=True)
-            p = gp.gpma_profile_read(g.h, reset=True)
-            gp.gpma_profile_enable(g.h, False)
-            if k >= 3:
-                ts.append(p["update"]["ms"])
-                ab.append(st["alg_bytes"])
-        ms = statistics.median(ts)
-        gbs = statistics.median(ab) / (ms * 1e-3) / 1e9
-        sweep.append({"batch": B, "p50_ms": ms, "p99_ms": float(np.percentile(ts, 99)),
-                      "updates_per_s": B / (ms * 1e-3), "alg_bytes": int(statistics.median(ab)), "alg_GBps": gbs,
-                      "hbm_frac": gbs / peak})
-    out["update_sweep_scale24"] = sweep
+    clk.__exit__(None, None, None)
+    out["serve_clocks"] = clk.summary()
     out["check"] = g.check()
     g.close()
     return out
@@ -818,6 +851,16 @@ def main():
             line["sweep"] = out["sweep"]
         if world == 1 and not a.no_cpu_baseline:
             line["cpu_baseline"] = run_oracle(a, stream, 100, max_seconds=15.0)
+        if world == 1 and not a.no_studies:
+            # the other configurations on the same GPU, each against the plain path
+            for key, fn in (("scale24", serve_study), ("learned", learned_study), ("many", many_study)):
+                t0 = time.perf_counter()
+                try:
+                    line[key] = fn(a)
+                except Exception as e:  # a study that fails is reported, not fatal to the line
+                    line[key] = {"error": f"{type(e).__name__}: {e}"}
+                line[key]["wall_s"] = time.perf_counter() - t0
+                torch.cuda.empty_cache()
         print(json.dumps(line), flush=True)
     if dist:
         dist.barrier()

@@ -102,6 +102,7 @@ typedef struct {
   uint64_t touched_leaves; /* distinct leaves holding an update after cancellation */
   uint64_t covered_leaves; /* leaves rewritten by merges (0 on a resize) */
   uint64_t merges[GPMA_MAX_LEVELS]; /* segments merged at each level, Sec. 5.2 level order */
+  uint64_t delete_leaves;  /* distinct leaves holding a delete that took effect */
 } gpma_stats;
 
 /* Create an array for vertices [0, n_vertices) (n_vertices in [1, 2^31]; ignored

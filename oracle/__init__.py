@@ -48,6 +48,7 @@ class Stats(C.Structure):
         ("levels_climbed", C.c_uint32), ("resized", C.c_uint32),
         ("alg_bytes", C.c_uint64), ("touched_leaves", C.c_uint64),
         ("covered_leaves", C.c_uint64), ("merges", C.c_uint64 * MAX_LEVELS),
+        ("delete_leaves", C.c_uint64),
     ]
 
     def as_dict(self) -> dict:

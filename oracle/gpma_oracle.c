@@ -510,6 +510,9 @@ static int apply_batch(or_pma *p, uint64_t *I, uint64_t nI, uint64_t *D, uint64_
       if (cover[j] >= 0) { ncov++; ncov_untouched += !touched[j]; }
     }
     for (uint64_t i = 0; i < nD; i++) empties += cover[leafD[i]] < 0;
+    uint64_t ndl = 0;  /* leafD is non-decreasing: D is sorted */
+    for (uint64_t i = 0; i < nD; i++) ndl += i == 0 || leafD[i] != leafD[i - 1];
+    st->delete_leaves = ndl;
     st->n_inserted = nI;
     st->n_deleted = nD;
     st->n_ignored = n_raw - nI - nD;

@@ -47,6 +47,7 @@ typedef struct {
   uint64_t touched_leaves;  /* distinct leaves holding an insert or delete after cancellation */
   uint64_t covered_leaves;  /* leaves rewritten by a merge (union of merged segments) */
   uint64_t merges[OR_MAX_LEVELS]; /* segments merged per level, in the paper's level order */
+  uint64_t delete_leaves;   /* distinct leaves holding a delete that took effect */
 } or_stats;
 
 /* Threshold rule: per-level maximum/minimum entry counts for a tree of height h. */

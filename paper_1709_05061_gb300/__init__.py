@@ -44,7 +44,7 @@ class gpma_stats(C.Structure):
         ("n_inserted", C.c_uint64), ("n_deleted", C.c_uint64), ("n_ignored", C.c_uint64),
         ("levels_climbed", C.c_uint32), ("resized", C.c_uint32), ("alg_bytes", C.c_uint64),
         ("touched_leaves", C.c_uint64), ("covered_leaves", C.c_uint64),
-        ("merges", C.c_uint64 * GPMA_MAX_LEVELS),
+        ("merges", C.c_uint64 * GPMA_MAX_LEVELS), ("delete_leaves", C.c_uint64),
     ]
 
     def as_dict(self) -> dict:

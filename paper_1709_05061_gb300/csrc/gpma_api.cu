@@ -772,6 +772,7 @@ int update(gpma *h, const uint64_t *ins, uint64_t n_ins, const uint64_t *del, ui
         launch_unmark(h->geo, h->ctl, h->w, n32, s);
         if ((rc = do_resize(h, h->h_ctl->total, s))) return rc;
         resized = true;
+        if (stats) launch_stats(h->geo, h->ctl, h->w, n32, s);  // touched leaves with a delete
       }
     } else {
       h->count_ub += n_ins;
@@ -818,6 +819,7 @@ int update(gpma *h, const uint64_t *ins, uint64_t n_ins, const uint64_t *del, ui
   stats->n_deleted = c.n_deleted;
   stats->n_ignored = n - c.n_inserted - c.n_deleted;
   stats->touched_leaves = c.nruns;
+  stats->delete_leaves = c.st_del_leaves;
   stats->resized = resized ? 1 : (shrunk ? 2 : 0);
   for (int i = 0; i < GPMA_MAX_LEVELS && i < kMaxLv; i++) stats->merges[i] = c.merges[i];
   stats->merges[0] = c.n_merged0;

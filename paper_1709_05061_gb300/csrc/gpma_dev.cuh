@@ -75,6 +75,7 @@ struct Ctl {
   uint64_t total;     // logical number of stored keys (guards included)
   uint64_t n_inserted, n_deleted;
   uint64_t st_cov_touched, st_l0_only, st_empties;
+  uint64_t st_del_leaves;  // runs holding an applied delete
   uint32_t levels_climbed;
   uint32_t n_merged0;
   uint64_t merges[kMaxLv];

@@ -63,7 +63,7 @@ __global__ void k_init_batch(Ctl *ctl, uint32_t *hist, uint32_t nhist, uint32_t 
     ctl->m = ctl->nruns = ctl->npend = ctl->neruns = ctl->nsegs = ctl->nleafw = 0;
     for (int i = 0; i < 16; i++) ctl->ticket[i] = 0;
     ctl->n_inserted = ctl->n_deleted = 0;
-    ctl->st_cov_touched = ctl->st_l0_only = ctl->st_empties = 0;
+    ctl->st_cov_touched = ctl->st_l0_only = ctl->st_empties = ctl->st_del_leaves = 0;
     ctl->levels_climbed = 0;
     ctl->n_merged0 = 0;
     for (int i = 0; i < kMaxLv; i++) ctl->merges[i] = 0;
@@ -259,7 +259,7 @@ __global__ void __launch_bounds__(1024) k_small_front(PrepArgs a, const uint64_t
     ctl->m = ctl->nruns = ctl->npend = ctl->neruns = ctl->nsegs = ctl->nleafw = 0;
     for (int i = 0; i < 16; i++) ctl->ticket[i] = 0;
     ctl->n_inserted = ctl->n_deleted = 0;
-    ctl->st_cov_touched = ctl->st_l0_only = ctl->st_empties = 0;
+    ctl->st_cov_touched = ctl->st_l0_only = ctl->st_empties = ctl->st_del_leaves = 0;
     ctl->levels_climbed = 0;
     ctl->n_merged0 = 0;
     for (int i = 0; i < kMaxLv; i++) ctl->merges[i] = 0;

@@ -810,8 +810,9 @@ __global__ void k_seg_write(Geo dst, Ctl *ctl, Work w, SegArgs sa, const uint64_
 // ---- statistics (only when the caller asks for them) -------------------------------------------
 __global__ void k_stats(Ctl *ctl, Work w) {
   const uint32_t nruns = ctl->nruns, nsegs = ctl->nsegs;
-  uint64_t cov = 0, emp = 0, l0 = 0;
+  uint64_t cov = 0, emp = 0, l0 = 0, dl = 0;
   for (uint32_t r = blockIdx.x * blockDim.x + threadIdx.x; r < nruns; r += gridDim.x * blockDim.x) {
+    dl += w.rdel[r] != 0;
     const uint32_t leaf = w.rleaf[r], info = w.rinfo[r];
     bool in = false;
     if (nsegs) {
@@ -831,7 +832,9 @@ __global__ void k_stats(Ctl *ctl, Work w) {
   cov = warp_sum(cov);
   emp = warp_sum(emp);
   l0 = warp_sum(l0);
+  dl = warp_sum(dl);
   if (lane_id() == 0) {
+    if (dl) atomicAdd((unsigned long long *)&ctl->st_del_leaves, (unsigned long long)dl);
     if (cov) atomicAdd((unsigned long long *)&ctl->st_cov_touched, (unsigned long long)cov);
     if (emp) atomicAdd((unsigned long long *)&ctl->st_empties, (unsigned long long)emp);
     if (l0) atomicAdd((unsigned long long *)&ctl->st_l0_only, (unsigned long long)l0);

@@ -19,7 +19,7 @@ from paper_1709_05061_gb300 import workloads as W  # noqa: E402
 
 PR_TOL = 1e-5
 STAT_KEYS = ("n_inserted", "n_deleted", "n_ignored", "levels_climbed", "resized", "alg_bytes",
-             "touched_leaves", "covered_leaves", "merges")
+             "touched_leaves", "covered_leaves", "merges", "delete_leaves")
 
 
 def dev(a):

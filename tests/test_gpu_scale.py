@@ -18,7 +18,7 @@ import paper_1709_05061_gb300 as gp  # noqa: E402
 from paper_1709_05061_gb300 import workloads as W  # noqa: E402
 
 STATS = ("n_inserted", "n_deleted", "n_ignored", "levels_climbed", "resized", "alg_bytes", "touched_leaves",
-         "covered_leaves", "merges")
+         "covered_leaves", "merges", "delete_leaves")
 
 
 def dev(a):

@@ -168,6 +168,8 @@ def test_lazy_delete_is_in_place():
     assert set(before[changed].tolist()) == set(int(x) for x in d)
     assert np.all(after[changed] == np.uint64(EMPTY))
     assert st["merges"][0] == 0 and st["resized"] == 0
+    # the leaves holding a delete, counted from the slots that changed
+    assert st["delete_leaves"] == len(set((changed // 16).tolist()))
 
 
 def test_bulk_load_closed_form():
