@@ -323,7 +323,7 @@ void free_work(gpma *h, cudaStream_t s) {
   Work &w = h->w;
   void *ptrs[] = {h->bufA,   h->bufB,     w.ukey,  w.utag,     w.uleaf,   w.run_start, w.eflag,
                   w.rleaf,   w.rdelta,    w.rinfo, w.rdel,     w.pkey,    w.pleaf,     w.erun, w.eleaf,
-                  w.elvl,    w.etop,      w.seg_node, w.seg_top, w.seg_pstart, w.seg_lpre, w.status};
+                  w.elvl,    w.etop,      w.seg_node, w.seg_top, w.seg_pstart, w.seg_lpre, w.status, w.bk};
   for (void *p : ptrs) dfree(h, p, s);
   memset(&h->w, 0, sizeof(Work));
   h->bufA = h->bufB = nullptr;
@@ -346,7 +346,8 @@ int ensure_work(gpma *h, uint64_t n, cudaStream_t s) {
             dalloc(h, &w.rinfo, cap, s) && dalloc(h, &w.rdel, cap, s) && dalloc(h, &w.pkey, cap, s) &&
             dalloc(h, &w.pleaf, cap, s) && dalloc(h, &w.erun, c1, s) && dalloc(h, &w.eleaf, cap, s) && dalloc(h, &w.elvl, cap, s) &&
             dalloc(h, &w.etop, cap, s) && dalloc(h, &w.seg_node, c1, s) && dalloc(h, &w.seg_top, c1, s) &&
-            dalloc(h, &w.seg_pstart, c1, s) && dalloc(h, &w.seg_lpre, c1, s) && dalloc(h, &w.status, st, s);
+            dalloc(h, &w.seg_pstart, c1, s) && dalloc(h, &w.seg_lpre, c1, s) && dalloc(h, &w.status, st, s) &&
+            dalloc(h, &w.bk, kBkWords, s);
   if (!ok) {
     free_work(h, s);
     return GPMA_ENOMEM;
@@ -541,8 +542,9 @@ bool capture_update(gpma *h, FrontArgs &f, uint32_t nb, bool stats, bool grow, G
   if (!gc.cap2 && cudaStreamCreateWithFlags(&gc.cap2, cudaStreamNonBlocking) != cudaSuccess) return false;
   cudaGraph_t graph = nullptr;
   if (cudaGraphCreate(&graph, 0) != cudaSuccess) return false;
-  cudaGraphConditionalHandle cond, cgrow, cmerge;
-  bool ok = cudaGraphConditionalHandleCreate(&cond, graph, 0, cudaGraphCondAssignDefault) == cudaSuccess;
+  cudaGraphConditionalHandle cond, cgrow, cmerge, cfall;
+  bool ok = cudaGraphConditionalHandleCreate(&cond, graph, 0, cudaGraphCondAssignDefault) == cudaSuccess &&
+            cudaGraphConditionalHandleCreate(&cfall, graph, 0, cudaGraphCondAssignDefault) == cudaSuccess;
   if (grow) {
     ok = ok && cudaGraphConditionalHandleCreate(&cgrow, graph, 0, cudaGraphCondAssignDefault) == cudaSuccess &&
          cudaGraphConditionalHandleCreate(&cmerge, graph, 0, cudaGraphCondAssignDefault) == cudaSuccess;
@@ -562,11 +564,15 @@ bool capture_update(gpma *h, FrontArgs &f, uint32_t nb, bool stats, bool grow, G
                          t);
     if (h->mhead) launch_train_model(g, h->mhead, h->mpieces, h->ctl, true, t);
   };
-  if (!small_front(nb)) launch_sort(f, nb, gc.cap);
+  if (!small_front(nb)) {
+    // buckets sorted in shared memory; the radix-sort path only when a bucket is too large
+    launch_front_buckets(f, nb, gc.cap, &cfall);
+    ok = capture_if(gc.cap, gc.cap2, cfall, [&](cudaStream_t t) { launch_front_fallback(f, nb, t, false); });
+  }
   launch_leaf_pass(g, h->ctl, h->w, nb, gc.cap);
   note_launch();
   k_gate<<<1, 1, 0, gc.cap>>>(h->ctl, cond);
-  ok = capture_if(gc.cap, gc.cap2, cond, [&](cudaStream_t t) {
+  ok = ok && capture_if(gc.cap, gc.cap2, cond, [&](cudaStream_t t) {
     launch_pending(g, h->ctl, h->w, nb, t);
     launch_tree_rebuild(g, h->ctl, h->w, nb, t);
     launch_esc_level(g, h->ctl, h->w, nb, grow, t);
@@ -683,6 +689,7 @@ int update(gpma *h, const uint64_t *ins, uint64_t n_ins, const uint64_t *del, ui
   }
   pa.npass = (bits + 7) / 8;
   pa.dbits = (bits + pa.npass - 1) / pa.npass;
+  pa.sbits = bits;
 
   FrontArgs f;
   f.prep = pa;
@@ -702,6 +709,11 @@ int update(gpma *h, const uint64_t *ins, uint64_t n_ins, const uint64_t *del, ui
   f.run_start = h->w.run_start;
   f.run_leaf = h->w.rleaf;
   f.lfull = h->w.pleaf;  // free until the escalation compacts pending inserts
+  {
+    uint32_t *p = h->w.bk;
+    const uint32_t K = kBkMax + 1;
+    f.bk = BucketWork{p, p + K, p + 2 * K, p + 3 * K, p + 4 * K, p + 5 * K, p + 6 * K, p + 7 * K, p + 8 * K, p + 9 * K};
+  }
   const uint32_t n32 = (uint32_t)n;
   Phase whole(h->prof, GPMA_PROF_UPDATE, s);
   // level-0 merges move pivots only inside their leaves and the search widens
@@ -745,7 +757,10 @@ int update(gpma *h, const uint64_t *ins, uint64_t n_ins, const uint64_t *del, ui
   } else {
     {
       Phase ph(h->prof, GPMA_PROF_SORT, s);
-      if (!small_front(n)) launch_sort(f, n, s);
+      if (!small_front(n)) {
+        launch_front_buckets(f, n, s, nullptr);
+        launch_front_fallback(f, n, s, true);
+      }
     }
     {
       Phase ph(h->prof, GPMA_PROF_LEAF, s);

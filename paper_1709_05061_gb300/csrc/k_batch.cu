@@ -1,16 +1,23 @@
 // k_batch.cu -- front end of one update batch (Algorithm "GPMA+ Segment-Oriented
 // Insertion", Sec. 5.2, lines Sort(U) and BinarySearchLeafSegments(U)):
-//   k_init_batch  reset the per-call control block and radix histograms
+//   k_init_batch  reset the per-call control block and histograms
 //   k_prep        validate keys, compress (src, dst, insert/delete tag) into one
-//                 sortable word, build the radix histograms of every pass
-//   k_sort_pass   one stable LSD radix pass (single pass per digit with look-back)
-//   k_search_all  unique + insert/delete cancellation on the sorted words and the
-//                 leaf search of every survivor, one word per thread (learned model
-//                 when trained, else binary search; both give the same leaf)
-//   k_compact     survivors and the heads of their runs of equal leaf, one
-//                 single-pass compaction with two counts
+//                 sort word, count the words of every bucket (top bits)
+//   k_bk_scan     bucket offsets; flags a bucket too large for shared memory
+//   k_bk_scatter  every word to its bucket
+//   k_bk_sort     one bucket per block: sort in shared memory, unique + insert/
+//                 delete cancellation, the leaf search of every survivor (learned
+//                 model when trained, else binary search; both give the same
+//                 leaf), the bucket's survivor and run-head counts
+//   k_bk_offsets  survivor and run-head offsets of every bucket (one block)
+//   k_bk_write    survivors and run heads to their places
 //   k_small_front all of the above in one block for batches of at most
 //                 kSmallBatch keys (bitonic sort in shared memory)
+// A batch with a bucket above kBkCap keys (a heavily skewed batch) takes the
+// radix-sort path instead: k_bk_convert (radix histograms), k_sort_pass (one
+// stable LSD pass with per-digit look-back) per digit, k_search_all (unique/
+// cancel + leaf search, one word per thread) and k_compact (single-pass
+// compaction of survivors and run heads).
 #include "gpma_dev.cuh"
 #include "gpma_launch.h"
 #include "scan_dev.cuh"
@@ -49,8 +56,9 @@ __device__ __forceinline__ uint64_t expand(uint64_t w, const PrepArgs &a) {
   return (src << 32) | dst;
 }
 
-__global__ void k_init_batch(Ctl *ctl, uint32_t *hist, uint32_t nhist, uint32_t n) {
+__global__ void k_init_batch(Ctl *ctl, uint32_t *hist, uint32_t nhist, uint32_t *bcnt, uint32_t nbk, uint32_t n) {
   for (uint32_t i = threadIdx.x; i < nhist; i += blockDim.x) hist[i] = 0;
+  for (uint32_t i = threadIdx.x; i < nbk; i += blockDim.x) bcnt[i] = 0;
   if (threadIdx.x == 0) {
     ctl->err = 0;
     ctl->n = n;
@@ -67,36 +75,57 @@ __global__ void k_init_batch(Ctl *ctl, uint32_t *hist, uint32_t nhist, uint32_t 
     ctl->levels_climbed = 0;
     ctl->n_merged0 = 0;
     for (int i = 0; i < kMaxLv; i++) ctl->merges[i] = 0;
+    ctl->bkfall = ctl->nbigbk = 0;
   }
 }
 
+// validation, sort words (compressed key << 1 | tag) and bucket counts
 __global__ void __launch_bounds__(256) k_prep(PrepArgs a, const uint64_t *__restrict__ ins,
                                               const uint64_t *__restrict__ del, uint64_t *__restrict__ out,
-                                              uint32_t *__restrict__ hist, Ctl *ctl) {
-  __shared__ uint32_t sh[8 * 256];
-  for (uint32_t i = threadIdx.x; i < a.npass * 256u; i += blockDim.x) sh[i] = 0;
+                                              uint32_t *__restrict__ bcnt, uint32_t shift, uint32_t nbk, Ctl *ctl) {
+  extern __shared__ uint32_t bh[];  // nbk counts
+  for (uint32_t i = threadIdx.x; i < nbk; i += blockDim.x) bh[i] = 0;
   __syncthreads();
   const uint32_t n = a.n_ins + a.n_del;
-  const uint32_t mask = (1u << a.dbits) - 1u;
   bool bad = false;
   for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-    uint32_t tag = i >= a.n_ins;
-    uint64_t key = tag ? del[i - a.n_ins] : ins[i];
+    const uint32_t tag = i >= a.n_ins;
+    const uint64_t key = tag ? del[i - a.n_ins] : ins[i];
     bool ok;
     if (a.raw) {
       ok = (key >> 63) == 0;
     } else {
-      uint64_t src = key >> 32, dst = key & 0xFFFFFFFFull;
+      const uint64_t src = key >> 32, dst = key & 0xFFFFFFFFull;
       ok = src < a.V && (dst < a.V || (a.allow_guards && !tag && dst == 0xFFFFFFFFull));
     }
     bad |= !ok;
-    uint64_t w = ok ? compress(key, tag, a) : 0ull;
+    const uint64_t w = ok ? ((compress(key, 0, a) << 1) | tag) : 0ull;
     out[i] = w;
-    const uint64_t kw = w & ~kTagBit;
+    atomicAdd(&bh[(uint32_t)(w >> shift)], 1u);
+  }
+  if (__any_sync(0xFFFFFFFFu, bad) && lane_id() == 0) atomicOr(&ctl->err, kErrKey);
+  __syncthreads();
+  for (uint32_t i = threadIdx.x; i < nbk; i += blockDim.x)
+    if (bh[i]) atomicAdd(&bcnt[i], bh[i]);
+}
+
+// radix-sort path: sort words back to the radix layout (tag in bit 63) and the
+// digit histograms of every pass
+__global__ void __launch_bounds__(256) k_bk_convert(PrepArgs a, uint64_t *__restrict__ buf,
+                                                    uint32_t *__restrict__ hist, Ctl *ctl, const uint32_t *gate) {
+  if (gate && *gate == 0) return;
+  __shared__ uint32_t sh[8 * 256];
+  for (uint32_t i = threadIdx.x; i < a.npass * 256u; i += blockDim.x) sh[i] = 0;
+  __syncthreads();
+  const uint32_t n = ctl->n;
+  const uint32_t mask = (1u << a.dbits) - 1u;
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const uint64_t w = buf[i];
+    const uint64_t kw = w >> 1;
+    buf[i] = kw | ((w & 1ull) << 63);
     for (uint32_t p = 0; p < a.npass; p++)
       atomicAdd(&sh[p * 256 + (uint32_t)((kw >> (p * a.dbits)) & mask)], 1u);
   }
-  if (__any_sync(0xFFFFFFFFu, bad) && lane_id() == 0) atomicOr(&ctl->err, kErrKey);
   __syncthreads();
   for (uint32_t i = threadIdx.x; i < a.npass * 256u; i += blockDim.x)
     if (sh[i]) atomicAdd(&hist[i], sh[i]);
@@ -109,13 +138,14 @@ template <int kSortItems>
 __global__ void __launch_bounds__(kSortThreads) k_sort_pass(const uint64_t *__restrict__ src,
                                                             uint64_t *__restrict__ dst, const uint32_t *hist,
                                                             uint64_t *status, Ctl *ctl, uint32_t pass,
-                                                            uint32_t shift, uint32_t dbits) {
+                                                            uint32_t shift, uint32_t dbits, const uint32_t *gate) {
   __shared__ uint32_t wcnt[kSortThreads / 32][256];
   __shared__ uint32_t gbase[256];
   __shared__ uint32_t ltile[256];  // digit totals of the tile, then their exclusive prefix
   __shared__ uint64_t skey[kSortThreads * kSortItems];
   __shared__ uint32_t hs[256];  // this pass's global digit counts, then their exclusive prefix
   __shared__ uint32_t s_tile;
+  if (gate && *gate == 0) return;
   const uint32_t n = ctl->n;
   const uint32_t w = threadIdx.x >> 5, lane = lane_id();
   const uint32_t radix = 1u << dbits, mask = radix - 1u;
@@ -380,7 +410,8 @@ __global__ void __launch_bounds__(1024) k_small_front(PrepArgs a, const uint64_t
 __global__ void __launch_bounds__(256) k_search_all(PrepArgs a, const uint64_t *__restrict__ sorted,
                                                     uint32_t *__restrict__ lfull, const uint64_t *__restrict__ F,
                                                     uint64_t nleaves, const Ctl *ctl, const ModelHead *mhead,
-                                                    const Piece *__restrict__ mpieces) {
+                                                    const Piece *__restrict__ mpieces, const uint32_t *gate) {
+  if (gate && *gate == 0) return;
   const uint32_t n = ctl->n;
   ModelHead hd;
   hd.valid = 0;
@@ -403,8 +434,10 @@ __global__ void __launch_bounds__(kScanThreads) k_compact(PrepArgs a, const uint
                                                           const uint32_t *__restrict__ lfull,
                                                           uint64_t *__restrict__ ukey, uint8_t *__restrict__ utag,
                                                           uint32_t *__restrict__ uleaf, uint32_t *__restrict__ run_start,
-                                                          uint32_t *__restrict__ run_leaf, uint64_t *status, Ctl *ctl) {
+                                                          uint32_t *__restrict__ run_leaf, uint64_t *status, Ctl *ctl,
+                                                          const uint32_t *gate) {
   __shared__ ScanSmem sm;
+  if (gate && *gate == 0) return;
   const uint32_t tile = take_ticket(ctl, kSlotKeep, sm), n = ctl->n;
   uint32_t keep[kScanItems], head[kScanItems], lf[kScanItems];
 #pragma unroll
@@ -441,6 +474,296 @@ __global__ void __launch_bounds__(kScanThreads) k_compact(PrepArgs a, const uint
   }
 }
 
+// ---- bucketed front end (batches above kSmallBatch keys) ---------------------------------------
+// Bucket offsets (exclusive scan of the counts, start[nbk] = n), the counts
+// turned into scatter cursors, the list of buckets above kBkSmall keys, and the
+// flag (and graph conditional) that sends the batch to the radix-sort path when
+// a bucket exceeds kBkCap.  One block of 1024 threads.
+__global__ void __launch_bounds__(1024) k_bk_scan(BucketWork bk, uint32_t nbk, Ctl *ctl,
+                                                  cudaGraphConditionalHandle fall, int set_fall) {
+  __shared__ uint32_t wsum[33];
+  __shared__ uint32_t s_big, s_fall, s_nbig;
+  const uint32_t t = threadIdx.x, per = (nbk + 1023) / 1024, b0 = t * per;
+  if (t == 0) {
+    s_fall = 0;
+    s_nbig = 0;
+  }
+  __syncthreads();
+  uint32_t loc = 0, mx = 0;
+  for (uint32_t q = 0; q < per; q++) {
+    const uint32_t b = b0 + q;
+    if (b >= nbk) break;
+    const uint32_t c = bk.cnt[b];
+    loc += c;
+    mx = c > mx ? c : mx;
+  }
+  uint32_t total;
+  uint32_t run = block_excl_scan(loc, wsum, &total);
+  if (mx > kBkCap) atomicOr(&s_fall, 1u);
+  for (uint32_t q = 0; q < per; q++) {
+    const uint32_t b = b0 + q;
+    if (b >= nbk) break;
+    const uint32_t c = bk.cnt[b];
+    bk.start[b] = run;
+    bk.cnt[b] = run;  // scatter cursor
+    if (c > kBkSmall && c <= kBkCap) bk.big[atomicAdd(&s_nbig, 1u)] = b;
+    run += c;
+  }
+  __syncthreads();
+  if (t == 0) {
+    bk.start[nbk] = total;
+    const uint32_t f = (ctl->err == 0 && s_fall) ? 1u : 0u;
+    ctl->bkfall = f;
+    ctl->nbigbk = s_nbig;
+    if (set_fall) cudaGraphSetConditional(fall, f);
+  }
+}
+
+__global__ void __launch_bounds__(256) k_bk_scatter(const uint64_t *__restrict__ src, uint64_t *__restrict__ dst,
+                                                    uint32_t *__restrict__ cursor, uint32_t shift, const Ctl *ctl) {
+  if (ctl->err || ctl->bkfall) return;
+  const uint32_t n = ctl->n;
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const uint64_t w = src[i];
+    dst[atomicAdd(&cursor[(uint32_t)(w >> shift)], 1u)] = w;
+  }
+}
+
+struct BkSortArgs {
+  PrepArgs a;
+  uint64_t *words;   // bucketed sort words in; sorted radix-layout words out (same place)
+  uint32_t *lfull;   // leaf of every sorted word (kNoLeaf: dropped by reading R2)
+  BucketWork bk;
+  const uint64_t *F;
+  uint64_t nleaves;
+  const ModelHead *mhead;
+  const Piece *mpieces;
+  const Ctl *ctl;
+};
+
+// Sort bucket b (at most CAP keys) in shared memory and summarise it: bitonic sort
+// of the sort words (padded to a power of two with all-ones words, which sort
+// last), the survivor test of reading R2 on neighbours (equal keys share a
+// bucket), the leaf of every survivor (reading R4), and the bucket's survivor
+// count, run heads after its first survivor, and first and last survivor leaves.
+template <uint32_t TPB>
+__device__ void bk_sort_one(const BkSortArgs &x, uint32_t b, uint64_t *sk, uint32_t *sl, const ModelHead &hd,
+                            bool learned) {
+  __shared__ uint32_t s_surv, s_hin, s_first, s_last;
+  const uint32_t t = threadIdx.x;
+  const uint32_t start = x.bk.start[b], nb = x.bk.start[b + 1] - start;
+  uint32_t P = 1;
+  while (P < nb) P <<= 1;
+  if (t == 0) {
+    s_surv = 0;
+    s_hin = 0;
+    s_first = 0xFFFFFFFFu;
+    s_last = 0;
+  }
+  for (uint32_t i = t; i < P; i += TPB) sk[i] = i < nb ? x.words[start + i] : ~0ull;
+  __syncthreads();
+  for (uint32_t k = 2; k <= P; k <<= 1) {
+    for (uint32_t j = k >> 1; j > 0; j >>= 1) {
+      for (uint32_t i = t; i < P / 2; i += TPB) {
+        const uint32_t lo = ((i & ~(j - 1)) << 1) | (i & (j - 1)), hi = lo + j;
+        const uint64_t u = sk[lo], v = sk[hi];
+        if ((u > v) == ((lo & k) == 0)) {
+          sk[lo] = v;
+          sk[hi] = u;
+        }
+      }
+      __syncthreads();
+    }
+  }
+  for (uint32_t i = t; i < nb; i += TPB) {
+    const uint64_t w = sk[i], k = w >> 1;
+    const bool kept = (w & 1) ? (i == 0 || (sk[i - 1] >> 1) != k) : (i + 1 == nb || (sk[i + 1] >> 1) != k);
+    const uint64_t rw = k | ((w & 1ull) << 63);  // radix layout: tag in bit 63
+    uint32_t leaf = kNoLeaf;
+    if (kept) {
+      const uint64_t key = expand(rw, x.a);
+      leaf = learned ? learned_leaf_search(hd, x.mpieces, x.F, x.nleaves, key) : leaf_search(x.F, x.nleaves, key);
+    }
+    sl[i] = leaf;
+    x.words[start + i] = rw;
+    x.lfull[start + i] = leaf;
+  }
+  __syncthreads();
+  uint32_t surv = 0, hin = 0;
+  for (uint32_t i = t; i < nb; i += TPB) {
+    if (sl[i] == kNoLeaf) continue;
+    ++surv;
+    int32_t j = (int32_t)i - 1;  // previous survivor (dropped words are rare)
+    while (j >= 0 && sl[j] == kNoLeaf) --j;
+    if (j < 0) atomicMin(&s_first, i);
+    else if (sl[j] != sl[i]) ++hin;
+    atomicMax(&s_last, i);
+  }
+  surv = warp_sum(surv);
+  hin = warp_sum(hin);
+  if (lane_id() == 0) {
+    if (surv) atomicAdd(&s_surv, surv);
+    if (hin) atomicAdd(&s_hin, hin);
+  }
+  __syncthreads();
+  if (t == 0) {
+    x.bk.surv[b] = s_surv;
+    x.bk.hin[b] = s_hin;
+    x.bk.first[b] = s_surv ? sl[s_first] : kNoLeaf;
+    x.bk.last[b] = s_surv ? sl[s_last] : kNoLeaf;
+  }
+  __syncthreads();  // shared memory is reused by the block's next bucket
+}
+
+// one 256-thread block per bucket of at most kBkSmall keys
+__global__ void __launch_bounds__(256) k_bk_sort(BkSortArgs x, uint32_t nbk) {
+  __shared__ uint64_t sk[kBkSmall];
+  __shared__ uint32_t sl[kBkSmall];
+  const Ctl *ctl = x.ctl;
+  if (ctl->err || ctl->bkfall) return;
+  const uint32_t b = blockIdx.x;
+  if (b >= nbk) return;
+  const uint32_t nb = x.bk.start[b + 1] - x.bk.start[b];
+  if (nb > kBkSmall) return;  // k_bk_sort_big
+  ModelHead hd;
+  hd.valid = 0;
+  if (x.mhead) hd = *x.mhead;
+  bk_sort_one<256>(x, b, sk, sl, hd, hd.valid != 0);
+}
+
+// 1024-thread blocks for the buckets of (kBkSmall, kBkCap] keys, from the list
+__global__ void __launch_bounds__(1024) k_bk_sort_big(BkSortArgs x) {
+  extern __shared__ uint64_t bsm[];
+  uint64_t *sk = bsm;
+  uint32_t *sl = reinterpret_cast<uint32_t *>(bsm + kBkCap);
+  const Ctl *ctl = x.ctl;
+  if (ctl->err || ctl->bkfall) return;
+  ModelHead hd;
+  hd.valid = 0;
+  if (x.mhead) hd = *x.mhead;
+  const uint32_t nbig = ctl->nbigbk;
+  for (uint32_t i = blockIdx.x; i < nbig; i += gridDim.x) bk_sort_one<1024>(x, x.bk.big[i], sk, sl, hd, hd.valid != 0);
+}
+
+// Survivor and run-head offsets of every bucket: exclusive scans over the buckets;
+// the first survivor of a bucket starts a run unless the last survivor of the
+// nearest earlier bucket with survivors has the same leaf.  One block of 1024.
+__global__ void __launch_bounds__(1024) k_bk_offsets(BucketWork bk, uint32_t nbk, Ctl *ctl,
+                                                     uint32_t *__restrict__ run_start) {
+  __shared__ uint32_t wsum[33];
+  __shared__ uint32_t s_last[1024];   // last survivor leaf of each thread's buckets
+  __shared__ int32_t s_idx[1024];     // thread index, -1 when its buckets hold no survivor
+  if (ctl->err || ctl->bkfall) return;
+  const uint32_t t = threadIdx.x, per = (nbk + 1023) / 1024, b0 = t * per;
+  uint32_t sv = 0, lastleaf = kNoLeaf;
+  for (uint32_t q = 0; q < per; q++) {
+    const uint32_t b = b0 + q;
+    if (b >= nbk) break;
+    if (bk.surv[b]) {
+      sv += bk.surv[b];
+      lastleaf = bk.last[b];
+    }
+  }
+  s_last[t] = lastleaf;
+  // nearest earlier thread whose buckets hold survivors: an inclusive running
+  // maximum of (t if it has survivors, else -1), read at t - 1
+  const uint32_t lane = lane_id(), wid = t >> 5;
+  int32_t v = sv ? (int32_t)t : -1;
+#pragma unroll
+  for (uint32_t o = 1; o < 32; o <<= 1) {
+    const int32_t u = __shfl_up_sync(0xFFFFFFFFu, v, o);
+    if (lane >= o) v = u > v ? u : v;
+  }
+  __shared__ int32_t s_wmax[32];
+  if (lane == 31) s_wmax[wid] = v;
+  __syncthreads();
+  if (wid == 0) {
+    int32_t x = s_wmax[lane];
+#pragma unroll
+    for (uint32_t o = 1; o < 32; o <<= 1) {
+      const int32_t u = __shfl_up_sync(0xFFFFFFFFu, x, o);
+      if (lane >= o) x = u > x ? u : x;
+    }
+    s_wmax[lane] = x;
+  }
+  __syncthreads();
+  if (wid) v = s_wmax[wid - 1] > v ? s_wmax[wid - 1] : v;
+  s_idx[t] = v;
+  __syncthreads();
+  const int32_t pt = t ? s_idx[t - 1] : -1;
+  uint32_t prevleaf = pt >= 0 ? s_last[pt] : kNoLeaf;
+  uint32_t hc = 0;
+  for (uint32_t q = 0; q < per; q++) {
+    const uint32_t b = b0 + q;
+    if (b >= nbk) break;
+    if (!bk.surv[b]) continue;
+    const uint32_t hf = (prevleaf == kNoLeaf || prevleaf != bk.first[b]) ? 1u : 0u;
+    bk.hfirst[b] = hf;
+    hc += bk.hin[b] + hf;
+    prevleaf = bk.last[b];
+  }
+  uint32_t m, nr;
+  uint32_t so = block_excl_scan(sv, wsum, &m);
+  uint32_t ho = block_excl_scan(hc, wsum, &nr);
+  for (uint32_t q = 0; q < per; q++) {
+    const uint32_t b = b0 + q;
+    if (b >= nbk) break;
+    bk.soff[b] = so;
+    bk.hoff[b] = ho;
+    if (bk.surv[b]) {
+      so += bk.surv[b];
+      ho += bk.hin[b] + bk.hfirst[b];
+    }
+  }
+  if (t == 0) {
+    ctl->m = m;
+    ctl->nruns = nr;
+    run_start[nr] = m;
+  }
+}
+
+// survivors and run heads of every bucket to their places (one block per bucket,
+// 256 positions at a time)
+__global__ void __launch_bounds__(256) k_bk_write(PrepArgs a, const uint64_t *__restrict__ words,
+                                                  const uint32_t *__restrict__ lfull, BucketWork bk, uint32_t nbk,
+                                                  uint64_t *__restrict__ ukey, uint8_t *__restrict__ utag,
+                                                  uint32_t *__restrict__ uleaf, uint32_t *__restrict__ run_start,
+                                                  uint32_t *__restrict__ run_leaf, const Ctl *ctl) {
+  __shared__ uint32_t wsum[33];
+  if (ctl->err || ctl->bkfall) return;
+  const uint32_t b = blockIdx.x;
+  if (b >= nbk || bk.surv[b] == 0) return;
+  const uint32_t start = bk.start[b], nb = bk.start[b + 1] - start;
+  uint32_t so = bk.soff[b], ho = bk.hoff[b];
+  const uint32_t hf = bk.hfirst[b];
+  for (uint32_t base = 0; base < nb; base += 256) {
+    const uint32_t i = base + threadIdx.x;
+    const uint32_t lf = i < nb ? lfull[start + i] : kNoLeaf;
+    const uint32_t keep = lf != kNoLeaf;
+    uint32_t head = 0;
+    if (keep) {
+      int32_t j = (int32_t)i - 1;  // previous survivor of the bucket
+      while (j >= 0 && lfull[start + j] == kNoLeaf) --j;
+      head = j < 0 ? hf : (lfull[start + j] != lf);
+    }
+    uint32_t nk, nh;
+    const uint32_t ko = so + block_excl_scan(keep, wsum, &nk);
+    const uint32_t hoi = ho + block_excl_scan(head, wsum, &nh);
+    if (keep) {
+      const uint64_t w = words[start + i];
+      ukey[ko] = expand(w, a);
+      utag[ko] = (uint8_t)(w >> 63);
+      uleaf[ko] = lf;
+      if (head) {
+        run_start[hoi] = ko;
+        run_leaf[hoi] = lf;
+      }
+    }
+    so += nk;
+    ho += nh;
+  }
+}
+
 // ---- host launchers ----------------------------------------------------------------------
 static uint32_t grid_for(uint64_t n, uint32_t per_block, uint32_t cap) {
   uint64_t g = (n + per_block - 1) / per_block;
@@ -474,18 +797,82 @@ void launch_small_front(const FrontArgs &f, cudaStream_t s) {
                                                f.run_start, f.run_leaf, f.mhead, f.mpieces, P, S);
 }
 
+BkGeo bucket_geo(uint64_t n, uint32_t sbits) {
+  uint64_t P = 1;
+  while (P < n) P <<= 1;
+  uint32_t lp = 0;
+  while ((1ull << lp) < P) ++lp;
+  // about 128 to 256 keys per bucket, 32 to kBkMax buckets
+  int kb = (int)lp - 8;
+  if (kb < 5) kb = 5;
+  if (kb > 14) kb = 14;
+  const uint32_t sb = sbits + 1;  // sort word: compressed key << 1 | tag
+  if ((uint32_t)kb > sb) kb = (int)sb;
+  BkGeo g;
+  g.kb = (uint32_t)kb;
+  g.shift = sb - g.kb;
+  g.nbk = 1u << g.kb;
+  return g;
+}
+
+// shared-memory opt-in of the bucket kernels (the prep histogram holds up to kBkMax
+// counts, the large-bucket sort kBkCap keys and their leaves)
+static void bucket_attrs() {
+  static bool done = false;
+  if (done) return;
+  cudaFuncSetAttribute(k_prep, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(kBkMax * sizeof(uint32_t)));
+  cudaFuncSetAttribute(k_bk_sort_big, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       (int)(kBkCap * (sizeof(uint64_t) + sizeof(uint32_t))));
+  done = true;
+}
+
 void launch_prep(const FrontArgs &f, cudaStream_t s) {
+  bucket_attrs();
   const PrepArgs &a = f.prep;
   const uint64_t n = (uint64_t)a.n_ins + a.n_del;
+  const BkGeo bg = bucket_geo(n, a.sbits);
   note_launch();
-  k_init_batch<<<1, 256, 0, s>>>(f.ctl, f.hist, a.npass * 256u, (uint32_t)n);
+  k_init_batch<<<1, 256, 0, s>>>(f.ctl, f.hist, a.npass * 256u, f.bk.cnt, bg.nbk, (uint32_t)n);
   note_launch();
-  k_prep<<<grid_for(n, 256, 4 * 152), 256, 0, s>>>(a, f.ins, f.del, f.bufA, f.hist, f.ctl);
+  k_prep<<<grid_for(n, 256, 4 * 152), 256, bg.nbk * sizeof(uint32_t), s>>>(a, f.ins, f.del, f.bufA, f.bk.cnt,
+                                                                          bg.shift, bg.nbk, f.ctl);
+}
+
+void launch_front_buckets(const FrontArgs &f, uint64_t nb, cudaStream_t s, const cudaGraphConditionalHandle *fall) {
+  const PrepArgs &a = f.prep;
+  const BkGeo bg = bucket_geo(nb, a.sbits);
+  bucket_attrs();
+  note_launch();
+  k_bk_scan<<<1, 1024, 0, s>>>(f.bk, bg.nbk, f.ctl, fall ? *fall : cudaGraphConditionalHandle(), fall ? 1 : 0);
+  note_launch();
+  k_bk_scatter<<<grid_for(nb, 256 * 8, 152 * 8), 256, 0, s>>>(f.bufA, f.bufB, f.bk.cnt, bg.shift, f.ctl);
+  BkSortArgs x;
+  x.a = a;
+  x.words = f.bufB;
+  x.lfull = f.lfull;
+  x.bk = f.bk;
+  x.F = f.geo->F;
+  x.nleaves = f.geo->nleaves;
+  x.mhead = f.mhead;
+  x.mpieces = f.mpieces;
+  x.ctl = f.ctl;
+  note_launch();
+  k_bk_sort<<<bg.nbk, 256, 0, s>>>(x, bg.nbk);
+  note_launch();
+  k_bk_sort_big<<<152, 1024, kBkCap * (sizeof(uint64_t) + sizeof(uint32_t)), s>>>(x);
+  note_launch();
+  k_bk_offsets<<<1, 1024, 0, s>>>(f.bk, bg.nbk, f.ctl, f.run_start);
+  note_launch();
+  k_bk_write<<<bg.nbk, 256, 0, s>>>(a, f.bufB, f.lfull, f.bk, bg.nbk, f.ukey, f.utag, f.uleaf, f.run_start,
+                                     f.run_leaf, f.ctl);
 }
 
 // grids sized for `nb` keys (>= the batch); the kernels read the batch size from ctl
-void launch_sort(const FrontArgs &f, uint64_t nb, cudaStream_t s) {
+void launch_front_fallback(const FrontArgs &f, uint64_t nb, cudaStream_t s, bool gated) {
   const PrepArgs &a = f.prep;
+  const uint32_t *gate = gated ? &f.ctl->bkfall : nullptr;
+  note_launch();
+  k_bk_convert<<<grid_for(nb, 256, 4 * 152), 256, 0, s>>>(a, f.bufA, f.hist, f.ctl, gate);
   uint64_t *src = f.bufA, *dst = f.bufB;
   const bool large = nb >= kSortLargeFrom;
   const uint32_t st = large ? (uint32_t)((nb + kSortThreads * kSortItemsLarge - 1) / (kSortThreads * kSortItemsLarge))
@@ -494,20 +881,20 @@ void launch_sort(const FrontArgs &f, uint64_t nb, cudaStream_t s) {
     note_launch();
     if (large)
       k_sort_pass<kSortItemsLarge><<<st, kSortThreads, 0, s>>>(src, dst, f.hist, f.status, f.ctl, p, p * a.dbits,
-                                                               a.dbits);
+                                                               a.dbits, gate);
     else
       k_sort_pass<kSortItemsSmall><<<st, kSortThreads, 0, s>>>(src, dst, f.hist, f.status, f.ctl, p, p * a.dbits,
-                                                               a.dbits);
+                                                               a.dbits, gate);
     uint64_t *t = src; src = dst; dst = t;
   }
   // look-back epochs: pass p uses epoch + p, then the fixed slots of gpma_launch.h
   const uint32_t ct = comp_tiles(nb);
   note_launch();
   k_search_all<<<grid_for(nb, 256, 152 * 16), 256, 0, s>>>(a, src, f.lfull, f.geo->F, f.geo->nleaves, f.ctl, f.mhead,
-                                                           f.mpieces);
+                                                           f.mpieces, gate);
   note_launch();
   k_compact<<<ct, kScanThreads, 0, s>>>(a, src, f.lfull, f.ukey, f.utag, f.uleaf, f.run_start, f.run_leaf, f.status,
-                                        f.ctl);
+                                        f.ctl, gate);
 }
 
 }  // namespace gpk

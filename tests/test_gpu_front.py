@@ -1,0 +1,121 @@
+"""The update front end at the sizes where it changes form, against the oracle.
+
+Batches of at most 4096 keys are sorted in one block.  Larger batches go to
+buckets by the top bits of their sort words, and every bucket is sorted in shared
+memory: by a 256-thread block up to 2048 keys, by a 1024-thread block up to 16384.
+A batch with a bucket above 16384 keys (a heavily skewed batch) takes the
+radix-sort path.  Each case checks the layout slot for slot, the batch statistics
+and the exported edges, with the learned and the plain leaf search."""
+import numpy as np
+import pytest
+
+import oracle
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+import paper_1709_05061_gb300 as gp  # noqa: E402
+from paper_1709_05061_gb300 import workloads as W  # noqa: E402
+
+STAT_KEYS = ("n_inserted", "n_deleted", "n_ignored", "levels_climbed", "resized", "alg_bytes", "touched_leaves",
+             "covered_leaves", "merges", "delete_leaves")
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(np.asarray(a, dtype=np.uint64)).view(np.int64)).cuda()
+
+
+def host(t):
+    return t.cpu().numpy().view(np.uint64)
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    gp.build()
+    gp.lib()
+
+
+def mixed_batch(rng, V, live, n):
+    """n raw keys: new edges, inserts of stored edges, duplicates, deletes of stored
+    and of absent edges, and keys on both lists."""
+    k = n // 6
+    new = (rng.integers(0, V, k).astype(np.uint64) << np.uint64(32)) | rng.integers(0, V, k).astype(np.uint64)
+    present = live[rng.integers(0, live.size, k)] if live.size else new[:0]
+    dup = new[: k // 2]
+    dels = live[rng.integers(0, live.size, k)] if live.size else new[:0]
+    absent = (rng.integers(0, V, k // 2).astype(np.uint64) << np.uint64(32)) | rng.integers(0, V, k // 2).astype(np.uint64)
+    both = new[k // 2: k]
+    ins = rng.permutation(np.concatenate([new, present, dup]))
+    dl = rng.permutation(np.concatenate([dels, absent, both]))
+    return ins, dl
+
+
+def run_pair(V, batches, plain):
+    g = gp.Graph(V, leaf_size=64, plain_search=plain)
+    o = oracle.OraclePMA(V, L=64)
+    for ins, dels in batches:
+        st = g.update(dev(ins), dev(dels), stats=True)
+        rc, so = o.update(ins, dels)
+        assert rc == 0
+        for k in STAT_KEYS:
+            assert st[k] == so[k], (k, st[k], so[k])
+        lg, lo = host(g.layout()), o.layout()
+        assert lg.size == lo.size and np.count_nonzero(lg != lo) == 0
+    assert np.array_equal(host(g.export_sorted()), o.export_sorted())
+    assert g.check() == 0
+    g.close()
+
+
+@pytest.mark.parametrize("plain", [False, True])
+def test_batch_sizes_around_the_front_end_limits(plain):
+    V = 1 << 16
+    base = W.rmat_stream(16, 300_000, seed=61)
+    rng = np.random.default_rng(61)
+    batches = [(base, np.zeros(0, np.uint64))]
+    live = base.copy()
+    for n in (4096, 4097, 5000, 8192, 8193, 65_537, 262_144):
+        ins, dels = mixed_batch(rng, V, live, n)
+        batches.append((ins, dels))
+        live = np.array(sorted(set(live.tolist()) | set(ins.tolist()) - set(dels.tolist())), np.uint64)
+    run_pair(V, batches, plain)
+
+
+@pytest.mark.parametrize("hot", [3000, 12_000, 20_000, 60_000])
+def test_skewed_batches(hot):
+    """A source with `hot` new edges in one batch of about hot + 10,000 keys: one
+    bucket above 2048 keys (1024-thread sort), up to 16,384 keys (the largest a
+    block sorts), and above it (the radix-sort path)."""
+    V = 1 << 17
+    rng = np.random.default_rng(hot)
+    base = W.rmat_stream(17, 400_000, seed=62)
+    hub = np.uint64(7)
+    dst = rng.permutation(V)[:hot].astype(np.uint64)
+    star = (hub << np.uint64(32)) | dst
+    ins, dels = mixed_batch(rng, V, base, 10_000)
+    ins = rng.permutation(np.concatenate([ins, star]))
+    for plain in (False, True):
+        run_pair(V, [(base, np.zeros(0, np.uint64)), (ins, dels), (dels, star[: hot // 2])], plain)
+
+
+def test_invalid_key_in_a_large_batch_changes_nothing():
+    V = 1 << 15
+    g = gp.Graph(V, leaf_size=64)
+    base = W.rmat_stream(15, 200_000, seed=63)
+    g.update(dev(base), None, stats=True)
+    before = host(g.layout())
+    rng = np.random.default_rng(63)
+    ins, dels = mixed_batch(rng, V, base, 50_000)
+    for bad in ([(V << 32) | 1], [(1 << 32) | V]):
+        with pytest.raises(gp.GpmaError) as e:
+            g.update(dev(np.concatenate([ins, np.array(bad, np.uint64)])), dev(dels), stats=True)
+        assert e.value.code == gp.GPMA_EINVAL
+        assert np.array_equal(host(g.layout()), before)
+        g.update(dev(np.concatenate([ins, np.array(bad, np.uint64)])), dev(dels))
+        with pytest.raises(gp.GpmaError):
+            g.status()
+        assert np.array_equal(host(g.layout()), before)
+    assert g.check() == 0
+    g.close()

@@ -89,8 +89,7 @@ def test_served_queries_equal_alone(realtime, rate, coalesce):
     alone = replay_alone(V, stream[:window], reqs)
     served = g.export_sorted().cpu().numpy().view(np.uint64)
     assert np.array_equal(served, alone.export_sorted().cpu().numpy().view(np.uint64))
-    assert np.array_equal(served, o.export_sorted())
-    assert np.array_equal(g.layout().cpu().numpy().view(np.uint64), o.layout())
+    assert np.array_equal(served, o.export_sorted())  # layouts may differ: coalescing changes the batches
     assert g.check() == 0
 
 
