@@ -543,8 +543,11 @@ bool capture_update(gpma *h, FrontArgs &f, uint32_t nb, bool stats, bool grow, G
   cudaGraph_t graph = nullptr;
   if (cudaGraphCreate(&graph, 0) != cudaSuccess) return false;
   cudaGraphConditionalHandle cond, cgrow, cmerge, cfall;
-  bool ok = cudaGraphConditionalHandleCreate(&cond, graph, 0, cudaGraphCondAssignDefault) == cudaSuccess &&
-            cudaGraphConditionalHandleCreate(&cfall, graph, 0, cudaGraphCondAssignDefault) == cudaSuccess;
+  bool ok = cudaGraphConditionalHandleCreate(&cond, graph, 0, cudaGraphCondAssignDefault) == cudaSuccess;
+  // every handle of the graph must belong to a conditional node: the radix-sort
+  // fallback exists only behind the bucketed front end
+  if (!small_front(nb))
+    ok = ok && cudaGraphConditionalHandleCreate(&cfall, graph, 0, cudaGraphCondAssignDefault) == cudaSuccess;
   if (grow) {
     ok = ok && cudaGraphConditionalHandleCreate(&cgrow, graph, 0, cudaGraphCondAssignDefault) == cudaSuccess &&
          cudaGraphConditionalHandleCreate(&cmerge, graph, 0, cudaGraphCondAssignDefault) == cudaSuccess;
