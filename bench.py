@@ -80,9 +80,6 @@ def parse():
                     help="load the window, run one call of this kind --repeat times and exit (a small, "
                          "self-contained run for ncu; GPMA_NO_GRAPHS=1 launches an update's kernels directly)")
     ap.add_argument("--repeat", type=int, default=1)
-    ap.add_argument("--stream-priority", choices=["equal", "pagerank-first"], default="equal",
-                    help="pagerank-first: the update and PageRank run on a high-priority stream, BFS and CC "
-                         "on a low-priority one (the update-PageRank chain is the step's critical path)")
     return ap.parse_args()
 
 
@@ -98,9 +95,7 @@ def workload_config(a, world):
         "leaf_size": LEAF,
         "l2": "inputs larger than L2: 268 MB array streamed by every step; sweep flushes L2 between batches",
         "parallelism": f"replicas x{world}" if world > 1 else "single GPU",
-        "streams": ("update + PageRank on a high-priority stream, BFS + CC on a low-priority one"
-                    if a.stream_priority == "pagerank-first" else
-                    "update + PageRank on one stream, BFS + CC on a second (equal priority)"),
+        "streams": "update + PageRank on one stream, BFS + CC on a second",
     }
 
 
@@ -254,8 +249,6 @@ def run_gpu(a, stream, rank, world, dist):
     def to_dev(x):
         return torch.from_numpy(np.ascontiguousarray(x).view(np.int64)).to(dev)
 
-    if a.stream_priority == "pagerank-first":
-        torch.cuda.set_stream(torch.cuda.Stream(priority=-1))
     g = gp.Graph(V, leaf_size=LEAF, push_pagerank=a.push_pagerank)
     st = g.update(to_dev(win.initial), None, stats=True)
     torch.cuda.synchronize()
@@ -315,7 +308,7 @@ def run_gpu(a, stream, rank, world, dist):
 
     # The three queries only read the array: BFS and CC run on a second stream beside
     # PageRank, and the next update waits for both.
-    cs, qs = torch.cuda.current_stream(), torch.cuda.Stream(priority=0)
+    cs, qs = torch.cuda.current_stream(), torch.cuda.Stream()
     ev_upd, ev_q = torch.cuda.Event(), torch.cuda.Event()
 
     def queries(rank_o, depth_o, label_o):

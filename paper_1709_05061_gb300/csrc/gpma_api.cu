@@ -323,7 +323,7 @@ void free_work(gpma *h, cudaStream_t s) {
   Work &w = h->w;
   void *ptrs[] = {h->bufA,   h->bufB,     w.ukey,  w.utag,     w.uleaf,   w.run_start, w.eflag,
                   w.rleaf,   w.rdelta,    w.rinfo, w.rdel,     w.pkey,    w.pleaf,     w.erun, w.eleaf,
-                  w.elvl,    w.etop,      w.seg_node, w.seg_top, w.seg_pstart, w.seg_lpre, w.status, w.bk};
+                  w.elvl,    w.etop,      w.seg_node, w.seg_top, w.seg_pstart, w.seg_lpre, w.status, w.rs};
   for (void *p : ptrs) dfree(h, p, s);
   memset(&h->w, 0, sizeof(Work));
   h->bufA = h->bufB = nullptr;
@@ -339,7 +339,7 @@ int ensure_work(gpma *h, uint64_t n, cudaStream_t s) {
   free_work(h, s);
   Work &w = h->w;
   const uint64_t c1 = cap + 1;
-  const uint64_t st = (uint64_t)sort_tiles(cap) * 256 + comp_tiles(cap) * 2 + 64;
+  const uint64_t st = (uint64_t)comp_tiles(cap) * 2 + 64;
   bool ok = dalloc(h, &h->bufA, cap, s) && dalloc(h, &h->bufB, cap, s) && dalloc(h, &w.ukey, cap, s) &&
             dalloc(h, &w.utag, cap, s) && dalloc(h, &w.uleaf, cap, s) && dalloc(h, &w.run_start, c1, s) &&
             dalloc(h, &w.eflag, cap, s) && dalloc(h, &w.rleaf, cap, s) && dalloc(h, &w.rdelta, cap, s) &&
@@ -347,7 +347,7 @@ int ensure_work(gpma *h, uint64_t n, cudaStream_t s) {
             dalloc(h, &w.pleaf, cap, s) && dalloc(h, &w.erun, c1, s) && dalloc(h, &w.eleaf, cap, s) && dalloc(h, &w.elvl, cap, s) &&
             dalloc(h, &w.etop, cap, s) && dalloc(h, &w.seg_node, c1, s) && dalloc(h, &w.seg_top, c1, s) &&
             dalloc(h, &w.seg_pstart, c1, s) && dalloc(h, &w.seg_lpre, c1, s) && dalloc(h, &w.status, st, s) &&
-            dalloc(h, &w.bk, kBkWords, s);
+            dalloc(h, &w.rs, front_scratch_words(cap), s);
   if (!ok) {
     free_work(h, s);
     return GPMA_ENOMEM;
@@ -542,12 +542,8 @@ bool capture_update(gpma *h, FrontArgs &f, uint32_t nb, bool stats, bool grow, G
   if (!gc.cap2 && cudaStreamCreateWithFlags(&gc.cap2, cudaStreamNonBlocking) != cudaSuccess) return false;
   cudaGraph_t graph = nullptr;
   if (cudaGraphCreate(&graph, 0) != cudaSuccess) return false;
-  cudaGraphConditionalHandle cond, cgrow, cmerge, cfall;
+  cudaGraphConditionalHandle cond, cgrow, cmerge;
   bool ok = cudaGraphConditionalHandleCreate(&cond, graph, 0, cudaGraphCondAssignDefault) == cudaSuccess;
-  // every handle of the graph must belong to a conditional node: the radix-sort
-  // fallback exists only behind the bucketed front end
-  if (!small_front(nb))
-    ok = ok && cudaGraphConditionalHandleCreate(&cfall, graph, 0, cudaGraphCondAssignDefault) == cudaSuccess;
   if (grow) {
     ok = ok && cudaGraphConditionalHandleCreate(&cgrow, graph, 0, cudaGraphCondAssignDefault) == cudaSuccess &&
          cudaGraphConditionalHandleCreate(&cmerge, graph, 0, cudaGraphCondAssignDefault) == cudaSuccess;
@@ -567,11 +563,7 @@ bool capture_update(gpma *h, FrontArgs &f, uint32_t nb, bool stats, bool grow, G
                          t);
     if (h->mhead) launch_train_model(g, h->mhead, h->mpieces, h->ctl, true, t);
   };
-  if (!small_front(nb)) {
-    // buckets sorted in shared memory; the radix-sort path only when a bucket is too large
-    launch_front_buckets(f, nb, gc.cap, &cfall);
-    ok = capture_if(gc.cap, gc.cap2, cfall, [&](cudaStream_t t) { launch_front_fallback(f, nb, t, false); });
-  }
+  if (!small_front(nb)) launch_front(f, nb, gc.cap);
   launch_leaf_pass(g, h->ctl, h->w, nb, gc.cap);
   note_launch();
   k_gate<<<1, 1, 0, gc.cap>>>(h->ctl, cond);
@@ -712,18 +704,18 @@ int update(gpma *h, const uint64_t *ins, uint64_t n_ins, const uint64_t *del, ui
   f.run_start = h->w.run_start;
   f.run_leaf = h->w.rleaf;
   f.lfull = h->w.pleaf;  // free until the escalation compacts pending inserts
-  {
-    uint32_t *p = h->w.bk;
-    const uint32_t K = kBkMax + 1;
-    f.bk = BucketWork{p, p + K, p + 2 * K, p + 3 * K, p + 4 * K, p + 5 * K, p + 6 * K, p + 7 * K, p + 8 * K, p + 9 * K};
-  }
+  f.rs = h->w.rs;
   const uint32_t n32 = (uint32_t)n;
   Phase whole(h->prof, GPMA_PROF_UPDATE, s);
   // level-0 merges move pivots only inside their leaves and the search widens
   // its window when the model has drifted; retrain now and then all the same
   if (h->mhead && ++h->since_train >= 64) train_model(h, s);
+  // one batch-size bucket (a power of two) sizes the front end's grids and tiles,
+  // in a replayed graph and in directly launched kernels alike
+  uint64_t nb_front = kSmallBatch;
+  while (nb_front < n) nb_front <<= 1;
   if (small_front(n)) launch_small_front(f, s);
-  else launch_prep(f, s);
+  else launch_prep(f, nb_front, s);
   // the root can only refuse inserts when the count might exceed its bound
   const bool may_fail = h->count_ub + n_ins > h->geo.maxc[h->geo.h];
   // such a batch still replays a graph (no host wait) when one level of growth
@@ -738,8 +730,7 @@ int update(gpma *h, const uint64_t *ins, uint64_t n_ins, const uint64_t *del, ui
   bool resized = false;
   if ((!may_fail || grow) && h->graphs->enabled) {
     // replay: sort .. segment merge as one graph, grids sized for the bucket
-    uint64_t bucket = kSmallBatch;  // one graph serves every batch of the fused front end
-    while (bucket < n) bucket <<= 1;
+    const uint64_t bucket = nb_front;  // one graph serves every batch of the fused front end
     const uint32_t nb = (uint32_t)bucket;
     // the key layout of a guard batch differs: never share its graph
     const uint64_t key = h->alloc_epoch + (allow_guards ? (1ull << 62) : 0) + (grow ? (1ull << 61) : 0);
@@ -760,10 +751,7 @@ int update(gpma *h, const uint64_t *ins, uint64_t n_ins, const uint64_t *del, ui
   } else {
     {
       Phase ph(h->prof, GPMA_PROF_SORT, s);
-      if (!small_front(n)) {
-        launch_front_buckets(f, n, s, nullptr);
-        launch_front_fallback(f, n, s, true);
-      }
+      if (!small_front(n)) launch_front(f, nb_front, s);
     }
     {
       Phase ph(h->prof, GPMA_PROF_LEAF, s);

@@ -83,8 +83,6 @@ struct Ctl {
   uint32_t resized;    // this call grew the array on the device (into the spare)
   uint32_t nvlong;     // runs longer than kLongRun, left to the chunked level-0 path
   uint32_t spin_limit; // polls a bounded wait may make before it gives up (0: the built-in limits)
-  uint32_t bkfall;     // some bucket of the batch is above kBkCap: the radix-sort path runs
-  uint32_t nbigbk;     // buckets above kBkSmall (sorted by 1024-thread blocks)
 };
 
 __device__ __forceinline__ bool is_guard(uint64_t k) {

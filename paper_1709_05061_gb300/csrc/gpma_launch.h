@@ -24,32 +24,6 @@ struct PrepArgs {
   uint32_t sbits;  // sorted bits of the compressed key (the tag is not among them)
 };
 
-// Front end of batches above kSmallBatch keys: the sort word (compressed key << 1 |
-// tag) goes to one of nbk buckets by its top kb bits; every bucket is then sorted
-// in one block's shared memory.  Per-bucket arrays, kBkMax entries each (+1 where
-// noted), carved from one allocation.
-constexpr uint32_t kBkMax = 16384;    // most buckets of one batch
-constexpr uint32_t kBkSmall = 2048;   // keys a 256-thread block sorts (smaller buckets)
-constexpr uint32_t kBkCap = 16384;    // keys a 1024-thread block sorts; a larger bucket
-                                      // sends the batch to the radix-sort path
-struct BucketWork {
-  uint32_t *cnt;     // keys per bucket, then the scatter cursors
-  uint32_t *start;   // kBkMax + 1: first position of every bucket (exclusive scan)
-  uint32_t *surv;    // survivors of reading R2 per bucket
-  uint32_t *hin;     // run heads per bucket, not counting its first survivor
-  uint32_t *first;   // leaf of the first / last survivor (kNoLeaf: none)
-  uint32_t *last;
-  uint32_t *soff;    // kBkMax + 1: survivors before the bucket
-  uint32_t *hoff;    // kBkMax + 1: run heads before the bucket
-  uint32_t *hfirst;  // 1 if the bucket's first survivor starts a run
-  uint32_t *big;     // buckets with more than kBkSmall keys
-};
-constexpr uint64_t kBkWords = 10ull * (kBkMax + 1);
-struct BkGeo {
-  uint32_t kb, shift, nbk;  // bucket = sort word >> shift, nbk = 2^kb buckets
-};
-BkGeo bucket_geo(uint64_t n, uint32_t sbits);
-
 struct FrontArgs {
   PrepArgs prep;
   const ModelHead *mhead;  // learned leaf search (nullptr: plain binary search)
@@ -66,7 +40,7 @@ struct FrontArgs {
   uint32_t *run_start;
   uint32_t *run_leaf;
   uint32_t *lfull;        // leaf of every sorted word (kNoLeaf if dropped), before compaction
-  BucketWork bk;
+  uint32_t *rs;           // front_scratch_words(nb) words: per-tile digit counts, block summaries
 };
 
 // per-batch work arrays of the update kernels
@@ -91,11 +65,10 @@ struct Work {
   uint32_t *seg_pstart;
   uint32_t *seg_lpre;
   uint64_t *status;
-  uint32_t *bk;       // kBkWords words of BucketWork
+  uint32_t *rs;       // front_scratch_words(cap) words for the radix front end
   uint32_t cap;       // capacity of the per-key arrays
 };
 
-uint32_t sort_tiles(uint64_t n);
 uint32_t comp_tiles(uint64_t n);
 // k_init_batch + k_prep (take the batch's own pointers and sizes)
 // runs longer than this (bulk loads) take the chunked level-0 path: many warps
@@ -105,16 +78,13 @@ constexpr uint32_t kLongRun = 1024;
 constexpr uint32_t kSmallBatch = 4096;
 bool small_front(uint64_t n);
 void launch_small_front(const FrontArgs &f, cudaStream_t s);
-// k_init_batch + k_prep (validation, sort words, bucket counts)
-void launch_prep(const FrontArgs &f, cudaStream_t s);
-// Sort, unique/cancel, leaf search and run heads of a batch of more than
-// kSmallBatch keys by buckets; grids for nb >= batch keys (the kernels read the
-// batch size from ctl).  `fall` (graph capture): the conditional that
-// launch_front_fallback's IF node waits on, set when some bucket exceeds kBkCap.
-void launch_front_buckets(const FrontArgs &f, uint64_t nb, cudaStream_t s, const cudaGraphConditionalHandle *fall);
-// The same by stable LSD radix passes over the whole batch, for batches with a
-// bucket above kBkCap; with `gated` every kernel first checks that flag itself.
-void launch_front_fallback(const FrontArgs &f, uint64_t nb, cudaStream_t s, bool gated);
+// Batches of more than kSmallBatch keys; `nb` (>= the batch, the same in the two
+// calls) sizes the grids, the kernels read the batch size from ctl.
+// k_init_batch + k_prep: validation, sort words, first-pass counts per tile
+void launch_prep(const FrontArgs &f, uint64_t nb, cudaStream_t s);
+// the radix passes, unique/cancel + leaf search, survivors and run heads
+void launch_front(const FrontArgs &f, uint64_t nb, cudaStream_t s);
+uint64_t front_scratch_words(uint64_t nb);  // size of FrontArgs::rs for batches of up to nb keys
 
 // k_update.cu
 void launch_leaf_pass(const Geo &g, Ctl *ctl, const Work &w, uint32_t n, cudaStream_t s);

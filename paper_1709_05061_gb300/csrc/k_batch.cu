@@ -1,23 +1,22 @@
 // k_batch.cu -- front end of one update batch (Algorithm "GPMA+ Segment-Oriented
 // Insertion", Sec. 5.2, lines Sort(U) and BinarySearchLeafSegments(U)):
-//   k_init_batch  reset the per-call control block and histograms
-//   k_prep        validate keys, compress (src, dst, insert/delete tag) into one
-//                 sort word, count the words of every bucket (top bits)
-//   k_bk_scan     bucket offsets; flags a bucket too large for shared memory
-//   k_bk_scatter  every word to its bucket
-//   k_bk_sort     one bucket per block: sort in shared memory, unique + insert/
-//                 delete cancellation, the leaf search of every survivor (learned
-//                 model when trained, else binary search; both give the same
-//                 leaf), the bucket's survivor and run-head counts
-//   k_bk_offsets  survivor and run-head offsets of every bucket (one block)
-//   k_bk_write    survivors and run heads to their places
+//   k_init_batch  reset the per-call control block and the radix histograms
+//   k_prep        one sort tile per block: validate keys, compress (src, dst,
+//                 insert/delete tag) into one sortable word, count the tile's
+//                 first-pass digits and every pass's digits over the batch
+//   per radix pass (stable LSD, reduce then scan: no chained waits between tiles)
+//   k_rcolscan    per digit, the exclusive prefix of the per-tile counts plus the
+//                 digit's global offset: where every tile's keys of that digit go
+//   k_rscatter    one tile per block: rank the keys by digit, write them to their
+//                 places, count the next pass's digits per destination tile
+//   k_rsearch     1024 sorted words per block: unique + insert/delete cancellation,
+//                 the leaf search of every survivor (learned model when trained,
+//                 else binary search; both give the same leaf), the block's
+//                 survivor and run-head counts
+//   k_toffsets    survivor and run-head offsets of every block (one block)
+//   k_twrite      survivors and the heads of their runs of equal leaf to their places
 //   k_small_front all of the above in one block for batches of at most
 //                 kSmallBatch keys (bitonic sort in shared memory)
-// A batch with a bucket above kBkCap keys (a heavily skewed batch) takes the
-// radix-sort path instead: k_bk_convert (radix histograms), k_sort_pass (one
-// stable LSD pass with per-digit look-back) per digit, k_search_all (unique/
-// cancel + leaf search, one word per thread) and k_compact (single-pass
-// compaction of survivors and run heads).
 #include "gpma_dev.cuh"
 #include "gpma_launch.h"
 #include "scan_dev.cuh"
@@ -25,11 +24,15 @@
 namespace gpk {
 
 constexpr int kSortThreads = 256;
-// keys per thread per pass: 8 for small batches (more tiles in flight, fewer
-// registers), 16 for large ones (half the tiles on the look-back chain)
-constexpr int kSortItemsSmall = 8, kSortItemsLarge = 16;
-constexpr uint64_t kSortLargeFrom = 1ull << 19;
-constexpr int kSortTile = kSortThreads * kSortItemsSmall;  // status words are sized for the small tile
+// keys per thread of a sort tile: 4 below kSortLargeFrom keys (more tiles than
+// SMs), 16 from there on (fewer, fuller tiles)
+constexpr int kSortItemsSmall = 4, kSortItemsLarge = 16;
+constexpr uint64_t kSortLargeFrom = 1ull << 18;
+constexpr uint32_t kSearchTile = 1024;  // sorted words per block of the search and the compaction
+
+static __host__ __device__ __forceinline__ uint32_t sort_tile_keys(uint64_t n) {
+  return kSortThreads * (n >= kSortLargeFrom ? kSortItemsLarge : kSortItemsSmall);
+}
 
 // ---- key compression -----------------------------------------------------------------
 // Graph mode: word = (src << db) | d with d = dst, or d = V for a guard (so a
@@ -56,9 +59,8 @@ __device__ __forceinline__ uint64_t expand(uint64_t w, const PrepArgs &a) {
   return (src << 32) | dst;
 }
 
-__global__ void k_init_batch(Ctl *ctl, uint32_t *hist, uint32_t nhist, uint32_t *bcnt, uint32_t nbk, uint32_t n) {
+__global__ void k_init_batch(Ctl *ctl, uint32_t *hist, uint32_t nhist, uint32_t n) {
   for (uint32_t i = threadIdx.x; i < nhist; i += blockDim.x) hist[i] = 0;
-  for (uint32_t i = threadIdx.x; i < nbk; i += blockDim.x) bcnt[i] = 0;
   if (threadIdx.x == 0) {
     ctl->err = 0;
     ctl->n = n;
@@ -75,20 +77,27 @@ __global__ void k_init_batch(Ctl *ctl, uint32_t *hist, uint32_t nhist, uint32_t 
     ctl->levels_climbed = 0;
     ctl->n_merged0 = 0;
     for (int i = 0; i < kMaxLv; i++) ctl->merges[i] = 0;
-    ctl->bkfall = ctl->nbigbk = 0;
   }
 }
 
-// validation, sort words (compressed key << 1 | tag) and bucket counts
-__global__ void __launch_bounds__(256) k_prep(PrepArgs a, const uint64_t *__restrict__ ins,
-                                              const uint64_t *__restrict__ del, uint64_t *__restrict__ out,
-                                              uint32_t *__restrict__ bcnt, uint32_t shift, uint32_t nbk, Ctl *ctl) {
-  extern __shared__ uint32_t bh[];  // nbk counts
-  for (uint32_t i = threadIdx.x; i < nbk; i += blockDim.x) bh[i] = 0;
+// One sort tile (blockDim * ITEMS keys) per block: validation, compression, the
+// tile's first-pass digit counts (column-major: H0[d * T + tile]) and the batch's
+// digit counts of every pass (hist[p * 256 + d]).
+template <int ITEMS>
+__global__ void __launch_bounds__(kSortThreads) k_prep(PrepArgs a, const uint64_t *__restrict__ ins,
+                                                       const uint64_t *__restrict__ del, uint64_t *__restrict__ out,
+                                                       uint32_t *__restrict__ hist, uint32_t *__restrict__ H0,
+                                                       uint32_t T, Ctl *ctl) {
+  __shared__ uint32_t sh[8 * 256];
+  for (uint32_t i = threadIdx.x; i < a.npass * 256u; i += blockDim.x) sh[i] = 0;
   __syncthreads();
   const uint32_t n = a.n_ins + a.n_del;
+  const uint32_t mask = (1u << a.dbits) - 1u;
   bool bad = false;
-  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+#pragma unroll
+  for (int r = 0; r < ITEMS; r++) {
+    const uint32_t i = blockIdx.x * (kSortThreads * ITEMS) + r * kSortThreads + threadIdx.x;
+    if (i >= n) break;
     const uint32_t tag = i >= a.n_ins;
     const uint64_t key = tag ? del[i - a.n_ins] : ins[i];
     bool ok;
@@ -99,85 +108,95 @@ __global__ void __launch_bounds__(256) k_prep(PrepArgs a, const uint64_t *__rest
       ok = src < a.V && (dst < a.V || (a.allow_guards && !tag && dst == 0xFFFFFFFFull));
     }
     bad |= !ok;
-    const uint64_t w = ok ? ((compress(key, 0, a) << 1) | tag) : 0ull;
+    const uint64_t w = ok ? compress(key, tag, a) : 0ull;
     out[i] = w;
-    atomicAdd(&bh[(uint32_t)(w >> shift)], 1u);
-  }
-  if (__any_sync(0xFFFFFFFFu, bad) && lane_id() == 0) atomicOr(&ctl->err, kErrKey);
-  __syncthreads();
-  for (uint32_t i = threadIdx.x; i < nbk; i += blockDim.x)
-    if (bh[i]) atomicAdd(&bcnt[i], bh[i]);
-}
-
-// radix-sort path: sort words back to the radix layout (tag in bit 63) and the
-// digit histograms of every pass
-__global__ void __launch_bounds__(256) k_bk_convert(PrepArgs a, uint64_t *__restrict__ buf,
-                                                    uint32_t *__restrict__ hist, Ctl *ctl, const uint32_t *gate) {
-  if (gate && *gate == 0) return;
-  __shared__ uint32_t sh[8 * 256];
-  for (uint32_t i = threadIdx.x; i < a.npass * 256u; i += blockDim.x) sh[i] = 0;
-  __syncthreads();
-  const uint32_t n = ctl->n;
-  const uint32_t mask = (1u << a.dbits) - 1u;
-  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-    const uint64_t w = buf[i];
-    const uint64_t kw = w >> 1;
-    buf[i] = kw | ((w & 1ull) << 63);
+    const uint64_t kw = w & ~kTagBit;
     for (uint32_t p = 0; p < a.npass; p++)
       atomicAdd(&sh[p * 256 + (uint32_t)((kw >> (p * a.dbits)) & mask)], 1u);
   }
-  __syncthreads();
+  if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(&ctl->err, kErrKey);
+  for (uint32_t d = threadIdx.x; d <= mask; d += blockDim.x) H0[(uint64_t)d * T + blockIdx.x] = sh[d];
   for (uint32_t i = threadIdx.x; i < a.npass * 256u; i += blockDim.x)
     if (sh[i]) atomicAdd(&hist[i], sh[i]);
 }
 
-// One stable LSD pass.  A tile is ITEMS rounds x 256 keys; warp w owns the
-// contiguous sub-tile [w*32*ITEMS, (w+1)*32*ITEMS) so ranks inside a warp need no
-// block barrier; tiles are ordered by ticket and chained by a per-digit look-back.
-template <int kSortItems>
-__global__ void __launch_bounds__(kSortThreads) k_sort_pass(const uint64_t *__restrict__ src,
-                                                            uint64_t *__restrict__ dst, const uint32_t *hist,
-                                                            uint64_t *status, Ctl *ctl, uint32_t pass,
-                                                            uint32_t shift, uint32_t dbits, const uint32_t *gate) {
+// Pass `pass`, digit blockIdx.x: H[d * T + t] (keys of tile t with digit d)
+// becomes the position of the tile's first such key: the digit's global offset
+// (keys of smaller digits, from the batch histogram) plus the same digit's keys
+// in earlier tiles.  Also zeroes the next pass's counts Hn (may be nullptr).
+__global__ void __launch_bounds__(1024) k_rcolscan(uint32_t *__restrict__ H, uint32_t *__restrict__ Hn, uint32_t T,
+                                                   const uint32_t *__restrict__ hist, const Ctl *ctl) {
+  __shared__ uint32_t wsum[33];
+  __shared__ uint32_t s_base;
+  if (ctl->err) return;
+  const uint32_t d = blockIdx.x;
+  if (threadIdx.x < 32) {  // sum of the counts of the smaller digits
+    uint32_t v = 0;
+    for (uint32_t e = threadIdx.x; e < d; e += 32) v += hist[e];
+    v = warp_sum(v);
+    if (threadIdx.x == 0) s_base = v;
+  }
+  __syncthreads();
+  uint32_t carry = s_base;
+  uint32_t *col = H + (uint64_t)d * T;
+  constexpr uint32_t kPer = 8;
+  for (uint32_t c = 0; c < T; c += 1024 * kPer) {
+    const uint32_t t0 = c + threadIdx.x * kPer;
+    uint32_t v[kPer], loc = 0;
+#pragma unroll
+    for (uint32_t q = 0; q < kPer; q++) {
+      v[q] = t0 + q < T ? col[t0 + q] : 0u;
+      loc += v[q];
+    }
+    uint32_t total;
+    uint32_t run = carry + block_excl_scan(loc, wsum, &total);
+#pragma unroll
+    for (uint32_t q = 0; q < kPer; q++) {
+      if (t0 + q < T) col[t0 + q] = run;
+      run += v[q];
+    }
+    carry += total;
+  }
+  if (Hn)
+    for (uint32_t t = threadIdx.x; t < T; t += 1024) Hn[(uint64_t)d * T + t] = 0;
+}
+
+// One stable LSD pass over tile blockIdx.x (ITEMS rounds x 256 keys; warp w owns
+// the contiguous sub-tile [w*32*ITEMS, (w+1)*32*ITEMS), so ranks inside a warp
+// need no block barrier).  O[d * T + t]: where the tile's keys of digit d start.
+// With Hn, every key also counts its next-pass digit in its destination tile.
+template <int ITEMS>
+__global__ void __launch_bounds__(kSortThreads) k_rscatter(const uint64_t *__restrict__ src,
+                                                           uint64_t *__restrict__ dst, const uint32_t *__restrict__ O,
+                                                           uint32_t *__restrict__ Hn, uint32_t T, uint32_t shift,
+                                                           uint32_t nshift, uint32_t dbits, const Ctl *ctl) {
   __shared__ uint32_t wcnt[kSortThreads / 32][256];
   __shared__ uint32_t gbase[256];
   __shared__ uint32_t ltile[256];  // digit totals of the tile, then their exclusive prefix
-  __shared__ uint64_t skey[kSortThreads * kSortItems];
-  __shared__ uint32_t hs[256];  // this pass's global digit counts, then their exclusive prefix
-  __shared__ uint32_t s_tile;
-  if (gate && *gate == 0) return;
+  __shared__ uint64_t skey[kSortThreads * ITEMS];
+  if (ctl->err) return;
   const uint32_t n = ctl->n;
   const uint32_t w = threadIdx.x >> 5, lane = lane_id();
   const uint32_t radix = 1u << dbits, mask = radix - 1u;
+  const uint32_t tile = blockIdx.x;
   for (uint32_t d = threadIdx.x; d < 256; d += kSortThreads) {
     for (int q = 0; q < kSortThreads / 32; q++) wcnt[q][d] = 0;
-    hs[d] = d < radix ? hist[pass * 256 + d] : 0u;
+    gbase[d] = d < radix ? O[(uint64_t)d * T + tile] : 0u;
   }
-  if (threadIdx.x == 0) s_tile = atomicAdd(&ctl->ticket[pass], 1u);
   __syncthreads();
-  if (w == 0) {  // the global offsets, while the other warps rank their keys
-    uint32_t carry = 0;
-    for (int c = 0; c < 256; c += 32) {
-      const uint32_t v = hs[c + lane];
-      const uint32_t inc = warp_incl_scan(v);
-      hs[c + lane] = carry + inc - v;
-      carry += __shfl_sync(0xFFFFFFFFu, inc, 31);
-    }
-  }
-  const uint32_t tile = s_tile;
-  const uint64_t base = (uint64_t)tile * (kSortThreads * kSortItems) + w * (kSortItems * 32);
-  uint64_t key[kSortItems];
-  uint32_t rank[kSortItems];
-  uint32_t dig[kSortItems];
+  const uint64_t base = (uint64_t)tile * (kSortThreads * ITEMS) + w * (ITEMS * 32);
+  uint64_t key[ITEMS];
+  uint32_t rank[ITEMS];
+  uint32_t dig[ITEMS];
 #pragma unroll
-  for (int r = 0; r < kSortItems; r++) {
-    uint64_t idx = base + r * 32 + lane;
-    bool valid = idx < n;
+  for (int r = 0; r < ITEMS; r++) {
+    const uint64_t idx = base + r * 32 + lane;
+    const bool valid = idx < n;
     key[r] = valid ? src[idx] : 0ull;
     dig[r] = valid ? (uint32_t)(((key[r] & ~kTagBit) >> shift) & mask) : 0xFFFFu;
   }
 #pragma unroll
-  for (int r = 0; r < kSortItems; r++) {
+  for (int r = 0; r < ITEMS; r++) {
     // lanes holding the same digit, from one ballot per digit bit (cheaper than match.any)
     uint32_t peers = 0xFFFFFFFFu;
     for (uint32_t b = 0; b < dbits; b++) {
@@ -198,20 +217,16 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_pass(const uint64_t *__re
     __syncwarp();
   }
   __syncthreads();
-  // per digit: exclusive prefix over warps, tile total, look-back, global base
-  for (uint32_t d = threadIdx.x; d < radix; d += kSortThreads) {
+  // per digit: exclusive prefix over the warps, and the tile's total
+  for (uint32_t d = threadIdx.x; d < 256; d += kSortThreads) {
     uint32_t run = 0;
     for (int q = 0; q < kSortThreads / 32; q++) {
-      uint32_t c = wcnt[q][d];
+      const uint32_t c = wcnt[q][d];
       wcnt[q][d] = run;
       run += c;
     }
     ltile[d] = run;
-    uint32_t excl = lookback(status, 256, d, tile, run, ctl->epoch + pass, ctl);
-    gbase[d] = excl;
   }
-  for (uint32_t d = radix + threadIdx.x; d < 256; d += kSortThreads) ltile[d] = 0;
-  // exclusive scan of the global histogram of this pass
   __syncthreads();
   if (threadIdx.x < 32) {  // digit offsets inside the tile
     uint32_t carry = 0;
@@ -226,16 +241,17 @@ __global__ void __launch_bounds__(kSortThreads) k_sort_pass(const uint64_t *__re
   // the tile sorted by digit in shared memory, then written out in digit runs
   // (consecutive keys of one digit go to consecutive addresses)
 #pragma unroll
-  for (int r = 0; r < kSortItems; r++)
+  for (int r = 0; r < ITEMS; r++)
     if (dig[r] != 0xFFFFu) skey[ltile[dig[r]] + wcnt[w][dig[r]] + rank[r]] = key[r];
   __syncthreads();
-  const uint64_t t0 = (uint64_t)tile * (kSortThreads * kSortItems);
-  const uint32_t cnt = t0 >= n ? 0u : (n - t0 < kSortThreads * kSortItems ? (uint32_t)(n - t0) : kSortThreads * kSortItems);
+  const uint64_t t0 = (uint64_t)tile * (kSortThreads * ITEMS);
+  const uint32_t cnt = t0 >= n ? 0u : (n - t0 < kSortThreads * ITEMS ? (uint32_t)(n - t0) : kSortThreads * ITEMS);
   for (uint32_t i = threadIdx.x; i < cnt; i += kSortThreads) {
     const uint64_t k = skey[i];
     const uint32_t d = (uint32_t)(((k & ~kTagBit) >> shift) & mask);
-    const uint32_t pos = hs[d] + gbase[d] + (i - ltile[d]);
-    if (pos < n) dst[pos] = k;  // always true unless a look-back gave up
+    const uint32_t pos = gbase[d] + (i - ltile[d]);
+    dst[pos] = k;
+    if (Hn) atomicAdd(&Hn[(uint64_t)(((k & ~kTagBit) >> nshift) & mask) * T + pos / (kSortThreads * ITEMS)], 1u);
   }
 }
 
@@ -402,202 +418,60 @@ __global__ void __launch_bounds__(1024) k_small_front(PrepArgs a, const uint64_t
   }
 }
 
-// ---- unique/cancel, leaf search and run heads in two kernels ---------------------------------
-// k_search_all: one sorted word per thread: the survivor test of reading R2 and,
-// for survivors, the leaf (reading R4); lfull[e] = kNoLeaf for dropped words.
-// k_compact: one single-pass compaction with two counts (survivors, runs): a run
-// starts at a survivor whose leaf differs from the previous survivor's.
-__global__ void __launch_bounds__(256) k_search_all(PrepArgs a, const uint64_t *__restrict__ sorted,
-                                                    uint32_t *__restrict__ lfull, const uint64_t *__restrict__ F,
-                                                    uint64_t nleaves, const Ctl *ctl, const ModelHead *mhead,
-                                                    const Piece *__restrict__ mpieces, const uint32_t *gate) {
-  if (gate && *gate == 0) return;
-  const uint32_t n = ctl->n;
-  ModelHead hd;
-  hd.valid = 0;
-  if (mhead) hd = *mhead;
-  const bool learned = hd.valid != 0;
-  for (uint32_t e = blockIdx.x * blockDim.x + threadIdx.x; e < n; e += gridDim.x * blockDim.x) {
-    const uint64_t w = sorted[e], k = w & ~kTagBit;
-    const bool kept = (w & kTagBit) ? (e == 0 || (sorted[e - 1] & ~kTagBit) != k)
-                                    : (e + 1 == n || (sorted[e + 1] & ~kTagBit) != k);
-    uint32_t leaf = kNoLeaf;
-    if (kept) {
-      const uint64_t key = expand(w, a);
-      leaf = learned ? learned_leaf_search(hd, mpieces, F, nleaves, key) : leaf_search(F, nleaves, key);
-    }
-    lfull[e] = leaf;
-  }
-}
-
-__global__ void __launch_bounds__(kScanThreads) k_compact(PrepArgs a, const uint64_t *__restrict__ sorted,
-                                                          const uint32_t *__restrict__ lfull,
-                                                          uint64_t *__restrict__ ukey, uint8_t *__restrict__ utag,
-                                                          uint32_t *__restrict__ uleaf, uint32_t *__restrict__ run_start,
-                                                          uint32_t *__restrict__ run_leaf, uint64_t *status, Ctl *ctl,
-                                                          const uint32_t *gate) {
-  __shared__ ScanSmem sm;
-  if (gate && *gate == 0) return;
-  const uint32_t tile = take_ticket(ctl, kSlotKeep, sm), n = ctl->n;
-  uint32_t keep[kScanItems], head[kScanItems], lf[kScanItems];
-#pragma unroll
-  for (int r = 0; r < kScanItems; r++) {
-    const uint64_t e = scan_elem(tile, r);
-    lf[r] = e < n ? lfull[e] : kNoLeaf;
-    keep[r] = lf[r] != kNoLeaf;
-    head[r] = 0;
-    if (keep[r]) {
-      int64_t j = (int64_t)e - 1;  // previous survivor (dropped words are rare)
-      while (j >= 0 && lfull[j] == kNoLeaf) --j;
-      head[r] = j < 0 || lfull[j] != lf[r];
-    }
-  }
-  uint32_t koff[kScanItems], hoff[kScanItems];
-  const uint32_t m = tile_scan(keep, koff, tile, status, 2, 0, ctl->epoch + kSlotKeep, ctl, sm);
-  const uint32_t nr = tile_scan(head, hoff, tile, status, 2, 1, ctl->epoch + kSlotKeep, ctl, sm);
-#pragma unroll
-  for (int r = 0; r < kScanItems; r++) {
-    if (!keep[r] || koff[r] >= n) continue;
-    const uint64_t w = sorted[scan_elem(tile, r)];
-    ukey[koff[r]] = expand(w, a);
-    utag[koff[r]] = (uint8_t)(w >> 63);
-    uleaf[koff[r]] = lf[r];
-    if (head[r]) {
-      run_start[hoff[r]] = koff[r];
-      run_leaf[hoff[r]] = lf[r];
-    }
-  }
-  if ((uint64_t)(tile + 1) * kScanTile >= n && threadIdx.x == 0) {
-    ctl->m = m;
-    ctl->nruns = nr;
-    run_start[nr] = m;
-  }
-}
-
-// ---- bucketed front end (batches above kSmallBatch keys) ---------------------------------------
-// Bucket offsets (exclusive scan of the counts, start[nbk] = n), the counts
-// turned into scatter cursors, the list of buckets above kBkSmall keys, and the
-// flag (and graph conditional) that sends the batch to the radix-sort path when
-// a bucket exceeds kBkCap.  One block of 1024 threads.
-__global__ void __launch_bounds__(1024) k_bk_scan(BucketWork bk, uint32_t nbk, Ctl *ctl,
-                                                  cudaGraphConditionalHandle fall, int set_fall) {
-  __shared__ uint32_t wsum[33];
-  __shared__ uint32_t s_big, s_fall, s_nbig;
-  const uint32_t t = threadIdx.x, per = (nbk + 1023) / 1024, b0 = t * per;
-  if (t == 0) {
-    s_fall = 0;
-    s_nbig = 0;
-  }
-  __syncthreads();
-  uint32_t loc = 0, mx = 0;
-  for (uint32_t q = 0; q < per; q++) {
-    const uint32_t b = b0 + q;
-    if (b >= nbk) break;
-    const uint32_t c = bk.cnt[b];
-    loc += c;
-    mx = c > mx ? c : mx;
-  }
-  uint32_t total;
-  uint32_t run = block_excl_scan(loc, wsum, &total);
-  if (mx > kBkCap) atomicOr(&s_fall, 1u);
-  for (uint32_t q = 0; q < per; q++) {
-    const uint32_t b = b0 + q;
-    if (b >= nbk) break;
-    const uint32_t c = bk.cnt[b];
-    bk.start[b] = run;
-    bk.cnt[b] = run;  // scatter cursor
-    if (c > kBkSmall && c <= kBkCap) bk.big[atomicAdd(&s_nbig, 1u)] = b;
-    run += c;
-  }
-  __syncthreads();
-  if (t == 0) {
-    bk.start[nbk] = total;
-    const uint32_t f = (ctl->err == 0 && s_fall) ? 1u : 0u;
-    ctl->bkfall = f;
-    ctl->nbigbk = s_nbig;
-    if (set_fall) cudaGraphSetConditional(fall, f);
-  }
-}
-
-__global__ void __launch_bounds__(256) k_bk_scatter(const uint64_t *__restrict__ src, uint64_t *__restrict__ dst,
-                                                    uint32_t *__restrict__ cursor, uint32_t shift, const Ctl *ctl) {
-  if (ctl->err || ctl->bkfall) return;
-  const uint32_t n = ctl->n;
-  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
-    const uint64_t w = src[i];
-    dst[atomicAdd(&cursor[(uint32_t)(w >> shift)], 1u)] = w;
-  }
-}
-
-struct BkSortArgs {
-  PrepArgs a;
-  uint64_t *words;   // bucketed sort words in; sorted radix-layout words out (same place)
-  uint32_t *lfull;   // leaf of every sorted word (kNoLeaf: dropped by reading R2)
-  BucketWork bk;
-  const uint64_t *F;
-  uint64_t nleaves;
-  const ModelHead *mhead;
-  const Piece *mpieces;
-  const Ctl *ctl;
+// ---- unique/cancel, leaf search, run heads and compaction (after the radix passes) ------------
+// Per-block survivor summaries of the sorted words, kSearchTile words a block.
+struct TileSums {
+  uint32_t *surv;    // survivors of reading R2 in the block
+  uint32_t *hin;     // run heads among them, not counting the block's first survivor
+  uint32_t *first;   // leaf of the block's first / last survivor (kNoLeaf: none)
+  uint32_t *last;
+  uint32_t *soff;    // survivors before the block
+  uint32_t *hoff;    // run heads before the block
+  uint32_t *hfirst;  // 1 if the block's first survivor starts a run
 };
 
-// Sort bucket b (at most CAP keys) in shared memory and summarise it: bitonic sort
-// of the sort words (padded to a power of two with all-ones words, which sort
-// last), the survivor test of reading R2 on neighbours (equal keys share a
-// bucket), the leaf of every survivor (reading R4), and the bucket's survivor
-// count, run heads after its first survivor, and first and last survivor leaves.
-template <uint32_t TPB>
-__device__ void bk_sort_one(const BkSortArgs &x, uint32_t b, uint64_t *sk, uint32_t *sl, const ModelHead &hd,
-                            bool learned) {
+// One sorted word per thread: the survivor test of reading R2 (an insert survives
+// unless the next word has its key, a delete unless the previous one has), the
+// leaf of every survivor (reading R4), and the block's summary.
+__global__ void __launch_bounds__(kSearchTile) k_rsearch(PrepArgs a, const uint64_t *__restrict__ sorted,
+                                                         uint32_t *__restrict__ lfull, const uint64_t *__restrict__ F,
+                                                         uint64_t nleaves, TileSums ts, const Ctl *ctl,
+                                                         const ModelHead *mhead, const Piece *__restrict__ mpieces) {
+  __shared__ uint32_t sl[kSearchTile];
   __shared__ uint32_t s_surv, s_hin, s_first, s_last;
-  const uint32_t t = threadIdx.x;
-  const uint32_t start = x.bk.start[b], nb = x.bk.start[b + 1] - start;
-  uint32_t P = 1;
-  while (P < nb) P <<= 1;
+  if (ctl->err) return;
+  const uint32_t n = ctl->n, t = threadIdx.x;
+  const uint32_t e = blockIdx.x * kSearchTile + t;
   if (t == 0) {
     s_surv = 0;
     s_hin = 0;
     s_first = 0xFFFFFFFFu;
     s_last = 0;
   }
-  for (uint32_t i = t; i < P; i += TPB) sk[i] = i < nb ? x.words[start + i] : ~0ull;
-  __syncthreads();
-  for (uint32_t k = 2; k <= P; k <<= 1) {
-    for (uint32_t j = k >> 1; j > 0; j >>= 1) {
-      for (uint32_t i = t; i < P / 2; i += TPB) {
-        const uint32_t lo = ((i & ~(j - 1)) << 1) | (i & (j - 1)), hi = lo + j;
-        const uint64_t u = sk[lo], v = sk[hi];
-        if ((u > v) == ((lo & k) == 0)) {
-          sk[lo] = v;
-          sk[hi] = u;
-        }
-      }
-      __syncthreads();
-    }
-  }
-  for (uint32_t i = t; i < nb; i += TPB) {
-    const uint64_t w = sk[i], k = w >> 1;
-    const bool kept = (w & 1) ? (i == 0 || (sk[i - 1] >> 1) != k) : (i + 1 == nb || (sk[i + 1] >> 1) != k);
-    const uint64_t rw = k | ((w & 1ull) << 63);  // radix layout: tag in bit 63
-    uint32_t leaf = kNoLeaf;
+  ModelHead hd;
+  hd.valid = 0;
+  if (mhead) hd = *mhead;
+  uint32_t leaf = kNoLeaf;
+  if (e < n) {
+    const uint64_t w = sorted[e], k = w & ~kTagBit;
+    const bool kept = (w & kTagBit) ? (e == 0 || (sorted[e - 1] & ~kTagBit) != k)
+                                    : (e + 1 == n || (sorted[e + 1] & ~kTagBit) != k);
     if (kept) {
-      const uint64_t key = expand(rw, x.a);
-      leaf = learned ? learned_leaf_search(hd, x.mpieces, x.F, x.nleaves, key) : leaf_search(x.F, x.nleaves, key);
+      const uint64_t key = expand(w, a);
+      leaf = hd.valid ? learned_leaf_search(hd, mpieces, F, nleaves, key) : leaf_search(F, nleaves, key);
     }
-    sl[i] = leaf;
-    x.words[start + i] = rw;
-    x.lfull[start + i] = leaf;
+    lfull[e] = leaf;
   }
+  sl[t] = leaf;
   __syncthreads();
-  uint32_t surv = 0, hin = 0;
-  for (uint32_t i = t; i < nb; i += TPB) {
-    if (sl[i] == kNoLeaf) continue;
-    ++surv;
-    int32_t j = (int32_t)i - 1;  // previous survivor (dropped words are rare)
+  uint32_t hin = 0, surv = 0;
+  if (leaf != kNoLeaf) {
+    surv = 1;
+    int32_t j = (int32_t)t - 1;  // previous survivor of the block (dropped words are rare)
     while (j >= 0 && sl[j] == kNoLeaf) --j;
-    if (j < 0) atomicMin(&s_first, i);
-    else if (sl[j] != sl[i]) ++hin;
-    atomicMax(&s_last, i);
+    if (j < 0) s_first = t;  // exactly one survivor has none before it
+    else hin = sl[j] != leaf;
+    atomicMax(&s_last, t);
   }
   surv = warp_sum(surv);
   hin = warp_sum(hin);
@@ -607,66 +481,36 @@ __device__ void bk_sort_one(const BkSortArgs &x, uint32_t b, uint64_t *sk, uint3
   }
   __syncthreads();
   if (t == 0) {
-    x.bk.surv[b] = s_surv;
-    x.bk.hin[b] = s_hin;
-    x.bk.first[b] = s_surv ? sl[s_first] : kNoLeaf;
-    x.bk.last[b] = s_surv ? sl[s_last] : kNoLeaf;
+    ts.surv[blockIdx.x] = s_surv;
+    ts.hin[blockIdx.x] = s_hin;
+    ts.first[blockIdx.x] = s_surv ? sl[s_first] : kNoLeaf;
+    ts.last[blockIdx.x] = s_surv ? sl[s_last] : kNoLeaf;
   }
-  __syncthreads();  // shared memory is reused by the block's next bucket
 }
 
-// one 256-thread block per bucket of at most kBkSmall keys
-__global__ void __launch_bounds__(256) k_bk_sort(BkSortArgs x, uint32_t nbk) {
-  __shared__ uint64_t sk[kBkSmall];
-  __shared__ uint32_t sl[kBkSmall];
-  const Ctl *ctl = x.ctl;
-  if (ctl->err || ctl->bkfall) return;
-  const uint32_t b = blockIdx.x;
-  if (b >= nbk) return;
-  const uint32_t nb = x.bk.start[b + 1] - x.bk.start[b];
-  if (nb > kBkSmall) return;  // k_bk_sort_big
-  ModelHead hd;
-  hd.valid = 0;
-  if (x.mhead) hd = *x.mhead;
-  bk_sort_one<256>(x, b, sk, sl, hd, hd.valid != 0);
-}
-
-// 1024-thread blocks for the buckets of (kBkSmall, kBkCap] keys, from the list
-__global__ void __launch_bounds__(1024) k_bk_sort_big(BkSortArgs x) {
-  extern __shared__ uint64_t bsm[];
-  uint64_t *sk = bsm;
-  uint32_t *sl = reinterpret_cast<uint32_t *>(bsm + kBkCap);
-  const Ctl *ctl = x.ctl;
-  if (ctl->err || ctl->bkfall) return;
-  ModelHead hd;
-  hd.valid = 0;
-  if (x.mhead) hd = *x.mhead;
-  const uint32_t nbig = ctl->nbigbk;
-  for (uint32_t i = blockIdx.x; i < nbig; i += gridDim.x) bk_sort_one<1024>(x, x.bk.big[i], sk, sl, hd, hd.valid != 0);
-}
-
-// Survivor and run-head offsets of every bucket: exclusive scans over the buckets;
-// the first survivor of a bucket starts a run unless the last survivor of the
-// nearest earlier bucket with survivors has the same leaf.  One block of 1024.
-__global__ void __launch_bounds__(1024) k_bk_offsets(BucketWork bk, uint32_t nbk, Ctl *ctl,
-                                                     uint32_t *__restrict__ run_start) {
+// Survivor and run-head offsets of every block of k_rsearch: exclusive scans over
+// the blocks; a block's first survivor starts a run unless the last survivor of
+// the nearest earlier block with survivors has the same leaf.  One block of 1024.
+__global__ void __launch_bounds__(1024) k_toffsets(TileSums ts, uint32_t nt, Ctl *ctl,
+                                                   uint32_t *__restrict__ run_start) {
   __shared__ uint32_t wsum[33];
-  __shared__ uint32_t s_last[1024];   // last survivor leaf of each thread's buckets
-  __shared__ int32_t s_idx[1024];     // thread index, -1 when its buckets hold no survivor
-  if (ctl->err || ctl->bkfall) return;
-  const uint32_t t = threadIdx.x, per = (nbk + 1023) / 1024, b0 = t * per;
+  __shared__ uint32_t s_last[1024];  // last survivor leaf of each thread's blocks
+  __shared__ int32_t s_idx[1024];    // nearest thread <= t whose blocks hold a survivor, -1 if none
+  __shared__ int32_t s_wmax[32];
+  if (ctl->err) return;
+  const uint32_t t = threadIdx.x, per = (nt + 1023) / 1024, b0 = t * per;
   uint32_t sv = 0, lastleaf = kNoLeaf;
   for (uint32_t q = 0; q < per; q++) {
     const uint32_t b = b0 + q;
-    if (b >= nbk) break;
-    if (bk.surv[b]) {
-      sv += bk.surv[b];
-      lastleaf = bk.last[b];
+    if (b >= nt) break;
+    const uint32_t c = ts.surv[b];
+    if (c) {
+      sv += c;
+      lastleaf = ts.last[b];
     }
   }
   s_last[t] = lastleaf;
-  // nearest earlier thread whose buckets hold survivors: an inclusive running
-  // maximum of (t if it has survivors, else -1), read at t - 1
+  // inclusive running maximum of (t if its blocks hold survivors, else -1)
   const uint32_t lane = lane_id(), wid = t >> 5;
   int32_t v = sv ? (int32_t)t : -1;
 #pragma unroll
@@ -674,7 +518,6 @@ __global__ void __launch_bounds__(1024) k_bk_offsets(BucketWork bk, uint32_t nbk
     const int32_t u = __shfl_up_sync(0xFFFFFFFFu, v, o);
     if (lane >= o) v = u > v ? u : v;
   }
-  __shared__ int32_t s_wmax[32];
   if (lane == 31) s_wmax[wid] = v;
   __syncthreads();
   if (wid == 0) {
@@ -695,24 +538,24 @@ __global__ void __launch_bounds__(1024) k_bk_offsets(BucketWork bk, uint32_t nbk
   uint32_t hc = 0;
   for (uint32_t q = 0; q < per; q++) {
     const uint32_t b = b0 + q;
-    if (b >= nbk) break;
-    if (!bk.surv[b]) continue;
-    const uint32_t hf = (prevleaf == kNoLeaf || prevleaf != bk.first[b]) ? 1u : 0u;
-    bk.hfirst[b] = hf;
-    hc += bk.hin[b] + hf;
-    prevleaf = bk.last[b];
+    if (b >= nt) break;
+    if (!ts.surv[b]) continue;
+    const uint32_t hf = (prevleaf == kNoLeaf || prevleaf != ts.first[b]) ? 1u : 0u;
+    ts.hfirst[b] = hf;
+    hc += ts.hin[b] + hf;
+    prevleaf = ts.last[b];
   }
   uint32_t m, nr;
   uint32_t so = block_excl_scan(sv, wsum, &m);
   uint32_t ho = block_excl_scan(hc, wsum, &nr);
   for (uint32_t q = 0; q < per; q++) {
     const uint32_t b = b0 + q;
-    if (b >= nbk) break;
-    bk.soff[b] = so;
-    bk.hoff[b] = ho;
-    if (bk.surv[b]) {
-      so += bk.surv[b];
-      ho += bk.hin[b] + bk.hfirst[b];
+    if (b >= nt) break;
+    ts.soff[b] = so;
+    ts.hoff[b] = ho;
+    if (ts.surv[b]) {
+      so += ts.surv[b];
+      ho += ts.hin[b] + ts.hfirst[b];
     }
   }
   if (t == 0) {
@@ -722,45 +565,40 @@ __global__ void __launch_bounds__(1024) k_bk_offsets(BucketWork bk, uint32_t nbk
   }
 }
 
-// survivors and run heads of every bucket to their places (one block per bucket,
-// 256 positions at a time)
-__global__ void __launch_bounds__(256) k_bk_write(PrepArgs a, const uint64_t *__restrict__ words,
-                                                  const uint32_t *__restrict__ lfull, BucketWork bk, uint32_t nbk,
-                                                  uint64_t *__restrict__ ukey, uint8_t *__restrict__ utag,
-                                                  uint32_t *__restrict__ uleaf, uint32_t *__restrict__ run_start,
-                                                  uint32_t *__restrict__ run_leaf, const Ctl *ctl) {
+// survivors and run heads of every block to their places, one word per thread
+__global__ void __launch_bounds__(kSearchTile) k_twrite(PrepArgs a, const uint64_t *__restrict__ sorted,
+                                                        const uint32_t *__restrict__ lfull, TileSums ts,
+                                                        uint64_t *__restrict__ ukey, uint8_t *__restrict__ utag,
+                                                        uint32_t *__restrict__ uleaf, uint32_t *__restrict__ run_start,
+                                                        uint32_t *__restrict__ run_leaf, const Ctl *ctl) {
   __shared__ uint32_t wsum[33];
-  if (ctl->err || ctl->bkfall) return;
-  const uint32_t b = blockIdx.x;
-  if (b >= nbk || bk.surv[b] == 0) return;
-  const uint32_t start = bk.start[b], nb = bk.start[b + 1] - start;
-  uint32_t so = bk.soff[b], ho = bk.hoff[b];
-  const uint32_t hf = bk.hfirst[b];
-  for (uint32_t base = 0; base < nb; base += 256) {
-    const uint32_t i = base + threadIdx.x;
-    const uint32_t lf = i < nb ? lfull[start + i] : kNoLeaf;
-    const uint32_t keep = lf != kNoLeaf;
-    uint32_t head = 0;
-    if (keep) {
-      int32_t j = (int32_t)i - 1;  // previous survivor of the bucket
-      while (j >= 0 && lfull[start + j] == kNoLeaf) --j;
-      head = j < 0 ? hf : (lfull[start + j] != lf);
+  __shared__ uint32_t sl[kSearchTile];
+  if (ctl->err) return;
+  const uint32_t b = blockIdx.x, t = threadIdx.x, n = ctl->n;
+  if (ts.surv[b] == 0) return;
+  const uint32_t e = b * kSearchTile + t;
+  const uint32_t lf = e < n ? lfull[e] : kNoLeaf;
+  sl[t] = lf;
+  __syncthreads();
+  const uint32_t keep = lf != kNoLeaf;
+  uint32_t head = 0;
+  if (keep) {
+    int32_t j = (int32_t)t - 1;  // previous survivor of the block
+    while (j >= 0 && sl[j] == kNoLeaf) --j;
+    head = j < 0 ? ts.hfirst[b] : (sl[j] != lf);
+  }
+  uint32_t nk, nh;
+  const uint32_t ko = ts.soff[b] + block_excl_scan(keep, wsum, &nk);
+  const uint32_t ho = ts.hoff[b] + block_excl_scan(head, wsum, &nh);
+  if (keep) {
+    const uint64_t w = sorted[e];
+    ukey[ko] = expand(w, a);
+    utag[ko] = (uint8_t)(w >> 63);
+    uleaf[ko] = lf;
+    if (head) {
+      run_start[ho] = ko;
+      run_leaf[ho] = lf;
     }
-    uint32_t nk, nh;
-    const uint32_t ko = so + block_excl_scan(keep, wsum, &nk);
-    const uint32_t hoi = ho + block_excl_scan(head, wsum, &nh);
-    if (keep) {
-      const uint64_t w = words[start + i];
-      ukey[ko] = expand(w, a);
-      utag[ko] = (uint8_t)(w >> 63);
-      uleaf[ko] = lf;
-      if (head) {
-        run_start[hoi] = ko;
-        run_leaf[hoi] = lf;
-      }
-    }
-    so += nk;
-    ho += nh;
   }
 }
 
@@ -772,7 +610,6 @@ static uint32_t grid_for(uint64_t n, uint32_t per_block, uint32_t cap) {
   return (uint32_t)g;
 }
 
-uint32_t sort_tiles(uint64_t n) { return (uint32_t)((n + kSortTile - 1) / kSortTile); }
 uint32_t comp_tiles(uint64_t n) { return (uint32_t)((n + kScanTile - 1) / kScanTile); }
 
 bool small_front(uint64_t n) { return n <= kSmallBatch; }
@@ -797,104 +634,55 @@ void launch_small_front(const FrontArgs &f, cudaStream_t s) {
                                                f.run_start, f.run_leaf, f.mhead, f.mpieces, P, S);
 }
 
-BkGeo bucket_geo(uint64_t n, uint32_t sbits) {
-  uint64_t P = 1;
-  while (P < n) P <<= 1;
-  uint32_t lp = 0;
-  while ((1ull << lp) < P) ++lp;
-  // about 128 to 256 keys per bucket, 32 to kBkMax buckets
-  int kb = (int)lp - 8;
-  if (kb < 5) kb = 5;
-  if (kb > 14) kb = 14;
-  const uint32_t sb = sbits + 1;  // sort word: compressed key << 1 | tag
-  if ((uint32_t)kb > sb) kb = (int)sb;
-  BkGeo g;
-  g.kb = (uint32_t)kb;
-  g.shift = sb - g.kb;
-  g.nbk = 1u << g.kb;
-  return g;
-}
+uint32_t front_tiles(uint64_t nb) { return (uint32_t)((nb + sort_tile_keys(nb) - 1) / sort_tile_keys(nb)); }
+uint32_t search_tiles(uint64_t nb) { return (uint32_t)((nb + kSearchTile - 1) / kSearchTile); }
 
-// shared-memory opt-in of the bucket kernels (the prep histogram holds up to kBkMax
-// counts, the large-bucket sort kBkCap keys and their leaves)
-static void bucket_attrs() {
-  static bool done = false;
-  if (done) return;
-  cudaFuncSetAttribute(k_prep, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(kBkMax * sizeof(uint32_t)));
-  cudaFuncSetAttribute(k_bk_sort_big, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       (int)(kBkCap * (sizeof(uint64_t) + sizeof(uint32_t))));
-  done = true;
-}
-
-void launch_prep(const FrontArgs &f, cudaStream_t s) {
-  bucket_attrs();
+void launch_prep(const FrontArgs &f, uint64_t nb, cudaStream_t s) {
   const PrepArgs &a = f.prep;
   const uint64_t n = (uint64_t)a.n_ins + a.n_del;
-  const BkGeo bg = bucket_geo(n, a.sbits);
+  const uint32_t T = front_tiles(nb);
   note_launch();
-  k_init_batch<<<1, 256, 0, s>>>(f.ctl, f.hist, a.npass * 256u, f.bk.cnt, bg.nbk, (uint32_t)n);
+  k_init_batch<<<1, 256, 0, s>>>(f.ctl, f.hist, a.npass * 256u, (uint32_t)n);
   note_launch();
-  k_prep<<<grid_for(n, 256, 4 * 152), 256, bg.nbk * sizeof(uint32_t), s>>>(a, f.ins, f.del, f.bufA, f.bk.cnt,
-                                                                          bg.shift, bg.nbk, f.ctl);
+  if (nb >= kSortLargeFrom)
+    k_prep<kSortItemsLarge><<<T, kSortThreads, 0, s>>>(a, f.ins, f.del, f.bufA, f.hist, f.rs, T, f.ctl);
+  else
+    k_prep<kSortItemsSmall><<<T, kSortThreads, 0, s>>>(a, f.ins, f.del, f.bufA, f.hist, f.rs, T, f.ctl);
 }
 
-void launch_front_buckets(const FrontArgs &f, uint64_t nb, cudaStream_t s, const cudaGraphConditionalHandle *fall) {
+void launch_front(const FrontArgs &f, uint64_t nb, cudaStream_t s) {
   const PrepArgs &a = f.prep;
-  const BkGeo bg = bucket_geo(nb, a.sbits);
-  bucket_attrs();
-  note_launch();
-  k_bk_scan<<<1, 1024, 0, s>>>(f.bk, bg.nbk, f.ctl, fall ? *fall : cudaGraphConditionalHandle(), fall ? 1 : 0);
-  note_launch();
-  k_bk_scatter<<<grid_for(nb, 256 * 8, 152 * 8), 256, 0, s>>>(f.bufA, f.bufB, f.bk.cnt, bg.shift, f.ctl);
-  BkSortArgs x;
-  x.a = a;
-  x.words = f.bufB;
-  x.lfull = f.lfull;
-  x.bk = f.bk;
-  x.F = f.geo->F;
-  x.nleaves = f.geo->nleaves;
-  x.mhead = f.mhead;
-  x.mpieces = f.mpieces;
-  x.ctl = f.ctl;
-  note_launch();
-  k_bk_sort<<<bg.nbk, 256, 0, s>>>(x, bg.nbk);
-  note_launch();
-  k_bk_sort_big<<<152, 1024, kBkCap * (sizeof(uint64_t) + sizeof(uint32_t)), s>>>(x);
-  note_launch();
-  k_bk_offsets<<<1, 1024, 0, s>>>(f.bk, bg.nbk, f.ctl, f.run_start);
-  note_launch();
-  k_bk_write<<<bg.nbk, 256, 0, s>>>(a, f.bufB, f.lfull, f.bk, bg.nbk, f.ukey, f.utag, f.uleaf, f.run_start,
-                                     f.run_leaf, f.ctl);
-}
-
-// grids sized for `nb` keys (>= the batch); the kernels read the batch size from ctl
-void launch_front_fallback(const FrontArgs &f, uint64_t nb, cudaStream_t s, bool gated) {
-  const PrepArgs &a = f.prep;
-  const uint32_t *gate = gated ? &f.ctl->bkfall : nullptr;
-  note_launch();
-  k_bk_convert<<<grid_for(nb, 256, 4 * 152), 256, 0, s>>>(a, f.bufA, f.hist, f.ctl, gate);
+  const uint32_t T = front_tiles(nb), radix = 1u << a.dbits;
+  uint32_t *H[2] = {f.rs, f.rs + (uint64_t)256 * T};
   uint64_t *src = f.bufA, *dst = f.bufB;
-  const bool large = nb >= kSortLargeFrom;
-  const uint32_t st = large ? (uint32_t)((nb + kSortThreads * kSortItemsLarge - 1) / (kSortThreads * kSortItemsLarge))
-                            : sort_tiles(nb);
   for (uint32_t p = 0; p < a.npass; p++) {
+    uint32_t *O = H[p & 1], *Hn = p + 1 < a.npass ? H[(p + 1) & 1] : nullptr;
     note_launch();
-    if (large)
-      k_sort_pass<kSortItemsLarge><<<st, kSortThreads, 0, s>>>(src, dst, f.hist, f.status, f.ctl, p, p * a.dbits,
-                                                               a.dbits, gate);
+    k_rcolscan<<<radix, 1024, 0, s>>>(O, Hn, T, f.hist + p * 256, f.ctl);
+    const uint32_t shift = p * a.dbits, nshift = (p + 1) * a.dbits;
+    note_launch();
+    if (nb >= kSortLargeFrom)
+      k_rscatter<kSortItemsLarge><<<T, kSortThreads, 0, s>>>(src, dst, O, Hn, T, shift, nshift, a.dbits, f.ctl);
     else
-      k_sort_pass<kSortItemsSmall><<<st, kSortThreads, 0, s>>>(src, dst, f.hist, f.status, f.ctl, p, p * a.dbits,
-                                                               a.dbits, gate);
+      k_rscatter<kSortItemsSmall><<<T, kSortThreads, 0, s>>>(src, dst, O, Hn, T, shift, nshift, a.dbits, f.ctl);
     uint64_t *t = src; src = dst; dst = t;
   }
-  // look-back epochs: pass p uses epoch + p, then the fixed slots of gpma_launch.h
-  const uint32_t ct = comp_tiles(nb);
+  const uint32_t T1 = search_tiles(nb);
+  uint32_t *q = f.rs + (uint64_t)512 * T;
+  const uint32_t K = T1 + 1;
+  TileSums ts{q, q + K, q + 2 * K, q + 3 * K, q + 4 * K, q + 5 * K, q + 6 * K};
   note_launch();
-  k_search_all<<<grid_for(nb, 256, 152 * 16), 256, 0, s>>>(a, src, f.lfull, f.geo->F, f.geo->nleaves, f.ctl, f.mhead,
-                                                           f.mpieces, gate);
+  k_rsearch<<<T1, kSearchTile, 0, s>>>(a, src, f.lfull, f.geo->F, f.geo->nleaves, ts, f.ctl, f.mhead, f.mpieces);
   note_launch();
-  k_compact<<<ct, kScanThreads, 0, s>>>(a, src, f.lfull, f.ukey, f.utag, f.uleaf, f.run_start, f.run_leaf, f.status,
-                                        f.ctl, gate);
+  k_toffsets<<<1, 1024, 0, s>>>(ts, T1, f.ctl, f.run_start);
+  note_launch();
+  k_twrite<<<T1, kSearchTile, 0, s>>>(a, src, f.lfull, ts, f.ukey, f.utag, f.uleaf, f.run_start, f.run_leaf, f.ctl);
+}
+
+// enough for every batch of at most nb keys (the smaller tiles give the most tiles)
+uint64_t front_scratch_words(uint64_t nb) {
+  const uint64_t small = kSortThreads * kSortItemsSmall;
+  return (uint64_t)512 * ((nb + small - 1) / small) + 7ull * (search_tiles(nb) + 1);
 }
 
 }  // namespace gpk

@@ -1,11 +1,11 @@
 """The update front end at the sizes where it changes form, against the oracle.
 
-Batches of at most 4096 keys are sorted in one block.  Larger batches go to
-buckets by the top bits of their sort words, and every bucket is sorted in shared
-memory: by a 256-thread block up to 2048 keys, by a 1024-thread block up to 16384.
-A batch with a bucket above 16384 keys (a heavily skewed batch) takes the
-radix-sort path.  Each case checks the layout slot for slot, the batch statistics
-and the exported edges, with the learned and the plain leaf search."""
+Batches of at most 4096 keys are sorted in one block.  Larger batches are sorted
+by stable radix passes over tiles of 1024 keys (below 2^18 keys) or 4096 keys, and
+their survivors and run heads are placed from per-block counts of 1024 sorted
+words.  Each case checks the layout slot for slot, the batch statistics and the
+exported edges, with the learned and the plain leaf search; skewed batches (one
+source holding many of the batch's keys) and invalid keys in large batches too."""
 import numpy as np
 import pytest
 
@@ -76,7 +76,7 @@ def test_batch_sizes_around_the_front_end_limits(plain):
     rng = np.random.default_rng(61)
     batches = [(base, np.zeros(0, np.uint64))]
     live = base.copy()
-    for n in (4096, 4097, 5000, 8192, 8193, 65_537, 262_144):
+    for n in (4096, 4097, 5000, 8192, 8193, 65_537, 262_143, 262_144, 262_145):
         ins, dels = mixed_batch(rng, V, live, n)
         batches.append((ins, dels))
         live = np.array(sorted(set(live.tolist()) | set(ins.tolist()) - set(dels.tolist())), np.uint64)
@@ -85,9 +85,8 @@ def test_batch_sizes_around_the_front_end_limits(plain):
 
 @pytest.mark.parametrize("hot", [3000, 12_000, 20_000, 60_000])
 def test_skewed_batches(hot):
-    """A source with `hot` new edges in one batch of about hot + 10,000 keys: one
-    bucket above 2048 keys (1024-thread sort), up to 16,384 keys (the largest a
-    block sorts), and above it (the radix-sort path)."""
+    """A source with `hot` new edges in one batch of about hot + 10,000 keys: many
+    equal digits in the upper radix passes, and long runs of one source."""
     V = 1 << 17
     rng = np.random.default_rng(hot)
     base = W.rmat_stream(17, 400_000, seed=62)
