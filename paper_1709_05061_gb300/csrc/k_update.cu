@@ -111,10 +111,6 @@ __global__ void k_leaf_pass(Geo g, Ctl *ctl, Work w, uint32_t per_warp, int rest
       nins += __popc(bs);
       ndel += __popc(__ballot_sync(0xFFFFFFFFu, dl));
       if (act) w.eflag[e] = dl ? 1 : (sv ? 2 : 0);
-      if (!g.raw) {
-        degree_delta(g.deg, sv && !is_guard(key), key, 1);
-        degree_delta(g.deg, dl, key, -1);
-      }
     }
     __syncwarp();
     const uint32_t cnt_del = nv - ndel;
@@ -253,10 +249,6 @@ __global__ void k_long_a(Geo g, Ctl *ctl, Work w, uint32_t per_warp) {
       if (sv && slot < L) {  // record (a level-0 merge takes fewer than L; the run has more than L keys)
         w.pkey[rs + slot] = key;
         w.pleaf[rs + slot] = e;
-      }
-      if (!g.raw) {
-        degree_delta(g.deg, sv && !is_guard(key), key, 1);
-        degree_delta(g.deg, dl, key, -1);
       }
       __syncwarp();
     }
@@ -431,7 +423,6 @@ __global__ void __launch_bounds__(256) k_leaf64(Geo g, Ctl *ctl, Work w) {
     }
     const bool dl = act && tag && found;
     if (act) w.eflag[rs + lane] = dl ? 1 : (sv ? (fits ? 1 : 2) : 0);
-    if (!g.raw) run_degree_delta(g.deg, len, key, (sv && !is_guard(key)) ? 1 : (dl ? -1 : 0));
     if (lane == 0) {
       w.rdelta[r] = (int32_t)nins - (int32_t)ndel;
       w.rinfo[r] = fits ? 1 : ((nins || g.dual) ? 2 : 0);
@@ -867,6 +858,31 @@ void allow_big_smem() {
   done = true;
 }
 
+// Out-degree change of the batch, one key per thread after the level-0 passes
+// (every surviving insert ends up stored, pending ones by the merges of this
+// batch; guards are not edges): lanes of one source (keys are sorted, so they
+// are adjacent) add once.
+__global__ void __launch_bounds__(256) k_deg_batch(Geo g, const Ctl *ctl, Work w) {
+  if (ctl->err) return;
+  const uint32_t m = ctl->m;
+  for (uint32_t b = blockIdx.x * blockDim.x; b < m; b += gridDim.x * blockDim.x) {
+    const uint32_t e = b + threadIdx.x;
+    int d = 0;
+    uint64_t key = 0;
+    if (e < m) {
+      key = w.ukey[e];
+      const uint8_t f = w.eflag[e];
+      if (w.utag[e]) d = f == 1 ? -1 : 0;
+      else d = (f != 0 && !is_guard(key)) ? 1 : 0;
+    }
+    const uint32_t src = d ? (uint32_t)(key >> 32) : 0xFFFFFFFFu;
+    const uint32_t peers = __match_any_sync(0xFFFFFFFFu, src);
+    const uint32_t pos = __ballot_sync(0xFFFFFFFFu, d > 0), neg = __ballot_sync(0xFFFFFFFFu, d < 0);
+    const int sum = __popc(peers & pos) - __popc(peers & neg);
+    if (d && lane_id() == (uint32_t)(__ffs(peers) - 1) && sum) atomicAdd(&g.deg[src], (uint32_t)sum);
+  }
+}
+
 void launch_leaf_pass(const Geo &g, Ctl *ctl, const Work &w, uint32_t n, cudaStream_t s) {
   allow_big_smem();
   const uint32_t pw = leaf_smem_bytes(g.L), wpb = warps_per_block(g.L);
@@ -882,6 +898,10 @@ void launch_leaf_pass(const Geo &g, Ctl *ctl, const Work &w, uint32_t n, cudaStr
     k_long_a<<<blocks_for((n + 31) / 32, wpb, 152 * 16), wpb * 32, wpb * pw, s>>>(g, ctl, w, pw);
     note_launch();
     k_long_b<<<blocks_for(n / kLongRun + 1, wpb, 152 * 16), wpb * 32, wpb * pw, s>>>(g, ctl, w, pw);
+  }
+  if (!g.raw) {
+    note_launch();
+    k_deg_batch<<<blocks_for(n, 256, 152 * 8), 256, 0, s>>>(g, ctl, w);
   }
 }
 
