@@ -486,6 +486,10 @@ int maybe_shrink(gpma *h, uint64_t total, cudaStream_t s, bool *shrunk) {
   return rebuild_at(h, h2, s);
 }
 
+__global__ void k_gate_rest(const Ctl *ctl, cudaGraphConditionalHandle cond) {
+  cudaGraphSetConditional(cond, (ctl->err == 0 && ctl->nlong > 0) ? 1u : 0u);
+}
+
 __global__ void k_gate(const Ctl *ctl, cudaGraphConditionalHandle cond) {
   cudaGraphSetConditional(cond, (ctl->err == 0 && ctl->nesc > 0) ? 1u : 0u);
 }
@@ -542,8 +546,11 @@ bool capture_update(gpma *h, FrontArgs &f, uint32_t nb, bool stats, bool grow, G
   if (!gc.cap2 && cudaStreamCreateWithFlags(&gc.cap2, cudaStreamNonBlocking) != cudaSuccess) return false;
   cudaGraph_t graph = nullptr;
   if (cudaGraphCreate(&graph, 0) != cudaSuccess) return false;
-  cudaGraphConditionalHandle cond, cgrow, cmerge;
+  cudaGraphConditionalHandle cond, cgrow, cmerge, crest;
   bool ok = cudaGraphConditionalHandleCreate(&cond, graph, 0, cudaGraphCondAssignDefault) == cudaSuccess;
+  // (every handle of a graph must belong to one of its conditional nodes)
+  const bool fast = h->geo.L == 64;
+  if (fast) ok = ok && cudaGraphConditionalHandleCreate(&crest, graph, 0, cudaGraphCondAssignDefault) == cudaSuccess;
   if (grow) {
     ok = ok && cudaGraphConditionalHandleCreate(&cgrow, graph, 0, cudaGraphCondAssignDefault) == cudaSuccess &&
          cudaGraphConditionalHandleCreate(&cmerge, graph, 0, cudaGraphCondAssignDefault) == cudaSuccess;
@@ -564,7 +571,18 @@ bool capture_update(gpma *h, FrontArgs &f, uint32_t nb, bool stats, bool grow, G
     if (h->mhead) launch_train_model(g, h->mhead, h->mpieces, h->ctl, true, t);
   };
   if (!small_front(nb)) launch_front(f, nb, gc.cap);
-  launch_leaf_pass(g, h->ctl, h->w, nb, gc.cap);
+  if (fast) {
+    // runs longer than 32 keys (bulk loads, hot rows) go to the general pass, which
+    // a sliding window almost never needs
+    launch_leaf64(g, h->ctl, h->w, nb, gc.cap);
+    note_launch();
+    k_gate_rest<<<1, 1, 0, gc.cap>>>(h->ctl, crest);
+    ok = ok && capture_if(gc.cap, gc.cap2, crest,
+                          [&](cudaStream_t t) { launch_leaf_rest(g, h->ctl, h->w, nb, true, t); });
+  } else {
+    launch_leaf_rest(g, h->ctl, h->w, nb, false, gc.cap);
+  }
+  launch_degrees_batch(g, h->ctl, h->w, nb, gc.cap);
   note_launch();
   k_gate<<<1, 1, 0, gc.cap>>>(h->ctl, cond);
   ok = ok && capture_if(gc.cap, gc.cap2, cond, [&](cudaStream_t t) {
@@ -978,7 +996,7 @@ int gpma_create(uint32_t n_vertices, const gpma_params *params, const gpma_alloc
     h->has_alloc = true;
   }
   make_geo(h, 0, &h->geo);
-  bool ok = alloc_arrays(h, &h->geo, s) && dalloc(h, &h->ctl, 1, s) && dalloc(h, &h->hist, 8 * 256, s) &&
+  bool ok = alloc_arrays(h, &h->geo, s) && dalloc(h, &h->ctl, 1, s) && dalloc(h, &h->hist, 16 * 256, s) &&
             dalloc(h, &h->check_buf, 4, s);
   if (ok && !(p.flags & GPMA_PLAIN_SEARCH)) {
     ok = dalloc(h, &h->mhead, 1, s) && dalloc(h, &h->mpieces, kPieces, s);

@@ -87,7 +87,13 @@ void launch_front(const FrontArgs &f, uint64_t nb, cudaStream_t s);
 uint64_t front_scratch_words(uint64_t nb);  // size of FrontArgs::rs for batches of up to nb keys
 
 // k_update.cu
+// level 0: k_leaf64 (L = 64, runs of at most 32 keys), then the general pass (the
+// other runs; with rest_only the fast path handled the short ones) and the chunked
+// path for runs above kLongRun keys, then the batch's out-degree changes
 void launch_leaf_pass(const Geo &g, Ctl *ctl, const Work &w, uint32_t n, cudaStream_t s);
+void launch_leaf64(const Geo &g, Ctl *ctl, const Work &w, uint32_t n, cudaStream_t s);
+void launch_leaf_rest(const Geo &g, Ctl *ctl, const Work &w, uint32_t n, bool rest_only, cudaStream_t s);
+void launch_degrees_batch(const Geo &g, Ctl *ctl, const Work &w, uint32_t n, cudaStream_t s);
 // levels 1..h of the count tree from the leaf counts and this batch's pending
 // inserts (run after launch_pending; does nothing when no insert is pending)
 void launch_tree_rebuild(const Geo &g, Ctl *ctl, const Work &w, uint32_t n, cudaStream_t s);

@@ -24,15 +24,13 @@
 namespace gpk {
 
 constexpr int kSortThreads = 256;
-// keys per thread of a sort tile: 4 below kSortLargeFrom keys (more tiles than
-// SMs), 16 from there on (fewer, fuller tiles)
-constexpr int kSortItemsSmall = 4, kSortItemsLarge = 16;
-constexpr uint64_t kSortLargeFrom = 1ull << 18;
+// keys per thread of a sort tile (1024-key tiles: many small blocks resident at once)
+constexpr int kSortItems = 4;
+constexpr uint32_t kSortTile = kSortThreads * kSortItems;
 constexpr uint32_t kSearchTile = 1024;  // sorted words per block of the search and the compaction
-
-static __host__ __device__ __forceinline__ uint32_t sort_tile_keys(uint64_t n) {
-  return kSortThreads * (n >= kSortLargeFrom ? kSortItemsLarge : kSortItemsSmall);
-}
+constexpr uint32_t kSearchPer = 4;      // of them per thread (their leaf searches run in lock step)
+constexpr uint32_t kSearchThreads = kSearchTile / kSearchPer;
+constexpr uint32_t kPrepDone = 7;       // Ctl::ticket slot counting finished prep blocks
 
 // ---- key compression -----------------------------------------------------------------
 // Graph mode: word = (src << db) | d with d = dst, or d = V for a guard (so a
@@ -118,29 +116,40 @@ __global__ void __launch_bounds__(kSortThreads) k_prep(PrepArgs a, const uint64_
   for (uint32_t d = threadIdx.x; d <= mask; d += blockDim.x) H0[(uint64_t)d * T + blockIdx.x] = sh[d];
   for (uint32_t i = threadIdx.x; i < a.npass * 256u; i += blockDim.x)
     if (sh[i]) atomicAdd(&hist[i], sh[i]);
+  // the last block to finish turns the batch's digit counts of every pass into
+  // digit offsets: hist[8 * 256 + p * 256 + d] = keys of pass p with a smaller digit
+  __shared__ uint32_t s_last;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) s_last = atomicAdd(&ctl->ticket[kPrepDone], 1u) == gridDim.x - 1;
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  const uint32_t w = threadIdx.x >> 5, lane = lane_id();
+  for (uint32_t p = w; p < a.npass; p += blockDim.x >> 5) {  // one warp per pass
+    uint32_t carry = 0;
+    for (uint32_t c = 0; c < 256; c += 32) {
+      const uint32_t v = __ldcg(&hist[p * 256 + c + lane]);
+      const uint32_t inc = warp_incl_scan(v);
+      hist[8 * 256 + p * 256 + c + lane] = carry + inc - v;
+      carry += __shfl_sync(0xFFFFFFFFu, inc, 31);
+    }
+  }
 }
 
 // Pass `pass`, digit blockIdx.x: H[d * T + t] (keys of tile t with digit d)
 // becomes the position of the tile's first such key: the digit's global offset
 // (keys of smaller digits, from the batch histogram) plus the same digit's keys
 // in earlier tiles.  Also zeroes the next pass's counts Hn (may be nullptr).
-__global__ void __launch_bounds__(1024) k_rcolscan(uint32_t *__restrict__ H, uint32_t *__restrict__ Hn, uint32_t T,
-                                                   const uint32_t *__restrict__ hist, const Ctl *ctl) {
+__global__ void __launch_bounds__(256) k_rcolscan(uint32_t *__restrict__ H, uint32_t *__restrict__ Hn, uint32_t T,
+                                                  const uint32_t *__restrict__ dbase, const Ctl *ctl) {
   __shared__ uint32_t wsum[33];
-  __shared__ uint32_t s_base;
   if (ctl->err) return;
   const uint32_t d = blockIdx.x;
-  if (threadIdx.x < 32) {  // sum of the counts of the smaller digits
-    uint32_t v = 0;
-    for (uint32_t e = threadIdx.x; e < d; e += 32) v += hist[e];
-    v = warp_sum(v);
-    if (threadIdx.x == 0) s_base = v;
-  }
-  __syncthreads();
-  uint32_t carry = s_base;
+  uint32_t carry = dbase[d];
   uint32_t *col = H + (uint64_t)d * T;
   constexpr uint32_t kPer = 8;
-  for (uint32_t c = 0; c < T; c += 1024 * kPer) {
+  for (uint32_t c = 0; c < T; c += 256 * kPer) {
     const uint32_t t0 = c + threadIdx.x * kPer;
     uint32_t v[kPer], loc = 0;
 #pragma unroll
@@ -158,7 +167,7 @@ __global__ void __launch_bounds__(1024) k_rcolscan(uint32_t *__restrict__ H, uin
     carry += total;
   }
   if (Hn)
-    for (uint32_t t = threadIdx.x; t < T; t += 1024) Hn[(uint64_t)d * T + t] = 0;
+    for (uint32_t t = threadIdx.x; t < T; t += 256) Hn[(uint64_t)d * T + t] = 0;
 }
 
 // One stable LSD pass over tile blockIdx.x (ITEMS rounds x 256 keys; warp w owns
@@ -430,18 +439,59 @@ struct TileSums {
   uint32_t *hfirst;  // 1 if the block's first survivor starts a run
 };
 
-// One sorted word per thread: the survivor test of reading R2 (an insert survives
-// unless the next word has its key, a delete unless the previous one has), the
-// leaf of every survivor (reading R4), and the block's summary.
-__global__ void __launch_bounds__(kSearchTile) k_rsearch(PrepArgs a, const uint64_t *__restrict__ sorted,
-                                                         uint32_t *__restrict__ lfull, const uint64_t *__restrict__ F,
-                                                         uint64_t nleaves, TileSums ts, const Ctl *ctl,
-                                                         const ModelHead *mhead, const Piece *__restrict__ mpieces) {
+// Leaf search of Q keys at once (reading R4): the Q binary searches of
+// search_first_above advance in lock step, so their loads are in flight
+// together; an empty leaf is skipped forward as there.  inactive keys get 0.
+template <int Q>
+__device__ __forceinline__ void leaf_search_lockstep(const uint64_t *__restrict__ F, uint64_t nleaves,
+                                                     const uint64_t (&k)[Q], const bool (&act)[Q],
+                                                     uint32_t (&out)[Q]) {
+  uint64_t lo[Q], hi[Q];
+#pragma unroll
+  for (int q = 0; q < Q; q++) {
+    lo[q] = 0;
+    hi[q] = act[q] ? nleaves : 0;
+  }
+  for (;;) {
+    uint64_t mid[Q], f[Q];
+    bool any = false;
+#pragma unroll
+    for (int q = 0; q < Q; q++) {
+      mid[q] = (lo[q] + hi[q]) >> 1;
+      f[q] = kEmpty;
+      if (lo[q] < hi[q]) {
+        f[q] = __ldg(F + mid[q]);
+        any = true;
+      }
+    }
+    if (!any) break;
+#pragma unroll
+    for (int q = 0; q < Q; q++) {
+      if (lo[q] >= hi[q]) continue;
+      uint64_t j = mid[q], fv = f[q];
+      while (fv == kEmpty && ++j < hi[q]) fv = __ldg(F + j);
+      if (j >= hi[q] || fv > k[q]) hi[q] = mid[q];
+      else lo[q] = j + 1;
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < Q; q++) out[q] = lo[q] ? (uint32_t)(lo[q] - 1) : 0u;
+}
+
+// kSearchPer consecutive sorted words per thread: the survivor test of reading R2
+// (an insert survives unless the next word has its key, a delete unless the
+// previous one has), the leaf of every survivor (reading R4), and the block's
+// summary.
+__global__ void __launch_bounds__(kSearchThreads) k_rsearch(PrepArgs a, const uint64_t *__restrict__ sorted,
+                                                            uint32_t *__restrict__ lfull,
+                                                            const uint64_t *__restrict__ F, uint64_t nleaves,
+                                                            TileSums ts, const Ctl *ctl, const ModelHead *mhead,
+                                                            const Piece *__restrict__ mpieces) {
   __shared__ uint32_t sl[kSearchTile];
   __shared__ uint32_t s_surv, s_hin, s_first, s_last;
   if (ctl->err) return;
   const uint32_t n = ctl->n, t = threadIdx.x;
-  const uint32_t e = blockIdx.x * kSearchTile + t;
+  const uint32_t e0 = blockIdx.x * kSearchTile + t * kSearchPer;
   if (t == 0) {
     s_surv = 0;
     s_hin = 0;
@@ -451,27 +501,49 @@ __global__ void __launch_bounds__(kSearchTile) k_rsearch(PrepArgs a, const uint6
   ModelHead hd;
   hd.valid = 0;
   if (mhead) hd = *mhead;
-  uint32_t leaf = kNoLeaf;
-  if (e < n) {
-    const uint64_t w = sorted[e], k = w & ~kTagBit;
-    const bool kept = (w & kTagBit) ? (e == 0 || (sorted[e - 1] & ~kTagBit) != k)
-                                    : (e + 1 == n || (sorted[e + 1] & ~kTagBit) != k);
-    if (kept) {
-      const uint64_t key = expand(w, a);
-      leaf = hd.valid ? learned_leaf_search(hd, mpieces, F, nleaves, key) : leaf_search(F, nleaves, key);
-    }
-    lfull[e] = leaf;
+  uint64_t w[kSearchPer + 2];  // words e0 - 1 .. e0 + kSearchPer
+#pragma unroll
+  for (int q = 0; q < (int)kSearchPer + 2; q++) {
+    const int64_t e = (int64_t)e0 - 1 + q;
+    w[q] = (e >= 0 && e < (int64_t)n) ? sorted[e] : kEmpty;
   }
-  sl[t] = leaf;
+  uint64_t key[kSearchPer];
+  bool kept[kSearchPer];
+  uint32_t leaf[kSearchPer];
+#pragma unroll
+  for (int q = 0; q < (int)kSearchPer; q++) {
+    const uint32_t e = e0 + q;
+    const uint64_t wq = w[q + 1], kq = wq & ~kTagBit;
+    kept[q] = e < n && ((wq & kTagBit) ? (e == 0 || (w[q] & ~kTagBit) != kq) : (e + 1 == n || (w[q + 2] & ~kTagBit) != kq));
+    key[q] = kept[q] ? expand(wq, a) : 0ull;
+  }
+  if (hd.valid) {
+#pragma unroll
+    for (int q = 0; q < (int)kSearchPer; q++)
+      leaf[q] = kept[q] ? learned_leaf_search(hd, mpieces, F, nleaves, key[q]) : kNoLeaf;
+  } else {
+    leaf_search_lockstep<kSearchPer>(F, nleaves, key, kept, leaf);
+#pragma unroll
+    for (int q = 0; q < (int)kSearchPer; q++)
+      if (!kept[q]) leaf[q] = kNoLeaf;
+  }
+#pragma unroll
+  for (int q = 0; q < (int)kSearchPer; q++) {
+    if (e0 + q < n) lfull[e0 + q] = leaf[q];
+    sl[t * kSearchPer + q] = leaf[q];
+  }
   __syncthreads();
   uint32_t hin = 0, surv = 0;
-  if (leaf != kNoLeaf) {
-    surv = 1;
-    int32_t j = (int32_t)t - 1;  // previous survivor of the block (dropped words are rare)
+#pragma unroll
+  for (int q = 0; q < (int)kSearchPer; q++) {
+    if (leaf[q] == kNoLeaf) continue;
+    const uint32_t i = t * kSearchPer + q;
+    ++surv;
+    int32_t j = (int32_t)i - 1;  // previous survivor of the block (dropped words are rare)
     while (j >= 0 && sl[j] == kNoLeaf) --j;
-    if (j < 0) s_first = t;  // exactly one survivor has none before it
-    else hin = sl[j] != leaf;
-    atomicMax(&s_last, t);
+    if (j < 0) s_first = i;  // exactly one survivor has none before it
+    else hin += sl[j] != leaf[q];
+    atomicMax(&s_last, i);
   }
   surv = warp_sum(surv);
   hin = warp_sum(hin);
@@ -565,40 +637,48 @@ __global__ void __launch_bounds__(1024) k_toffsets(TileSums ts, uint32_t nt, Ctl
   }
 }
 
-// survivors and run heads of every block to their places, one word per thread
-__global__ void __launch_bounds__(kSearchTile) k_twrite(PrepArgs a, const uint64_t *__restrict__ sorted,
-                                                        const uint32_t *__restrict__ lfull, TileSums ts,
-                                                        uint64_t *__restrict__ ukey, uint8_t *__restrict__ utag,
-                                                        uint32_t *__restrict__ uleaf, uint32_t *__restrict__ run_start,
-                                                        uint32_t *__restrict__ run_leaf, const Ctl *ctl) {
+// survivors and run heads of every block to their places, kSearchPer words per thread
+__global__ void __launch_bounds__(kSearchThreads) k_twrite(PrepArgs a, const uint64_t *__restrict__ sorted,
+                                                           const uint32_t *__restrict__ lfull, TileSums ts,
+                                                           uint64_t *__restrict__ ukey, uint8_t *__restrict__ utag,
+                                                           uint32_t *__restrict__ uleaf,
+                                                           uint32_t *__restrict__ run_start,
+                                                           uint32_t *__restrict__ run_leaf, const Ctl *ctl) {
   __shared__ uint32_t wsum[33];
   __shared__ uint32_t sl[kSearchTile];
   if (ctl->err) return;
   const uint32_t b = blockIdx.x, t = threadIdx.x, n = ctl->n;
   if (ts.surv[b] == 0) return;
-  const uint32_t e = b * kSearchTile + t;
-  const uint32_t lf = e < n ? lfull[e] : kNoLeaf;
-  sl[t] = lf;
+  const uint32_t base = b * kSearchTile;
+  for (uint32_t i = t; i < kSearchTile; i += kSearchThreads) sl[i] = base + i < n ? lfull[base + i] : kNoLeaf;
   __syncthreads();
-  const uint32_t keep = lf != kNoLeaf;
-  uint32_t head = 0;
-  if (keep) {
-    int32_t j = (int32_t)t - 1;  // previous survivor of the block
+  uint32_t keep = 0, head = 0;
+#pragma unroll
+  for (int q = 0; q < (int)kSearchPer; q++) {
+    const uint32_t i = t * kSearchPer + q, lf = sl[i];
+    if (lf == kNoLeaf) continue;
+    keep |= 1u << q;
+    int32_t j = (int32_t)i - 1;  // previous survivor of the block
     while (j >= 0 && sl[j] == kNoLeaf) --j;
-    head = j < 0 ? ts.hfirst[b] : (sl[j] != lf);
+    if (j < 0 ? ts.hfirst[b] != 0 : sl[j] != lf) head |= 1u << q;
   }
   uint32_t nk, nh;
-  const uint32_t ko = ts.soff[b] + block_excl_scan(keep, wsum, &nk);
-  const uint32_t ho = ts.hoff[b] + block_excl_scan(head, wsum, &nh);
-  if (keep) {
-    const uint64_t w = sorted[e];
+  uint32_t ko = ts.soff[b] + block_excl_scan(__popc(keep), wsum, &nk);
+  uint32_t ho = ts.hoff[b] + block_excl_scan(__popc(head), wsum, &nh);
+#pragma unroll
+  for (int q = 0; q < (int)kSearchPer; q++) {
+    if (!((keep >> q) & 1u)) continue;
+    const uint32_t i = t * kSearchPer + q;
+    const uint64_t w = sorted[base + i];
     ukey[ko] = expand(w, a);
     utag[ko] = (uint8_t)(w >> 63);
-    uleaf[ko] = lf;
-    if (head) {
+    uleaf[ko] = sl[i];
+    if ((head >> q) & 1u) {
       run_start[ho] = ko;
-      run_leaf[ho] = lf;
+      run_leaf[ho] = sl[i];
+      ++ho;
     }
+    ++ko;
   }
 }
 
@@ -634,7 +714,7 @@ void launch_small_front(const FrontArgs &f, cudaStream_t s) {
                                                f.run_start, f.run_leaf, f.mhead, f.mpieces, P, S);
 }
 
-uint32_t front_tiles(uint64_t nb) { return (uint32_t)((nb + sort_tile_keys(nb) - 1) / sort_tile_keys(nb)); }
+uint32_t front_tiles(uint64_t nb) { return (uint32_t)((nb + kSortTile - 1) / kSortTile); }
 uint32_t search_tiles(uint64_t nb) { return (uint32_t)((nb + kSearchTile - 1) / kSearchTile); }
 
 void launch_prep(const FrontArgs &f, uint64_t nb, cudaStream_t s) {
@@ -644,10 +724,7 @@ void launch_prep(const FrontArgs &f, uint64_t nb, cudaStream_t s) {
   note_launch();
   k_init_batch<<<1, 256, 0, s>>>(f.ctl, f.hist, a.npass * 256u, (uint32_t)n);
   note_launch();
-  if (nb >= kSortLargeFrom)
-    k_prep<kSortItemsLarge><<<T, kSortThreads, 0, s>>>(a, f.ins, f.del, f.bufA, f.hist, f.rs, T, f.ctl);
-  else
-    k_prep<kSortItemsSmall><<<T, kSortThreads, 0, s>>>(a, f.ins, f.del, f.bufA, f.hist, f.rs, T, f.ctl);
+  k_prep<kSortItems><<<T, kSortThreads, 0, s>>>(a, f.ins, f.del, f.bufA, f.hist, f.rs, T, f.ctl);
 }
 
 void launch_front(const FrontArgs &f, uint64_t nb, cudaStream_t s) {
@@ -658,13 +735,10 @@ void launch_front(const FrontArgs &f, uint64_t nb, cudaStream_t s) {
   for (uint32_t p = 0; p < a.npass; p++) {
     uint32_t *O = H[p & 1], *Hn = p + 1 < a.npass ? H[(p + 1) & 1] : nullptr;
     note_launch();
-    k_rcolscan<<<radix, 1024, 0, s>>>(O, Hn, T, f.hist + p * 256, f.ctl);
+    k_rcolscan<<<radix, 256, 0, s>>>(O, Hn, T, f.hist + 8 * 256 + p * 256, f.ctl);
     const uint32_t shift = p * a.dbits, nshift = (p + 1) * a.dbits;
     note_launch();
-    if (nb >= kSortLargeFrom)
-      k_rscatter<kSortItemsLarge><<<T, kSortThreads, 0, s>>>(src, dst, O, Hn, T, shift, nshift, a.dbits, f.ctl);
-    else
-      k_rscatter<kSortItemsSmall><<<T, kSortThreads, 0, s>>>(src, dst, O, Hn, T, shift, nshift, a.dbits, f.ctl);
+    k_rscatter<kSortItems><<<T, kSortThreads, 0, s>>>(src, dst, O, Hn, T, shift, nshift, a.dbits, f.ctl);
     uint64_t *t = src; src = dst; dst = t;
   }
   const uint32_t T1 = search_tiles(nb);
@@ -672,17 +746,15 @@ void launch_front(const FrontArgs &f, uint64_t nb, cudaStream_t s) {
   const uint32_t K = T1 + 1;
   TileSums ts{q, q + K, q + 2 * K, q + 3 * K, q + 4 * K, q + 5 * K, q + 6 * K};
   note_launch();
-  k_rsearch<<<T1, kSearchTile, 0, s>>>(a, src, f.lfull, f.geo->F, f.geo->nleaves, ts, f.ctl, f.mhead, f.mpieces);
+  k_rsearch<<<T1, kSearchThreads, 0, s>>>(a, src, f.lfull, f.geo->F, f.geo->nleaves, ts, f.ctl, f.mhead, f.mpieces);
   note_launch();
   k_toffsets<<<1, 1024, 0, s>>>(ts, T1, f.ctl, f.run_start);
   note_launch();
-  k_twrite<<<T1, kSearchTile, 0, s>>>(a, src, f.lfull, ts, f.ukey, f.utag, f.uleaf, f.run_start, f.run_leaf, f.ctl);
+  k_twrite<<<T1, kSearchThreads, 0, s>>>(a, src, f.lfull, ts, f.ukey, f.utag, f.uleaf, f.run_start, f.run_leaf,
+                                          f.ctl);
 }
 
-// enough for every batch of at most nb keys (the smaller tiles give the most tiles)
-uint64_t front_scratch_words(uint64_t nb) {
-  const uint64_t small = kSortThreads * kSortItemsSmall;
-  return (uint64_t)512 * ((nb + small - 1) / small) + 7ull * (search_tiles(nb) + 1);
-}
+// enough for every batch of at most nb keys
+uint64_t front_scratch_words(uint64_t nb) { return (uint64_t)512 * front_tiles(nb) + 7ull * (search_tiles(nb) + 1); }
 
 }  // namespace gpk

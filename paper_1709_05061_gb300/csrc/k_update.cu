@@ -883,26 +883,35 @@ __global__ void __launch_bounds__(256) k_deg_batch(Geo g, const Ctl *ctl, Work w
   }
 }
 
-void launch_leaf_pass(const Geo &g, Ctl *ctl, const Work &w, uint32_t n, cudaStream_t s) {
+void launch_leaf64(const Geo &g, Ctl *ctl, const Work &w, uint32_t n, cudaStream_t s) {
+  note_launch();
+  k_leaf64<<<blocks_for(n, 8, 152 * 8), 256, 0, s>>>(g, ctl, w);
+}
+
+void launch_leaf_rest(const Geo &g, Ctl *ctl, const Work &w, uint32_t n, bool rest_only, cudaStream_t s) {
   allow_big_smem();
   const uint32_t pw = leaf_smem_bytes(g.L), wpb = warps_per_block(g.L);
-  const int fast = g.L == 64;
-  if (fast) {
-    note_launch();
-    k_leaf64<<<blocks_for(n, 8, 152 * 8), 256, 0, s>>>(g, ctl, w);
-  }
   note_launch();
-  k_leaf_pass<<<blocks_for(n, wpb, 152 * 16), wpb * 32, wpb * pw, s>>>(g, ctl, w, pw, fast);
+  k_leaf_pass<<<blocks_for(n, wpb, 152 * 16), wpb * 32, wpb * pw, s>>>(g, ctl, w, pw, rest_only ? 1 : 0);
   if (n > kLongRun) {  // only a batch this large can hold a run this long
     note_launch();
     k_long_a<<<blocks_for((n + 31) / 32, wpb, 152 * 16), wpb * 32, wpb * pw, s>>>(g, ctl, w, pw);
     note_launch();
     k_long_b<<<blocks_for(n / kLongRun + 1, wpb, 152 * 16), wpb * 32, wpb * pw, s>>>(g, ctl, w, pw);
   }
-  if (!g.raw) {
-    note_launch();
-    k_deg_batch<<<blocks_for(n, 256, 152 * 8), 256, 0, s>>>(g, ctl, w);
-  }
+}
+
+void launch_degrees_batch(const Geo &g, Ctl *ctl, const Work &w, uint32_t n, cudaStream_t s) {
+  if (g.raw) return;
+  note_launch();
+  k_deg_batch<<<blocks_for(n, 256, 152 * 8), 256, 0, s>>>(g, ctl, w);
+}
+
+void launch_leaf_pass(const Geo &g, Ctl *ctl, const Work &w, uint32_t n, cudaStream_t s) {
+  const bool fast = g.L == 64;
+  if (fast) launch_leaf64(g, ctl, w, n, s);
+  launch_leaf_rest(g, ctl, w, n, fast, s);
+  launch_degrees_batch(g, ctl, w, n, s);
 }
 
 void launch_tree_rebuild(const Geo &g, Ctl *ctl, const Work &w, uint32_t n, cudaStream_t s) {
