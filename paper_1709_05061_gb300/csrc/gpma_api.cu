@@ -486,10 +486,6 @@ int maybe_shrink(gpma *h, uint64_t total, cudaStream_t s, bool *shrunk) {
   return rebuild_at(h, h2, s);
 }
 
-__global__ void k_gate_rest(const Ctl *ctl, cudaGraphConditionalHandle cond) {
-  cudaGraphSetConditional(cond, (ctl->err == 0 && ctl->nlong > 0) ? 1u : 0u);
-}
-
 __global__ void k_gate(const Ctl *ctl, cudaGraphConditionalHandle cond) {
   cudaGraphSetConditional(cond, (ctl->err == 0 && ctl->nesc > 0) ? 1u : 0u);
 }
@@ -546,11 +542,8 @@ bool capture_update(gpma *h, FrontArgs &f, uint32_t nb, bool stats, bool grow, G
   if (!gc.cap2 && cudaStreamCreateWithFlags(&gc.cap2, cudaStreamNonBlocking) != cudaSuccess) return false;
   cudaGraph_t graph = nullptr;
   if (cudaGraphCreate(&graph, 0) != cudaSuccess) return false;
-  cudaGraphConditionalHandle cond, cgrow, cmerge, crest;
+  cudaGraphConditionalHandle cond, cgrow, cmerge;
   bool ok = cudaGraphConditionalHandleCreate(&cond, graph, 0, cudaGraphCondAssignDefault) == cudaSuccess;
-  // (every handle of a graph must belong to one of its conditional nodes)
-  const bool fast = h->geo.L == 64;
-  if (fast) ok = ok && cudaGraphConditionalHandleCreate(&crest, graph, 0, cudaGraphCondAssignDefault) == cudaSuccess;
   if (grow) {
     ok = ok && cudaGraphConditionalHandleCreate(&cgrow, graph, 0, cudaGraphCondAssignDefault) == cudaSuccess &&
          cudaGraphConditionalHandleCreate(&cmerge, graph, 0, cudaGraphCondAssignDefault) == cudaSuccess;
@@ -571,18 +564,9 @@ bool capture_update(gpma *h, FrontArgs &f, uint32_t nb, bool stats, bool grow, G
     if (h->mhead) launch_train_model(g, h->mhead, h->mpieces, h->ctl, true, t);
   };
   if (!small_front(nb)) launch_front(f, nb, gc.cap);
-  if (fast) {
-    // runs longer than 32 keys (bulk loads, hot rows) go to the general pass, which
-    // a sliding window almost never needs
-    launch_leaf64(g, h->ctl, h->w, nb, gc.cap);
-    note_launch();
-    k_gate_rest<<<1, 1, 0, gc.cap>>>(h->ctl, crest);
-    ok = ok && capture_if(gc.cap, gc.cap2, crest,
-                          [&](cudaStream_t t) { launch_leaf_rest(g, h->ctl, h->w, nb, true, t); });
-  } else {
-    launch_leaf_rest(g, h->ctl, h->w, nb, false, gc.cap);
-  }
-  launch_degrees_batch(g, h->ctl, h->w, nb, gc.cap);
+  // (an IF node around the general pass, which a sliding window rarely needs,
+  // measured slower than its three kernels returning at once)
+  launch_leaf_pass(g, h->ctl, h->w, nb, gc.cap);
   note_launch();
   k_gate<<<1, 1, 0, gc.cap>>>(h->ctl, cond);
   ok = ok && capture_if(gc.cap, gc.cap2, cond, [&](cudaStream_t t) {
