@@ -983,7 +983,7 @@ int gpma_create(uint32_t n_vertices, const gpma_params *params, const gpma_alloc
   bool ok = alloc_arrays(h, &h->geo, s) && dalloc(h, &h->ctl, 1, s) && dalloc(h, &h->hist, 16 * 256, s) &&
             dalloc(h, &h->check_buf, 4, s);
   if (ok && !(p.flags & GPMA_PLAIN_SEARCH)) {
-    ok = dalloc(h, &h->mhead, 1, s) && dalloc(h, &h->mpieces, kPieces, s);
+    ok = dalloc(h, &h->mhead, 1, s) && dalloc(h, &h->mpieces, kModelPieces, s);
     if (ok) ok = cudaMemsetAsync(h->mhead, 0, sizeof(ModelHead), s) == cudaSuccess;
   }
   if (ok && !raw) ok = dalloc(h, &h->geo.row_end, h->V, s) && dalloc(h, &h->geo.deg, h->V, s);

@@ -224,13 +224,34 @@ struct ModelHead {
   uint32_t valid;
   uint32_t train;    // this call retrains (decided by k_lm_decide)
   uint64_t drift;    // leaves rewritten by merges above level 0 since the model was trained
+  uint64_t rbase;    // radix table over the boundaries: prefix(k) = min((k - rbase) >> rshift,
+  uint32_t rshift;   // kRadix - 1) (0 for k < rbase)
+  uint32_t pad;
 };
+
+// Radix table of the root stage: rt[r] = first piece whose boundary has a prefix
+// >= r (rt[kRadix] = npieces), so the piece of key k (the last piece whose
+// boundary is <= k) is rt[r] - 1 or one of the pieces [rt[r], rt[r + 1]) for
+// r = prefix(k).  It lives right after the pieces.
+constexpr uint32_t kRadix = 4096;
+constexpr uint32_t kModelPieces = kPieces + (uint32_t)(((kRadix + 1) * 4 + 31) / 32);  // Piece slots allocated
+__device__ __forceinline__ const uint32_t *model_radix(const Piece *pieces) {
+  return reinterpret_cast<const uint32_t *>(pieces + kPieces);
+}
+__device__ __forceinline__ uint32_t model_prefix(const ModelHead &m, uint64_t k) {
+  if (k < m.rbase) return 0;
+  const uint64_t r = (k - m.rbase) >> m.rshift;
+  return r < kRadix - 1 ? (uint32_t)r : kRadix - 1;
+}
 
 constexpr uint32_t kNoLeaf = 0xFFFFFFFFu;
 
-// last piece whose boundary is <= k, or -1
+// last piece whose boundary is <= k, or -1 (the binary search runs over the
+// pieces of k's radix-table entry only)
 __device__ __forceinline__ int32_t model_route(const ModelHead &m, const Piece *__restrict__ pieces, uint64_t k) {
-  uint32_t a = 0, b = m.npieces;
+  const uint32_t *rt = model_radix(pieces);
+  const uint32_t r = model_prefix(m, k);
+  uint32_t a = __ldg(rt + r), b = __ldg(rt + r + 1);
   while (a < b) {
     const uint32_t mid = (a + b) >> 1;
     if (__ldg(&pieces[mid].kb) <= k) a = mid + 1;
@@ -287,6 +308,128 @@ __device__ __forceinline__ uint32_t learned_leaf_search(const ModelHead &m, cons
   }
   const uint64_t p = search_first_above(F, (uint64_t)a, (uint64_t)b, k);
   return p ? (uint32_t)(p - 1) : 0u;
+}
+
+// ---- Q leaf searches in lock step ----------------------------------------------------------------
+// search_first_above for Q keys at once, each inside its own [lo, hi): the Q
+// bisections advance together, so their loads are in flight together.  out = the
+// leaf (p - 1, or 0 for p = 0); keys with lo >= hi on entry get lo - 1 (or 0).
+template <int Q>
+__device__ __forceinline__ void bisect_lockstep(const uint64_t *__restrict__ F, uint64_t (&lo)[Q], uint64_t (&hi)[Q],
+                                                const uint64_t (&k)[Q], uint32_t (&out)[Q]) {
+  for (;;) {
+    uint64_t mid[Q], f[Q];
+    bool any = false;
+#pragma unroll
+    for (int q = 0; q < Q; q++) {
+      mid[q] = (lo[q] + hi[q]) >> 1;
+      f[q] = kEmpty;
+      if (lo[q] < hi[q]) {
+        f[q] = __ldg(F + mid[q]);
+        any = true;
+      }
+    }
+    if (!any) break;
+#pragma unroll
+    for (int q = 0; q < Q; q++) {
+      if (lo[q] >= hi[q]) continue;
+      uint64_t j = mid[q], fv = f[q];
+      while (fv == kEmpty && ++j < hi[q]) fv = __ldg(F + j);  // empty leaves skipped forward
+      if (j >= hi[q] || fv > k[q]) hi[q] = mid[q];
+      else lo[q] = j + 1;
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < Q; q++) out[q] = lo[q] ? (uint32_t)(lo[q] - 1) : 0u;
+}
+
+// leaf_search for Q keys (inactive keys get 0)
+template <int Q>
+__device__ __forceinline__ void leaf_search_lockstep(const uint64_t *__restrict__ F, uint64_t nleaves,
+                                                     const uint64_t (&k)[Q], const bool (&act)[Q],
+                                                     uint32_t (&out)[Q]) {
+  uint64_t lo[Q], hi[Q];
+#pragma unroll
+  for (int q = 0; q < Q; q++) {
+    lo[q] = 0;
+    hi[q] = act[q] ? nleaves : 0;
+  }
+  bisect_lockstep<Q>(F, lo, hi, k, out);
+}
+
+// learned_leaf_search for Q keys in lock step: the route (radix table, then the
+// pieces of the entry), the piece's prediction and its bracket check together;
+// keys whose window is bracketed finish with one lock-step bisection inside it,
+// the others (a stale model) take learned_leaf_search alone.  Same leaves.
+template <int Q>
+__device__ __forceinline__ void learned_search_lockstep(const ModelHead &m, const Piece *__restrict__ pieces,
+                                                        const uint64_t *__restrict__ F, uint64_t nleaves,
+                                                        const uint64_t (&k)[Q], const bool (&act)[Q],
+                                                        uint32_t (&out)[Q]) {
+  const uint32_t *rt = model_radix(pieces);
+  uint32_t a[Q], b[Q];
+#pragma unroll
+  for (int q = 0; q < Q; q++) {
+    const uint32_t r = model_prefix(m, k[q]);
+    a[q] = act[q] ? __ldg(rt + r) : 0u;
+    b[q] = act[q] ? __ldg(rt + r + 1) : 0u;
+  }
+  for (;;) {  // last piece whose boundary is <= k
+    uint32_t mid[Q];
+    uint64_t kb[Q];
+    bool any = false;
+#pragma unroll
+    for (int q = 0; q < Q; q++) {
+      mid[q] = (a[q] + b[q]) >> 1;
+      kb[q] = 0;
+      if (a[q] < b[q]) {
+        kb[q] = __ldg(&pieces[mid[q]].kb);
+        any = true;
+      }
+    }
+    if (!any) break;
+#pragma unroll
+    for (int q = 0; q < Q; q++) {
+      if (a[q] >= b[q]) continue;
+      if (kb[q] <= k[q]) a[q] = mid[q] + 1;
+      else b[q] = mid[q];
+    }
+  }
+  uint64_t lo[Q], hi[Q], fa[Q], fb[Q];
+  bool ok[Q];
+#pragma unroll
+  for (int q = 0; q < Q; q++) {
+    const int32_t pi = (int32_t)a[q] - 1;
+    const Piece pc = pieces[pi < 0 ? 0 : pi];
+    int64_t pred = pi < 0 ? 0 : (int64_t)pc.lo;
+    if (pi >= 0 && pc.first != kNoLeaf) {
+      const float d = (float)(k[q] > pc.kb ? k[q] - pc.kb : 0ull) * pc.slope;
+      pred = (int64_t)pc.first + (int64_t)d;
+      if (pred < (int64_t)pc.lo) pred = pc.lo;
+      if (pred > (int64_t)pc.hi) pred = pc.hi;
+    }
+    int64_t wa = pred - (int64_t)pc.err, wb = pred + (int64_t)pc.err + 2;
+    if (wa < 0) wa = 0;
+    if (wa > (int64_t)nleaves) wa = (int64_t)nleaves;
+    if (wb > (int64_t)nleaves) wb = (int64_t)nleaves;
+    if (wb < wa) wb = wa;
+    lo[q] = (uint64_t)wa;
+    hi[q] = (uint64_t)wb;
+    ok[q] = act[q] && wa > 0 && wb < (int64_t)nleaves;
+    fa[q] = ok[q] ? __ldg(F + (wa - 1)) : kEmpty;
+    fb[q] = ok[q] ? __ldg(F + wb) : kEmpty;
+  }
+#pragma unroll
+  for (int q = 0; q < Q; q++) {
+    ok[q] = ok[q] && fa[q] != kEmpty && fb[q] != kEmpty && fa[q] <= k[q] && fb[q] > k[q];
+    if (!ok[q]) lo[q] = hi[q] = 0;  // left to the single search below
+  }
+  bisect_lockstep<Q>(F, lo, hi, k, out);
+#pragma unroll
+  for (int q = 0; q < Q; q++) {
+    if (!act[q]) out[q] = 0;
+    else if (!ok[q]) out[q] = learned_leaf_search(m, pieces, F, nleaves, k[q]);
+  }
 }
 
 // ---- single-pass look-back (tiles take tickets in launch order) -------------------

@@ -439,45 +439,6 @@ struct TileSums {
   uint32_t *hfirst;  // 1 if the block's first survivor starts a run
 };
 
-// Leaf search of Q keys at once (reading R4): the Q binary searches of
-// search_first_above advance in lock step, so their loads are in flight
-// together; an empty leaf is skipped forward as there.  inactive keys get 0.
-template <int Q>
-__device__ __forceinline__ void leaf_search_lockstep(const uint64_t *__restrict__ F, uint64_t nleaves,
-                                                     const uint64_t (&k)[Q], const bool (&act)[Q],
-                                                     uint32_t (&out)[Q]) {
-  uint64_t lo[Q], hi[Q];
-#pragma unroll
-  for (int q = 0; q < Q; q++) {
-    lo[q] = 0;
-    hi[q] = act[q] ? nleaves : 0;
-  }
-  for (;;) {
-    uint64_t mid[Q], f[Q];
-    bool any = false;
-#pragma unroll
-    for (int q = 0; q < Q; q++) {
-      mid[q] = (lo[q] + hi[q]) >> 1;
-      f[q] = kEmpty;
-      if (lo[q] < hi[q]) {
-        f[q] = __ldg(F + mid[q]);
-        any = true;
-      }
-    }
-    if (!any) break;
-#pragma unroll
-    for (int q = 0; q < Q; q++) {
-      if (lo[q] >= hi[q]) continue;
-      uint64_t j = mid[q], fv = f[q];
-      while (fv == kEmpty && ++j < hi[q]) fv = __ldg(F + j);
-      if (j >= hi[q] || fv > k[q]) hi[q] = mid[q];
-      else lo[q] = j + 1;
-    }
-  }
-#pragma unroll
-  for (int q = 0; q < Q; q++) out[q] = lo[q] ? (uint32_t)(lo[q] - 1) : 0u;
-}
-
 // kSearchPer consecutive sorted words per thread: the survivor test of reading R2
 // (an insert survives unless the next word has its key, a delete unless the
 // previous one has), the leaf of every survivor (reading R4), and the block's
@@ -517,16 +478,11 @@ __global__ void __launch_bounds__(kSearchThreads) k_rsearch(PrepArgs a, const ui
     kept[q] = e < n && ((wq & kTagBit) ? (e == 0 || (w[q] & ~kTagBit) != kq) : (e + 1 == n || (w[q + 2] & ~kTagBit) != kq));
     key[q] = kept[q] ? expand(wq, a) : 0ull;
   }
-  if (hd.valid) {
+  if (hd.valid) learned_search_lockstep<kSearchPer>(hd, mpieces, F, nleaves, key, kept, leaf);
+  else leaf_search_lockstep<kSearchPer>(F, nleaves, key, kept, leaf);
 #pragma unroll
-    for (int q = 0; q < (int)kSearchPer; q++)
-      leaf[q] = kept[q] ? learned_leaf_search(hd, mpieces, F, nleaves, key[q]) : kNoLeaf;
-  } else {
-    leaf_search_lockstep<kSearchPer>(F, nleaves, key, kept, leaf);
-#pragma unroll
-    for (int q = 0; q < (int)kSearchPer; q++)
-      if (!kept[q]) leaf[q] = kNoLeaf;
-  }
+  for (int q = 0; q < (int)kSearchPer; q++)
+    if (!kept[q]) leaf[q] = kNoLeaf;
 #pragma unroll
   for (int q = 0; q < (int)kSearchPer; q++) {
     if (e0 + q < n) lfull[e0 + q] = leaf[q];

@@ -9,7 +9,8 @@
 //                last non-empty leaf, boundary, slope, answer bracket and the
 //                largest prediction error over its leaves
 //   k_lm_valid   one block: empty pieces take the next boundary (so the
-//                boundaries never decrease), then the model is published
+//                boundaries never decrease), the radix table of the root stage
+//                over the boundaries, then the model is published
 #include "gpma_dev.cuh"
 #include "gpma_launch.h"
 
@@ -129,12 +130,52 @@ __global__ void __launch_bounds__(1024) k_lm_valid(ModelHead *head, Piece *piece
   uint64_t right = __shfl_down_sync(0xFFFFFFFFu, inc, 1);  // threads after this one in the warp
   if (lane == 31) right = kEmpty;
   if (w + 1 < 32 && wmin[w + 1] < right) right = wmin[w + 1];
+  uint64_t kmax = 0;  // largest boundary of a non-empty piece
   for (uint32_t q = 0; q < kPer; q++) {
     const uint32_t p = t * kPer + q;
     if (p >= np) break;
     const uint64_t fill = v[q] < right ? v[q] : right;
     if (pieces[p].first == kNoLeaf) pieces[p].kb = fill;
+    else kmax = pieces[p].kb > kmax ? pieces[p].kb : kmax;
   }
+  // radix table: prefix(k) = (k - rbase) >> rshift with the smallest shift that
+  // maps every boundary below kRadix; rt[r] = first piece with prefix >= r
+  __shared__ uint64_t s_max[32];
+  __shared__ uint64_t s_base;
+  __shared__ uint32_t s_shift;
+  for (int o = 16; o > 0; o >>= 1) {
+    const uint64_t u = __shfl_xor_sync(0xFFFFFFFFu, kmax, o);
+    kmax = u > kmax ? u : kmax;
+  }
+  if (lane == 0) s_max[w] = kmax;
+  __syncthreads();
+  if (t == 0) {
+    uint64_t mx = 0;
+    for (int i = 0; i < 32; i++) mx = s_max[i] > mx ? s_max[i] : mx;
+    const uint64_t base = pieces[0].kb;
+    const uint64_t range = (any && mx > base) ? mx - base : 0;
+    uint32_t sh = 0;
+    while ((range >> sh) >= kRadix) sh++;
+    s_base = base;
+    s_shift = sh;
+    head->rbase = base;
+    head->rshift = sh;
+  }
+  __syncthreads();
+  uint32_t *rt = reinterpret_cast<uint32_t *>(pieces + kPieces);
+  for (uint32_t r = t; r <= kRadix; r += blockDim.x) {
+    uint32_t lo = 0, hi = np;
+    if (r < kRadix) {
+      const uint64_t target = s_base + ((uint64_t)r << s_shift);
+      while (lo < hi) {
+        const uint32_t mid = (lo + hi) >> 1;
+        if (pieces[mid].kb < target) lo = mid + 1;
+        else hi = mid;
+      }
+    }
+    rt[r] = lo;
+  }
+  __syncthreads();
   if (t == 0) head->valid = any;
 }
 
