@@ -80,6 +80,7 @@ def parse():
                     help="load the window, run one call of this kind --repeat times and exit (a small, "
                          "self-contained run for ncu; GPMA_NO_GRAPHS=1 launches an update's kernels directly)")
     ap.add_argument("--repeat", type=int, default=1)
+    ap.add_argument("--plain-search", action="store_true", help="profile case: binary leaf search only")
     return ap.parse_args()
 
 
@@ -740,7 +741,7 @@ def profile_case(a):
 
     def dev(x):
         return torch.from_numpy(np.ascontiguousarray(x).view(np.int64)).cuda()
-    g = gp.Graph(1 << a.scale, leaf_size=LEAF, push_pagerank=a.push_pagerank)
+    g = gp.Graph(1 << a.scale, leaf_size=LEAF, push_pagerank=a.push_pagerank, plain_search=a.plain_search)
     g.update(dev(win.initial), None)
     ins, dels = win.slide(half)
     g.update(dev(ins), dev(dels))
