@@ -222,11 +222,11 @@ struct ModelHead {
   uint32_t npieces;  // pieces in use (min(kPieces, leaves))
   uint32_t span;     // log2 leaves per piece
   uint32_t valid;
-  uint32_t train;    // this call retrains (decided by k_lm_decide)
+  uint32_t pad0;
   uint64_t drift;    // leaves rewritten by merges above level 0 since the model was trained
   uint64_t rbase;    // radix table over the boundaries: prefix(k) = min((k - rbase) >> rshift,
   uint32_t rshift;   // kRadix - 1) (0 for k < rbase)
-  uint32_t pad;
+  uint32_t done;     // blocks of the training kernel finished so far (0 between launches)
 };
 
 // Radix table of the root stage: rt[r] = first piece whose boundary has a prefix

@@ -27,9 +27,11 @@ constexpr int kSortThreads = 256;
 // keys per thread of a sort tile (1024-key tiles: many small blocks resident at once)
 constexpr int kSortItems = 4;
 constexpr uint32_t kSortTile = kSortThreads * kSortItems;
-constexpr uint32_t kSearchTile = 1024;  // sorted words per block of the search and the compaction
-constexpr uint32_t kSearchPer = 4;      // of them per thread (their leaf searches run in lock step)
-constexpr uint32_t kSearchThreads = kSearchTile / kSearchPer;
+// search and compaction: 256 threads a block, Q sorted words a thread (their leaf
+// searches in lock step): Q = 4 from kSearchWideFrom keys on, else 1 (small
+// batches need every thread they can get to hide the search latency)
+constexpr uint32_t kSearchThreads = 256;
+constexpr uint64_t kSearchWideFrom = 1ull << 19;
 constexpr uint32_t kPrepDone = 7;       // Ctl::ticket slot counting finished prep blocks
 
 // ---- key compression -----------------------------------------------------------------
@@ -428,7 +430,7 @@ __global__ void __launch_bounds__(1024) k_small_front(PrepArgs a, const uint64_t
 }
 
 // ---- unique/cancel, leaf search, run heads and compaction (after the radix passes) ------------
-// Per-block survivor summaries of the sorted words, kSearchTile words a block.
+// Per-block survivor summaries of the sorted words (256 Q words a block).
 struct TileSums {
   uint32_t *surv;    // survivors of reading R2 in the block
   uint32_t *hin;     // run heads among them, not counting the block's first survivor
@@ -439,20 +441,21 @@ struct TileSums {
   uint32_t *hfirst;  // 1 if the block's first survivor starts a run
 };
 
-// kSearchPer consecutive sorted words per thread: the survivor test of reading R2
+// Q consecutive sorted words per thread: the survivor test of reading R2
 // (an insert survives unless the next word has its key, a delete unless the
 // previous one has), the leaf of every survivor (reading R4), and the block's
 // summary.
+template <int Q>
 __global__ void __launch_bounds__(kSearchThreads) k_rsearch(PrepArgs a, const uint64_t *__restrict__ sorted,
                                                             uint32_t *__restrict__ lfull,
                                                             const uint64_t *__restrict__ F, uint64_t nleaves,
                                                             TileSums ts, const Ctl *ctl, const ModelHead *mhead,
                                                             const Piece *__restrict__ mpieces) {
-  __shared__ uint32_t sl[kSearchTile];
+  __shared__ uint32_t sl[(kSearchThreads * Q)];
   __shared__ uint32_t s_surv, s_hin, s_first, s_last;
   if (ctl->err) return;
   const uint32_t n = ctl->n, t = threadIdx.x;
-  const uint32_t e0 = blockIdx.x * kSearchTile + t * kSearchPer;
+  const uint32_t e0 = blockIdx.x * (kSearchThreads * Q) + t * Q;
   if (t == 0) {
     s_surv = 0;
     s_hin = 0;
@@ -462,38 +465,38 @@ __global__ void __launch_bounds__(kSearchThreads) k_rsearch(PrepArgs a, const ui
   ModelHead hd;
   hd.valid = 0;
   if (mhead) hd = *mhead;
-  uint64_t w[kSearchPer + 2];  // words e0 - 1 .. e0 + kSearchPer
+  uint64_t w[Q + 2];  // words e0 - 1 .. e0 + Q
 #pragma unroll
-  for (int q = 0; q < (int)kSearchPer + 2; q++) {
+  for (int q = 0; q < Q + 2; q++) {
     const int64_t e = (int64_t)e0 - 1 + q;
     w[q] = (e >= 0 && e < (int64_t)n) ? sorted[e] : kEmpty;
   }
-  uint64_t key[kSearchPer];
-  bool kept[kSearchPer];
-  uint32_t leaf[kSearchPer];
+  uint64_t key[Q];
+  bool kept[Q];
+  uint32_t leaf[Q];
 #pragma unroll
-  for (int q = 0; q < (int)kSearchPer; q++) {
+  for (int q = 0; q < Q; q++) {
     const uint32_t e = e0 + q;
     const uint64_t wq = w[q + 1], kq = wq & ~kTagBit;
     kept[q] = e < n && ((wq & kTagBit) ? (e == 0 || (w[q] & ~kTagBit) != kq) : (e + 1 == n || (w[q + 2] & ~kTagBit) != kq));
     key[q] = kept[q] ? expand(wq, a) : 0ull;
   }
-  if (hd.valid) learned_search_lockstep<kSearchPer>(hd, mpieces, F, nleaves, key, kept, leaf);
-  else leaf_search_lockstep<kSearchPer>(F, nleaves, key, kept, leaf);
+  if (hd.valid) learned_search_lockstep<Q>(hd, mpieces, F, nleaves, key, kept, leaf);
+  else leaf_search_lockstep<Q>(F, nleaves, key, kept, leaf);
 #pragma unroll
-  for (int q = 0; q < (int)kSearchPer; q++)
+  for (int q = 0; q < Q; q++)
     if (!kept[q]) leaf[q] = kNoLeaf;
 #pragma unroll
-  for (int q = 0; q < (int)kSearchPer; q++) {
+  for (int q = 0; q < Q; q++) {
     if (e0 + q < n) lfull[e0 + q] = leaf[q];
-    sl[t * kSearchPer + q] = leaf[q];
+    sl[t * Q + q] = leaf[q];
   }
   __syncthreads();
   uint32_t hin = 0, surv = 0;
 #pragma unroll
-  for (int q = 0; q < (int)kSearchPer; q++) {
+  for (int q = 0; q < Q; q++) {
     if (leaf[q] == kNoLeaf) continue;
-    const uint32_t i = t * kSearchPer + q;
+    const uint32_t i = t * Q + q;
     ++surv;
     int32_t j = (int32_t)i - 1;  // previous survivor of the block (dropped words are rare)
     while (j >= 0 && sl[j] == kNoLeaf) --j;
@@ -593,7 +596,8 @@ __global__ void __launch_bounds__(1024) k_toffsets(TileSums ts, uint32_t nt, Ctl
   }
 }
 
-// survivors and run heads of every block to their places, kSearchPer words per thread
+// survivors and run heads of every block to their places, Q words per thread
+template <int Q>
 __global__ void __launch_bounds__(kSearchThreads) k_twrite(PrepArgs a, const uint64_t *__restrict__ sorted,
                                                            const uint32_t *__restrict__ lfull, TileSums ts,
                                                            uint64_t *__restrict__ ukey, uint8_t *__restrict__ utag,
@@ -601,17 +605,17 @@ __global__ void __launch_bounds__(kSearchThreads) k_twrite(PrepArgs a, const uin
                                                            uint32_t *__restrict__ run_start,
                                                            uint32_t *__restrict__ run_leaf, const Ctl *ctl) {
   __shared__ uint32_t wsum[33];
-  __shared__ uint32_t sl[kSearchTile];
+  __shared__ uint32_t sl[(kSearchThreads * Q)];
   if (ctl->err) return;
   const uint32_t b = blockIdx.x, t = threadIdx.x, n = ctl->n;
   if (ts.surv[b] == 0) return;
-  const uint32_t base = b * kSearchTile;
-  for (uint32_t i = t; i < kSearchTile; i += kSearchThreads) sl[i] = base + i < n ? lfull[base + i] : kNoLeaf;
+  const uint32_t base = b * (kSearchThreads * Q);
+  for (uint32_t i = t; i < (kSearchThreads * Q); i += kSearchThreads) sl[i] = base + i < n ? lfull[base + i] : kNoLeaf;
   __syncthreads();
   uint32_t keep = 0, head = 0;
 #pragma unroll
-  for (int q = 0; q < (int)kSearchPer; q++) {
-    const uint32_t i = t * kSearchPer + q, lf = sl[i];
+  for (int q = 0; q < Q; q++) {
+    const uint32_t i = t * Q + q, lf = sl[i];
     if (lf == kNoLeaf) continue;
     keep |= 1u << q;
     int32_t j = (int32_t)i - 1;  // previous survivor of the block
@@ -622,9 +626,9 @@ __global__ void __launch_bounds__(kSearchThreads) k_twrite(PrepArgs a, const uin
   uint32_t ko = ts.soff[b] + block_excl_scan(__popc(keep), wsum, &nk);
   uint32_t ho = ts.hoff[b] + block_excl_scan(__popc(head), wsum, &nh);
 #pragma unroll
-  for (int q = 0; q < (int)kSearchPer; q++) {
+  for (int q = 0; q < Q; q++) {
     if (!((keep >> q) & 1u)) continue;
-    const uint32_t i = t * kSearchPer + q;
+    const uint32_t i = t * Q + q;
     const uint64_t w = sorted[base + i];
     ukey[ko] = expand(w, a);
     utag[ko] = (uint8_t)(w >> 63);
@@ -671,7 +675,11 @@ void launch_small_front(const FrontArgs &f, cudaStream_t s) {
 }
 
 uint32_t front_tiles(uint64_t nb) { return (uint32_t)((nb + kSortTile - 1) / kSortTile); }
-uint32_t search_tiles(uint64_t nb) { return (uint32_t)((nb + kSearchTile - 1) / kSearchTile); }
+static uint32_t search_per(uint64_t nb) { return nb >= kSearchWideFrom ? 4u : 1u; }
+uint32_t search_tiles(uint64_t nb) {
+  const uint64_t tile = (uint64_t)kSearchThreads * search_per(nb);
+  return (uint32_t)((nb + tile - 1) / tile);
+}
 
 void launch_prep(const FrontArgs &f, uint64_t nb, cudaStream_t s) {
   const PrepArgs &a = f.prep;
@@ -701,16 +709,28 @@ void launch_front(const FrontArgs &f, uint64_t nb, cudaStream_t s) {
   uint32_t *q = f.rs + (uint64_t)512 * T;
   const uint32_t K = T1 + 1;
   TileSums ts{q, q + K, q + 2 * K, q + 3 * K, q + 4 * K, q + 5 * K, q + 6 * K};
+  const bool wide = search_per(nb) == 4;
   note_launch();
-  k_rsearch<<<T1, kSearchThreads, 0, s>>>(a, src, f.lfull, f.geo->F, f.geo->nleaves, ts, f.ctl, f.mhead, f.mpieces);
+  if (wide)
+    k_rsearch<4><<<T1, kSearchThreads, 0, s>>>(a, src, f.lfull, f.geo->F, f.geo->nleaves, ts, f.ctl, f.mhead,
+                                               f.mpieces);
+  else
+    k_rsearch<1><<<T1, kSearchThreads, 0, s>>>(a, src, f.lfull, f.geo->F, f.geo->nleaves, ts, f.ctl, f.mhead,
+                                               f.mpieces);
   note_launch();
   k_toffsets<<<1, 1024, 0, s>>>(ts, T1, f.ctl, f.run_start);
   note_launch();
-  k_twrite<<<T1, kSearchThreads, 0, s>>>(a, src, f.lfull, ts, f.ukey, f.utag, f.uleaf, f.run_start, f.run_leaf,
-                                          f.ctl);
+  if (wide)
+    k_twrite<4><<<T1, kSearchThreads, 0, s>>>(a, src, f.lfull, ts, f.ukey, f.utag, f.uleaf, f.run_start,
+                                              f.run_leaf, f.ctl);
+  else
+    k_twrite<1><<<T1, kSearchThreads, 0, s>>>(a, src, f.lfull, ts, f.ukey, f.utag, f.uleaf, f.run_start,
+                                              f.run_leaf, f.ctl);
 }
 
-// enough for every batch of at most nb keys
-uint64_t front_scratch_words(uint64_t nb) { return (uint64_t)512 * front_tiles(nb) + 7ull * (search_tiles(nb) + 1); }
+// enough for every batch of at most nb keys (one word a thread gives the most search blocks)
+uint64_t front_scratch_words(uint64_t nb) {
+  return (uint64_t)512 * front_tiles(nb) + 7ull * ((nb + kSearchThreads - 1) / kSearchThreads + 1);
+}
 
 }  // namespace gpk

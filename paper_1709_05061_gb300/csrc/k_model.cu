@@ -1,46 +1,27 @@
 // k_model.cu -- training of the learned leaf search (the model and the search
 // are in gpma_dev.cuh).  Everything runs on the device from the current pivots:
-//   k_lm_decide  retrain now?  Always after a resize or import and periodically;
+// one kernel, k_lm_train:
+//   decide       retrain now?  Always after a resize or import and periodically;
 //                after a batch only once merges above level 0 have rewritten a
 //                thirty-second of the leaves since the last training (a level-0
 //                merge moves keys only inside their leaf, and the search stays
-//                exact whatever the staleness, only slower)
-//   k_lm_fit     one warp per piece (2^span consecutive leaves): its first and
+//                exact whatever the staleness, only slower).  Every block takes
+//                the same decision from the same inputs.
+//   fit          one warp per piece (2^span consecutive leaves): its first and
 //                last non-empty leaf, boundary, slope, answer bracket and the
 //                largest prediction error over its leaves
-//   k_lm_valid   one block: empty pieces take the next boundary (so the
-//                boundaries never decrease), the radix table of the root stage
-//                over the boundaries, then the model is published
+//   publish      the last block to finish: empty pieces take the next boundary
+//                (so the boundaries never decrease), the radix table of the root
+//                stage over the boundaries, then the model is published (or,
+//                without training, the drift is carried over)
 #include "gpma_dev.cuh"
 #include "gpma_launch.h"
 
 namespace gpk {
 
-__global__ void k_lm_decide(Geo g, ModelHead *head, const Ctl *ctl, int after_batch) {
-  bool now = true;
-  if (after_batch) {
-    const uint64_t d = head->drift + (ctl->err == 0 ? ctl->nleafw : 0u);
-    now = head->valid == 0 || d * 32 >= g.nleaves;
-    head->drift = now ? 0 : d;
-  } else {
-    head->drift = 0;
-  }
-  uint32_t span = 0;
-  while ((g.nleaves >> span) > kPieces) span++;
-  head->train = now ? 1u : 0u;
-  if (now) {
-    head->valid = 0;
-    head->span = span;
-    head->npieces = (uint32_t)(g.nleaves >> span);
-  }
-}
-
-__global__ void __launch_bounds__(256) k_lm_fit(Geo g, const ModelHead *head, Piece *pieces) {
-  if (!head->train) return;
-  const uint32_t lane = lane_id(), span = head->span, np = head->npieces;
+__device__ __forceinline__ void lm_fit_piece(const Geo &g, uint32_t span, uint32_t p, Piece *pieces) {
+  const uint32_t lane = lane_id();
   const uint64_t S = 1ull << span;
-  const uint32_t p = blockIdx.x * 8 + (threadIdx.x >> 5);
-  if (p >= np) return;
   const uint64_t j0 = (uint64_t)p << span;
   // first and last non-empty leaf of the piece
   uint64_t first = kEmpty, last = kEmpty;
@@ -56,7 +37,7 @@ __global__ void __launch_bounds__(256) k_lm_fit(Geo g, const ModelHead *head, Pi
   Piece pc;
   pc.pad = 0;
   if (first == kEmpty) {
-    pc.kb = kEmpty;  // filled in by k_lm_valid
+    pc.kb = kEmpty;  // filled in when the model is published
     pc.first = kNoLeaf;
     pc.lo = pc.hi = (uint32_t)j0;
     pc.slope = 0.0f;
@@ -91,14 +72,21 @@ __global__ void __launch_bounds__(256) k_lm_fit(Geo g, const ModelHead *head, Pi
   if (lane == 0) pieces[p] = pc;
 }
 
-// suffix minimum of the boundaries (an empty piece takes the next boundary), then publish
-__global__ void __launch_bounds__(1024) k_lm_valid(ModelHead *head, Piece *pieces) {
-  __shared__ uint64_t wmin[32];
+constexpr uint32_t kLmThreads = 256;
+
+// Publish (one block of kLmThreads): suffix minimum of the boundaries (an empty
+// piece takes the next boundary), the radix table, the head fields, valid last.
+__device__ void lm_publish(ModelHead *head, Piece *pieces, uint32_t np, uint32_t span) {
+  __shared__ uint64_t wmin[kLmThreads / 32];
+  __shared__ uint64_t s_max[kLmThreads / 32];
   __shared__ uint32_t any;
-  if (!head->train) return;
-  const uint32_t np = head->npieces, t = threadIdx.x, lane = lane_id(), w = t >> 5;
-  constexpr uint32_t kPer = kPieces / 1024;
+  __shared__ uint64_t s_base;
+  __shared__ uint32_t s_shift;
+  const uint32_t t = threadIdx.x, lane = lane_id(), w = t >> 5;
+  constexpr uint32_t kW = kLmThreads / 32;
+  constexpr uint32_t kPer = kPieces / kLmThreads;
   if (t == 0) any = 0;
+  __syncthreads();
   // this thread's pieces [t*kPer, (t+1)*kPer), scanned from the right
   uint64_t v[kPer], run = kEmpty;
   bool mine = false;
@@ -116,20 +104,14 @@ __global__ void __launch_bounds__(1024) k_lm_valid(ModelHead *head, Piece *piece
     if (lane + o < 32 && u < inc) inc = u;
   }
   if (lane == 0) wmin[w] = inc;
-  __syncthreads();
-  if (w == 0) {
-    uint64_t x = wmin[lane];
-    for (int o = 1; o < 32; o <<= 1) {
-      const uint64_t u = __shfl_down_sync(0xFFFFFFFFu, x, o);
-      if (lane + o < 32 && u < x) x = u;
-    }
-    wmin[lane] = x;  // minimum over warps lane..31
-  }
   if (mine) atomicOr(&any, 1u);
+  __syncthreads();
+  if (t == 0)  // minimum over warps w..kW-1, in place
+    for (int i = (int)kW - 2; i >= 0; i--) wmin[i] = wmin[i + 1] < wmin[i] ? wmin[i + 1] : wmin[i];
   __syncthreads();
   uint64_t right = __shfl_down_sync(0xFFFFFFFFu, inc, 1);  // threads after this one in the warp
   if (lane == 31) right = kEmpty;
-  if (w + 1 < 32 && wmin[w + 1] < right) right = wmin[w + 1];
+  if (w + 1 < kW && wmin[w + 1] < right) right = wmin[w + 1];
   uint64_t kmax = 0;  // largest boundary of a non-empty piece
   for (uint32_t q = 0; q < kPer; q++) {
     const uint32_t p = t * kPer + q;
@@ -140,9 +122,6 @@ __global__ void __launch_bounds__(1024) k_lm_valid(ModelHead *head, Piece *piece
   }
   // radix table: prefix(k) = (k - rbase) >> rshift with the smallest shift that
   // maps every boundary below kRadix; rt[r] = first piece with prefix >= r
-  __shared__ uint64_t s_max[32];
-  __shared__ uint64_t s_base;
-  __shared__ uint32_t s_shift;
   for (int o = 16; o > 0; o >>= 1) {
     const uint64_t u = __shfl_xor_sync(0xFFFFFFFFu, kmax, o);
     kmax = u > kmax ? u : kmax;
@@ -151,19 +130,17 @@ __global__ void __launch_bounds__(1024) k_lm_valid(ModelHead *head, Piece *piece
   __syncthreads();
   if (t == 0) {
     uint64_t mx = 0;
-    for (int i = 0; i < 32; i++) mx = s_max[i] > mx ? s_max[i] : mx;
+    for (uint32_t i = 0; i < kW; i++) mx = s_max[i] > mx ? s_max[i] : mx;
     const uint64_t base = pieces[0].kb;
     const uint64_t range = (any && mx > base) ? mx - base : 0;
     uint32_t sh = 0;
     while ((range >> sh) >= kRadix) sh++;
     s_base = base;
     s_shift = sh;
-    head->rbase = base;
-    head->rshift = sh;
   }
   __syncthreads();
   uint32_t *rt = reinterpret_cast<uint32_t *>(pieces + kPieces);
-  for (uint32_t r = t; r <= kRadix; r += blockDim.x) {
+  for (uint32_t r = t; r <= kRadix; r += kLmThreads) {
     uint32_t lo = 0, hi = np;
     if (r < kRadix) {
       const uint64_t target = s_base + ((uint64_t)r << s_shift);
@@ -176,18 +153,55 @@ __global__ void __launch_bounds__(1024) k_lm_valid(ModelHead *head, Piece *piece
     rt[r] = lo;
   }
   __syncthreads();
-  if (t == 0) head->valid = any;
+  if (t == 0) {
+    head->span = span;
+    head->npieces = np;
+    head->rbase = s_base;
+    head->rshift = s_shift;
+    head->drift = 0;
+    __threadfence();
+    head->valid = any;
+  }
+}
+
+__global__ void __launch_bounds__(kLmThreads) k_lm_train(Geo g, ModelHead *head, Piece *pieces, const Ctl *ctl,
+                                                         int after_batch) {
+  __shared__ uint32_t s_last;
+  uint32_t span = 0;
+  while ((g.nleaves >> span) > kPieces) span++;
+  const uint32_t np = (uint32_t)(g.nleaves >> span);
+  uint64_t d = 0;
+  bool now = true;
+  if (after_batch) {
+    d = head->drift + (ctl->err == 0 ? ctl->nleafw : 0u);
+    now = head->valid == 0 || d * 32 >= g.nleaves;
+  }
+  if (now) {
+    const uint32_t p = blockIdx.x * (kLmThreads / 32) + (threadIdx.x >> 5);
+    if (p < np) lm_fit_piece(g, span, p, pieces);
+  }
+  // the last block to finish publishes (head->done counts finished blocks and is
+  // reset by that block, ready for the next launch)
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) s_last = atomicAdd(&head->done, 1u) == gridDim.x - 1;
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  if (threadIdx.x == 0) head->done = 0;
+  if (now) {
+    if (threadIdx.x == 0) head->valid = 0;
+    lm_publish(head, pieces, np, span);
+  } else if (threadIdx.x == 0) {
+    head->drift = d;
+  }
 }
 
 void launch_train_model(const Geo &g, ModelHead *head, Piece *pieces, const Ctl *ctl, bool after_batch,
                         cudaStream_t s) {
-  note_launch();
-  k_lm_decide<<<1, 1, 0, s>>>(g, head, ctl, after_batch ? 1 : 0);
   const uint64_t np = g.nleaves < kPieces ? g.nleaves : kPieces;
   note_launch();
-  k_lm_fit<<<(uint32_t)((np + 7) / 8), 256, 0, s>>>(g, head, pieces);
-  note_launch();
-  k_lm_valid<<<1, 1024, 0, s>>>(head, pieces);
+  k_lm_train<<<(uint32_t)((np + 7) / 8), kLmThreads, 0, s>>>(g, head, pieces, ctl, after_batch ? 1 : 0);
 }
 
 }  // namespace gpk

@@ -1,9 +1,9 @@
 """The update front end at the sizes where it changes form, against the oracle.
 
 Batches of at most 4096 keys are sorted in one block.  Larger batches are sorted
-by stable radix passes over tiles of 1024 keys (below 2^18 keys) or 4096 keys, and
-their survivors and run heads are placed from per-block counts of 1024 sorted
-words.  Each case checks the layout slot for slot, the batch statistics and the
+by stable radix passes over tiles of 1024 keys, and their survivors and run heads
+are placed from per-block counts of 256 sorted words (one a thread, below 2^19
+keys) or 1024 (four a thread).  Each case checks the layout slot for slot, the batch statistics and the
 exported edges, with the learned and the plain leaf search; skewed batches (one
 source holding many of the batch's keys) and invalid keys in large batches too."""
 import numpy as np
@@ -76,7 +76,7 @@ def test_batch_sizes_around_the_front_end_limits(plain):
     rng = np.random.default_rng(61)
     batches = [(base, np.zeros(0, np.uint64))]
     live = base.copy()
-    for n in (4096, 4097, 5000, 8192, 8193, 65_537, 262_143, 262_144, 262_145):
+    for n in (4096, 4097, 5000, 8192, 8193, 65_537, 262_145, 524_287, 524_288, 524_289):
         ins, dels = mixed_batch(rng, V, live, n)
         batches.append((ins, dels))
         live = np.array(sorted(set(live.tolist()) | set(ins.tolist()) - set(dels.tolist())), np.uint64)
