@@ -323,7 +323,8 @@ __global__ void k_long_b(Geo g, Ctl *ctl, Work w, uint32_t per_warp) {
 // Lane l holds slots 2l and 2l+1 of the leaf in registers (one 16-byte load),
 // lane i < len holds update i of the run; presence, deletes and ranks are warp
 // ballots.  The next run's leaf is loaded before the current one is processed.
-__global__ void __launch_bounds__(256) k_leaf64(Geo g, Ctl *ctl, Work w) {
+// 5 blocks of 256 threads an SM (48 registers): more runs in flight hide the leaf loads
+__global__ void __launch_bounds__(256, 5) k_leaf64(Geo g, Ctl *ctl, Work w) {
   __shared__ uint64_t sout[8][64];
   if (ctl->err) return;
   const uint32_t lane = lane_id(), wib = threadIdx.x >> 5;
@@ -354,6 +355,64 @@ __global__ void __launch_bounds__(256) k_leaf64(Geo g, Ctl *ctl, Work w) {
     const uint32_t len = re - rs;
     if (len > 32) {
       acc_long++;
+      continue;
+    }
+    if (len == 1 && !g.dual) {
+      // one update (most runs of a large batch over a large array): every lane
+      // reads it, no loop over the run; the same result as the general case below
+      const uint64_t ku = w.ukey[rs];
+      const bool del = w.utag[rs] != 0;
+      const bool m0 = k0 == ku, m1 = k1 == ku;
+      const bool found = __any_sync(0xFFFFFFFFu, m0 || m1);
+      const bool d0 = del && m0, d1 = del && m1;
+      const bool kp0 = k0 != kEmpty && !d0, kp1 = k1 != kEmpty && !d1;
+      const uint32_t kb0 = __ballot_sync(0xFFFFFFFFu, kp0), kb1 = __ballot_sync(0xFFFFFFFFu, kp1);
+      const uint32_t nkept = __popc(kb0) + __popc(kb1);
+      const uint32_t nins = (!del && !found) ? 1u : 0u, ndel = (del && found) ? 1u : 0u;
+      const bool fits = nins && nkept + 1 <= g.maxc[0];
+      if (fits) {
+        // TryInsert+ at level 0: the kept keys and the insert, left-packed
+        const uint32_t lt_mask = lanemask_lt();
+        const uint32_t before = __popc(kb0 & lt_mask) + __popc(kb1 & lt_mask);
+        const uint32_t pk = __popc(__ballot_sync(0xFFFFFFFFu, kp0 && k0 < ku)) +
+                            __popc(__ballot_sync(0xFFFFFFFFu, kp1 && k1 < ku));
+        if (kp0) sout[wib][before + (ku < k0)] = k0;
+        if (kp1) sout[wib][before + kp0 + (ku < k1)] = k1;
+        if (lane == 0) sout[wib][pk] = ku;
+        __syncwarp();
+        const uint32_t n = nkept + 1;
+        const uint32_t o = 2 * lane;
+        const uint64_t a = o < n ? sout[wib][o] : kEmpty, b = o + 1 < n ? sout[wib][o + 1] : kEmpty;
+        s2[(uint64_t)j * 32 + lane] = make_ulonglong2(a, b);
+        if (!g.raw) {
+          if (o < n && is_guard(a)) g.row_end[a >> 32] = j * 64u + o;
+          if (o + 1 < n && is_guard(b)) g.row_end[b >> 32] = j * 64u + o + 1;
+        }
+        if (lane == 0) {
+          g.F[j] = sout[wib][0];
+          g.cnt[j] = n;
+        }
+        __syncwarp();
+      } else if (ndel) {
+        if (d0 || d1) s2[(uint64_t)j * 32 + lane] = make_ulonglong2(d0 ? kEmpty : k0, d1 ? kEmpty : k1);
+        const uint32_t fb = kb0 | kb1;
+        const uint32_t fl = fb ? __ffs(fb) - 1 : 0;
+        const uint64_t fk = __shfl_sync(0xFFFFFFFFu, ((kb0 >> fl) & 1u) ? k0 : k1, fl);
+        if (lane == 0) {
+          g.F[j] = fb ? fk : kEmpty;
+          g.cnt[j] = nkept;
+        }
+      }
+      if (lane == 0) {
+        w.eflag[rs] = ndel ? 1 : (nins ? (fits ? 1 : 2) : 0);
+        w.rdelta[r] = (int32_t)nins - (int32_t)ndel;
+        w.rinfo[r] = fits ? 1 : (nins ? 2 : 0);
+        w.rdel[r] = ndel;
+      }
+      acc_ins += nins;
+      acc_del += ndel;
+      acc_m0 += fits;
+      acc_esc += !fits && nins;
       continue;
     }
     const bool act = lane < len;
@@ -885,7 +944,7 @@ __global__ void __launch_bounds__(256) k_deg_batch(Geo g, const Ctl *ctl, Work w
 
 void launch_leaf64(const Geo &g, Ctl *ctl, const Work &w, uint32_t n, cudaStream_t s) {
   note_launch();
-  k_leaf64<<<blocks_for(n, 8, 152 * 8), 256, 0, s>>>(g, ctl, w);
+  k_leaf64<<<blocks_for(n, 8, 152 * 5), 256, 0, s>>>(g, ctl, w);  // one wave of resident blocks
 }
 
 void launch_leaf_rest(const Geo &g, Ctl *ctl, const Work &w, uint32_t n, bool rest_only, cudaStream_t s) {
