@@ -81,6 +81,9 @@ def parse():
                          "self-contained run for ncu; GPMA_NO_GRAPHS=1 launches an update's kernels directly)")
     ap.add_argument("--repeat", type=int, default=1)
     ap.add_argument("--plain-search", action="store_true", help="profile case: binary leaf search only")
+    ap.add_argument("--graph", choices=["rmat", "chunglu"], default="rmat",
+                    help="profile case: R-MAT window, or the power-law graph of the learned-search study "
+                         "(1.6M vertices, 30M edges; batches of --batch keys, 70%% new edges, 30%% random live edges)")
     return ap.parse_args()
 
 
@@ -730,6 +733,8 @@ def profile_case(a):
     gp.build()
     torch.cuda.set_device(0)
     half = a.batch // 2
+    if a.graph == "chunglu":
+        return profile_case_chunglu(a)
     if a.scale >= 22:  # large graphs: drawn on the device (2^(scale+4) samples), window = all but the slides
         st = W.rmat_stream_device(a.scale, 1 << (a.scale + 4), seed=a.seed)
         stream = st.cpu().numpy().view(np.uint64)
@@ -760,6 +765,35 @@ def profile_case(a):
     g.status()
     torch.cuda.synchronize()
     out = {"profile_case": a.profile_case, "capacity": g.capacity, "check": g.check()}
+    g.close()
+    return out
+
+
+def profile_case_chunglu(a):
+    """The learned-search study's graph and batches, for ncu: load, one warm-up
+    batch, then --repeat batches."""
+    import torch
+    import paper_1709_05061_gb300 as gp
+    from paper_1709_05061_gb300 import workloads as W
+    gp.build()
+    torch.cuda.set_device(0)
+    V, E0 = 1_600_000, 30_000_000
+    n_ins = int(a.batch * 0.7)
+    n_del = a.batch - n_ins
+    stream = W.chung_lu_stream(V, E0 + (a.repeat + 1) * n_ins, gamma=2.1, seed=7)
+    rng = np.random.default_rng(7)
+
+    def dev(x):
+        return torch.from_numpy(np.ascontiguousarray(x).view(np.int64)).cuda()
+    g = gp.Graph(V, leaf_size=LEAF, plain_search=a.plain_search)
+    g.update(dev(stream[:E0]), None)
+    for i in range(a.repeat + 1):
+        ins = stream[E0 + i * n_ins: E0 + (i + 1) * n_ins]
+        dels = stream[rng.choice(E0, n_del, replace=False)]  # live: the first E0 edges are never deleted twice here
+        g.update(dev(ins), dev(dels))
+    g.status()
+    torch.cuda.synchronize()
+    out = {"profile_case": "update", "graph": "chunglu", "capacity": g.capacity, "check": g.check()}
     g.close()
     return out
 

@@ -113,15 +113,20 @@ __device__ void lm_publish(ModelHead *head, Piece *pieces, uint32_t np, uint32_t
   if (lane == 31) right = kEmpty;
   if (w + 1 < kW && wmin[w + 1] < right) right = wmin[w + 1];
   uint64_t kmax = 0;  // largest boundary of a non-empty piece
+  uint64_t kbf[kPer];  // the final boundaries of this thread's pieces
   for (uint32_t q = 0; q < kPer; q++) {
     const uint32_t p = t * kPer + q;
-    if (p >= np) break;
+    kbf[q] = kEmpty;
+    if (p >= np) continue;
     const uint64_t fill = v[q] < right ? v[q] : right;
     if (pieces[p].first == kNoLeaf) pieces[p].kb = fill;
     else kmax = pieces[p].kb > kmax ? pieces[p].kb : kmax;
+    kbf[q] = pieces[p].first == kNoLeaf ? fill : pieces[p].kb;
   }
-  // radix table: prefix(k) = (k - rbase) >> rshift with the smallest shift that
-  // maps every boundary below kRadix; rt[r] = first piece with prefix >= r
+  // radix table: prefix(k) = min((k - rbase) >> rshift, kRadix - 1) with the
+  // smallest shift that maps every boundary below kRadix; rt[r] = first piece with
+  // prefix >= r, i.e. rt[r] = p for prefix(piece p - 1) < r <= prefix(piece p):
+  // every thread writes the entries its pieces own (each entry once)
   for (int o = 16; o > 0; o >>= 1) {
     const uint64_t u = __shfl_xor_sync(0xFFFFFFFFu, kmax, o);
     kmax = u > kmax ? u : kmax;
@@ -139,19 +144,30 @@ __device__ void lm_publish(ModelHead *head, Piece *pieces, uint32_t np, uint32_t
     s_shift = sh;
   }
   __syncthreads();
+  const uint64_t base = s_base;
+  const uint32_t sh = s_shift;
+  auto prefix = [&](uint64_t kb) -> int32_t {
+    if (kb < base) return 0;
+    const uint64_t r = (kb - base) >> sh;
+    return r < kRadix - 1 ? (int32_t)r : (int32_t)(kRadix - 1);
+  };
   uint32_t *rt = reinterpret_cast<uint32_t *>(pieces + kPieces);
-  for (uint32_t r = t; r <= kRadix; r += kLmThreads) {
-    uint32_t lo = 0, hi = np;
-    if (r < kRadix) {
-      const uint64_t target = s_base + ((uint64_t)r << s_shift);
-      while (lo < hi) {
-        const uint32_t mid = (lo + hi) >> 1;
-        if (pieces[mid].kb < target) lo = mid + 1;
-        else hi = mid;
-      }
-    }
-    rt[r] = lo;
+  // prefix of the piece before this thread's first (-1 before piece 0)
+  int32_t prev = -1;
+  if (t > 0 && t * kPer <= np) prev = prefix(pieces[t * kPer - 1].kb);
+  for (uint32_t q = 0; q < kPer; q++) {
+    const uint32_t p = t * kPer + q;
+    if (p >= np) break;
+    const int32_t cur = prefix(kbf[q]);
+    for (int32_t r = prev + 1; r <= cur; r++) rt[r] = p;
+    prev = cur > prev ? cur : prev;
   }
+  // entries above the last piece's prefix: npieces
+  if ((t + 1) * kPer >= np && t * kPer < np) {
+    for (int32_t r = prev + 1; r <= (int32_t)kRadix; r++) rt[r] = np;
+  }
+  if (t == 0 && np == 0)
+    for (uint32_t r = 0; r <= kRadix; r++) rt[r] = 0;
   __syncthreads();
   if (t == 0) {
     head->span = span;
