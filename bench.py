@@ -551,7 +551,8 @@ def learned_study(a):
     out = {"workload": f"chung-lu V={V} E={E0} gamma=2.1 seed=7, batch {B} (70% insert / 30% random delete)",
            "clocks": clk.summary(),
            "plain_p50_ms": statistics.median(times["plain"]), "learned_p50_ms": statistics.median(times["learned"]),
-           "layouts_identical": same, "capacity_slots": graphs["plain"].capacity}
+           "layouts_identical": same, "capacity_slots": graphs["plain"].capacity,
+           "plain_ms": times["plain"], "learned_ms": times["learned"]}
     out["speedup"] = out["plain_p50_ms"] / out["learned_p50_ms"]
     for g in graphs.values():
         g.close()

@@ -82,6 +82,7 @@ struct Ctl {
   uint64_t gen_count;  // general-purpose counter (exports)
   uint32_t resized;    // this call grew the array on the device (into the spare)
   uint32_t nvlong;     // runs longer than kLongRun, left to the chunked level-0 path
+  uint32_t lm_miss;    // learned searches of this batch whose predicted window missed the leaf
   uint32_t spin_limit; // polls a bounded wait may make before it gives up (0: the built-in limits)
 };
 
@@ -362,7 +363,7 @@ __device__ __forceinline__ void leaf_search_lockstep(const uint64_t *__restrict_
 // keys whose window is bracketed finish with one lock-step bisection inside it,
 // the others (a stale model) take learned_leaf_search alone.  Same leaves.
 template <int Q>
-__device__ __forceinline__ void learned_search_lockstep(const ModelHead &m, const Piece *__restrict__ pieces,
+__device__ __forceinline__ uint32_t learned_search_lockstep(const ModelHead &m, const Piece *__restrict__ pieces,
                                                         const uint64_t *__restrict__ F, uint64_t nleaves,
                                                         const uint64_t (&k)[Q], const bool (&act)[Q],
                                                         uint32_t (&out)[Q]) {
@@ -425,11 +426,17 @@ __device__ __forceinline__ void learned_search_lockstep(const ModelHead &m, cons
     if (!ok[q]) lo[q] = hi[q] = 0;  // left to the single search below
   }
   bisect_lockstep<Q>(F, lo, hi, k, out);
+  uint32_t miss = 0;
 #pragma unroll
   for (int q = 0; q < Q; q++) {
-    if (!act[q]) out[q] = 0;
-    else if (!ok[q]) out[q] = learned_leaf_search(m, pieces, F, nleaves, k[q]);
+    if (!act[q]) {
+      out[q] = 0;
+    } else if (!ok[q]) {
+      out[q] = learned_leaf_search(m, pieces, F, nleaves, k[q]);
+      ++miss;
+    }
   }
+  return miss;  // keys whose window missed (a model that has drifted)
 }
 
 // ---- single-pass look-back (tiles take tickets in launch order) -------------------

@@ -649,6 +649,13 @@ __global__ void k_bfs_flag(const uint32_t *err, Ctl *ctl) {
   if (*err) atomicOr(&ctl->sticky, kErrTimeout);
 }
 
+// resident blocks of the persistent BFS kernel per SM (it holds them for the whole
+// search, so it also sets how much of the GPU a concurrent PageRank keeps)
+#ifndef GPMA_BFS_BLOCKS_PER_SM
+#define GPMA_BFS_BLOCKS_PER_SM 4
+#endif
+constexpr int kBfsBlocksPerSm = GPMA_BFS_BLOCKS_PER_SM;
+
 int run_bfs(const Geo &g, uint32_t src, int32_t *depth, uint32_t *q0, uint32_t *q1, uint32_t *q2,
             uint32_t *counter, Ctl *ctl, cudaStream_t s) {
   static int grid = 0;
@@ -657,7 +664,8 @@ int run_bfs(const Geo &g, uint32_t src, int32_t *depth, uint32_t *q0, uint32_t *
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_bfs_persist, 256, 0);
-    grid = sms * (per_sm > 4 ? 4 : per_sm);
+    const int want = kBfsBlocksPerSm;
+    grid = sms * (per_sm > want ? want : per_sm);
     if (grid < 1) grid = 1;
   }
   // counter layout: cnt[0..15], barrier words, error word

@@ -74,6 +74,7 @@ __global__ void k_init_batch(Ctl *ctl, uint32_t *hist, uint32_t nhist, uint32_t 
     for (int i = 0; i < 16; i++) ctl->ticket[i] = 0;
     ctl->n_inserted = ctl->n_deleted = 0;
     ctl->st_cov_touched = ctl->st_l0_only = ctl->st_empties = ctl->st_del_leaves = 0;
+    ctl->lm_miss = 0;
     ctl->levels_climbed = 0;
     ctl->n_merged0 = 0;
     for (int i = 0; i < kMaxLv; i++) ctl->merges[i] = 0;
@@ -257,12 +258,22 @@ __global__ void __launch_bounds__(kSortThreads) k_rscatter(const uint64_t *__res
   __syncthreads();
   const uint64_t t0 = (uint64_t)tile * (kSortThreads * ITEMS);
   const uint32_t cnt = t0 >= n ? 0u : (n - t0 < kSortThreads * ITEMS ? (uint32_t)(n - t0) : kSortThreads * ITEMS);
-  for (uint32_t i = threadIdx.x; i < cnt; i += kSortThreads) {
-    const uint64_t k = skey[i];
-    const uint32_t d = (uint32_t)(((k & ~kTagBit) >> shift) & mask);
-    const uint32_t pos = gbase[d] + (i - ltile[d]);
-    dst[pos] = k;
-    if (Hn) atomicAdd(&Hn[(uint64_t)(((k & ~kTagBit) >> nshift) & mask) * T + pos / (kSortThreads * ITEMS)], 1u);
+  for (uint32_t i0 = 0; i0 < cnt; i0 += kSortThreads) {
+    const uint32_t i = i0 + threadIdx.x;
+    uint32_t cell = 0xFFFFFFFFu;
+    if (i < cnt) {
+      const uint64_t k = skey[i];
+      const uint32_t d = (uint32_t)(((k & ~kTagBit) >> shift) & mask);
+      const uint32_t pos = gbase[d] + (i - ltile[d]);
+      dst[pos] = k;
+      cell = (uint32_t)(((k & ~kTagBit) >> nshift) & mask) * T + pos / (kSortThreads * ITEMS);
+    }
+    if (Hn) {
+      // staged keys leave in order, so lanes of one warp often share a destination
+      // tile and (for skewed keys) the next digit: one atomic per distinct cell
+      const uint32_t peers = __match_any_sync(0xFFFFFFFFu, cell);
+      if (cell != 0xFFFFFFFFu && lane == (uint32_t)(__ffs(peers) - 1)) atomicAdd(&Hn[cell], (uint32_t)__popc(peers));
+    }
   }
 }
 
@@ -317,6 +328,7 @@ __global__ void __launch_bounds__(1024) k_small_front(PrepArgs a, const uint64_t
     for (int i = 0; i < 16; i++) ctl->ticket[i] = 0;
     ctl->n_inserted = ctl->n_deleted = 0;
     ctl->st_cov_touched = ctl->st_l0_only = ctl->st_empties = ctl->st_del_leaves = 0;
+    ctl->lm_miss = 0;
     ctl->levels_climbed = 0;
     ctl->n_merged0 = 0;
     for (int i = 0; i < kMaxLv; i++) ctl->merges[i] = 0;
@@ -449,7 +461,7 @@ template <int Q>
 __global__ void __launch_bounds__(kSearchThreads) k_rsearch(PrepArgs a, const uint64_t *__restrict__ sorted,
                                                             uint32_t *__restrict__ lfull,
                                                             const uint64_t *__restrict__ F, uint64_t nleaves,
-                                                            TileSums ts, const Ctl *ctl, const ModelHead *mhead,
+                                                            TileSums ts, Ctl *ctl, const ModelHead *mhead,
                                                             const Piece *__restrict__ mpieces) {
   __shared__ uint32_t sl[(kSearchThreads * Q)];
   __shared__ uint32_t s_surv, s_hin, s_first, s_last;
@@ -481,7 +493,8 @@ __global__ void __launch_bounds__(kSearchThreads) k_rsearch(PrepArgs a, const ui
     kept[q] = e < n && ((wq & kTagBit) ? (e == 0 || (w[q] & ~kTagBit) != kq) : (e + 1 == n || (w[q + 2] & ~kTagBit) != kq));
     key[q] = kept[q] ? expand(wq, a) : 0ull;
   }
-  if (hd.valid) learned_search_lockstep<Q>(hd, mpieces, F, nleaves, key, kept, leaf);
+  uint32_t miss = 0;
+  if (hd.valid) miss = learned_search_lockstep<Q>(hd, mpieces, F, nleaves, key, kept, leaf);
   else leaf_search_lockstep<Q>(F, nleaves, key, kept, leaf);
 #pragma unroll
   for (int q = 0; q < Q; q++)
@@ -506,9 +519,11 @@ __global__ void __launch_bounds__(kSearchThreads) k_rsearch(PrepArgs a, const ui
   }
   surv = warp_sum(surv);
   hin = warp_sum(hin);
+  miss = warp_sum(miss);
   if (lane_id() == 0) {
     if (surv) atomicAdd(&s_surv, surv);
     if (hin) atomicAdd(&s_hin, hin);
+    if (miss) atomicAdd(&ctl->lm_miss, miss);
   }
   __syncthreads();
   if (t == 0) {

@@ -2,8 +2,9 @@
 // are in gpma_dev.cuh).  Everything runs on the device from the current pivots:
 // one kernel, k_lm_train:
 //   decide       retrain now?  Always after a resize or import and periodically;
-//                after a batch only once merges above level 0 have rewritten a
-//                thirty-second of the leaves since the last training (a level-0
+//                after a batch only once merges above level 0 have rewritten an
+//                eighth of the leaves since the last training, or more than 1% of
+//                the batch's searches missed their predicted window (a level-0
 //                merge moves keys only inside their leaf, and the search stays
 //                exact whatever the staleness, only slower).  Every block takes
 //                the same decision from the same inputs.
@@ -189,8 +190,10 @@ __global__ void __launch_bounds__(kLmThreads) k_lm_train(Geo g, ModelHead *head,
   uint64_t d = 0;
   bool now = true;
   if (after_batch) {
+    // retrain once merges above level 0 have rewritten an eighth of the leaves, or
+    // when more than 1% of this batch's searches missed their predicted window
     d = head->drift + (ctl->err == 0 ? ctl->nleafw : 0u);
-    now = head->valid == 0 || d * 32 >= g.nleaves;
+    now = head->valid == 0 || d * 8 >= g.nleaves || (uint64_t)ctl->lm_miss * 100 > ctl->m;
   }
   if (now) {
     const uint32_t p = blockIdx.x * (kLmThreads / 32) + (threadIdx.x >> 5);
