@@ -871,7 +871,7 @@ bool ensure_pb(gpma *h, const PbPlan &p, cudaStream_t s) {
   if (!h->pb_cnt) {
     const uint64_t n = (uint64_t)p.nb * kPbMaxChunks;
     if (!dalloc(h, &h->pb_cnt, n, s) || !dalloc(h, &h->pb_off, n + 1, s) ||
-        !dalloc(h, &h->pb_scan, scan_partials(n), s) ||
+        !dalloc(h, &h->pb_scan, (uint64_t)kPbMaxBuckets / 2 + 16, s) ||  // bucket totals (u32)
         !dalloc(h, &h->pb_dang, (uint64_t)p.nparts * p.nb, s)) {
       dfree(h, h->pb_cnt, s);
       dfree(h, h->pb_off, s);

@@ -145,7 +145,7 @@ void launch_pr_apply(const Geo &g, float damping, float *rank, uint64_t *y, uint
                      cudaStream_t s);
 // Bucketed pass: buckets of kPbBucket heads, G chunks of the slot array, a
 // cluster of nparts blocks per bucket.  cnt: u32[nb * G]; off: u64[nb * G + 1]
-// (scan output, off[nb*G] = edges); scan_tmp >= scan_partials(nb * G); keys:
+// (off[nb*G] = edges); scan_tmp: nb u32 bucket totals; keys:
 // u64[edges] (<= C).  One iteration reads cf_in and writes cf_out (FP32 x/outdeg,
 // V each), the ranks when last, and dsum_out; partials >= nb * nparts.
 constexpr uint32_t kPbShift = 12, kPbMaxShift = 14;

@@ -167,7 +167,8 @@ __global__ void k_pr_apply(uint32_t V, float damping, const uint32_t *__restrict
 // the high half, so the sum is exact modulo 2^64 whatever the order, as in the
 // push pass.
 __global__ void __launch_bounds__(256) k_pb_count(const ulonglong2 *__restrict__ s2, uint64_t npairs, uint64_t chunk,
-                                                  uint32_t nb, uint32_t shift, uint32_t *__restrict__ cnt) {
+                                                  uint32_t nb, uint32_t shift, uint32_t *__restrict__ cnt,
+                                                  uint32_t *__restrict__ tot) {
   __shared__ uint32_t hist[kPbMaxBuckets];
   for (uint32_t b = threadIdx.x; b < nb; b += blockDim.x) hist[b] = 0;
   __syncthreads();
@@ -178,7 +179,49 @@ __global__ void __launch_bounds__(256) k_pb_count(const ulonglong2 *__restrict__
     if (k.y != kEmpty && !is_guard(k.y)) atomicAdd(&hist[(uint32_t)k.y >> shift], 1u);
   }
   __syncthreads();
-  for (uint32_t b = threadIdx.x; b < nb; b += blockDim.x) cnt[(uint64_t)b * gridDim.x + blockIdx.x] = hist[b];
+  for (uint32_t b = threadIdx.x; b < nb; b += blockDim.x) {
+    cnt[(uint64_t)b * gridDim.x + blockIdx.x] = hist[b];
+    if (hist[b]) atomicAdd(&tot[b], hist[b]);
+  }
+}
+
+// Offsets of the bucketed copy: off[b * G + c] = edges of smaller buckets plus
+// bucket b's edges in chunks before c (off[nb * G] = all edges).  One block per
+// bucket; tot[b] = bucket b's edges.
+__global__ void __launch_bounds__(256) k_pb_offsets(const uint32_t *__restrict__ cnt, const uint32_t *__restrict__ tot,
+                                                    uint64_t *__restrict__ off, uint32_t G, uint32_t nb) {
+  __shared__ uint32_t wsum[33];
+  __shared__ unsigned long long s_base;
+  const uint32_t b = blockIdx.x;
+  if (threadIdx.x == 0) s_base = 0;
+  __syncthreads();
+  unsigned long long part = 0;
+  for (uint32_t e = threadIdx.x; e < b; e += blockDim.x) part += tot[e];
+  part = warp_sum(part);
+  if (lane_id() == 0 && part) atomicAdd(&s_base, part);
+  __syncthreads();
+  uint64_t carry = s_base;
+  const uint32_t *col = cnt + (uint64_t)b * G;
+  uint64_t *o = off + (uint64_t)b * G;
+  constexpr uint32_t kPer = 8;
+  for (uint32_t c0 = 0; c0 < G; c0 += 256 * kPer) {
+    const uint32_t t0 = c0 + threadIdx.x * kPer;
+    uint32_t v[kPer], loc = 0;
+#pragma unroll
+    for (uint32_t q = 0; q < kPer; q++) {
+      v[q] = t0 + q < G ? col[t0 + q] : 0u;
+      loc += v[q];
+    }
+    uint32_t total;
+    uint64_t run = carry + block_excl_scan(loc, wsum, &total);
+#pragma unroll
+    for (uint32_t q = 0; q < kPer; q++) {
+      if (t0 + q < G) o[t0 + q] = run;
+      run += v[q];
+    }
+    carry += total;
+  }
+  if (b + 1 == nb && threadIdx.x == 0) off[(uint64_t)nb * G] = carry;
 }
 
 // Placement, one tile of kPbTile slots at a time: the tile's edges are ranked
@@ -407,9 +450,12 @@ PbPlan pb_plan(const Geo &g) {
 void launch_pb_build(const Geo &g, const PbPlan &p, uint32_t *cnt, uint64_t *off, uint64_t *scan_tmp, uint64_t *keys,
                      cudaStream_t s) {
   const ulonglong2 *s2 = reinterpret_cast<const ulonglong2 *>(g.slots);
+  uint32_t *tot = reinterpret_cast<uint32_t *>(scan_tmp);  // nb bucket totals
+  cudaMemsetAsync(tot, 0, sizeof(uint32_t) * p.nb, s);
   note_launch();
-  k_pb_count<<<p.G, 256, 0, s>>>(s2, g.C >> 1, p.chunk, p.nb, p.shift, cnt);
-  launch_scan_u32_u64(cnt, off, (uint64_t)p.nb * p.G, scan_tmp, s);
+  k_pb_count<<<p.G, 256, 0, s>>>(s2, g.C >> 1, p.chunk, p.nb, p.shift, cnt, tot);
+  note_launch();
+  k_pb_offsets<<<p.nb, 256, 0, s>>>(cnt, tot, off, p.G, p.nb);
   if (p.nb > kPbStageMax) {
     note_launch();
     k_pb_place_direct<<<p.G, 256, 0, s>>>(s2, g.C >> 1, p.chunk, p.nb, p.shift, off, keys);
@@ -650,9 +696,12 @@ __global__ void k_bfs_flag(const uint32_t *err, Ctl *ctl) {
 }
 
 // resident blocks of the persistent BFS kernel per SM (it holds them for the whole
-// search, so it also sets how much of the GPU a concurrent PageRank keeps)
+// search, so it also sets how much of the GPU a concurrent PageRank keeps).
+// Measured in the bench step (R-MAT scale 20, BFS and CC beside PageRank-20): 2
+// blocks 2.26 ms per step against 2.39 with 4 and 2.29 with 1 (BFS alone takes
+// longer with fewer blocks, but the PageRank bucketing beside it halves)
 #ifndef GPMA_BFS_BLOCKS_PER_SM
-#define GPMA_BFS_BLOCKS_PER_SM 4
+#define GPMA_BFS_BLOCKS_PER_SM 2
 #endif
 constexpr int kBfsBlocksPerSm = GPMA_BFS_BLOCKS_PER_SM;
 

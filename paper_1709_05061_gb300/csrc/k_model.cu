@@ -3,8 +3,9 @@
 // one kernel, k_lm_train:
 //   decide       retrain now?  Always after a resize or import and periodically;
 //                after a batch only once merges above level 0 have rewritten an
-//                eighth of the leaves since the last training, or more than 1% of
-//                the batch's searches missed their predicted window (a level-0
+//                eighth of the leaves since the last training, or a quarter of the
+//                batch's searches missed their predicted window (a miss costs one
+//                more search, a training about two search kernels; a level-0
 //                merge moves keys only inside their leaf, and the search stays
 //                exact whatever the staleness, only slower).  Every block takes
 //                the same decision from the same inputs.
@@ -73,7 +74,7 @@ __device__ __forceinline__ void lm_fit_piece(const Geo &g, uint32_t span, uint32
   if (lane == 0) pieces[p] = pc;
 }
 
-constexpr uint32_t kLmThreads = 256;
+constexpr uint32_t kLmThreads = 1024;
 
 // Publish (one block of kLmThreads): suffix minimum of the boundaries (an empty
 // piece takes the next boundary), the radix table, the head fields, valid last.
@@ -191,9 +192,9 @@ __global__ void __launch_bounds__(kLmThreads) k_lm_train(Geo g, ModelHead *head,
   bool now = true;
   if (after_batch) {
     // retrain once merges above level 0 have rewritten an eighth of the leaves, or
-    // when more than 1% of this batch's searches missed their predicted window
+    // when a quarter of this batch's searches missed their predicted window
     d = head->drift + (ctl->err == 0 ? ctl->nleafw : 0u);
-    now = head->valid == 0 || d * 8 >= g.nleaves || (uint64_t)ctl->lm_miss * 100 > ctl->m;
+    now = head->valid == 0 || d * 8 >= g.nleaves || (uint64_t)ctl->lm_miss * 4 > ctl->m;
   }
   if (now) {
     const uint32_t p = blockIdx.x * (kLmThreads / 32) + (threadIdx.x >> 5);
@@ -220,7 +221,8 @@ void launch_train_model(const Geo &g, ModelHead *head, Piece *pieces, const Ctl 
                         cudaStream_t s) {
   const uint64_t np = g.nleaves < kPieces ? g.nleaves : kPieces;
   note_launch();
-  k_lm_train<<<(uint32_t)((np + 7) / 8), kLmThreads, 0, s>>>(g, head, pieces, ctl, after_batch ? 1 : 0);
+  constexpr uint32_t kWarps = kLmThreads / 32;  // one piece per warp
+  k_lm_train<<<(uint32_t)((np + kWarps - 1) / kWarps), kLmThreads, 0, s>>>(g, head, pieces, ctl, after_batch ? 1 : 0);
 }
 
 }  // namespace gpk
