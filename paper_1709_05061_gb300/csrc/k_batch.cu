@@ -351,9 +351,14 @@ __global__ void __launch_bounds__(1024) k_small_front(PrepArgs a, const uint64_t
     }
     sk[i] = word;
   }
-  // sampled pivots (the stores land in cv; compacted in place below)
+  ModelHead hd;
+  hd.valid = 0;
+  if (mhead) hd = *mhead;
+  const bool learned = hd.valid != 0;
+  // sampled pivots (the stores land in cv; compacted in place below); a trained
+  // model replaces them, so it skips the loads
   uint32_t nonempty = 0;
-  for (uint32_t q = 0; q < spt; q++) {
+  for (uint32_t q = 0; q < spt && !learned; q++) {
     const uint32_t i = s0 + q;
     if (i >= S) break;
     const uint64_t f = __ldg(F + i * stride);
@@ -380,7 +385,7 @@ __global__ void __launch_bounds__(1024) k_small_front(PrepArgs a, const uint64_t
   }
   // compact the non-empty samples in order (read own values before the scan's barrier)
   uint64_t mine[8];
-  for (uint32_t q = 0; q < spt && q < 8; q++) mine[q] = s0 + q < S ? cv[s0 + q] : kEmpty;
+  for (uint32_t q = 0; q < spt && q < 8; q++) mine[q] = (!learned && s0 + q < S) ? cv[s0 + q] : kEmpty;
   uint32_t cnt;
   uint32_t co = block_excl_scan(nonempty, wsum, &cnt);
   for (uint32_t q = 0; q < spt && q < 8; q++) {
@@ -404,10 +409,6 @@ __global__ void __launch_bounds__(1024) k_small_front(PrepArgs a, const uint64_t
     if ((keep >> q) & 1) sw[off++] = sk[e0 + q];
   __syncthreads();
   // the leaf of every survivor (reading R4), one survivor per thread at a time
-  ModelHead hd;
-  hd.valid = 0;
-  if (mhead) hd = *mhead;
-  const bool learned = hd.valid != 0;
   for (uint32_t e = t; e < m; e += nt) {
     const uint64_t w = sw[e];
     const uint64_t key = expand(w >> 1, a);
