@@ -206,6 +206,14 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def hold_gpu(cycles: int = 200_000):
+    """Keep the GPU busy for ~0.1 ms so that the host has enqueued the next call's
+    launches before the device reaches them: the call's events then measure device
+    time, not the host's enqueue latency (which the first call after host work pays)."""
+    import torch
+    torch.cuda._sleep(cycles)
+
+
 def alg_bytes_table(st: dict, n_raw: int, C_old: int, C_new: int) -> int:
     """Algorithmic bytes of one batch by the measurement plan's formula: 16 B per
     raw update key (read once, written once while staging), a 512-byte read of
@@ -272,6 +280,7 @@ def run_gpu(a, stream, rank, world, dist):
                 di, dd = to_dev(ins), to_dev(dels)
                 flush.zero_()
                 c_old = g.capacity
+                hold_gpu()
                 gp.gpma_profile_enable(g.h, True)
                 s = g.update(di, dd, stats=True)
                 p = gp.gpma_profile_read(g.h, reset=True)
@@ -279,6 +288,7 @@ def run_gpu(a, stream, rank, world, dist):
                 ms = p["update"]["ms"]
                 # sort-and-rebuild CSR baseline on the same batch
                 flush.zero_()
+                hold_gpu()
                 e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
                 e0.record()
                 keep = ~torch.isin(live, dd)
@@ -538,8 +548,11 @@ def learned_study(a):
         keep[pick] = False
         live = np.concatenate([live[keep], ins])
         di, dd = dev(ins), dev(dels)
-        for name, g in graphs.items():
+        # alternate which handle goes first, and let the host run ahead of the device
+        for name in (("learned", "plain") if i % 2 == 0 else ("plain", "learned")):
+            g = graphs[name]
             flush.zero_()
+            hold_gpu()
             gp.gpma_profile_enable(g.h, True)
             g.update(di, dd, stats=True)
             p = gp.gpma_profile_read(g.h, reset=True)
@@ -680,6 +693,7 @@ def serve_study(a):
             di = torch.from_numpy(np.ascontiguousarray(ins).view(np.int64)).cuda()
             dd = torch.from_numpy(np.ascontiguousarray(dels).view(np.int64)).cuda()
             c_old = g.capacity
+            hold_gpu()
             gp.gpma_profile_enable(g.h, True)
             st = g.update(di, dd, stats=True)
             p = gp.gpma_profile_read(g.h, reset=True)
