@@ -175,6 +175,22 @@ int gpma_cc(gpma_t h, uint32_t *d_label, void *stream);
  * the slot array).  Stream-ordered. */
 int gpma_pagerank(gpma_t h, uint32_t iters, float damping, float *d_rank, void *stream);
 
+/* PageRank in two steps, so that updates need not wait for the iterations (the
+ * stream of Sec. 3 keeps flowing while a query runs).  gpma_pagerank_snapshot takes
+ * a snapshot of the graph on `stream`: the stored edges bucketed by head and the
+ * out-degrees, in buffers of the handle.  gpma_pagerank_run then iterates exactly
+ * as gpma_pagerank does, but over the last snapshot only: once the snapshot's work
+ * has completed (an event recorded after it), updates may run on other streams
+ * while the iterations run, and the ranks are those of the graph at snapshot time.
+ * A new snapshot, or a gpma_pagerank call (which rebuilds the same buffers and
+ * discards the snapshot), must not start before the runs on the previous one have
+ * finished; runs share their scratch with each other and with gpma_pagerank, so
+ * they must not overlap on the GPU either.  gpma_pagerank_snapshot returns GPMA_EINVAL for a handle that sums by
+ * the push pass (GPMA_PUSH_PAGERANK, or more than 2^24 vertices), which reads the
+ * array itself; gpma_pagerank_run returns GPMA_EINVAL without a snapshot. */
+int gpma_pagerank_snapshot(gpma_t h, void *stream);
+int gpma_pagerank_run(gpma_t h, uint32_t iters, float damping, float *d_rank, void *stream);
+
 /* Copy the stored edges (no guards) in ascending key order into d_out[cap]:
  * the edge set a query of the stream model sees (Sec. 3, "Graph Streams" and the
  * query buffer of Fig. 1), read off the gapped array in slot order.  *n_out =

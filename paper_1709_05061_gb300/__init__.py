@@ -143,6 +143,8 @@ def lib():
             "gpma_bfs": ([vp, u32, vp, vp], i),
             "gpma_cc": ([vp, vp, vp], i),
             "gpma_pagerank": ([vp, u32, C.c_float, vp, vp], i),
+            "gpma_pagerank_snapshot": ([vp, vp], i),
+            "gpma_pagerank_run": ([vp, u32, C.c_float, vp, vp], i),
             "gpma_export_sorted": ([vp, vp, u64, P(u64), vp], i),
             "gpma_export_sorted_noalloc": ([vp, vp, u64, P(u64), vp], i),
             "gpma_export_csr": ([vp, vp, vp, u64, P(u64), vp], i),
@@ -251,6 +253,20 @@ def gpma_cc(h: int, out, stream=None):
 
 def gpma_pagerank(h: int, iters: int, damping: float, out, stream=None):
     _check(lib().gpma_pagerank(C.c_void_p(h), iters, damping, _ptr(out), _stream(stream)), "gpma_pagerank")
+    return out
+
+
+def gpma_pagerank_snapshot(h: int, stream=None) -> bool:
+    """True when a snapshot was taken; False for a handle that sums by the push pass."""
+    rc = lib().gpma_pagerank_snapshot(C.c_void_p(h), _stream(stream))
+    if rc == GPMA_EINVAL:
+        return False
+    _check(rc, "gpma_pagerank_snapshot")
+    return True
+
+
+def gpma_pagerank_run(h: int, iters: int, damping: float, out, stream=None):
+    _check(lib().gpma_pagerank_run(C.c_void_p(h), iters, damping, _ptr(out), _stream(stream)), "gpma_pagerank_run")
     return out
 
 

@@ -210,6 +210,11 @@ struct gpma {
   uint32_t *pb_cnt;
   uint64_t *pb_off, *pb_scan, *pb_keys, *pb_dang;
   uint64_t pb_keys_cap;
+  // the snapshot the iterations read: the bucketed copy above plus the out-degrees
+  // at snapshot time, and the plan it was built with
+  uint32_t *pb_deg;
+  PbPlan snap_plan;
+  bool snap_valid;
   uint32_t *check_buf;
   uint64_t *guards;
   uint64_t count_ub;
@@ -894,6 +899,41 @@ bool ensure_pb(gpma *h, const PbPlan &p, cudaStream_t s) {
   return true;
 }
 
+// The PageRank snapshot: the stored edges bucketed by head and, with `own_deg`,
+// a copy of the out-degrees as they are now (bucketed pass only; *bucketed = false
+// when the handle sums by the push pass, which reads the array itself).
+int pr_snapshot(gpma *h, cudaStream_t s, bool own_deg, bool *bucketed) {
+  *bucketed = false;
+  const PbPlan plan = pb_plan(h->geo);
+  if (!ensure_pb(h, plan, s)) return GPMA_OK;
+  if (own_deg && !h->pb_deg && !dalloc(h, &h->pb_deg, h->V, s)) return GPMA_ENOMEM;
+  {
+    Phase ph(h->prof, GPMA_PROF_PR_BUCKET, s);
+    launch_pb_build(h->geo, plan, h->pb_cnt, h->pb_off, h->pb_scan, h->pb_keys, s);
+    if (own_deg) cudaMemcpyAsync(h->pb_deg, h->geo.deg, sizeof(uint32_t) * h->V, cudaMemcpyDeviceToDevice, s);
+  }
+  h->snap_plan = plan;
+  h->snap_valid = own_deg;  // only a snapshot with its own degrees outlives the call
+  *bucketed = true;
+  return cuda_ok(h);
+}
+
+// iterations over the bucketed copy (with `own_deg`, over the snapshot alone: the
+// live array may change meanwhile)
+int pr_run(gpma *h, uint32_t iters, float damping, float *d_rank, bool own_deg, cudaStream_t s) {
+  Geo gs = h->geo;
+  if (own_deg) gs.deg = h->pb_deg;
+  // bucketed: the two halves of cfx hold the FP32 contributions of alternate iterations
+  float *cf[2] = {reinterpret_cast<float *>(h->cfx), reinterpret_cast<float *>(h->cfx) + h->V};
+  launch_pr_setup(gs, iters, d_rank, h->y, h->cfx, cf[0], h->dsum, h->pr_partials, h->pr_counter, s);
+  for (uint32_t it = 0; it < iters; it++) {
+    Phase ph(h->prof, GPMA_PROF_PR_SCATTER, s);
+    launch_pb_iter(gs, h->snap_plan, h->pb_keys, h->pb_off, damping, cf[it & 1], cf[(it + 1) & 1], d_rank,
+                   it + 1 == iters, h->dsum + it, h->dsum + it + 1, h->pb_dang, h->pr_counter, s);
+  }
+  return cuda_ok(h);
+}
+
 }  // namespace
 
 namespace gpk {
@@ -1033,7 +1073,7 @@ int gpma_destroy(gpma_t h) {
   free_work(h, s);
   void *ptrs[] = {h->mhead, h->mpieces, h->ctl, h->hist, h->scratch, h->vbuf, h->partials, h->cfx, h->y,
                   h->dsum, h->q0,  h->q1,  h->q2,    h->counter, h->check_buf, h->guards, h->pr_partials,
-                  h->pr_counter, h->pb_cnt, h->pb_off, h->pb_scan, h->pb_keys, h->pb_dang};
+                  h->pr_counter, h->pb_cnt, h->pb_off, h->pb_scan, h->pb_keys, h->pb_dang, h->pb_deg};
   for (void *p : ptrs) dfree(h, p, s);
   cudaStreamSynchronize(s);
   if (h->h_ctl) cudaFreeHost(h->h_ctl);
@@ -1095,30 +1135,42 @@ int gpma_pagerank(gpma_t h, uint32_t iters, float damping, float *d_rank, void *
   cudaStream_t s = (cudaStream_t)stream;
   if (ensure_analytics(h, iters, s)) return GPMA_ENOMEM;
   Phase all(h->prof, GPMA_PROF_PAGERANK, s);
-  const PbPlan plan = pb_plan(h->geo);
-  const bool bucketed = iters > 0 && ensure_pb(h, plan, s);
-  // bucketed: the two halves of cfx hold the FP32 contributions of alternate iterations
-  float *cf[2] = {reinterpret_cast<float *>(h->cfx), reinterpret_cast<float *>(h->cfx) + h->V};
-  if (bucketed) {
-    Phase ph(h->prof, GPMA_PROF_PR_BUCKET, s);
-    launch_pb_build(h->geo, plan, h->pb_cnt, h->pb_off, h->pb_scan, h->pb_keys, s);
+  bool bucketed = false;
+  if (iters > 0) {
+    const int rc = pr_snapshot(h, s, false, &bucketed);
+    if (rc) return rc;
   }
-  launch_pr_setup(h->geo, iters, d_rank, h->y, h->cfx, bucketed ? cf[0] : nullptr, h->dsum, h->pr_partials,
-                  h->pr_counter, s);
+  if (bucketed) return pr_run(h, iters, damping, d_rank, false, s);
+  // push pass: every iteration reads the array itself
+  launch_pr_setup(h->geo, iters, d_rank, h->y, h->cfx, nullptr, h->dsum, h->pr_partials, h->pr_counter, s);
   for (uint32_t it = 0; it < iters; it++) {
     Phase ph(h->prof, GPMA_PROF_PR_SCATTER, s);
-    if (bucketed) {
-      launch_pb_iter(h->geo, plan, h->pb_keys, h->pb_off, damping, cf[it & 1], cf[(it + 1) & 1], d_rank,
-                     it + 1 == iters, h->dsum + it, h->dsum + it + 1, h->pb_dang, h->pr_counter, s);
-    } else {
-      launch_pr_scatter(h->geo, h->cfx, h->y, s);
-      ph.end();
-      launch_pr_apply(h->geo, damping, d_rank, h->y, h->cfx, h->dsum + it, h->dsum + it + 1, h->pr_partials,
-                      h->pr_counter, it + 1 == iters, s);
-    }
+    launch_pr_scatter(h->geo, h->cfx, h->y, s);
+    ph.end();
+    launch_pr_apply(h->geo, damping, d_rank, h->y, h->cfx, h->dsum + it, h->dsum + it + 1, h->pr_partials,
+                    h->pr_counter, it + 1 == iters, s);
   }
   all.end();
   return cuda_ok(h);
+}
+
+int gpma_pagerank_snapshot(gpma_t h, void *stream) {
+  if (!h || h->raw) return GPMA_EINVAL;
+  if (h->poisoned) return h->poisoned;
+  if (int rs = settle(h, (cudaStream_t)stream)) return rs;
+  bool bucketed = false;
+  const int rc = pr_snapshot(h, (cudaStream_t)stream, true, &bucketed);
+  if (rc) return rc;
+  return bucketed ? GPMA_OK : GPMA_EINVAL;  // the push pass reads the array itself
+}
+
+int gpma_pagerank_run(gpma_t h, uint32_t iters, float damping, float *d_rank, void *stream) {
+  if (!h || !d_rank || h->raw || !(damping >= 0.0f && damping <= 1.0f) || !h->snap_valid) return GPMA_EINVAL;
+  if (h->poisoned) return h->poisoned;
+  cudaStream_t s = (cudaStream_t)stream;
+  if (ensure_analytics(h, iters, s)) return GPMA_ENOMEM;
+  Phase all(h->prof, GPMA_PROF_PAGERANK, s);
+  return pr_run(h, iters, damping, d_rank, true, s);
 }
 
 int gpma_export_sorted(gpma_t h, uint64_t *d_out, uint64_t cap, uint64_t *n_out, void *stream) {

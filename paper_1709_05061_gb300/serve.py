@@ -16,9 +16,12 @@ queries).  The server admits them in arrival order:
   ``result_slots`` device buffers (a query waits for a free slot);
   ``Server.with_budget`` derives both from a byte budget.
 
-Two CUDA streams overlap transfers with compute: host-to-device copies of
+Three CUDA streams overlap transfers with compute: host-to-device copies of
 update keys and device-to-host copies of query results run on the copy stream,
-updates and queries on the compute stream, ordered by events.  The host keeps
+updates and queries on the compute stream, ordered by events.  A PageRank query
+takes its snapshot of the graph on the compute stream (in order with the
+updates) and iterates on a third stream, so the updates after it need not wait
+for its iterations (the snapshot holds the graph as it was).  The host keeps
 at most ``max_inflight`` operations queued on the compute stream, so requests
 that arrive while the GPU is busy are coalesced instead of queued one by one.
 
@@ -125,6 +128,9 @@ class Server:
         self.max_inflight = int(max_inflight)
         self.compute = torch.cuda.Stream()
         self.copy = torch.cuda.Stream()
+        self.pr_stream = torch.cuda.Stream()  # PageRank iterations over a snapshot
+        self.pr_done = None                   # event: the last PageRank run has finished
+        self.split_pr = True                  # snapshot + run (False once the handle refuses)
         # staging: pinned host keys and their device copies (two sets, alternating)
         self.h_keys = [torch.empty(self.max_batch_keys, dtype=torch.int64, pin_memory=True) for _ in range(2)]
         self.d_keys = [torch.empty(self.max_batch_keys, dtype=torch.int64, device="cuda") for _ in range(2)]
@@ -204,7 +210,7 @@ class Server:
 
     def _issue_query(self, op, t0):
         torch = self.torch
-        from . import gpma_bfs, gpma_cc, gpma_pagerank
+        from . import gpma_bfs, gpma_cc, gpma_pagerank, gpma_pagerank_run, gpma_pagerank_snapshot
         while True:
             free = [k for k, b in enumerate(self.slot_busy) if b is None]
             if free:
@@ -213,14 +219,27 @@ class Server:
         k = free[0]
         r = op.reqs[0]
         out = self.d_res[k]
+        ran = torch.cuda.Event()
         if r.kind == BFS:
             gpma_bfs(self.g.h, r.src, out, self.compute)
+            ran.record(self.compute)
         elif r.kind == CC:
             gpma_cc(self.g.h, out, self.compute)
+            ran.record(self.compute)
         else:
-            gpma_pagerank(self.g.h, r.iters, self.damping, out.view(torch.float32), self.compute)
-        ran = torch.cuda.Event()
-        ran.record(self.compute)
+            if self.pr_done is not None:
+                self.compute.wait_event(self.pr_done)  # the snapshot buffers are free again
+            if self.split_pr and gpma_pagerank_snapshot(self.g.h, self.compute):
+                snap = torch.cuda.Event()
+                snap.record(self.compute)
+                self.pr_stream.wait_event(snap)
+                gpma_pagerank_run(self.g.h, r.iters, self.damping, out.view(torch.float32), self.pr_stream)
+                ran.record(self.pr_stream)
+                self.pr_done = ran
+            else:
+                self.split_pr = False
+                gpma_pagerank(self.g.h, r.iters, self.damping, out.view(torch.float32), self.compute)
+                ran.record(self.compute)
         self.copy.wait_event(ran)
         with torch.cuda.stream(self.copy):
             self.h_res[k].copy_(out, non_blocking=True)

@@ -371,3 +371,55 @@ def test_pagerank_bucketed_equals_push(V, n_edges, seed):
         assert np.max(np.abs(a.astype(np.float64) - ref) / ref) <= PR_TOL
     gb.status()
     gpush.status()
+
+
+def test_pagerank_snapshot_holds_the_graph_it_was_taken_on():
+    """gpma_pagerank_snapshot copies the edges and out-degrees of the graph as it is
+    at that point of the stream; gpma_pagerank_run then iterates over the copy.
+    Updates between the two (here: inserts that grow the array, then deletes of a
+    third of the edges) do not change the ranks, which equal those of one
+    gpma_pagerank call on the earlier graph bit for bit and the oracle's within the
+    tolerance.  A second run over the same snapshot repeats the ranks; a handle that
+    sums by the push pass takes no snapshot; a run with no snapshot is refused."""
+    V = 1 << 15
+    stream = W.rmat_stream(15, 400_000, seed=71)
+    first, more = stream[:150_000], stream[150_000:]
+    g = gp.Graph(V, leaf_size=64)
+    o = oracle.OraclePMA(V, L=64)
+    out = torch.empty(V, dtype=torch.float32, device="cuda")
+    with pytest.raises(gp.GpmaError) as e:
+        gp.gpma_pagerank_run(g.h, 5, 0.85, out)
+    assert e.value.code == gp.GPMA_EINVAL
+    g.update(dev(first), None)
+    o.update(first)
+    alone = g.pagerank(20, 0.85).clone()
+    ref = o.pagerank(20, 0.85)
+    assert gp.gpma_pagerank_snapshot(g.h)
+    cap0 = g.capacity
+    g.update(dev(more), None)
+    g.update(None, dev(first[::3]))
+    assert g.capacity > cap0
+    gp.gpma_pagerank_run(g.h, 20, 0.85, out)
+    assert torch.equal(out.view(torch.int32), alone.view(torch.int32))
+    assert np.max(np.abs(out.cpu().numpy().astype(np.float64) - ref) / ref) <= PR_TOL
+    out2 = torch.empty_like(out)
+    gp.gpma_pagerank_run(g.h, 20, 0.85, out2)
+    assert torch.equal(out2.view(torch.int32), out.view(torch.int32))
+    # a new snapshot sees the updates
+    o.update(more)
+    o.update(np.zeros(0, np.uint64), first[::3])
+    assert gp.gpma_pagerank_snapshot(g.h)
+    gp.gpma_pagerank_run(g.h, 20, 0.85, out)
+    assert torch.equal(out.view(torch.int32), g.pagerank(20, 0.85).view(torch.int32))
+    ref2 = o.pagerank(20, 0.85)
+    assert np.max(np.abs(out.cpu().numpy().astype(np.float64) - ref2) / ref2) <= PR_TOL
+    g.status()
+    g.close()
+    gpush = gp.Graph(V, leaf_size=64, push_pagerank=True)
+    gpush.update(dev(first), None)
+    assert not gp.gpma_pagerank_snapshot(gpush.h)
+    with pytest.raises(gp.GpmaError) as e:
+        gp.gpma_pagerank_run(gpush.h, 5, 0.85, out)
+    assert e.value.code == gp.GPMA_EINVAL
+    gpush.status()
+    gpush.close()
