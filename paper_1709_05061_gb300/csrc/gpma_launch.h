@@ -148,11 +148,13 @@ void launch_pr_apply(const Geo &g, float damping, float *rank, uint64_t *y, uint
 // (off[nb*G] = edges); scan_tmp: nb u32 bucket totals; keys:
 // u64[edges] (<= C).  One iteration reads cf_in and writes cf_out (FP32 x/outdeg,
 // V each), the ranks when last, and dsum_out; partials >= nb * nparts.
-constexpr uint32_t kPbShift = 12, kPbMaxShift = 14;
+constexpr uint32_t kPbShift = 13, kPbMaxShift = 14;
 constexpr uint32_t kPbMaxBuckets = 4096;  // heads < kPbMaxBuckets << shift
 constexpr uint32_t kPbMaxChunks = 152 * 8, kPbTargetBlocks = 512, kPbMaxParts = 8;
 constexpr uint32_t kPbTile = 8192, kPbPlaceThreads = 512;  // placement: slots per tile, threads
-constexpr uint32_t kPbStageMax = 512;  // more buckets than this: placement without staging
+// more buckets than this: placement without staging (a staged tile of 8192 slots
+// then holds only about 8 edges of each bucket, too few to group the writes)
+constexpr uint32_t kPbStageMax = 256;
 struct PbPlan {
   uint32_t shift, nb, G, nparts, threads;  // 2^shift heads per bucket; threads per iteration block
   uint64_t chunk;  // slot pairs per chunk

@@ -154,10 +154,10 @@ __global__ void k_pr_apply(uint32_t V, float damping, const uint32_t *__restrict
 }
 
 // ---- bucketed PageRank pass ----------------------------------------------------------------------
-// Once per call the stored edges are copied into buckets by head (v >> 12, a
+// Once per call the stored edges are copied into buckets by head (v >> 13, a
 // counting sort by chunk of the array: per-chunk bucket counts, a scan, a
 // placement pass).  Every iteration then gives each bucket a cluster of blocks;
-// each block sums the contributions of its share of the bucket into a 4096-entry
+// each block sums the contributions of its share of the bucket into an 8192-entry
 // table in shared memory, and the cluster adds its tables through distributed
 // shared memory and applies the update.  The random reductions of the push pass
 // become shared-memory atomics.  The copy keeps the chunks in slot order, so
@@ -427,7 +427,10 @@ void launch_pr_apply(const Geo &g, float damping, float *rank, uint64_t *y, uint
 
 PbPlan pb_plan(const Geo &g) {
   PbPlan p;
-  p.shift = kPbShift;  // 4096 heads: wider buckets (2^13, 2^14) measured slower at scales 20 and 24
+  // 8192 heads a bucket (a 64 KB table): a warp's 32 edges then span half as
+  // many contribution lines as with 4096 heads (measured, one iteration at R-MAT
+  // scale 20: 0.058 ms against 0.062 ms with 4096 heads and 0.097 ms with 16384)
+  p.shift = kPbShift;
   p.nb = (uint32_t)((g.V + (1u << p.shift) - 1) >> p.shift);
   const uint64_t npairs = g.C >> 1;
   uint64_t G = (npairs + 2047) / 2048;
@@ -439,11 +442,10 @@ PbPlan pb_plan(const Geo &g) {
   const uint32_t want = (kPbTargetBlocks + p.nb - 1) / p.nb;
   p.nparts = 1;
   while (p.nparts * 2 <= want && p.nparts * 2 <= kPbMaxParts) p.nparts *= 2;
-  // a bucket per block (many buckets): 1024 threads; a cluster per bucket: 512
-  // (measured: PageRank-20 at R-MAT scale 20, 2 blocks per bucket, 1.47 ms with 512
-  // threads against 1.68 with 1024 and 2.40 with 256; at scale 24, one block per
-  // bucket, 29.1 ms with 1024 against 31.0 with 512)
-  p.threads = p.nparts == 1 ? 1024 : 512;
+  // 1024 threads (measured at scale 20 with 8192-head buckets: 4 blocks a bucket
+  // 0.058 ms per iteration against 0.072 ms with 512 threads, 0.074 ms with 8
+  // blocks a bucket)
+  p.threads = 1024;
   return p;
 }
 
@@ -477,7 +479,6 @@ void launch_pb_iter(const Geo &g, const PbPlan &p, const uint64_t *keys, const u
                     uint64_t *dsum_out, uint64_t *partials, unsigned *counter, cudaStream_t s) {
   static bool big = false;
   if (!big) {
-    cudaFuncSetAttribute(k_pb_iter<512>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(8u << kPbMaxShift));
     cudaFuncSetAttribute(k_pb_iter<1024>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(8u << kPbMaxShift));
     big = true;
   }
@@ -494,7 +495,7 @@ void launch_pb_iter(const Geo &g, const PbPlan &p, const uint64_t *keys, const u
   cfg.attrs = at;
   cfg.numAttrs = 1;
   note_launch();
-  auto kern = p.threads == 1024 ? k_pb_iter<1024> : k_pb_iter<512>;
+  auto kern = k_pb_iter<1024>;
   cudaLaunchKernelEx(&cfg, kern, keys, off, p.G, p.shift, p.nparts, g.V, damping, (const uint32_t *)g.deg, cf_in, cf_out,
                      rank, last ? 1 : 0, dsum_in, dsum_out, partials, counter);
 }

@@ -334,7 +334,7 @@ def test_pagerank_mid_size():
 @pytest.mark.parametrize("V,n_edges,seed", [(1 << 16, 1_000_000, 8), (5000, 60_000, 3), (4097, 20_000, 4),
                                             (1, 0, 0), (300, 0, 0)])
 def test_pagerank_bucketed_equals_push(V, n_edges, seed):
-    """The bucketed sum pass (edges copied into head buckets of 4096, partial sums
+    """The bucketed sum pass (edges copied into head buckets of 8192, partial sums
     in shared memory) and the push pass (one L2 reduction per stored edge) add the
     same fixed-point contributions, so their ranks agree bit for bit: on an R-MAT
     graph with heavy heads, on vertex counts that leave a ragged last bucket, and on

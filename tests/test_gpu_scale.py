@@ -95,15 +95,15 @@ def test_chung_lu_learned_full_size():
         assert g.check() == 0
 
 
-@pytest.mark.parametrize("V", [1 << 24, (1 << 24) + 1])
+@pytest.mark.parametrize("V", [1 << 25, (1 << 25) + 1])
 def test_pagerank_largest_bucketed_graph(V):
-    """2^24 vertices is the largest graph the bucketed PageRank pass takes (4096
-    buckets of 4096 heads: the bucket tables of the count and placement kernels at
+    """2^25 vertices is the largest graph the bucketed PageRank pass takes (4096
+    buckets of 8192 heads: the bucket tables of the count and placement kernels at
     their largest); one vertex more and the library takes the push pass.  Both give
     the ranks of a handle forced onto the push pass, bit for bit, on an R-MAT
-    scale-24 stream of 2^22 samples held on the device."""
+    scale-25 stream of 2^22 samples held on the device."""
     gp.build()
-    st = W.rmat_stream_device(24, 1 << 22, seed=5)
+    st = W.rmat_stream_device(25, 1 << 22, seed=5)
     a, b = gp.Graph(V, leaf_size=64), gp.Graph(V, leaf_size=64, push_pagerank=True)
     for g in (a, b):
         g.update(st)
@@ -118,9 +118,9 @@ def test_pagerank_largest_bucketed_graph(V):
 @pytest.mark.parametrize("scale", [21, 22])
 def test_large_graph_analytics_match_oracle(scale):
     """Graphs past 2^20 vertices take other branches of the analytics: at 2^21
-    vertices (512 head buckets) the bucketed PageRank runs one 1024-thread block per
-    bucket; past 2^21 (1024 buckets at scale 22) the placement writes every edge
-    straight to its bucket.  R-MAT with 2^(scale+1) distinct edges: layout slot for
+    vertices (256 head buckets of 8192) the bucketed PageRank runs clusters of two
+    blocks per bucket; at 2^22 (512 buckets) one block per bucket, and the
+    placement writes every edge straight to its bucket.  R-MAT with 2^(scale+1) distinct edges: layout slot for
     slot, BFS from two sources and CC exactly, PageRank-20 (bucketed and push
     passes) within 1e-5 of the oracle's FP64 ranks, and the two passes bit for bit
     equal."""
