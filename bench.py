@@ -29,7 +29,8 @@ import time
 import numpy as np
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
-# more hardware work queues: the batched many-graph update forks onto one stream per graph
+# more hardware work queues: queries run on their own streams, and the batches of the
+# many-graph update that may resize their array run on one side stream each
 os.environ.setdefault("CUDA_DEVICE_MAX_CONNECTIONS", "32")
 sys.path.insert(0, ROOT)
 
@@ -575,12 +576,13 @@ def learned_study(a):
 def many_study(a):
     """64 independent R-MAT graphs, window sizes log-uniform in [2^10, 2^22]
     edges, per-step batches log-uniform in [64, 2^18] updates (half inserts, half
-    deletes).  Per step: all 64 batches through gpma_update_many (forked onto side
-    streams, each replaying its graph) against the same batches applied one
-    graph after another on one stream, at leaf size 64 and at the leaf size the
-    autotuner picks per graph.  Batches are resident on the device before timing;
-    device time with CUDA events on the calling stream; the batched and the
-    sequential arrays are compared slot for slot at the end."""
+    deletes).  Per step: all 64 batches through gpma_update_many (one CUDA graph
+    whose every stage is one launch over all graphs' work) against the same
+    batches applied one graph after another on one stream, at leaf size 64 and at
+    the leaf size and warps per leaf-pass block the autotuner picks per graph.
+    Batches are resident on the device before timing; device time with CUDA events
+    on the calling stream; the batched and the sequential arrays are compared slot
+    for slot at the end."""
     import torch
     import paper_1709_05061_gb300 as gp
     from paper_1709_05061_gb300 import tune
@@ -597,20 +599,20 @@ def many_study(a):
     batches = [[(dev(i), dev(d)) for i, d in wl.slide()] for _ in range(warm + timed)]
     # autotune on the first step's batches, on copies of the initial graphs
     t0 = time.perf_counter()
-    tuned, tables = [], []
+    tuned, warps = [], []
     for i in range(n):
-        L, tab = tune.autotune_leaf_size(wl.n_vertices(i), init[i], batches[0][i][0], batches[0][i][1], reps=3)
+        L, w, _, _ = tune.autotune(wl.n_vertices(i), init[i], batches[0][i][0], batches[0][i][1], reps=3)
         tuned.append(L)
-        tables.append(tab)
+        warps.append(w)
     tune_s = time.perf_counter() - t0
     s = torch.cuda.current_stream()
     flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.int32, device="cuda")
     res = {}
     layouts = {}
     clk = ClockSampler(torch.cuda.current_device()).__enter__()
-    for label, sizes in (("L64", [64] * n), ("tuned", tuned)):
+    for label, sizes, wpb in (("L64", [64] * n, [0] * n), ("tuned", tuned, warps)):
         for mode in ("sequential", "batched"):
-            gs = [gp.Graph(wl.n_vertices(i), leaf_size=sizes[i]) for i in range(n)]
+            gs = [gp.Graph(wl.n_vertices(i), leaf_size=sizes[i], leaf_warps=wpb[i]) for i in range(n)]
             gp.Graph.update_many(gs, init, [None] * n)
             ts = []
             for k, b in enumerate(batches):
@@ -642,6 +644,7 @@ def many_study(a):
                        f"(total {int(wl.edges.sum())}), batches log-uniform in [64, 2^18] "
                        f"(total {int(wl.batch.sum())} updates per step), size seed 11, graph seeds 1000+g")
     res["tuned_leaf_sizes"] = {str(L): tuned.count(L) for L in sorted(set(tuned))}
+    res["tuned_leaf_warps"] = {str(w): warps.count(w) for w in sorted(set(warps))}
     res["autotune_seconds"] = tune_s
     res["speedup_batched_vs_sequential_L64"] = res["L64_sequential"]["p50_ms"] / res["L64_batched"]["p50_ms"]
     res["speedup_tuned_batched_vs_L64_sequential"] = res["L64_sequential"]["p50_ms"] / res["tuned_batched"]["p50_ms"]

@@ -60,7 +60,7 @@ typedef struct gpma *gpma_t;
                                 (Sec. 6.1), slots become EMPTY in place */
 #define GPMA_PUSH_PAGERANK 8u /* PageRank sums by one push pass over the slots per iteration
                                 (a reduction per edge into the L2).  Default, for graphs
-                                of at most 2^24 vertices: the edges are bucketed by head
+                                of at most 2^25 vertices: the edges are bucketed by head
                                 once per call and each iteration sums every bucket in
                                 shared memory.  Both give the same ranks, bit for bit */
 
@@ -76,6 +76,12 @@ typedef struct {
   uint32_t tau0_pct, tauh_pct, rho0_pct, rhoh_pct;
   uint32_t flags;     /* GPMA_RAW_KEYS | GPMA_PLAIN_SEARCH | GPMA_DUAL_DELETE |
                          GPMA_PUSH_PAGERANK, or 0 */
+  uint32_t leaf_warps; /* warps per block of the level-0 pass that gives one warp to
+                          each touched leaf (the pass for leaves other than 64 slots and
+                          for the runs the 64-slot pass leaves over): 1, 2, 4 or 8, fewer
+                          when a leaf's shared memory does not fit; 0 = the largest
+                          count that fits 96 KB of shared memory, at most 8 (App. A: the
+                          threads given to one segment are a tuning choice) */
 } gpma_params;
 
 /* Optional device allocator.  alloc returns NULL on failure; both receive the
@@ -137,15 +143,22 @@ int gpma_destroy(gpma_t h);
 int gpma_update_batch(gpma_t h, const uint64_t *d_ins, uint64_t n_ins, const uint64_t *d_del,
                       uint64_t n_del, void *stream, gpma_stats *stats);
 
-/* Apply one batch to each of `count` distinct handles (the batched form of
- * gpma_update_batch for many independent graphs).  d_ins[i][n_ins[i]] and
+/* Apply one batch to each of `count` distinct handles: the update of Sec. 5.2
+ * applied to many independent graphs at once.  d_ins[i][n_ins[i]] and
  * d_del[i][n_del[i]] go to handles[i] with exactly the semantics of
  * gpma_update_batch; each handle ends as if its batch had been applied alone.
- * The batches are forked from `stream` onto side streams (each replaying its
- * handle's CUDA graph) and joined back, so the GPU overlaps the graphs' kernels;
- * work enqueued on `stream` afterwards sees every batch applied.  Returns the
- * first host-detected error; device-detected GPMA_EINVAL is reported per handle by
- * gpma_status().  The handles must not be in use on other streams meanwhile. */
+ * Batches that cannot overflow their root run together: every stage of the front
+ * end (validation, radix passes, unique/cancel + leaf search, run heads) and of the
+ * level-0 pass is one kernel launch over the work of all those handles, each block
+ * finding its handle in a table uploaded by the call; a handle whose inserts did not
+ * all fit their leaves runs its merge levels in its own branch of the same CUDA
+ * graph, taken only then (a conditional node).  The graph is captured once per set
+ * of handles and sizes and replayed by later calls.  The other batches (a possible
+ * root resize, dual deletion) take gpma_update_batch's path on side streams forked
+ * from `stream`.  Work enqueued on `stream` afterwards sees every batch applied.
+ * Returns the first host-detected error; device-detected GPMA_EINVAL is reported per
+ * handle by gpma_status().  The handles must not be in use on other streams
+ * meanwhile; calls from several host threads are serialised. */
 int gpma_update_many(gpma_t const *handles, const uint64_t *const *d_ins, const uint64_t *n_ins,
                      const uint64_t *const *d_del, const uint64_t *n_del, uint32_t count, void *stream);
 

@@ -36,7 +36,8 @@ class GpmaError(RuntimeError):
 
 class gpma_params(C.Structure):
     _fields_ = [("leaf_size", C.c_uint32), ("tau0_pct", C.c_uint32), ("tauh_pct", C.c_uint32),
-                ("rho0_pct", C.c_uint32), ("rhoh_pct", C.c_uint32), ("flags", C.c_uint32)]
+                ("rho0_pct", C.c_uint32), ("rhoh_pct", C.c_uint32), ("flags", C.c_uint32),
+                ("leaf_warps", C.c_uint32)]
 
 
 class gpma_stats(C.Structure):
@@ -201,10 +202,11 @@ def _check(rc: int, where: str):
 # ---- the C entry points, one to one --------------------------------------------------------
 def gpma_create(n_vertices: int, leaf_size: int = 64, tau0: int = 92, tauh: int = 80, rho0: int = 8,
                 rhoh: int = 40, raw_keys: bool = False, plain_search: bool = False, dual: bool = False,
-                push_pagerank: bool = False, stream=None, allocator: "Allocator | None" = None) -> int:
+                push_pagerank: bool = False, leaf_warps: int = 0, stream=None,
+                allocator: "Allocator | None" = None) -> int:
     flags = ((GPMA_RAW_KEYS if raw_keys else 0) | (GPMA_PLAIN_SEARCH if plain_search else 0) |
              (GPMA_DUAL_DELETE if dual else 0) | (GPMA_PUSH_PAGERANK if push_pagerank else 0))
-    p = gpma_params(leaf_size, tau0, tauh, rho0, rhoh, flags)
+    p = gpma_params(leaf_size, tau0, tauh, rho0, rhoh, flags, leaf_warps)
     h = C.c_void_p()
     a = C.byref(allocator.struct) if allocator is not None else None
     _check(lib().gpma_create(n_vertices, C.byref(p), a, _stream(stream), C.byref(h)), "gpma_create")
@@ -225,7 +227,7 @@ def gpma_update_batch(h: int, ins, dels, stream=None, stats: bool = False):
 
 
 def gpma_update_many(handles, ins_list, del_list, stream=None):
-    """One batch per handle, overlapped on the GPU (see include/gpma.h)."""
+    """One batch per handle; the batches run as one launch per stage (see include/gpma.h)."""
     n = len(handles)
     ins_list = [_keys(x) for x in ins_list]
     del_list = [_keys(x) for x in del_list]
@@ -363,20 +365,22 @@ class Graph:
     Flags (include/gpma.h): ``raw_keys`` (opaque keys, no guards or queries),
     ``plain_search`` (binary leaf search only), ``dual`` (deletion as the dual of
     insertion), ``push_pagerank`` (PageRank by the push pass instead of the bucketed
-    pass; same ranks).  Extra keywords ``tau0``, ``tauh``, ``rho0``, ``rhoh`` set the
-    density bounds in whole percent.  ``allocator`` (an ``Allocator``, e.g.
-    ``torch_allocator()``) supplies the library's device memory; default
-    cudaMallocAsync."""
+    pass; same ranks).  ``leaf_warps`` (1, 2, 4, 8; 0 = the library's choice) sets the
+    warps per block of the one-warp-per-leaf level-0 pass.  Extra keywords ``tau0``,
+    ``tauh``, ``rho0``, ``rhoh`` set the density bounds in whole percent.  ``allocator``
+    (an ``Allocator``, e.g. ``torch_allocator()``) supplies the library's device
+    memory; default cudaMallocAsync."""
 
     def __init__(self, n_vertices: int, leaf_size: int = 64, raw_keys: bool = False, plain_search: bool = False,
-                 dual: bool = False, push_pagerank: bool = False, stream=None, allocator: Allocator | None = None,
-                 **dens):
+                 dual: bool = False, push_pagerank: bool = False, leaf_warps: int = 0, stream=None,
+                 allocator: Allocator | None = None, **dens):
         self.n_vertices = 0 if raw_keys else int(n_vertices)
         self.raw = raw_keys
         self.allocator = allocator  # the callbacks must outlive the handle
         self.h = None
         self.h = gpma_create(n_vertices, leaf_size=leaf_size, raw_keys=raw_keys, plain_search=plain_search,
-                             dual=dual, push_pagerank=push_pagerank, stream=stream, allocator=allocator, **dens)
+                             dual=dual, push_pagerank=push_pagerank, leaf_warps=leaf_warps, stream=stream,
+                             allocator=allocator, **dens)
 
     def close(self):
         if getattr(self, "h", None):
@@ -394,7 +398,7 @@ class Graph:
 
     @staticmethod
     def update_many(graphs, ins_list, del_list, stream=None):
-        """Apply ins_list[i] / del_list[i] to graphs[i], all batches overlapped."""
+        """Apply ins_list[i] / del_list[i] to graphs[i], all batches in one batched call."""
         gpma_update_many([g.h for g in graphs], ins_list, del_list, stream=stream)
 
     def status(self, stream=None):

@@ -236,6 +236,9 @@ struct gpma {
   Ctl *h_mirror;
   cudaEvent_t ev_mirror;
   bool mirror_pending;
+  uint32_t leaf_warps;  // warps per block of the general level-0 pass (0: by shared memory)
+  uint64_t uid;         // unique per handle created in the process (keys of batched graphs)
+  uint64_t spare_epochs;  // the alloc_epoch steps that only allocated a spare (batched graphs ignore them)
 };
 
 namespace {
@@ -296,6 +299,7 @@ void make_geo(gpma *h, uint32_t hh, Geo *g) {
   level_bounds(h->L, hh, h->tau0, h->tauh, g->maxc);
   level_min_bounds(h->L, hh, h->rho0, h->rhoh, g->minc);
   g->dual = h->dual;
+  g->leaf_warps = h->leaf_warps;
 }
 
 bool alloc_arrays(gpma *h, Geo *g, cudaStream_t s) {
@@ -635,6 +639,7 @@ int ensure_spare(gpma *h, cudaStream_t s) {
   }
   h->has_spare = true;
   h->alloc_epoch++;
+  h->spare_epochs++;
   return GPMA_OK;
 }
 
@@ -658,21 +663,8 @@ int settle(gpma *h, cudaStream_t s) {
   return cuda_ok(h);
 }
 
-int update(gpma *h, const uint64_t *ins, uint64_t n_ins, const uint64_t *del, uint64_t n_del, cudaStream_t s,
-           gpma_stats *stats, bool allow_guards) {
-  if (h->poisoned) return h->poisoned;
-  if (stats) memset(stats, 0, sizeof(*stats));
-  const uint64_t n = n_ins + n_del;
-  if (n >= (1ull << 30) || (n_ins && !ins) || (n_del && !del)) return GPMA_EINVAL;
-  if (n == 0) return GPMA_OK;
-  int rc = settle(h, s);
-  if (rc) return rc;
-  rc = ensure_work(h, n, s);
-  if (rc) return rc;
-  if ((rc = ensure_merge_scratch(h, s))) return rc;
-  const uint32_t h_old = h->geo.h;
-  const uint64_t C_old = h->geo.C;
-
+// Front-end arguments of a batch: sizes and the compressed key's bits and passes
+PrepArgs make_prep(const gpma *h, uint64_t n_ins, uint64_t n_del, bool allow_guards) {
   PrepArgs pa;
   memset(&pa, 0, sizeof(pa));
   pa.n_ins = (uint32_t)n_ins;
@@ -692,6 +684,25 @@ int update(gpma *h, const uint64_t *ins, uint64_t n_ins, const uint64_t *del, ui
   pa.npass = (bits + 7) / 8;
   pa.dbits = (bits + pa.npass - 1) / pa.npass;
   pa.sbits = bits;
+  return pa;
+}
+
+int update(gpma *h, const uint64_t *ins, uint64_t n_ins, const uint64_t *del, uint64_t n_del, cudaStream_t s,
+           gpma_stats *stats, bool allow_guards) {
+  if (h->poisoned) return h->poisoned;
+  if (stats) memset(stats, 0, sizeof(*stats));
+  const uint64_t n = n_ins + n_del;
+  if (n >= (1ull << 30) || (n_ins && !ins) || (n_del && !del)) return GPMA_EINVAL;
+  if (n == 0) return GPMA_OK;
+  int rc = settle(h, s);
+  if (rc) return rc;
+  rc = ensure_work(h, n, s);
+  if (rc) return rc;
+  if ((rc = ensure_merge_scratch(h, s))) return rc;
+  const uint32_t h_old = h->geo.h;
+  const uint64_t C_old = h->geo.C;
+
+  const PrepArgs pa = make_prep(h, n_ins, n_del, allow_guards);
 
   FrontArgs f;
   f.prep = pa;
@@ -934,6 +945,344 @@ int pr_run(gpma *h, uint32_t iters, float damping, float *d_rank, bool own_deg, 
   return cuda_ok(h);
 }
 
+// ---- batched update of many handles (gpma_update_many) -----------------------------------------
+__global__ void k_m_gate(const ManyDesc *d, const cudaGraphConditionalHandle *cond) {
+  const uint32_t k = threadIdx.x;
+  if (k >= d->count) return;
+  const Ctl *ctl = d->item[k].ctl;
+  cudaGraphSetConditional(cond[k], (d->item[k].active && ctl->err == 0 && ctl->nesc > 0) ? 1u : 0u);
+}
+
+__global__ void k_m_finish(const ManyDesc *d) {
+  const uint32_t k = threadIdx.x;
+  if (k < d->count && d->item[k].active) d->item[k].ctl->sticky |= d->item[k].ctl->err;
+}
+
+// Process-wide state of the batched update: the plan table on the device (read by
+// every batched kernel), pinned staging copies of it, side streams, and captured
+// graphs keyed by the handles they serve.
+struct ManyCtx {
+  static constexpr int kStage = 4, kGraphs = 4;
+  std::mutex mu;
+  ManyDesc *d_desc = nullptr;
+  ManyDesc *h_desc[kStage] = {};
+  cudaEvent_t up[kStage] = {};
+  uint32_t next_stage = 0;
+  cudaEvent_t done = nullptr, fork = nullptr, cfork = nullptr;
+  std::vector<cudaStream_t> side, cside;  // lone batches; branches of a graph being captured
+  std::vector<cudaEvent_t> join, cjoin;
+  cudaStream_t cap = nullptr, cap2 = nullptr;
+  struct Graph {
+    std::vector<uint64_t> key;
+    cudaGraphExec_t exec = nullptr;
+    cudaGraphConditionalHandle *d_cond = nullptr;
+    uint64_t kernels = 0, used = 0;
+  } graphs[kGraphs];
+  uint64_t tick = 0;
+  bool graphs_on = true;
+
+  bool init() {
+    if (d_desc) return true;
+    const char *ng = getenv("GPMA_NO_GRAPHS");
+    graphs_on = !(ng && ng[0] == '1');
+    prepare_many_front();
+    prepare_many_leaf();
+    allow_big_smem();
+    if (cudaMalloc(&d_desc, sizeof(ManyDesc)) != cudaSuccess) return false;
+    for (int i = 0; i < kStage; i++)
+      if (cudaMallocHost(&h_desc[i], sizeof(ManyDesc)) != cudaSuccess ||
+          cudaEventCreateWithFlags(&up[i], cudaEventDisableTiming) != cudaSuccess)
+        return false;
+    return cudaEventCreateWithFlags(&done, cudaEventDisableTiming) == cudaSuccess &&
+           cudaEventCreateWithFlags(&fork, cudaEventDisableTiming) == cudaSuccess &&
+           cudaEventCreateWithFlags(&cfork, cudaEventDisableTiming) == cudaSuccess &&
+           cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking) == cudaSuccess &&
+           cudaStreamCreateWithFlags(&cap2, cudaStreamNonBlocking) == cudaSuccess;
+  }
+  static bool grow(std::vector<cudaStream_t> &ss, std::vector<cudaEvent_t> &es, uint32_t n) {
+    while (ss.size() < n) {
+      cudaStream_t t = nullptr;
+      cudaEvent_t e = nullptr;
+      if (cudaStreamCreateWithFlags(&t, cudaStreamNonBlocking) != cudaSuccess ||
+          cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess)
+        return false;
+      ss.push_back(t);
+      es.push_back(e);
+    }
+    return true;
+  }
+  bool ensure_streams(uint32_t n) { return init() && grow(side, join, n); }
+  bool ensure_branches(uint32_t n) { return init() && grow(cside, cjoin, n); }
+};
+
+ManyCtx &many_ctx() {
+  static ManyCtx *c = new ManyCtx;  // lives until the process exits
+  return *c;
+}
+
+// Blocks of one batched launch: a grid of G blocks (fixed when the graph is
+// captured) shared among the handles with work, each getting at least one block
+// and otherwise in proportion to its work, never more than cap[k].
+uint32_t add_plan(ManyDesc &D, ManyPlans &pl, uint32_t &nplans, uint32_t G, const std::vector<uint64_t> &work,
+                  const std::vector<uint32_t> &cap) {
+  const uint32_t id = nplans++;
+  ManyPlan &p = D.plan[id];
+  uint64_t tot = 0;
+  uint32_t nw = 0;
+  for (size_t k = 0; k < work.size(); k++)
+    if (work[k]) {
+      tot += work[k];
+      nw++;
+    }
+  p.n = 0;
+  uint32_t start = 0;
+  for (size_t k = 0; k < work.size(); k++) {
+    if (!work[k]) continue;
+    uint64_t b = 1 + (uint64_t)(G - nw) * work[k] / tot;
+    if (b > cap[k]) b = cap[k];
+    if (b < 1) b = 1;
+    p.item[p.n] = (uint32_t)k;
+    p.start[p.n] = start;
+    start += (uint32_t)b;
+    p.n++;
+  }
+  p.start[p.n] = start;
+  pl.total[id] = G;
+  return id;
+}
+
+uint32_t ceil_div(uint64_t a, uint64_t b) { return (uint32_t)((a + b - 1) / b); }
+
+// One handle's merge levels (the IF-node body of its branch): the same launches as
+// gpma_update_batch's escalation, grids sized for the handle's work capacity.
+void many_escalation(gpma *h, cudaStream_t t) {
+  const Geo &g = h->geo;
+  const uint32_t nb = h->cap;
+  launch_pending(g, h->ctl, h->w, nb, t);
+  launch_tree_rebuild(g, h->ctl, h->w, nb, t);
+  launch_esc_level(g, h->ctl, h->w, nb, false, t);
+  launch_esc_top(g, h->ctl, h->w, nb, t);
+  launch_segments(g, h->ctl, h->w, nb, t);
+  launch_segment_merge(g, g, h->ctl, h->w, h->scratch_cap, g.nleaves, h->scratch, h->vbuf, h->partials, false, t);
+  if (h->mhead) launch_train_model(g, h->mhead, h->mpieces, h->ctl, true, t);
+}
+
+bool capture_many(ManyCtx &mc, const std::vector<gpma *> &hs, const ManyPlans &pl, ManyCtx::Graph *ge) {
+  const uint32_t nb = (uint32_t)hs.size();
+  if (!mc.ensure_branches(nb)) return false;
+  cudaGraph_t graph = nullptr;
+  if (cudaGraphCreate(&graph, 0) != cudaSuccess) return false;
+  std::vector<cudaGraphConditionalHandle> cond(nb);
+  bool ok = true;
+  for (uint32_t k = 0; k < nb && ok; k++)
+    ok = cudaGraphConditionalHandleCreate(&cond[k], graph, 0, cudaGraphCondAssignDefault) == cudaSuccess;
+  if (ok && !ge->d_cond) ok = cudaMalloc(&ge->d_cond, sizeof(cudaGraphConditionalHandle) * kMaxMany) == cudaSuccess;
+  ok = ok && cudaMemcpy(ge->d_cond, cond.data(), sizeof(cudaGraphConditionalHandle) * nb, cudaMemcpyHostToDevice) ==
+                 cudaSuccess;
+  const uint64_t l0 = launch_count();
+  ok = ok && cudaStreamBeginCaptureToGraph(mc.cap, graph, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal) ==
+                 cudaSuccess;
+  if (!ok) {
+    cudaGetLastError();
+    cudaGraphDestroy(graph);
+    return false;
+  }
+  launch_many_front(mc.d_desc, pl, mc.cap);
+  launch_many_leaf(mc.d_desc, pl, mc.cap);
+  note_launch();
+  k_m_gate<<<1, nb, 0, mc.cap>>>(mc.d_desc, ge->d_cond);
+  // one branch per handle, its merge levels behind its own IF node
+  ok = cudaEventRecord(mc.cfork, mc.cap) == cudaSuccess;
+  for (uint32_t k = 0; k < nb && ok; k++) {
+    ok = cudaStreamWaitEvent(mc.cside[k], mc.cfork, 0) == cudaSuccess &&
+         capture_if(mc.cside[k], mc.cap2, cond[k], [&](cudaStream_t t) { many_escalation(hs[k], t); }) &&
+         cudaEventRecord(mc.cjoin[k], mc.cside[k]) == cudaSuccess &&
+         cudaStreamWaitEvent(mc.cap, mc.cjoin[k], 0) == cudaSuccess;
+  }
+  note_launch();
+  k_m_finish<<<1, nb, 0, mc.cap>>>(mc.d_desc);
+  cudaGraph_t done = nullptr;
+  const bool ended = cudaStreamEndCapture(mc.cap, &done) == cudaSuccess;
+  const uint64_t kernels = launch_count() - l0;
+  unnote_launches(kernels);
+  if (!ok || !ended) {
+    cudaGetLastError();
+    cudaGraphDestroy(graph);
+    return false;
+  }
+  const cudaError_t ie = cudaGraphInstantiate(&ge->exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (ie != cudaSuccess) {
+    cudaGetLastError();
+    ge->exec = nullptr;
+    return false;
+  }
+  ge->kernels = kernels;
+  return true;
+}
+
+// The handles `sel` of a call as one batched graph; act[k]: sel[k] is updated by this
+// call (the others keep their place in the graph, which is then reused as long as
+// the same handles come back, and are left alone by every kernel).
+int run_many(ManyCtx &mc, gpma_t const *handles, const uint64_t *const *d_ins, const uint64_t *n_ins,
+             const uint64_t *const *d_del, const uint64_t *n_del, const std::vector<uint32_t> &sel,
+             const std::vector<uint8_t> &act, cudaStream_t s) {
+  if (!mc.init()) return GPMA_EDEVICE;
+  const uint32_t nb = (uint32_t)sel.size();
+  std::vector<gpma *> hs(nb);
+  for (uint32_t k = 0; k < nb; k++) hs[k] = handles[sel[k]];
+  // level-0 merges move pivots only inside their leaves; retrain now and then all the same
+  for (uint32_t k = 0; k < nb; k++)
+    if (act[k] && hs[k]->mhead && ++hs[k]->since_train >= 64) train_model(hs[k], s);
+  // the staging copy this call fills (waits only when every copy is still in flight)
+  const uint32_t st = mc.next_stage;
+  mc.next_stage = (st + 1) % ManyCtx::kStage;
+  if (cudaEventSynchronize(mc.up[st]) != cudaSuccess) return GPMA_EDEVICE;
+  ManyDesc &D = *mc.h_desc[st];
+  D.count = nb;
+  std::vector<uint64_t> n(nb), wt(nb), wr(nb), w1(nb), w4(nb), w64(nb), wdeg(nb);
+  std::vector<uint32_t> ct(nb), cr(nb), c1(nb), c4(nb), c64(nb), cdeg(nb), one(nb, 1);
+  uint32_t maxpass = 0;
+  for (uint32_t k = 0; k < nb; k++) {
+    gpma *h = hs[k];
+    const uint32_t i = sel[k];
+    ManyItem &it = D.item[k];
+    it.active = act[k];
+    n[k] = act[k] ? n_ins[i] + n_del[i] : 0;
+    it.prep = make_prep(h, act[k] ? n_ins[i] : 0, act[k] ? n_del[i] : 0, false);
+    it.ins = d_ins ? d_ins[i] : nullptr;
+    it.del = d_del ? d_del[i] : nullptr;
+    it.bufA = h->bufA;
+    it.bufB = h->bufB;
+    it.hist = h->hist;
+    it.ctl = h->ctl;
+    it.mhead = h->mhead;
+    it.mpieces = h->mpieces;
+    it.small = small_front(n[k]) ? 1u : 0u;
+    it.T = front_tiles(n[k]);
+    it.wide = search_wide(n[k]) ? 1u : 0u;
+    it.T1 = search_tiles(n[k]);
+    it.P = 64;
+    while (it.P < n[k]) it.P <<= 1;
+    it.S = h->geo.nleaves < 2048 ? (uint32_t)h->geo.nleaves : 2048u;
+    it.per_warp = leaf_smem_bytes(h->L);
+    it.g = h->geo;
+    it.w = h->w;
+    if (it.prep.npass > maxpass) maxpass = it.prep.npass;
+    const uint32_t radix = 1u << it.prep.dbits;
+    wt[k] = it.small ? 0 : it.T;
+    ct[k] = it.T;
+    wr[k] = it.small ? 0 : (uint64_t)radix * it.T;
+    cr[k] = radix;
+    w1[k] = (!it.small && !it.wide) ? it.T1 : 0;
+    c1[k] = it.T1;
+    w4[k] = (!it.small && it.wide) ? it.T1 : 0;
+    c4[k] = it.T1;
+    w64[k] = h->L == 64 ? n[k] : 0;
+    c64[k] = ceil_div(n[k], 8);
+    wdeg[k] = h->raw ? 0 : n[k];
+    cdeg[k] = ceil_div(n[k], 256);
+  }
+  // plans: the grid of every launch depends only on the set of handles
+  ManyPlans pl;
+  memset(&pl, 0, sizeof(pl));
+  uint32_t np = 0;
+  pl.one = add_plan(D, pl, np, nb, std::vector<uint64_t>(nb, 1), one);  // every handle: kernels test `active`
+  pl.tiles = add_plan(D, pl, np, 1216 + nb, wt, ct);
+  pl.radix = add_plan(D, pl, np, 2432 + nb, wr, cr);
+  pl.search[0] = add_plan(D, pl, np, 2432 + nb, w1, c1);
+  pl.search[1] = add_plan(D, pl, np, 1216 + nb, w4, c4);
+  pl.leaf64 = add_plan(D, pl, np, 760 + nb, w64, c64);
+  pl.deg = add_plan(D, pl, np, 1216 + nb, wdeg, cdeg);
+  pl.maxpass = maxpass;
+  // the one-warp-per-leaf pass: one launch per block size (warps per block, 1..8);
+  // a block's warps use its own handle's shared-memory stride, and the launch
+  // reserves the group's largest
+  std::vector<uint64_t> key;
+  key.reserve(4 * nb + 2);
+  key.push_back(nb);
+  for (uint32_t k = 0; k < nb; k++) {
+    gpma *h = hs[k];
+    const uint32_t wpb = leaf_pass_warps(h->L, h->leaf_warps);
+    uint32_t gi = 0;
+    while (gi < pl.ngroups && pl.group[gi].wpb != wpb) gi++;
+    if (gi == pl.ngroups) {
+      pl.group[gi].wpb = wpb;
+      pl.group[gi].per_warp = 0;
+      pl.ngroups++;
+    }
+    if (leaf_smem_bytes(h->L) > pl.group[gi].per_warp) pl.group[gi].per_warp = leaf_smem_bytes(h->L);
+    key.push_back(h->uid);
+    key.push_back(h->alloc_epoch - h->spare_epochs);  // a batched graph never uses the spare array
+    key.push_back(((uint64_t)gi << 32) | ((uint64_t)(h->cap > kLongRun) << 16) | (h->mhead ? 1u : 0u));
+  }
+  for (uint32_t gi = 0; gi < pl.ngroups; gi++) {
+    ManyPlans::Group &gr = pl.group[gi];
+    std::vector<uint64_t> wrest(nb, 0), wla(nb, 0), wlb(nb, 0);
+    std::vector<uint32_t> crest(nb), cla(nb), clb(nb);
+    bool any_long = false;
+    for (uint32_t k = 0; k < nb; k++) {
+      gpma *h = hs[k];
+      if (leaf_pass_warps(h->L, h->leaf_warps) != gr.wpb) continue;
+      wrest[k] = n[k];
+      crest[k] = ceil_div(n[k], gr.wpb);
+      any_long |= h->cap > kLongRun;
+      if (n[k] > kLongRun) {
+        wla[k] = wlb[k] = n[k];
+        cla[k] = ceil_div(ceil_div(n[k], 32), gr.wpb);
+        clb[k] = ceil_div(n[k] / kLongRun + 1, gr.wpb);
+      }
+    }
+    gr.rest = add_plan(D, pl, np, 2432 + nb, wrest, crest);
+    gr.long_a = gr.long_b = ~0u;
+    if (any_long) {
+      gr.long_a = add_plan(D, pl, np, 2432 + nb, wla, cla);
+      gr.long_b = add_plan(D, pl, np, 2432 + nb, wlb, clb);
+    }
+  }
+  // upload after the previous batched call has finished reading the table
+  const size_t bytes = offsetof(ManyDesc, item) + sizeof(ManyItem) * nb;
+  if (cudaStreamWaitEvent(s, mc.done, 0) != cudaSuccess ||
+      cudaMemcpyAsync(mc.d_desc, &D, bytes, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+      cudaEventRecord(mc.up[st], s) != cudaSuccess)
+    return GPMA_EDEVICE;
+  if (mc.graphs_on) {
+    ManyCtx::Graph *ge = nullptr;
+    for (auto &g : mc.graphs)
+      if (g.exec && g.key == key) ge = &g;
+    if (!ge) {
+      ge = &mc.graphs[0];
+      for (auto &g : mc.graphs) {
+        if (!g.exec) {
+          ge = &g;
+          break;
+        }
+        if (g.used < ge->used) ge = &g;
+      }
+      if (ge->exec) cudaGraphExecDestroy(ge->exec);
+      ge->exec = nullptr;
+      if (!capture_many(mc, hs, pl, ge)) return GPMA_EDEVICE;
+      ge->key = key;
+    }
+    ge->used = ++mc.tick;
+    if (cudaGraphLaunch(ge->exec, s) != cudaSuccess) return GPMA_EDEVICE;
+    for (uint64_t k = 0; k < ge->kernels; k++) note_launch();
+  } else {
+    // direct launches (profilers see every kernel): every updated handle's merge
+    // levels run and return at once when nothing is pending
+    launch_many_front(mc.d_desc, pl, s);
+    launch_many_leaf(mc.d_desc, pl, s);
+    for (uint32_t k = 0; k < nb; k++)
+      if (act[k]) many_escalation(hs[k], s);
+    note_launch();
+    k_m_finish<<<1, nb, 0, s>>>(mc.d_desc);
+  }
+  if (cudaEventRecord(mc.done, s) != cudaSuccess) return GPMA_EDEVICE;
+  for (uint32_t k = 0; k < nb; k++)
+    if (act[k]) hs[k]->count_ub += n_ins[sel[k]];
+  return GPMA_OK;
+}
+
 }  // namespace
 
 namespace gpk {
@@ -982,6 +1331,8 @@ int gpma_create(uint32_t n_vertices, const gpma_params *params, const gpma_alloc
   if (!p.rhoh_pct) p.rhoh_pct = 40;
   const uint32_t L = p.leaf_size;
   if (L < 2 || L > 1024 || (L & (L - 1))) return GPMA_EINVAL;
+  if (p.leaf_warps != 0 && p.leaf_warps != 1 && p.leaf_warps != 2 && p.leaf_warps != 4 && p.leaf_warps != 8)
+    return GPMA_EINVAL;
   if (!(p.tauh_pct <= p.tau0_pct && p.tau0_pct <= 100 && p.rho0_pct <= p.rhoh_pct && p.rhoh_pct < p.tauh_pct))
     return GPMA_EINVAL;
   const bool raw = (p.flags & GPMA_RAW_KEYS) != 0;
@@ -1007,6 +1358,9 @@ int gpma_create(uint32_t n_vertices, const gpma_params *params, const gpma_alloc
   if (ng && ng[0] == '1') h->graphs->enabled = false;
   h->V = raw ? 0 : n_vertices;
   h->L = L;
+  h->leaf_warps = p.leaf_warps;
+  static std::atomic<uint64_t> next_uid{1};
+  h->uid = next_uid.fetch_add(1);
   h->logL = bits_for(L) - 1;
   h->raw = raw ? 1 : 0;
   h->dual = (p.flags & GPMA_DUAL_DELETE) ? 1 : 0;
@@ -1323,33 +1677,63 @@ int gpma_update_many(gpma_t const *handles, const uint64_t *const *d_ins, const 
     for (uint32_t j = 0; j < i; j++)
       if (handles[j] == handles[i]) return GPMA_EINVAL;  // one batch per handle
   }
-  // process-wide pool of side streams and events for the fork / join
-  static std::mutex mu;
-  static std::vector<cudaStream_t> side;
-  static std::vector<cudaEvent_t> ev;
-  std::lock_guard<std::mutex> lock(mu);
-  while (side.size() < count) {
-    cudaStream_t t = nullptr;
-    if (cudaStreamCreateWithFlags(&t, cudaStreamNonBlocking) != cudaSuccess) return GPMA_EDEVICE;
-    side.push_back(t);
-  }
-  while (ev.size() < (size_t)count + 1) {
-    cudaEvent_t e = nullptr;
-    if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) return GPMA_EDEVICE;
-    ev.push_back(e);
-  }
+  ManyCtx &mc = many_ctx();
+  std::lock_guard<std::mutex> lock(mc.mu);
   cudaStream_t s = (cudaStream_t)stream;
-  if (cudaEventRecord(ev[count], s) != cudaSuccess) return GPMA_EDEVICE;
   int first_err = GPMA_OK;
-  for (uint32_t i = 0; i < count; i++) {
-    cudaStreamWaitEvent(side[i], ev[count], 0);
-    const int rc = update(handles[i], d_ins ? d_ins[i] : nullptr, n_ins[i], d_del ? d_del[i] : nullptr, n_del[i],
-                          side[i], nullptr, false);
+  auto note_err = [&](int rc) {
     if (rc && !first_err) first_err = rc;
-    cudaEventRecord(ev[i], side[i]);
-    cudaStreamWaitEvent(s, ev[i], 0);
+  };
+  // batches that cannot overflow their root run batched; the others alone.  The
+  // batched graph holds the call's first kMaxMany handles whatever they do this time
+  const uint32_t ng = count < kMaxMany ? count : kMaxMany;
+  std::vector<uint32_t> graph_sel(ng), alone;
+  std::vector<uint8_t> act(ng, 0);
+  bool any = false;
+  for (uint32_t i = 0; i < ng; i++) graph_sel[i] = i;
+  for (uint32_t i = 0; i < count; i++) {
+    gpma *h = handles[i];
+    const uint64_t ni = n_ins[i], nd = n_del[i], n = ni + nd;
+    const uint64_t *ins = d_ins ? d_ins[i] : nullptr, *del = d_del ? d_del[i] : nullptr;
+    if (h->poisoned) {
+      note_err(h->poisoned);
+      continue;
+    }
+    if (n == 0) continue;
+    if (n >= (1ull << 30) || (ni && !ins) || (nd && !del)) {
+      note_err(GPMA_EINVAL);
+      continue;
+    }
+    int rc = settle(h, s);
+    if (!rc) rc = ensure_work(h, n, s);
+    if (!rc) rc = ensure_merge_scratch(h, s);
+    if (rc) {
+      note_err(rc);
+      continue;
+    }
+    const bool may_fail = h->count_ub + ni > h->geo.maxc[h->geo.h];
+    if (may_fail || h->dual || i >= ng) {
+      alone.push_back(i);
+    } else {
+      act[i] = 1;
+      any = true;
+    }
   }
-  if (cudaGetLastError() != cudaSuccess && !first_err) first_err = GPMA_EDEVICE;
+  // the lone batches: gpma_update_batch's path, forked onto side streams
+  if (!alone.empty()) {
+    if (!mc.ensure_streams((uint32_t)alone.size())) return GPMA_EDEVICE;
+    if (cudaEventRecord(mc.fork, s) != cudaSuccess) return GPMA_EDEVICE;
+    for (size_t k = 0; k < alone.size(); k++) {
+      const uint32_t i = alone[k];
+      cudaStreamWaitEvent(mc.side[k], mc.fork, 0);
+      note_err(update(handles[i], d_ins ? d_ins[i] : nullptr, n_ins[i], d_del ? d_del[i] : nullptr, n_del[i],
+                      mc.side[k], nullptr, false));
+      cudaEventRecord(mc.join[k], mc.side[k]);
+    }
+  }
+  if (any) note_err(run_many(mc, handles, d_ins, n_ins, d_del, n_del, graph_sel, act, s));
+  for (size_t k = 0; k < alone.size(); k++) cudaStreamWaitEvent(s, mc.join[k], 0);
+  if (cudaGetLastError() != cudaSuccess) note_err(GPMA_EDEVICE);
   return first_err;
 }
 

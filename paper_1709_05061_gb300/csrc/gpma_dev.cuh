@@ -36,6 +36,7 @@ struct Geo {
   uint64_t C, nleaves;
   uint32_t L, logL, h, V, raw;
   uint32_t dual;              // deletion as the dual of insertion: lower bounds kept
+  uint32_t leaf_warps;        // warps per block of the general level-0 pass (0: by shared memory)
   uint64_t tree_off[kMaxLv];  // offset of level i (1..h) inside tree/mark
   uint64_t maxc[kMaxLv];      // max_i: largest admissible count at level i
   uint64_t minc[kMaxLv];      // min_i: smallest admissible count at level i (dual mode)
@@ -91,6 +92,18 @@ __device__ __forceinline__ bool is_guard(uint64_t k) {
 }
 
 __device__ __forceinline__ uint32_t lane_id() { return threadIdx.x & 31u; }
+
+// Block index seen by a kernel body: the launch's own grid (one handle), or one
+// handle's share of a launch that serves many handles (blocks [0, n) of its own).
+struct GridIdx {
+  __device__ __forceinline__ uint32_t x() const { return blockIdx.x; }
+  __device__ __forceinline__ uint32_t n() const { return gridDim.x; }
+};
+struct SubIdx {
+  uint32_t bx, bn;
+  __device__ __forceinline__ uint32_t x() const { return bx; }
+  __device__ __forceinline__ uint32_t n() const { return bn; }
+};
 
 // add +1 / -1 to the out-degree of the source of every marked lane's key; lanes
 // of one source (rows are contiguous) combine into one atomic

@@ -171,6 +171,95 @@ int run_bfs(const Geo &g, uint32_t src, int32_t *depth, uint32_t *q0, uint32_t *
             uint32_t *counter, Ctl *ctl, cudaStream_t s);
 void launch_cc(const Geo &g, uint32_t *label, cudaStream_t s);
 
+// per-warp shared memory of the leaf kernels: three key buffers of L, a u16
+// index array of L+1 and a byte mask of L
+__host__ __device__ inline uint32_t leaf_smem_bytes(uint32_t L) {
+  return 24u * L + ((2u * (L + 1u) + 15u) & ~15u) + ((L + 15u) & ~15u);
+}
+
+// ---- many handles in one launch per stage (gpma_update_many) ------------------------------
+constexpr uint32_t kMaxMany = 128;  // handles of one batched launch
+constexpr uint32_t kMaxPlans = 32;  // batched launches with their own block ranges
+
+// One handle of a batched update: the arguments its own front end and level-0
+// pass take, and this call's sizes.
+struct ManyItem {
+  PrepArgs prep;
+  const uint64_t *ins, *del;
+  uint64_t *bufA, *bufB;  // radix ping-pong (the sorted words end in bufB after an odd pass count)
+  uint32_t *hist;
+  Ctl *ctl;
+  const ModelHead *mhead;
+  const Piece *mpieces;
+  uint32_t active;        // this call updates the handle here (else: no kernel touches it)
+  uint32_t small;         // the whole front end in one block (at most kSmallBatch keys)
+  uint32_t T, T1, wide;   // sort tiles, search blocks, four sorted words a search thread
+  uint32_t P, S;          // one-block front end: padded batch, sampled pivots
+  uint32_t per_warp;      // general level-0 pass: shared memory of a warp
+  Geo g;
+  Work w;
+};
+
+// Block ranges of one batched launch: item[k] runs on blocks [start[k], start[k+1]),
+// k < n (handles without blocks in the launch are left out).
+struct ManyPlan {
+  uint32_t n;
+  uint32_t item[kMaxMany];
+  uint32_t start[kMaxMany + 1];
+};
+
+struct ManyDesc {
+  uint32_t count;
+  ManyPlan plan[kMaxPlans];
+  ManyItem item[kMaxMany];  // last: a call uploads the first `count` only
+};
+
+// The handle and its own block index of this block of launch `plan` (false: no work)
+__device__ __forceinline__ bool many_block(const ManyDesc *d, uint32_t plan, const ManyItem **it, uint32_t *sub,
+                                           uint32_t *nblk) {
+  const ManyPlan &p = d->plan[plan];
+  const uint32_t b = blockIdx.x, n = p.n;
+  if (n == 0 || b >= p.start[n]) return false;
+  uint32_t lo = 0, hi = n;  // the last k with start[k] <= b
+  while (hi - lo > 1) {
+    const uint32_t mid = (lo + hi) >> 1;
+    if (p.start[mid] <= b) lo = mid;
+    else hi = mid;
+  }
+  *it = &d->item[p.item[lo]];
+  *sub = b - p.start[lo];
+  *nblk = p.start[lo + 1] - p.start[lo];
+  return true;
+}
+
+// Plans of a batched update, by stage; the general level-0 pass has one launch
+// per group of handles sharing its block shape (leaf size, warps per block).
+struct ManyPlans {
+  uint32_t one;        // one block a handle
+  uint32_t tiles;      // sort tiles at the handle's work capacity
+  uint32_t radix;      // digits of the handle's radix passes
+  uint32_t search[2];  // search blocks at one / four sorted words a thread
+  uint32_t leaf64;     // 64-slot level-0 pass
+  uint32_t deg;        // out-degree changes
+  uint32_t ngroups;
+  struct Group {  // handles whose one-warp-per-leaf pass has wpb warps per block
+    uint32_t rest, long_a, long_b;  // plans (long_a == ~0u: no handle of the group has long runs)
+    uint32_t wpb, per_warp;         // per_warp: the largest shared memory a warp of the group takes
+  } group[8];
+  uint32_t maxpass;
+  uint32_t total[kMaxPlans];  // blocks of each plan's launch
+};
+// k_batch.cu / k_update.cu: the batched stages (kernels read d, which the call uploaded);
+// prepare_* set the kernels' shared-memory limits (once, outside any stream capture)
+void prepare_many_front();
+void prepare_many_leaf();
+void launch_many_front(const ManyDesc *d, const ManyPlans &pl, cudaStream_t s);
+void launch_many_leaf(const ManyDesc *d, const ManyPlans &pl, cudaStream_t s);
+uint32_t search_tiles(uint64_t nb);
+uint32_t front_tiles(uint64_t nb);
+bool search_wide(uint64_t n);
+uint32_t leaf_pass_warps(uint32_t L, uint32_t want);  // warps per block of the general level-0 pass
+
 // read-only view of a handle (defined beside the handle in gpma_api.cu)
 struct HandleView {
   const Geo *geo;

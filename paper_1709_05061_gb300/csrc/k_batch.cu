@@ -59,7 +59,8 @@ __device__ __forceinline__ uint64_t expand(uint64_t w, const PrepArgs &a) {
   return (src << 32) | dst;
 }
 
-__global__ void k_init_batch(Ctl *ctl, uint32_t *hist, uint32_t nhist, uint32_t n) {
+template <class Blk>
+__device__ __forceinline__ void init_batch_body(const Blk &bk, Ctl *ctl, uint32_t *hist, uint32_t nhist, uint32_t n) {
   for (uint32_t i = threadIdx.x; i < nhist; i += blockDim.x) hist[i] = 0;
   if (threadIdx.x == 0) {
     ctl->err = 0;
@@ -81,50 +82,55 @@ __global__ void k_init_batch(Ctl *ctl, uint32_t *hist, uint32_t nhist, uint32_t 
   }
 }
 
-// One sort tile (blockDim * ITEMS keys) per block: validation, compression, the
-// tile's first-pass digit counts (column-major: H0[d * T + tile]) and the batch's
-// digit counts of every pass (hist[p * 256 + d]).
-template <int ITEMS>
-__global__ void __launch_bounds__(kSortThreads) k_prep(PrepArgs a, const uint64_t *__restrict__ ins,
-                                                       const uint64_t *__restrict__ del, uint64_t *__restrict__ out,
-                                                       uint32_t *__restrict__ hist, uint32_t *__restrict__ H0,
-                                                       uint32_t T, Ctl *ctl) {
+__global__ void k_init_batch(Ctl *ctl, uint32_t *hist, uint32_t nhist, uint32_t n) { init_batch_body(GridIdx{}, ctl, hist, nhist, n); }
+
+// Sort tiles (blockDim * ITEMS keys) tile, tile + nblocks, ... of a block:
+// validation, compression, each tile's first-pass digit counts (column-major:
+// H0[d * T + tile]) and the batch's digit counts of every pass (hist[p * 256 + d]).
+template <int ITEMS, class Blk>
+__device__ __forceinline__ void prep_body(const Blk &bk, const PrepArgs &a, const uint64_t *__restrict__ ins,
+                                          const uint64_t *__restrict__ del, uint64_t *__restrict__ out,
+                                          uint32_t *__restrict__ hist, uint32_t *__restrict__ H0, uint32_t T,
+                                          Ctl *ctl) {
   __shared__ uint32_t sh[8 * 256];
-  for (uint32_t i = threadIdx.x; i < a.npass * 256u; i += blockDim.x) sh[i] = 0;
-  __syncthreads();
   const uint32_t n = a.n_ins + a.n_del;
   const uint32_t mask = (1u << a.dbits) - 1u;
-  bool bad = false;
+  for (uint32_t tile = bk.x(); tile < T; tile += bk.n()) {
+    for (uint32_t i = threadIdx.x; i < a.npass * 256u; i += blockDim.x) sh[i] = 0;
+    __syncthreads();
+    bool bad = false;
 #pragma unroll
-  for (int r = 0; r < ITEMS; r++) {
-    const uint32_t i = blockIdx.x * (kSortThreads * ITEMS) + r * kSortThreads + threadIdx.x;
-    if (i >= n) break;
-    const uint32_t tag = i >= a.n_ins;
-    const uint64_t key = tag ? del[i - a.n_ins] : ins[i];
-    bool ok;
-    if (a.raw) {
-      ok = (key >> 63) == 0;
-    } else {
-      const uint64_t src = key >> 32, dst = key & 0xFFFFFFFFull;
-      ok = src < a.V && (dst < a.V || (a.allow_guards && !tag && dst == 0xFFFFFFFFull));
+    for (int r = 0; r < ITEMS; r++) {
+      const uint32_t i = tile * (kSortThreads * ITEMS) + r * kSortThreads + threadIdx.x;
+      if (i >= n) break;
+      const uint32_t tag = i >= a.n_ins;
+      const uint64_t key = tag ? del[i - a.n_ins] : ins[i];
+      bool ok;
+      if (a.raw) {
+        ok = (key >> 63) == 0;
+      } else {
+        const uint64_t src = key >> 32, dst = key & 0xFFFFFFFFull;
+        ok = src < a.V && (dst < a.V || (a.allow_guards && !tag && dst == 0xFFFFFFFFull));
+      }
+      bad |= !ok;
+      const uint64_t w = ok ? compress(key, tag, a) : 0ull;
+      out[i] = w;
+      const uint64_t kw = w & ~kTagBit;
+      for (uint32_t p = 0; p < a.npass; p++)
+        atomicAdd(&sh[p * 256 + (uint32_t)((kw >> (p * a.dbits)) & mask)], 1u);
     }
-    bad |= !ok;
-    const uint64_t w = ok ? compress(key, tag, a) : 0ull;
-    out[i] = w;
-    const uint64_t kw = w & ~kTagBit;
-    for (uint32_t p = 0; p < a.npass; p++)
-      atomicAdd(&sh[p * 256 + (uint32_t)((kw >> (p * a.dbits)) & mask)], 1u);
+    if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(&ctl->err, kErrKey);
+    for (uint32_t d = threadIdx.x; d <= mask; d += blockDim.x) H0[(uint64_t)d * T + tile] = sh[d];
+    for (uint32_t i = threadIdx.x; i < a.npass * 256u; i += blockDim.x)
+      if (sh[i]) atomicAdd(&hist[i], sh[i]);
+    __syncthreads();
   }
-  if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(&ctl->err, kErrKey);
-  for (uint32_t d = threadIdx.x; d <= mask; d += blockDim.x) H0[(uint64_t)d * T + blockIdx.x] = sh[d];
-  for (uint32_t i = threadIdx.x; i < a.npass * 256u; i += blockDim.x)
-    if (sh[i]) atomicAdd(&hist[i], sh[i]);
   // the last block to finish turns the batch's digit counts of every pass into
   // digit offsets: hist[8 * 256 + p * 256 + d] = keys of pass p with a smaller digit
   __shared__ uint32_t s_last;
   __threadfence();
   __syncthreads();
-  if (threadIdx.x == 0) s_last = atomicAdd(&ctl->ticket[kPrepDone], 1u) == gridDim.x - 1;
+  if (threadIdx.x == 0) s_last = atomicAdd(&ctl->ticket[kPrepDone], 1u) == bk.n() - 1;
   __syncthreads();
   if (!s_last) return;
   __threadfence();
@@ -140,48 +146,61 @@ __global__ void __launch_bounds__(kSortThreads) k_prep(PrepArgs a, const uint64_
   }
 }
 
-// Pass `pass`, digit blockIdx.x: H[d * T + t] (keys of tile t with digit d)
-// becomes the position of the tile's first such key: the digit's global offset
-// (keys of smaller digits, from the batch histogram) plus the same digit's keys
-// in earlier tiles.  Also zeroes the next pass's counts Hn (may be nullptr).
-__global__ void __launch_bounds__(256) k_rcolscan(uint32_t *__restrict__ H, uint32_t *__restrict__ Hn, uint32_t T,
-                                                  const uint32_t *__restrict__ dbase, const Ctl *ctl) {
+template <int ITEMS>
+__global__ void __launch_bounds__(kSortThreads) k_prep(PrepArgs a, const uint64_t *__restrict__ ins,
+                                                       const uint64_t *__restrict__ del, uint64_t *__restrict__ out,
+                                                       uint32_t *__restrict__ hist, uint32_t *__restrict__ H0,
+                                                       uint32_t T, Ctl *ctl) { prep_body<ITEMS>(GridIdx{}, a, ins, del, out, hist, H0, T, ctl); }
+
+// Pass `pass`, digits d = block, block + nblocks, ... < radix: H[d * T + t] (keys
+// of tile t with digit d) becomes the position of the tile's first such key: the
+// digit's global offset (keys of smaller digits, from the batch histogram) plus the
+// same digit's keys in earlier tiles.  Also zeroes the next pass's counts Hn (may be
+// nullptr).
+template <class Blk>
+__device__ __forceinline__ void rcolscan_body(const Blk &bk, uint32_t *__restrict__ H, uint32_t *__restrict__ Hn,
+                                              uint32_t T, const uint32_t *__restrict__ dbase, uint32_t radix,
+                                              const Ctl *ctl) {
   __shared__ uint32_t wsum[33];
   if (ctl->err) return;
-  const uint32_t d = blockIdx.x;
-  uint32_t carry = dbase[d];
-  uint32_t *col = H + (uint64_t)d * T;
-  constexpr uint32_t kPer = 8;
-  for (uint32_t c = 0; c < T; c += 256 * kPer) {
-    const uint32_t t0 = c + threadIdx.x * kPer;
-    uint32_t v[kPer], loc = 0;
+  for (uint32_t d = bk.x(); d < radix; d += bk.n()) {
+    uint32_t carry = dbase[d];
+    uint32_t *col = H + (uint64_t)d * T;
+    constexpr uint32_t kPer = 8;
+    for (uint32_t c = 0; c < T; c += 256 * kPer) {
+      const uint32_t t0 = c + threadIdx.x * kPer;
+      uint32_t v[kPer], loc = 0;
 #pragma unroll
-    for (uint32_t q = 0; q < kPer; q++) {
-      v[q] = t0 + q < T ? col[t0 + q] : 0u;
-      loc += v[q];
-    }
-    uint32_t total;
-    uint32_t run = carry + block_excl_scan(loc, wsum, &total);
+      for (uint32_t q = 0; q < kPer; q++) {
+        v[q] = t0 + q < T ? col[t0 + q] : 0u;
+        loc += v[q];
+      }
+      uint32_t total;
+      uint32_t run = carry + block_excl_scan(loc, wsum, &total);
 #pragma unroll
-    for (uint32_t q = 0; q < kPer; q++) {
-      if (t0 + q < T) col[t0 + q] = run;
-      run += v[q];
+      for (uint32_t q = 0; q < kPer; q++) {
+        if (t0 + q < T) col[t0 + q] = run;
+        run += v[q];
+      }
+      carry += total;
     }
-    carry += total;
+    if (Hn)
+      for (uint32_t t = threadIdx.x; t < T; t += 256) Hn[(uint64_t)d * T + t] = 0;
+    __syncthreads();
   }
-  if (Hn)
-    for (uint32_t t = threadIdx.x; t < T; t += 256) Hn[(uint64_t)d * T + t] = 0;
+}
+
+__global__ void __launch_bounds__(256) k_rcolscan(uint32_t *__restrict__ H, uint32_t *__restrict__ Hn, uint32_t T,
+                                                  const uint32_t *__restrict__ dbase, const Ctl *ctl) {
+  rcolscan_body(GridIdx{}, H, Hn, T, dbase, gridDim.x, ctl);
 }
 
 // One stable LSD pass over tile blockIdx.x (ITEMS rounds x 256 keys; warp w owns
 // the contiguous sub-tile [w*32*ITEMS, (w+1)*32*ITEMS), so ranks inside a warp
 // need no block barrier).  O[d * T + t]: where the tile's keys of digit d start.
 // With Hn, every key also counts its next-pass digit in its destination tile.
-template <int ITEMS>
-__global__ void __launch_bounds__(kSortThreads) k_rscatter(const uint64_t *__restrict__ src,
-                                                           uint64_t *__restrict__ dst, const uint32_t *__restrict__ O,
-                                                           uint32_t *__restrict__ Hn, uint32_t T, uint32_t shift,
-                                                           uint32_t nshift, uint32_t dbits, const Ctl *ctl) {
+template <int ITEMS, class Blk>
+__device__ __forceinline__ void rscatter_body(const Blk &bk, const uint64_t *__restrict__ src, uint64_t *__restrict__ dst, const uint32_t *__restrict__ O, uint32_t *__restrict__ Hn, uint32_t T, uint32_t shift, uint32_t nshift, uint32_t dbits, const Ctl *ctl) {
   __shared__ uint32_t wcnt[kSortThreads / 32][256];
   __shared__ uint32_t gbase[256];
   __shared__ uint32_t ltile[256];  // digit totals of the tile, then their exclusive prefix
@@ -190,92 +209,100 @@ __global__ void __launch_bounds__(kSortThreads) k_rscatter(const uint64_t *__res
   const uint32_t n = ctl->n;
   const uint32_t w = threadIdx.x >> 5, lane = lane_id();
   const uint32_t radix = 1u << dbits, mask = radix - 1u;
-  const uint32_t tile = blockIdx.x;
-  for (uint32_t d = threadIdx.x; d < 256; d += kSortThreads) {
-    for (int q = 0; q < kSortThreads / 32; q++) wcnt[q][d] = 0;
-    gbase[d] = d < radix ? O[(uint64_t)d * T + tile] : 0u;
-  }
-  __syncthreads();
-  const uint64_t base = (uint64_t)tile * (kSortThreads * ITEMS) + w * (ITEMS * 32);
-  uint64_t key[ITEMS];
-  uint32_t rank[ITEMS];
-  uint32_t dig[ITEMS];
+  for (uint32_t tile = bk.x(); tile < T; tile += bk.n()) {
+    for (uint32_t d = threadIdx.x; d < 256; d += kSortThreads) {
+      for (int q = 0; q < kSortThreads / 32; q++) wcnt[q][d] = 0;
+      gbase[d] = d < radix ? O[(uint64_t)d * T + tile] : 0u;
+    }
+    __syncthreads();
+    const uint64_t base = (uint64_t)tile * (kSortThreads * ITEMS) + w * (ITEMS * 32);
+    uint64_t key[ITEMS];
+    uint32_t rank[ITEMS];
+    uint32_t dig[ITEMS];
 #pragma unroll
-  for (int r = 0; r < ITEMS; r++) {
-    const uint64_t idx = base + r * 32 + lane;
-    const bool valid = idx < n;
-    key[r] = valid ? src[idx] : 0ull;
-    dig[r] = valid ? (uint32_t)(((key[r] & ~kTagBit) >> shift) & mask) : 0xFFFFu;
-  }
+    for (int r = 0; r < ITEMS; r++) {
+      const uint64_t idx = base + r * 32 + lane;
+      const bool valid = idx < n;
+      key[r] = valid ? src[idx] : 0ull;
+      dig[r] = valid ? (uint32_t)(((key[r] & ~kTagBit) >> shift) & mask) : 0xFFFFu;
+    }
 #pragma unroll
-  for (int r = 0; r < ITEMS; r++) {
-    // lanes holding the same digit, from one ballot per digit bit (cheaper than match.any)
-    uint32_t peers = 0xFFFFFFFFu;
-    for (uint32_t b = 0; b < dbits; b++) {
-      const bool bit = (dig[r] >> b) & 1u;
-      const uint32_t bal = __ballot_sync(0xFFFFFFFFu, bit);
-      peers &= bit ? bal : ~bal;
+    for (int r = 0; r < ITEMS; r++) {
+      // lanes holding the same digit, from one ballot per digit bit (cheaper than match.any)
+      uint32_t peers = 0xFFFFFFFFu;
+      for (uint32_t b = 0; b < dbits; b++) {
+        const bool bit = (dig[r] >> b) & 1u;
+        const uint32_t bal = __ballot_sync(0xFFFFFFFFu, bit);
+        peers &= bit ? bal : ~bal;
+      }
+      {
+        const bool inv = dig[r] == 0xFFFFu;
+        const uint32_t bal = __ballot_sync(0xFFFFFFFFu, inv);
+        peers &= inv ? bal : ~bal;
+      }
+      uint32_t before = 0;
+      if (dig[r] != 0xFFFFu) before = wcnt[w][dig[r]];
+      rank[r] = before + __popc(peers & lanemask_lt());
+      __syncwarp();
+      if (dig[r] != 0xFFFFu && lane == (uint32_t)(__ffs(peers) - 1)) wcnt[w][dig[r]] = before + __popc(peers);
+      __syncwarp();
     }
-    {
-      const bool inv = dig[r] == 0xFFFFu;
-      const uint32_t bal = __ballot_sync(0xFFFFFFFFu, inv);
-      peers &= inv ? bal : ~bal;
+    __syncthreads();
+    // per digit: exclusive prefix over the warps, and the tile's total
+    for (uint32_t d = threadIdx.x; d < 256; d += kSortThreads) {
+      uint32_t run = 0;
+      for (int q = 0; q < kSortThreads / 32; q++) {
+        const uint32_t c = wcnt[q][d];
+        wcnt[q][d] = run;
+        run += c;
+      }
+      ltile[d] = run;
     }
-    uint32_t before = 0;
-    if (dig[r] != 0xFFFFu) before = wcnt[w][dig[r]];
-    rank[r] = before + __popc(peers & lanemask_lt());
-    __syncwarp();
-    if (dig[r] != 0xFFFFu && lane == (uint32_t)(__ffs(peers) - 1)) wcnt[w][dig[r]] = before + __popc(peers);
-    __syncwarp();
-  }
-  __syncthreads();
-  // per digit: exclusive prefix over the warps, and the tile's total
-  for (uint32_t d = threadIdx.x; d < 256; d += kSortThreads) {
-    uint32_t run = 0;
-    for (int q = 0; q < kSortThreads / 32; q++) {
-      const uint32_t c = wcnt[q][d];
-      wcnt[q][d] = run;
-      run += c;
+    __syncthreads();
+    if (threadIdx.x < 32) {  // digit offsets inside the tile
+      uint32_t carry = 0;
+      for (int c = 0; c < 256; c += 32) {
+        const uint32_t v = ltile[c + lane];
+        const uint32_t inc = warp_incl_scan(v);
+        ltile[c + lane] = carry + inc - v;
+        carry += __shfl_sync(0xFFFFFFFFu, inc, 31);
+      }
     }
-    ltile[d] = run;
-  }
-  __syncthreads();
-  if (threadIdx.x < 32) {  // digit offsets inside the tile
-    uint32_t carry = 0;
-    for (int c = 0; c < 256; c += 32) {
-      const uint32_t v = ltile[c + lane];
-      const uint32_t inc = warp_incl_scan(v);
-      ltile[c + lane] = carry + inc - v;
-      carry += __shfl_sync(0xFFFFFFFFu, inc, 31);
-    }
-  }
-  __syncthreads();
-  // the tile sorted by digit in shared memory, then written out in digit runs
-  // (consecutive keys of one digit go to consecutive addresses)
+    __syncthreads();
+    // the tile sorted by digit in shared memory, then written out in digit runs
+    // (consecutive keys of one digit go to consecutive addresses)
 #pragma unroll
-  for (int r = 0; r < ITEMS; r++)
-    if (dig[r] != 0xFFFFu) skey[ltile[dig[r]] + wcnt[w][dig[r]] + rank[r]] = key[r];
-  __syncthreads();
-  const uint64_t t0 = (uint64_t)tile * (kSortThreads * ITEMS);
-  const uint32_t cnt = t0 >= n ? 0u : (n - t0 < kSortThreads * ITEMS ? (uint32_t)(n - t0) : kSortThreads * ITEMS);
-  for (uint32_t i0 = 0; i0 < cnt; i0 += kSortThreads) {
-    const uint32_t i = i0 + threadIdx.x;
-    uint32_t cell = 0xFFFFFFFFu;
-    if (i < cnt) {
-      const uint64_t k = skey[i];
-      const uint32_t d = (uint32_t)(((k & ~kTagBit) >> shift) & mask);
-      const uint32_t pos = gbase[d] + (i - ltile[d]);
-      dst[pos] = k;
-      cell = (uint32_t)(((k & ~kTagBit) >> nshift) & mask) * T + pos / (kSortThreads * ITEMS);
+    for (int r = 0; r < ITEMS; r++)
+      if (dig[r] != 0xFFFFu) skey[ltile[dig[r]] + wcnt[w][dig[r]] + rank[r]] = key[r];
+    __syncthreads();
+    const uint64_t t0 = (uint64_t)tile * (kSortThreads * ITEMS);
+    const uint32_t cnt = t0 >= n ? 0u : (n - t0 < kSortThreads * ITEMS ? (uint32_t)(n - t0) : kSortThreads * ITEMS);
+    for (uint32_t i0 = 0; i0 < cnt; i0 += kSortThreads) {
+      const uint32_t i = i0 + threadIdx.x;
+      uint32_t cell = 0xFFFFFFFFu;
+      if (i < cnt) {
+        const uint64_t k = skey[i];
+        const uint32_t d = (uint32_t)(((k & ~kTagBit) >> shift) & mask);
+        const uint32_t pos = gbase[d] + (i - ltile[d]);
+        dst[pos] = k;
+        cell = (uint32_t)(((k & ~kTagBit) >> nshift) & mask) * T + pos / (kSortThreads * ITEMS);
+      }
+      if (Hn) {
+        // staged keys leave in order, so lanes of one warp often share a destination
+        // tile and (for skewed keys) the next digit: one atomic per distinct cell
+        const uint32_t peers = __match_any_sync(0xFFFFFFFFu, cell);
+        if (cell != 0xFFFFFFFFu && lane == (uint32_t)(__ffs(peers) - 1)) atomicAdd(&Hn[cell], (uint32_t)__popc(peers));
+      }
     }
-    if (Hn) {
-      // staged keys leave in order, so lanes of one warp often share a destination
-      // tile and (for skewed keys) the next digit: one atomic per distinct cell
-      const uint32_t peers = __match_any_sync(0xFFFFFFFFu, cell);
-      if (cell != 0xFFFFFFFFu && lane == (uint32_t)(__ffs(peers) - 1)) atomicAdd(&Hn[cell], (uint32_t)__popc(peers));
-    }
+    __syncthreads();
   }
 }
+
+template <int ITEMS>
+__global__ void __launch_bounds__(kSortThreads) k_rscatter(const uint64_t *__restrict__ src,
+                                                           uint64_t *__restrict__ dst, const uint32_t *__restrict__ O,
+                                                           uint32_t *__restrict__ Hn, uint32_t T, uint32_t shift,
+                                                           uint32_t nshift, uint32_t dbits, const Ctl *ctl) { rscatter_body<ITEMS>(GridIdx{}, src, dst, O, Hn, T, shift, nshift, dbits, ctl); }
 
 // ---- small batches: the whole front end in one block ---------------------------------------
 // Sort word = (compressed key without tag) << 1 | tag.  Inserts (tag 0) order
@@ -302,13 +329,8 @@ __device__ __forceinline__ uint32_t sampled_leaf_search(const uint64_t *__restri
   return p ? (uint32_t)(p - 1) : 0u;
 }
 
-__global__ void __launch_bounds__(1024) k_small_front(PrepArgs a, const uint64_t *__restrict__ ins,
-                                                      const uint64_t *__restrict__ del, Ctl *ctl,
-                                                      const uint64_t *__restrict__ F, uint64_t nleaves,
-                                                      uint64_t *__restrict__ ukey, uint8_t *__restrict__ utag,
-                                                      uint32_t *__restrict__ uleaf, uint32_t *__restrict__ run_start,
-                                                      uint32_t *__restrict__ run_leaf, const ModelHead *mhead,
-                                                      const Piece *__restrict__ mpieces, uint32_t P, uint32_t S) {
+template <class Blk>
+__device__ __forceinline__ void small_front_body(const Blk &bk, const PrepArgs &a, const uint64_t *__restrict__ ins, const uint64_t *__restrict__ del, Ctl *ctl, const uint64_t *__restrict__ F, uint64_t nleaves, uint64_t *__restrict__ ukey, uint8_t *__restrict__ utag, uint32_t *__restrict__ uleaf, uint32_t *__restrict__ run_start, uint32_t *__restrict__ run_leaf, const ModelHead *mhead, const Piece *__restrict__ mpieces, uint32_t P, uint32_t S) {
   extern __shared__ uint64_t sk[];           // P sort words
   uint64_t *sw = sk + P;                     // P survivor words
   uint64_t *cv = sw + P;                     // S compacted sampled pivots
@@ -442,6 +464,14 @@ __global__ void __launch_bounds__(1024) k_small_front(PrepArgs a, const uint64_t
   }
 }
 
+__global__ void __launch_bounds__(1024) k_small_front(PrepArgs a, const uint64_t *__restrict__ ins,
+                                                      const uint64_t *__restrict__ del, Ctl *ctl,
+                                                      const uint64_t *__restrict__ F, uint64_t nleaves,
+                                                      uint64_t *__restrict__ ukey, uint8_t *__restrict__ utag,
+                                                      uint32_t *__restrict__ uleaf, uint32_t *__restrict__ run_start,
+                                                      uint32_t *__restrict__ run_leaf, const ModelHead *mhead,
+                                                      const Piece *__restrict__ mpieces, uint32_t P, uint32_t S) { small_front_body(GridIdx{}, a, ins, del, ctl, F, nleaves, ukey, utag, uleaf, run_start, run_leaf, mhead, mpieces, P, S); }
+
 // ---- unique/cancel, leaf search, run heads and compaction (after the radix passes) ------------
 // Per-block survivor summaries of the sorted words (256 Q words a block).
 struct TileSums {
@@ -458,88 +488,94 @@ struct TileSums {
 // (an insert survives unless the next word has its key, a delete unless the
 // previous one has), the leaf of every survivor (reading R4), and the block's
 // summary.
+template <int Q, class Blk>
+__device__ __forceinline__ void rsearch_body(const Blk &bk, const PrepArgs &a, const uint64_t *__restrict__ sorted, uint32_t *__restrict__ lfull, const uint64_t *__restrict__ F, uint64_t nleaves, const TileSums &ts, uint32_t ntiles, Ctl *ctl, const ModelHead *mhead, const Piece *__restrict__ mpieces) {
+  __shared__ uint32_t sl[(kSearchThreads * Q)];
+  __shared__ uint32_t s_surv, s_hin, s_first, s_last;
+  if (ctl->err) return;
+  const uint32_t n = ctl->n, t = threadIdx.x;
+  for (uint32_t tile = bk.x(); tile < ntiles; tile += bk.n()) {
+    const uint32_t e0 = tile * (kSearchThreads * Q) + t * Q;
+    if (t == 0) {
+      s_surv = 0;
+      s_hin = 0;
+      s_first = 0xFFFFFFFFu;
+      s_last = 0;
+    }
+    ModelHead hd;
+    hd.valid = 0;
+    if (mhead) hd = *mhead;
+    uint64_t w[Q + 2];  // words e0 - 1 .. e0 + Q
+#pragma unroll
+    for (int q = 0; q < Q + 2; q++) {
+      const int64_t e = (int64_t)e0 - 1 + q;
+      w[q] = (e >= 0 && e < (int64_t)n) ? sorted[e] : kEmpty;
+    }
+    uint64_t key[Q];
+    bool kept[Q];
+    uint32_t leaf[Q];
+#pragma unroll
+    for (int q = 0; q < Q; q++) {
+      const uint32_t e = e0 + q;
+      const uint64_t wq = w[q + 1], kq = wq & ~kTagBit;
+      kept[q] = e < n && ((wq & kTagBit) ? (e == 0 || (w[q] & ~kTagBit) != kq) : (e + 1 == n || (w[q + 2] & ~kTagBit) != kq));
+      key[q] = kept[q] ? expand(wq, a) : 0ull;
+    }
+    uint32_t miss = 0;
+    if (hd.valid) miss = learned_search_lockstep<Q>(hd, mpieces, F, nleaves, key, kept, leaf);
+    else leaf_search_lockstep<Q>(F, nleaves, key, kept, leaf);
+#pragma unroll
+    for (int q = 0; q < Q; q++)
+      if (!kept[q]) leaf[q] = kNoLeaf;
+#pragma unroll
+    for (int q = 0; q < Q; q++) {
+      if (e0 + q < n) lfull[e0 + q] = leaf[q];
+      sl[t * Q + q] = leaf[q];
+    }
+    __syncthreads();
+    uint32_t hin = 0, surv = 0;
+#pragma unroll
+    for (int q = 0; q < Q; q++) {
+      if (leaf[q] == kNoLeaf) continue;
+      const uint32_t i = t * Q + q;
+      ++surv;
+      int32_t j = (int32_t)i - 1;  // previous survivor of the block (dropped words are rare)
+      while (j >= 0 && sl[j] == kNoLeaf) --j;
+      if (j < 0) s_first = i;  // exactly one survivor has none before it
+      else hin += sl[j] != leaf[q];
+      atomicMax(&s_last, i);
+    }
+    surv = warp_sum(surv);
+    hin = warp_sum(hin);
+    miss = warp_sum(miss);
+    if (lane_id() == 0) {
+      if (surv) atomicAdd(&s_surv, surv);
+      if (hin) atomicAdd(&s_hin, hin);
+      if (miss) atomicAdd(&ctl->lm_miss, miss);
+    }
+    __syncthreads();
+    if (t == 0) {
+      ts.surv[tile] = s_surv;
+      ts.hin[tile] = s_hin;
+      ts.first[tile] = s_surv ? sl[s_first] : kNoLeaf;
+      ts.last[tile] = s_surv ? sl[s_last] : kNoLeaf;
+    }
+    __syncthreads();
+  }
+}
+
 template <int Q>
 __global__ void __launch_bounds__(kSearchThreads) k_rsearch(PrepArgs a, const uint64_t *__restrict__ sorted,
                                                             uint32_t *__restrict__ lfull,
                                                             const uint64_t *__restrict__ F, uint64_t nleaves,
                                                             TileSums ts, Ctl *ctl, const ModelHead *mhead,
-                                                            const Piece *__restrict__ mpieces) {
-  __shared__ uint32_t sl[(kSearchThreads * Q)];
-  __shared__ uint32_t s_surv, s_hin, s_first, s_last;
-  if (ctl->err) return;
-  const uint32_t n = ctl->n, t = threadIdx.x;
-  const uint32_t e0 = blockIdx.x * (kSearchThreads * Q) + t * Q;
-  if (t == 0) {
-    s_surv = 0;
-    s_hin = 0;
-    s_first = 0xFFFFFFFFu;
-    s_last = 0;
-  }
-  ModelHead hd;
-  hd.valid = 0;
-  if (mhead) hd = *mhead;
-  uint64_t w[Q + 2];  // words e0 - 1 .. e0 + Q
-#pragma unroll
-  for (int q = 0; q < Q + 2; q++) {
-    const int64_t e = (int64_t)e0 - 1 + q;
-    w[q] = (e >= 0 && e < (int64_t)n) ? sorted[e] : kEmpty;
-  }
-  uint64_t key[Q];
-  bool kept[Q];
-  uint32_t leaf[Q];
-#pragma unroll
-  for (int q = 0; q < Q; q++) {
-    const uint32_t e = e0 + q;
-    const uint64_t wq = w[q + 1], kq = wq & ~kTagBit;
-    kept[q] = e < n && ((wq & kTagBit) ? (e == 0 || (w[q] & ~kTagBit) != kq) : (e + 1 == n || (w[q + 2] & ~kTagBit) != kq));
-    key[q] = kept[q] ? expand(wq, a) : 0ull;
-  }
-  uint32_t miss = 0;
-  if (hd.valid) miss = learned_search_lockstep<Q>(hd, mpieces, F, nleaves, key, kept, leaf);
-  else leaf_search_lockstep<Q>(F, nleaves, key, kept, leaf);
-#pragma unroll
-  for (int q = 0; q < Q; q++)
-    if (!kept[q]) leaf[q] = kNoLeaf;
-#pragma unroll
-  for (int q = 0; q < Q; q++) {
-    if (e0 + q < n) lfull[e0 + q] = leaf[q];
-    sl[t * Q + q] = leaf[q];
-  }
-  __syncthreads();
-  uint32_t hin = 0, surv = 0;
-#pragma unroll
-  for (int q = 0; q < Q; q++) {
-    if (leaf[q] == kNoLeaf) continue;
-    const uint32_t i = t * Q + q;
-    ++surv;
-    int32_t j = (int32_t)i - 1;  // previous survivor of the block (dropped words are rare)
-    while (j >= 0 && sl[j] == kNoLeaf) --j;
-    if (j < 0) s_first = i;  // exactly one survivor has none before it
-    else hin += sl[j] != leaf[q];
-    atomicMax(&s_last, i);
-  }
-  surv = warp_sum(surv);
-  hin = warp_sum(hin);
-  miss = warp_sum(miss);
-  if (lane_id() == 0) {
-    if (surv) atomicAdd(&s_surv, surv);
-    if (hin) atomicAdd(&s_hin, hin);
-    if (miss) atomicAdd(&ctl->lm_miss, miss);
-  }
-  __syncthreads();
-  if (t == 0) {
-    ts.surv[blockIdx.x] = s_surv;
-    ts.hin[blockIdx.x] = s_hin;
-    ts.first[blockIdx.x] = s_surv ? sl[s_first] : kNoLeaf;
-    ts.last[blockIdx.x] = s_surv ? sl[s_last] : kNoLeaf;
-  }
-}
+                                                            const Piece *__restrict__ mpieces) { rsearch_body<Q>(GridIdx{}, a, sorted, lfull, F, nleaves, ts, gridDim.x, ctl, mhead, mpieces); }
 
 // Survivor and run-head offsets of every block of k_rsearch: exclusive scans over
 // the blocks; a block's first survivor starts a run unless the last survivor of
 // the nearest earlier block with survivors has the same leaf.  One block of 1024.
-__global__ void __launch_bounds__(1024) k_toffsets(TileSums ts, uint32_t nt, Ctl *ctl,
-                                                   uint32_t *__restrict__ run_start) {
+template <class Blk>
+__device__ __forceinline__ void toffsets_body(const Blk &bk, const TileSums &ts, uint32_t nt, Ctl *ctl, uint32_t *__restrict__ run_start) {
   __shared__ uint32_t wsum[33];
   __shared__ uint32_t s_last[1024];  // last survivor leaf of each thread's blocks
   __shared__ int32_t s_idx[1024];    // nearest thread <= t whose blocks hold a survivor, -1 if none
@@ -612,51 +648,60 @@ __global__ void __launch_bounds__(1024) k_toffsets(TileSums ts, uint32_t nt, Ctl
   }
 }
 
+__global__ void __launch_bounds__(1024) k_toffsets(TileSums ts, uint32_t nt, Ctl *ctl,
+                                                   uint32_t *__restrict__ run_start) { toffsets_body(GridIdx{}, ts, nt, ctl, run_start); }
+
 // survivors and run heads of every block to their places, Q words per thread
+template <int Q, class Blk>
+__device__ __forceinline__ void twrite_body(const Blk &bk, const PrepArgs &a, const uint64_t *__restrict__ sorted, const uint32_t *__restrict__ lfull, const TileSums &ts, uint32_t ntiles, uint64_t *__restrict__ ukey, uint8_t *__restrict__ utag, uint32_t *__restrict__ uleaf, uint32_t *__restrict__ run_start, uint32_t *__restrict__ run_leaf, const Ctl *ctl) {
+  __shared__ uint32_t wsum[33];
+  __shared__ uint32_t sl[(kSearchThreads * Q)];
+  if (ctl->err) return;
+  const uint32_t t = threadIdx.x, n = ctl->n;
+  for (uint32_t b = bk.x(); b < ntiles; b += bk.n()) {
+    if (ts.surv[b] == 0) continue;  // the same for the whole block
+    const uint32_t base = b * (kSearchThreads * Q);
+    for (uint32_t i = t; i < (kSearchThreads * Q); i += kSearchThreads) sl[i] = base + i < n ? lfull[base + i] : kNoLeaf;
+    __syncthreads();
+    uint32_t keep = 0, head = 0;
+#pragma unroll
+    for (int q = 0; q < Q; q++) {
+      const uint32_t i = t * Q + q, lf = sl[i];
+      if (lf == kNoLeaf) continue;
+      keep |= 1u << q;
+      int32_t j = (int32_t)i - 1;  // previous survivor of the block
+      while (j >= 0 && sl[j] == kNoLeaf) --j;
+      if (j < 0 ? ts.hfirst[b] != 0 : sl[j] != lf) head |= 1u << q;
+    }
+    uint32_t nk, nh;
+    uint32_t ko = ts.soff[b] + block_excl_scan(__popc(keep), wsum, &nk);
+    uint32_t ho = ts.hoff[b] + block_excl_scan(__popc(head), wsum, &nh);
+#pragma unroll
+    for (int q = 0; q < Q; q++) {
+      if (!((keep >> q) & 1u)) continue;
+      const uint32_t i = t * Q + q;
+      const uint64_t w = sorted[base + i];
+      ukey[ko] = expand(w, a);
+      utag[ko] = (uint8_t)(w >> 63);
+      uleaf[ko] = sl[i];
+      if ((head >> q) & 1u) {
+        run_start[ho] = ko;
+        run_leaf[ho] = sl[i];
+        ++ho;
+      }
+      ++ko;
+    }
+    __syncthreads();
+  }
+}
+
 template <int Q>
 __global__ void __launch_bounds__(kSearchThreads) k_twrite(PrepArgs a, const uint64_t *__restrict__ sorted,
                                                            const uint32_t *__restrict__ lfull, TileSums ts,
                                                            uint64_t *__restrict__ ukey, uint8_t *__restrict__ utag,
                                                            uint32_t *__restrict__ uleaf,
                                                            uint32_t *__restrict__ run_start,
-                                                           uint32_t *__restrict__ run_leaf, const Ctl *ctl) {
-  __shared__ uint32_t wsum[33];
-  __shared__ uint32_t sl[(kSearchThreads * Q)];
-  if (ctl->err) return;
-  const uint32_t b = blockIdx.x, t = threadIdx.x, n = ctl->n;
-  if (ts.surv[b] == 0) return;
-  const uint32_t base = b * (kSearchThreads * Q);
-  for (uint32_t i = t; i < (kSearchThreads * Q); i += kSearchThreads) sl[i] = base + i < n ? lfull[base + i] : kNoLeaf;
-  __syncthreads();
-  uint32_t keep = 0, head = 0;
-#pragma unroll
-  for (int q = 0; q < Q; q++) {
-    const uint32_t i = t * Q + q, lf = sl[i];
-    if (lf == kNoLeaf) continue;
-    keep |= 1u << q;
-    int32_t j = (int32_t)i - 1;  // previous survivor of the block
-    while (j >= 0 && sl[j] == kNoLeaf) --j;
-    if (j < 0 ? ts.hfirst[b] != 0 : sl[j] != lf) head |= 1u << q;
-  }
-  uint32_t nk, nh;
-  uint32_t ko = ts.soff[b] + block_excl_scan(__popc(keep), wsum, &nk);
-  uint32_t ho = ts.hoff[b] + block_excl_scan(__popc(head), wsum, &nh);
-#pragma unroll
-  for (int q = 0; q < Q; q++) {
-    if (!((keep >> q) & 1u)) continue;
-    const uint32_t i = t * Q + q;
-    const uint64_t w = sorted[base + i];
-    ukey[ko] = expand(w, a);
-    utag[ko] = (uint8_t)(w >> 63);
-    uleaf[ko] = sl[i];
-    if ((head >> q) & 1u) {
-      run_start[ho] = ko;
-      run_leaf[ho] = sl[i];
-      ++ho;
-    }
-    ++ko;
-  }
-}
+                                                           uint32_t *__restrict__ run_leaf, const Ctl *ctl) { twrite_body<Q>(GridIdx{}, a, sorted, lfull, ts, gridDim.x, ukey, utag, uleaf, run_start, run_leaf, ctl); }
 
 // ---- host launchers ----------------------------------------------------------------------
 static uint32_t grid_for(uint64_t n, uint32_t per_block, uint32_t cap) {
@@ -742,6 +787,129 @@ void launch_front(const FrontArgs &f, uint64_t nb, cudaStream_t s) {
   else
     k_twrite<1><<<T1, kSearchThreads, 0, s>>>(a, src, f.lfull, ts, f.ukey, f.utag, f.uleaf, f.run_start,
                                               f.run_leaf, f.ctl);
+}
+
+bool search_wide(uint64_t n) { return search_per(n) == 4; }
+
+// ---- many handles: one launch per stage over the work of all of them ---------------------------
+// Each block finds its handle (and its block index within that handle's share)
+// in the call's plan table and runs the same body as the single-handle kernel,
+// with the handle's own sizes; blocks beyond what this call's batch needs return.
+__device__ __forceinline__ TileSums tile_sums(uint32_t *rs, uint32_t T, uint32_t T1) {
+  uint32_t *q = rs + (uint64_t)512 * T;
+  const uint32_t K = T1 + 1;
+  return TileSums{q, q + K, q + 2 * K, q + 3 * K, q + 4 * K, q + 5 * K, q + 6 * K};
+}
+
+__global__ void k_m_init(const ManyDesc *d, uint32_t plan) {
+  const ManyItem *it;
+  uint32_t sub, nb;
+  if (!many_block(d, plan, &it, &sub, &nb) || !it->active || it->small) return;
+  init_batch_body(GridIdx{}, it->ctl, it->hist, it->prep.npass * 256u, it->prep.n_ins + it->prep.n_del);
+}
+
+__global__ void __launch_bounds__(1024) k_m_small_front(const ManyDesc *d, uint32_t plan) {
+  const ManyItem *it;
+  uint32_t sub, nb;
+  if (!many_block(d, plan, &it, &sub, &nb) || !it->active || !it->small) return;
+  small_front_body(GridIdx{}, it->prep, it->ins, it->del, it->ctl, it->g.F, it->g.nleaves, it->w.ukey, it->w.utag,
+                   it->w.uleaf, it->w.run_start, it->w.rleaf, it->mhead, it->mpieces, it->P, it->S);
+}
+
+__global__ void __launch_bounds__(kSortThreads) k_m_prep(const ManyDesc *d, uint32_t plan) {
+  const ManyItem *it;
+  uint32_t sub, nb;
+  // every block of the handle takes the prep ticket: the plan gives it at most T blocks
+  if (!many_block(d, plan, &it, &sub, &nb) || it->small) return;
+  prep_body<kSortItems>(SubIdx{sub, nb}, it->prep, it->ins, it->del, it->bufA, it->hist, it->w.rs, it->T, it->ctl);
+}
+
+__global__ void __launch_bounds__(256) k_m_rcolscan(const ManyDesc *d, uint32_t plan, uint32_t p) {
+  const ManyItem *it;
+  uint32_t sub, nb;
+  if (!many_block(d, plan, &it, &sub, &nb) || it->small || p >= it->prep.npass) return;
+  const uint32_t T = it->T;
+  uint32_t *H[2] = {it->w.rs, it->w.rs + (uint64_t)256 * T};
+  rcolscan_body(SubIdx{sub, nb}, H[p & 1], p + 1 < it->prep.npass ? H[(p + 1) & 1] : nullptr, T,
+                it->hist + 8 * 256 + p * 256, 1u << it->prep.dbits, it->ctl);
+}
+
+__global__ void __launch_bounds__(kSortThreads) k_m_rscatter(const ManyDesc *d, uint32_t plan, uint32_t p) {
+  const ManyItem *it;
+  uint32_t sub, nb;
+  if (!many_block(d, plan, &it, &sub, &nb) || it->small || p >= it->prep.npass) return;
+  const uint32_t T = it->T, db = it->prep.dbits;
+  uint32_t *H[2] = {it->w.rs, it->w.rs + (uint64_t)256 * T};
+  const uint64_t *src = (p & 1) ? it->bufB : it->bufA;
+  uint64_t *dst = (p & 1) ? it->bufA : it->bufB;
+  rscatter_body<kSortItems>(SubIdx{sub, nb}, src, dst, H[p & 1], p + 1 < it->prep.npass ? H[(p + 1) & 1] : nullptr,
+                            T, p * db, (p + 1) * db, db, it->ctl);
+}
+
+template <int Q>
+__global__ void __launch_bounds__(kSearchThreads) k_m_rsearch(const ManyDesc *d, uint32_t plan) {
+  const ManyItem *it;
+  uint32_t sub, nb;
+  if (!many_block(d, plan, &it, &sub, &nb) || it->small || it->wide != (Q == 4 ? 1u : 0u)) return;
+  const uint64_t *sorted = (it->prep.npass & 1) ? it->bufB : it->bufA;
+  rsearch_body<Q>(SubIdx{sub, nb}, it->prep, sorted, it->w.pleaf, it->g.F, it->g.nleaves,
+                  tile_sums(it->w.rs, it->T, it->T1), it->T1, it->ctl, it->mhead, it->mpieces);
+}
+
+__global__ void __launch_bounds__(1024) k_m_toffsets(const ManyDesc *d, uint32_t plan) {
+  const ManyItem *it;
+  uint32_t sub, nb;
+  if (!many_block(d, plan, &it, &sub, &nb) || !it->active || it->small) return;
+  toffsets_body(GridIdx{}, tile_sums(it->w.rs, it->T, it->T1), it->T1, it->ctl, it->w.run_start);
+}
+
+template <int Q>
+__global__ void __launch_bounds__(kSearchThreads) k_m_twrite(const ManyDesc *d, uint32_t plan) {
+  const ManyItem *it;
+  uint32_t sub, nb;
+  if (!many_block(d, plan, &it, &sub, &nb) || it->small || it->wide != (Q == 4 ? 1u : 0u)) return;
+  const uint64_t *sorted = (it->prep.npass & 1) ? it->bufB : it->bufA;
+  twrite_body<Q>(SubIdx{sub, nb}, it->prep, sorted, it->w.pleaf, tile_sums(it->w.rs, it->T, it->T1), it->T1,
+                 it->w.ukey, it->w.utag, it->w.uleaf, it->w.run_start, it->w.rleaf, it->ctl);
+}
+
+void prepare_many_front() {
+  cudaFuncSetAttribute(k_m_small_front, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmallBatch * 20 + 2048 * 12);
+}
+
+void launch_many_front(const ManyDesc *d, const ManyPlans &pl, cudaStream_t s) {
+  const uint32_t one = pl.total[pl.one];
+  note_launch();
+  k_m_small_front<<<one, 1024, kSmallBatch * 20 + 2048 * 12, s>>>(d, pl.one);
+  if (!pl.total[pl.tiles]) return;  // no handle's work arrays can hold more than kSmallBatch keys
+  note_launch();
+  k_m_init<<<one, 256, 0, s>>>(d, pl.one);
+  note_launch();
+  k_m_prep<<<pl.total[pl.tiles], kSortThreads, 0, s>>>(d, pl.tiles);
+  for (uint32_t p = 0; p < pl.maxpass; p++) {
+    note_launch();
+    k_m_rcolscan<<<pl.total[pl.radix], 256, 0, s>>>(d, pl.radix, p);
+    note_launch();
+    k_m_rscatter<<<pl.total[pl.tiles], kSortThreads, 0, s>>>(d, pl.tiles, p);
+  }
+  if (pl.total[pl.search[0]]) {
+    note_launch();
+    k_m_rsearch<1><<<pl.total[pl.search[0]], kSearchThreads, 0, s>>>(d, pl.search[0]);
+  }
+  if (pl.total[pl.search[1]]) {
+    note_launch();
+    k_m_rsearch<4><<<pl.total[pl.search[1]], kSearchThreads, 0, s>>>(d, pl.search[1]);
+  }
+  note_launch();
+  k_m_toffsets<<<one, 1024, 0, s>>>(d, pl.one);
+  if (pl.total[pl.search[0]]) {
+    note_launch();
+    k_m_twrite<1><<<pl.total[pl.search[0]], kSearchThreads, 0, s>>>(d, pl.search[0]);
+  }
+  if (pl.total[pl.search[1]]) {
+    note_launch();
+    k_m_twrite<4><<<pl.total[pl.search[1]], kSearchThreads, 0, s>>>(d, pl.search[1]);
+  }
 }
 
 // enough for every batch of at most nb keys (one word a thread gives the most search blocks)

@@ -25,11 +25,6 @@
 
 namespace gpk {
 
-// per-warp shared memory of the leaf kernels: three key buffers of L, a u16
-// index array of L+1 and a byte mask of L
-__host__ __device__ inline uint32_t leaf_smem_bytes(uint32_t L) {
-  return 24u * L + ((2u * (L + 1u) + 15u) & ~15u) + ((L + 15u) & ~15u);
-}
 
 struct WarpBufs {
   uint64_t *a, *b, *out;
@@ -49,7 +44,8 @@ __device__ __forceinline__ WarpBufs warp_bufs(unsigned char *smem, uint32_t per_
 }
 
 // ---- level 0: one warp per touched leaf ------------------------------------------------------
-__global__ void k_leaf_pass(Geo g, Ctl *ctl, Work w, uint32_t per_warp, int rest_only) {
+template <class Blk>
+__device__ __forceinline__ void leaf_pass_body(const Blk &bk, const Geo &g, Ctl *ctl, const Work &w, uint32_t per_warp, int rest_only) {
   extern __shared__ __align__(16) unsigned char smem[];
   if (ctl->err) return;
   if (rest_only && ctl->nlong == 0) return;
@@ -62,7 +58,7 @@ __global__ void k_leaf_pass(Geo g, Ctl *ctl, Work w, uint32_t per_warp, int rest
   const uint32_t nruns = ctl->nruns;
   uint64_t acc_ins = 0, acc_del = 0;
   uint32_t acc_m0 = 0, acc_esc = 0;
-  for (uint32_t r = blockIdx.x * wpb + (threadIdx.x >> 5); r < nruns; r += gridDim.x * wpb) {
+  for (uint32_t r = bk.x() * wpb + (threadIdx.x >> 5); r < nruns; r += bk.n() * wpb) {
     const uint32_t rs = w.run_start[r], re = w.run_start[r + 1];
     if (rest_only && re - rs <= 32) continue;  // done by the 64-slot fast path
     if (re - rs > kLongRun) {  // done by the chunked path: reset its accumulators
@@ -181,6 +177,8 @@ __global__ void k_leaf_pass(Geo g, Ctl *ctl, Work w, uint32_t per_warp, int rest
   }
 }
 
+__global__ void k_leaf_pass(Geo g, Ctl *ctl, Work w, uint32_t per_warp, int rest_only) { leaf_pass_body(GridIdx{}, g, ctl, w, per_warp, rest_only); }
+
 // ---- level 0 for runs longer than kLongRun (bulk loads) -----------------------------------------
 // Phase A, a warp per 32 consecutive keys: the presence filter against the
 // leaf's valid keys, deletes made EMPTY in place (distinct slots), surviving
@@ -216,13 +214,14 @@ __device__ __forceinline__ uint32_t load_leaf(const uint64_t *leaf, uint32_t L, 
   return nv;
 }
 
-__global__ void k_long_a(Geo g, Ctl *ctl, Work w, uint32_t per_warp) {
+template <class Blk>
+__device__ __forceinline__ void long_a_body(const Blk &bk, const Geo &g, Ctl *ctl, const Work &w, uint32_t per_warp) {
   extern __shared__ __align__(16) unsigned char smem[];
   if (ctl->err || ctl->nvlong == 0) return;
   const uint32_t L = g.L, lane = lane_id(), wpb = blockDim.x >> 5;
   WarpBufs B = warp_bufs(smem, per_warp, L);
   const uint32_t m = ctl->m, nruns = ctl->nruns;
-  for (uint32_t c = (blockIdx.x * wpb + (threadIdx.x >> 5)) * 32; c < m; c += gridDim.x * wpb * 32) {
+  for (uint32_t c = (bk.x() * wpb + (threadIdx.x >> 5)) * 32; c < m; c += bk.n() * wpb * 32) {
     // the keys [c, c+32) span at most two runs: the run of the first key, then the next
     const uint32_t r0 = run_of(w.run_start, nruns, c);
     for (uint32_t r = r0; r < nruns && w.run_start[r] < c + 32 && w.run_start[r] < m; r++) {
@@ -255,7 +254,10 @@ __global__ void k_long_a(Geo g, Ctl *ctl, Work w, uint32_t per_warp) {
   }
 }
 
-__global__ void k_long_b(Geo g, Ctl *ctl, Work w, uint32_t per_warp) {
+__global__ void k_long_a(Geo g, Ctl *ctl, Work w, uint32_t per_warp) { long_a_body(GridIdx{}, g, ctl, w, per_warp); }
+
+template <class Blk>
+__device__ __forceinline__ void long_b_body(const Blk &bk, const Geo &g, Ctl *ctl, const Work &w, uint32_t per_warp) {
   extern __shared__ __align__(16) unsigned char smem[];
   if (ctl->err || ctl->nvlong == 0) return;
   const uint32_t L = g.L, lane = lane_id(), wpb = blockDim.x >> 5;
@@ -264,7 +266,7 @@ __global__ void k_long_b(Geo g, Ctl *ctl, Work w, uint32_t per_warp) {
   const uint32_t nruns = ctl->nruns;
   uint64_t acc_ins = 0, acc_del = 0;
   uint32_t acc_m0 = 0, acc_esc = 0;
-  for (uint32_t r = blockIdx.x * wpb + (threadIdx.x >> 5); r < nruns; r += gridDim.x * wpb) {
+  for (uint32_t r = bk.x() * wpb + (threadIdx.x >> 5); r < nruns; r += bk.n() * wpb) {
     const uint32_t rs = w.run_start[r], re = w.run_start[r + 1];
     if (re - rs <= kLongRun) continue;
     const uint32_t j = w.rleaf[r];
@@ -319,21 +321,24 @@ __global__ void k_long_b(Geo g, Ctl *ctl, Work w, uint32_t per_warp) {
   }
 }
 
+__global__ void k_long_b(Geo g, Ctl *ctl, Work w, uint32_t per_warp) { long_b_body(GridIdx{}, g, ctl, w, per_warp); }
+
 // ---- level 0, fast path for 64-slot leaves and runs of at most 32 updates ---------------------
 // Lane l holds slots 2l and 2l+1 of the leaf in registers (one 16-byte load),
 // lane i < len holds update i of the run; presence, deletes and ranks are warp
 // ballots.  The next run's leaf is loaded before the current one is processed.
 // 5 blocks of 256 threads an SM (48 registers): more runs in flight hide the leaf loads
-__global__ void __launch_bounds__(256, 5) k_leaf64(Geo g, Ctl *ctl, Work w) {
+template <class Blk>
+__device__ __forceinline__ void leaf64_body(const Blk &bk, const Geo &g, Ctl *ctl, const Work &w) {
   __shared__ uint64_t sout[8][64];
   if (ctl->err) return;
   const uint32_t lane = lane_id(), wib = threadIdx.x >> 5;
   const uint32_t nruns = ctl->nruns;
-  const uint32_t nw = gridDim.x * 8;
+  const uint32_t nw = bk.n() * 8;
   ulonglong2 *s2 = reinterpret_cast<ulonglong2 *>(g.slots);
   uint64_t acc_ins = 0, acc_del = 0;
   uint32_t acc_m0 = 0, acc_esc = 0, acc_long = 0;
-  uint32_t r = blockIdx.x * 8 + wib;
+  uint32_t r = bk.x() * 8 + wib;
   uint32_t jn = 0, rsn = 0, ren = 0;
   ulonglong2 kn = make_ulonglong2(kEmpty, kEmpty);
   if (r < nruns) {
@@ -502,6 +507,8 @@ __global__ void __launch_bounds__(256, 5) k_leaf64(Geo g, Ctl *ctl, Work w) {
     if (acc_long) atomicAdd(&ctl->nlong, acc_long);
   }
 }
+
+__global__ void __launch_bounds__(256, 5) k_leaf64(Geo g, Ctl *ctl, Work w) { leaf64_body(GridIdx{}, g, ctl, w); }
 
 // ---- count tree, rebuilt only when some inserts did not fit their leaf ----------------------
 // Levels 1..h of the tree hold logical counts for the merge-level test: valid
@@ -899,13 +906,17 @@ static uint32_t blocks_for(uint64_t items, uint32_t per_block, uint32_t cap) {
   return (uint32_t)b;
 }
 
-static uint32_t warps_per_block(uint32_t L) {
+// warps per block of the one-warp-per-leaf kernels: as many as fit 96 KB of
+// shared memory, at most 8, or `want` (a tuned choice) when that fits
+static uint32_t warps_per_block(uint32_t L, uint32_t want = 0) {
   uint32_t pw = leaf_smem_bytes(L);
   uint32_t wpb = (96u * 1024u) / pw;
   if (wpb > 8) wpb = 8;
   if (wpb < 1) wpb = 1;
+  if (want && want < wpb) wpb = want;
   return wpb;
 }
+uint32_t leaf_pass_warps(uint32_t L, uint32_t want) { return warps_per_block(L, want); }
 
 void allow_big_smem() {
   static bool done = false;
@@ -921,10 +932,11 @@ void allow_big_smem() {
 // (every surviving insert ends up stored, pending ones by the merges of this
 // batch; guards are not edges): lanes of one source (keys are sorted, so they
 // are adjacent) add once.
-__global__ void __launch_bounds__(256) k_deg_batch(Geo g, const Ctl *ctl, Work w) {
+template <class Blk>
+__device__ __forceinline__ void deg_batch_body(const Blk &bk, const Geo &g, const Ctl *ctl, const Work &w) {
   if (ctl->err) return;
   const uint32_t m = ctl->m;
-  for (uint32_t b = blockIdx.x * blockDim.x; b < m; b += gridDim.x * blockDim.x) {
+  for (uint32_t b = bk.x() * blockDim.x; b < m; b += bk.n() * blockDim.x) {
     const uint32_t e = b + threadIdx.x;
     int d = 0;
     uint64_t key = 0;
@@ -942,6 +954,8 @@ __global__ void __launch_bounds__(256) k_deg_batch(Geo g, const Ctl *ctl, Work w
   }
 }
 
+__global__ void __launch_bounds__(256) k_deg_batch(Geo g, const Ctl *ctl, Work w) { deg_batch_body(GridIdx{}, g, ctl, w); }
+
 void launch_leaf64(const Geo &g, Ctl *ctl, const Work &w, uint32_t n, cudaStream_t s) {
   note_launch();
   k_leaf64<<<blocks_for(n, 8, 152 * 5), 256, 0, s>>>(g, ctl, w);  // one wave of resident blocks
@@ -949,7 +963,7 @@ void launch_leaf64(const Geo &g, Ctl *ctl, const Work &w, uint32_t n, cudaStream
 
 void launch_leaf_rest(const Geo &g, Ctl *ctl, const Work &w, uint32_t n, bool rest_only, cudaStream_t s) {
   allow_big_smem();
-  const uint32_t pw = leaf_smem_bytes(g.L), wpb = warps_per_block(g.L);
+  const uint32_t pw = leaf_smem_bytes(g.L), wpb = warps_per_block(g.L, g.leaf_warps);
   note_launch();
   k_leaf_pass<<<blocks_for(n, wpb, 152 * 16), wpb * 32, wpb * pw, s>>>(g, ctl, w, pw, rest_only ? 1 : 0);
   if (n > kLongRun) {  // only a batch this large can hold a run this long
@@ -971,6 +985,71 @@ void launch_leaf_pass(const Geo &g, Ctl *ctl, const Work &w, uint32_t n, cudaStr
   if (fast) launch_leaf64(g, ctl, w, n, s);
   launch_leaf_rest(g, ctl, w, n, fast, s);
   launch_degrees_batch(g, ctl, w, n, s);
+}
+
+// ---- many handles: the level-0 stages as one launch over all of them ---------------------------
+__global__ void __launch_bounds__(256, 5) k_m_leaf64(const ManyDesc *d, uint32_t plan) {
+  const ManyItem *it;
+  uint32_t sub, nb;
+  if (!many_block(d, plan, &it, &sub, &nb)) return;
+  leaf64_body(SubIdx{sub, nb}, it->g, it->ctl, it->w);
+}
+
+__global__ void k_m_leaf_pass(const ManyDesc *d, uint32_t plan) {
+  const ManyItem *it;
+  uint32_t sub, nb;
+  if (!many_block(d, plan, &it, &sub, &nb)) return;
+  leaf_pass_body(SubIdx{sub, nb}, it->g, it->ctl, it->w, it->per_warp, it->g.L == 64 ? 1 : 0);
+}
+
+__global__ void k_m_long_a(const ManyDesc *d, uint32_t plan) {
+  const ManyItem *it;
+  uint32_t sub, nb;
+  if (!many_block(d, plan, &it, &sub, &nb)) return;
+  long_a_body(SubIdx{sub, nb}, it->g, it->ctl, it->w, it->per_warp);
+}
+
+__global__ void k_m_long_b(const ManyDesc *d, uint32_t plan) {
+  const ManyItem *it;
+  uint32_t sub, nb;
+  if (!many_block(d, plan, &it, &sub, &nb)) return;
+  long_b_body(SubIdx{sub, nb}, it->g, it->ctl, it->w, it->per_warp);
+}
+
+__global__ void __launch_bounds__(256) k_m_deg_batch(const ManyDesc *d, uint32_t plan) {
+  const ManyItem *it;
+  uint32_t sub, nb;
+  if (!many_block(d, plan, &it, &sub, &nb)) return;
+  deg_batch_body(SubIdx{sub, nb}, it->g, it->ctl, it->w);
+}
+
+void prepare_many_leaf() {
+  cudaFuncSetAttribute(k_m_leaf_pass, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  cudaFuncSetAttribute(k_m_long_a, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+  cudaFuncSetAttribute(k_m_long_b, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+}
+
+void launch_many_leaf(const ManyDesc *d, const ManyPlans &pl, cudaStream_t s) {
+  if (pl.total[pl.leaf64]) {
+    note_launch();
+    k_m_leaf64<<<pl.total[pl.leaf64], 256, 0, s>>>(d, pl.leaf64);
+  }
+  for (uint32_t k = 0; k < pl.ngroups; k++) {
+    const ManyPlans::Group &gr = pl.group[k];
+    const uint32_t smem = gr.wpb * gr.per_warp;
+    note_launch();
+    k_m_leaf_pass<<<pl.total[gr.rest], gr.wpb * 32, smem, s>>>(d, gr.rest);
+    if (gr.long_a != ~0u) {
+      note_launch();
+      k_m_long_a<<<pl.total[gr.long_a], gr.wpb * 32, smem, s>>>(d, gr.long_a);
+      note_launch();
+      k_m_long_b<<<pl.total[gr.long_b], gr.wpb * 32, smem, s>>>(d, gr.long_b);
+    }
+  }
+  if (pl.total[pl.deg]) {
+    note_launch();
+    k_m_deg_batch<<<pl.total[pl.deg], 256, 0, s>>>(d, pl.deg);
+  }
 }
 
 void launch_tree_rebuild(const Geo &g, Ctl *ctl, const Work &w, uint32_t n, cudaStream_t s) {

@@ -54,6 +54,13 @@ def test_argument_errors_without_gpu(lib):
     assert lib.gpma_create(10, ctypes.byref(p), None, None, ctypes.byref(out)) == gp.GPMA_EINVAL
     p = gp.gpma_params(64, 0, 0, 0, 0, 0)
     assert lib.gpma_create(0, ctypes.byref(p), None, None, ctypes.byref(out)) == gp.GPMA_EINVAL
+    p = gp.gpma_params(64, 0, 0, 0, 0, 0, 3)  # warps per leaf-pass block not 1, 2, 4 or 8
+    assert lib.gpma_create(10, ctypes.byref(p), None, None, ctypes.byref(out)) == gp.GPMA_EINVAL
+    # gpma_update_many: a missing handle array, a null handle
+    n = ctypes.c_uint64(1)
+    assert lib.gpma_update_many(None, None, ctypes.byref(n), None, ctypes.byref(n), 1, None) == gp.GPMA_EINVAL
+    H = (ctypes.c_void_p * 1)(None)
+    assert lib.gpma_update_many(H, None, ctypes.byref(n), None, ctypes.byref(n), 1, None) == gp.GPMA_EINVAL
 
 
 def header_defines():

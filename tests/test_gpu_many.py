@@ -1,7 +1,7 @@
 """Batched many-graph update: gpma_update_many against per-graph sequential GPU
 runs and the oracle, slot for slot, on R-MAT sliding windows of uneven sizes
 (edge counts and batch sizes log-uniform), at the fixed leaf size and at the
-leaf size the autotuner picks."""
+leaf size and warps per leaf-pass block the autotuner picks."""
 import numpy as np
 import pytest
 
@@ -26,10 +26,11 @@ def host(t):
     return t.cpu().numpy().view(np.uint64)
 
 
-def run_many(wl, leaf_sizes, check_oracle=True):
+def run_many(wl, leaf_sizes, check_oracle=True, leaf_warps=None):
     n = wl.n_graphs
-    many = [gp.Graph(wl.n_vertices(i), leaf_size=leaf_sizes[i]) for i in range(n)]
-    seq = [gp.Graph(wl.n_vertices(i), leaf_size=leaf_sizes[i]) for i in range(n)]
+    wpb = leaf_warps or [0] * n
+    many = [gp.Graph(wl.n_vertices(i), leaf_size=leaf_sizes[i], leaf_warps=wpb[i]) for i in range(n)]
+    seq = [gp.Graph(wl.n_vertices(i), leaf_size=leaf_sizes[i], leaf_warps=wpb[i]) for i in range(n)]
     orc = [oracle.OraclePMA(wl.n_vertices(i), L=leaf_sizes[i]) for i in range(n)] if check_oracle else []
     init = [dev(w.initial) for w in wl.windows]
     gp.Graph.update_many(many, init, [None] * n)
@@ -73,16 +74,18 @@ def test_many_mixed_leaf_sizes():
 
 def test_many_at_tuned_leaf_size():
     wl = W.ManyGraphWorkload(4, 1 << 12, 1 << 15, 256, 1 << 12, steps=3, seed=5)
-    sizes = []
+    sizes, warps = [], []
     for i, w in enumerate(wl.windows):
         half = int(wl.batch[i]) // 2
         ins = w.stream[w.tail: w.tail + half]
         dels = w.stream[w.head: w.head + half]
-        L, table = tune.autotune_leaf_size(wl.n_vertices(i), dev(w.initial), dev(ins), dev(dels), reps=2)
-        assert set(table) == set(tune.LEAF_CANDIDATES) and all(t > 0 for t in table.values())
-        assert L == tune.pick_leaf_size(table)
+        L, wpb, ltab, wtab = tune.autotune(wl.n_vertices(i), dev(w.initial), dev(ins), dev(dels), reps=2)
+        assert set(ltab) == set(tune.LEAF_CANDIDATES) and all(t > 0 for t in ltab.values())
+        assert set(wtab) == set(tune.WARP_CANDIDATES) and all(t > 0 for t in wtab.values())
+        assert L == tune.pick_leaf_size(ltab) and wpb == tune.pick_warps(wtab)
         sizes.append(L)
-    run_many(wl, sizes)
+        warps.append(wpb)
+    run_many(wl, sizes, leaf_warps=warps)
 
 
 def test_many_edge_cases():
@@ -104,6 +107,69 @@ def test_many_edge_cases():
     assert np.array_equal(host(b.layout()), before_b)
     assert a.num_edges() == 50 and b.num_edges() == 100
     assert a.check() == 0 and b.check() == 0
+
+
+def test_many_batched_stages_vary_per_call():
+    """One set of handles, several calls with different batch sizes (the batched
+    graph is captured once; the per-call plan table sizes every launch): one-block
+    and radix front ends in the same call, a batch that needs four search words a
+    thread (more than 2^19 keys), leaf sizes 32..1024 with the tuned warps per
+    block of the one-warp-per-leaf pass, a raw-key handle, and inserts crowded into
+    a few rows so that leaves overflow and the handles' merge levels run in their
+    own graph branches.  After every call each handle equals the same handle
+    updated alone and the oracle, slot for slot."""
+    gp.build()
+    rng = np.random.default_rng(21)
+    specs = [(1 << 12, 32, 0), (1 << 14, 64, 0), (1 << 15, 128, 2), (1 << 16, 256, 4), (1 << 13, 512, 1),
+             (1 << 12, 1024, 8), (1 << 20, 64, 0), (1 << 14, 16, 0)]
+    many, seq, orc, streams = [], [], [], []
+    for i, (V, L, wpb) in enumerate(specs):
+        raw = i == len(specs) - 1
+        many.append(gp.Graph(V, leaf_size=L, leaf_warps=wpb, raw_keys=raw))
+        seq.append(gp.Graph(V, leaf_size=L, leaf_warps=wpb, raw_keys=raw))
+        orc.append(oracle.OraclePMA(V, L=L, raw_keys=raw))
+        scale = int(np.log2(V))
+        streams.append(W.rmat_stream(scale, (1 << 20) + 3 * 600_000 if V == 1 << 20 else 6 * V, seed=300 + i))
+    wins = [W.SlidingWindow(st, len(st) // 3 if len(st) < 1 << 20 else 1 << 20) for st in streams]
+    init = [dev(w.initial) for w in wins]
+    gp.Graph.update_many(many, init, [None] * len(specs))
+    for i in range(len(specs)):
+        seq[i].update(init[i])
+        assert orc[i].update(wins[i].initial)[0] == 0
+
+    def hot_rows(i, n):
+        V = specs[i][0]
+        rows = rng.integers(0, V, 4, dtype=np.uint64)
+        cols = rng.integers(0, V, n, dtype=np.uint64)
+        k = (rows[rng.integers(0, 4, n)] << np.uint64(32)) | cols
+        k = k[(k >> np.uint64(32)) != (k & np.uint64(0xFFFFFFFF))]
+        return np.unique(k)
+
+    for step, sizes in enumerate([(100, 3000, 20_000, 50, 9000, 200, 600_000, 700),
+                                  (5000, 64, 4096, 4097, 300, 10_000, 2000, 8000),
+                                  (2, 20_000, 128, 30_000, 6000, 4000, 100_000, 50)]):
+        ins_l, del_l = [], []
+        for i, b in enumerate(sizes):
+            ins, dels = wins[i].slide(max(1, b // 2))
+            if step == 1 and i in (1, 2, 3):  # crowded rows: leaves overflow, merge levels run
+                extra = hot_rows(i, 3000)
+                ins = np.unique(np.concatenate([ins, extra]))
+            ins_l.append(ins)
+            del_l.append(dels)
+        gp.Graph.update_many(many, [dev(x) for x in ins_l], [dev(x) for x in del_l])
+        for i in range(len(specs)):
+            seq[i].update(dev(ins_l[i]), dev(del_l[i]))
+            assert orc[i].update(ins_l[i], del_l[i])[0] == 0
+        torch.cuda.synchronize()
+        for i in range(len(specs)):
+            many[i].status()
+            lm = host(many[i].layout())
+            assert np.array_equal(lm, host(seq[i].layout())), f"step {step} graph {i}: batched != alone"
+            lo = orc[i].layout()
+            assert lm.size == lo.size and np.count_nonzero(lm != lo) == 0, f"step {step} graph {i}: != oracle"
+            assert many[i].check() == 0
+    for g in many + seq:
+        g.close()
 
 
 def test_many_full_size_graphs():

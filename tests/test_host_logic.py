@@ -47,6 +47,12 @@ def test_pick_leaf_size():
         with pytest.raises(ValueError):
             tune.pick_leaf_size(bad)
     assert all(L & (L - 1) == 0 for L in tune.LEAF_CANDIDATES)
+    assert tune.pick_warps({1: 0.5, 2: 0.3, 4: 0.4, 8: 0.6}) == 2
+    assert tune.pick_warps({2: 0.3, 8: 0.3}) == 8  # tie: more warps
+    with pytest.raises(ValueError):
+        tune.pick_warps({3: 0.1})
+    with pytest.raises(ValueError):
+        tune.pick_warps({})
 
 
 def _req(rid, kind, t, n=0):
