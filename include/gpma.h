@@ -109,6 +109,12 @@ typedef struct {
   uint64_t covered_leaves; /* leaves rewritten by merges (0 on a resize) */
   uint64_t merges[GPMA_MAX_LEVELS]; /* segments merged at each level, Sec. 5.2 level order */
   uint64_t delete_leaves;  /* distinct leaves holding a delete that took effect */
+  uint32_t model_sorted;   /* 1: the batch was sorted by bucketing its keys on the learned
+                              model's pieces and sorting each bucket (learned handles); 0:
+                              by the radix passes (plain handles, small batches, no trained
+                              model yet, or a bucket too large for shared memory).  Either
+                              way the sorted batch, and so every result, is the same */
+  uint32_t pad;
 } gpma_stats;
 
 /* Create an array for vertices [0, n_vertices) (n_vertices in [1, 2^31]; ignored

@@ -46,6 +46,7 @@ class gpma_stats(C.Structure):
         ("levels_climbed", C.c_uint32), ("resized", C.c_uint32), ("alg_bytes", C.c_uint64),
         ("touched_leaves", C.c_uint64), ("covered_leaves", C.c_uint64),
         ("merges", C.c_uint64 * GPMA_MAX_LEVELS), ("delete_leaves", C.c_uint64),
+        ("model_sorted", C.c_uint32), ("pad", C.c_uint32),
     ]
 
     def as_dict(self) -> dict:

@@ -332,7 +332,8 @@ void free_work(gpma *h, cudaStream_t s) {
   Work &w = h->w;
   void *ptrs[] = {h->bufA,   h->bufB,     w.ukey,  w.utag,     w.uleaf,   w.run_start, w.eflag,
                   w.rleaf,   w.rdelta,    w.rinfo, w.rdel,     w.pkey,    w.pleaf,     w.erun, w.eleaf,
-                  w.elvl,    w.etop,      w.seg_node, w.seg_top, w.seg_pstart, w.seg_lpre, w.status, w.rs};
+                  w.elvl,    w.etop,      w.seg_node, w.seg_top, w.seg_pstart, w.seg_lpre, w.status, w.rs,
+                  w.lbkt,    w.lcnt,      w.lcur};
   for (void *p : ptrs) dfree(h, p, s);
   memset(&h->w, 0, sizeof(Work));
   h->bufA = h->bufB = nullptr;
@@ -356,7 +357,8 @@ int ensure_work(gpma *h, uint64_t n, cudaStream_t s) {
             dalloc(h, &w.pleaf, cap, s) && dalloc(h, &w.erun, c1, s) && dalloc(h, &w.eleaf, cap, s) && dalloc(h, &w.elvl, cap, s) &&
             dalloc(h, &w.etop, cap, s) && dalloc(h, &w.seg_node, c1, s) && dalloc(h, &w.seg_top, c1, s) &&
             dalloc(h, &w.seg_pstart, c1, s) && dalloc(h, &w.seg_lpre, c1, s) && dalloc(h, &w.status, st, s) &&
-            dalloc(h, &w.rs, front_scratch_words(cap), s);
+            dalloc(h, &w.rs, front_scratch_words(cap), s) && dalloc(h, &w.lbkt, cap, s) &&
+            dalloc(h, &w.lcnt, (uint64_t)kPieces + 1, s) && dalloc(h, &w.lcur, (uint64_t)kPieces, s);
   if (!ok) {
     free_work(h, s);
     return GPMA_ENOMEM;
@@ -572,7 +574,12 @@ bool capture_update(gpma *h, FrontArgs &f, uint32_t nb, bool stats, bool grow, G
                          t);
     if (h->mhead) launch_train_model(g, h->mhead, h->mpieces, h->ctl, true, t);
   };
-  if (!small_front(nb)) launch_front(f, nb, gc.cap);
+  if (learned_front(f.prep, h->mhead != nullptr, nb)) {  // sorted by bucketing on the model's pieces
+    launch_lfront_sort(f, h->w.lbkt, h->w.lcnt, h->w.lcur, nb, gc.cap);
+    launch_front_search(f, nb, gc.cap);
+  } else if (!small_front(nb)) {
+    launch_front(f, nb, gc.cap);
+  }
   // (an IF node around the general pass, which a sliding window rarely needs,
   // measured slower than its three kernels returning at once)
   launch_leaf_pass(g, h->ctl, h->w, nb, gc.cap);
@@ -732,8 +739,6 @@ int update(gpma *h, const uint64_t *ins, uint64_t n_ins, const uint64_t *del, ui
   // in a replayed graph and in directly launched kernels alike
   uint64_t nb_front = kSmallBatch;
   while (nb_front < n) nb_front <<= 1;
-  if (small_front(n)) launch_small_front(f, s);
-  else launch_prep(f, nb_front, s);
   // the root can only refuse inserts when the count might exceed its bound
   const bool may_fail = h->count_ub + n_ins > h->geo.maxc[h->geo.h];
   // such a batch still replays a graph (no host wait) when one level of growth
@@ -745,8 +750,13 @@ int update(gpma *h, const uint64_t *ins, uint64_t n_ins, const uint64_t *del, ui
     level_bounds(h->L, h->geo.h + 1, h->tau0, h->tauh, mx);
     grow = h->count_ub + n_ins <= mx[h->geo.h + 1] && ensure_spare(h, s) == GPMA_OK;
   }
+  const bool replay = (!may_fail || grow) && h->graphs->enabled;
+  const bool by_model = !small_front(n) && replay && learned_front(pa, h->mhead != nullptr, n);
+  if (small_front(n)) launch_small_front(f, s);
+  else if (by_model) launch_lprep(f, h->w.lbkt, h->w.lcnt, nb_front, s);  // the graph sorts by model piece
+  else launch_prep(f, nb_front, s);
   bool resized = false;
-  if ((!may_fail || grow) && h->graphs->enabled) {
+  if (replay) {
     // replay: sort .. segment merge as one graph, grids sized for the bucket
     const uint64_t bucket = nb_front;  // one graph serves every batch of the fused front end
     const uint32_t nb = (uint32_t)bucket;
@@ -844,6 +854,7 @@ int update(gpma *h, const uint64_t *ins, uint64_t n_ins, const uint64_t *del, ui
   stats->n_ignored = n - c.n_inserted - c.n_deleted;
   stats->touched_leaves = c.nruns;
   stats->delete_leaves = c.st_del_leaves;
+  stats->model_sorted = by_model ? 1u : 0u;
   stats->resized = resized ? 1 : (shrunk ? 2 : 0);
   for (int i = 0; i < GPMA_MAX_LEVELS && i < kMaxLv; i++) stats->merges[i] = c.merges[i];
   stats->merges[0] = c.n_merged0;

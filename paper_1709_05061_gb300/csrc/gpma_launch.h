@@ -66,6 +66,9 @@ struct Work {
   uint32_t *seg_lpre;
   uint64_t *status;
   uint32_t *rs;       // front_scratch_words(cap) words for the radix front end
+  uint16_t *lbkt;     // model-bucketed front end: bucket (model piece) of every key
+  uint32_t *lcnt;     // kPieces + 1 bucket counts, then offsets
+  uint32_t *lcur;     // kPieces scatter cursors
   uint32_t cap;       // capacity of the per-key arrays
 };
 
@@ -85,6 +88,20 @@ void launch_prep(const FrontArgs &f, uint64_t nb, cudaStream_t s);
 // the radix passes, unique/cancel + leaf search, survivors and run heads
 void launch_front(const FrontArgs &f, uint64_t nb, cudaStream_t s);
 uint64_t front_scratch_words(uint64_t nb);  // size of FrontArgs::rs for batches of up to nb keys
+// The model-bucketed front end of a learned handle (large batches, inside a captured
+// graph): launch_lprep (direct, reads the batch) validates and compresses every key
+// and counts it in its bucket (the model piece its key routes to; the top key bits
+// before the model is trained); in the graph, launch_lfront_sort turns the counts into
+// offsets, scatters the words into their buckets and sorts every bucket (in shared
+// memory up to kLSortMax words, else in place); launch_front_search then finishes as
+// after the radix passes (launch_front_radix), which plain handles keep.
+constexpr uint32_t kLSortMax = 4096;  // words of the largest bucket sorted in shared memory
+bool learned_front(const PrepArgs &a, bool has_model, uint64_t n);
+void launch_lprep(const FrontArgs &f, uint16_t *bkt, uint32_t *cnt, uint64_t nb, cudaStream_t s);
+void launch_lfront_sort(const FrontArgs &f, const uint16_t *bkt, uint32_t *cnt, uint32_t *cur, uint64_t nb,
+                        cudaStream_t s);
+void launch_front_radix(const FrontArgs &f, uint64_t nb, cudaStream_t s);
+void launch_front_search(const FrontArgs &f, uint64_t nb, cudaStream_t s);
 
 // k_update.cu
 // level 0: k_leaf64 (L = 64, runs of at most 32 keys), then the general pass (the

@@ -150,7 +150,9 @@ template <int ITEMS>
 __global__ void __launch_bounds__(kSortThreads) k_prep(PrepArgs a, const uint64_t *__restrict__ ins,
                                                        const uint64_t *__restrict__ del, uint64_t *__restrict__ out,
                                                        uint32_t *__restrict__ hist, uint32_t *__restrict__ H0,
-                                                       uint32_t T, Ctl *ctl) { prep_body<ITEMS>(GridIdx{}, a, ins, del, out, hist, H0, T, ctl); }
+                                                       uint32_t T, Ctl *ctl) {
+  prep_body<ITEMS>(GridIdx{}, a, ins, del, out, hist, H0, T, ctl);
+}
 
 // Pass `pass`, digits d = block, block + nblocks, ... < radix: H[d * T + t] (keys
 // of tile t with digit d) becomes the position of the tile's first such key: the
@@ -703,6 +705,163 @@ __global__ void __launch_bounds__(kSearchThreads) k_twrite(PrepArgs a, const uin
                                                            uint32_t *__restrict__ run_start,
                                                            uint32_t *__restrict__ run_leaf, const Ctl *ctl) { twrite_body<Q>(GridIdx{}, a, sorted, lfull, ts, gridDim.x, ukey, utag, uleaf, run_start, run_leaf, ctl); }
 
+// ---- model-bucketed front end (learned handles) ----------------------------------------------
+// The model's pieces split the keys into kPieces ordered ranges whose sizes follow
+// the array's own key distribution: bucket(k) = the last piece whose boundary is
+// <= k, a non-decreasing function of k.  Bucketing the batch by piece and sorting
+// every bucket therefore sorts the batch, in one scatter instead of the radix
+// passes.  Equal keys keep inserts before deletes (the bucket sort compares
+// (key, tag)), so the sorted words equal the stable radix sort's.  Before the model
+// is trained the bucket is the top bits of the compressed key, also non-decreasing.
+
+// (key, tag) order of a sort word (tag in bit 63, at most 62 key bits)
+__device__ __forceinline__ uint64_t word_order(uint64_t w) { return ((w & ~kTagBit) << 1) | (w >> 63); }
+
+// validation and compression as in k_prep, and the bucket of every key
+template <int ITEMS>
+__global__ void __launch_bounds__(kSortThreads) k_lprep(PrepArgs a, const uint64_t *__restrict__ ins,
+                                                        const uint64_t *__restrict__ del, uint64_t *__restrict__ out,
+                                                        uint16_t *__restrict__ bkt, uint32_t *__restrict__ cnt,
+                                                        Ctl *ctl, const ModelHead *mhead,
+                                                        const Piece *__restrict__ mpieces) {
+  const ModelHead hd = *mhead;
+  const uint32_t top = a.sbits > 12 ? a.sbits - 12 : 0;  // key-bit buckets: kPieces = 2^12
+  const uint32_t n = a.n_ins + a.n_del;
+  bool bad = false;
+#pragma unroll
+  for (int r = 0; r < ITEMS; r++) {
+    const uint32_t i = blockIdx.x * (kSortThreads * ITEMS) + r * kSortThreads + threadIdx.x;
+    if (i >= n) break;
+    const uint32_t tag = i >= a.n_ins;
+    const uint64_t key = tag ? del[i - a.n_ins] : ins[i];
+    const uint64_t src = key >> 32, dst = key & 0xFFFFFFFFull;
+    const bool ok = src < a.V && dst < a.V;
+    bad |= !ok;
+    const uint64_t w = ok ? compress(key, tag, a) : 0ull;
+    out[i] = w;
+    uint32_t b;
+    if (hd.valid) {
+      const int32_t pi = ok ? model_route(hd, mpieces, key) : 0;
+      b = pi < 0 ? 0u : (uint32_t)pi;
+    } else {
+      b = (uint32_t)((w & ~kTagBit) >> top);
+    }
+    bkt[i] = (uint16_t)b;
+    atomicAdd(&cnt[b], 1u);
+  }
+  if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(&ctl->err, kErrKey);
+}
+
+// bucket counts -> offsets (cnt, cnt[kPieces] = all) and scatter cursors (cur)
+__global__ void __launch_bounds__(1024) k_lscan(const Ctl *ctl, uint32_t *__restrict__ cnt,
+                                                uint32_t *__restrict__ cur) {
+  __shared__ uint32_t wsum[33];
+  if (ctl->err) return;  // nothing of the batch is applied
+  const uint32_t t = threadIdx.x;
+  constexpr uint32_t kPer = kPieces / 1024;
+  uint32_t v[kPer], loc = 0;
+#pragma unroll
+  for (uint32_t q = 0; q < kPer; q++) {
+    v[q] = cnt[t * kPer + q];
+    loc += v[q];
+  }
+  uint32_t total;
+  uint32_t run = block_excl_scan(loc, wsum, &total);
+#pragma unroll
+  for (uint32_t q = 0; q < kPer; q++) {
+    cnt[t * kPer + q] = run;
+    cur[t * kPer + q] = run;
+    run += v[q];
+  }
+  if (t == 0) cnt[kPieces] = total;
+}
+
+template <int ITEMS>
+__global__ void __launch_bounds__(kSortThreads) k_lscatter(const uint64_t *__restrict__ src,
+                                                           const uint16_t *__restrict__ bkt,
+                                                           uint32_t *__restrict__ cur, uint64_t *__restrict__ dst,
+                                                           Ctl *ctl) {
+  if (ctl->err) return;
+  const uint32_t n = ctl->n;
+#pragma unroll
+  for (int r = 0; r < ITEMS; r++) {
+    const uint32_t i = blockIdx.x * (kSortThreads * ITEMS) + r * kSortThreads + threadIdx.x;
+    if (i >= n) break;
+    const uint32_t b = bkt[i];
+    const uint32_t pos = b < kPieces ? atomicAdd(&cur[b], 1u) : n;
+    if (pos < n) dst[pos] = src[i];
+    else atomicOr(&ctl->err, kErrInternal);  // cannot happen when the counts are consistent
+  }
+}
+
+// One bucket per block, sorted by (key, tag): in shared memory (bitonic) up to
+// kLSortMax words; a larger bucket (many new edges of one row, or key-bit buckets)
+// in place in dst with the bitonic network whose comparators all put the smaller
+// word first, positions past the bucket counting as +infinity (so a comparator
+// that reaches past it does nothing).
+__global__ void __launch_bounds__(256) k_lsort(const uint64_t *__restrict__ src, uint64_t *__restrict__ dst,
+                                               const uint32_t *__restrict__ off, Ctl *ctl) {
+  __shared__ uint64_t sk[kLSortMax];
+  if (ctl->err) return;
+  const uint32_t t = threadIdx.x, nt = blockDim.x;
+  const uint32_t o0 = off[blockIdx.x], nb = off[blockIdx.x + 1] - o0;
+  if (nb == 0) return;
+  if (o0 + nb > ctl->n) {  // cannot happen: the offsets count the batch's words
+    if (t == 0) atomicOr(&ctl->err, kErrInternal);
+    return;
+  }
+  uint32_t P = 1;
+  while (P < nb) P <<= 1;
+  if (nb <= kLSortMax) {
+    for (uint32_t i = t; i < P; i += nt) sk[i] = i < nb ? word_order(src[o0 + i]) : ~0ull;  // padding sorts last
+    __syncthreads();
+    for (uint32_t k = 2; k <= P; k <<= 1) {
+      for (uint32_t j = k >> 1; j > 0; j >>= 1) {
+        for (uint32_t i = t; i < P / 2; i += nt) {
+          const uint32_t lo = ((i & ~(j - 1)) << 1) | (i & (j - 1)), hi = lo + j;
+          const uint64_t x = sk[lo], y = sk[hi];
+          if ((x > y) == ((lo & k) == 0)) {
+            sk[lo] = y;
+            sk[hi] = x;
+          }
+        }
+        __syncthreads();
+      }
+    }
+    for (uint32_t i = t; i < nb; i += nt) {
+      const uint64_t sw = sk[i];
+      dst[o0 + i] = (sw >> 1) | ((sw & 1ull) << 63);
+    }
+    return;
+  }
+  uint64_t *d = dst + o0;
+  if (src != dst)
+    for (uint32_t i = t; i < nb; i += nt) d[i] = src[o0 + i];
+  __syncthreads();
+  for (uint32_t k = 2; k <= P; k <<= 1) {
+    for (uint32_t j = k >> 1; j > 0; j >>= 1) {
+      for (uint32_t i = t; i < P / 2; i += nt) {
+        uint32_t lo, hi;
+        if (j == (k >> 1)) {  // first step of a merge: mirror inside the block of k
+          lo = (i / j) * k + (i % j);
+          hi = (i / j) * k + k - 1 - (i % j);
+        } else {
+          lo = ((i & ~(j - 1)) << 1) | (i & (j - 1));
+          hi = lo + j;
+        }
+        if (hi < nb) {
+          const uint64_t x = d[lo], y = d[hi];
+          if (word_order(x) > word_order(y)) {
+            d[lo] = y;
+            d[hi] = x;
+          }
+        }
+      }
+      __syncthreads();
+    }
+  }
+}
+
 // ---- host launchers ----------------------------------------------------------------------
 static uint32_t grid_for(uint64_t n, uint32_t per_block, uint32_t cap) {
   uint64_t g = (n + per_block - 1) / per_block;
@@ -752,7 +911,10 @@ void launch_prep(const FrontArgs &f, uint64_t nb, cudaStream_t s) {
   k_prep<kSortItems><<<T, kSortThreads, 0, s>>>(a, f.ins, f.del, f.bufA, f.hist, f.rs, T, f.ctl);
 }
 
-void launch_front(const FrontArgs &f, uint64_t nb, cudaStream_t s) {
+// the words after the radix passes (bufA for an even pass count, else bufB)
+static uint64_t *sorted_words(const FrontArgs &f) { return (f.prep.npass & 1) ? f.bufB : f.bufA; }
+
+void launch_front_radix(const FrontArgs &f, uint64_t nb, cudaStream_t s) {
   const PrepArgs &a = f.prep;
   const uint32_t T = front_tiles(nb), radix = 1u << a.dbits;
   uint32_t *H[2] = {f.rs, f.rs + (uint64_t)256 * T};
@@ -766,6 +928,12 @@ void launch_front(const FrontArgs &f, uint64_t nb, cudaStream_t s) {
     k_rscatter<kSortItems><<<T, kSortThreads, 0, s>>>(src, dst, O, Hn, T, shift, nshift, a.dbits, f.ctl);
     uint64_t *t = src; src = dst; dst = t;
   }
+}
+
+void launch_front_search(const FrontArgs &f, uint64_t nb, cudaStream_t s) {
+  const PrepArgs &a = f.prep;
+  const uint32_t T = front_tiles(nb);
+  const uint64_t *src = sorted_words(f);
   const uint32_t T1 = search_tiles(nb);
   uint32_t *q = f.rs + (uint64_t)512 * T;
   const uint32_t K = T1 + 1;
@@ -787,6 +955,39 @@ void launch_front(const FrontArgs &f, uint64_t nb, cudaStream_t s) {
   else
     k_twrite<1><<<T1, kSearchThreads, 0, s>>>(a, src, f.lfull, ts, f.ukey, f.utag, f.uleaf, f.run_start,
                                               f.run_leaf, f.ctl);
+}
+
+void launch_front(const FrontArgs &f, uint64_t nb, cudaStream_t s) {
+  launch_front_radix(f, nb, s);
+  launch_front_search(f, nb, s);
+}
+
+// sorted (key, tag) words need one bit more than the key: graph batches only
+// (no guards, so at most 62 sorted bits), with a model, above the one-block size
+bool learned_front(const PrepArgs &a, bool has_model, uint64_t n) {
+  return !a.raw && !a.allow_guards && has_model && a.sbits <= 62 && !small_front(n);
+}
+
+void launch_lprep(const FrontArgs &f, uint16_t *bkt, uint32_t *cnt, uint64_t nb, cudaStream_t s) {
+  const PrepArgs &a = f.prep;
+  const uint64_t n = (uint64_t)a.n_ins + a.n_del;
+  cudaMemsetAsync(cnt, 0, sizeof(uint32_t) * (kPieces + 1), s);
+  note_launch();
+  k_init_batch<<<1, 256, 0, s>>>(f.ctl, f.hist, a.npass * 256u, (uint32_t)n);
+  note_launch();
+  k_lprep<kSortItems><<<front_tiles(nb), kSortThreads, 0, s>>>(a, f.ins, f.del, f.bufA, bkt, cnt, f.ctl, f.mhead,
+                                                                f.mpieces);
+}
+
+void launch_lfront_sort(const FrontArgs &f, const uint16_t *bkt, uint32_t *cnt, uint32_t *cur, uint64_t nb,
+                        cudaStream_t s) {
+  note_launch();
+  k_lscan<<<1, 1024, 0, s>>>(f.ctl, cnt, cur);
+  const uint32_t *off = cnt;
+  note_launch();
+  k_lscatter<kSortItems><<<front_tiles(nb), kSortThreads, 0, s>>>(f.bufA, bkt, cur, f.bufB, f.ctl);
+  note_launch();
+  k_lsort<<<kPieces, 256, 0, s>>>(f.bufB, sorted_words(f), off, f.ctl);
 }
 
 bool search_wide(uint64_t n) { return search_per(n) == 4; }
@@ -821,7 +1022,8 @@ __global__ void __launch_bounds__(kSortThreads) k_m_prep(const ManyDesc *d, uint
   uint32_t sub, nb;
   // every block of the handle takes the prep ticket: the plan gives it at most T blocks
   if (!many_block(d, plan, &it, &sub, &nb) || it->small) return;
-  prep_body<kSortItems>(SubIdx{sub, nb}, it->prep, it->ins, it->del, it->bufA, it->hist, it->w.rs, it->T, it->ctl);
+  prep_body<kSortItems>(SubIdx{sub, nb}, it->prep, it->ins, it->del, it->bufA, it->hist, it->w.rs, it->T,
+                        it->ctl);
 }
 
 __global__ void __launch_bounds__(256) k_m_rcolscan(const ManyDesc *d, uint32_t plan, uint32_t p) {

@@ -54,10 +54,14 @@ def mixed_batch(rng, V, live, n):
 
 
 def run_pair(V, batches, plain):
+    """Apply the batches to a handle and to the oracle, comparing stats and layout
+    after each; returns, per batch, whether the model-bucketed sort took it."""
     g = gp.Graph(V, leaf_size=64, plain_search=plain)
     o = oracle.OraclePMA(V, L=64)
+    by_model = []
     for ins, dels in batches:
         st = g.update(dev(ins), dev(dels), stats=True)
+        by_model.append(st["model_sorted"])
         rc, so = o.update(ins, dels)
         assert rc == 0
         for k in STAT_KEYS:
@@ -67,6 +71,7 @@ def run_pair(V, batches, plain):
     assert np.array_equal(host(g.export_sorted()), o.export_sorted())
     assert g.check() == 0
     g.close()
+    return by_model
 
 
 @pytest.mark.parametrize("plain", [False, True])
@@ -80,7 +85,36 @@ def test_batch_sizes_around_the_front_end_limits(plain):
         ins, dels = mixed_batch(rng, V, live, n)
         batches.append((ins, dels))
         live = np.array(sorted(set(live.tolist()) | set(ins.tolist()) - set(dels.tolist())), np.uint64)
-    run_pair(V, batches, plain)
+    by_model = run_pair(V, batches, plain)
+    # the plain handle always sorts by radix passes; the learned one buckets the
+    # batches above the one-block size by model piece once they replay a graph
+    assert not any(by_model) if plain else any(by_model[2:]), by_model
+
+
+def test_model_bucketed_sort():
+    """A learned handle with room in its root (half of its edges deleted) replays
+    its graph for every batch, so the batches above the one-block size are sorted by
+    bucketing on the model's pieces: layout and stats equal the oracle's at sizes
+    from 4097 to 2^19 + 1 keys (with duplicates, cancellations, present inserts and
+    absent deletes), and for a batch crowding 20,000 new edges into one short row,
+    whose bucket is too large for shared memory and is sorted in place."""
+    V = 1 << 16
+    base = W.rmat_stream(16, 1_200_000, seed=63)
+    rng = np.random.default_rng(63)
+    live = base[600_000:]
+    batches = [(base, np.zeros(0, np.uint64)), (np.zeros(0, np.uint64), base[:600_000])]
+    for n in (5462, 6000, 8193, 30_000, 65_537, 200_000, 524_289, 800_000):  # about 3n/4 keys each
+        ins, dels = mixed_batch(rng, V, live, n)
+        batches.append((ins, dels))
+        live = np.array(sorted(set(live.tolist()) | set(ins.tolist()) - set(dels.tolist())), np.uint64)
+    srcs, deg = np.unique(live >> np.uint64(32), return_counts=True)
+    hub = np.uint64(srcs[np.argmin(deg)])  # a short row: it lies within one or two model pieces
+    star = (hub << np.uint64(32)) | rng.permutation(V)[:20_000].astype(np.uint64)
+    batches.append((star, np.zeros(0, np.uint64)))
+    by_model = run_pair(V, batches, False)
+    # every batch after the bulk load replays a graph: above the one-block size the model sorts it
+    expect = [int(ins.size + dels.size > 4096) for ins, dels in batches[1:]]
+    assert by_model[1:] == expect and sum(expect) >= 7, (by_model, expect)
 
 
 @pytest.mark.parametrize("hot", [3000, 12_000, 20_000, 60_000])
@@ -96,7 +130,9 @@ def test_skewed_batches(hot):
     ins, dels = mixed_batch(rng, V, base, 10_000)
     ins = rng.permutation(np.concatenate([ins, star]))
     for plain in (False, True):
-        run_pair(V, [(base, np.zeros(0, np.uint64)), (ins, dels), (dels, star[: hot // 2])], plain)
+        by_model = run_pair(V, [(base, np.zeros(0, np.uint64)), (ins, dels), (dels, star[: hot // 2])], plain)
+        if plain:
+            assert not any(by_model)
 
 
 def test_invalid_key_in_a_large_batch_changes_nothing():
