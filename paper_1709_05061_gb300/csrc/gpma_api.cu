@@ -751,9 +751,12 @@ int update(gpma *h, const uint64_t *ins, uint64_t n_ins, const uint64_t *del, ui
     grow = h->count_ub + n_ins <= mx[h->geo.h + 1] && ensure_spare(h, s) == GPMA_OK;
   }
   const bool replay = (!may_fail || grow) && h->graphs->enabled;
-  const bool by_model = !small_front(n) && replay && learned_front(pa, h->mhead != nullptr, n);
+  // the model-bucketed sort for every batch that cannot need more than one doubling
+  // (replayed, or launched directly when graphs are off); a bulk load keeps the radix
+  // passes (a model trained on a nearly empty array gives very uneven buckets)
+  const bool by_model = (!may_fail || grow) && learned_front(pa, h->mhead != nullptr, n);
   if (small_front(n)) launch_small_front(f, s);
-  else if (by_model) launch_lprep(f, h->w.lbkt, h->w.lcnt, nb_front, s);  // the graph sorts by model piece
+  else if (by_model) launch_lprep(f, h->w.lbkt, h->w.lcnt, nb_front, s);  // buckets by model piece
   else launch_prep(f, nb_front, s);
   bool resized = false;
   if (replay) {
@@ -779,7 +782,12 @@ int update(gpma *h, const uint64_t *ins, uint64_t n_ins, const uint64_t *del, ui
   } else {
     {
       Phase ph(h->prof, GPMA_PROF_SORT, s);
-      if (!small_front(n)) launch_front(f, nb_front, s);
+      if (by_model) {
+        launch_lfront_sort(f, h->w.lbkt, h->w.lcnt, h->w.lcur, nb_front, s);
+        launch_front_search(f, nb_front, s);
+      } else if (!small_front(n)) {
+        launch_front(f, nb_front, s);
+      }
     }
     {
       Phase ph(h->prof, GPMA_PROF_LEAF, s);
