@@ -204,9 +204,10 @@ int gpma_pagerank(gpma_t h, uint32_t iters, float damping, float *d_rank, void *
  * A new snapshot, or a gpma_pagerank call (which rebuilds the same buffers and
  * discards the snapshot), must not start before the runs on the previous one have
  * finished; runs share their scratch with each other and with gpma_pagerank, so
- * they must not overlap on the GPU either.  gpma_pagerank_snapshot returns GPMA_EINVAL for a handle that sums by
- * the push pass (GPMA_PUSH_PAGERANK, or more than 2^24 vertices), which reads the
- * array itself; gpma_pagerank_run returns GPMA_EINVAL without a snapshot. */
+ * they must not overlap on the GPU either.  gpma_pagerank_snapshot returns
+ * GPMA_EINVAL for a handle that sums by the push pass (GPMA_PUSH_PAGERANK, or more
+ * than 2^25 vertices), which reads the array itself; gpma_pagerank_run returns
+ * GPMA_EINVAL without a snapshot. */
 int gpma_pagerank_snapshot(gpma_t h, void *stream);
 int gpma_pagerank_run(gpma_t h, uint32_t iters, float damping, float *d_rank, void *stream);
 

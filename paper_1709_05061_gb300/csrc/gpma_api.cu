@@ -333,7 +333,7 @@ void free_work(gpma *h, cudaStream_t s) {
   void *ptrs[] = {h->bufA,   h->bufB,     w.ukey,  w.utag,     w.uleaf,   w.run_start, w.eflag,
                   w.rleaf,   w.rdelta,    w.rinfo, w.rdel,     w.pkey,    w.pleaf,     w.erun, w.eleaf,
                   w.elvl,    w.etop,      w.seg_node, w.seg_top, w.seg_pstart, w.seg_lpre, w.status, w.rs,
-                  w.lbkt,    w.lcnt,      w.lcur};
+                  w.lbkt,    w.lcnt,      w.lrank};
   for (void *p : ptrs) dfree(h, p, s);
   memset(&h->w, 0, sizeof(Work));
   h->bufA = h->bufB = nullptr;
@@ -358,7 +358,7 @@ int ensure_work(gpma *h, uint64_t n, cudaStream_t s) {
             dalloc(h, &w.etop, cap, s) && dalloc(h, &w.seg_node, c1, s) && dalloc(h, &w.seg_top, c1, s) &&
             dalloc(h, &w.seg_pstart, c1, s) && dalloc(h, &w.seg_lpre, c1, s) && dalloc(h, &w.status, st, s) &&
             dalloc(h, &w.rs, front_scratch_words(cap), s) && dalloc(h, &w.lbkt, cap, s) &&
-            dalloc(h, &w.lcnt, (uint64_t)kPieces + 1, s) && dalloc(h, &w.lcur, (uint64_t)kPieces, s);
+            dalloc(h, &w.lcnt, (uint64_t)kPieces + 1, s) && dalloc(h, &w.lrank, cap, s);
   if (!ok) {
     free_work(h, s);
     return GPMA_ENOMEM;
@@ -575,7 +575,7 @@ bool capture_update(gpma *h, FrontArgs &f, uint32_t nb, bool stats, bool grow, G
     if (h->mhead) launch_train_model(g, h->mhead, h->mpieces, h->ctl, true, t);
   };
   if (learned_front(f.prep, h->mhead != nullptr, nb)) {  // sorted by bucketing on the model's pieces
-    launch_lfront_sort(f, h->w.lbkt, h->w.lcnt, h->w.lcur, nb, gc.cap);
+    launch_lfront_sort(f, h->w.lbkt, h->w.lrank, h->w.lcnt, nb, gc.cap);
     launch_front_search(f, nb, gc.cap);
   } else if (!small_front(nb)) {
     launch_front(f, nb, gc.cap);
@@ -756,7 +756,7 @@ int update(gpma *h, const uint64_t *ins, uint64_t n_ins, const uint64_t *del, ui
   // passes (a model trained on a nearly empty array gives very uneven buckets)
   const bool by_model = (!may_fail || grow) && learned_front(pa, h->mhead != nullptr, n);
   if (small_front(n)) launch_small_front(f, s);
-  else if (by_model) launch_lprep(f, h->w.lbkt, h->w.lcnt, nb_front, s);  // buckets by model piece
+  else if (by_model) launch_lprep(f, h->w.lbkt, h->w.lrank, h->w.lcnt, nb_front, s);  // buckets by model piece
   else launch_prep(f, nb_front, s);
   bool resized = false;
   if (replay) {
@@ -783,7 +783,7 @@ int update(gpma *h, const uint64_t *ins, uint64_t n_ins, const uint64_t *del, ui
     {
       Phase ph(h->prof, GPMA_PROF_SORT, s);
       if (by_model) {
-        launch_lfront_sort(f, h->w.lbkt, h->w.lcnt, h->w.lcur, nb_front, s);
+        launch_lfront_sort(f, h->w.lbkt, h->w.lrank, h->w.lcnt, nb_front, s);
         launch_front_search(f, nb_front, s);
       } else if (!small_front(n)) {
         launch_front(f, nb_front, s);

@@ -274,6 +274,45 @@ __device__ __forceinline__ int32_t model_route(const ModelHead &m, const Piece *
   return (int32_t)a - 1;
 }
 
+// model_route of Q keys at once (their dependent loads in flight together);
+// bucket[q] = the piece, 0 when the key lies below every boundary or !act[q]
+template <int Q>
+__device__ __forceinline__ void model_route_lockstep(const ModelHead &m, const Piece *__restrict__ pieces,
+                                                     const uint64_t (&k)[Q], const bool (&act)[Q],
+                                                     uint32_t (&bucket)[Q]) {
+  const uint32_t *rt = model_radix(pieces);
+  uint32_t a[Q], b[Q];
+#pragma unroll
+  for (int q = 0; q < Q; q++) {
+    const uint32_t r = model_prefix(m, k[q]);
+    a[q] = act[q] ? __ldg(rt + r) : 0u;
+    b[q] = act[q] ? __ldg(rt + r + 1) : 0u;
+  }
+  for (;;) {
+    uint32_t mid[Q];
+    uint64_t kb[Q];
+    bool any = false;
+#pragma unroll
+    for (int q = 0; q < Q; q++) {
+      mid[q] = (a[q] + b[q]) >> 1;
+      kb[q] = 0;
+      if (a[q] < b[q]) {
+        kb[q] = __ldg(&pieces[mid[q]].kb);
+        any = true;
+      }
+    }
+    if (!any) break;
+#pragma unroll
+    for (int q = 0; q < Q; q++) {
+      if (a[q] >= b[q]) continue;
+      if (kb[q] <= k[q]) a[q] = mid[q] + 1;
+      else b[q] = mid[q];
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < Q; q++) bucket[q] = a[q] ? a[q] - 1 : 0u;
+}
+
 // eff(j) <= k ?
 __device__ __forceinline__ bool eff_at_most(const uint64_t *__restrict__ F, uint64_t nleaves, uint64_t j, uint64_t k) {
   for (; j < nleaves; ++j) {

@@ -68,7 +68,7 @@ struct Work {
   uint32_t *rs;       // front_scratch_words(cap) words for the radix front end
   uint16_t *lbkt;     // model-bucketed front end: bucket (model piece) of every key
   uint32_t *lcnt;     // kPieces + 1 bucket counts, then offsets
-  uint32_t *lcur;     // kPieces scatter cursors
+  uint32_t *lrank;    // rank of every key among the keys of its bucket
   uint32_t cap;       // capacity of the per-key arrays
 };
 
@@ -91,14 +91,15 @@ uint64_t front_scratch_words(uint64_t nb);  // size of FrontArgs::rs for batches
 // The model-bucketed front end of a learned handle (large batches, inside a captured
 // graph): launch_lprep (direct, reads the batch) validates and compresses every key
 // and counts it in its bucket (the model piece its key routes to; the top key bits
-// before the model is trained); in the graph, launch_lfront_sort turns the counts into
-// offsets, scatters the words into their buckets and sorts every bucket (in shared
+// before the model is trained), keeping its rank there; in the graph,
+// launch_lfront_sort turns the counts into offsets, places every word at its bucket's
+// offset plus its rank and sorts every bucket (in shared
 // memory up to kLSortMax words, else in place); launch_front_search then finishes as
 // after the radix passes (launch_front_radix), which plain handles keep.
 constexpr uint32_t kLSortMax = 4096;  // words of the largest bucket sorted in shared memory
 bool learned_front(const PrepArgs &a, bool has_model, uint64_t n);
-void launch_lprep(const FrontArgs &f, uint16_t *bkt, uint32_t *cnt, uint64_t nb, cudaStream_t s);
-void launch_lfront_sort(const FrontArgs &f, const uint16_t *bkt, uint32_t *cnt, uint32_t *cur, uint64_t nb,
+void launch_lprep(const FrontArgs &f, uint16_t *bkt, uint32_t *rank, uint32_t *cnt, uint64_t nb, cudaStream_t s);
+void launch_lfront_sort(const FrontArgs &f, const uint16_t *bkt, const uint32_t *rank, uint32_t *cnt, uint64_t nb,
                         cudaStream_t s);
 void launch_front_radix(const FrontArgs &f, uint64_t nb, cudaStream_t s);
 void launch_front_search(const FrontArgs &f, uint64_t nb, cudaStream_t s);

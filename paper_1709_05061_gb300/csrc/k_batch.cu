@@ -82,7 +82,9 @@ __device__ __forceinline__ void init_batch_body(const Blk &bk, Ctl *ctl, uint32_
   }
 }
 
-__global__ void k_init_batch(Ctl *ctl, uint32_t *hist, uint32_t nhist, uint32_t n) { init_batch_body(GridIdx{}, ctl, hist, nhist, n); }
+__global__ void k_init_batch(Ctl *ctl, uint32_t *hist, uint32_t nhist, uint32_t n) {
+  init_batch_body(GridIdx{}, ctl, hist, nhist, n);
+}
 
 // Sort tiles (blockDim * ITEMS keys) tile, tile + nblocks, ... of a block:
 // validation, compression, each tile's first-pass digit counts (column-major:
@@ -202,7 +204,10 @@ __global__ void __launch_bounds__(256) k_rcolscan(uint32_t *__restrict__ H, uint
 // need no block barrier).  O[d * T + t]: where the tile's keys of digit d start.
 // With Hn, every key also counts its next-pass digit in its destination tile.
 template <int ITEMS, class Blk>
-__device__ __forceinline__ void rscatter_body(const Blk &bk, const uint64_t *__restrict__ src, uint64_t *__restrict__ dst, const uint32_t *__restrict__ O, uint32_t *__restrict__ Hn, uint32_t T, uint32_t shift, uint32_t nshift, uint32_t dbits, const Ctl *ctl) {
+__device__ __forceinline__ void rscatter_body(const Blk &bk, const uint64_t *__restrict__ src,
+                                              uint64_t *__restrict__ dst, const uint32_t *__restrict__ O,
+                                              uint32_t *__restrict__ Hn, uint32_t T, uint32_t shift, uint32_t nshift,
+                                              uint32_t dbits, const Ctl *ctl) {
   __shared__ uint32_t wcnt[kSortThreads / 32][256];
   __shared__ uint32_t gbase[256];
   __shared__ uint32_t ltile[256];  // digit totals of the tile, then their exclusive prefix
@@ -304,7 +309,9 @@ template <int ITEMS>
 __global__ void __launch_bounds__(kSortThreads) k_rscatter(const uint64_t *__restrict__ src,
                                                            uint64_t *__restrict__ dst, const uint32_t *__restrict__ O,
                                                            uint32_t *__restrict__ Hn, uint32_t T, uint32_t shift,
-                                                           uint32_t nshift, uint32_t dbits, const Ctl *ctl) { rscatter_body<ITEMS>(GridIdx{}, src, dst, O, Hn, T, shift, nshift, dbits, ctl); }
+                                                           uint32_t nshift, uint32_t dbits, const Ctl *ctl) {
+  rscatter_body<ITEMS>(GridIdx{}, src, dst, O, Hn, T, shift, nshift, dbits, ctl);
+}
 
 // ---- small batches: the whole front end in one block ---------------------------------------
 // Sort word = (compressed key without tag) << 1 | tag.  Inserts (tag 0) order
@@ -332,7 +339,13 @@ __device__ __forceinline__ uint32_t sampled_leaf_search(const uint64_t *__restri
 }
 
 template <class Blk>
-__device__ __forceinline__ void small_front_body(const Blk &bk, const PrepArgs &a, const uint64_t *__restrict__ ins, const uint64_t *__restrict__ del, Ctl *ctl, const uint64_t *__restrict__ F, uint64_t nleaves, uint64_t *__restrict__ ukey, uint8_t *__restrict__ utag, uint32_t *__restrict__ uleaf, uint32_t *__restrict__ run_start, uint32_t *__restrict__ run_leaf, const ModelHead *mhead, const Piece *__restrict__ mpieces, uint32_t P, uint32_t S) {
+__device__ __forceinline__ void small_front_body(const Blk &bk, const PrepArgs &a, const uint64_t *__restrict__ ins,
+                                                 const uint64_t *__restrict__ del, Ctl *ctl,
+                                                 const uint64_t *__restrict__ F, uint64_t nleaves,
+                                                 uint64_t *__restrict__ ukey, uint8_t *__restrict__ utag,
+                                                 uint32_t *__restrict__ uleaf, uint32_t *__restrict__ run_start,
+                                                 uint32_t *__restrict__ run_leaf, const ModelHead *mhead,
+                                                 const Piece *__restrict__ mpieces, uint32_t P, uint32_t S) {
   extern __shared__ uint64_t sk[];           // P sort words
   uint64_t *sw = sk + P;                     // P survivor words
   uint64_t *cv = sw + P;                     // S compacted sampled pivots
@@ -472,7 +485,10 @@ __global__ void __launch_bounds__(1024) k_small_front(PrepArgs a, const uint64_t
                                                       uint64_t *__restrict__ ukey, uint8_t *__restrict__ utag,
                                                       uint32_t *__restrict__ uleaf, uint32_t *__restrict__ run_start,
                                                       uint32_t *__restrict__ run_leaf, const ModelHead *mhead,
-                                                      const Piece *__restrict__ mpieces, uint32_t P, uint32_t S) { small_front_body(GridIdx{}, a, ins, del, ctl, F, nleaves, ukey, utag, uleaf, run_start, run_leaf, mhead, mpieces, P, S); }
+                                                      const Piece *__restrict__ mpieces, uint32_t P, uint32_t S) {
+  small_front_body(GridIdx{}, a, ins, del, ctl, F, nleaves, ukey, utag, uleaf, run_start, run_leaf, mhead, mpieces, P,
+                   S);
+}
 
 // ---- unique/cancel, leaf search, run heads and compaction (after the radix passes) ------------
 // Per-block survivor summaries of the sorted words (256 Q words a block).
@@ -491,7 +507,10 @@ struct TileSums {
 // previous one has), the leaf of every survivor (reading R4), and the block's
 // summary.
 template <int Q, class Blk>
-__device__ __forceinline__ void rsearch_body(const Blk &bk, const PrepArgs &a, const uint64_t *__restrict__ sorted, uint32_t *__restrict__ lfull, const uint64_t *__restrict__ F, uint64_t nleaves, const TileSums &ts, uint32_t ntiles, Ctl *ctl, const ModelHead *mhead, const Piece *__restrict__ mpieces) {
+__device__ __forceinline__ void rsearch_body(const Blk &bk, const PrepArgs &a, const uint64_t *__restrict__ sorted,
+                                             uint32_t *__restrict__ lfull, const uint64_t *__restrict__ F,
+                                             uint64_t nleaves, const TileSums &ts, uint32_t ntiles, Ctl *ctl,
+                                             const ModelHead *mhead, const Piece *__restrict__ mpieces) {
   __shared__ uint32_t sl[(kSearchThreads * Q)];
   __shared__ uint32_t s_surv, s_hin, s_first, s_last;
   if (ctl->err) return;
@@ -520,7 +539,8 @@ __device__ __forceinline__ void rsearch_body(const Blk &bk, const PrepArgs &a, c
     for (int q = 0; q < Q; q++) {
       const uint32_t e = e0 + q;
       const uint64_t wq = w[q + 1], kq = wq & ~kTagBit;
-      kept[q] = e < n && ((wq & kTagBit) ? (e == 0 || (w[q] & ~kTagBit) != kq) : (e + 1 == n || (w[q + 2] & ~kTagBit) != kq));
+      kept[q] = e < n && ((wq & kTagBit) ? (e == 0 || (w[q] & ~kTagBit) != kq)
+                                         : (e + 1 == n || (w[q + 2] & ~kTagBit) != kq));
       key[q] = kept[q] ? expand(wq, a) : 0ull;
     }
     uint32_t miss = 0;
@@ -571,13 +591,16 @@ __global__ void __launch_bounds__(kSearchThreads) k_rsearch(PrepArgs a, const ui
                                                             uint32_t *__restrict__ lfull,
                                                             const uint64_t *__restrict__ F, uint64_t nleaves,
                                                             TileSums ts, Ctl *ctl, const ModelHead *mhead,
-                                                            const Piece *__restrict__ mpieces) { rsearch_body<Q>(GridIdx{}, a, sorted, lfull, F, nleaves, ts, gridDim.x, ctl, mhead, mpieces); }
+                                                            const Piece *__restrict__ mpieces) {
+  rsearch_body<Q>(GridIdx{}, a, sorted, lfull, F, nleaves, ts, gridDim.x, ctl, mhead, mpieces);
+}
 
 // Survivor and run-head offsets of every block of k_rsearch: exclusive scans over
 // the blocks; a block's first survivor starts a run unless the last survivor of
 // the nearest earlier block with survivors has the same leaf.  One block of 1024.
 template <class Blk>
-__device__ __forceinline__ void toffsets_body(const Blk &bk, const TileSums &ts, uint32_t nt, Ctl *ctl, uint32_t *__restrict__ run_start) {
+__device__ __forceinline__ void toffsets_body(const Blk &bk, const TileSums &ts, uint32_t nt, Ctl *ctl,
+                                              uint32_t *__restrict__ run_start) {
   __shared__ uint32_t wsum[33];
   __shared__ uint32_t s_last[1024];  // last survivor leaf of each thread's blocks
   __shared__ int32_t s_idx[1024];    // nearest thread <= t whose blocks hold a survivor, -1 if none
@@ -651,11 +674,17 @@ __device__ __forceinline__ void toffsets_body(const Blk &bk, const TileSums &ts,
 }
 
 __global__ void __launch_bounds__(1024) k_toffsets(TileSums ts, uint32_t nt, Ctl *ctl,
-                                                   uint32_t *__restrict__ run_start) { toffsets_body(GridIdx{}, ts, nt, ctl, run_start); }
+                                                   uint32_t *__restrict__ run_start) {
+  toffsets_body(GridIdx{}, ts, nt, ctl, run_start);
+}
 
 // survivors and run heads of every block to their places, Q words per thread
 template <int Q, class Blk>
-__device__ __forceinline__ void twrite_body(const Blk &bk, const PrepArgs &a, const uint64_t *__restrict__ sorted, const uint32_t *__restrict__ lfull, const TileSums &ts, uint32_t ntiles, uint64_t *__restrict__ ukey, uint8_t *__restrict__ utag, uint32_t *__restrict__ uleaf, uint32_t *__restrict__ run_start, uint32_t *__restrict__ run_leaf, const Ctl *ctl) {
+__device__ __forceinline__ void twrite_body(const Blk &bk, const PrepArgs &a, const uint64_t *__restrict__ sorted,
+                                            const uint32_t *__restrict__ lfull, const TileSums &ts, uint32_t ntiles,
+                                            uint64_t *__restrict__ ukey, uint8_t *__restrict__ utag,
+                                            uint32_t *__restrict__ uleaf, uint32_t *__restrict__ run_start,
+                                            uint32_t *__restrict__ run_leaf, const Ctl *ctl) {
   __shared__ uint32_t wsum[33];
   __shared__ uint32_t sl[(kSearchThreads * Q)];
   if (ctl->err) return;
@@ -663,7 +692,8 @@ __device__ __forceinline__ void twrite_body(const Blk &bk, const PrepArgs &a, co
   for (uint32_t b = bk.x(); b < ntiles; b += bk.n()) {
     if (ts.surv[b] == 0) continue;  // the same for the whole block
     const uint32_t base = b * (kSearchThreads * Q);
-    for (uint32_t i = t; i < (kSearchThreads * Q); i += kSearchThreads) sl[i] = base + i < n ? lfull[base + i] : kNoLeaf;
+    for (uint32_t i = t; i < (kSearchThreads * Q); i += kSearchThreads)
+      sl[i] = base + i < n ? lfull[base + i] : kNoLeaf;
     __syncthreads();
     uint32_t keep = 0, head = 0;
 #pragma unroll
@@ -703,7 +733,9 @@ __global__ void __launch_bounds__(kSearchThreads) k_twrite(PrepArgs a, const uin
                                                            uint64_t *__restrict__ ukey, uint8_t *__restrict__ utag,
                                                            uint32_t *__restrict__ uleaf,
                                                            uint32_t *__restrict__ run_start,
-                                                           uint32_t *__restrict__ run_leaf, const Ctl *ctl) { twrite_body<Q>(GridIdx{}, a, sorted, lfull, ts, gridDim.x, ukey, utag, uleaf, run_start, run_leaf, ctl); }
+                                                           uint32_t *__restrict__ run_leaf, const Ctl *ctl) {
+  twrite_body<Q>(GridIdx{}, a, sorted, lfull, ts, gridDim.x, ukey, utag, uleaf, run_start, run_leaf, ctl);
+}
 
 // ---- model-bucketed front end (learned handles) ----------------------------------------------
 // The model's pieces split the keys into kPieces ordered ranges whose sizes follow
@@ -717,44 +749,56 @@ __global__ void __launch_bounds__(kSearchThreads) k_twrite(PrepArgs a, const uin
 // (key, tag) order of a sort word (tag in bit 63, at most 62 key bits)
 __device__ __forceinline__ uint64_t word_order(uint64_t w) { return ((w & ~kTagBit) << 1) | (w >> 63); }
 
-// validation and compression as in k_prep, and the bucket of every key
+// validation and compression as in k_prep, the bucket of every key, and its rank
+// among the keys of its bucket (the order of those ranks is arbitrary: the bucket
+// is sorted afterwards)
 template <int ITEMS>
 __global__ void __launch_bounds__(kSortThreads) k_lprep(PrepArgs a, const uint64_t *__restrict__ ins,
                                                         const uint64_t *__restrict__ del, uint64_t *__restrict__ out,
-                                                        uint16_t *__restrict__ bkt, uint32_t *__restrict__ cnt,
-                                                        Ctl *ctl, const ModelHead *mhead,
-                                                        const Piece *__restrict__ mpieces) {
+                                                        uint16_t *__restrict__ bkt, uint32_t *__restrict__ rank,
+                                                        uint32_t *__restrict__ cnt, Ctl *ctl,
+                                                        const ModelHead *mhead, const Piece *__restrict__ mpieces) {
   const ModelHead hd = *mhead;
   const uint32_t top = a.sbits > 12 ? a.sbits - 12 : 0;  // key-bit buckets: kPieces = 2^12
   const uint32_t n = a.n_ins + a.n_del;
+  uint64_t key[ITEMS], w[ITEMS];
+  bool act[ITEMS];
   bool bad = false;
 #pragma unroll
   for (int r = 0; r < ITEMS; r++) {
     const uint32_t i = blockIdx.x * (kSortThreads * ITEMS) + r * kSortThreads + threadIdx.x;
-    if (i >= n) break;
+    act[r] = false;
+    key[r] = 0;
+    w[r] = 0;
+    if (i >= n) continue;
     const uint32_t tag = i >= a.n_ins;
-    const uint64_t key = tag ? del[i - a.n_ins] : ins[i];
-    const uint64_t src = key >> 32, dst = key & 0xFFFFFFFFull;
+    key[r] = tag ? del[i - a.n_ins] : ins[i];
+    const uint64_t src = key[r] >> 32, dst = key[r] & 0xFFFFFFFFull;
     const bool ok = src < a.V && dst < a.V;
     bad |= !ok;
-    const uint64_t w = ok ? compress(key, tag, a) : 0ull;
-    out[i] = w;
-    uint32_t b;
-    if (hd.valid) {
-      const int32_t pi = ok ? model_route(hd, mpieces, key) : 0;
-      b = pi < 0 ? 0u : (uint32_t)pi;
-    } else {
-      b = (uint32_t)((w & ~kTagBit) >> top);
-    }
-    bkt[i] = (uint16_t)b;
-    atomicAdd(&cnt[b], 1u);
+    w[r] = ok ? compress(key[r], tag, a) : 0ull;
+    out[i] = w[r];
+    act[r] = ok;
+  }
+  uint32_t b[ITEMS];
+  if (hd.valid) {
+    model_route_lockstep<ITEMS>(hd, mpieces, key, act, b);
+  } else {
+#pragma unroll
+    for (int r = 0; r < ITEMS; r++) b[r] = (uint32_t)((w[r] & ~kTagBit) >> top);
+  }
+#pragma unroll
+  for (int r = 0; r < ITEMS; r++) {
+    const uint32_t i = blockIdx.x * (kSortThreads * ITEMS) + r * kSortThreads + threadIdx.x;
+    if (i >= n) continue;
+    bkt[i] = (uint16_t)b[r];
+    rank[i] = atomicAdd(&cnt[b[r]], 1u);
   }
   if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(&ctl->err, kErrKey);
 }
 
-// bucket counts -> offsets (cnt, cnt[kPieces] = all) and scatter cursors (cur)
-__global__ void __launch_bounds__(1024) k_lscan(const Ctl *ctl, uint32_t *__restrict__ cnt,
-                                                uint32_t *__restrict__ cur) {
+// bucket counts -> offsets (cnt[kPieces] = all)
+__global__ void __launch_bounds__(1024) k_lscan(const Ctl *ctl, uint32_t *__restrict__ cnt) {
   __shared__ uint32_t wsum[33];
   if (ctl->err) return;  // nothing of the batch is applied
   const uint32_t t = threadIdx.x;
@@ -770,17 +814,18 @@ __global__ void __launch_bounds__(1024) k_lscan(const Ctl *ctl, uint32_t *__rest
 #pragma unroll
   for (uint32_t q = 0; q < kPer; q++) {
     cnt[t * kPer + q] = run;
-    cur[t * kPer + q] = run;
     run += v[q];
   }
   if (t == 0) cnt[kPieces] = total;
 }
 
+// every word to its bucket's offset plus its rank
 template <int ITEMS>
 __global__ void __launch_bounds__(kSortThreads) k_lscatter(const uint64_t *__restrict__ src,
                                                            const uint16_t *__restrict__ bkt,
-                                                           uint32_t *__restrict__ cur, uint64_t *__restrict__ dst,
-                                                           Ctl *ctl) {
+                                                           const uint32_t *__restrict__ rank,
+                                                           const uint32_t *__restrict__ off,
+                                                           uint64_t *__restrict__ dst, Ctl *ctl) {
   if (ctl->err) return;
   const uint32_t n = ctl->n;
 #pragma unroll
@@ -788,7 +833,7 @@ __global__ void __launch_bounds__(kSortThreads) k_lscatter(const uint64_t *__res
     const uint32_t i = blockIdx.x * (kSortThreads * ITEMS) + r * kSortThreads + threadIdx.x;
     if (i >= n) break;
     const uint32_t b = bkt[i];
-    const uint32_t pos = b < kPieces ? atomicAdd(&cur[b], 1u) : n;
+    const uint32_t pos = b < kPieces ? off[b] + rank[i] : n;
     if (pos < n) dst[pos] = src[i];
     else atomicOr(&ctl->err, kErrInternal);  // cannot happen when the counts are consistent
   }
@@ -968,26 +1013,25 @@ bool learned_front(const PrepArgs &a, bool has_model, uint64_t n) {
   return !a.raw && !a.allow_guards && has_model && a.sbits <= 62 && !small_front(n);
 }
 
-void launch_lprep(const FrontArgs &f, uint16_t *bkt, uint32_t *cnt, uint64_t nb, cudaStream_t s) {
+void launch_lprep(const FrontArgs &f, uint16_t *bkt, uint32_t *rank, uint32_t *cnt, uint64_t nb, cudaStream_t s) {
   const PrepArgs &a = f.prep;
   const uint64_t n = (uint64_t)a.n_ins + a.n_del;
   cudaMemsetAsync(cnt, 0, sizeof(uint32_t) * (kPieces + 1), s);
   note_launch();
   k_init_batch<<<1, 256, 0, s>>>(f.ctl, f.hist, a.npass * 256u, (uint32_t)n);
   note_launch();
-  k_lprep<kSortItems><<<front_tiles(nb), kSortThreads, 0, s>>>(a, f.ins, f.del, f.bufA, bkt, cnt, f.ctl, f.mhead,
-                                                                f.mpieces);
+  k_lprep<kSortItems><<<front_tiles(nb), kSortThreads, 0, s>>>(a, f.ins, f.del, f.bufA, bkt, rank, cnt, f.ctl,
+                                                                f.mhead, f.mpieces);
 }
 
-void launch_lfront_sort(const FrontArgs &f, const uint16_t *bkt, uint32_t *cnt, uint32_t *cur, uint64_t nb,
+void launch_lfront_sort(const FrontArgs &f, const uint16_t *bkt, const uint32_t *rank, uint32_t *cnt, uint64_t nb,
                         cudaStream_t s) {
   note_launch();
-  k_lscan<<<1, 1024, 0, s>>>(f.ctl, cnt, cur);
-  const uint32_t *off = cnt;
+  k_lscan<<<1, 1024, 0, s>>>(f.ctl, cnt);
   note_launch();
-  k_lscatter<kSortItems><<<front_tiles(nb), kSortThreads, 0, s>>>(f.bufA, bkt, cur, f.bufB, f.ctl);
+  k_lscatter<kSortItems><<<front_tiles(nb), kSortThreads, 0, s>>>(f.bufA, bkt, rank, cnt, f.bufB, f.ctl);
   note_launch();
-  k_lsort<<<kPieces, 256, 0, s>>>(f.bufB, sorted_words(f), off, f.ctl);
+  k_lsort<<<kPieces, 256, 0, s>>>(f.bufB, sorted_words(f), cnt, f.ctl);
 }
 
 bool search_wide(uint64_t n) { return search_per(n) == 4; }

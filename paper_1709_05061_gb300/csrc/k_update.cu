@@ -45,7 +45,8 @@ __device__ __forceinline__ WarpBufs warp_bufs(unsigned char *smem, uint32_t per_
 
 // ---- level 0: one warp per touched leaf ------------------------------------------------------
 template <class Blk>
-__device__ __forceinline__ void leaf_pass_body(const Blk &bk, const Geo &g, Ctl *ctl, const Work &w, uint32_t per_warp, int rest_only) {
+__device__ __forceinline__ void leaf_pass_body(const Blk &bk, const Geo &g, Ctl *ctl, const Work &w, uint32_t per_warp,
+                                               int rest_only) {
   extern __shared__ __align__(16) unsigned char smem[];
   if (ctl->err) return;
   if (rest_only && ctl->nlong == 0) return;
@@ -177,7 +178,9 @@ __device__ __forceinline__ void leaf_pass_body(const Blk &bk, const Geo &g, Ctl 
   }
 }
 
-__global__ void k_leaf_pass(Geo g, Ctl *ctl, Work w, uint32_t per_warp, int rest_only) { leaf_pass_body(GridIdx{}, g, ctl, w, per_warp, rest_only); }
+__global__ void k_leaf_pass(Geo g, Ctl *ctl, Work w, uint32_t per_warp, int rest_only) {
+  leaf_pass_body(GridIdx{}, g, ctl, w, per_warp, rest_only);
+}
 
 // ---- level 0 for runs longer than kLongRun (bulk loads) -----------------------------------------
 // Phase A, a warp per 32 consecutive keys: the presence filter against the
@@ -954,7 +957,9 @@ __device__ __forceinline__ void deg_batch_body(const Blk &bk, const Geo &g, cons
   }
 }
 
-__global__ void __launch_bounds__(256) k_deg_batch(Geo g, const Ctl *ctl, Work w) { deg_batch_body(GridIdx{}, g, ctl, w); }
+__global__ void __launch_bounds__(256) k_deg_batch(Geo g, const Ctl *ctl, Work w) {
+  deg_batch_body(GridIdx{}, g, ctl, w);
+}
 
 void launch_leaf64(const Geo &g, Ctl *ctl, const Work &w, uint32_t n, cudaStream_t s) {
   note_launch();
