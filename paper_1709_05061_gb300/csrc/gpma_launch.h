@@ -91,9 +91,9 @@ uint64_t front_scratch_words(uint64_t nb);  // size of FrontArgs::rs for batches
 // The model-bucketed front end of a learned handle (large batches, inside a captured
 // graph): launch_lprep (direct, reads the batch) validates and compresses every key
 // and counts it in its bucket (the model piece its key routes to; the top key bits
-// before the model is trained), keeping its rank there; in the graph,
-// launch_lfront_sort turns the counts into offsets, places every word at its bucket's
-// offset plus its rank and sorts every bucket (in shared
+// before the model is trained), keeping its rank there, and turns the counts into
+// offsets; in the graph, launch_lfront_sort places every word at its bucket's offset
+// plus its rank and sorts every bucket (in shared
 // memory up to kLSortMax words, else in place); launch_front_search then finishes as
 // after the radix passes (launch_front_radix), which plain handles keep.
 constexpr uint32_t kLSortMax = 4096;  // words of the largest bucket sorted in shared memory

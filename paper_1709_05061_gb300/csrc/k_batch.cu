@@ -33,6 +33,8 @@ constexpr uint32_t kSortTile = kSortThreads * kSortItems;
 constexpr uint32_t kSearchThreads = 256;
 constexpr uint64_t kSearchWideFrom = 1ull << 19;
 constexpr uint32_t kPrepDone = 7;       // Ctl::ticket slot counting finished prep blocks
+constexpr uint32_t kSearchDone = 6;     // ... finished search blocks
+constexpr uint32_t kLPrepDone = 5;      // ... finished blocks of the model-bucketed prep
 
 // ---- key compression -----------------------------------------------------------------
 // Graph mode: word = (src << db) | d with d = dst, or d = V for a guard (so a
@@ -586,14 +588,6 @@ __device__ __forceinline__ void rsearch_body(const Blk &bk, const PrepArgs &a, c
   }
 }
 
-template <int Q>
-__global__ void __launch_bounds__(kSearchThreads) k_rsearch(PrepArgs a, const uint64_t *__restrict__ sorted,
-                                                            uint32_t *__restrict__ lfull,
-                                                            const uint64_t *__restrict__ F, uint64_t nleaves,
-                                                            TileSums ts, Ctl *ctl, const ModelHead *mhead,
-                                                            const Piece *__restrict__ mpieces) {
-  rsearch_body<Q>(GridIdx{}, a, sorted, lfull, F, nleaves, ts, gridDim.x, ctl, mhead, mpieces);
-}
 
 // Survivor and run-head offsets of every block of k_rsearch: exclusive scans over
 // the blocks; a block's first survivor starts a run unless the last survivor of
@@ -606,15 +600,16 @@ __device__ __forceinline__ void toffsets_body(const Blk &bk, const TileSums &ts,
   __shared__ int32_t s_idx[1024];    // nearest thread <= t whose blocks hold a survivor, -1 if none
   __shared__ int32_t s_wmax[32];
   if (ctl->err) return;
-  const uint32_t t = threadIdx.x, per = (nt + 1023) / 1024, b0 = t * per;
+  const uint32_t t = threadIdx.x, per = (nt + blockDim.x - 1) / blockDim.x, b0 = t * per;
+  const uint32_t nw = blockDim.x >> 5;
   uint32_t sv = 0, lastleaf = kNoLeaf;
   for (uint32_t q = 0; q < per; q++) {
     const uint32_t b = b0 + q;
     if (b >= nt) break;
-    const uint32_t c = ts.surv[b];
+    const uint32_t c = __ldcg(ts.surv + b);  // written by other blocks (L2, not this block's L1)
     if (c) {
       sv += c;
-      lastleaf = ts.last[b];
+      lastleaf = __ldcg(ts.last + b);
     }
   }
   s_last[t] = lastleaf;
@@ -629,7 +624,7 @@ __device__ __forceinline__ void toffsets_body(const Blk &bk, const TileSums &ts,
   if (lane == 31) s_wmax[wid] = v;
   __syncthreads();
   if (wid == 0) {
-    int32_t x = s_wmax[lane];
+    int32_t x = lane < nw ? s_wmax[lane] : -1;
 #pragma unroll
     for (uint32_t o = 1; o < 32; o <<= 1) {
       const int32_t u = __shfl_up_sync(0xFFFFFFFFu, x, o);
@@ -647,11 +642,11 @@ __device__ __forceinline__ void toffsets_body(const Blk &bk, const TileSums &ts,
   for (uint32_t q = 0; q < per; q++) {
     const uint32_t b = b0 + q;
     if (b >= nt) break;
-    if (!ts.surv[b]) continue;
-    const uint32_t hf = (prevleaf == kNoLeaf || prevleaf != ts.first[b]) ? 1u : 0u;
+    if (!__ldcg(ts.surv + b)) continue;
+    const uint32_t hf = (prevleaf == kNoLeaf || prevleaf != __ldcg(ts.first + b)) ? 1u : 0u;
     ts.hfirst[b] = hf;
-    hc += ts.hin[b] + hf;
-    prevleaf = ts.last[b];
+    hc += __ldcg(ts.hin + b) + hf;
+    prevleaf = __ldcg(ts.last + b);
   }
   uint32_t m, nr;
   uint32_t so = block_excl_scan(sv, wsum, &m);
@@ -661,9 +656,10 @@ __device__ __forceinline__ void toffsets_body(const Blk &bk, const TileSums &ts,
     if (b >= nt) break;
     ts.soff[b] = so;
     ts.hoff[b] = ho;
-    if (ts.surv[b]) {
-      so += ts.surv[b];
-      ho += ts.hin[b] + ts.hfirst[b];
+    const uint32_t c = __ldcg(ts.surv + b);
+    if (c) {
+      so += c;
+      ho += __ldcg(ts.hin + b) + ts.hfirst[b];
     }
   }
   if (t == 0) {
@@ -676,6 +672,28 @@ __device__ __forceinline__ void toffsets_body(const Blk &bk, const TileSums &ts,
 __global__ void __launch_bounds__(1024) k_toffsets(TileSums ts, uint32_t nt, Ctl *ctl,
                                                    uint32_t *__restrict__ run_start) {
   toffsets_body(GridIdx{}, ts, nt, ctl, run_start);
+}
+
+// Unique/cancel, leaf search and block summaries (rsearch_body); the last block to
+// finish then computes every block's survivor and run-head offsets (what k_toffsets
+// does, without a launch of its own).
+template <int Q>
+__global__ void __launch_bounds__(kSearchThreads) k_rsearch(PrepArgs a, const uint64_t *__restrict__ sorted,
+                                                            uint32_t *__restrict__ lfull,
+                                                            const uint64_t *__restrict__ F, uint64_t nleaves,
+                                                            TileSums ts, Ctl *ctl, const ModelHead *mhead,
+                                                            const Piece *__restrict__ mpieces,
+                                                            uint32_t *__restrict__ run_start) {
+  __shared__ uint32_t s_done;
+  rsearch_body<Q>(GridIdx{}, a, sorted, lfull, F, nleaves, ts, gridDim.x, ctl, mhead, mpieces);
+  if (ctl->err) return;  // the same for every block: nothing of the batch is applied
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) s_done = atomicAdd(&ctl->ticket[kSearchDone], 1u) == gridDim.x - 1;
+  __syncthreads();
+  if (!s_done) return;
+  __threadfence();
+  toffsets_body(GridIdx{}, ts, gridDim.x, ctl, run_start);
 }
 
 // survivors and run heads of every block to their places, Q words per thread
@@ -751,7 +769,7 @@ __device__ __forceinline__ uint64_t word_order(uint64_t w) { return ((w & ~kTagB
 
 // validation and compression as in k_prep, the bucket of every key, and its rank
 // among the keys of its bucket (the order of those ranks is arbitrary: the bucket
-// is sorted afterwards)
+// is sorted afterwards); the last block turns the bucket counts into offsets
 template <int ITEMS>
 __global__ void __launch_bounds__(kSortThreads) k_lprep(PrepArgs a, const uint64_t *__restrict__ ins,
                                                         const uint64_t *__restrict__ del, uint64_t *__restrict__ out,
@@ -795,18 +813,21 @@ __global__ void __launch_bounds__(kSortThreads) k_lprep(PrepArgs a, const uint64
     rank[i] = atomicAdd(&cnt[b[r]], 1u);
   }
   if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(&ctl->err, kErrKey);
-}
-
-// bucket counts -> offsets (cnt[kPieces] = all)
-__global__ void __launch_bounds__(1024) k_lscan(const Ctl *ctl, uint32_t *__restrict__ cnt) {
+  // the last block to finish turns the counts into offsets (cnt[kPieces] = all keys)
+  __shared__ uint32_t s_done;
   __shared__ uint32_t wsum[33];
-  if (ctl->err) return;  // nothing of the batch is applied
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) s_done = atomicAdd(&ctl->ticket[kLPrepDone], 1u) == gridDim.x - 1;
+  __syncthreads();
+  if (!s_done) return;
+  __threadfence();
+  constexpr uint32_t kPer = kPieces / kSortThreads;
   const uint32_t t = threadIdx.x;
-  constexpr uint32_t kPer = kPieces / 1024;
   uint32_t v[kPer], loc = 0;
 #pragma unroll
   for (uint32_t q = 0; q < kPer; q++) {
-    v[q] = cnt[t * kPer + q];
+    v[q] = __ldcg(cnt + t * kPer + q);
     loc += v[q];
   }
   uint32_t total;
@@ -987,12 +1008,10 @@ void launch_front_search(const FrontArgs &f, uint64_t nb, cudaStream_t s) {
   note_launch();
   if (wide)
     k_rsearch<4><<<T1, kSearchThreads, 0, s>>>(a, src, f.lfull, f.geo->F, f.geo->nleaves, ts, f.ctl, f.mhead,
-                                               f.mpieces);
+                                               f.mpieces, f.run_start);
   else
     k_rsearch<1><<<T1, kSearchThreads, 0, s>>>(a, src, f.lfull, f.geo->F, f.geo->nleaves, ts, f.ctl, f.mhead,
-                                               f.mpieces);
-  note_launch();
-  k_toffsets<<<1, 1024, 0, s>>>(ts, T1, f.ctl, f.run_start);
+                                               f.mpieces, f.run_start);
   note_launch();
   if (wide)
     k_twrite<4><<<T1, kSearchThreads, 0, s>>>(a, src, f.lfull, ts, f.ukey, f.utag, f.uleaf, f.run_start,
@@ -1026,8 +1045,6 @@ void launch_lprep(const FrontArgs &f, uint16_t *bkt, uint32_t *rank, uint32_t *c
 
 void launch_lfront_sort(const FrontArgs &f, const uint16_t *bkt, const uint32_t *rank, uint32_t *cnt, uint64_t nb,
                         cudaStream_t s) {
-  note_launch();
-  k_lscan<<<1, 1024, 0, s>>>(f.ctl, cnt);
   note_launch();
   k_lscatter<kSortItems><<<front_tiles(nb), kSortThreads, 0, s>>>(f.bufA, bkt, rank, cnt, f.bufB, f.ctl);
   note_launch();
