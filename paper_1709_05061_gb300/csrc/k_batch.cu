@@ -860,18 +860,57 @@ __global__ void __launch_bounds__(kSortThreads) k_lscatter(const uint64_t *__res
   }
 }
 
-// One bucket per block, sorted by (key, tag): in shared memory (bitonic) up to
-// kLSortMax words; a larger bucket (many new edges of one row, or key-bit buckets)
-// in place in dst with the bitonic network whose comparators all put the smaller
-// word first, positions past the bucket counting as +infinity (so a comparator
-// that reaches past it does nothing).
+// Buckets of up to kLWarpMax words: one warp per bucket (eight a block), bitonic
+// sort of (key, tag) in the warp's own shared memory, warp synchronisation only.
+constexpr uint32_t kLWarpMax = 512;
+__global__ void __launch_bounds__(256) k_lsort_warp(const uint64_t *__restrict__ src, uint64_t *__restrict__ dst,
+                                                    const uint32_t *__restrict__ off, Ctl *ctl) {
+  __shared__ uint64_t sk[8][kLWarpMax];
+  if (ctl->err) return;
+  const uint32_t lane = lane_id(), w = threadIdx.x >> 5;
+  const uint32_t bucket = blockIdx.x * 8 + w;
+  const uint32_t o0 = off[bucket], nb = off[bucket + 1] - o0;
+  if (nb == 0 || nb > kLWarpMax) return;  // larger buckets: k_lsort
+  if (o0 + nb > ctl->n) {                  // cannot happen: the offsets count the batch's words
+    if (lane == 0) atomicOr(&ctl->err, kErrInternal);
+    return;
+  }
+  uint64_t *k = sk[w];
+  uint32_t P = 1;
+  while (P < nb) P <<= 1;
+  for (uint32_t i = lane; i < P; i += 32) k[i] = i < nb ? word_order(src[o0 + i]) : ~0ull;  // padding sorts last
+  __syncwarp();
+  for (uint32_t kk = 2; kk <= P; kk <<= 1) {
+    for (uint32_t j = kk >> 1; j > 0; j >>= 1) {
+      for (uint32_t i = lane; i < P / 2; i += 32) {
+        const uint32_t lo = ((i & ~(j - 1)) << 1) | (i & (j - 1)), hi = lo + j;
+        const uint64_t x = k[lo], y = k[hi];
+        if ((x > y) == ((lo & kk) == 0)) {
+          k[lo] = y;
+          k[hi] = x;
+        }
+      }
+      __syncwarp();
+    }
+  }
+  for (uint32_t i = lane; i < nb; i += 32) {
+    const uint64_t sw = k[i];
+    dst[o0 + i] = (sw >> 1) | ((sw & 1ull) << 63);
+  }
+}
+
+// Buckets above kLWarpMax words, one block per bucket: bitonic sort in shared memory
+// up to kLSortMax words; a larger bucket (many new edges of one row, or key-bit
+// buckets) in place in dst with the bitonic network whose comparators all put the
+// smaller word first, positions past the bucket counting as +infinity (so a
+// comparator that reaches past it does nothing).
 __global__ void __launch_bounds__(256) k_lsort(const uint64_t *__restrict__ src, uint64_t *__restrict__ dst,
                                                const uint32_t *__restrict__ off, Ctl *ctl) {
   __shared__ uint64_t sk[kLSortMax];
   if (ctl->err) return;
   const uint32_t t = threadIdx.x, nt = blockDim.x;
   const uint32_t o0 = off[blockIdx.x], nb = off[blockIdx.x + 1] - o0;
-  if (nb == 0) return;
+  if (nb <= kLWarpMax) return;  // sorted by k_lsort_warp
   if (o0 + nb > ctl->n) {  // cannot happen: the offsets count the batch's words
     if (t == 0) atomicOr(&ctl->err, kErrInternal);
     return;
@@ -1047,6 +1086,8 @@ void launch_lfront_sort(const FrontArgs &f, const uint16_t *bkt, const uint32_t 
                         cudaStream_t s) {
   note_launch();
   k_lscatter<kSortItems><<<front_tiles(nb), kSortThreads, 0, s>>>(f.bufA, bkt, rank, cnt, f.bufB, f.ctl);
+  note_launch();
+  k_lsort_warp<<<kPieces / 8, 256, 0, s>>>(f.bufB, sorted_words(f), cnt, f.ctl);
   note_launch();
   k_lsort<<<kPieces, 256, 0, s>>>(f.bufB, sorted_words(f), cnt, f.ctl);
 }
