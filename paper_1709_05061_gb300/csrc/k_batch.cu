@@ -891,15 +891,88 @@ __global__ void __launch_bounds__(kSortThreads) k_lscatter(const uint64_t *__res
   }
 }
 
-// Buckets of up to kLWarpMax words: one warp per bucket (eight a block), bitonic
-// sort of (key, tag) in the warp's own shared memory, warp synchronisation only.
-// (Measured, serialised: 1e5 keys over 4096 buckets, ~24 a bucket, 13 us for both
-// sort kernels against 18 us with a block per bucket; at ~244 a bucket a warp per
-// bucket took 52 us against 47 us, so larger buckets go to the block sort.)
-constexpr uint32_t kLWarpMax = 64;
+// Buckets of up to kLWarpMax words: one warp per bucket (eight a block). The warp
+// holds the bucket padded to P = 32 E words, E consecutive words a lane (moved there
+// through the warp's shared memory, so that the global loads and stores stay
+// coalesced), and runs the bitonic network on registers: comparators inside a lane's
+// E words directly, the others against the partner lane by shuffles, with no shared
+// memory and no synchronisation inside the network.
+constexpr uint32_t kLWarpMax = 512;
+constexpr uint32_t kLWarpPad = kLWarpMax + kLWarpMax / 16;  // word i at i + i / E (E <= 16)
+
+__device__ __forceinline__ uint64_t word_unorder(uint64_t sw) { return (sw >> 1) | ((sw & 1ull) << 63); }
+
+template <uint32_t E>
+__device__ __forceinline__ void lsort_warp_regs(const uint64_t *__restrict__ src, uint64_t *__restrict__ dst,
+                                                uint32_t nb, uint64_t *s, uint32_t lane) {
+  constexpr uint32_t P = 32u * E;
+  // the padding puts both the striped (32 r + lane) and the blocked (E lane + r) index
+  // of one access on distinct bank pairs within each half warp (up to a 2-way overlap)
+  uint64_t v[E];
+  if (E == 1) {
+    v[0] = lane < nb ? word_order(src[lane]) : ~0ull;  // padding sorts last
+  } else {
+#pragma unroll
+    for (uint32_t r = 0; r < E; r++) {
+      const uint32_t i = 32u * r + lane;
+      s[i + i / E] = i < nb ? word_order(src[i]) : ~0ull;
+    }
+    __syncwarp();
+#pragma unroll
+    for (uint32_t r = 0; r < E; r++) {
+      const uint32_t i = E * lane + r;
+      v[r] = s[i + i / E];
+    }
+  }
+  // element e = E lane + r; merge size k, stride j; of the pair (e, e ^ j) the element
+  // with (e & j) == 0 keeps the smaller word when (e & k) == 0, else the larger
+  for (uint32_t k = 2; k <= P; k <<= 1) {
+    const bool asc_lane = ((E * lane) & k) == 0;
+    for (uint32_t j = k >> 1; j >= E; j >>= 1) {  // partner in lane ^ (j / E), same r
+      const uint32_t lm = j / E;
+      const bool keep_min = ((lane & lm) == 0) == asc_lane;  // here k >= 2E: r adds no bit of k
+#pragma unroll
+      for (uint32_t r = 0; r < E; r++) {
+        const uint64_t o = __shfl_xor_sync(0xFFFFFFFFu, v[r], lm);
+        const bool less = o < v[r];
+        v[r] = (less == keep_min) ? o : v[r];
+      }
+    }
+#pragma unroll
+    for (uint32_t j = E / 2; j > 0; j >>= 1) {  // partner r ^ j in the same lane
+      if (j >= k) continue;
+#pragma unroll
+      for (uint32_t r = 0; r < E; r++) {
+        if (r & j) continue;
+        const bool asc = asc_lane && (r & k) == 0;
+        const uint64_t x = v[r], y = v[r | j];
+        const bool sw = (x > y) == asc;
+        v[r] = sw ? y : x;
+        v[r | j] = sw ? x : y;
+      }
+    }
+  }
+  if (E == 1) {
+    if (lane < nb) dst[lane] = word_unorder(v[0]);
+  } else {
+    __syncwarp();  // every lane has read its words before they are overwritten
+#pragma unroll
+    for (uint32_t r = 0; r < E; r++) {
+      const uint32_t i = E * lane + r;
+      s[i + i / E] = v[r];
+    }
+    __syncwarp();
+#pragma unroll
+    for (uint32_t r = 0; r < E; r++) {
+      const uint32_t i = 32u * r + lane;
+      if (i < nb) dst[i] = word_unorder(s[i + i / E]);
+    }
+  }
+}
+
 __global__ void __launch_bounds__(256) k_lsort_warp(const uint64_t *__restrict__ src, uint64_t *__restrict__ dst,
                                                     const uint32_t *__restrict__ off, Ctl *ctl) {
-  __shared__ uint64_t sk[8][kLWarpMax];
+  __shared__ uint64_t sk[8][kLWarpPad];
   if (ctl->err) return;
   const uint32_t lane = lane_id(), w = threadIdx.x >> 5;
   const uint32_t bucket = blockIdx.x * 8 + w;
@@ -909,94 +982,80 @@ __global__ void __launch_bounds__(256) k_lsort_warp(const uint64_t *__restrict__
     if (lane == 0) atomicOr(&ctl->err, kErrInternal);
     return;
   }
-  uint64_t *k = sk[w];
-  uint32_t P = 1;
-  while (P < nb) P <<= 1;
-  for (uint32_t i = lane; i < P; i += 32) k[i] = i < nb ? word_order(src[o0 + i]) : ~0ull;  // padding sorts last
-  __syncwarp();
-  for (uint32_t kk = 2; kk <= P; kk <<= 1) {
-    for (uint32_t j = kk >> 1; j > 0; j >>= 1) {
-      for (uint32_t i = lane; i < P / 2; i += 32) {
-        const uint32_t lo = ((i & ~(j - 1)) << 1) | (i & (j - 1)), hi = lo + j;
-        const uint64_t x = k[lo], y = k[hi];
-        if ((x > y) == ((lo & kk) == 0)) {
-          k[lo] = y;
-          k[hi] = x;
-        }
-      }
-      __syncwarp();
-    }
-  }
-  for (uint32_t i = lane; i < nb; i += 32) {
-    const uint64_t sw = k[i];
-    dst[o0 + i] = (sw >> 1) | ((sw & 1ull) << 63);
-  }
+  const uint64_t *in = src + o0;
+  uint64_t *out = dst + o0;
+  if (nb <= 32) lsort_warp_regs<1>(in, out, nb, sk[w], lane);
+  else if (nb <= 64) lsort_warp_regs<2>(in, out, nb, sk[w], lane);
+  else if (nb <= 128) lsort_warp_regs<4>(in, out, nb, sk[w], lane);
+  else if (nb <= 256) lsort_warp_regs<8>(in, out, nb, sk[w], lane);
+  else lsort_warp_regs<16>(in, out, nb, sk[w], lane);
 }
 
-// Buckets above kLWarpMax words, one block per bucket: bitonic sort in shared memory
-// up to kLSortMax words; a larger bucket (many new edges of one row, or key-bit
-// buckets) in place in dst with the bitonic network whose comparators all put the
-// smaller word first, positions past the bucket counting as +infinity (so a
-// comparator that reaches past it does nothing).
+// Buckets above kLWarpMax words, a block per bucket (the grid strides over the
+// buckets, most of which the warp sort has taken): bitonic sort in shared memory up
+// to kLSortMax words; a larger bucket (many new edges of one row, or key-bit buckets)
+// in place in dst with the bitonic network whose comparators all put the smaller word
+// first, positions past the bucket counting as +infinity (so a comparator that reaches
+// past it does nothing).
 __global__ void __launch_bounds__(256) k_lsort(const uint64_t *__restrict__ src, uint64_t *__restrict__ dst,
                                                const uint32_t *__restrict__ off, Ctl *ctl) {
   __shared__ uint64_t sk[kLSortMax];
   if (ctl->err) return;
   const uint32_t t = threadIdx.x, nt = blockDim.x;
-  const uint32_t o0 = off[blockIdx.x], nb = off[blockIdx.x + 1] - o0;
-  if (nb <= kLWarpMax) return;  // sorted by k_lsort_warp
-  if (o0 + nb > ctl->n) {  // cannot happen: the offsets count the batch's words
-    if (t == 0) atomicOr(&ctl->err, kErrInternal);
-    return;
-  }
-  uint32_t P = 1;
-  while (P < nb) P <<= 1;
-  if (nb <= kLSortMax) {
-    for (uint32_t i = t; i < P; i += nt) sk[i] = i < nb ? word_order(src[o0 + i]) : ~0ull;  // padding sorts last
+  for (uint32_t bucket = blockIdx.x; bucket < kPieces; bucket += gridDim.x) {
+    const uint32_t o0 = off[bucket], nb = off[bucket + 1] - o0;
+    if (nb <= kLWarpMax) continue;  // sorted by k_lsort_warp
+    if (o0 + nb > ctl->n) {         // cannot happen: the offsets count the batch's words
+      if (t == 0) atomicOr(&ctl->err, kErrInternal);
+      return;
+    }
+    uint32_t P = 1;
+    while (P < nb) P <<= 1;
+    if (nb <= kLSortMax) {
+      for (uint32_t i = t; i < P; i += nt) sk[i] = i < nb ? word_order(src[o0 + i]) : ~0ull;  // padding sorts last
+      __syncthreads();
+      for (uint32_t k = 2; k <= P; k <<= 1) {
+        for (uint32_t j = k >> 1; j > 0; j >>= 1) {
+          for (uint32_t i = t; i < P / 2; i += nt) {
+            const uint32_t lo = ((i & ~(j - 1)) << 1) | (i & (j - 1)), hi = lo + j;
+            const uint64_t x = sk[lo], y = sk[hi];
+            if ((x > y) == ((lo & k) == 0)) {
+              sk[lo] = y;
+              sk[hi] = x;
+            }
+          }
+          __syncthreads();
+        }
+      }
+      for (uint32_t i = t; i < nb; i += nt) dst[o0 + i] = word_unorder(sk[i]);
+      __syncthreads();  // the next bucket overwrites sk
+      continue;
+    }
+    uint64_t *d = dst + o0;
+    if (src != dst)
+      for (uint32_t i = t; i < nb; i += nt) d[i] = src[o0 + i];
     __syncthreads();
     for (uint32_t k = 2; k <= P; k <<= 1) {
       for (uint32_t j = k >> 1; j > 0; j >>= 1) {
         for (uint32_t i = t; i < P / 2; i += nt) {
-          const uint32_t lo = ((i & ~(j - 1)) << 1) | (i & (j - 1)), hi = lo + j;
-          const uint64_t x = sk[lo], y = sk[hi];
-          if ((x > y) == ((lo & k) == 0)) {
-            sk[lo] = y;
-            sk[hi] = x;
+          uint32_t lo, hi;
+          if (j == (k >> 1)) {  // first step of a merge: mirror inside the block of k
+            lo = (i / j) * k + (i % j);
+            hi = (i / j) * k + k - 1 - (i % j);
+          } else {
+            lo = ((i & ~(j - 1)) << 1) | (i & (j - 1));
+            hi = lo + j;
+          }
+          if (hi < nb) {
+            const uint64_t x = d[lo], y = d[hi];
+            if (word_order(x) > word_order(y)) {
+              d[lo] = y;
+              d[hi] = x;
+            }
           }
         }
         __syncthreads();
       }
-    }
-    for (uint32_t i = t; i < nb; i += nt) {
-      const uint64_t sw = sk[i];
-      dst[o0 + i] = (sw >> 1) | ((sw & 1ull) << 63);
-    }
-    return;
-  }
-  uint64_t *d = dst + o0;
-  if (src != dst)
-    for (uint32_t i = t; i < nb; i += nt) d[i] = src[o0 + i];
-  __syncthreads();
-  for (uint32_t k = 2; k <= P; k <<= 1) {
-    for (uint32_t j = k >> 1; j > 0; j >>= 1) {
-      for (uint32_t i = t; i < P / 2; i += nt) {
-        uint32_t lo, hi;
-        if (j == (k >> 1)) {  // first step of a merge: mirror inside the block of k
-          lo = (i / j) * k + (i % j);
-          hi = (i / j) * k + k - 1 - (i % j);
-        } else {
-          lo = ((i & ~(j - 1)) << 1) | (i & (j - 1));
-          hi = lo + j;
-        }
-        if (hi < nb) {
-          const uint64_t x = d[lo], y = d[hi];
-          if (word_order(x) > word_order(y)) {
-            d[lo] = y;
-            d[hi] = x;
-          }
-        }
-      }
-      __syncthreads();
     }
   }
 }
@@ -1120,6 +1179,19 @@ void launch_lprep(const FrontArgs &f, uint16_t *bkt, uint32_t *rank, uint32_t *c
                                                                          f.ctl, f.mhead, f.mpieces);
 }
 
+// seven blocks of k_lsort fit an SM (32 KB of shared memory each)
+static uint32_t lsort_blocks() {
+  static uint32_t nblk = 0;
+  if (!nblk) {
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    nblk = sms > 0 ? 7u * (uint32_t)sms : 1024u;
+    if (nblk > kPieces) nblk = kPieces;
+  }
+  return nblk;
+}
+
 void launch_lfront_sort(const FrontArgs &f, const uint16_t *bkt, const uint32_t *rank, uint32_t *cnt, uint64_t nb,
                         cudaStream_t s) {
   note_launch();
@@ -1127,7 +1199,7 @@ void launch_lfront_sort(const FrontArgs &f, const uint16_t *bkt, const uint32_t 
   note_launch();
   k_lsort_warp<<<kPieces / 8, 256, 0, s>>>(f.bufB, sorted_words(f), cnt, f.ctl);
   note_launch();
-  k_lsort<<<kPieces, 256, 0, s>>>(f.bufB, sorted_words(f), cnt, f.ctl);
+  k_lsort<<<lsort_blocks(), 256, 0, s>>>(f.bufB, sorted_words(f), cnt, f.ctl);
 }
 
 bool search_wide(uint64_t n) { return search_per(n) == 4; }

@@ -96,8 +96,10 @@ def test_model_bucketed_sort():
     its graph for every batch, so the batches above the one-block size are sorted by
     bucketing on the model's pieces: layout and stats equal the oracle's at sizes
     from 4097 to 2^19 + 1 keys (with duplicates, cancellations, present inserts and
-    absent deletes), and for a batch crowding 20,000 new edges into one short row,
-    whose bucket is too large for shared memory and is sorted in place."""
+    absent deletes), for a batch crowding 20,000 new edges into one short row, whose
+    bucket is too large for shared memory and is sorted in place, and for one with
+    stars of 480 and 2000 new edges on other short rows (buckets near the largest one
+    a warp sorts in registers, and buckets for the block sort in shared memory)."""
     V = 1 << 16
     base = W.rmat_stream(16, 1_200_000, seed=63)
     rng = np.random.default_rng(63)
@@ -111,6 +113,11 @@ def test_model_bucketed_sort():
     hub = np.uint64(srcs[np.argmin(deg)])  # a short row: it lies within one or two model pieces
     star = (hub << np.uint64(32)) | rng.permutation(V)[:20_000].astype(np.uint64)
     batches.append((star, np.zeros(0, np.uint64)))
+    short = srcs[np.argsort(deg, kind="stable")[1:5]].astype(np.uint64)  # four more short rows
+    stars = [(s << np.uint64(32)) | rng.permutation(V)[:c].astype(np.uint64)
+             for s, c in zip(short, (480, 480, 480, 2000))]
+    ins, dels = mixed_batch(rng, V, live, 8000)
+    batches.append((rng.permutation(np.concatenate([ins] + stars)), dels))
     by_model = run_pair(V, batches, False)
     # every batch after the bulk load replays a graph: above the one-block size the model sorts it
     expect = [int(ins.size + dels.size > 4096) for ins, dels in batches[1:]]
