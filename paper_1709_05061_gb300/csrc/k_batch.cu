@@ -9,14 +9,23 @@
 //                 digit's global offset: where every tile's keys of that digit go
 //   k_rscatter    one tile per block: rank the keys by digit, write them to their
 //                 places, count the next pass's digits per destination tile
-//   k_rsearch     1024 sorted words per block: unique + insert/delete cancellation,
-//                 the leaf search of every survivor (learned model when trained,
-//                 else binary search; both give the same leaf), the block's
-//                 survivor and run-head counts
-//   k_toffsets    survivor and run-head offsets of every block (one block)
+//   or, for a handle with a trained position model, the model-bucketed sort:
+//   k_lprep       validate and compress as k_prep, route every key to its model
+//                 piece (its bucket) and take its rank in the bucket; the last block
+//                 turns the bucket counts into offsets
+//   k_lscatter    every word to its bucket's offset plus its rank
+//   k_lsort_warp  buckets of up to 512 words, one warp each, bitonic in registers
+//   k_lsort       the larger buckets, a block each (shared memory, or in place)
+//   then
+//   k_rsearch     256 or 1024 sorted words per block: unique + insert/delete
+//                 cancellation, the leaf search of every survivor (learned model when
+//                 trained, else binary search; both give the same leaf), the block's
+//                 survivor and run-head counts; the last block to finish turns them
+//                 into every block's offsets
 //   k_twrite      survivors and the heads of their runs of equal leaf to their places
 //   k_small_front all of the above in one block for batches of at most
 //                 kSmallBatch keys (bitonic sort in shared memory)
+//   k_m_*         the same stages as one launch over many handles
 #include "gpma_dev.cuh"
 #include "gpma_launch.h"
 #include "scan_dev.cuh"
@@ -669,14 +678,9 @@ __device__ __forceinline__ void toffsets_body(const Blk &bk, const TileSums &ts,
   }
 }
 
-__global__ void __launch_bounds__(1024) k_toffsets(TileSums ts, uint32_t nt, Ctl *ctl,
-                                                   uint32_t *__restrict__ run_start) {
-  toffsets_body(GridIdx{}, ts, nt, ctl, run_start);
-}
-
 // Unique/cancel, leaf search and block summaries (rsearch_body); the last block to
-// finish then computes every block's survivor and run-head offsets (what k_toffsets
-// does, without a launch of its own).
+// finish then computes every block's survivor and run-head offsets (toffsets_body,
+// without a launch of its own).
 template <int Q>
 __global__ void __launch_bounds__(kSearchThreads) k_rsearch(PrepArgs a, const uint64_t *__restrict__ sorted,
                                                             uint32_t *__restrict__ lfull,
