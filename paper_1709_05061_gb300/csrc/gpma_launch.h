@@ -168,7 +168,7 @@ void launch_pr_apply(const Geo &g, float damping, float *rank, uint64_t *y, uint
 // V each), the ranks when last, and dsum_out; partials >= nb * nparts.
 constexpr uint32_t kPbShift = 13, kPbMaxShift = 14;
 constexpr uint32_t kPbMaxBuckets = 4096;  // heads < kPbMaxBuckets << shift
-constexpr uint32_t kPbMaxChunks = 152 * 8, kPbTargetBlocks = 512, kPbMaxParts = 8;
+constexpr uint32_t kPbMaxChunks = 152 * 8, kPbTargetBlocks = 256, kPbMaxParts = 8;
 constexpr uint32_t kPbTile = 8192, kPbPlaceThreads = 512;  // placement: slots per tile, threads
 // more buckets than this: placement without staging (a staged tile of 8192 slots
 // then holds only about 8 edges of each bucket, too few to group the writes)

@@ -438,13 +438,14 @@ PbPlan pb_plan(const Geo &g) {
   if (G > kPbMaxChunks) G = kPbMaxChunks;
   p.G = (uint32_t)G;
   p.chunk = (npairs + G - 1) / G;
-  // blocks per bucket: a power of two (the cluster size), at most kPbMaxParts
+  // blocks per bucket: a power of two (the cluster size), at most kPbMaxParts, for
+  // a grid of about kPbTargetBlocks blocks of 1024 threads: one wave at two blocks
+  // an SM (measured at R-MAT scale 20, 8192-head buckets, one iteration alone:
+  // 2 blocks a bucket 0.0565 ms, 4 blocks 0.0598 ms, 8 blocks 0.074 ms, 1 block
+  // 0.068 ms; 512 threads with 4 blocks a bucket 0.072 ms)
   const uint32_t want = (kPbTargetBlocks + p.nb - 1) / p.nb;
   p.nparts = 1;
   while (p.nparts * 2 <= want && p.nparts * 2 <= kPbMaxParts) p.nparts *= 2;
-  // 1024 threads (measured at scale 20 with 8192-head buckets: 4 blocks a bucket
-  // 0.058 ms per iteration against 0.072 ms with 512 threads, 0.074 ms with 8
-  // blocks a bucket)
   p.threads = 1024;
   return p;
 }

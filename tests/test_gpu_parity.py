@@ -334,13 +334,14 @@ def test_pagerank_mid_size():
     assert np.array_equal(g.cc().cpu().numpy().view(np.uint32), o.cc())
 
 
-@pytest.mark.parametrize("V,n_edges,seed", [(1 << 16, 1_000_000, 8), (5000, 60_000, 3), (4097, 20_000, 4),
-                                            (1, 0, 0), (300, 0, 0)])
+@pytest.mark.parametrize("V,n_edges,seed", [(1 << 16, 1_000_000, 8), (1 << 19, 1_000_000, 9), (5000, 60_000, 3),
+                                            (4097, 20_000, 4), (1, 0, 0), (300, 0, 0)])
 def test_pagerank_bucketed_equals_push(V, n_edges, seed):
     """The bucketed sum pass (edges copied into head buckets of 8192, partial sums
     in shared memory) and the push pass (one L2 reduction per stored edge) add the
-    same fixed-point contributions, so their ranks agree bit for bit: on an R-MAT
-    graph with heavy heads, on vertex counts that leave a ragged last bucket, and on
+    same fixed-point contributions, so their ranks agree bit for bit: on R-MAT
+    graphs with heavy heads (8 buckets summed by clusters of 8 blocks, and 64 buckets
+    by clusters of 4), on vertex counts that leave a ragged last bucket, and on
     graphs without edges.  Both stay within the tolerance of the oracle."""
     if n_edges:
         scale = max(1, int(np.ceil(np.log2(V))))

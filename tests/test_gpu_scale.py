@@ -117,10 +117,10 @@ def test_pagerank_largest_bucketed_graph(V):
 
 @pytest.mark.parametrize("scale", [21, 22])
 def test_large_graph_analytics_match_oracle(scale):
-    """Graphs past 2^20 vertices take other branches of the analytics: at 2^21
-    vertices (256 head buckets of 8192) the bucketed PageRank runs clusters of two
-    blocks per bucket; at 2^22 (512 buckets) one block per bucket, and the
-    placement writes every edge straight to its bucket.  R-MAT with 2^(scale+1) distinct edges: layout slot for
+    """Graphs past 2^20 vertices take other branches of the analytics: from 2^21
+    vertices (256 head buckets of 8192) the bucketed PageRank runs one block per
+    bucket, and at 2^22 (512 buckets) the placement writes every edge straight to
+    its bucket.  R-MAT with 2^(scale+1) distinct edges: layout slot for
     slot, BFS from two sources and CC exactly, PageRank-20 (bucketed and push
     passes) within 1e-5 of the oracle's FP64 ranks, and the two passes bit for bit
     equal."""
