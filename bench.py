@@ -45,8 +45,8 @@ PROFILED_STEPS = 10
 # pass on the default workload (R-MAT scale 20, 16M-edge window, 2^25 slots), from one ncu
 # capture of each kernel as it stands (profiles/): push pass 285,246,720 read + 3,048,448
 # written; bucketed iteration (8192-head buckets, 2 blocks of 1024 threads a bucket)
-# 136,441,088 read + 2,805,760 written
-PR_PASS_TRAFFIC = {"k_pr_scatter": 288_295_168, "k_pb_iter": 139_246_848}
+# 136,487,424 read + 3,047,680 written
+PR_PASS_TRAFFIC = {"k_pr_scatter": 288_295_168, "k_pb_iter": 139_535_104}
 # the library buckets the edges for PageRank on graphs of at most 2^25 vertices
 PB_MAX_V = 1 << 25
 METRIC = "edge updates/sec vs batch size (+HBM GB/s frac); p50/p99 update+query latency"
