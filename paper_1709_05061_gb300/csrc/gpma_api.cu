@@ -1211,7 +1211,7 @@ int run_many(ManyCtx &mc, gpma_t const *handles, const uint64_t *const *d_ins, c
   pl.radix = add_plan(D, pl, np, 2432 + nb, wr, cr);
   pl.search[0] = add_plan(D, pl, np, 2432 + nb, w1, c1);
   pl.search[1] = add_plan(D, pl, np, 1216 + nb, w4, c4);
-  pl.leaf64 = add_plan(D, pl, np, 760 + nb, w64, c64);
+  pl.leaf64 = add_plan(D, pl, np, 608 + nb, w64, c64);
   pl.deg = add_plan(D, pl, np, 1216 + nb, wdeg, cdeg);
   pl.maxpass = maxpass;
   // the one-warp-per-leaf pass: one launch per block size (warps per block, 1..8);

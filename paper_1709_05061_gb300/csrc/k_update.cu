@@ -330,7 +330,7 @@ __global__ void k_long_b(Geo g, Ctl *ctl, Work w, uint32_t per_warp) { long_b_bo
 // Lane l holds slots 2l and 2l+1 of the leaf in registers (one 16-byte load),
 // lane i < len holds update i of the run; presence, deletes and ranks are warp
 // ballots.  The next run's leaf is loaded before the current one is processed.
-// 5 blocks of 256 threads an SM (48 registers): more runs in flight hide the leaf loads
+// 4 blocks of 256 threads an SM (64 registers)
 template <class Blk>
 __device__ __forceinline__ void leaf64_body(const Blk &bk, const Geo &g, Ctl *ctl, const Work &w) {
   __shared__ uint64_t sout[8][64];
@@ -342,23 +342,48 @@ __device__ __forceinline__ void leaf64_body(const Blk &bk, const Geo &g, Ctl *ct
   uint64_t acc_ins = 0, acc_del = 0;
   uint32_t acc_m0 = 0, acc_esc = 0, acc_long = 0;
   uint32_t r = bk.x() * 8 + wib;
-  uint32_t jn = 0, rsn = 0, ren = 0;
+  // a run's leaf and updates are loaded one run ahead, its leaf index and bounds two
+  // runs ahead, so that no load of an iteration waits on another
+  uint32_t jn = 0, rsn = 0, ren = 0, jm = 0, rsm = 0, rem = 0, tagn = 0;
+  uint64_t keyn = 0;
   ulonglong2 kn = make_ulonglong2(kEmpty, kEmpty);
   if (r < nruns) {
     jn = w.rleaf[r];
     rsn = w.run_start[r];
     ren = w.run_start[r + 1];
     kn = __ldcg(s2 + (uint64_t)jn * 32 + lane);
+    if (lane < ren - rsn) {
+      keyn = w.ukey[rsn + lane];
+      tagn = w.utag[rsn + lane];
+    }
+  }
+  if (r + nw < nruns) {
+    jm = w.rleaf[r + nw];
+    rsm = w.run_start[r + nw];
+    rem = w.run_start[r + nw + 1];
   }
   for (; r < nruns; r += nw) {
     const uint32_t j = jn, rs = rsn, re = ren;
     const uint64_t k0 = kn.x, k1 = kn.y;
+    const uint64_t ukey = keyn;  // update `lane` of the run (lanes below its length)
+    const uint32_t utag = tagn;
     const uint32_t rn = r + nw;
-    if (rn < nruns) {  // prefetch the next run's leaf (a different leaf: runs are distinct)
-      jn = w.rleaf[rn];
-      rsn = w.run_start[rn];
-      ren = w.run_start[rn + 1];
+    if (rn < nruns) {  // the next run's leaf (a different leaf: runs are distinct) and updates
+      jn = jm;
+      rsn = rsm;
+      ren = rem;
       kn = __ldcg(s2 + (uint64_t)jn * 32 + lane);
+      keyn = 0;
+      tagn = 0;
+      if (lane < ren - rsn) {
+        keyn = w.ukey[rsn + lane];
+        tagn = w.utag[rsn + lane];
+      }
+      if (rn + nw < nruns) {
+        jm = w.rleaf[rn + nw];
+        rsm = w.run_start[rn + nw];
+        rem = w.run_start[rn + nw + 1];
+      }
     }
     const uint32_t len = re - rs;
     if (len > 32) {
@@ -368,8 +393,8 @@ __device__ __forceinline__ void leaf64_body(const Blk &bk, const Geo &g, Ctl *ct
     if (len == 1 && !g.dual) {
       // one update (most runs of a large batch over a large array): every lane
       // reads it, no loop over the run; the same result as the general case below
-      const uint64_t ku = w.ukey[rs];
-      const bool del = w.utag[rs] != 0;
+      const uint64_t ku = __shfl_sync(0xFFFFFFFFu, ukey, 0);
+      const bool del = __shfl_sync(0xFFFFFFFFu, utag, 0) != 0;
       const bool m0 = k0 == ku, m1 = k1 == ku;
       const bool found = __any_sync(0xFFFFFFFFu, m0 || m1);
       const bool d0 = del && m0, d1 = del && m1;
@@ -424,8 +449,8 @@ __device__ __forceinline__ void leaf64_body(const Blk &bk, const Geo &g, Ctl *ct
       continue;
     }
     const bool act = lane < len;
-    const uint64_t key = act ? w.ukey[rs + lane] : 0ull;
-    const uint32_t tag = act ? (uint32_t)w.utag[rs + lane] : 0u;
+    const uint64_t key = act ? ukey : 0ull;
+    const uint32_t tag = act ? utag : 0u;
     const bool v0 = k0 != kEmpty, v1 = k1 != kEmpty;
     const uint32_t tbal = __ballot_sync(0xFFFFFFFFu, tag != 0);  // deletes of the run
     bool d0 = false, d1 = false;
@@ -511,7 +536,7 @@ __device__ __forceinline__ void leaf64_body(const Blk &bk, const Geo &g, Ctl *ct
   }
 }
 
-__global__ void __launch_bounds__(256, 5) k_leaf64(Geo g, Ctl *ctl, Work w) { leaf64_body(GridIdx{}, g, ctl, w); }
+__global__ void __launch_bounds__(256, 4) k_leaf64(Geo g, Ctl *ctl, Work w) { leaf64_body(GridIdx{}, g, ctl, w); }
 
 // ---- count tree, rebuilt only when some inserts did not fit their leaf ----------------------
 // Levels 1..h of the tree hold logical counts for the merge-level test: valid
@@ -963,7 +988,7 @@ __global__ void __launch_bounds__(256) k_deg_batch(Geo g, const Ctl *ctl, Work w
 
 void launch_leaf64(const Geo &g, Ctl *ctl, const Work &w, uint32_t n, cudaStream_t s) {
   note_launch();
-  k_leaf64<<<blocks_for(n, 8, 152 * 5), 256, 0, s>>>(g, ctl, w);  // one wave of resident blocks
+  k_leaf64<<<blocks_for(n, 8, 152 * 4), 256, 0, s>>>(g, ctl, w);  // one wave of resident blocks
 }
 
 void launch_leaf_rest(const Geo &g, Ctl *ctl, const Work &w, uint32_t n, bool rest_only, cudaStream_t s) {
@@ -993,7 +1018,7 @@ void launch_leaf_pass(const Geo &g, Ctl *ctl, const Work &w, uint32_t n, cudaStr
 }
 
 // ---- many handles: the level-0 stages as one launch over all of them ---------------------------
-__global__ void __launch_bounds__(256, 5) k_m_leaf64(const ManyDesc *d, uint32_t plan) {
+__global__ void __launch_bounds__(256, 4) k_m_leaf64(const ManyDesc *d, uint32_t plan) {
   const ManyItem *it;
   uint32_t sub, nb;
   if (!many_block(d, plan, &it, &sub, &nb)) return;
