@@ -576,7 +576,7 @@ bool capture_update(gpma *h, FrontArgs &f, uint32_t nb, bool stats, bool grow, G
   };
   if (learned_front(f.prep, h->mhead != nullptr, nb)) {  // sorted by bucketing on the model's pieces
     launch_lfront_sort(f, h->w.lbkt, h->w.lrank, h->w.lcnt, nb, gc.cap);
-    launch_front_search(f, nb, gc.cap);
+    launch_front_search(f, nb, gc.cap, h->w.lbkt);
   } else if (!small_front(nb)) {
     launch_front(f, nb, gc.cap);
   }
@@ -784,7 +784,7 @@ int update(gpma *h, const uint64_t *ins, uint64_t n_ins, const uint64_t *del, ui
       Phase ph(h->prof, GPMA_PROF_SORT, s);
       if (by_model) {
         launch_lfront_sort(f, h->w.lbkt, h->w.lrank, h->w.lcnt, nb_front, s);
-        launch_front_search(f, nb_front, s);
+        launch_front_search(f, nb_front, s, h->w.lbkt);
       } else if (!small_front(n)) {
         launch_front(f, nb_front, s);
       }

@@ -414,18 +414,27 @@ __device__ __forceinline__ void leaf_search_lockstep(const uint64_t *__restrict_
 // pieces of the entry), the piece's prediction and its bracket check together;
 // keys whose window is bracketed finish with one lock-step bisection inside it,
 // the others (a stale model) take learned_leaf_search alone.  Same leaves.
+// bucket (or nullptr): each key's bucket from model_route_lockstep (the sort by
+// model piece routed the keys already); it fixes the route's result up to the keys
+// before the first piece boundary, which share bucket 0 with the first piece.
 template <int Q>
 __device__ __forceinline__ uint32_t learned_search_lockstep(const ModelHead &m, const Piece *__restrict__ pieces,
                                                         const uint64_t *__restrict__ F, uint64_t nleaves,
                                                         const uint64_t (&k)[Q], const bool (&act)[Q],
-                                                        uint32_t (&out)[Q]) {
+                                                        uint32_t (&out)[Q], const uint16_t *bucket = nullptr) {
   const uint32_t *rt = model_radix(pieces);
-  uint32_t a[Q], b[Q];
+  uint32_t a[Q], b[Q];  // a: pieces whose boundary is <= k, once a = b
 #pragma unroll
   for (int q = 0; q < Q; q++) {
-    const uint32_t r = model_prefix(m, k[q]);
-    a[q] = act[q] ? __ldg(rt + r) : 0u;
-    b[q] = act[q] ? __ldg(rt + r + 1) : 0u;
+    if (bucket) {
+      const uint32_t bq = bucket[q];
+      a[q] = !act[q] ? 0u : (bq ? bq + 1u : (__ldg(&pieces[0].kb) <= k[q] ? 1u : 0u));
+      b[q] = a[q];
+    } else {
+      const uint32_t r = model_prefix(m, k[q]);
+      a[q] = act[q] ? __ldg(rt + r) : 0u;
+      b[q] = act[q] ? __ldg(rt + r + 1) : 0u;
+    }
   }
   for (;;) {  // last piece whose boundary is <= k
     uint32_t mid[Q];

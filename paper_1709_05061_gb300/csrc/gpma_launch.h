@@ -93,16 +93,19 @@ uint64_t front_scratch_words(uint64_t nb);  // size of FrontArgs::rs for batches
 // and counts it in its bucket (the model piece its key routes to; the top key bits
 // before the model is trained), keeping its rank there, and turns the counts into
 // offsets; in the graph, launch_lfront_sort places every word at its bucket's offset
-// plus its rank and sorts every bucket (in shared
-// memory up to kLSortMax words, else in place); launch_front_search then finishes as
-// after the radix passes (launch_front_radix), which plain handles keep.
+// plus its rank, sorts every bucket (in registers up to 512 words, in shared memory up
+// to kLSortMax, else in place) and leaves each sorted word's bucket in bkt;
+// launch_front_search (given bkt) then finishes as after the radix passes
+// (launch_front_radix), which plain handles keep.
 constexpr uint32_t kLSortMax = 4096;  // words of the largest bucket sorted in shared memory
 bool learned_front(const PrepArgs &a, bool has_model, uint64_t n);
 void launch_lprep(const FrontArgs &f, uint16_t *bkt, uint32_t *rank, uint32_t *cnt, uint64_t nb, cudaStream_t s);
-void launch_lfront_sort(const FrontArgs &f, const uint16_t *bkt, const uint32_t *rank, uint32_t *cnt, uint64_t nb,
+void launch_lfront_sort(const FrontArgs &f, uint16_t *bkt, const uint32_t *rank, uint32_t *cnt, uint64_t nb,
                         cudaStream_t s);
 void launch_front_radix(const FrontArgs &f, uint64_t nb, cudaStream_t s);
-void launch_front_search(const FrontArgs &f, uint64_t nb, cudaStream_t s);
+// spiece: each sorted word's model piece (the model-bucketed sort leaves it in its
+// bucket array), or nullptr: the learned search then routes every key itself
+void launch_front_search(const FrontArgs &f, uint64_t nb, cudaStream_t s, const uint16_t *spiece = nullptr);
 
 // k_update.cu
 // level 0: k_leaf64 (L = 64, runs of at most 32 keys), then the general pass (the

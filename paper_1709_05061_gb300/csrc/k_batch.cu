@@ -521,7 +521,8 @@ template <int Q, class Blk>
 __device__ __forceinline__ void rsearch_body(const Blk &bk, const PrepArgs &a, const uint64_t *__restrict__ sorted,
                                              uint32_t *__restrict__ lfull, const uint64_t *__restrict__ F,
                                              uint64_t nleaves, const TileSums &ts, uint32_t ntiles, Ctl *ctl,
-                                             const ModelHead *mhead, const Piece *__restrict__ mpieces) {
+                                             const ModelHead *mhead, const Piece *__restrict__ mpieces,
+                                             const uint16_t *__restrict__ spiece) {
   __shared__ uint32_t sl[(kSearchThreads * Q)];
   __shared__ uint32_t s_surv, s_hin, s_first, s_last;
   if (ctl->err) return;
@@ -555,8 +556,16 @@ __device__ __forceinline__ void rsearch_body(const Blk &bk, const PrepArgs &a, c
       key[q] = kept[q] ? expand(wq, a) : 0ull;
     }
     uint32_t miss = 0;
-    if (hd.valid) miss = learned_search_lockstep<Q>(hd, mpieces, F, nleaves, key, kept, leaf);
-    else leaf_search_lockstep<Q>(F, nleaves, key, kept, leaf);
+    if (hd.valid && spiece) {  // sorted by model piece: each word's bucket is known
+      uint16_t pb[Q];
+#pragma unroll
+      for (int q = 0; q < Q; q++) pb[q] = e0 + q < n ? spiece[e0 + q] : (uint16_t)0;
+      miss = learned_search_lockstep<Q>(hd, mpieces, F, nleaves, key, kept, leaf, pb);
+    } else if (hd.valid) {
+      miss = learned_search_lockstep<Q>(hd, mpieces, F, nleaves, key, kept, leaf);
+    } else {
+      leaf_search_lockstep<Q>(F, nleaves, key, kept, leaf);
+    }
 #pragma unroll
     for (int q = 0; q < Q; q++)
       if (!kept[q]) leaf[q] = kNoLeaf;
@@ -687,9 +696,10 @@ __global__ void __launch_bounds__(kSearchThreads) k_rsearch(PrepArgs a, const ui
                                                             const uint64_t *__restrict__ F, uint64_t nleaves,
                                                             TileSums ts, Ctl *ctl, const ModelHead *mhead,
                                                             const Piece *__restrict__ mpieces,
+                                                            const uint16_t *__restrict__ spiece,
                                                             uint32_t *__restrict__ run_start) {
   __shared__ uint32_t s_done;
-  rsearch_body<Q>(GridIdx{}, a, sorted, lfull, F, nleaves, ts, gridDim.x, ctl, mhead, mpieces);
+  rsearch_body<Q>(GridIdx{}, a, sorted, lfull, F, nleaves, ts, gridDim.x, ctl, mhead, mpieces, spiece);
   if (ctl->err) return;  // the same for every block: nothing of the batch is applied
   __threadfence();
   __syncthreads();
@@ -975,7 +985,8 @@ __device__ __forceinline__ void lsort_warp_regs(const uint64_t *__restrict__ src
 }
 
 __global__ void __launch_bounds__(256) k_lsort_warp(const uint64_t *__restrict__ src, uint64_t *__restrict__ dst,
-                                                    const uint32_t *__restrict__ off, Ctl *ctl) {
+                                                    const uint32_t *__restrict__ off, uint16_t *__restrict__ spiece,
+                                                    Ctl *ctl) {
   __shared__ uint64_t sk[8][kLWarpPad];
   if (ctl->err) return;
   const uint32_t lane = lane_id(), w = threadIdx.x >> 5;
@@ -986,6 +997,7 @@ __global__ void __launch_bounds__(256) k_lsort_warp(const uint64_t *__restrict__
     if (lane == 0) atomicOr(&ctl->err, kErrInternal);
     return;
   }
+  for (uint32_t i = lane; i < nb; i += 32) spiece[o0 + i] = (uint16_t)bucket;  // for the leaf search
   const uint64_t *in = src + o0;
   uint64_t *out = dst + o0;
   if (nb <= 32) lsort_warp_regs<1>(in, out, nb, sk[w], lane);
@@ -1002,7 +1014,8 @@ __global__ void __launch_bounds__(256) k_lsort_warp(const uint64_t *__restrict__
 // first, positions past the bucket counting as +infinity (so a comparator that reaches
 // past it does nothing).
 __global__ void __launch_bounds__(256) k_lsort(const uint64_t *__restrict__ src, uint64_t *__restrict__ dst,
-                                               const uint32_t *__restrict__ off, Ctl *ctl) {
+                                               const uint32_t *__restrict__ off, uint16_t *__restrict__ spiece,
+                                               Ctl *ctl) {
   __shared__ uint64_t sk[kLSortMax];
   if (ctl->err) return;
   const uint32_t t = threadIdx.x, nt = blockDim.x;
@@ -1013,6 +1026,7 @@ __global__ void __launch_bounds__(256) k_lsort(const uint64_t *__restrict__ src,
       if (t == 0) atomicOr(&ctl->err, kErrInternal);
       return;
     }
+    for (uint32_t i = t; i < nb; i += nt) spiece[o0 + i] = (uint16_t)bucket;  // for the leaf search
     uint32_t P = 1;
     while (P < nb) P <<= 1;
     if (nb <= kLSortMax) {
@@ -1132,7 +1146,7 @@ void launch_front_radix(const FrontArgs &f, uint64_t nb, cudaStream_t s) {
   }
 }
 
-void launch_front_search(const FrontArgs &f, uint64_t nb, cudaStream_t s) {
+void launch_front_search(const FrontArgs &f, uint64_t nb, cudaStream_t s, const uint16_t *spiece) {
   const PrepArgs &a = f.prep;
   const uint32_t T = front_tiles(nb);
   const uint64_t *src = sorted_words(f);
@@ -1144,10 +1158,10 @@ void launch_front_search(const FrontArgs &f, uint64_t nb, cudaStream_t s) {
   note_launch();
   if (wide)
     k_rsearch<4><<<T1, kSearchThreads, 0, s>>>(a, src, f.lfull, f.geo->F, f.geo->nleaves, ts, f.ctl, f.mhead,
-                                               f.mpieces, f.run_start);
+                                               f.mpieces, spiece, f.run_start);
   else
     k_rsearch<1><<<T1, kSearchThreads, 0, s>>>(a, src, f.lfull, f.geo->F, f.geo->nleaves, ts, f.ctl, f.mhead,
-                                               f.mpieces, f.run_start);
+                                               f.mpieces, spiece, f.run_start);
   note_launch();
   if (wide)
     k_twrite<4><<<T1, kSearchThreads, 0, s>>>(a, src, f.lfull, ts, f.ukey, f.utag, f.uleaf, f.run_start,
@@ -1196,14 +1210,15 @@ static uint32_t lsort_blocks() {
   return nblk;
 }
 
-void launch_lfront_sort(const FrontArgs &f, const uint16_t *bkt, const uint32_t *rank, uint32_t *cnt, uint64_t nb,
+void launch_lfront_sort(const FrontArgs &f, uint16_t *bkt, const uint32_t *rank, uint32_t *cnt, uint64_t nb,
                         cudaStream_t s) {
   note_launch();
   k_lscatter<kSortItems><<<front_tiles(nb), kSortThreads, 0, s>>>(f.bufA, bkt, rank, cnt, f.bufB, f.ctl);
   note_launch();
-  k_lsort_warp<<<kPieces / 8, 256, 0, s>>>(f.bufB, sorted_words(f), cnt, f.ctl);
+  // bkt, read by k_lscatter by batch position, then takes each sorted word's bucket
+  k_lsort_warp<<<kPieces / 8, 256, 0, s>>>(f.bufB, sorted_words(f), cnt, bkt, f.ctl);
   note_launch();
-  k_lsort<<<lsort_blocks(), 256, 0, s>>>(f.bufB, sorted_words(f), cnt, f.ctl);
+  k_lsort<<<lsort_blocks(), 256, 0, s>>>(f.bufB, sorted_words(f), cnt, bkt, f.ctl);
 }
 
 bool search_wide(uint64_t n) { return search_per(n) == 4; }
@@ -1271,7 +1286,8 @@ __global__ void __launch_bounds__(kSearchThreads) k_m_rsearch(const ManyDesc *d,
   if (!many_block(d, plan, &it, &sub, &nb) || it->small || it->wide != (Q == 4 ? 1u : 0u)) return;
   const uint64_t *sorted = (it->prep.npass & 1) ? it->bufB : it->bufA;
   rsearch_body<Q>(SubIdx{sub, nb}, it->prep, sorted, it->w.pleaf, it->g.F, it->g.nleaves,
-                  tile_sums(it->w.rs, it->T, it->T1), it->T1, it->ctl, it->mhead, it->mpieces);
+                  tile_sums(it->w.rs, it->T, it->T1), it->T1, it->ctl, it->mhead, it->mpieces,
+                  nullptr);
 }
 
 __global__ void __launch_bounds__(1024) k_m_toffsets(const ManyDesc *d, uint32_t plan) {
