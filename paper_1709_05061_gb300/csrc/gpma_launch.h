@@ -172,9 +172,13 @@ void launch_pr_apply(const Geo &g, float damping, float *rank, uint64_t *y, uint
 constexpr uint32_t kPbShift = 13, kPbMaxShift = 14;
 constexpr uint32_t kPbMaxBuckets = 4096;  // heads < kPbMaxBuckets << shift
 constexpr uint32_t kPbMaxChunks = 152 * 8, kPbTargetBlocks = 256, kPbMaxParts = 8;
-constexpr uint32_t kPbTile = 8192, kPbPlaceThreads = 512;  // placement: slots per tile, threads
-// more buckets than this: placement without staging (a staged tile of 8192 slots
-// then holds only about 8 edges of each bucket, too few to group the writes)
+// placement: slots per tile, threads (4096-slot tiles at 40 registers fit three blocks
+// an SM; measured at R-MAT scale 20 against 8192-slot tiles at two blocks an SM:
+// 0.38-0.41 against 0.42-0.45 ms of bucketing per call in the bench step)
+constexpr uint32_t kPbTile = 4096, kPbPlaceThreads = 512;
+// more buckets than this: placement without staging (a staged tile of 4096 slots,
+// about half of them edges, then holds fewer than 8 edges of each bucket, too few to
+// group the writes)
 constexpr uint32_t kPbStageMax = 256;
 struct PbPlan {
   uint32_t shift, nb, G, nparts, threads;  // 2^shift heads per bucket; threads per iteration block

@@ -228,7 +228,7 @@ __global__ void __launch_bounds__(256) k_pb_offsets(const uint32_t *__restrict__
 // within their bucket (shared-memory counters), the counts scanned, the edges
 // staged in bucket order in shared memory, and then written out so that the
 // edges of one bucket go to consecutive addresses.
-__global__ void __launch_bounds__(kPbPlaceThreads) k_pb_place(const ulonglong2 *__restrict__ s2, uint64_t npairs,
+__global__ void __launch_bounds__(kPbPlaceThreads, 3) k_pb_place(const ulonglong2 *__restrict__ s2, uint64_t npairs,
                                                               uint64_t chunk, uint32_t nb, uint32_t shift,
                                                               const uint64_t *__restrict__ off,
                                                               uint64_t *__restrict__ keys) {
